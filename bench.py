@@ -1,0 +1,328 @@
+"""Benchmark: points/s of the full hull (filter + device hull) on one or more GB300s.
+
+Default workload: the 1e8-point normal distribution (sigma 2^21, centred,
+rounded and clamped to [0, 2^24)), inputs resident in HBM (800 MB, larger than
+the 129 MB L2, so no flush is needed between steps).  One step = one ch_hull
+call (all stages).  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+With N > 1 (torchrun, one process per GPU) every rank runs an independent
+replica of the workload (the single-hull path has no data-parallel exchange
+on one GPU); value = all ranks' points / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+LAUNCHES_PER_HULL = 10   # init, pass1, finalize, pass2, 3 sort passes, plan, chain, stitch
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="normal_1e8")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--n", type=int, default=None, help="override the point count (testing)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_config(name, n):
+    from synth import workloads as W
+    kind, n0, seed = W.SINGLE[name]
+    desc = {
+        "normal": "isotropic normal, centre (2^23, 2^23), sigma 2^21, rounded, clamped to [0, 2^24)",
+        "ring": "ring: angle U[0, 2pi), radius 2^23 - U[0, 64), rounded, clamped",
+        "uniform": "uniform integers in [0, 2^24)^2",
+    }[kind]
+    return kind, (n or n0), seed, desc
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def source_sha(path):
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def traffic_from_profile(kernel, workload, n_bench):
+    """Per-launch DRAM bytes of `kernel` from its committed ncu summary, scaled to
+    the benchmark's point count; None when the kernel source changed since."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    m_n = re.search(r"points_per_launch:\s*([0-9.eE+]+)", text)
+    m_s = re.search(r"source_sha:\s*([0-9a-f]+)", text)
+    m_f = re.search(r"source_file:\s*(\S+)", text)
+    if not (m_t and m_s and m_f):
+        return None
+    if source_sha(os.path.join(ROOT, m_f.group(1))) != m_s.group(1):
+        return None
+    scale = n_bench / float(m_n.group(1)) if m_n else 1.0
+    return float(m_t.group(1)) * scale
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, reasons)."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_baseline(kind, seed, seconds):
+    """The oracle as it stands, single-threaded, on a bounded sample of the workload."""
+    import oracle
+    from synth import workloads as W
+    n = 2_000_000
+    pts = W.make(kind, n, seed)
+    oracle.hull(pts[:1000])
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.hull(pts)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return {"value": n * reps / el, "unit": "points/s", "cores": 1, "kind": "oracle",
+            "sample": f"{reps} x {n} points of the same {kind} distribution (seed {seed}), "
+                      f"single-threaded C Andrew monotone chain, {el:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    kind, n, seed, desc = workload_config(args.workload, args.n)
+    import oracle
+    from synth import workloads as W
+    sample = 1_000_000
+    pts = W.make(kind, sample, seed)
+    for _ in range(args.warmup):
+        oracle.hull(pts)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.hull(pts)
+    el = time.perf_counter() - t0
+    value = sample * args.steps / el
+    line = {
+        "impl": "reference", "metric": "points/s (filter+hull)", "value": value, "unit": "points/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": args.workload, "n": n, "distribution": desc,
+                   "reference_step": f"oracle on a {sample}-point sample of the workload"},
+        "cpu_baseline": {"value": value, "unit": "points/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{sample} points of the same {kind} distribution per step"},
+        "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from __graft_entry__ import build
+    build()
+    import paper_2209_12310_gb300 as ch
+    from synth import workloads as W
+
+    kind, n, seed, desc = workload_config(args.workload, args.n)
+    host = W.make(kind, n, seed)
+    pts = torch.from_numpy(host).cuda()
+    out_idx = torch.empty(n, dtype=torch.int32, device="cuda")
+    out_n = torch.empty(1, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+
+    def step():
+        ch.ch_hull(pts.data_ptr(), n, out_idx.data_ptr(), out_n.data_ptr(), sp)
+
+    ch.ch_reserve(n, 1, sp)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    h = int(out_n.item())
+    if h < 0:
+        raise SystemExit(f"hull failed: {ch.ch_strerror(h)}")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # Timed region: device events around exactly K steps; per-kernel events live.
+    ch.ch_profile_reset()
+    ch.ch_profile_enable(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ch.ch_profile_enable(False)
+    prof = ch.ch_profile_read()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n * args.steps / (ms / 1e3)
+
+    # Roofline of the dominant kernel (largest device time in the timed region).
+    survivors = None
+    peak, peak_src = peaks()
+    kern = max((k for k in prof if k in ("pass1_extremes", "pass2_filter", "sort", "hull_chains")),
+               key=lambda k: prof[k][1])
+    launches, tot = prof[kern]
+    avg_s = tot / launches / 1e3
+    algo = {"pass1_extremes": 8.0 * n, "pass2_filter": 8.0 * n}.get(kern)
+    roof = None
+    if algo is not None:
+        achieved = algo / avg_s / 1e9
+        roof = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": f"{peak_src} hbm_gbs",
+                "algorithmic_bytes_per_launch": algo, "avg_launch_ms": avg_s * 1e3,
+                "traffic": traffic_from_profile(kern, args.workload, n)}
+    kernels = {k: {"launches": v[0], "avg_ms": v[1] / max(v[0], 1)} for k, v in prof.items()}
+
+    # End to end through the host-buffer entry point: pinned input, H2D, hull, D2H.
+    import ctypes
+    pinned = torch.from_numpy(host).pin_memory()
+    out_host = torch.empty(n, dtype=torch.int32).pin_memory()
+    hn = ctypes.c_int64()
+    ch.ch_hull_host(pinned.data_ptr(), n, out_host.data_ptr(), ctypes.addressof(hn), sp)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        ch.ch_hull_host(pinned.data_ptr(), n, out_host.data_ptr(), ctypes.addressof(hn), sp)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * n * args.e2e_steps / e2e_s, "unit": "points/s",
+           "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 + 4 * int(hn.value),
+           "steps": args.e2e_steps, "entry_point": "ch_hull_host (pinned host buffers)"}
+
+    if rank == 0:
+        cpu = cpu_baseline(kind, seed, args.cpu_seconds) if world == 1 else None
+        line = {
+            "metric": "points/s (filter+hull, device-timed)", "value": value, "unit": "points/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "distribution": desc, "seed": seed,
+                       "hull_vertices": h, "l2": "inputs 800 MB per step > 129 MB L2 (no flush needed)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": roof, "kernels": kernels, "e2e": e2e, "cpu_baseline": cpu,
+            "gpu_launches": LAUNCHES_PER_HULL * args.steps, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,169 @@
+/*
+ * ch.h -- C ABI of the GB300 convex-hull library (libconvhull.so).
+ *
+ * The library computes the 2-D convex hull of a point set on one GPU with the
+ * filtering method of GPU heaphull (Keith, Ferrada, Navarro; Alg. 1 and
+ * Alg. 2): find the 8 directional extreme points, discard every point
+ * strictly inside the octagon they span, sort the survivors of each of the
+ * four corner queues, and build the hull of the survivors on the device.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Points are AoS float32 pairs (x0, y0, x1, y1, ...).  Every coordinate must
+ *   be an integer value in [0, 2^24) (the paper only says "floating point",
+ *   Alg. 2; integer values keep every predicate exact in int64).  A
+ *   coordinate outside that domain (fraction, negative, >= 2^24, NaN, Inf)
+ *   is a DATA error: it is detected on the device and reported through the
+ *   output count as CH_ERANGE (never by a trap or a fault).
+ * - "device" pointers are CUDA device (or managed) memory of the current
+ *   device; "host" pointers are ordinary or pinned host memory.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   Device entry points are stream-ordered and return as soon as the work is
+ *   enqueued; they never synchronise the host with the device, so a sequence
+ *   of calls can be captured in a CUDA graph (after ch_reserve, see below).
+ * - Return value: CH_OK when the work was enqueued, or a negative ch_status
+ *   for an error the host can see at call time (null pointer, bad size or
+ *   alignment, allocation or launch failure).  No C++ exception crosses the ABI.
+ * - The caller owns every buffer it passes.  The library owns an internal
+ *   workspace per (device, stream), grown on demand and freed by ch_release().
+ *   Calls on the SAME stream share that workspace in stream order; calls on
+ *   different streams use different workspaces and may overlap.
+ */
+#ifndef CONVHULL_CH_H
+#define CONVHULL_CH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CH_OK = 0,
+    CH_PENDING = 1,     /* ch_poll: request admitted, result not ready yet */
+    CH_EINVAL = -1,     /* bad argument (null pointer, negative size, alignment) */
+    CH_ERANGE = -2,     /* a coordinate is not an integer in [0, 2^24) */
+    CH_ENOMEM = -3,     /* device or host allocation failed / budget exceeded */
+    CH_ECUDA = -4,      /* a CUDA runtime call failed */
+    CH_ETIMEOUT = -5,   /* a bounded device-side wait gave up */
+    CH_EBUSY = -6       /* serving queue full; retry later */
+} ch_status;
+
+/* Largest point count of one hull (indices are int32). */
+#define CH_MAX_POINTS ((int64_t)0x7FFFFFF0)
+
+/*
+ * ch_hull -- convex hull of n points (Alg. 1's problem: P[1..n] in, the h hull
+ * points in counter-clockwise order out).
+ *   pts      device, 8-byte aligned, n*2 float32 (x, y interleaved).
+ *   n        0 <= n <= CH_MAX_POINTS.
+ *   out_idx  device int32, capacity n (h <= n).  On success holds the indices
+ *            of the strictly convex hull vertices, counter-clockwise, starting
+ *            at the lexicographically smallest (x, then y) vertex; points in
+ *            the interior of a hull edge are excluded; a vertex whose
+ *            coordinates occur several times is named by its lowest index.
+ *            All points collinear: [lex-min, lex-max]; all identical: [lowest index].
+ *   out_n    device int64*: the device writes h, or a negative ch_status when
+ *            the input holds a value outside the domain (CH_ERANGE) or a
+ *            device wait timed out (CH_ETIMEOUT).
+ * Returns CH_OK on enqueue.  Pass 1 and pass 2 of the filter each stream the
+ * points once (8 bytes per point); the hull stage touches only survivors.
+ */
+int ch_hull(const float* pts, int64_t n, int32_t* out_idx, int64_t* out_n, void* stream);
+
+/*
+ * ch_hull_batched -- k independent hulls in one set of launches.
+ *   pts      device, 8-byte aligned, the k point sets packed back to back.
+ *   offsets  device int64[k+1]: set i is points [offsets[i], offsets[i+1]);
+ *            offsets[0] == 0, non-decreasing, each set <= CH_MAX_POINTS.
+ *   k        0 <= k <= 2^20.
+ *   out_idx  device int32, capacity offsets[k]; hull i is written to
+ *            out_idx[offsets[i] .. offsets[i] + out_n[i]) as LOCAL indices
+ *            (relative to offsets[i]), same order rules as ch_hull.
+ *   out_n    device int64[k]: hull sizes, or a negative ch_status per set.
+ *   host_offsets  optional HOST copy of offsets (NULL allowed): lets the
+ *            library size its launches without reading the device array.
+ * Each result equals ch_hull on that set alone.
+ */
+int ch_hull_batched(const float* pts, const int64_t* offsets, int32_t k,
+                    int32_t* out_idx, int64_t* out_n, const int64_t* host_offsets,
+                    void* stream);
+
+/*
+ * ch_filter -- the paper's GPUfilter (Alg. 2) on its own.
+ *   out_ext8     device int32[8]: indices of the extreme points in the order
+ *                W, SW, S, SE, E, NE, N, NW (argmin x, argmin x+y, argmin y,
+ *                argmax x-y, argmax x, argmax x+y, argmax y, argmin x-y;
+ *                lowest index on ties; Sec. 3 finds the last four by minimum
+ *                Manhattan distance to the bounding-box corners, which selects
+ *                the same points).  Entries are -1 when n == 0.
+ *   out_labels   device uint8[n] or NULL: the array Q of Alg. 2; 0 when the
+ *                point is strictly inside the octagon W..NW (or in no queue),
+ *                else its queue 1..4: 1 = strictly right of W->S, 2 = right of
+ *                S->E, 3 = right of E->N, 4 = right of N->W (first match).
+ *   out_counts4  device int64[4] or NULL: number of points in each queue, or
+ *                all four set to a negative ch_status on a data error.
+ */
+int ch_filter(const float* pts, int64_t n, int32_t* out_ext8, uint8_t* out_labels,
+              int64_t* out_counts4, void* stream);
+
+/*
+ * ch_hull_host -- ch_hull on HOST buffers: copies pts (host, n*2 float32) to
+ * the device, computes the hull, copies the result back and waits for it.
+ * Writes h (or a negative status) to *out_n and the indices to out_idx (host,
+ * capacity n).  Returns CH_OK or a negative status.  Blocking.
+ */
+int ch_hull_host(const float* pts, int64_t n, int32_t* out_idx, int64_t* out_n, void* stream);
+
+/*
+ * ch_reserve -- grow the workspace of `stream` on the current device for
+ * hulls of up to n points (batched: n = total points, k sets).  Call it before
+ * capturing ch_hull / ch_hull_batched into a CUDA graph: allocation is not
+ * allowed during capture.  Blocking (may synchronise `stream`).
+ */
+int ch_reserve(int64_t n, int32_t k, void* stream);
+
+/* Bytes of workspace ch_hull needs for n points. */
+size_t ch_workspace_bytes(int64_t n);
+
+/* Free every workspace of every device (synchronises the streams involved). */
+int ch_release(void);
+
+/* Static text for a status code. */
+const char* ch_strerror(int status);
+
+/*
+ * Device-timed kernel statistics.  When enabled, the library records CUDA
+ * events around each kernel it launches, on the launching stream.
+ * ch_profile_read synchronises those events and returns, for up to `cap`
+ * kernels, the name, the number of launches and the summed milliseconds;
+ * the return value is the number of distinct kernels (may exceed cap).
+ */
+int ch_profile_enable(int on);
+int ch_profile_reset(void);
+int ch_profile_read(const char** names, int64_t* launches, double* total_ms, int cap);
+
+/*
+ * Serving (continuous batching).  A server owns a device memory pool of
+ * budget_bytes on `device` and an engine thread with its own stream.
+ * ch_submit copies the request (host points) in, without blocking; it returns
+ * CH_OK with a ticket, or CH_EBUSY when the admission queue is full, or
+ * CH_ENOMEM when the request can never fit the budget.  Requests that arrive
+ * while others run are admitted as memory frees up and batched together.
+ * ch_poll returns CH_PENDING, or CH_OK after copying the h result indices to
+ * out_idx_host (capacity cap) and setting *out_n (the request's ticket is
+ * then retired), or a negative status (CH_EINVAL for an unknown ticket).
+ * ch_server_stats fills p50/p99 request latency in ms and served points/s.
+ */
+int ch_server_create(size_t budget_bytes, int device, void** srv);
+int ch_submit(void* srv, const float* pts_host, int64_t n, uint64_t* ticket);
+int ch_poll(void* srv, uint64_t ticket, int32_t* out_idx_host, int64_t cap, int64_t* out_n);
+int ch_server_stats(void* srv, double* p50_ms, double* p99_ms, double* points_per_s,
+                    int64_t* completed);
+int ch_server_destroy(void* srv);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CONVHULL_CH_H */

@@ -1,0 +1,423 @@
+// api.cu -- C ABI entry points (ch.h): argument checks, workspace management,
+// launch sequences and device-timed kernel statistics.
+#include "ch_internal.cuh"
+#include "launch.h"
+#include "host.h"
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
+
+namespace ch {
+
+// ---------------------------------------------------------------------------
+// Device information (SM count, resident blocks per SM of every kernel).
+struct DevInfo {
+    int sms = 0;
+    int occ_p1 = 1, occ_p2 = 1, occ_lab = 1, occ_sort = 1, occ_chain = 1;
+};
+
+static std::mutex g_mu;
+static std::map<int, DevInfo> g_dev;
+
+static int device_info(int dev, DevInfo* out) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_dev.find(dev);
+    if (it != g_dev.end()) { *out = it->second; return CH_OK; }
+    DevInfo di;
+    if (cudaDeviceGetAttribute(&di.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return CH_ECUDA;
+    if (configure_hull_kernels() != cudaSuccess) return CH_ECUDA;
+    if (occupancy_filter(&di.occ_p1, &di.occ_p2, &di.occ_lab) != cudaSuccess) return CH_ECUDA;
+    if (occupancy_sort(&di.occ_sort) != cudaSuccess) return CH_ECUDA;
+    if (occupancy_chain(&di.occ_chain) != cudaSuccess) return CH_ECUDA;
+    di.occ_p1 = std::max(1, di.occ_p1);
+    di.occ_p2 = std::max(1, di.occ_p2);
+    di.occ_lab = std::max(1, di.occ_lab);
+    di.occ_sort = std::max(1, di.occ_sort);
+    di.occ_chain = std::max(1, di.occ_chain);
+    g_dev[dev] = di;
+    *out = di;
+    return CH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Workspace layout for one hull of up to n points.
+static size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+Layout make_layout(long long n) {
+    Layout L{};
+    L.cap = n + 8;
+    L.sort_tiles = (L.cap + kSortTile - 1) / kSortTile;
+    L.ctcap = (L.cap + kChainTile - 1) / kChainTile + 4;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t r = o;
+        o = align_up(o + bytes);
+        return r;
+    };
+    L.off_ctl = take(sizeof(Ctl));
+    L.off_kA = take(4 * (size_t)L.cap);
+    L.off_kB = take(4 * (size_t)L.cap);
+    L.off_vA = take(8 * (size_t)L.cap);
+    L.off_vB = take(8 * (size_t)L.cap);
+    L.off_status = take(8 * (size_t)kDigits * L.sort_tiles);
+    L.zero_bytes = o;   // control block and look-back status are zeroed at allocation
+    L.off_cu = take(4 * (size_t)L.ctcap * kChainTile);
+    L.off_cv = take(4 * (size_t)L.ctcap * kChainTile);
+    L.off_ci = take(4 * (size_t)L.ctcap * kChainTile);
+    L.off_clen = take(4 * (size_t)L.ctcap);
+    L.off_counters = take(4 * (size_t)kMaxLevels * L.ctcap);
+    L.total = o;
+    return L;
+}
+
+struct Workspace {
+    char* base = nullptr;
+    size_t bytes = 0;
+    long long n_cap = -1;
+    // staging for the host-buffer entry point
+    char* stage = nullptr;
+    size_t stage_bytes = 0;
+};
+
+static std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
+
+static int grow_workspace(Workspace& ws, long long n, cudaStream_t s) {
+    if (n <= ws.n_cap) return CH_OK;
+    const long long want = std::max(n, (long long)(ws.n_cap > 0 ? ws.n_cap + ws.n_cap / 4 : n));
+    const Layout L = make_layout(want);
+    if (ws.base) {
+        cudaStreamSynchronize(s);
+        cudaFree(ws.base);
+        ws.base = nullptr;
+        ws.bytes = 0;
+        ws.n_cap = -1;
+    }
+    void* p = nullptr;
+    if (cudaMalloc(&p, L.total) != cudaSuccess) {
+        cudaGetLastError();
+        return CH_ENOMEM;
+    }
+    if (cudaMemsetAsync(p, 0, L.zero_bytes, s) != cudaSuccess) {
+        cudaFree(p);
+        return CH_ECUDA;
+    }
+    ws.base = (char*)p;
+    ws.bytes = L.total;
+    ws.n_cap = want;
+    return CH_OK;
+}
+
+int get_workspace(int dev, cudaStream_t s, long long n, char** base, Layout* L) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    Workspace& ws = g_ws[std::make_pair(dev, s)];
+    const int st = grow_workspace(ws, n, s);
+    if (st != CH_OK) return st;
+    *base = ws.base;
+    *L = make_layout(ws.n_cap);
+    return CH_OK;
+}
+
+void release_stream_workspace(int dev, cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_ws.find(std::make_pair(dev, s));
+    if (it == g_ws.end()) return;
+    cudaStreamSynchronize(s);
+    if (it->second.base) cudaFree(it->second.base);
+    if (it->second.stage) cudaFree(it->second.stage);
+    g_ws.erase(it);
+}
+
+static int get_stage(int dev, cudaStream_t s, size_t bytes, char** out) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    Workspace& ws = g_ws[std::make_pair(dev, s)];
+    if (ws.stage_bytes < bytes) {
+        if (ws.stage) {
+            cudaStreamSynchronize(s);
+            cudaFree(ws.stage);
+            ws.stage = nullptr;
+            ws.stage_bytes = 0;
+        }
+        void* p = nullptr;
+        const size_t want = std::max(bytes, ws.stage_bytes + ws.stage_bytes / 4);
+        if (cudaMalloc(&p, want) != cudaSuccess) {
+            cudaGetLastError();
+            return CH_ENOMEM;
+        }
+        ws.stage = (char*)p;
+        ws.stage_bytes = want;
+    }
+    *out = ws.stage;
+    return CH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Device-timed statistics: CUDA events recorded on the launching stream.
+struct ProfPending {
+    const char* name;
+    cudaEvent_t a, b;
+};
+static bool g_prof = false;
+static std::mutex g_prof_mu;
+static std::vector<ProfPending> g_pending;
+static std::vector<cudaEvent_t> g_event_pool;
+static std::map<std::string, std::pair<long long, double>> g_acc;
+static std::vector<std::string> g_names;   // stable storage for names returned to callers
+
+static cudaEvent_t take_event() {
+    if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+ProfScope::ProfScope(const char* name, cudaStream_t s) : name_(name), s_(s), a_(nullptr) {
+    if (!g_prof) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    a_ = take_event();
+    cudaEventRecord((cudaEvent_t)a_, s_);
+}
+
+ProfScope::~ProfScope() {
+    if (!a_) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    cudaEvent_t b = take_event();
+    cudaEventRecord(b, s_);
+    g_pending.push_back(ProfPending{name_, (cudaEvent_t)a_, b});
+}
+
+static void prof_drain() {
+    for (auto& p : g_pending) {
+        cudaEventSynchronize(p.b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, p.a, p.b);
+        auto& acc = g_acc[p.name];
+        acc.first += 1;
+        acc.second += ms;
+        g_event_pool.push_back(p.a);
+        g_event_pool.push_back(p.b);
+    }
+    g_pending.clear();
+}
+
+// ---------------------------------------------------------------------------
+// The launch sequence of one hull (n >= 1) on an allocated workspace.
+int enqueue_hull(const float* pts, long long n, int32_t* out_idx, int64_t* out_n, cudaStream_t s,
+                 int dev) {
+    DevInfo di;
+    int st = device_info(dev, &di);
+    if (st != CH_OK) return st;
+    char* base = nullptr;
+    Layout L;
+    st = get_workspace(dev, s, n, &base, &L);
+    if (st != CH_OK) return st;
+    Ctl* ctl = (Ctl*)(base + L.off_ctl);
+    uint32_t* kA = (uint32_t*)(base + L.off_kA);
+    uint32_t* kB = (uint32_t*)(base + L.off_kB);
+    uint64_t* vA = (uint64_t*)(base + L.off_vA);
+    uint64_t* vB = (uint64_t*)(base + L.off_vB);
+    unsigned long long* status = (unsigned long long*)(base + L.off_status);
+    int* cu = (int*)(base + L.off_cu);
+    int* cv = (int*)(base + L.off_cv);
+    int* ci = (int*)(base + L.off_ci);
+    int* clen = (int*)(base + L.off_clen);
+    int* counters = (int*)(base + L.off_counters);
+
+    const int head = (((uintptr_t)pts & 15u) != 0u && n > 0) ? 1 : 0;
+    const long long ntiles = (n - head) / kWarpTilePts;
+    const int grid1 = di.sms * di.occ_p1;
+    const int grid2 = di.sms * di.occ_p2;
+    const int grid_sort = di.sms * di.occ_sort;
+    const int grid_chain = di.sms * di.occ_chain;
+
+    { ProfScope p("init", s); launch_init(ctl, s); }
+    { ProfScope p("pass1_extremes", s); launch_pass1(pts, n, head, ntiles, ctl, grid1, s); }
+    { ProfScope p("finalize_octagon", s); launch_finalize(pts, n, head, ctl, kA, vA, s); }
+    { ProfScope p("pass2_filter", s); launch_pass2(pts, n, head, ntiles, ctl, kA, vA, grid2, s); }
+    {
+        ProfScope p("sort", s);
+        launch_sort_pass(kA, vA, kB, vB, ctl, status, 0, grid_sort, s);
+        launch_sort_pass(kB, vB, kA, vA, ctl, status, 1, grid_sort, s);
+        launch_sort_pass(kA, vA, kB, vB, ctl, status, 2, grid_sort, s);
+    }
+    {
+        ProfScope p("hull_chains", s);
+        launch_plan(ctl, kB, counters, (int)L.ctcap, s);
+        launch_chain(ctl, kB, vB, cu, cv, ci, clen, counters, (int)L.ctcap, grid_chain, s);
+    }
+    {
+        ProfScope p("stitch", s);
+        launch_stitch(pts, n, ctl, cu, cv, ci, clen, (int*)vA, (int*)kA, out_idx, out_n, s);
+    }
+    return cudaGetLastError() == cudaSuccess ? CH_OK : CH_ECUDA;
+}
+
+int check_points_args(const float* pts, long long n) {
+    if (n < 0 || n > CH_MAX_POINTS) return CH_EINVAL;
+    if (n > 0 && !pts) return CH_EINVAL;
+    if (((uintptr_t)pts & 7u) != 0u) return CH_EINVAL;
+    return CH_OK;
+}
+
+}  // namespace ch
+
+using namespace ch;
+
+extern "C" {
+
+int ch_hull(const float* pts, int64_t n, int32_t* out_idx, int64_t* out_n, void* stream) {
+    int st = check_points_args(pts, n);
+    if (st != CH_OK) return st;
+    if (!out_n || (n > 0 && !out_idx)) return CH_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n == 0) return cudaMemsetAsync(out_n, 0, sizeof(int64_t), s) == cudaSuccess ? CH_OK : CH_ECUDA;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CH_ECUDA;
+    return enqueue_hull(pts, n, out_idx, out_n, s, dev);
+}
+
+int ch_filter(const float* pts, int64_t n, int32_t* out_ext8, uint8_t* out_labels, int64_t* out_counts4,
+              void* stream) {
+    int st = check_points_args(pts, n);
+    if (st != CH_OK) return st;
+    if (!out_ext8) return CH_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n == 0) {
+        if (cudaMemsetAsync(out_ext8, 0xFF, 8 * sizeof(int32_t), s) != cudaSuccess) return CH_ECUDA;
+        if (out_counts4 && cudaMemsetAsync(out_counts4, 0, 4 * sizeof(int64_t), s) != cudaSuccess)
+            return CH_ECUDA;
+        return CH_OK;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CH_ECUDA;
+    DevInfo di;
+    if ((st = device_info(dev, &di)) != CH_OK) return st;
+    char* base = nullptr;
+    Layout L;
+    if ((st = get_workspace(dev, s, n, &base, &L)) != CH_OK) return st;
+    Ctl* ctl = (Ctl*)(base + L.off_ctl);
+    const int head = (((uintptr_t)pts & 15u) != 0u) ? 1 : 0;
+    const long long ntiles = (n - head) / kWarpTilePts;
+    { ProfScope p("init", s); launch_init(ctl, s); }
+    { ProfScope p("pass1_extremes", s); launch_pass1(pts, n, head, ntiles, ctl, di.sms * di.occ_p1, s); }
+    {
+        ProfScope p("finalize_octagon", s);
+        launch_finalize(pts, n, head, ctl, (uint32_t*)(base + L.off_kA), (uint64_t*)(base + L.off_vA), s);
+    }
+    if (out_labels || out_counts4) {
+        ProfScope p("labels", s);
+        launch_labels(pts, n, ctl, out_labels, di.sms * di.occ_lab, s);
+    }
+    launch_filter_output(ctl, n, out_ext8, out_counts4, s);
+    return cudaGetLastError() == cudaSuccess ? CH_OK : CH_ECUDA;
+}
+
+int ch_hull_host(const float* pts, int64_t n, int32_t* out_idx, int64_t* out_n, void* stream) {
+    int st = check_points_args(pts, n);
+    if (st != CH_OK) return st;
+    if (!out_n || (n > 0 && !out_idx)) return CH_EINVAL;
+    if (n == 0) { *out_n = 0; return CH_OK; }
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CH_ECUDA;
+    const size_t pts_bytes = align_up(8 * (size_t)n), idx_bytes = align_up(4 * (size_t)n);
+    char* stage = nullptr;
+    if ((st = get_stage(dev, s, pts_bytes + idx_bytes + 256, &stage)) != CH_OK) return st;
+    float* dpts = (float*)stage;
+    int32_t* didx = (int32_t*)(stage + pts_bytes);
+    int64_t* dn = (int64_t*)(stage + pts_bytes + idx_bytes);
+    if (cudaMemcpyAsync(dpts, pts, 8 * (size_t)n, cudaMemcpyHostToDevice, s) != cudaSuccess) return CH_ECUDA;
+    if ((st = enqueue_hull(dpts, n, didx, dn, s, dev)) != CH_OK) return st;
+    int64_t h = 0;
+    if (cudaMemcpyAsync(&h, dn, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CH_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return CH_ECUDA;
+    *out_n = h;
+    if (h > 0) {
+        if (cudaMemcpyAsync(out_idx, didx, 4 * (size_t)h, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            return CH_ECUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return CH_ECUDA;
+    }
+    return CH_OK;
+}
+
+int ch_reserve(int64_t n, int32_t k, void* stream) {
+    if (n < 0 || k < 0) return CH_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CH_ECUDA;
+    DevInfo di;
+    int st = device_info(dev, &di);
+    if (st != CH_OK) return st;
+    char* base;
+    Layout L;
+    st = get_workspace(dev, (cudaStream_t)stream, std::max<int64_t>(n, 1), &base, &L);
+    if (st != CH_OK) return st;
+    return reserve_batched(dev, (cudaStream_t)stream, n, k);
+}
+
+size_t ch_workspace_bytes(int64_t n) { return n < 0 ? 0 : make_layout(n).total; }
+
+int ch_release(void) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto& kv : g_ws) {
+        cudaStreamSynchronize(kv.first.second);
+        if (kv.second.base) cudaFree(kv.second.base);
+        if (kv.second.stage) cudaFree(kv.second.stage);
+    }
+    g_ws.clear();
+    release_batched();
+    return CH_OK;
+}
+
+const char* ch_strerror(int status) {
+    switch (status) {
+        case CH_OK: return "ok";
+        case CH_PENDING: return "pending";
+        case CH_EINVAL: return "invalid argument";
+        case CH_ERANGE: return "coordinate outside the integer domain [0, 2^24)";
+        case CH_ENOMEM: return "out of memory or over budget";
+        case CH_ECUDA: return "CUDA error";
+        case CH_ETIMEOUT: return "device wait timed out";
+        case CH_EBUSY: return "busy, retry";
+        default: return "unknown status";
+    }
+}
+
+int ch_profile_enable(int on) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof = on != 0;
+    return CH_OK;
+}
+
+int ch_profile_reset(void) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    prof_drain();
+    g_acc.clear();
+    return CH_OK;
+}
+
+int ch_profile_read(const char** names, int64_t* launches, double* total_ms, int cap) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    prof_drain();
+    g_names.clear();
+    for (auto& kv : g_acc) g_names.push_back(kv.first);
+    int i = 0;
+    for (auto& kv : g_acc) {
+        if (i < cap) {
+            if (names) names[i] = g_names[i].c_str();
+            if (launches) launches[i] = kv.second.first;
+            if (total_ms) total_ms[i] = kv.second.second;
+        }
+        ++i;
+    }
+    return (int)g_acc.size();
+}
+
+}  // extern "C"

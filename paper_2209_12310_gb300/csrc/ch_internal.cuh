@@ -1,0 +1,139 @@
+// ch_internal.cuh -- device-side data layout and helpers shared by the CUDA
+// translation units of libconvhull (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ch.h"
+
+namespace ch {
+
+// ---------------------------------------------------------------------------
+// Geometry of the input domain.  Coordinates are integers in [0, 2^24), so
+// x + y < 2^25 and every orientation product is below 2^50 (exact in int64).
+// ---------------------------------------------------------------------------
+constexpr int kCoordBits = 24;
+constexpr int kCoordLimit = 1 << kCoordBits;
+constexpr int kKeyBits = 25;                  // bits of the per-queue sort key u
+constexpr uint32_t kKeyMask = (1u << kKeyBits) - 1;
+constexpr int kSortBits = 27;                 // queue (2 bits) | u (25 bits)
+constexpr int kDigitBits = 9;                 // 3 LSD passes of 9 bits
+constexpr int kDigits = 1 << kDigitBits;
+constexpr int kSortPasses = 3;
+
+// Streaming passes: a warp tile is 256 float4 = 512 points (8 float4 / lane).
+constexpr int kLoadsPerLane = 8;
+constexpr int kWarpTileF4 = 32 * kLoadsPerLane;
+constexpr int kWarpTilePts = 2 * kWarpTileF4;
+
+// Onesweep radix sort tile: 256 threads x 16 keys.
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;
+
+// Hull stage tile: 256 threads x 16 sorted records.
+constexpr int kChainThreads = 256;
+constexpr int kChainItems = 16;
+constexpr int kChainTile = kChainThreads * kChainItems;
+constexpr int kMergeSmemCap = 8192;           // chain points a global merge keeps on chip
+constexpr int kMaxLevels = 32;
+
+// Float edge-function error bound: |e_float - e_exact| < 2^28 for every edge
+// and query point of the domain (see octagon setup in filter.cu).
+constexpr float kEdgeTol = 268435456.0f;      // 2^28
+constexpr float kHugePositive = 1.0e30f;      // "always inside" coefficient of a skipped edge
+
+constexpr unsigned kSpinLimit = 1u << 20;     // bounded waits (onesweep look-back)
+
+// Directions of the 8 extremes in counter-clockwise octagon order.
+enum Dir { W = 0, SW, S, SE, E, NE, N, NW };
+
+// Edge function  e(p) = A*px + B*py + C  equals orient(a, b, p) (positive when
+// p is left of a->b); exact data kept for the ambiguous band |e| <= kEdgeTol.
+struct Edge {
+    float A, B, C;
+    int ax, ay, dx, dy;  // origin and direction (dx = dy = 0: skipped edge)
+};
+
+struct Octagon {
+    int vx[8], vy[8];    // vertices W, SW, S, SE, E, NE, N, NW
+    int ext[8];          // their indices
+    Edge oct[8];         // octagon edges V[k] -> V[k+1]
+    Edge quad[4];        // W->S, S->E, E->N, N->W (queue rule)
+    float bxl, bxh, byl, byh;  // open box strictly inside the octagon (may be empty)
+    int discard_none;    // octagon of zero area: nothing is discarded
+    int pad[3];
+};
+
+// Per-call control block in device memory.
+struct Ctl {
+    unsigned long long ext_packed[8];   // (key, ~tile) packed maxima of pass 1
+    int status;                         // CH_OK or a negative ch_status
+    int abort;                          // set by a timed-out wait; all waits give up
+    unsigned int count;                 // records in the survivor buffer (8 extremes first)
+    unsigned int epoch;                 // onesweep status epoch (incremented per call)
+    unsigned int tile_ctr[4];           // onesweep tile claim counters
+    unsigned int digit_hist[kSortPasses][kDigits];
+    unsigned int reg_start[4], reg_end[4];
+    unsigned int reg_tile_base[5];      // chain tiles of queue r: [base[r], base[r+1])
+    unsigned int counts4[4];            // survivors per queue (ch_filter)
+    Octagon oct;
+};
+
+// ---------------------------------------------------------------------------
+// Small helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long orient64(long long ax, long long ay, long long bx,
+                                              long long by, long long px, long long py) {
+    return (bx - ax) * (py - ay) - (by - ay) * (px - ax);
+}
+
+__device__ __forceinline__ float4 ld_stream_f4(const float4* p) {
+    float4 r;
+    asm("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+        : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+        : "l"(p));
+    return r;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ void set_status(Ctl* ctl, int st) {
+    atomicCAS(&ctl->status, CH_OK, st);
+}
+
+__device__ __forceinline__ int read_status(const Ctl* ctl) {
+    return *(volatile const int*)&ctl->status;
+}
+
+// Queue-frame coordinates of a survivor.  For queue r the chain from its
+// start extreme to its end extreme is strictly increasing in u, and among
+// points of equal u only the one of minimum v can be a hull vertex.  Every
+// map (x, y) -> (u, v) is a rotation by a multiple of 90 degrees plus 45,
+// scaled by sqrt(2): orientation-preserving, so cross products keep their sign.
+//   r = 0 (W->S):  u = x - y + 2^24,      v = x + y
+//   r = 1 (S->E):  u = x + y,             v = y - x + 2^24
+//   r = 2 (E->N):  u = y - x + 2^24,      v = 2^25 - 2 - x - y
+//   r = 3 (N->W):  u = 2^25 - 2 - x - y,  v = x - y + 2^24
+__device__ __forceinline__ void queue_frame(int r, int x, int y, uint32_t& u, uint32_t& v) {
+    const int off = kCoordLimit;
+    const int top = 2 * kCoordLimit - 2;
+    switch (r) {
+        case 0: u = (uint32_t)(x - y + off); v = (uint32_t)(x + y); break;
+        case 1: u = (uint32_t)(x + y); v = (uint32_t)(y - x + off); break;
+        case 2: u = (uint32_t)(y - x + off); v = (uint32_t)(top - x - y); break;
+        default: u = (uint32_t)(top - x - y); v = (uint32_t)(x - y + off); break;
+    }
+}
+
+__device__ __forceinline__ uint32_t make_key(int r, uint32_t u) { return ((uint32_t)r << kKeyBits) | u; }
+__device__ __forceinline__ uint64_t make_val(uint32_t v, uint32_t idx) {
+    return ((uint64_t)v << 31) | (uint64_t)idx;
+}
+
+}  // namespace ch

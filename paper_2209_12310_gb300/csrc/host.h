@@ -1,0 +1,40 @@
+// host.h -- host-side internals shared by api.cu, batched.cu and server.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace ch {
+
+// Workspace layout of one hull of up to n points (byte offsets from the base).
+struct Layout {
+    size_t off_ctl, off_kA, off_kB, off_vA, off_vB, off_status, zero_bytes;
+    size_t off_cu, off_cv, off_ci, off_clen, off_counters, total;
+    long long cap, sort_tiles, ctcap;
+};
+
+Layout make_layout(long long n);
+int get_workspace(int dev, cudaStream_t s, long long n, char** base, Layout* L);
+int enqueue_hull(const float* pts, long long n, int32_t* out_idx, int64_t* out_n, cudaStream_t s, int dev);
+int check_points_args(const float* pts, long long n);
+
+int reserve_batched(int dev, cudaStream_t s, long long n, int k);
+void release_stream_workspace(int dev, cudaStream_t s);
+void release_batched();
+
+// Records a CUDA event pair around a scope when profiling is enabled.
+class ProfScope {
+  public:
+    ProfScope(const char* name, cudaStream_t s);
+    ~ProfScope();
+    ProfScope(const ProfScope&) = delete;
+    ProfScope& operator=(const ProfScope&) = delete;
+
+  private:
+    const char* name_;
+    cudaStream_t s_;
+    void* a_;
+};
+
+}  // namespace ch

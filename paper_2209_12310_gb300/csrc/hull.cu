@@ -1,0 +1,549 @@
+// hull.cu -- hull of the sorted survivors on the device.
+//
+// The paper ends with "for i = 1..4: CH <- CH U hull(Q_i, n_i)" (Alg. 1): one
+// hull per queue, joined.  Here every queue r is a chain from quad vertex r
+// to quad vertex r+1 that is strictly monotone in the queue-frame coordinate u
+// (see queue_frame), and its hull chain is Andrew's lower chain (Table I) in
+// the (u, v) frame:
+//   plan_kernel    queue boundaries in the sorted records, chain-tile layout;
+//   chain_kernel   per tile of 4096 records: keep the minimum-(v, index)
+//                  record of every run of equal u (only it can be a vertex),
+//                  build per-thread chains, merge them pairwise in shared
+//                  memory, then merge tiles pairwise up a binary tree: the
+//                  block that completes a pair (second arrival on an atomic
+//                  counter) performs that merge, so no block ever waits;
+//   stitch_kernel  join the four queue chains, drop collinear junction
+//                  vertices, handle the degenerate (collinear / single point)
+//                  cases, rotate to the lexicographically smallest vertex.
+//
+// Merging two chains A, B (all u of A below all u of B): a_k (k > 0) stays iff
+// every b in B is strictly left of a_{k-1} -> a_k; b_l (l < |B|-1) stays iff
+// every a in A is strictly left of b_l -> b_{l+1}.  Both predicates hold on a
+// prefix of A / a suffix of B, and "every b" reduces to the minimum of a
+// linear function over the convex chain B, found by binary search.
+#include "ch_internal.cuh"
+#include "launch.h"
+
+#include <climits>
+
+namespace ch {
+
+struct ChainPtr {   // structure-of-arrays view of a chain (u, v, index)
+    int* u;
+    int* v;
+    int* i;
+};
+
+__device__ __forceinline__ long long cross_uv(int ou, int ov, int au, int av, int bu, int bv) {
+    return (long long)(au - ou) * (long long)(bv - ov) - (long long)(av - ov) * (long long)(bu - ou);
+}
+
+template <bool kGlobal>
+__device__ __forceinline__ int ldi(const int* p) {
+    if (kGlobal) return __ldcg(p);
+    return *p;
+}
+
+// Minimum over chain C[0..lc) of f(c) = cross(p, q, c), q.u > p.u.  Along a
+// lower convex chain the increments cross(q - p, c_{l+1} - c_l) change sign
+// once (negative, then >= 0), so f is minimal at the first l whose next edge
+// does not decrease it.
+template <bool kGlobal>
+__device__ long long min_cross_over(const int* cu, const int* cv, int lc, int pu, int pv, int qu,
+                                    int qv) {
+    int lo = 0, hi = lc - 1;   // answer in [lo, hi]
+    const long long du = qu - pu, dv = qv - pv;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        const long long eu = (long long)ldi<kGlobal>(cu + mid + 1) - ldi<kGlobal>(cu + mid);
+        const long long ev = (long long)ldi<kGlobal>(cv + mid + 1) - ldi<kGlobal>(cv + mid);
+        if (du * ev - dv * eu >= 0) hi = mid; else lo = mid + 1;
+    }
+    return cross_uv(pu, pv, qu, qv, ldi<kGlobal>(cu + lo), ldi<kGlobal>(cv + lo));
+}
+
+template <bool kGlobal>
+__device__ __forceinline__ bool keep_a(const ChainPtr& A, int k, const ChainPtr& B, int lb) {
+    if (k == 0) return true;
+    return min_cross_over<kGlobal>(B.u, B.v, lb, ldi<kGlobal>(A.u + k - 1), ldi<kGlobal>(A.v + k - 1),
+                                   ldi<kGlobal>(A.u + k), ldi<kGlobal>(A.v + k)) > 0;
+}
+
+template <bool kGlobal>
+__device__ __forceinline__ bool keep_b(const ChainPtr& A, int la, const ChainPtr& B, int l, int lb) {
+    if (l == lb - 1) return true;
+    return min_cross_over<kGlobal>(A.u, A.v, la, ldi<kGlobal>(B.u + l), ldi<kGlobal>(B.v + l),
+                                   ldi<kGlobal>(B.u + l + 1), ldi<kGlobal>(B.v + l + 1)) > 0;
+}
+
+// Sequential bridge (one thread): last kept index of A, first kept of B.
+template <bool kGlobal>
+__device__ void bridge_seq(const ChainPtr& A, int la, const ChainPtr& B, int lb, int& is, int& js) {
+    int lo = 0, hi = la - 1;               // keep_a(lo) true
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (keep_a<kGlobal>(A, mid, B, lb)) lo = mid; else hi = mid - 1;
+    }
+    is = lo;
+    lo = 0; hi = lb - 1;                   // keep_b(hi) true
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (keep_b<kGlobal>(A, la, B, mid, lb)) hi = mid; else lo = mid + 1;
+    }
+    js = lo;
+}
+
+// Block-cooperative bridge: repeated 256-way probing of the monotone keep
+// predicates (each probe is a sequential binary search over the other chain).
+template <bool kGlobal>
+__device__ void bridge_block(const ChainPtr& A, int la, const ChainPtr& B, int lb, int& is, int& js,
+                             int* s_red) {
+    const int T = blockDim.x;
+    // A: largest k with keep_a(k); predicate true on [0, is]
+    int lo = 0, hi = la - 1;
+    while (lo < hi) {
+        const long long span = (long long)hi - lo;
+        const int k = lo + 1 + (int)(span * threadIdx.x / T);   // probes in (lo, hi]
+        const bool ok = (k <= hi) && keep_a<kGlobal>(A, k, B, lb);
+        if (threadIdx.x == 0) { s_red[0] = lo; s_red[1] = hi; }
+        __syncthreads();
+        if (k <= hi) {
+            if (ok) atomicMax(&s_red[0], k);
+            else atomicMin(&s_red[1], k - 1);
+        }
+        __syncthreads();
+        const int nlo = s_red[0], nhi = s_red[1];
+        __syncthreads();
+        lo = nlo; hi = max(nhi, nlo);
+    }
+    is = lo;
+    lo = 0; hi = lb - 1;   // smallest l with keep_b(l); true on [js, lb-1]
+    while (lo < hi) {
+        const long long span = (long long)hi - lo;
+        const int l = lo + (int)(span * threadIdx.x / T);       // probes in [lo, hi)
+        const bool ok = (l < hi) && keep_b<kGlobal>(A, la, B, l, lb);
+        if (threadIdx.x == 0) { s_red[0] = lo; s_red[1] = hi; }
+        __syncthreads();
+        if (l < hi) {
+            if (ok) atomicMin(&s_red[1], l);
+            else atomicMax(&s_red[0], l + 1);
+        }
+        __syncthreads();
+        const int nlo = s_red[0], nhi = s_red[1];
+        __syncthreads();
+        hi = nhi; lo = min(nlo, nhi);
+    }
+    js = lo;
+}
+
+// ---------------------------------------------------------------------------
+__global__ void plan_kernel(Ctl* ctl, const uint32_t* __restrict__ keys, int* counters, int ctcap) {
+    __shared__ unsigned s_b[5];
+    if (read_status(ctl) != CH_OK) return;
+    const unsigned count = ctl->count;
+    const int t = threadIdx.x;
+    if (t < 5) {
+        unsigned pos;
+        if (t == 0) pos = 0;
+        else if (t == 4) pos = count;
+        else {   // first record of queue t
+            const uint32_t target = (uint32_t)t << kKeyBits;
+            unsigned lo = 0, hi = count;
+            while (lo < hi) {
+                const unsigned mid = (lo + hi) >> 1;
+                if (keys[mid] < target) lo = mid + 1; else hi = mid;
+            }
+            pos = lo;
+        }
+        s_b[t] = pos;
+    }
+    __syncthreads();
+    if (t == 0) {
+        unsigned base = 0;
+        for (int r = 0; r < 4; ++r) {
+            ctl->reg_start[r] = s_b[r];
+            ctl->reg_end[r] = s_b[r + 1];
+            ctl->reg_tile_base[r] = base;
+            const unsigned len = s_b[r + 1] - s_b[r];
+            base += (len + kChainTile - 1) / kChainTile;
+        }
+        ctl->reg_tile_base[4] = base;
+    }
+    __syncthreads();
+    // Reset the merge counters of every tree node this call will use.
+    for (int r = 0; r < 4; ++r) {
+        const unsigned b0 = ctl->reg_tile_base[r];
+        const unsigned ct = ctl->reg_tile_base[r + 1] - b0;
+        for (int P = 1; P < kMaxLevels && ((1u << (P - 1)) < ct); ++P) {
+            const unsigned nodes = (ct + (1u << P) - 1) >> P;
+            for (unsigned k = t; k < nodes; k += blockDim.x)
+                counters[(size_t)(P - 1) * ctcap + b0 + (k << P)] = 0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+struct HullBufs {
+    const uint32_t* keys;   // sorted records
+    const uint64_t* vals;
+    int* cu;                // chain storage: tile c at [c*kChainTile, ...)
+    int* cv;
+    int* ci;
+    int* clen;
+    int* counters;
+    int ctcap;
+};
+
+// Merge chain B (at sb, length lb) into chain A (at sa, length la) in shared
+// memory, one thread.  Returns the new length of A.
+__device__ int merge_smem_seq(int* su, int* sv, int* si, int sa, int la, int sb, int lb) {
+    if (lb == 0) return la;
+    if (la == 0) {
+        for (int j = 0; j < lb; ++j) { su[sa + j] = su[sb + j]; sv[sa + j] = sv[sb + j]; si[sa + j] = si[sb + j]; }
+        return lb;
+    }
+    ChainPtr A{su + sa, sv + sa, si + sa}, B{su + sb, sv + sb, si + sb};
+    int is, js;
+    bridge_seq<false>(A, la, B, lb, is, js);
+    const int n = lb - js;
+    for (int j = 0; j < n; ++j) {
+        su[sa + is + 1 + j] = su[sb + js + j];
+        sv[sa + is + 1 + j] = sv[sb + js + j];
+        si[sa + is + 1 + j] = si[sb + js + j];
+    }
+    return is + 1 + n;
+}
+
+// Block-wide forward copy of n entries, dst <= src (possibly overlapping),
+// in chunks fully loaded before they are stored.
+__device__ void copy_down(int* du, int* dv, int* di, const int* su, const int* sv, const int* si, int n) {
+    for (int base = 0; base < n; base += blockDim.x) {
+        const int j = base + threadIdx.x;
+        int a = 0, b = 0, c = 0;
+        if (j < n) { a = __ldcg(su + j); b = __ldcg(sv + j); c = __ldcg(si + j); }
+        __syncthreads();
+        if (j < n) { du[j] = a; dv[j] = b; di[j] = c; }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kChainThreads) chain_kernel(Ctl* ctl, HullBufs hb) {
+    extern __shared__ int smem[];
+    int* su = smem;
+    int* sv = su + kMergeSmemCap;
+    int* si = sv + kMergeSmemCap;
+    __shared__ int s_len[kChainThreads];
+    __shared__ int s_red[4];
+    __shared__ int s_old;
+
+    if (read_status(ctl) != CH_OK) return;
+    const int tid = threadIdx.x;
+    const unsigned total_tiles = ctl->reg_tile_base[4];
+
+    for (unsigned c = blockIdx.x; c < total_tiles; c += gridDim.x) {
+        int r = 0;
+        while (r < 3 && c >= ctl->reg_tile_base[r + 1]) ++r;
+        const unsigned rb = ctl->reg_tile_base[r];
+        const unsigned ct = ctl->reg_tile_base[r + 1] - rb;
+        const unsigned t_local = c - rb;
+        const unsigned q0 = ctl->reg_start[r], q1 = ctl->reg_end[r];
+        const unsigned ts = q0 + t_local * kChainTile;
+        const unsigned te = min(q1, ts + kChainTile);
+
+        // 1) run reduction + per-thread chain (records [ts + 16 tid, +16)).
+        {
+            const int sbase = tid * kChainItems;
+            int sp = 0;
+            const unsigned p0 = ts + tid * kChainItems;
+            for (int m = 0; m < kChainItems; ++m) {
+                const unsigned p = p0 + m;
+                if (p >= te) break;
+                const uint32_t key = hb.keys[p];
+                if (p != q0 && hb.keys[p - 1] == key) continue;   // not a run start
+                uint64_t best = hb.vals[p];
+                for (unsigned q = p + 1; q < q1; ++q) {
+                    if (hb.keys[q] != key) break;
+                    const uint64_t w = hb.vals[q];
+                    best = w < best ? w : best;
+                }
+                const int pu = (int)(key & kKeyMask);
+                const int pv = (int)(best >> 31);
+                const int pi = (int)(best & 0x7FFFFFFFull);
+                while (sp >= 2 && cross_uv(su[sbase + sp - 2], sv[sbase + sp - 2], su[sbase + sp - 1],
+                                           sv[sbase + sp - 1], pu, pv) <= 0)
+                    --sp;
+                su[sbase + sp] = pu; sv[sbase + sp] = pv; si[sbase + sp] = pi;
+                ++sp;
+            }
+            s_len[tid] = sp;
+        }
+        __syncthreads();
+        // 2) pairwise merge of the 256 thread chains.
+        for (int l = 0; (1 << l) < kChainThreads; ++l) {
+            const int g = 1 << l;
+            if ((tid & (2 * g - 1)) == 0) {
+                const int b = tid + g;
+                s_len[tid] = merge_smem_seq(su, sv, si, tid * kChainItems, s_len[tid],
+                                            b * kChainItems, s_len[b]);
+            }
+            __syncthreads();
+        }
+        // 3) write the tile chain.
+        const int len = s_len[0];
+        {
+            const size_t o = (size_t)c * kChainTile;
+            for (int j = tid; j < len; j += blockDim.x) {
+                hb.cu[o + j] = su[j]; hb.cv[o + j] = sv[j]; hb.ci[o + j] = si[j];
+            }
+            if (tid == 0) hb.clen[c] = len;
+        }
+        // 4) climb the merge tree of queue r.
+        unsigned L = 0, k = t_local;
+        for (;;) {
+            if (k == 0 && (1u << L) >= ct) break;             // root
+            const unsigned sib = k ^ 1u;
+            if ((sib << L) >= ct) { ++L; k >>= 1; continue; }  // no sibling: pass through
+            __threadfence();
+            __syncthreads();
+            if (tid == 0)
+                s_old = atomicAdd(&hb.counters[(size_t)L * hb.ctcap + rb + ((k >> 1) << (L + 1))], 1);
+            __syncthreads();
+            if (s_old == 0) break;                              // sibling merges later
+            __threadfence();
+            const unsigned left = rb + ((k & ~1u) << L), right = rb + ((k | 1u) << L);
+            const int la = __ldcg(hb.clen + left), lb = __ldcg(hb.clen + right);
+            const size_t oa = (size_t)left * kChainTile, ob = (size_t)right * kChainTile;
+            int is, js;
+            if (lb == 0) {
+                // nothing to add
+            } else if (la == 0) {
+                copy_down(hb.cu + oa, hb.cv + oa, hb.ci + oa, hb.cu + ob, hb.cv + ob, hb.ci + ob, lb);
+                if (tid == 0) hb.clen[left] = lb;
+            } else if (la + lb <= kMergeSmemCap) {
+                for (int j = tid; j < la; j += blockDim.x) {
+                    su[j] = __ldcg(hb.cu + oa + j); sv[j] = __ldcg(hb.cv + oa + j); si[j] = __ldcg(hb.ci + oa + j);
+                }
+                for (int j = tid; j < lb; j += blockDim.x) {
+                    su[la + j] = __ldcg(hb.cu + ob + j); sv[la + j] = __ldcg(hb.cv + ob + j);
+                    si[la + j] = __ldcg(hb.ci + ob + j);
+                }
+                __syncthreads();
+                ChainPtr A{su, sv, si}, B{su + la, sv + la, si + la};
+                bridge_block<false>(A, la, B, lb, is, js, s_red);
+                const int n = lb - js;
+                for (int j = tid; j < n; j += blockDim.x) {
+                    hb.cu[oa + is + 1 + j] = su[la + js + j];
+                    hb.cv[oa + is + 1 + j] = sv[la + js + j];
+                    hb.ci[oa + is + 1 + j] = si[la + js + j];
+                }
+                if (tid == 0) hb.clen[left] = is + 1 + n;
+            } else {
+                ChainPtr A{hb.cu + oa, hb.cv + oa, hb.ci + oa}, B{hb.cu + ob, hb.cv + ob, hb.ci + ob};
+                bridge_block<true>(A, la, B, lb, is, js, s_red);
+                const int n = lb - js;
+                copy_down(hb.cu + oa + is + 1, hb.cv + oa + is + 1, hb.ci + oa + is + 1,
+                          hb.cu + ob + js, hb.cv + ob + js, hb.ci + ob + js, n);
+                if (tid == 0) hb.clen[left] = is + 1 + n;
+            }
+            if (tid == 0) hb.counters[(size_t)L * hb.ctcap + rb + ((k >> 1) << (L + 1))] = 0;
+            __syncthreads();
+            ++L;
+            k >>= 1;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pt_of(const float* pts, int i, long long& x, long long& y) {
+    const float2 p = reinterpret_cast<const float2*>(pts)[i];
+    x = (long long)p.x;
+    y = (long long)p.y;
+}
+
+
+template <typename T, typename Op>
+__device__ T block_reduce(T v, Op op, T* s_tmp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v = op(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+    if (lane == 0) s_tmp[warp] = v;
+    __syncthreads();
+    T r = s_tmp[0];
+    for (int w = 1; w < nw; ++w) r = op(r, s_tmp[w]);
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(1024) stitch_kernel(const float* __restrict__ pts, long long n,
+                                                      Ctl* ctl, HullBufs hb, int* vbuf, int* kbuf,
+                                                      int32_t* out_idx, int64_t* out_n) {
+    __shared__ unsigned long long s_u64[32];
+    __shared__ long long s_i64[32];
+    __shared__ int s_off[5];
+    const int st = read_status(ctl);
+    if (st != CH_OK) {
+        if (threadIdx.x == 0) *out_n = st;
+        return;
+    }
+    const int tid = threadIdx.x, T = blockDim.x;
+    if (tid == 0) {
+        int o = 0;
+        bool bad = false;
+        for (int r = 0; r < 4; ++r) {
+            s_off[r] = o;
+            const int len = hb.clen[ctl->reg_tile_base[r]];
+            bad |= (len < 1) || (ctl->reg_tile_base[r + 1] <= ctl->reg_tile_base[r]);
+            o += len - 1;
+        }
+        s_off[4] = (bad || o > 2 * n + 8) ? -1 : o;
+    }
+    __syncthreads();
+    const int m = s_off[4];
+    if (m < 0) {   // inconsistent chain state: report instead of reading out of range
+        if (tid == 0) { set_status(ctl, CH_ECUDA); *out_n = CH_ECUDA; }
+        return;
+    }
+    if (m == 0) {   // all four quad vertices coincide: a single point
+        if (tid == 0) { out_idx[0] = ctl->oct.ext[W]; *out_n = 1; }
+        return;
+    }
+    for (int r = 0; r < 4; ++r) {
+        const size_t o = (size_t)ctl->reg_tile_base[r] * kChainTile;
+        const int len = s_off[r + 1] - s_off[r];
+        for (int j = tid; j < len; j += T) vbuf[s_off[r] + j] = hb.ci[o + j];
+    }
+    __syncthreads();
+    // turn at every vertex of the cyclic sequence
+    long long npos = 0, nneg = 0;
+    for (int i = tid; i < m; i += T) {
+        long long ax, ay, bx, by, cx, cy;
+        pt_of(pts, vbuf[(i + m - 1) % m], ax, ay);
+        pt_of(pts, vbuf[i], bx, by);
+        pt_of(pts, vbuf[(i + 1) % m], cx, cy);
+        const long long tr = orient64(ax, ay, bx, by, cx, cy);
+        kbuf[i] = tr > 0;
+        npos += tr > 0;
+        nneg += tr < 0;
+    }
+    auto add = [](long long a, long long b) { return a + b; };
+    npos = block_reduce<long long>(npos, add, s_i64);
+    nneg = block_reduce<long long>(nneg, add, s_i64);
+    auto mn = [](unsigned long long a, unsigned long long b) { return a < b ? a : b; };
+    auto mx = [](unsigned long long a, unsigned long long b) { return a > b ? a : b; };
+    __shared__ int s_ia, s_ib;
+    if (npos == 0) {
+        // Degenerate: all points on a line (or one point): [lex-min, lex-max].
+        unsigned long long lo = ~0ull, hi = 0ull;
+        for (int i = tid; i < m; i += T) {
+            long long x, y;
+            pt_of(pts, vbuf[i], x, y);
+            const unsigned long long key = ((unsigned long long)x << 24) | (unsigned long long)y;
+            lo = key < lo ? key : lo;
+            hi = key > hi ? key : hi;
+        }
+        lo = block_reduce<unsigned long long>(lo, mn, s_u64);
+        hi = block_reduce<unsigned long long>(hi, mx, s_u64);
+        if (tid == 0) { s_ia = INT_MAX; s_ib = INT_MAX; }
+        __syncthreads();
+        for (int i = tid; i < m; i += T) {
+            long long x, y;
+            const int id = vbuf[i];
+            pt_of(pts, id, x, y);
+            const unsigned long long key = ((unsigned long long)x << 24) | (unsigned long long)y;
+            if (key == lo) atomicMin(&s_ia, id);
+            if (key == hi) atomicMin(&s_ib, id);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            out_idx[0] = s_ia;
+            if (lo == hi) *out_n = 1;
+            else { out_idx[1] = s_ib; *out_n = 2; }
+        }
+        return;
+    }
+    if (nneg != 0 && tid == 0) set_status(ctl, CH_ECUDA);   // internal consistency check
+    // Compact the strictly convex vertices and find the lexicographic minimum.
+    __shared__ int s_warp[32];
+    int written = 0;
+    unsigned long long best = ~0ull;
+    for (int base = 0; base < m; base += T) {
+        const int i = base + tid;
+        const int f = (i < m) ? kbuf[i] : 0;
+        const int lane = tid & 31, warp = tid >> 5;
+        int incl = f;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t2 = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += t2;
+        }
+        if (lane == 31) s_warp[warp] = incl;
+        __syncthreads();
+        int off = 0, tot = 0;
+        for (int w = 0; w < (T >> 5); ++w) { if (w < warp) off += s_warp[w]; tot += s_warp[w]; }
+        __syncthreads();
+        if (f) {
+            const int id = vbuf[i];
+            long long x, y;
+            pt_of(pts, id, x, y);
+            const unsigned long long key = ((unsigned long long)x << 24) | (unsigned long long)y;
+            best = key < best ? key : best;
+            vbuf[m + written + off + incl - f] = id;   // second half of the scratch
+        }
+        written += tot;
+    }
+    best = block_reduce<unsigned long long>(best, mn, s_u64);
+    const int h = written;
+    if (h > n) {   // cannot happen for a correct hull; never write past out_idx
+        if (tid == 0) { set_status(ctl, CH_ECUDA); *out_n = CH_ECUDA; }
+        return;
+    }
+    if (tid == 0) s_ia = 0;
+    __syncthreads();
+    for (int j = tid; j < h; j += T) {
+        long long x, y;
+        pt_of(pts, vbuf[m + j], x, y);
+        if ((((unsigned long long)x << 24) | (unsigned long long)y) == best) s_ia = j;
+    }
+    __syncthreads();
+    const int start = s_ia;
+    for (int j = tid; j < h; j += T) out_idx[j] = vbuf[m + (start + j) % h];
+    __syncthreads();
+    if (tid == 0) {
+        const int st2 = read_status(ctl);
+        *out_n = (st2 == CH_OK) ? h : st2;
+    }
+}
+
+// ---------------------------------------------------------------------------
+void launch_plan(Ctl* ctl, const uint32_t* keys, int* counters, int ctcap, cudaStream_t s) {
+    plan_kernel<<<1, 256, 0, s>>>(ctl, keys, counters, ctcap);
+}
+
+size_t chain_smem_bytes() { return (size_t)3 * kMergeSmemCap * sizeof(int); }
+
+void launch_chain(Ctl* ctl, const uint32_t* keys, const uint64_t* vals, int* cu, int* cv, int* ci,
+                  int* clen, int* counters, int ctcap, int grid, cudaStream_t s) {
+    HullBufs hb{keys, vals, cu, cv, ci, clen, counters, ctcap};
+    chain_kernel<<<grid, kChainThreads, chain_smem_bytes(), s>>>(ctl, hb);
+}
+
+void launch_stitch(const float* pts, long long n, Ctl* ctl, const int* cu, const int* cv, const int* ci,
+                   const int* clen, int* vbuf, int* kbuf, int32_t* out_idx, int64_t* out_n,
+                   cudaStream_t s) {
+    HullBufs hb{nullptr, nullptr, const_cast<int*>(cu), const_cast<int*>(cv), const_cast<int*>(ci),
+                const_cast<int*>(clen), nullptr, 0};
+    stitch_kernel<<<1, 1024, 0, s>>>(pts, n, ctl, hb, vbuf, kbuf, out_idx, out_n);
+}
+
+cudaError_t configure_hull_kernels() {
+    return cudaFuncSetAttribute(chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)chain_smem_bytes());
+}
+
+
+cudaError_t occupancy_chain(int* b) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(b, chain_kernel, kChainThreads, chain_smem_bytes());
+}
+
+}  // namespace ch

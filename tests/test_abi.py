@@ -1,0 +1,65 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, and exports every
+function include/ch.h declares; host-side argument checks answer without
+touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ch.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ch_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def native():
+    from paper_2209_12310_gb300 import build as pkg_build
+    path = pkg_build()
+    assert os.path.exists(path)
+    import paper_2209_12310_gb300 as ch
+    return ch.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("ch_hull", "ch_hull_batched", "ch_filter", "ch_submit", "ch_poll",
+                 "ch_server_create", "ch_server_destroy", "ch_workspace_bytes", "ch_strerror"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(native):
+    lib = ctypes.CDLL(native._name)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, f"not exported: {missing}"
+
+
+def test_binding_names_match_header():
+    from paper_2209_12310_gb300 import _native
+    assert sorted(_native.SIGNATURES) == _declared()
+
+
+def test_host_side_checks_without_gpu(native):
+    import paper_2209_12310_gb300 as ch
+    assert native.ch_hull(None, -1, None, None, None) == ch.CH_EINVAL
+    assert native.ch_hull(8, 10, 0, 0, None) == ch.CH_EINVAL          # null outputs
+    assert native.ch_hull(12, 10, 64, 64, None) == ch.CH_EINVAL        # pts not 8-byte aligned
+    assert native.ch_filter(None, -5, None, None, None, None) == ch.CH_EINVAL
+    assert native.ch_hull_batched(None, None, -1, None, None, None, None) == ch.CH_EINVAL
+    assert native.ch_hull_batched(None, None, 0, None, None, None, None) == ch.CH_OK
+    assert native.ch_poll(None, 1, None, 0, None) == ch.CH_EINVAL
+    assert native.ch_submit(None, None, 1, None) == ch.CH_EINVAL
+    assert ch.ch_strerror(ch.CH_ERANGE).startswith("coordinate")
+
+
+def test_workspace_size_is_linear(native):
+    import paper_2209_12310_gb300 as ch
+    a = ch.ch_workspace_bytes(1_000_000)
+    b = ch.ch_workspace_bytes(2_000_000)
+    assert 20 * 1_000_000 < a < 80 * 1_000_000
+    assert 1.8 < b / a < 2.2

@@ -1,0 +1,83 @@
+"""Continuous-batching server: each request's result equals the oracle (and
+ch_hull) whether it runs alone or in a mix of concurrent requests; admission
+and ticket errors are reported with status codes."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _wait(lib, srv, tickets, caps, timeout=120.0):
+    out = {}
+    t0 = time.time()
+    pending = set(tickets)
+    while pending and time.time() - t0 < timeout:
+        for t in list(pending):
+            buf = np.empty(max(caps[t], 1), np.int32)
+            st, n = lib.ch_poll(srv, t, buf.ctypes.data, caps[t])
+            if st == lib.CH_PENDING:
+                continue
+            assert st == lib.CH_OK, lib.ch_strerror(st)
+            out[t] = buf[:n].copy()
+            pending.discard(t)
+        time.sleep(0.001)
+    assert not pending, f"{len(pending)} requests not served in time"
+    return out
+
+
+def test_server_mix_matches_oracle(lib):
+    srv = lib.ch_server_create(2 << 30, 0)
+    try:
+        plan_sizes = [1000, 250_000, 3, 70_000, 1_000_000, 5000, 12, 400_000, 999, 150_000] * 3
+        kinds = ["normal", "uniform", "ring"]
+        reqs = [np.ascontiguousarray(W.make(kinds[i % 3], n, 100 + i)) for i, n in enumerate(plan_sizes)]
+        tickets, caps = [], {}
+        for i, p in enumerate(reqs):
+            st, t = lib.ch_submit(srv, p.ctypes.data, p.shape[0])
+            assert st == lib.CH_OK
+            tickets.append(t)
+            caps[t] = p.shape[0]
+            if i % 7 == 0:
+                time.sleep(0.002)   # arrivals while earlier batches run
+        res = _wait(lib, srv, tickets, caps)
+        for t, p in zip(tickets, reqs):
+            np.testing.assert_array_equal(res[t], oracle.hull(p))
+        # alone: the same request submitted by itself gives the same answer
+        p = reqs[4]
+        st, t = lib.ch_submit(srv, p.ctypes.data, p.shape[0])
+        alone = _wait(lib, srv, [t], {t: p.shape[0]})[t]
+        np.testing.assert_array_equal(alone, res[tickets[4]])
+        stats = lib.ch_server_stats(srv)
+        assert stats["completed"] == len(reqs) + 1
+        assert stats["p99_ms"] >= stats["p50_ms"] > 0
+    finally:
+        lib.ch_server_destroy(srv)
+
+
+def test_server_errors(lib):
+    srv = lib.ch_server_create(256 << 20, 0)
+    try:
+        st, _ = lib.ch_poll(srv, 987654321, None, 0)
+        assert st == lib.CH_EINVAL
+        # a request that can never fit the budget is refused before it is read
+        st, _ = lib.ch_submit(srv, 4096, 100_000_000)
+        assert st == lib.CH_ENOMEM
+        bad = np.array([[1.5, 2.0], [3.0, 4.0], [5.0, 1.0]], np.float32)
+        st, t = lib.ch_submit(srv, bad.ctypes.data, 3)
+        assert st == lib.CH_OK
+        t0 = time.time()
+        while True:
+            buf = np.empty(3, np.int32)
+            st, n = lib.ch_poll(srv, t, buf.ctypes.data, 3)
+            if st != lib.CH_PENDING or time.time() - t0 > 30:
+                break
+            time.sleep(0.001)
+        assert st == lib.CH_ERANGE and n == lib.CH_ERANGE
+    finally:
+        lib.ch_server_destroy(srv)
