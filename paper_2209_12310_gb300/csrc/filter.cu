@@ -225,32 +225,54 @@ __device__ __forceinline__ bool box_fits(const Octagon& o, int cx, int cy, int h
 __global__ void __launch_bounds__(256) finalize_kernel(const float* __restrict__ pts, long long n,
                                                        int head, Ctl* ctl, uint32_t* keys,
                                                        uint64_t* vals) {
-    __shared__ long long s_ext[8];
+    __shared__ unsigned long long s_ext[8];
+    __shared__ int s_G[8];
+    __shared__ long long s_lo[8], s_hi[8];
     __shared__ Octagon s_oct;
     if (read_status(ctl) != CH_OK) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (warp < 8) {
-        const int d = warp;
+    if (threadIdx.x < 8) {
+        const int d = threadIdx.x;
         const unsigned long long pk = ctl->ext_packed[d];
         const unsigned code = 0xFFFFFFFFu - (unsigned)(pk & 0xFFFFFFFFull);
         const unsigned hi32 = (unsigned)(pk >> 32);
-        const int G = dir_is_max(d) ? (int)hi32 : (int)(0xFFFFFFFFu - hi32);
+        s_G[d] = dir_is_max(d) ? (int)hi32 : (int)(0xFFFFFFFFu - hi32);
         long long lo, hi;
         if (code == 0u) { lo = 0; hi = head; }
         else { lo = head + (long long)(code - 1u) * kWarpTilePts; hi = min(n, lo + kWarpTilePts); }
-        long long found = LLONG_MAX;
-        for (long long i = lo + lane; i < hi; i += 32) {
-            const int X = __float2int_rn(pts[2 * i]), Y = __float2int_rn(pts[2 * i + 1]);
-            if (dir_key(d, X, Y) == G) { found = i; break; }
+        s_lo[d] = lo;
+        s_hi[d] = hi;
+        s_ext[d] = ~0ull;
+    }
+    __syncthreads();
+    // Rescan the winning tile of every direction for its lowest index (all
+    // loads issued up front: 8 directions x 2 points per thread).
+    {
+        float px[8][2], py[8][2];
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const long long i = s_lo[d] + threadIdx.x + h * 256;
+                px[d][h] = 0.0f; py[d][h] = 0.0f;
+                if (i < s_hi[d]) { px[d][h] = pts[2 * i]; py[d][h] = pts[2 * i + 1]; }
+            }
         }
 #pragma unroll
-        for (int o = 16; o; o >>= 1) found = min(found, __shfl_xor_sync(0xFFFFFFFFu, found, o));
-        if (lane == 0) s_ext[d] = found;
+        for (int d = 0; d < 8; ++d) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const long long i = s_lo[d] + threadIdx.x + h * 256;
+                if (i < s_hi[d] &&
+                    dir_key(d, __float2int_rn(px[d][h]), __float2int_rn(py[d][h])) == s_G[d])
+                    atomicMin(&s_ext[d], (unsigned long long)i);
+            }
+        }
     }
     __syncthreads();
     if (warp != 0) return;
     for (int d = 0; d < 8; ++d) {
-        if (s_ext[d] < 0 || s_ext[d] >= n) {   // cannot happen for valid input; fail safe
+        if (s_ext[d] >= (unsigned long long)n) {   // cannot happen for valid input; fail safe
             if (lane == 0) set_status(ctl, CH_ECUDA);
             return;
         }

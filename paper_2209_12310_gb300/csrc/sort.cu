@@ -67,14 +67,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(
     const unsigned epoch = ctl->epoch * 4u + (unsigned)pass;
     const int shift = pass * kDigitBits;
 
-    {   // global digit offsets of this pass
-        const unsigned a = ctl->digit_hist[pass][2 * threadIdx.x];
-        const unsigned b = ctl->digit_hist[pass][2 * threadIdx.x + 1];
-        const unsigned ex = block_excl_scan(a + b, s_warp);
-        s_base[2 * threadIdx.x] = ex;
-        s_base[2 * threadIdx.x + 1] = ex + a;
-    }
-
+    bool have_base = false;
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(&ctl->tile_ctr[pass], 1u);
         for (int i = threadIdx.x; i < (kSortThreads / 32) * kDigits; i += kSortThreads)
@@ -82,6 +75,14 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(
         __syncthreads();
         const unsigned tile = s_tile;
         if (tile >= ntiles) break;
+        if (!have_base) {   // global digit offsets of this pass (once per block)
+            const unsigned a = ctl->digit_hist[pass][2 * threadIdx.x];
+            const unsigned b = ctl->digit_hist[pass][2 * threadIdx.x + 1];
+            const unsigned ex = block_excl_scan(a + b, s_warp);
+            s_base[2 * threadIdx.x] = ex;
+            s_base[2 * threadIdx.x + 1] = ex + a;
+            have_base = true;
+        }
 
         const unsigned tbase = tile * kSortTile + warp * (32 * kSortItems);
         uint32_t k[kSortItems];
