@@ -175,7 +175,9 @@ def run_reference(args):
     kind, n, seed, desc = workload_config(args.workload, args.n)
     import oracle
     from synth import workloads as W
-    sample = 1_000_000
+    # per-step sample sized so the whole run stays near 90 s of single-core work
+    # (the oracle runs ~8e6 points/s on one core)
+    sample = int(min(1_000_000, max(10_000, 90.0 * 8e6 / max(1, args.steps + args.warmup))))
     pts = W.make(kind, sample, seed)
     for _ in range(args.warmup):
         oracle.hull(pts)
