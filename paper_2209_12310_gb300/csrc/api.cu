@@ -18,7 +18,7 @@ namespace ch {
 // Device information (SM count, resident blocks per SM of every kernel).
 struct DevInfo {
     int sms = 0;
-    int occ_p1 = 1, occ_p2 = 1, occ_lab = 1, occ_sort = 1, occ_chain = 1;
+    int occ_main = 1, occ_c = 1, occ_lab = 1, occ_sort = 1, occ_chain = 1;
 };
 
 static std::mutex g_mu;
@@ -31,11 +31,11 @@ static int device_info(int dev, DevInfo* out) {
     DevInfo di;
     if (cudaDeviceGetAttribute(&di.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return CH_ECUDA;
     if (configure_hull_kernels() != cudaSuccess) return CH_ECUDA;
-    if (occupancy_filter(&di.occ_p1, &di.occ_p2, &di.occ_lab) != cudaSuccess) return CH_ECUDA;
+    if (occupancy_filter(&di.occ_main, &di.occ_c, &di.occ_lab) != cudaSuccess) return CH_ECUDA;
     if (occupancy_sort(&di.occ_sort) != cudaSuccess) return CH_ECUDA;
     if (occupancy_chain(&di.occ_chain) != cudaSuccess) return CH_ECUDA;
-    di.occ_p1 = std::max(1, di.occ_p1);
-    di.occ_p2 = std::max(1, di.occ_p2);
+    di.occ_main = std::max(1, di.occ_main);
+    di.occ_c = std::max(1, di.occ_c);
     di.occ_lab = std::max(1, di.occ_lab);
     di.occ_sort = std::max(1, di.occ_sort);
     di.occ_chain = std::max(1, di.occ_chain);
@@ -233,15 +233,24 @@ int enqueue_hull(const float* pts, long long n, int32_t* out_idx, int64_t* out_n
 
     const int head = (((uintptr_t)pts & 15u) != 0u && n > 0) ? 1 : 0;
     const long long ntiles = (n - head) / kWarpTilePts;
-    const int grid1 = di.sms * di.occ_p1;
-    const int grid2 = di.sms * di.occ_p2;
+    const long long samples = std::min<long long>(ntiles, kSampleTiles);
+    const int grid_sample = (int)std::max<long long>(1, std::min<long long>(256, (samples + 7) / 8));
+    const int grid_main = di.sms * di.occ_main;
+    const int grid_c = di.sms * di.occ_c;
     const int grid_sort = di.sms * di.occ_sort;
     const int grid_chain = di.sms * di.occ_chain;
+    // Raw survivors of the fused pass live in the B buffers until stage C
+    // has turned them into sort records in the A buffers.
+    uint64_t* raw_xy = vB;
+    uint32_t* raw_idx = kB;
+    const unsigned switch_at = (unsigned)std::max<long long>(1 << 16, n >> 5);
 
-    { ProfScope p("init", s); launch_init(ctl, s); }
-    { ProfScope p("pass1_extremes", s); launch_pass1(pts, n, head, ntiles, ctl, grid1, s); }
-    { ProfScope p("finalize_octagon", s); launch_finalize(pts, n, head, ctl, kA, vA, s); }
-    { ProfScope p("pass2_filter", s); launch_pass2(pts, n, head, ntiles, ctl, kA, vA, grid2, s); }
+    { ProfScope p("init", s); launch_init(ctl, 0, s); }
+    { ProfScope p("sample", s); launch_sample(pts, n, head, ntiles, ctl, grid_sample, s); }
+    { ProfScope p("main_filter", s); launch_main(pts, n, head, ntiles, ctl, raw_xy, raw_idx, switch_at, grid_main, s); }
+    { ProfScope p("tail", s); launch_tail(pts, n, head, ctl, raw_xy, raw_idx, kA, vA, 0, 1, out_idx, out_n, s); }
+    { ProfScope p("stagec_filter", s); launch_stagec(pts, n, head, ntiles, ctl, raw_xy, raw_idx, kA, vA, grid_c, s); }
+    { ProfScope p("tail", s); launch_tail(pts, n, head, ctl, raw_xy, raw_idx, kA, vA, 1, 1, out_idx, out_n, s); }
     {
         ProfScope p("sort", s);
         launch_sort_pass(kA, vA, kB, vB, ctl, status, 0, grid_sort, s);
@@ -250,12 +259,8 @@ int enqueue_hull(const float* pts, long long n, int32_t* out_idx, int64_t* out_n
     }
     {
         ProfScope p("hull_chains", s);
-        launch_plan(ctl, kB, counters, (int)L.ctcap, s);
-        launch_chain(ctl, kB, vB, cu, cv, ci, clen, counters, (int)L.ctcap, grid_chain, s);
-    }
-    {
-        ProfScope p("stitch", s);
-        launch_stitch(pts, n, ctl, cu, cv, ci, clen, (int*)vA, (int*)kA, out_idx, out_n, s);
+        launch_chain(ctl, kB, vB, cu, cv, ci, clen, counters, (int)L.ctcap, (int*)vA, (int*)kA, pts, n, out_idx,
+                     out_n, grid_chain, s);
     }
     return cudaGetLastError() == cudaSuccess ? CH_OK : CH_ECUDA;
 }
@@ -306,12 +311,11 @@ int ch_filter(const float* pts, int64_t n, int32_t* out_ext8, uint8_t* out_label
     Ctl* ctl = (Ctl*)(base + L.off_ctl);
     const int head = (((uintptr_t)pts & 15u) != 0u) ? 1 : 0;
     const long long ntiles = (n - head) / kWarpTilePts;
-    { ProfScope p("init", s); launch_init(ctl, s); }
-    { ProfScope p("pass1_extremes", s); launch_pass1(pts, n, head, ntiles, ctl, di.sms * di.occ_p1, s); }
-    {
-        ProfScope p("finalize_octagon", s);
-        launch_finalize(pts, n, head, ctl, (uint32_t*)(base + L.off_kA), (uint64_t*)(base + L.off_vA), s);
-    }
+    uint32_t* kA = (uint32_t*)(base + L.off_kA);
+    uint64_t* vA = (uint64_t*)(base + L.off_vA);
+    { ProfScope p("init", s); launch_init(ctl, 1, s); }
+    { ProfScope p("main_filter", s); launch_main(pts, n, head, ntiles, ctl, nullptr, nullptr, 0xFFFFFFFFu, di.sms * di.occ_main, s); }
+    { ProfScope p("tail", s); launch_tail(pts, n, head, ctl, nullptr, nullptr, kA, vA, 0, 0, nullptr, nullptr, s); }
     if (out_labels || out_counts4) {
         ProfScope p("labels", s);
         launch_labels(pts, n, ctl, out_labels, di.sms * di.occ_lab, s);

@@ -37,6 +37,7 @@ constexpr int kChainThreads = 256;
 constexpr int kChainItems = 16;
 constexpr int kChainTile = kChainThreads * kChainItems;
 constexpr int kMergeSmemCap = 8192;           // chain points a global merge keeps on chip
+constexpr int kSampleTiles = 2048;            // warp tiles read by the sample pass
 constexpr int kMaxLevels = 32;
 
 // Float edge-function error bound: |e_float - e_exact| < 2^28 for every edge
@@ -58,27 +59,39 @@ struct Edge {
 
 struct Octagon {
     int vx[8], vy[8];    // vertices W, SW, S, SE, E, NE, N, NW
-    int ext[8];          // their indices
+    int ext[8];          // their indices (-1 for a sample octagon)
     Edge oct[8];         // octagon edges V[k] -> V[k+1]
     Edge quad[4];        // W->S, S->E, E->N, N->W (queue rule)
-    float bxl, bxh, byl, byh;  // open box strictly inside the octagon (may be empty)
+    int in_lo[4], in_hi[4];   // inner region: x, y, x+y, x-y+2^24 bounds (empty if lo > hi)
     int discard_none;    // octagon of zero area: nothing is discarded
     int pad[3];
 };
 
+// Small-path limits: the last block of a pass finishes the hull itself when
+// the survivors are few.
+constexpr unsigned kRawSmall = 16384;   // raw survivors one block re-classifies
+constexpr unsigned kTinyCap = 512;      // sort records one block turns into the hull
+
 // Per-call control block in device memory.
 struct Ctl {
     unsigned long long ext_packed[8];   // (key, ~tile) packed maxima of pass 1
+    unsigned long long samp_packed[8];  // (key, other coordinate) maxima of the sample pass
     int status;                         // CH_OK or a negative ch_status
     int abort;                          // set by a timed-out wait; all waits give up
-    unsigned int count;                 // records in the survivor buffer (8 extremes first)
+    unsigned int count;                 // sort records (the 8 extreme records first)
+    unsigned int count_raw;             // raw survivors of the fused pass
     unsigned int epoch;                 // onesweep status epoch (incremented per call)
+    int mode;                           // 0: fused single pass, 1: two streaming passes
+    int done;                           // the hull has been written by a small-path block
+    int records_ready;                  // sort records complete before the re-classify stage
+    unsigned int blocks_done[4];        // last-arriver counters (sample, main, stage C, roots)
     unsigned int tile_ctr[4];           // onesweep tile claim counters
     unsigned int digit_hist[kSortPasses][kDigits];
     unsigned int reg_start[4], reg_end[4];
     unsigned int reg_tile_base[5];      // chain tiles of queue r: [base[r], base[r+1])
     unsigned int counts4[4];            // survivors per queue (ch_filter)
-    Octagon oct;
+    Octagon oct;                        // octagon of the true extremes
+    Octagon oct_s;                      // octagon of a sample's extremes
 };
 
 // ---------------------------------------------------------------------------

@@ -1,20 +1,32 @@
 // filter.cu -- the filtering stage of GPU heaphull (Alg. 2, GPUfilter) on sm_103a.
 //
-//   init_kernel      reset the per-call control block
-//   pass1_kernel     findExtremes (Alg. 2; Sec. 3): one streaming pass computing
-//                    all 8 directional extremes (argmin/argmax of x, y, x+y, x-y).
-//                    The paper runs two reduction kernels because its corner
-//                    points are defined by Manhattan distance to the corners of
-//                    the axis-extreme box; that distance is x+y (or x-y) up to a
-//                    constant, so one pass finds all eight.
-//   finalize_kernel  lowest-index tie-break, octagon CP(E), queue quadrilateral,
-//                    inner box, float edge functions; writes the 8 extreme records.
-//   pass2_kernel     the loop of Alg. 1/2: drop points strictly inside CP(E),
-//                    findQueue by the quadrilateral rule, and compact the
-//                    survivors (warp-aggregated) into sort records.
-//   labels_kernel    the same loop writing the paper's label array Q (ch_filter).
+// Kernels (in launch order):
+//   init_kernel     reset the per-call control block.
+//   sample_kernel   extremes of an evenly spaced sample of warp tiles; its last
+//                   block builds the sample octagon (vertices are input points).
+//   main_kernel     findExtremes (Alg. 2; Sec. 3) over every point: all 8
+//                   directional extremes in one pass (the paper's second
+//                   kernel finds the corner points by Manhattan distance to the
+//                   bounding-box corners; that distance is x+y or x-y up to a
+//                   constant, so one pass suffices), with the lowest index on
+//                   ties.  In fused mode (ch_hull) the same pass also drops the
+//                   points in the closed sample octagon and compacts the rest
+//                   ("raw" survivors): one streaming read of the input instead
+//                   of two.  When the raw survivors grow past a threshold
+//                   (adversarial data such as points on a circle), the pass
+//                   stops filtering and the second pass does it (two-pass mode).
+//                   Its last block builds the octagon of the true extremes,
+//                   and when few raw survivors remain it re-classifies them,
+//                   and with few records left computes the hull itself.
+//   stagec_kernel   two-pass mode: the loop of Alg. 1/2 over every point
+//                   against the true octagon (findQueue by the quadrilateral
+//                   rule), or the re-classification of many raw survivors;
+//                   compaction into sort records (queue | u, v | index).
+//   labels_kernel   ch_filter: the label array Q of Alg. 2 (paper rule).
 #include "ch_internal.cuh"
+#include "hullcore.cuh"
 #include "launch.h"
+#include "octagon.cuh"
 
 #include <climits>
 
@@ -31,29 +43,151 @@ __device__ __forceinline__ int dir_key(int d, int X, int Y) {
     }
 }
 
+// Three-input max / min of non-negative int keys through their float bit
+// patterns: below 2^26 the patterns are positive finite floats (subnormal
+// below 2^23) that order like the integers; max.f32 without .ftz keeps
+// subnormals exact.
+__device__ __forceinline__ int kmax3(int a, int b, int c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(__int_as_float(a)), "f"(__int_as_float(b)), "f"(__int_as_float(c)));
+    return __float_as_int(r);
+}
+__device__ __forceinline__ int kmin3(int a, int b, int c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(__int_as_float(a)), "f"(__int_as_float(b)), "f"(__int_as_float(c)));
+    return __float_as_int(r);
+}
+
 // ---------------------------------------------------------------------------
-__global__ void init_kernel(Ctl* ctl) {
+__global__ void init_kernel(Ctl* ctl, int mode) {
     const int t = threadIdx.x;
-    if (t < 8) ctl->ext_packed[t] = 0ull;
-    if (t < 4) { ctl->tile_ctr[t] = 0u; ctl->counts4[t] = 0u; }
+    if (t < 8) { ctl->ext_packed[t] = 0ull; ctl->samp_packed[t] = 0ull; }
+    if (t < 4) { ctl->tile_ctr[t] = 0u; ctl->counts4[t] = 0u; ctl->blocks_done[t] = 0u; }
     if (t == 0) {
         ctl->status = CH_OK;
         ctl->abort = 0;
         ctl->count = 8u;
+        ctl->count_raw = 0u;
         ctl->epoch += 1u;
+        ctl->mode = mode;
+        ctl->done = 0;
+        ctl->records_ready = 0;
     }
     unsigned* h = &ctl->digit_hist[0][0];
     for (int i = t; i < kSortPasses * kDigits; i += blockDim.x) h[i] = 0u;
 }
 
+// Last-arriver election: returns true in exactly one block, after every other
+// block of the grid has finished (and made its writes visible).
+__device__ __forceinline__ bool last_block(unsigned* counter, int* s_flag) {
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) *s_flag = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!*s_flag) return false;
+    __threadfence();
+    if (threadIdx.x == 0) *counter = 0u;
+    return true;
+}
+
 // ---------------------------------------------------------------------------
-// Pass 1.  Each lane keeps, per direction, its best key and the first warp tile
-// (code) where that key occurred; tiles are visited in increasing index order,
-// so strict improvement keeps the earliest tile.  The grid-wide answer is the
-// maximum of (key, ~code) packed in 64 bits: the best key and, among tiles that
-// reach it, the lowest one.  finalize_kernel rescans that single tile (512
-// points) for the lowest index.  Tile codes: 0 = unaligned head point,
-// t + 1 = body warp tile t, ntiles + 1 = tail.
+// Sample pass: packed (key, other coordinate) maxima per direction; the other
+// coordinate recovers the point (no index needed: the sample octagon only
+// filters, and its vertices are input points).
+__device__ __forceinline__ unsigned long long samp_pack(int d, int X, int Y) {
+    const unsigned k = (unsigned)dir_key(d, X, Y);
+    const unsigned aux = (d == W || d == E) ? (unsigned)Y : (unsigned)X;
+    const unsigned hk = dir_is_max(d) ? k : 0xFFFFFFFFu - k;
+    return ((unsigned long long)hk << 32) | aux;
+}
+
+__global__ void __launch_bounds__(256) sample_kernel(const float* __restrict__ pts, long long n, int head,
+                                                     long long ntiles, Ctl* ctl) {
+    __shared__ unsigned long long s_red[8][8];
+    __shared__ Octagon s_o;
+    __shared__ int s_last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    unsigned long long best[8];
+#pragma unroll
+    for (int d = 0; d < 8; ++d) best[d] = 0ull;
+    const long long nsamp = ntiles < kSampleTiles ? ntiles : kSampleTiles;
+    const float4* p4 = reinterpret_cast<const float4*>(pts + 2 * head);
+    for (long long k = gwarp; k < nsamp; k += nwarps) {
+        const long long t = k * ntiles / nsamp;
+        const float4* base = p4 + t * kWarpTileF4 + lane;
+        float4 v[kLoadsPerLane];
+#pragma unroll
+        for (int j = 0; j < kLoadsPerLane; ++j) v[j] = ld_stream_f4(base + j * 32);
+#pragma unroll
+        for (int j = 0; j < kLoadsPerLane; ++j) {
+            const int X0 = __float2int_rn(v[j].x), Y0 = __float2int_rn(v[j].y);
+            const int X1 = __float2int_rn(v[j].z), Y1 = __float2int_rn(v[j].w);
+#pragma unroll
+            for (int d = 0; d < 8; ++d) {
+                const unsigned long long a = samp_pack(d, X0, Y0), b = samp_pack(d, X1, Y1);
+                const unsigned long long m = a > b ? a : b;
+                best[d] = m > best[d] ? m : best[d];
+            }
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+        unsigned long long p = best[d];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            const unsigned long long q = __shfl_xor_sync(0xFFFFFFFFu, p, o);
+            p = q > p ? q : p;
+        }
+        if (lane == 0) s_red[warp][d] = p;
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        unsigned long long m = 0ull;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = s_red[w][threadIdx.x] > m ? s_red[w][threadIdx.x] : m;
+        if (m) atomicMax(&ctl->samp_packed[threadIdx.x], m);
+    }
+    if (!last_block(&ctl->blocks_done[0], &s_last)) return;
+    if (warp != 0) return;
+    int vx[8], vy[8], ext[8];
+    bool ok = nsamp > 0;
+    for (int d = 0; d < 8; ++d) {
+        const unsigned long long p = *(volatile unsigned long long*)&ctl->samp_packed[d];
+        ok &= p != 0ull;
+        const unsigned hk = (unsigned)(p >> 32), aux = (unsigned)p;
+        const int key = dir_is_max(d) ? (int)hk : (int)(0xFFFFFFFFu - hk);
+        int x, y;
+        switch (d) {
+            case W: case E: x = key; y = (int)aux; break;
+            case S: case N: y = key; x = (int)aux; break;
+            case SW: case NE: x = (int)aux; y = key - x; break;
+            default: x = (int)aux; y = x - (key - kCoordLimit); break;
+        }
+        vx[d] = x; vy[d] = y; ext[d] = -1;
+    }
+    if (!ok) {   // too few points to sample: run the two-pass path
+        if (lane == 0) ctl->mode = 1;
+        return;
+    }
+    setup_octagon_warp(s_o, vx, vy, ext);
+    if (s_o.discard_none) {
+        if (lane == 0) ctl->mode = 1;
+        return;
+    }
+    const int words = (int)(sizeof(Octagon) / 4);
+    for (int i = lane; i < words; i += 32)
+        reinterpret_cast<int*>(&ctl->oct_s)[i] = reinterpret_cast<const int*>(&s_o)[i];
+}
+
+// ---------------------------------------------------------------------------
+// Main pass.  Each lane keeps, per direction, its best key and the first warp
+// tile (code) where that key occurred; tiles are visited in increasing index
+// order, so strict improvement keeps the earliest tile.  The grid-wide answer
+// is the maximum of (key, ~code) packed in 64 bits: the best key and, among
+// tiles reaching it, the lowest; the last block rescans that tile (512 points)
+// for the lowest index.  Tile codes: 0 = unaligned head point, t + 1 = body
+// warp tile t, ntiles + 1 = ragged tail.
 struct Track {
     int best[8];
     unsigned code[8];
@@ -71,7 +205,7 @@ __device__ __forceinline__ void track_init(Track& tr) {
     tr.orv = 0u;
 }
 
-// Convert one point, fold its validity into the tracker, return int coords.
+// Converts one point and folds its validity (integer value in [0, 2^24)).
 __device__ __forceinline__ void convert_pt(float x, float y, int& X, int& Y, Track& tr) {
     X = __float2int_rn(x);
     Y = __float2int_rn(y);
@@ -79,22 +213,18 @@ __device__ __forceinline__ void convert_pt(float x, float y, int& X, int& Y, Tra
     tr.orv |= (unsigned)X | (unsigned)Y;
 }
 
-__device__ __forceinline__ void tile_first(int (&tk)[8], int X, int Y) {
-    const int s = X + Y, d = X - Y + kCoordLimit;
-    tk[W] = X; tk[SW] = s; tk[S] = Y; tk[SE] = d;
-    tk[E] = X; tk[NE] = s; tk[N] = Y; tk[NW] = d;
-}
-
-__device__ __forceinline__ void tile_acc(int (&tk)[8], int X, int Y) {
-    const int s = X + Y, d = X - Y + kCoordLimit;
-    tk[W] = min(tk[W], X);
-    tk[SW] = min(tk[SW], s);
-    tk[S] = min(tk[S], Y);
-    tk[SE] = max(tk[SE], d);
-    tk[E] = max(tk[E], X);
-    tk[NE] = max(tk[NE], s);
-    tk[N] = max(tk[N], Y);
-    tk[NW] = min(tk[NW], d);
+__device__ __forceinline__ void tile_keys2(int (&tk)[8], int X0, int Y0, int X1, int Y1, bool first) {
+    const int s0 = X0 + Y0, s1 = X1 + Y1;
+    const int d0 = X0 - Y0 + kCoordLimit, d1 = X1 - Y1 + kCoordLimit;
+    if (first) {
+        tk[W] = min(X0, X1); tk[SW] = min(s0, s1); tk[S] = min(Y0, Y1); tk[SE] = max(d0, d1);
+        tk[E] = max(X0, X1); tk[NE] = max(s0, s1); tk[N] = max(Y0, Y1); tk[NW] = min(d0, d1);
+    } else {
+        tk[W] = kmin3(tk[W], X0, X1); tk[SW] = kmin3(tk[SW], s0, s1);
+        tk[S] = kmin3(tk[S], Y0, Y1); tk[SE] = kmax3(tk[SE], d0, d1);
+        tk[E] = kmax3(tk[E], X0, X1); tk[NE] = kmax3(tk[NE], s0, s1);
+        tk[N] = kmax3(tk[N], Y0, Y1); tk[NW] = kmin3(tk[NW], d0, d1);
+    }
 }
 
 __device__ __forceinline__ void track_tile(Track& tr, const int (&tk)[8], unsigned code) {
@@ -106,304 +236,61 @@ __device__ __forceinline__ void track_tile(Track& tr, const int (&tk)[8], unsign
     }
 }
 
+// Strictly inside the inner region of the sample octagon: the tile's key
+// extremes (or one point's keys) against the bounds, strict comparisons.
+__device__ __forceinline__ bool tile_in_inner(const int (&tk)[8], const int (&lo)[4], const int (&hi)[4]) {
+    return tk[W] > lo[0] && tk[E] < hi[0] && tk[S] > lo[1] && tk[N] < hi[1] &&
+           tk[SW] > lo[2] && tk[NE] < hi[2] && tk[NW] > lo[3] && tk[SE] < hi[3];
+}
+
+__device__ __forceinline__ bool pt_in_inner(int X, int Y, const int (&lo)[4], const int (&hi)[4]) {
+    const int S = X + Y, D = X - Y + kCoordLimit;
+    return X > lo[0] && X < hi[0] && Y > lo[1] && Y < hi[1] && S > lo[2] && S < hi[2] && D > lo[3] && D < hi[3];
+}
+
 __device__ __forceinline__ unsigned long long pack_best(int d, int best, unsigned code) {
     if (best == INT_MIN || best == INT_MAX) return 0ull;
     const unsigned k = dir_is_max(d) ? (unsigned)best : 0xFFFFFFFFu - (unsigned)best;
     return ((unsigned long long)k << 32) | (unsigned long long)(0xFFFFFFFFu - code);
 }
 
-// Head point and ragged tail (scalar loads), handled by global warp 0.
-__device__ void track_scalar_range(const float* __restrict__ pts, long long lo, long long hi,
-                                   unsigned code, int lane, Track& tr) {
-    int tk[8];
-    bool any = false;
-    for (long long i = lo + lane; i < hi; i += 32) {
-        int X, Y;
-        convert_pt(pts[2 * i], pts[2 * i + 1], X, Y, tr);
-        if (!any) tile_first(tk, X, Y); else tile_acc(tk, X, Y);
-        any = true;
-    }
-    if (any) track_tile(tr, tk, code);
-}
-
-__global__ void __launch_bounds__(256) pass1_kernel(const float* __restrict__ pts, long long n,
-                                                    int head, long long ntiles, Ctl* ctl) {
+// Warp-collective compaction of a lane's kept slots.  get(s, idx, x, y) reads
+// slot s; slots are unrolled so get indexes registers.
+template <int kSlots, typename Get>
+__device__ __forceinline__ void emit_raw(unsigned keep, Get get, Ctl* ctl, uint64_t* raw_xy, uint32_t* raw_idx,
+                                         unsigned& total_out) {
     const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    Track tr;
-    track_init(tr);
-    if (gwarp == 0 && head) track_scalar_range(pts, 0, head, 0u, lane, tr);
-
-    const float4* p4 = reinterpret_cast<const float4*>(pts + 2 * head);
-    for (long long t = gwarp; t < ntiles; t += nwarps) {
-        const float4* base = p4 + t * kWarpTileF4 + lane;
-        float4 v[kLoadsPerLane];
+    const unsigned c = __popc(keep);
+    unsigned incl = c;
 #pragma unroll
-        for (int j = 0; j < kLoadsPerLane; ++j) v[j] = ld_stream_f4(base + j * 32);
-        int tk[8];
-        int X, Y;
-        convert_pt(v[0].x, v[0].y, X, Y, tr);
-        tile_first(tk, X, Y);
-        convert_pt(v[0].z, v[0].w, X, Y, tr);
-        tile_acc(tk, X, Y);
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const unsigned total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    total_out = 0u;
+    if (total == 0u) return;
+    unsigned base = 0u;
+    if (lane == 31) base = atomicAdd(&ctl->count_raw, total);
+    base = __shfl_sync(0xFFFFFFFFu, base, 31);
+    total_out = base + total;
+    unsigned pos = base + incl - c;
 #pragma unroll
-        for (int j = 1; j < kLoadsPerLane; ++j) {
-            convert_pt(v[j].x, v[j].y, X, Y, tr);
-            tile_acc(tk, X, Y);
-            convert_pt(v[j].z, v[j].w, X, Y, tr);
-            tile_acc(tk, X, Y);
+    for (int s = 0; s < kSlots; ++s) {
+        if ((keep >> s) & 1u) {
+            long long idx;
+            float x, y;
+            get(s, idx, x, y);
+            raw_xy[pos] = ((unsigned long long)(unsigned)__float2int_rn(x) << 32) | (unsigned)__float2int_rn(y);
+            raw_idx[pos] = (uint32_t)idx;
+            ++pos;
         }
-        track_tile(tr, tk, (unsigned)(t + 1));
-    }
-    if (gwarp == 0) {
-        const long long ts = head + ntiles * kWarpTilePts;
-        if (ts < n) track_scalar_range(pts, ts, n, (unsigned)(ntiles + 1), lane, tr);
-    }
-
-    const bool err = tr.bad || (tr.orv >> kCoordBits) != 0u;
-    if (__any_sync(0xFFFFFFFFu, err) && lane == 0) set_status(ctl, CH_ERANGE);
-
-    __shared__ unsigned long long s_red[8][8];
-#pragma unroll
-    for (int d = 0; d < 8; ++d) {
-        unsigned long long p = pack_best(d, tr.best[d], tr.code[d]);
-#pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            const unsigned long long q = __shfl_xor_sync(0xFFFFFFFFu, p, o);
-            p = q > p ? q : p;
-        }
-        if (lane == 0) s_red[warp][d] = p;
-    }
-    __syncthreads();
-    if (threadIdx.x < 8) {
-        const int d = threadIdx.x;
-        unsigned long long m = 0ull;
-        const int nw = blockDim.x >> 5;
-        for (int w = 0; w < nw; ++w) m = s_red[w][d] > m ? s_red[w][d] : m;
-        if (m) atomicMax(&ctl->ext_packed[d], m);
     }
 }
 
-// ---------------------------------------------------------------------------
-// Octagon setup helpers (one warp).
-__device__ Edge make_edge(int ax, int ay, int bx, int by) {
-    Edge e;
-    e.ax = ax; e.ay = ay;
-    e.dx = bx - ax; e.dy = by - ay;
-    if (e.dx == 0 && e.dy == 0) {
-        e.A = 0.0f; e.B = 0.0f; e.C = kHugePositive;
-    } else {
-        // orient(a, b, p) = dx*py - dy*px + (dy*ax - dx*ay) = A*px + B*py + C.
-        // A, B, px, py are exact in fp32 (|.| < 2^24); C (|C| < 2^49) is rounded
-        // once.  With two FMAs the total error is below 2^25 + 2^26 + 2^27 < 2^28
-        // (= kEdgeTol): outside that band the float sign is the exact sign.
-        e.A = (float)(-e.dy);
-        e.B = (float)e.dx;
-        e.C = __ll2float_rn((long long)e.dy * ax - (long long)e.dx * ay);
-    }
-    return e;
-}
-
-__device__ __forceinline__ bool in_closed_octagon(const Octagon& o, long long px, long long py) {
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        const Edge& e = o.oct[k];
-        if ((e.dx | e.dy) == 0) continue;
-        if (orient64(e.ax, e.ay, (long long)e.ax + e.dx, (long long)e.ay + e.dy, px, py) < 0) return false;
-    }
-    return true;
-}
-
-__device__ __forceinline__ bool box_fits(const Octagon& o, int cx, int cy, int hw, int hh, int t) {
-    const long long a = (long long)hw * t / 1024, b = (long long)hh * t / 1024;
-    return in_closed_octagon(o, cx - a, cy - b) && in_closed_octagon(o, cx + a, cy - b) &&
-           in_closed_octagon(o, cx + a, cy + b) && in_closed_octagon(o, cx - a, cy + b);
-}
-
-__global__ void __launch_bounds__(256) finalize_kernel(const float* __restrict__ pts, long long n,
-                                                       int head, Ctl* ctl, uint32_t* keys,
-                                                       uint64_t* vals) {
-    __shared__ unsigned long long s_ext[8];
-    __shared__ int s_G[8];
-    __shared__ long long s_lo[8], s_hi[8];
-    __shared__ Octagon s_oct;
-    if (read_status(ctl) != CH_OK) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x < 8) {
-        const int d = threadIdx.x;
-        const unsigned long long pk = ctl->ext_packed[d];
-        const unsigned code = 0xFFFFFFFFu - (unsigned)(pk & 0xFFFFFFFFull);
-        const unsigned hi32 = (unsigned)(pk >> 32);
-        s_G[d] = dir_is_max(d) ? (int)hi32 : (int)(0xFFFFFFFFu - hi32);
-        long long lo, hi;
-        if (code == 0u) { lo = 0; hi = head; }
-        else { lo = head + (long long)(code - 1u) * kWarpTilePts; hi = min(n, lo + kWarpTilePts); }
-        s_lo[d] = lo;
-        s_hi[d] = hi;
-        s_ext[d] = ~0ull;
-    }
-    __syncthreads();
-    // Rescan the winning tile of every direction for its lowest index (all
-    // loads issued up front: 8 directions x 2 points per thread).
-    {
-        float px[8][2], py[8][2];
-#pragma unroll
-        for (int d = 0; d < 8; ++d) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const long long i = s_lo[d] + threadIdx.x + h * 256;
-                px[d][h] = 0.0f; py[d][h] = 0.0f;
-                if (i < s_hi[d]) { px[d][h] = pts[2 * i]; py[d][h] = pts[2 * i + 1]; }
-            }
-        }
-#pragma unroll
-        for (int d = 0; d < 8; ++d) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const long long i = s_lo[d] + threadIdx.x + h * 256;
-                if (i < s_hi[d] &&
-                    dir_key(d, __float2int_rn(px[d][h]), __float2int_rn(py[d][h])) == s_G[d])
-                    atomicMin(&s_ext[d], (unsigned long long)i);
-            }
-        }
-    }
-    __syncthreads();
-    if (warp != 0) return;
-    for (int d = 0; d < 8; ++d) {
-        if (s_ext[d] >= (unsigned long long)n) {   // cannot happen for valid input; fail safe
-            if (lane == 0) set_status(ctl, CH_ECUDA);
-            return;
-        }
-    }
-    if (lane == 0) {
-        long long area2 = 0;
-        for (int d = 0; d < 8; ++d) {
-            const long long i = s_ext[d];
-            s_oct.ext[d] = (int)i;
-            s_oct.vx[d] = __float2int_rn(pts[2 * i]);
-            s_oct.vy[d] = __float2int_rn(pts[2 * i + 1]);
-        }
-        for (int k = 0; k < 8; ++k) {
-            const int j = (k + 1) & 7;
-            area2 += (long long)s_oct.vx[k] * s_oct.vy[j] - (long long)s_oct.vx[j] * s_oct.vy[k];
-            s_oct.oct[k] = make_edge(s_oct.vx[k], s_oct.vy[k], s_oct.vx[j], s_oct.vy[j]);
-        }
-        for (int r = 0; r < 4; ++r) {
-            const int a = 2 * r, b = (2 * r + 2) & 7;
-            s_oct.quad[r] = make_edge(s_oct.vx[a], s_oct.vy[a], s_oct.vx[b], s_oct.vy[b]);
-        }
-        s_oct.discard_none = (area2 == 0);
-        s_oct.pad[0] = s_oct.pad[1] = s_oct.pad[2] = 0;
-    }
-    __syncwarp();
-    // Largest centred box (aspect of the bounding box) inside the closed
-    // octagon: two rounds of a 32-way search over t/1024.
-    const int cx = (s_oct.vx[W] + s_oct.vx[E]) / 2, cy = (s_oct.vy[S] + s_oct.vy[N]) / 2;
-    const int hw = (s_oct.vx[E] - s_oct.vx[W]) / 2, hh = (s_oct.vy[N] - s_oct.vy[S]) / 2;
-    int t1 = 0;
-    if (!s_oct.discard_none) {
-        unsigned ok = __ballot_sync(0xFFFFFFFFu, box_fits(s_oct, cx, cy, hw, hh, (lane + 1) * 32));
-        // nested boxes: predicate is monotone, so take the highest passing lane
-        t1 = ok ? (32 - __clz(ok)) * 32 : 0;
-        const int t2 = t1 + lane + 1;
-        ok = __ballot_sync(0xFFFFFFFFu, lane < 31 && t2 <= 1024 && box_fits(s_oct, cx, cy, hw, hh, t2));
-        if (ok) t1 += 32 - __clz(ok);
-    }
-    if (lane == 0) {
-        const long long a = (long long)hw * t1 / 1024, b = (long long)hh * t1 / 1024;
-        if (t1 > 0) {
-            s_oct.bxl = (float)(cx - a); s_oct.bxh = (float)(cx + a);
-            s_oct.byl = (float)(cy - b); s_oct.byh = (float)(cy + b);
-        } else {
-            s_oct.bxl = 1.0f; s_oct.bxh = 0.0f; s_oct.byl = 1.0f; s_oct.byh = 0.0f;
-        }
-    }
-    __syncwarp();
-    // Copy the octagon to the control block.
-    {
-        const int words = (int)(sizeof(Octagon) / 4);
-        const int* src = reinterpret_cast<const int*>(&s_oct);
-        int* dst = reinterpret_cast<int*>(&ctl->oct);
-        for (int i = lane; i < words; i += 32) dst[i] = src[i];
-    }
-    // The 8 chain end-point records: queue r runs from quad vertex r to r+1.
-    if (lane < 8) {
-        const int r = lane >> 1;
-        const int d = (lane & 1) ? ((2 * r + 2) & 7) : 2 * r;
-        uint32_t u, v;
-        queue_frame(r, s_oct.vx[d], s_oct.vy[d], u, v);
-        const uint32_t key = make_key(r, u);
-        keys[lane] = key;
-        vals[lane] = make_val(v, (uint32_t)s_oct.ext[d]);
-#pragma unroll
-        for (int p = 0; p < kSortPasses; ++p)
-            atomicAdd(&ctl->digit_hist[p][(key >> (p * kDigitBits)) & (kDigits - 1)], 1u);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Pass 2: classification of one point.  Returns -1 (discarded) or queue 0..3.
-// The octagon and queue tests run out of line: on filter-bound inputs almost
-// every point is settled by the inner-box test of classify().
-__device__ __noinline__ int classify_slow(float x, float y, const Octagon* op) {
-    const Octagon& o = *op;
-    if (!o.discard_none) {
-        float m = kHugePositive;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) m = fminf(m, fmaf(o.oct[k].A, x, fmaf(o.oct[k].B, y, o.oct[k].C)));
-        if (m > kEdgeTol) return -1;                                      // surely inside
-        if (m >= -kEdgeTol) {                                             // ambiguous band
-            const long long X = (long long)x, Y = (long long)y;
-            bool inside = true;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const Edge& e = o.oct[k];
-                if ((e.dx | e.dy) == 0) continue;
-                if (orient64(e.ax, e.ay, (long long)e.ax + e.dx, (long long)e.ay + e.dy, X, Y) <= 0)
-                    inside = false;
-            }
-            if (inside) return -1;
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const Edge& q = o.quad[r];
-        const float e = fmaf(q.A, x, fmaf(q.B, y, q.C));
-        if (e < -kEdgeTol) return r;
-        if (e <= kEdgeTol && (q.dx | q.dy) != 0) {
-            if (orient64(q.ax, q.ay, (long long)q.ax + q.dx, (long long)q.ay + q.dy,
-                         (long long)x, (long long)y) < 0)
-                return r;
-        }
-    }
-    return -1;
-}
-
-struct Box {
-    float xl, xh, yl, yh;
-};
-
-__device__ __forceinline__ int classify(float x, float y, const Box& b, const Octagon& o) {
-    if (x > b.xl && x < b.xh && y > b.yl && y < b.yh) return -1;   // strictly inside the box
-    return classify_slow(x, y, &o);
-}
-
-__device__ __forceinline__ void load_octagon_smem(Octagon& s, const Ctl* ctl) {
-    const int words = (int)(sizeof(Octagon) / 4);
-    const int* src = reinterpret_cast<const int*>(&ctl->oct);
-    int* dst = reinterpret_cast<int*>(&s);
-    for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
-}
-
-// Writes the records of the survivors held by this lane (bit s of keep = point
-// slot s, its queue in bits 2s..2s+1 of regs) with one atomic per warp.
-// get(s, idx, x, y) returns slot s; slots are unrolled so get indexes registers.
 template <int kSlots, typename Get>
 __device__ __forceinline__ void emit_records(unsigned keep, unsigned long long regs, Get get, Ctl* ctl,
-                                             uint32_t* keys, uint64_t* vals,
-                                             unsigned (*s_hist)[kDigits]) {
+                                             uint32_t* keys, uint64_t* vals, unsigned (*s_hist)[kDigits]) {
     const int lane = threadIdx.x & 31;
     const unsigned c = __popc(keep);
     unsigned incl = c;
@@ -426,7 +313,7 @@ __device__ __forceinline__ void emit_records(unsigned keep, unsigned long long r
             get(s, idx, x, y);
             const int r = (int)((regs >> (2 * s)) & 3ull);
             uint32_t u, v;
-            queue_frame(r, (int)x, (int)y, u, v);
+            queue_frame(r, __float2int_rn(x), __float2int_rn(y), u, v);
             const uint32_t key = make_key(r, u);
             keys[pos] = key;
             vals[pos] = make_val(v, (uint32_t)idx);
@@ -438,97 +325,366 @@ __device__ __forceinline__ void emit_records(unsigned keep, unsigned long long r
     }
 }
 
-__global__ void __launch_bounds__(256) pass2_kernel(const float* __restrict__ pts, long long n,
-                                                    int head, long long ntiles, Ctl* ctl,
-                                                    uint32_t* keys, uint64_t* vals) {
-    __shared__ Octagon s_oct;
-    __shared__ unsigned s_hist[kSortPasses][kDigits];
-    if (read_status(ctl) != CH_OK) return;
-    load_octagon_smem(s_oct, ctl);
-    for (int i = threadIdx.x; i < kSortPasses * kDigits; i += blockDim.x) (&s_hist[0][0])[i] = 0u;
-    __syncthreads();
-    const Octagon& o = s_oct;
-    const Box box{o.bxl, o.bxh, o.byl, o.byh};
-    const int lane = threadIdx.x & 31;
-    const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    const float4* p4 = reinterpret_cast<const float4*>(pts + 2 * head);
-
-    for (long long t = gwarp; t < ntiles; t += nwarps) {
-        const float4* base = p4 + t * kWarpTileF4 + lane;
-        float4 v[kLoadsPerLane];
-#pragma unroll
-        for (int j = 0; j < kLoadsPerLane; ++j) v[j] = ld_stream_f4(base + j * 32);
-        unsigned keep = 0u;
-        unsigned long long regs = 0ull;
-#pragma unroll
-        for (int j = 0; j < kLoadsPerLane; ++j) {
-            const int r0 = classify(v[j].x, v[j].y, box, o);
-            const int r1 = classify(v[j].z, v[j].w, box, o);
-            if (r0 >= 0) { keep |= 1u << (2 * j); regs |= (unsigned long long)r0 << (4 * j); }
-            if (r1 >= 0) { keep |= 1u << (2 * j + 1); regs |= (unsigned long long)r1 << (4 * j + 2); }
-        }
-        if (__any_sync(0xFFFFFFFFu, keep != 0u)) {
-            const long long i0 = head + 2 * (t * kWarpTileF4 + lane);
-            auto get = [&](int s, long long& idx, float& x, float& y) {
-                const int j = s >> 1;
-                idx = i0 + 64 * j + (s & 1);
-                x = (s & 1) ? v[j].z : v[j].x;
-                y = (s & 1) ? v[j].w : v[j].y;
-            };
-            emit_records<2 * kLoadsPerLane>(keep, regs, get, ctl, keys, vals, s_hist);
-        }
-    }
-    if (gwarp == 0) {   // head point and ragged tail, 16 points per lane per round
-        const long long ranges[2][2] = {{0, head}, {head + ntiles * kWarpTilePts, n}};
-        for (int rg = 0; rg < 2; ++rg) {
-            const long long hi = ranges[rg][1];
-            for (long long b = ranges[rg][0]; b < hi; b += 32 * 16) {
-                unsigned keep = 0u;
-                unsigned long long regs = 0ull;
-                float px[16], py[16];
-#pragma unroll
-                for (int s = 0; s < 16; ++s) {
-                    const long long i = b + s * 32 + lane;
-                    px[s] = 0.0f; py[s] = 0.0f;
-                    if (i < hi) {
-                        px[s] = pts[2 * i]; py[s] = pts[2 * i + 1];
-                        const int r = classify(px[s], py[s], box, o);
-                        if (r >= 0) { keep |= 1u << s; regs |= (unsigned long long)r << (2 * s); }
-                    }
-                }
-                auto get = [&](int s, long long& idx, float& x, float& y) {
-                    idx = b + s * 32 + lane;
-                    x = px[s];
-                    y = py[s];
-                };
-                emit_records<16>(keep, regs, get, ctl, keys, vals, s_hist);
-            }
-        }
-    }
+__device__ __forceinline__ void flush_hist(unsigned (*s_hist)[kDigits], Ctl* ctl) {
     __syncthreads();
     for (int i = threadIdx.x; i < kSortPasses * kDigits; i += blockDim.x) {
         const unsigned c = (&s_hist[0][0])[i];
         if (c) atomicAdd(&(&ctl->digit_hist[0][0])[i], c);
+        (&s_hist[0][0])[i] = 0u;
+    }
+    __syncthreads();
+}
+
+// Hull-rule classification: -1 = dropped, else queue.
+__device__ __forceinline__ int classify_hull(float x, float y, const Octagon& o) {
+    const int X = __float2int_rn(x), Y = __float2int_rn(y);
+    if (in_inner(o, X, Y)) return -1;
+    return classify_hull_slow(x, y, &o);
+}
+
+// Re-classifies raw survivors [0, hi) against the true octagon into sort
+// records; thread `start` of `stride` cooperating threads, warp-uniform loop.
+__device__ void reclassify_raw(const uint64_t* raw_xy, const uint32_t* raw_idx, unsigned hi, unsigned stride,
+                               unsigned start, const Octagon& o, Ctl* ctl, uint32_t* keys, uint64_t* vals,
+                               unsigned (*s_hist)[kDigits]) {
+    const int lane = threadIdx.x & 31;
+    for (unsigned b = start - lane; b < hi; b += stride) {
+        const unsigned i = b + lane;
+        unsigned keep = 0u;
+        unsigned long long regs = 0ull;
+        float x = 0.0f, y = 0.0f;
+        unsigned idx = 0u;
+        if (i < hi) {
+            const unsigned long long xy = raw_xy[i];
+            x = (float)(unsigned)(xy >> 32);
+            y = (float)(unsigned)(xy & 0xFFFFFFFFull);
+            idx = raw_idx[i];
+            const int r = classify_hull(x, y, o);
+            if (r >= 0) { keep = 1u; regs = (unsigned long long)r; }
+        }
+        auto get = [&](int, long long& id, float& px, float& py) { id = idx; px = x; py = y; };
+        emit_records<1>(keep, regs, get, ctl, keys, vals, s_hist);
+    }
+}
+
+// Finalize of the main pass (whole block): lowest-index tie-break, octagon of
+// the true extremes (-> s_o and ctl->oct), the 8 chain end-point records.
+__device__ void finalize_block(const float* __restrict__ pts, long long n, int head, Ctl* ctl, Octagon& s_o,
+                               uint32_t* keys, uint64_t* vals) {
+    __shared__ unsigned long long s_ext[8];
+    __shared__ int s_G[8];
+    __shared__ long long s_lo[8], s_hi[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x < 8) {
+        const int d = threadIdx.x;
+        const unsigned long long pk = *(volatile unsigned long long*)&ctl->ext_packed[d];
+        const unsigned code = 0xFFFFFFFFu - (unsigned)(pk & 0xFFFFFFFFull);
+        const unsigned hi32 = (unsigned)(pk >> 32);
+        s_G[d] = dir_is_max(d) ? (int)hi32 : (int)(0xFFFFFFFFu - hi32);
+        long long lo, hi;
+        if (code == 0u) { lo = 0; hi = head; }
+        else { lo = head + (long long)(code - 1u) * kWarpTilePts; hi = min(n, lo + kWarpTilePts); }
+        s_lo[d] = lo;
+        s_hi[d] = hi;
+        s_ext[d] = ~0ull;
+    }
+    __syncthreads();
+    for (int d = 0; d < 8; ++d) {
+        for (long long i = s_lo[d] + threadIdx.x; i < s_hi[d]; i += blockDim.x) {
+            const int X = __float2int_rn(pts[2 * i]), Y = __float2int_rn(pts[2 * i + 1]);
+            if (dir_key(d, X, Y) == s_G[d]) atomicMin(&s_ext[d], (unsigned long long)i);
+        }
+    }
+    __syncthreads();
+    bool bad = false;
+    for (int d = 0; d < 8; ++d) bad |= s_ext[d] >= (unsigned long long)n;
+    if (bad) {   // cannot happen for valid input; fail safe
+        if (threadIdx.x == 0) set_status(ctl, CH_ECUDA);
+        return;
+    }
+    if (warp == 0) {
+        int vx[8], vy[8], ext[8];
+        for (int d = 0; d < 8; ++d) {
+            const long long i = (long long)s_ext[d];
+            ext[d] = (int)i;
+            vx[d] = __float2int_rn(pts[2 * i]);
+            vy[d] = __float2int_rn(pts[2 * i + 1]);
+        }
+        setup_octagon_warp(s_o, vx, vy, ext);
+        if (lane < 8) {   // chain end points: queue r runs from quad vertex r to r+1
+            const int r = lane >> 1;
+            const int d = (lane & 1) ? ((2 * r + 2) & 7) : 2 * r;
+            uint32_t u, v;
+            queue_frame(r, vx[d], vy[d], u, v);
+            const uint32_t key = make_key(r, u);
+            keys[lane] = key;
+            vals[lane] = make_val(v, (uint32_t)ext[d]);
+#pragma unroll
+            for (int p = 0; p < kSortPasses; ++p)
+                atomicAdd(&ctl->digit_hist[p][(key >> (p * kDigitBits)) & (kDigits - 1)], 1u);
+        }
+    }
+    __syncthreads();
+    copy_octagon(&ctl->oct, &s_o);
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(256, 3) main_kernel(const float* __restrict__ pts, long long n, int head,
+                                                      long long ntiles, Ctl* ctl, uint64_t* raw_xy,
+                                                      uint32_t* raw_idx, unsigned switch_at) {
+    __shared__ int s_inner[8];
+    __shared__ unsigned long long s_red[8][8];
+    __shared__ int s_mode;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    if (threadIdx.x == 0) s_mode = *(volatile int*)&ctl->mode;   // one read: uniform per block
+    __syncthreads();
+    bool filt = s_mode == 0;
+    if (threadIdx.x < 4) {
+        s_inner[threadIdx.x] = ctl->oct_s.in_lo[threadIdx.x];
+        s_inner[4 + threadIdx.x] = ctl->oct_s.in_hi[threadIdx.x];
+    }
+    __syncthreads();
+    int lo[4], hi[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) { lo[k] = s_inner[k]; hi[k] = s_inner[4 + k]; }
+
+    Track tr;
+    track_init(tr);
+    // Scalar ranges (warp 0): the unaligned head point first and the ragged
+    // tail last, so every lane visits tile codes in increasing order.
+    auto scalar_range = [&](long long lo_i, long long hi_i, unsigned code) {
+        int tk[8];
+        bool any = false;
+        for (long long b = lo_i; b < hi_i; b += 32) {
+            const long long i = b + lane;
+            unsigned keep = 0u;
+            float x = 0.0f, y = 0.0f;
+            if (i < hi_i) {
+                x = pts[2 * i]; y = pts[2 * i + 1];
+                int X, Y;
+                convert_pt(x, y, X, Y, tr);
+                tile_keys2(tk, X, Y, X, Y, !any);
+                any = true;
+                if (filt && !pt_in_inner(X, Y, lo, hi)) keep = 1u;
+            }
+            auto get = [&](int, long long& idx, float& px, float& py) { idx = i; px = x; py = y; };
+            unsigned upto;
+            if (filt) emit_raw<1>(keep, get, ctl, raw_xy, raw_idx, upto);
+        }
+        if (any) track_tile(tr, tk, code);
+    };
+    if (gwarp == 0 && head) scalar_range(0, head, 0u);
+    const float4* p4 = reinterpret_cast<const float4*>(pts + 2 * head);
+    long long iter = 0;
+    for (long long t = gwarp; t < ntiles; t += nwarps, ++iter) {
+        const float4* base = p4 + t * kWarpTileF4 + lane;
+        float4 v[kLoadsPerLane];
+#pragma unroll
+        for (int j = 0; j < kLoadsPerLane; ++j) v[j] = ld_stream_f4(base + j * 32);
+        int tk[8];
+#pragma unroll
+        for (int j = 0; j < kLoadsPerLane; ++j) {
+            int X0, Y0, X1, Y1;
+            convert_pt(v[j].x, v[j].y, X0, Y0, tr);
+            convert_pt(v[j].z, v[j].w, X1, Y1, tr);
+            tile_keys2(tk, X0, Y0, X1, Y1, j == 0);
+        }
+        track_tile(tr, tk, (unsigned)(t + 1));
+        if (filt) {
+            // Points strictly inside the inner region of the sample octagon
+            // are strictly inside the hull; everything else is a raw survivor,
+            // classified against the true octagon once its extremes are known.
+            const bool inside = tile_in_inner(tk, lo, hi);
+            if (!__all_sync(0xFFFFFFFFu, inside)) {
+                // Reload the lane's points (just read, served by L2) rather than
+                // keeping them live across the tile: fewer registers in the
+                // streaming loop.
+                float4 w[kLoadsPerLane];
+                unsigned keep = 0u;
+                if (!inside) {
+#pragma unroll
+                    for (int j = 0; j < kLoadsPerLane; ++j) w[j] = __ldcg(base + j * 32);
+#pragma unroll
+                    for (int j = 0; j < kLoadsPerLane; ++j) {
+                        if (!pt_in_inner(__float2int_rn(w[j].x), __float2int_rn(w[j].y), lo, hi)) keep |= 1u << (2 * j);
+                        if (!pt_in_inner(__float2int_rn(w[j].z), __float2int_rn(w[j].w), lo, hi)) keep |= 2u << (2 * j);
+                    }
+                }
+                const long long i0 = head + 2 * (t * kWarpTileF4 + lane);
+                auto get = [&](int s, long long& idx, float& x, float& y) {
+                    const int j = s >> 1;
+                    idx = i0 + 64 * j + (s & 1);
+                    x = (s & 1) ? w[j].z : w[j].x;
+                    y = (s & 1) ? w[j].w : w[j].y;
+                };
+                unsigned upto;
+                emit_raw<2 * kLoadsPerLane>(keep, get, ctl, raw_xy, raw_idx, upto);
+                if (upto > switch_at) {   // dense data: leave filtering to the second pass
+                    if (lane == 0) atomicExch(&ctl->mode, 1);
+                    filt = false;
+                }
+            }
+            if ((iter & 7) == 7) {
+                int m = 0;
+                if (lane == 0) m = *(volatile int*)&ctl->mode;
+                filt = filt && __shfl_sync(0xFFFFFFFFu, m, 0) == 0;
+            }
+        }
+    }
+    if (gwarp == 0 && head + ntiles * kWarpTilePts < n)
+        scalar_range(head + ntiles * kWarpTilePts, n, (unsigned)(ntiles + 1));
+
+    const bool err = tr.bad || (tr.orv >> kCoordBits) != 0u;
+    if (__any_sync(0xFFFFFFFFu, err) && lane == 0) set_status(ctl, CH_ERANGE);
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+        unsigned long long p = pack_best(d, tr.best[d], tr.code[d]);
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            const unsigned long long q = __shfl_xor_sync(0xFFFFFFFFu, p, o);
+            p = q > p ? q : p;
+        }
+        if (lane == 0) s_red[warp][d] = p;
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        unsigned long long m = 0ull;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = s_red[w][threadIdx.x] > m ? s_red[w][threadIdx.x] : m;
+        if (m) atomicMax(&ctl->ext_packed[threadIdx.x], m);
+    }
+
+}
+
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256, 3) stagec_kernel(const float* __restrict__ pts, long long n, int head,
+                                                        long long ntiles, Ctl* ctl, const uint64_t* raw_xy,
+                                                        const uint32_t* raw_idx, uint32_t* keys, uint64_t* vals) {
+    __shared__ Octagon s_o;
+    __shared__ unsigned s_hist[kSortPasses][kDigits];
+    if (*(volatile int*)&ctl->done || *(volatile int*)&ctl->records_ready) return;
+    const int mode = *(volatile int*)&ctl->mode;
+    copy_octagon(&s_o, &ctl->oct);
+    for (int i = threadIdx.x; i < kSortPasses * kDigits; i += blockDim.x) (&s_hist[0][0])[i] = 0u;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    if (mode == 1) {   // second streaming pass over every point
+        const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+        const float4* p4 = reinterpret_cast<const float4*>(pts + 2 * head);
+        for (long long t = gwarp; t < ntiles; t += nwarps) {
+            const float4* base = p4 + t * kWarpTileF4 + lane;
+            float4 v[kLoadsPerLane];
+#pragma unroll
+            for (int j = 0; j < kLoadsPerLane; ++j) v[j] = ld_stream_f4(base + j * 32);
+            unsigned keep = 0u;
+            unsigned long long regs = 0ull;
+#pragma unroll
+            for (int j = 0; j < kLoadsPerLane; ++j) {
+                const int r0 = classify_hull(v[j].x, v[j].y, s_o);
+                const int r1 = classify_hull(v[j].z, v[j].w, s_o);
+                if (r0 >= 0) { keep |= 1u << (2 * j); regs |= (unsigned long long)r0 << (4 * j); }
+                if (r1 >= 0) { keep |= 1u << (2 * j + 1); regs |= (unsigned long long)r1 << (4 * j + 2); }
+            }
+            if (__any_sync(0xFFFFFFFFu, keep != 0u)) {
+                const long long i0 = head + 2 * (t * kWarpTileF4 + lane);
+                auto get = [&](int s, long long& idx, float& x, float& y) {
+                    const int j = s >> 1;
+                    idx = i0 + 64 * j + (s & 1);
+                    x = (s & 1) ? v[j].z : v[j].x;
+                    y = (s & 1) ? v[j].w : v[j].y;
+                };
+                emit_records<2 * kLoadsPerLane>(keep, regs, get, ctl, keys, vals, s_hist);
+            }
+        }
+        if (gwarp == 0) {
+            const long long ranges[2][2] = {{0, head}, {head + ntiles * kWarpTilePts, n}};
+            for (int rg = 0; rg < 2; ++rg) {
+                for (long long b = ranges[rg][0]; b < ranges[rg][1]; b += 32) {
+                    const long long i = b + lane;
+                    unsigned keep = 0u;
+                    unsigned long long regs = 0ull;
+                    float x = 0.0f, y = 0.0f;
+                    if (i < ranges[rg][1]) {
+                        x = pts[2 * i]; y = pts[2 * i + 1];
+                        const int r = classify_hull(x, y, s_o);
+                        if (r >= 0) { keep = 1u; regs = (unsigned long long)r; }
+                    }
+                    auto get = [&](int, long long& idx, float& px, float& py) { idx = i; px = x; py = y; };
+                    emit_records<1>(keep, regs, get, ctl, keys, vals, s_hist);
+                }
+            }
+        }
+    } else {   // many raw survivors of the fused pass: re-classify them
+        const unsigned nraw = *(volatile unsigned*)&ctl->count_raw;
+        reclassify_raw(raw_xy, raw_idx, nraw, gridDim.x * blockDim.x, blockIdx.x * blockDim.x + threadIdx.x,
+                       s_o, ctl, keys, vals, s_hist);
+    }
+    flush_hist(s_hist, ctl);
+}
+
+// ---------------------------------------------------------------------------
+// Single-block tail of a streaming pass.
+//   phase 0 (after main_kernel): octagon of the true extremes and the 8 chain
+//     end-point records; in fused mode with few raw survivors, re-classify them
+//     and, with few records left, compute the hull (ctl->done).
+//   phase 1 (after stagec_kernel): with few records, compute the hull.
+// Data errors found by the streaming pass end the call here: out_n = status.
+__global__ void __launch_bounds__(256) tail_kernel(const float* __restrict__ pts, long long n, int head, Ctl* ctl,
+                                                   const uint64_t* raw_xy, const uint32_t* raw_idx, uint32_t* keys,
+                                                   uint64_t* vals, int phase, int hull, int32_t* out_idx,
+                                                   int64_t* out_n) {
+    __shared__ Octagon s_o;
+    __shared__ unsigned s_hist[kSortPasses][kDigits];
+    __shared__ TinySmem s_tiny;
+    if (*(volatile int*)&ctl->done) return;
+    if (read_status(ctl) != CH_OK) {
+        if (hull && threadIdx.x == 0) { *out_n = read_status(ctl); ctl->done = 1; }
+        return;
+    }
+    if (phase == 0) {
+        finalize_block(pts, n, head, ctl, s_o, keys, vals);
+        if (read_status(ctl) != CH_OK) {
+            if (hull && threadIdx.x == 0) { *out_n = read_status(ctl); ctl->done = 1; }
+            return;
+        }
+        if (!hull) return;
+        const int mode = *(volatile int*)&ctl->mode;
+        const unsigned nraw = *(volatile unsigned*)&ctl->count_raw;
+        if (mode != 0 || nraw > kRawSmall) return;
+        for (int i = threadIdx.x; i < kSortPasses * kDigits; i += blockDim.x) (&s_hist[0][0])[i] = 0u;
+        __syncthreads();
+        reclassify_raw(raw_xy, raw_idx, nraw, blockDim.x, (unsigned)threadIdx.x, s_o, ctl, keys, vals, s_hist);
+        flush_hist(s_hist, ctl);
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) ctl->records_ready = 1;
+    }
+    const unsigned cnt = *(volatile unsigned*)&ctl->count;
+    if (phase == 1 && cnt > kTinyCap) return;
+    if (cnt <= kTinyCap) {
+        tiny_hull(keys, vals, (int)cnt, pts, n, ctl, out_idx, out_n, s_tiny);
+        if (threadIdx.x == 0) ctl->done = 1;
     }
 }
 
 // ---------------------------------------------------------------------------
-// ch_filter: the label array Q of Alg. 2 and the queue sizes.
+// ch_filter: the label array Q of Alg. 2 and the queue sizes (paper rule).
 __global__ void __launch_bounds__(256) labels_kernel(const float* __restrict__ pts, long long n,
                                                      Ctl* ctl, uint8_t* labels) {
-    __shared__ Octagon s_oct;
+    __shared__ Octagon s_o;
     __shared__ unsigned s_cnt[4];
     if (read_status(ctl) != CH_OK) return;
-    load_octagon_smem(s_oct, ctl);
+    copy_octagon(&s_o, &ctl->oct);
     if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0u;
     __syncthreads();
-    const Box box{s_oct.bxl, s_oct.bxh, s_oct.byl, s_oct.byh};
     unsigned c[4] = {0u, 0u, 0u, 0u};
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const float2 p = reinterpret_cast<const float2*>(pts)[i];
-        const int r = classify(p.x, p.y, box, s_oct);
+        const int X = __float2int_rn(p.x), Y = __float2int_rn(p.y);
+        const int r = in_inner_strict(s_o, X, Y) ? -1 : classify_paper_slow(p.x, p.y, &s_o);
         if (labels) labels[i] = (uint8_t)(r + 1);
         if (r >= 0) c[r]++;
     }
@@ -552,38 +708,40 @@ __global__ void filter_output_kernel(const Ctl* ctl, long long n, int32_t* out_e
 
 // ---------------------------------------------------------------------------
 // Host launchers
-void launch_init(Ctl* ctl, cudaStream_t s) { init_kernel<<<1, 256, 0, s>>>(ctl); }
+void launch_init(Ctl* ctl, int mode, cudaStream_t s) { init_kernel<<<1, 256, 0, s>>>(ctl, mode); }
 
-void launch_pass1(const float* pts, long long n, int head, long long ntiles, Ctl* ctl,
-                  int grid, cudaStream_t s) {
-    pass1_kernel<<<grid, 256, 0, s>>>(pts, n, head, ntiles, ctl);
+void launch_sample(const float* pts, long long n, int head, long long ntiles, Ctl* ctl, int grid, cudaStream_t s) {
+    sample_kernel<<<grid, 256, 0, s>>>(pts, n, head, ntiles, ctl);
 }
 
-void launch_finalize(const float* pts, long long n, int head, Ctl* ctl, uint32_t* keys,
-                     uint64_t* vals, cudaStream_t s) {
-    finalize_kernel<<<1, 256, 0, s>>>(pts, n, head, ctl, keys, vals);
+void launch_main(const float* pts, long long n, int head, long long ntiles, Ctl* ctl, uint64_t* raw_xy,
+                 uint32_t* raw_idx, unsigned switch_at, int grid, cudaStream_t s) {
+    main_kernel<<<grid, 256, 0, s>>>(pts, n, head, ntiles, ctl, raw_xy, raw_idx, switch_at);
 }
 
-void launch_pass2(const float* pts, long long n, int head, long long ntiles, Ctl* ctl,
-                  uint32_t* keys, uint64_t* vals, int grid, cudaStream_t s) {
-    pass2_kernel<<<grid, 256, 0, s>>>(pts, n, head, ntiles, ctl, keys, vals);
+void launch_tail(const float* pts, long long n, int head, Ctl* ctl, const uint64_t* raw_xy, const uint32_t* raw_idx,
+                 uint32_t* keys, uint64_t* vals, int phase, int hull, int32_t* out_idx, int64_t* out_n,
+                 cudaStream_t s) {
+    tail_kernel<<<1, 256, 0, s>>>(pts, n, head, ctl, raw_xy, raw_idx, keys, vals, phase, hull, out_idx, out_n);
 }
 
-void launch_labels(const float* pts, long long n, Ctl* ctl, uint8_t* labels, int grid,
-                   cudaStream_t s) {
+void launch_stagec(const float* pts, long long n, int head, long long ntiles, Ctl* ctl, const uint64_t* raw_xy,
+                   const uint32_t* raw_idx, uint32_t* keys, uint64_t* vals, int grid, cudaStream_t s) {
+    stagec_kernel<<<grid, 256, 0, s>>>(pts, n, head, ntiles, ctl, raw_xy, raw_idx, keys, vals);
+}
+
+void launch_labels(const float* pts, long long n, Ctl* ctl, uint8_t* labels, int grid, cudaStream_t s) {
     labels_kernel<<<grid, 256, 0, s>>>(pts, n, ctl, labels);
 }
 
-void launch_filter_output(const Ctl* ctl, long long n, int32_t* out_ext8, int64_t* out_counts4,
-                          cudaStream_t s) {
+void launch_filter_output(const Ctl* ctl, long long n, int32_t* out_ext8, int64_t* out_counts4, cudaStream_t s) {
     filter_output_kernel<<<1, 32, 0, s>>>(ctl, n, out_ext8, out_counts4);
 }
 
-
-cudaError_t occupancy_filter(int* p1, int* p2, int* lab) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(p1, pass1_kernel, 256, 0);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(p2, pass2_kernel, 256, 0);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(lab, labels_kernel, 256, 0);
+cudaError_t occupancy_filter(int* main_k, int* stagec, int* labels) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(main_k, main_kernel, 256, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(stagec, stagec_kernel, 256, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(labels, labels_kernel, 256, 0);
     return e;
 }
 

@@ -5,16 +5,16 @@
 // to quad vertex r+1 that is strictly monotone in the queue-frame coordinate u
 // (see queue_frame), and its hull chain is Andrew's lower chain (Table I) in
 // the (u, v) frame:
-//   plan_kernel    queue boundaries in the sorted records, chain-tile layout;
-//   chain_kernel   per tile of 4096 records: keep the minimum-(v, index)
+//   chain_kernel   queue boundaries from the top-digit histogram; per tile
+//                  of 4096 records: keep the minimum-(v, index)
 //                  record of every run of equal u (only it can be a vertex),
 //                  build per-thread chains, merge them pairwise in shared
 //                  memory, then merge tiles pairwise up a binary tree: the
 //                  block that completes a pair (second arrival on an atomic
 //                  counter) performs that merge, so no block ever waits;
-//   stitch_kernel  join the four queue chains, drop collinear junction
-//                  vertices, handle the degenerate (collinear / single point)
-//                  cases, rotate to the lexicographically smallest vertex.
+//                  the block completing the fourth queue root joins the
+//                  chains (stitch_core: collinear junction vertices dropped,
+//                  degenerate cases, rotation to the lex-smallest vertex).
 //
 // Merging two chains A, B (all u of A below all u of B): a_k (k > 0) stays iff
 // every b in B is strictly left of a_{k-1} -> a_k; b_l (l < |B|-1) stays iff
@@ -22,6 +22,7 @@
 // prefix of A / a suffix of B, and "every b" reduces to the minimum of a
 // linear function over the convex chain B, found by binary search.
 #include "ch_internal.cuh"
+#include "hullcore.cuh"
 #include "launch.h"
 
 #include <climits>
@@ -137,52 +138,6 @@ __device__ void bridge_block(const ChainPtr& A, int la, const ChainPtr& B, int l
 }
 
 // ---------------------------------------------------------------------------
-__global__ void plan_kernel(Ctl* ctl, const uint32_t* __restrict__ keys, int* counters, int ctcap) {
-    __shared__ unsigned s_b[5];
-    if (read_status(ctl) != CH_OK) return;
-    const unsigned count = ctl->count;
-    const int t = threadIdx.x;
-    if (t < 5) {
-        unsigned pos;
-        if (t == 0) pos = 0;
-        else if (t == 4) pos = count;
-        else {   // first record of queue t
-            const uint32_t target = (uint32_t)t << kKeyBits;
-            unsigned lo = 0, hi = count;
-            while (lo < hi) {
-                const unsigned mid = (lo + hi) >> 1;
-                if (keys[mid] < target) lo = mid + 1; else hi = mid;
-            }
-            pos = lo;
-        }
-        s_b[t] = pos;
-    }
-    __syncthreads();
-    if (t == 0) {
-        unsigned base = 0;
-        for (int r = 0; r < 4; ++r) {
-            ctl->reg_start[r] = s_b[r];
-            ctl->reg_end[r] = s_b[r + 1];
-            ctl->reg_tile_base[r] = base;
-            const unsigned len = s_b[r + 1] - s_b[r];
-            base += (len + kChainTile - 1) / kChainTile;
-        }
-        ctl->reg_tile_base[4] = base;
-    }
-    __syncthreads();
-    // Reset the merge counters of every tree node this call will use.
-    for (int r = 0; r < 4; ++r) {
-        const unsigned b0 = ctl->reg_tile_base[r];
-        const unsigned ct = ctl->reg_tile_base[r + 1] - b0;
-        for (int P = 1; P < kMaxLevels && ((1u << (P - 1)) < ct); ++P) {
-            const unsigned nodes = (ct + (1u << P) - 1) >> P;
-            for (unsigned k = t; k < nodes; k += blockDim.x)
-                counters[(size_t)(P - 1) * ctcap + b0 + (k << P)] = 0;
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
 struct HullBufs {
     const uint32_t* keys;   // sorted records
     const uint64_t* vals;
@@ -190,8 +145,14 @@ struct HullBufs {
     int* cv;
     int* ci;
     int* clen;
-    int* counters;
+    int* counters;          // merge-tree arrival counters (zero at rest)
     int ctcap;
+    int* vbuf;              // stitch scratch (2 * records ints)
+    int* kbuf;              // stitch scratch (records ints)
+    const float* pts;
+    long long n;
+    int32_t* out_idx;
+    int64_t* out_n;
 };
 
 // Merge chain B (at sb, length lb) into chain A (at sa, length la) in shared
@@ -235,18 +196,40 @@ __global__ void __launch_bounds__(kChainThreads) chain_kernel(Ctl* ctl, HullBufs
     __shared__ int s_len[kChainThreads];
     __shared__ int s_red[4];
     __shared__ int s_old;
+    __shared__ unsigned s_qn[4], s_q0[5], s_tb[5];
 
-    if (read_status(ctl) != CH_OK) return;
+    if (*(volatile int*)&ctl->done || read_status(ctl) != CH_OK) return;
     const int tid = threadIdx.x;
-    const unsigned total_tiles = ctl->reg_tile_base[4];
+    // Queue boundaries in the sorted records: queue r holds the top-pass
+    // digits [128 r, 128 (r + 1)), so its size is a sum of that histogram.
+    if (tid < 4) s_qn[tid] = 0u;
+    __syncthreads();
+    for (int d = tid; d < kDigits; d += blockDim.x) {
+        const unsigned c = ctl->digit_hist[kSortPasses - 1][d];
+        if (c) atomicAdd(&s_qn[d >> (kDigitBits - 2)], c);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        unsigned q = 0, tb = 0;
+        for (int r = 0; r < 4; ++r) {
+            s_q0[r] = q;
+            s_tb[r] = tb;
+            q += s_qn[r];
+            tb += (s_qn[r] + kChainTile - 1) / kChainTile;
+        }
+        s_q0[4] = q;
+        s_tb[4] = tb;
+    }
+    __syncthreads();
+    const unsigned total_tiles = s_tb[4];
 
     for (unsigned c = blockIdx.x; c < total_tiles; c += gridDim.x) {
         int r = 0;
-        while (r < 3 && c >= ctl->reg_tile_base[r + 1]) ++r;
-        const unsigned rb = ctl->reg_tile_base[r];
-        const unsigned ct = ctl->reg_tile_base[r + 1] - rb;
+        while (r < 3 && c >= s_tb[r + 1]) ++r;
+        const unsigned rb = s_tb[r];
+        const unsigned ct = s_tb[r + 1] - rb;
         const unsigned t_local = c - rb;
-        const unsigned q0 = ctl->reg_start[r], q1 = ctl->reg_end[r];
+        const unsigned q0 = s_q0[r], q1 = s_q0[r + 1];
         const unsigned ts = q0 + t_local * kChainTile;
         const unsigned te = min(q1, ts + kChainTile);
 
@@ -299,8 +282,9 @@ __global__ void __launch_bounds__(kChainThreads) chain_kernel(Ctl* ctl, HullBufs
         }
         // 4) climb the merge tree of queue r.
         unsigned L = 0, k = t_local;
+        bool root = false;
         for (;;) {
-            if (k == 0 && (1u << L) >= ct) break;             // root
+            if (k == 0 && (1u << L) >= ct) { root = true; break; }   // root of queue r
             const unsigned sib = k ^ 1u;
             if ((sib << L) >= ct) { ++L; k >>= 1; continue; }  // no sibling: pass through
             __threadfence();
@@ -351,189 +335,41 @@ __global__ void __launch_bounds__(kChainThreads) chain_kernel(Ctl* ctl, HullBufs
             k >>= 1;
         }
         __syncthreads();
+        if (!root) continue;
+        // 5) the block completing the fourth queue root joins the chains.
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) s_old = (int)atomicAdd(&ctl->blocks_done[3], 1u);
+        __syncthreads();
+        if (s_old != 3) continue;
+        __threadfence();
+        if (tid == 0) ctl->blocks_done[3] = 0u;
+        int off[5];
+        off[0] = 0;
+        for (int q = 0; q < 4; ++q) off[q + 1] = off[q] + __ldcg(hb.clen + s_tb[q]) - 1;
+        const int m = off[4];
+        if (m < 0 || m > (int)s_q0[4]) {   // inconsistent state: report, never read out of range
+            if (tid == 0) { set_status(ctl, CH_ECUDA); *hb.out_n = CH_ECUDA; }
+            return;
+        }
+        for (int q = 0; q < 4; ++q) {
+            const size_t o = (size_t)s_tb[q] * kChainTile;
+            for (int j = tid; j < off[q + 1] - off[q]; j += blockDim.x) hb.vbuf[off[q] + j] = __ldcg(hb.ci + o + j);
+        }
+        __syncthreads();
+        stitch_core(hb.vbuf, m, hb.kbuf, hb.vbuf + m, hb.pts, hb.n, ctl, hb.out_idx, hb.out_n);
+        return;
     }
 }
 
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void pt_of(const float* pts, int i, long long& x, long long& y) {
-    const float2 p = reinterpret_cast<const float2*>(pts)[i];
-    x = (long long)p.x;
-    y = (long long)p.y;
-}
-
-
-template <typename T, typename Op>
-__device__ T block_reduce(T v, Op op, T* s_tmp) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-    for (int o = 16; o; o >>= 1) v = op(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
-    if (lane == 0) s_tmp[warp] = v;
-    __syncthreads();
-    T r = s_tmp[0];
-    for (int w = 1; w < nw; ++w) r = op(r, s_tmp[w]);
-    __syncthreads();
-    return r;
-}
-
-__global__ void __launch_bounds__(1024) stitch_kernel(const float* __restrict__ pts, long long n,
-                                                      Ctl* ctl, HullBufs hb, int* vbuf, int* kbuf,
-                                                      int32_t* out_idx, int64_t* out_n) {
-    __shared__ unsigned long long s_u64[32];
-    __shared__ long long s_i64[32];
-    __shared__ int s_off[5];
-    const int st = read_status(ctl);
-    if (st != CH_OK) {
-        if (threadIdx.x == 0) *out_n = st;
-        return;
-    }
-    const int tid = threadIdx.x, T = blockDim.x;
-    if (tid == 0) {
-        int o = 0;
-        bool bad = false;
-        for (int r = 0; r < 4; ++r) {
-            s_off[r] = o;
-            const int len = hb.clen[ctl->reg_tile_base[r]];
-            bad |= (len < 1) || (ctl->reg_tile_base[r + 1] <= ctl->reg_tile_base[r]);
-            o += len - 1;
-        }
-        s_off[4] = (bad || o > 2 * n + 8) ? -1 : o;
-    }
-    __syncthreads();
-    const int m = s_off[4];
-    if (m < 0) {   // inconsistent chain state: report instead of reading out of range
-        if (tid == 0) { set_status(ctl, CH_ECUDA); *out_n = CH_ECUDA; }
-        return;
-    }
-    if (m == 0) {   // all four quad vertices coincide: a single point
-        if (tid == 0) { out_idx[0] = ctl->oct.ext[W]; *out_n = 1; }
-        return;
-    }
-    for (int r = 0; r < 4; ++r) {
-        const size_t o = (size_t)ctl->reg_tile_base[r] * kChainTile;
-        const int len = s_off[r + 1] - s_off[r];
-        for (int j = tid; j < len; j += T) vbuf[s_off[r] + j] = hb.ci[o + j];
-    }
-    __syncthreads();
-    // turn at every vertex of the cyclic sequence
-    long long npos = 0, nneg = 0;
-    for (int i = tid; i < m; i += T) {
-        long long ax, ay, bx, by, cx, cy;
-        pt_of(pts, vbuf[(i + m - 1) % m], ax, ay);
-        pt_of(pts, vbuf[i], bx, by);
-        pt_of(pts, vbuf[(i + 1) % m], cx, cy);
-        const long long tr = orient64(ax, ay, bx, by, cx, cy);
-        kbuf[i] = tr > 0;
-        npos += tr > 0;
-        nneg += tr < 0;
-    }
-    auto add = [](long long a, long long b) { return a + b; };
-    npos = block_reduce<long long>(npos, add, s_i64);
-    nneg = block_reduce<long long>(nneg, add, s_i64);
-    auto mn = [](unsigned long long a, unsigned long long b) { return a < b ? a : b; };
-    auto mx = [](unsigned long long a, unsigned long long b) { return a > b ? a : b; };
-    __shared__ int s_ia, s_ib;
-    if (npos == 0) {
-        // Degenerate: all points on a line (or one point): [lex-min, lex-max].
-        unsigned long long lo = ~0ull, hi = 0ull;
-        for (int i = tid; i < m; i += T) {
-            long long x, y;
-            pt_of(pts, vbuf[i], x, y);
-            const unsigned long long key = ((unsigned long long)x << 24) | (unsigned long long)y;
-            lo = key < lo ? key : lo;
-            hi = key > hi ? key : hi;
-        }
-        lo = block_reduce<unsigned long long>(lo, mn, s_u64);
-        hi = block_reduce<unsigned long long>(hi, mx, s_u64);
-        if (tid == 0) { s_ia = INT_MAX; s_ib = INT_MAX; }
-        __syncthreads();
-        for (int i = tid; i < m; i += T) {
-            long long x, y;
-            const int id = vbuf[i];
-            pt_of(pts, id, x, y);
-            const unsigned long long key = ((unsigned long long)x << 24) | (unsigned long long)y;
-            if (key == lo) atomicMin(&s_ia, id);
-            if (key == hi) atomicMin(&s_ib, id);
-        }
-        __syncthreads();
-        if (tid == 0) {
-            out_idx[0] = s_ia;
-            if (lo == hi) *out_n = 1;
-            else { out_idx[1] = s_ib; *out_n = 2; }
-        }
-        return;
-    }
-    if (nneg != 0 && tid == 0) set_status(ctl, CH_ECUDA);   // internal consistency check
-    // Compact the strictly convex vertices and find the lexicographic minimum.
-    __shared__ int s_warp[32];
-    int written = 0;
-    unsigned long long best = ~0ull;
-    for (int base = 0; base < m; base += T) {
-        const int i = base + tid;
-        const int f = (i < m) ? kbuf[i] : 0;
-        const int lane = tid & 31, warp = tid >> 5;
-        int incl = f;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t2 = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-            if (lane >= o) incl += t2;
-        }
-        if (lane == 31) s_warp[warp] = incl;
-        __syncthreads();
-        int off = 0, tot = 0;
-        for (int w = 0; w < (T >> 5); ++w) { if (w < warp) off += s_warp[w]; tot += s_warp[w]; }
-        __syncthreads();
-        if (f) {
-            const int id = vbuf[i];
-            long long x, y;
-            pt_of(pts, id, x, y);
-            const unsigned long long key = ((unsigned long long)x << 24) | (unsigned long long)y;
-            best = key < best ? key : best;
-            vbuf[m + written + off + incl - f] = id;   // second half of the scratch
-        }
-        written += tot;
-    }
-    best = block_reduce<unsigned long long>(best, mn, s_u64);
-    const int h = written;
-    if (h > n) {   // cannot happen for a correct hull; never write past out_idx
-        if (tid == 0) { set_status(ctl, CH_ECUDA); *out_n = CH_ECUDA; }
-        return;
-    }
-    if (tid == 0) s_ia = 0;
-    __syncthreads();
-    for (int j = tid; j < h; j += T) {
-        long long x, y;
-        pt_of(pts, vbuf[m + j], x, y);
-        if ((((unsigned long long)x << 24) | (unsigned long long)y) == best) s_ia = j;
-    }
-    __syncthreads();
-    const int start = s_ia;
-    for (int j = tid; j < h; j += T) out_idx[j] = vbuf[m + (start + j) % h];
-    __syncthreads();
-    if (tid == 0) {
-        const int st2 = read_status(ctl);
-        *out_n = (st2 == CH_OK) ? h : st2;
-    }
-}
-
-// ---------------------------------------------------------------------------
-void launch_plan(Ctl* ctl, const uint32_t* keys, int* counters, int ctcap, cudaStream_t s) {
-    plan_kernel<<<1, 256, 0, s>>>(ctl, keys, counters, ctcap);
-}
-
 size_t chain_smem_bytes() { return (size_t)3 * kMergeSmemCap * sizeof(int); }
 
-void launch_chain(Ctl* ctl, const uint32_t* keys, const uint64_t* vals, int* cu, int* cv, int* ci,
-                  int* clen, int* counters, int ctcap, int grid, cudaStream_t s) {
-    HullBufs hb{keys, vals, cu, cv, ci, clen, counters, ctcap};
+void launch_chain(Ctl* ctl, const uint32_t* keys, const uint64_t* vals, int* cu, int* cv, int* ci, int* clen,
+                  int* counters, int ctcap, int* vbuf, int* kbuf, const float* pts, long long n, int32_t* out_idx,
+                  int64_t* out_n, int grid, cudaStream_t s) {
+    HullBufs hb{keys, vals, cu, cv, ci, clen, counters, ctcap, vbuf, kbuf, pts, n, out_idx, out_n};
     chain_kernel<<<grid, kChainThreads, chain_smem_bytes(), s>>>(ctl, hb);
-}
-
-void launch_stitch(const float* pts, long long n, Ctl* ctl, const int* cu, const int* cv, const int* ci,
-                   const int* clen, int* vbuf, int* kbuf, int32_t* out_idx, int64_t* out_n,
-                   cudaStream_t s) {
-    HullBufs hb{nullptr, nullptr, const_cast<int*>(cu), const_cast<int*>(cv), const_cast<int*>(ci),
-                const_cast<int*>(clen), nullptr, 0};
-    stitch_kernel<<<1, 1024, 0, s>>>(pts, n, ctl, hb, vbuf, kbuf, out_idx, out_n);
 }
 
 cudaError_t configure_hull_kernels() {

@@ -9,32 +9,29 @@ namespace ch {
 
 struct Ctl;
 
-void launch_init(Ctl* ctl, cudaStream_t s);
-void launch_pass1(const float* pts, long long n, int head, long long ntiles, Ctl* ctl, int grid,
-                  cudaStream_t s);
-void launch_finalize(const float* pts, long long n, int head, Ctl* ctl, uint32_t* keys,
-                     uint64_t* vals, cudaStream_t s);
-void launch_pass2(const float* pts, long long n, int head, long long ntiles, Ctl* ctl,
-                  uint32_t* keys, uint64_t* vals, int grid, cudaStream_t s);
-void launch_labels(const float* pts, long long n, Ctl* ctl, uint8_t* labels, int grid,
-                   cudaStream_t s);
-void launch_filter_output(const Ctl* ctl, long long n, int32_t* out_ext8, int64_t* out_counts4,
-                          cudaStream_t s);
+void launch_init(Ctl* ctl, int mode, cudaStream_t s);
+void launch_sample(const float* pts, long long n, int head, long long ntiles, Ctl* ctl, int grid, cudaStream_t s);
+void launch_main(const float* pts, long long n, int head, long long ntiles, Ctl* ctl, uint64_t* raw_xy,
+                 uint32_t* raw_idx, unsigned switch_at, int grid, cudaStream_t s);
+void launch_tail(const float* pts, long long n, int head, Ctl* ctl, const uint64_t* raw_xy, const uint32_t* raw_idx,
+                 uint32_t* keys, uint64_t* vals, int phase, int hull, int32_t* out_idx, int64_t* out_n,
+                 cudaStream_t s);
+void launch_stagec(const float* pts, long long n, int head, long long ntiles, Ctl* ctl, const uint64_t* raw_xy,
+                   const uint32_t* raw_idx, uint32_t* keys, uint64_t* vals, int grid, cudaStream_t s);
+void launch_labels(const float* pts, long long n, Ctl* ctl, uint8_t* labels, int grid, cudaStream_t s);
+void launch_filter_output(const Ctl* ctl, long long n, int32_t* out_ext8, int64_t* out_counts4, cudaStream_t s);
 
 void launch_sort_pass(const uint32_t* kin, const uint64_t* vin, uint32_t* kout, uint64_t* vout,
                       Ctl* ctl, unsigned long long* status, int pass, int grid, cudaStream_t s);
 
-void launch_plan(Ctl* ctl, const uint32_t* keys, int* counters, int ctcap, cudaStream_t s);
-void launch_chain(Ctl* ctl, const uint32_t* keys, const uint64_t* vals, int* cu, int* cv, int* ci,
-                  int* clen, int* counters, int ctcap, int grid, cudaStream_t s);
-void launch_stitch(const float* pts, long long n, Ctl* ctl, const int* cu, const int* cv, const int* ci,
-                   const int* clen, int* vbuf, int* kbuf, int32_t* out_idx, int64_t* out_n,
-                   cudaStream_t s);
+void launch_chain(Ctl* ctl, const uint32_t* keys, const uint64_t* vals, int* cu, int* cv, int* ci, int* clen,
+                  int* counters, int ctcap, int* vbuf, int* kbuf, const float* pts, long long n, int32_t* out_idx,
+                  int64_t* out_n, int grid, cudaStream_t s);
 size_t chain_smem_bytes();
 cudaError_t configure_hull_kernels();
 
 // Occupancy (resident blocks per SM at each kernel's launch shape).
-cudaError_t occupancy_filter(int* pass1, int* pass2, int* labels);
+cudaError_t occupancy_filter(int* main_k, int* stagec, int* labels);
 cudaError_t occupancy_sort(int* sort);
 cudaError_t occupancy_chain(int* chain);
 

@@ -1,0 +1,226 @@
+// octagon.cuh -- the filter polygon CP(E) of Alg. 1/2 and its point tests.
+//
+// The octagon has the 8 extreme points as vertices, counter-clockwise
+// W, SW, S, SE, E, NE, N, NW.  Point tests:
+//   * paper rule (ch_filter labels, Alg. 2): discard p when it is STRICTLY
+//     inside the octagon;
+//   * hull rule (ch_hull): discard p when it is in the CLOSED octagon.  A point
+//     on an edge but not at a vertex lies between two input points and is no
+//     strictly convex hull vertex; a point at a vertex is a duplicate of an
+//     extreme, whose record carries the lowest index.  The hull is unchanged;
+//     collinear boundary points (common when coordinates clamp) are dropped
+//     early instead of in the hull stage.
+// An octagon of zero area discards nothing under either rule.
+//
+// Fast path: an inner region I = {x in [xl,xh], y in [yl,yh], x+y in [sl,sh],
+// x-y in [dl,dh]} (an octagon with axis and diagonal edges) verified exactly to
+// lie in the closed octagon.  Its bounds compare directly against the 8 keys
+// that pass 1 already computes, so a whole tile whose key extremes lie in I is
+// discarded with 8 comparisons.  Edge functions are evaluated in float with a
+// proven error bound (kEdgeTol) and fall back to exact int64 in the band.
+#pragma once
+
+#include "ch_internal.cuh"
+
+namespace ch {
+
+__device__ __forceinline__ Edge make_edge(int ax, int ay, int bx, int by) {
+    Edge e;
+    e.ax = ax; e.ay = ay;
+    e.dx = bx - ax; e.dy = by - ay;
+    if (e.dx == 0 && e.dy == 0) {
+        e.A = 0.0f; e.B = 0.0f; e.C = kHugePositive;
+    } else {
+        // orient(a, b, p) = dx*py - dy*px + (dy*ax - dx*ay) = A*px + B*py + C.
+        // A, B, px, py are exact in fp32 (|.| < 2^24); C (|C| < 2^49) is rounded
+        // once; each of the two FMAs adds at most half an ulp of a result below
+        // 2^50 and 2^51.  Total error < 2^25 + 2^26 + 2^27 < 2^28 = kEdgeTol.
+        e.A = (float)(-e.dy);
+        e.B = (float)e.dx;
+        e.C = __ll2float_rn((long long)e.dy * ax - (long long)e.dx * ay);
+    }
+    return e;
+}
+
+__device__ __forceinline__ long long edge_exact(const Edge& e, long long px, long long py) {
+    return (long long)e.dx * (py - e.ay) - (long long)e.dy * (px - e.ax);
+}
+
+__device__ __forceinline__ float edge_float(const Edge& e, float x, float y) {
+    return fmaf(e.A, x, fmaf(e.B, y, e.C));
+}
+
+__device__ __forceinline__ bool in_closed_octagon_exact(const Octagon& o, long long px, long long py) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const Edge& e = o.oct[k];
+        if ((e.dx | e.dy) == 0) continue;
+        if (edge_exact(e, px, py) < 0) return false;
+    }
+    return true;
+}
+
+// Inner-region membership from the pass-1 keys (X, Y, S = X + Y, D = X - Y + 2^24).
+__device__ __forceinline__ bool in_inner(const Octagon& o, int X, int Y) {
+    const int S = X + Y, D = X - Y + kCoordLimit;
+    return X >= o.in_lo[0] && X <= o.in_hi[0] && Y >= o.in_lo[1] && Y <= o.in_hi[1] &&
+           S >= o.in_lo[2] && S <= o.in_hi[2] && D >= o.in_lo[3] && D <= o.in_hi[3];
+}
+
+__device__ __forceinline__ bool in_inner_strict(const Octagon& o, int X, int Y) {
+    const int S = X + Y, D = X - Y + kCoordLimit;
+    return X > o.in_lo[0] && X < o.in_hi[0] && Y > o.in_lo[1] && Y < o.in_hi[1] &&
+           S > o.in_lo[2] && S < o.in_hi[2] && D > o.in_lo[3] && D < o.in_hi[3];
+}
+
+// Hull rule: -1 when p is in the closed octagon (or on the quadrilateral),
+// else its queue 0..3.  Out of line: the inner-region test settles most points.
+static __device__ __noinline__ int classify_hull_slow(float x, float y, const Octagon* op) {
+    const Octagon& o = *op;
+    if (!o.discard_none) {
+        float m = kHugePositive;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) m = fminf(m, edge_float(o.oct[k], x, y));
+        if (m > kEdgeTol) return -1;                            // surely inside
+        if (m >= -kEdgeTol && in_closed_octagon_exact(o, (long long)x, (long long)y)) return -1;
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const Edge& q = o.quad[r];
+        const float e = edge_float(q, x, y);
+        if (e < -kEdgeTol) return r;
+        if (e <= kEdgeTol && (q.dx | q.dy) != 0 && edge_exact(q, (long long)x, (long long)y) < 0) return r;
+    }
+    return -1;
+}
+
+// Paper rule: -1 when p is strictly inside the octagon (or in no queue).
+static __device__ __noinline__ int classify_paper_slow(float x, float y, const Octagon* op) {
+    const Octagon& o = *op;
+    if (!o.discard_none) {
+        float m = kHugePositive;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) m = fminf(m, edge_float(o.oct[k], x, y));
+        if (m > kEdgeTol) return -1;
+        if (m >= -kEdgeTol) {
+            bool inside = true;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const Edge& e = o.oct[k];
+                if ((e.dx | e.dy) == 0) continue;
+                if (edge_exact(e, (long long)x, (long long)y) <= 0) inside = false;
+            }
+            if (inside) return -1;
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const Edge& q = o.quad[r];
+        const float e = edge_float(q, x, y);
+        if (e < -kEdgeTol) return r;
+        if (e <= kEdgeTol && (q.dx | q.dy) != 0 && edge_exact(q, (long long)x, (long long)y) < 0) return r;
+    }
+    return -1;
+}
+
+// Strictly outside the closed octagon (the survivor test against a sample
+// octagon; no queue needed).  Degenerate octagons keep everything.
+static __device__ __noinline__ bool outside_closed_slow(float x, float y, const Octagon* op) {
+    const Octagon& o = *op;
+    if (o.discard_none) return true;
+    float m = kHugePositive;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) m = fminf(m, edge_float(o.oct[k], x, y));
+    if (m > kEdgeTol) return false;
+    if (m < -kEdgeTol) return true;
+    return !in_closed_octagon_exact(o, (long long)x, (long long)y);
+}
+
+// Inner region I(t): the 8-direction bounds of the octagon's own vertices,
+// shrunk about their centre by t/1024.  Its candidate vertices (the
+// intersections of consecutive bounding lines, integer points) span a polygon
+// that contains I(t), so all candidates in the closed octagon imply I(t) is.
+__device__ __forceinline__ void inner_bounds(const int lo0[4], const int hi0[4], int t, int lo[4], int hi[4]) {
+    const long long cx = ((long long)lo0[0] + hi0[0]) / 2, cy = ((long long)lo0[1] + hi0[1]) / 2;
+    const long long c[4] = {cx, cy, cx + cy, cx - cy + kCoordLimit};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        lo[k] = (int)(c[k] - (c[k] - lo0[k]) * t / 1024);
+        hi[k] = (int)(c[k] + (hi0[k] - c[k]) * t / 1024);
+    }
+}
+
+__device__ __forceinline__ bool inner_fits(const Octagon& o, const int lo[4], const int hi[4]) {
+    if (lo[0] > hi[0] || lo[1] > hi[1] || lo[2] > hi[2] || lo[3] > hi[3]) return false;
+    const long long xl = lo[0], xh = hi[0], yl = lo[1], yh = hi[1];
+    const long long sl = lo[2], sh = hi[2], dl = lo[3] - kCoordLimit, dh = hi[3] - kCoordLimit;
+    // consecutive lines: x=xl, x+y=sl, y=yl, x-y=dh, x=xh, x+y=sh, y=yh, x-y=dl
+    const long long px[8] = {xl, sl - yl, dh + yl, xh, xh, sh - yh, dl + yh, xl};
+    const long long py[8] = {sl - xl, yl, yl, xh - dh, sh - xh, yh, yh, xl - dl};
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        if (!in_closed_octagon_exact(o, px[k], py[k])) return false;
+    return true;
+}
+
+// Fills every field of o from the 8 vertices (one full warp calls this; lane 0
+// writes the scalar fields, all lanes search the inner region).
+static __device__ void setup_octagon_warp(Octagon& o, const int vx[8], const int vy[8], const int ext[8]) {
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) {
+        long long area2 = 0;
+        for (int d = 0; d < 8; ++d) {
+            o.vx[d] = vx[d];
+            o.vy[d] = vy[d];
+            o.ext[d] = ext[d];
+        }
+        for (int k = 0; k < 8; ++k) {
+            const int j = (k + 1) & 7;
+            area2 += (long long)vx[k] * vy[j] - (long long)vx[j] * vy[k];
+            o.oct[k] = make_edge(vx[k], vy[k], vx[j], vy[j]);
+        }
+        for (int r = 0; r < 4; ++r) {
+            const int a = 2 * r, b = (2 * r + 2) & 7;
+            o.quad[r] = make_edge(vx[a], vy[a], vx[b], vy[b]);
+        }
+        o.discard_none = (area2 == 0);
+    }
+    __syncwarp();
+    // 8-direction bounds of the octagon's vertices: x, y, x+y, x-y (biased).
+    const int lo0[4] = {vx[W], vy[S], vx[SW] + vy[SW], vx[NW] - vy[NW] + kCoordLimit};
+    const int hi0[4] = {vx[E], vy[N], vx[NE] + vy[NE], vx[SE] - vy[SE] + kCoordLimit};
+    int t1 = 0;
+    if (!o.discard_none) {
+        int lo[4], hi[4];
+        inner_bounds(lo0, hi0, (lane + 1) * 32, lo, hi);
+        unsigned ok = __ballot_sync(0xFFFFFFFFu, inner_fits(o, lo, hi));
+        t1 = ok ? (32 - __clz(ok)) * 32 : 0;   // nested regions: passing lanes form a prefix
+        const int t2 = t1 + lane + 1;
+        bool f = false;
+        if (lane < 31 && t2 <= 1024) {
+            inner_bounds(lo0, hi0, t2, lo, hi);
+            f = inner_fits(o, lo, hi);
+        }
+        ok = __ballot_sync(0xFFFFFFFFu, f);
+        if (ok) t1 += 32 - __clz(ok);
+    }
+    if (lane == 0) {
+        if (t1 > 0) {
+            int lo[4], hi[4];
+            inner_bounds(lo0, hi0, t1, lo, hi);
+            for (int k = 0; k < 4; ++k) { o.in_lo[k] = lo[k]; o.in_hi[k] = hi[k]; }
+        } else {
+            for (int k = 0; k < 4; ++k) { o.in_lo[k] = 1; o.in_hi[k] = 0; }   // empty
+        }
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ void copy_octagon(Octagon* dst, const Octagon* src) {
+    const int words = (int)(sizeof(Octagon) / 4);
+    const int* s = reinterpret_cast<const int*>(src);
+    int* d = reinterpret_cast<int*>(dst);
+    for (int i = threadIdx.x; i < words; i += blockDim.x) d[i] = s[i];
+}
+
+}  // namespace ch
