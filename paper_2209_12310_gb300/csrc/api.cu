@@ -50,7 +50,7 @@ static size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 
 Layout make_layout(long long n) {
     Layout L{};
-    L.cap = n + 8;
+    L.cap = n + 16;
     L.sort_tiles = (L.cap + kSortTile - 1) / kSortTile;
     L.ctcap = (L.cap + kChainTile - 1) / kChainTile + 4;
     size_t o = 0;

@@ -411,17 +411,34 @@ __device__ void finalize_block(const float* __restrict__ pts, long long n, int h
             vy[d] = __float2int_rn(pts[2 * i + 1]);
         }
         setup_octagon_warp(s_o, vx, vy, ext);
-        if (lane < 8) {   // chain end points: queue r runs from quad vertex r to r+1
-            const int r = lane >> 1;
-            const int d = (lane & 1) ? ((2 * r + 2) & 7) : 2 * r;
-            uint32_t u, v;
-            queue_frame(r, vx[d], vy[d], u, v);
-            const uint32_t key = make_key(r, u);
-            keys[lane] = key;
-            vals[lane] = make_val(v, (uint32_t)ext[d]);
+        if (lane < 12) {
+            // Lanes 0..7: chain end points (queue r runs from quad vertex r to
+            // r+1).  Lanes 8..11: the diagonal extreme of queue r, when it lies
+            // strictly right of the quad edge (the hull rule drops every point
+            // of the closed octagon, vertices included, so the vertices that
+            // can be hull vertices get their own record; on the edge it cannot).
+            int r, d;
+            bool emit = true;
+            if (lane < 8) {
+                r = lane >> 1;
+                d = (lane & 1) ? ((2 * r + 2) & 7) : 2 * r;
+            } else {
+                r = lane - 8;
+                d = 2 * r + 1;
+                const int a = 2 * r, b = (2 * r + 2) & 7;
+                emit = orient64(vx[a], vy[a], vx[b], vy[b], vx[d], vy[d]) < 0;
+            }
+            if (emit) {
+                uint32_t u, v;
+                queue_frame(r, vx[d], vy[d], u, v);
+                const uint32_t key = make_key(r, u);
+                const unsigned pos = lane < 8 ? (unsigned)lane : atomicAdd(&ctl->count, 1u);
+                keys[pos] = key;
+                vals[pos] = make_val(v, (uint32_t)ext[d]);
 #pragma unroll
-            for (int p = 0; p < kSortPasses; ++p)
-                atomicAdd(&ctl->digit_hist[p][(key >> (p * kDigitBits)) & (kDigits - 1)], 1u);
+                for (int p = 0; p < kSortPasses; ++p)
+                    atomicAdd(&ctl->digit_hist[p][(key >> (p * kDigitBits)) & (kDigits - 1)], 1u);
+            }
         }
     }
     __syncthreads();
