@@ -31,6 +31,7 @@ static int device_info(int dev, DevInfo* out) {
     DevInfo di;
     if (cudaDeviceGetAttribute(&di.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return CH_ECUDA;
     if (configure_hull_kernels() != cudaSuccess) return CH_ECUDA;
+    if (configure_filter_kernels() != cudaSuccess) return CH_ECUDA;
     if (occupancy_filter(&di.occ_main, &di.occ_c, &di.occ_lab) != cudaSuccess) return CH_ECUDA;
     if (occupancy_sort(&di.occ_sort) != cudaSuccess) return CH_ECUDA;
     if (occupancy_chain(&di.occ_chain) != cudaSuccess) return CH_ECUDA;
@@ -233,7 +234,7 @@ int enqueue_hull(const float* pts, long long n, int32_t* out_idx, int64_t* out_n
 
     const int head = (((uintptr_t)pts & 15u) != 0u && n > 0) ? 1 : 0;
     const long long ntiles = (n - head) / kWarpTilePts;
-    const long long samples = std::min<long long>(ntiles, kSampleTiles);
+    const long long samples = sample_tiles_host(ntiles);
     const int grid_sample = (int)std::max<long long>(1, std::min<long long>(256, (samples + 7) / 8));
     const int grid_main = di.sms * di.occ_main;
     const int grid_c = di.sms * di.occ_c;

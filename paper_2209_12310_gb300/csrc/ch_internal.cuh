@@ -69,8 +69,8 @@ struct Octagon {
 
 // Small-path limits: the last block of a pass finishes the hull itself when
 // the survivors are few.
-constexpr unsigned kRawSmall = 16384;   // raw survivors one block re-classifies
-constexpr unsigned kTinyCap = 512;      // sort records one block turns into the hull
+constexpr unsigned kRawSmall = 32768;   // raw survivors one block re-classifies
+constexpr int kMidCap = 8192;           // sort records one block turns into the hull
 
 // Per-call control block in device memory.
 struct Ctl {
@@ -90,6 +90,7 @@ struct Ctl {
     unsigned int reg_start[4], reg_end[4];
     unsigned int reg_tile_base[5];      // chain tiles of queue r: [base[r], base[r+1])
     unsigned int counts4[4];            // survivors per queue (ch_filter)
+    unsigned long long line_ep[8];      // end points of survivors on the 4 axis support lines
     Octagon oct;                        // octagon of the true extremes
     Octagon oct_s;                      // octagon of a sample's extremes
 };

@@ -61,7 +61,11 @@ __device__ __forceinline__ int kmin3(int a, int b, int c) {
 // ---------------------------------------------------------------------------
 __global__ void init_kernel(Ctl* ctl, int mode) {
     const int t = threadIdx.x;
-    if (t < 8) { ctl->ext_packed[t] = 0ull; ctl->samp_packed[t] = 0ull; }
+    if (t < 8) {
+        ctl->ext_packed[t] = 0ull;
+        ctl->samp_packed[t] = 0ull;
+        ctl->line_ep[t] = (t & 1) ? 0ull : ~0ull;   // even: minimum slot, odd: maximum slot
+    }
     if (t < 4) { ctl->tile_ctr[t] = 0u; ctl->counts4[t] = 0u; ctl->blocks_done[t] = 0u; }
     if (t == 0) {
         ctl->status = CH_OK;
@@ -90,6 +94,14 @@ __device__ __forceinline__ bool last_block(unsigned* counter, int* s_flag) {
     return true;
 }
 
+// Warp tiles read by the sample pass: about 1/32 of the input, at most
+// kSampleTiles (a million points), at least min(ntiles, 64).
+__host__ __device__ __forceinline__ long long sample_tiles(long long ntiles) {
+    long long s = ntiles / 32;
+    if (s < 64) s = ntiles < 64 ? ntiles : 64;
+    return s < kSampleTiles ? s : kSampleTiles;
+}
+
 // ---------------------------------------------------------------------------
 // Sample pass: packed (key, other coordinate) maxima per direction; the other
 // coordinate recovers the point (no index needed: the sample octagon only
@@ -112,7 +124,7 @@ __global__ void __launch_bounds__(256) sample_kernel(const float* __restrict__ p
     unsigned long long best[8];
 #pragma unroll
     for (int d = 0; d < 8; ++d) best[d] = 0ull;
-    const long long nsamp = ntiles < kSampleTiles ? ntiles : kSampleTiles;
+    const long long nsamp = sample_tiles(ntiles);
     const float4* p4 = reinterpret_cast<const float4*>(pts + 2 * head);
     for (long long k = gwarp; k < nsamp; k += nwarps) {
         const long long t = k * ntiles / nsamp;
@@ -254,11 +266,40 @@ __device__ __forceinline__ unsigned long long pack_best(int d, int best, unsigne
     return ((unsigned long long)k << 32) | (unsigned long long)(0xFFFFFFFFu - code);
 }
 
-// Warp-collective compaction of a lane's kept slots.  get(s, idx, x, y) reads
-// slot s; slots are unrolled so get indexes registers.
+// Raw survivors are staged per warp in shared memory and written out in
+// batches: one global atomic per batch instead of one per warp tile (a single
+// contended counter otherwise serialises at L2).
+constexpr int kWarpBuf = 256;
+struct RawBuf {
+    unsigned long long xy[kWarpBuf];
+    unsigned idx[kWarpBuf];
+};
+
+// Warp-collective; returns the global raw count after this batch.
+__device__ __forceinline__ unsigned flush_raw(RawBuf& b, unsigned& cnt, Ctl* ctl, uint64_t* raw_xy,
+                                              uint32_t* raw_idx) {
+    const int lane = threadIdx.x & 31;
+    if (cnt == 0u) return 0u;
+    unsigned base = 0u;
+    if (lane == 0) base = atomicAdd(&ctl->count_raw, cnt);
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    __syncwarp();
+    for (unsigned i = lane; i < cnt; i += 32) {
+        raw_xy[base + i] = b.xy[i];
+        raw_idx[base + i] = b.idx[i];
+    }
+    __syncwarp();
+    const unsigned after = base + cnt;
+    cnt = 0u;
+    return after;
+}
+
+// Warp-collective compaction of a lane's kept slots into the warp's buffer.
+// get(s, idx, x, y) reads slot s; slots are unrolled so get indexes registers.
+// Returns the global raw count when a batch was written out, else 0.
 template <int kSlots, typename Get>
-__device__ __forceinline__ void emit_raw(unsigned keep, Get get, Ctl* ctl, uint64_t* raw_xy, uint32_t* raw_idx,
-                                         unsigned& total_out) {
+__device__ __forceinline__ unsigned emit_raw(unsigned keep, Get get, RawBuf& b, unsigned& cnt, Ctl* ctl,
+                                             uint64_t* raw_xy, uint32_t* raw_idx) {
     const int lane = threadIdx.x & 31;
     const unsigned c = __popc(keep);
     unsigned incl = c;
@@ -268,12 +309,16 @@ __device__ __forceinline__ void emit_raw(unsigned keep, Get get, Ctl* ctl, uint6
         if (lane >= o) incl += t;
     }
     const unsigned total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-    total_out = 0u;
-    if (total == 0u) return;
-    unsigned base = 0u;
-    if (lane == 31) base = atomicAdd(&ctl->count_raw, total);
-    base = __shfl_sync(0xFFFFFFFFu, base, 31);
-    total_out = base + total;
+    if (total == 0u) return 0u;
+    unsigned after = 0u;
+    if (cnt + total > (unsigned)kWarpBuf) after = flush_raw(b, cnt, ctl, raw_xy, raw_idx);
+    const bool direct = total > (unsigned)kWarpBuf;   // a dense tile: straight to global memory
+    unsigned base = cnt;
+    if (direct) {
+        if (lane == 31) base = atomicAdd(&ctl->count_raw, total);
+        base = __shfl_sync(0xFFFFFFFFu, base, 31);
+        after = base + total;
+    }
     unsigned pos = base + incl - c;
 #pragma unroll
     for (int s = 0; s < kSlots; ++s) {
@@ -281,17 +326,55 @@ __device__ __forceinline__ void emit_raw(unsigned keep, Get get, Ctl* ctl, uint6
             long long idx;
             float x, y;
             get(s, idx, x, y);
-            raw_xy[pos] = ((unsigned long long)(unsigned)__float2int_rn(x) << 32) | (unsigned)__float2int_rn(y);
-            raw_idx[pos] = (uint32_t)idx;
+            const unsigned long long xy =
+                ((unsigned long long)(unsigned)__float2int_rn(x) << 32) | (unsigned)__float2int_rn(y);
+            if (direct) { raw_xy[pos] = xy; raw_idx[pos] = (uint32_t)idx; }
+            else { b.xy[pos] = xy; b.idx[pos] = (unsigned)idx; }
             ++pos;
         }
     }
+    __syncwarp();
+    if (!direct) cnt += total;
+    return after;
+}
+
+// Survivors on an axis support line of the true octagon (x = xmin, y = ymin,
+// x = xmax, y = ymax) lie on a hull edge; only the two extreme ones per line
+// can be hull vertices.  They are reduced into ctl->line_ep (minimum and
+// maximum along the line, lowest index on ties) instead of becoming records;
+// emit_line_records turns the end points into records afterwards.
+__device__ __forceinline__ bool reduce_on_line(const Octagon& o, int X, int Y, unsigned idx, Ctl* ctl) {
+    bool on = false;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        const bool hit = (l == 0) ? X == o.vx[W] : (l == 1) ? Y == o.vy[S] : (l == 2) ? X == o.vx[E] : Y == o.vy[N];
+        if (hit) {
+            const unsigned along = (l & 1) ? (unsigned)X : (unsigned)Y;
+            atomicMin(&ctl->line_ep[2 * l], ((unsigned long long)along << 32) | idx);
+            atomicMax(&ctl->line_ep[2 * l + 1], ((unsigned long long)along << 32) | (0xFFFFFFFFu - idx));
+            on = true;
+        }
+    }
+    return on;
 }
 
 template <int kSlots, typename Get>
 __device__ __forceinline__ void emit_records(unsigned keep, unsigned long long regs, Get get, Ctl* ctl,
-                                             uint32_t* keys, uint64_t* vals, unsigned (*s_hist)[kDigits]) {
+                                             uint32_t* keys, uint64_t* vals, unsigned (*s_hist)[kDigits],
+                                             const Octagon* lines = nullptr) {
     const int lane = threadIdx.x & 31;
+    if (lines) {   // divert support-line points to the end-point reduction
+#pragma unroll
+        for (int s = 0; s < kSlots; ++s) {
+            if ((keep >> s) & 1u) {
+                long long idx;
+                float x, y;
+                get(s, idx, x, y);
+                if (reduce_on_line(*lines, __float2int_rn(x), __float2int_rn(y), (unsigned)idx, ctl))
+                    keep &= ~(1u << s);
+            }
+        }
+    }
     const unsigned c = __popc(keep);
     unsigned incl = c;
 #pragma unroll
@@ -363,8 +446,37 @@ __device__ void reclassify_raw(const uint64_t* raw_xy, const uint32_t* raw_idx, 
             if (r >= 0) { keep = 1u; regs = (unsigned long long)r; }
         }
         auto get = [&](int, long long& id, float& px, float& py) { id = idx; px = x; py = y; };
-        emit_records<1>(keep, regs, get, ctl, keys, vals, s_hist);
+        emit_records<1>(keep, regs, get, ctl, keys, vals, s_hist, &o);
     }
+}
+
+// Records for the end points of the support-line survivors (one thread each).
+__device__ void emit_line_records(const Octagon& o, Ctl* ctl, uint32_t* keys, uint64_t* vals) {
+    const int t = threadIdx.x;
+    if (t >= 8) return;
+    const unsigned long long e = *(volatile unsigned long long*)&ctl->line_ep[t];
+    if ((t & 1) ? e == 0ull : e == ~0ull) return;   // no survivor on this line
+    const int l = t >> 1;
+    const int along = (int)(e >> 32);
+    const unsigned idx = (t & 1) ? 0xFFFFFFFFu - (unsigned)e : (unsigned)e;
+    int X, Y;
+    switch (l) {
+        case 0: X = o.vx[W]; Y = along; break;
+        case 1: X = along; Y = o.vy[S]; break;
+        case 2: X = o.vx[E]; Y = along; break;
+        default: X = along; Y = o.vy[N]; break;
+    }
+    const int r = classify_hull_slow((float)X, (float)Y, &o);
+    if (r < 0) return;   // cannot happen: it was a survivor
+    uint32_t u, v;
+    queue_frame(r, X, Y, u, v);
+    const uint32_t key = make_key(r, u);
+    const unsigned pos = atomicAdd(&ctl->count, 1u);
+    keys[pos] = key;
+    vals[pos] = make_val(v, idx);
+#pragma unroll
+    for (int p = 0; p < kSortPasses; ++p)
+        atomicAdd(&ctl->digit_hist[p][(key >> (p * kDigitBits)) & (kDigits - 1)], 1u);
 }
 
 // Finalize of the main pass (whole block): lowest-index tie-break, octagon of
@@ -452,6 +564,7 @@ __global__ void __launch_bounds__(256, 3) main_kernel(const float* __restrict__ 
     __shared__ int s_inner[8];
     __shared__ unsigned long long s_red[8][8];
     __shared__ int s_mode;
+    __shared__ RawBuf s_buf[8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -467,6 +580,8 @@ __global__ void __launch_bounds__(256, 3) main_kernel(const float* __restrict__ 
 #pragma unroll
     for (int k = 0; k < 4; ++k) { lo[k] = s_inner[k]; hi[k] = s_inner[4 + k]; }
 
+    RawBuf& wbuf = s_buf[warp];
+    unsigned wcnt = 0u;
     Track tr;
     track_init(tr);
     // Scalar ranges (warp 0): the unaligned head point first and the ragged
@@ -487,8 +602,7 @@ __global__ void __launch_bounds__(256, 3) main_kernel(const float* __restrict__ 
                 if (filt && !pt_in_inner(X, Y, lo, hi)) keep = 1u;
             }
             auto get = [&](int, long long& idx, float& px, float& py) { idx = i; px = x; py = y; };
-            unsigned upto;
-            if (filt) emit_raw<1>(keep, get, ctl, raw_xy, raw_idx, upto);
+            if (filt) emit_raw<1>(keep, get, wbuf, wcnt, ctl, raw_xy, raw_idx);
         }
         if (any) track_tile(tr, tk, code);
     };
@@ -536,8 +650,7 @@ __global__ void __launch_bounds__(256, 3) main_kernel(const float* __restrict__ 
                     x = (s & 1) ? w[j].z : w[j].x;
                     y = (s & 1) ? w[j].w : w[j].y;
                 };
-                unsigned upto;
-                emit_raw<2 * kLoadsPerLane>(keep, get, ctl, raw_xy, raw_idx, upto);
+                const unsigned upto = emit_raw<2 * kLoadsPerLane>(keep, get, wbuf, wcnt, ctl, raw_xy, raw_idx);
                 if (upto > switch_at) {   // dense data: leave filtering to the second pass
                     if (lane == 0) atomicExch(&ctl->mode, 1);
                     filt = false;
@@ -552,6 +665,7 @@ __global__ void __launch_bounds__(256, 3) main_kernel(const float* __restrict__ 
     }
     if (gwarp == 0 && head + ntiles * kWarpTilePts < n)
         scalar_range(head + ntiles * kWarpTilePts, n, (unsigned)(ntiles + 1));
+    flush_raw(wbuf, wcnt, ctl, raw_xy, raw_idx);
 
     const bool err = tr.bad || (tr.orv >> kCoordBits) != 0u;
     if (__any_sync(0xFFFFFFFFu, err) && lane == 0) set_status(ctl, CH_ERANGE);
@@ -612,7 +726,7 @@ __global__ void __launch_bounds__(256, 3) stagec_kernel(const float* __restrict_
                     x = (s & 1) ? v[j].z : v[j].x;
                     y = (s & 1) ? v[j].w : v[j].y;
                 };
-                emit_records<2 * kLoadsPerLane>(keep, regs, get, ctl, keys, vals, s_hist);
+                emit_records<2 * kLoadsPerLane>(keep, regs, get, ctl, keys, vals, s_hist, &s_o);
             }
         }
         if (gwarp == 0) {
@@ -629,7 +743,7 @@ __global__ void __launch_bounds__(256, 3) stagec_kernel(const float* __restrict_
                         if (r >= 0) { keep = 1u; regs = (unsigned long long)r; }
                     }
                     auto get = [&](int, long long& idx, float& px, float& py) { idx = i; px = x; py = y; };
-                    emit_records<1>(keep, regs, get, ctl, keys, vals, s_hist);
+                    emit_records<1>(keep, regs, get, ctl, keys, vals, s_hist, &s_o);
                 }
             }
         }
@@ -643,18 +757,19 @@ __global__ void __launch_bounds__(256, 3) stagec_kernel(const float* __restrict_
 
 // ---------------------------------------------------------------------------
 // Single-block tail of a streaming pass.
-//   phase 0 (after main_kernel): octagon of the true extremes and the 8 chain
+//   phase 0 (after main_kernel): octagon of the true extremes and the chain
 //     end-point records; in fused mode with few raw survivors, re-classify them
-//     and, with few records left, compute the hull (ctl->done).
-//   phase 1 (after stagec_kernel): with few records, compute the hull.
+//     here and, with few records, compute the hull (ctl->done).
+//   phase 1 (after stagec_kernel): support-line end-point records, then with
+//     few records compute the hull.
 // Data errors found by the streaming pass end the call here: out_n = status.
-__global__ void __launch_bounds__(256) tail_kernel(const float* __restrict__ pts, long long n, int head, Ctl* ctl,
-                                                   const uint64_t* raw_xy, const uint32_t* raw_idx, uint32_t* keys,
-                                                   uint64_t* vals, int phase, int hull, int32_t* out_idx,
-                                                   int64_t* out_n) {
+__global__ void __launch_bounds__(1024) tail_kernel(const float* __restrict__ pts, long long n, int head, Ctl* ctl,
+                                                    const uint64_t* raw_xy, const uint32_t* raw_idx, uint32_t* keys,
+                                                    uint64_t* vals, int phase, int hull, int32_t* out_idx,
+                                                    int64_t* out_n) {
+    extern __shared__ __align__(16) char dyn[];
     __shared__ Octagon s_o;
     __shared__ unsigned s_hist[kSortPasses][kDigits];
-    __shared__ TinySmem s_tiny;
     if (*(volatile int*)&ctl->done) return;
     if (read_status(ctl) != CH_OK) {
         if (hull && threadIdx.x == 0) { *out_n = read_status(ctl); ctl->done = 1; }
@@ -677,11 +792,17 @@ __global__ void __launch_bounds__(256) tail_kernel(const float* __restrict__ pts
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) ctl->records_ready = 1;
+    } else {
+        if (*(volatile int*)&ctl->records_ready) return;   // phase 0 produced every record
+        copy_octagon(&s_o, &ctl->oct);
+        __syncthreads();
     }
+    emit_line_records(s_o, ctl, keys, vals);
+    __threadfence();
+    __syncthreads();
     const unsigned cnt = *(volatile unsigned*)&ctl->count;
-    if (phase == 1 && cnt > kTinyCap) return;
-    if (cnt <= kTinyCap) {
-        tiny_hull(keys, vals, (int)cnt, pts, n, ctl, out_idx, out_n, s_tiny);
+    if (cnt <= (unsigned)kMidCap) {
+        mid_hull(keys, vals, (int)cnt, pts, n, ctl, out_idx, out_n, dyn);
         if (threadIdx.x == 0) ctl->done = 1;
     }
 }
@@ -739,7 +860,8 @@ void launch_main(const float* pts, long long n, int head, long long ntiles, Ctl*
 void launch_tail(const float* pts, long long n, int head, Ctl* ctl, const uint64_t* raw_xy, const uint32_t* raw_idx,
                  uint32_t* keys, uint64_t* vals, int phase, int hull, int32_t* out_idx, int64_t* out_n,
                  cudaStream_t s) {
-    tail_kernel<<<1, 256, 0, s>>>(pts, n, head, ctl, raw_xy, raw_idx, keys, vals, phase, hull, out_idx, out_n);
+    tail_kernel<<<1, 1024, kMidSmemBytes, s>>>(pts, n, head, ctl, raw_xy, raw_idx, keys, vals, phase, hull, out_idx,
+                                               out_n);
 }
 
 void launch_stagec(const float* pts, long long n, int head, long long ntiles, Ctl* ctl, const uint64_t* raw_xy,
@@ -753,6 +875,12 @@ void launch_labels(const float* pts, long long n, Ctl* ctl, uint8_t* labels, int
 
 void launch_filter_output(const Ctl* ctl, long long n, int32_t* out_ext8, int64_t* out_counts4, cudaStream_t s) {
     filter_output_kernel<<<1, 32, 0, s>>>(ctl, n, out_ext8, out_counts4);
+}
+
+long long sample_tiles_host(long long ntiles) { return sample_tiles(ntiles); }
+
+cudaError_t configure_filter_kernels() {
+    return cudaFuncSetAttribute(tail_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMidSmemBytes);
 }
 
 cudaError_t occupancy_filter(int* main_k, int* stagec, int* labels) {

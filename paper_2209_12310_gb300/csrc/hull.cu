@@ -29,71 +29,6 @@
 
 namespace ch {
 
-struct ChainPtr {   // structure-of-arrays view of a chain (u, v, index)
-    int* u;
-    int* v;
-    int* i;
-};
-
-__device__ __forceinline__ long long cross_uv(int ou, int ov, int au, int av, int bu, int bv) {
-    return (long long)(au - ou) * (long long)(bv - ov) - (long long)(av - ov) * (long long)(bu - ou);
-}
-
-template <bool kGlobal>
-__device__ __forceinline__ int ldi(const int* p) {
-    if (kGlobal) return __ldcg(p);
-    return *p;
-}
-
-// Minimum over chain C[0..lc) of f(c) = cross(p, q, c), q.u > p.u.  Along a
-// lower convex chain the increments cross(q - p, c_{l+1} - c_l) change sign
-// once (negative, then >= 0), so f is minimal at the first l whose next edge
-// does not decrease it.
-template <bool kGlobal>
-__device__ long long min_cross_over(const int* cu, const int* cv, int lc, int pu, int pv, int qu,
-                                    int qv) {
-    int lo = 0, hi = lc - 1;   // answer in [lo, hi]
-    const long long du = qu - pu, dv = qv - pv;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        const long long eu = (long long)ldi<kGlobal>(cu + mid + 1) - ldi<kGlobal>(cu + mid);
-        const long long ev = (long long)ldi<kGlobal>(cv + mid + 1) - ldi<kGlobal>(cv + mid);
-        if (du * ev - dv * eu >= 0) hi = mid; else lo = mid + 1;
-    }
-    return cross_uv(pu, pv, qu, qv, ldi<kGlobal>(cu + lo), ldi<kGlobal>(cv + lo));
-}
-
-template <bool kGlobal>
-__device__ __forceinline__ bool keep_a(const ChainPtr& A, int k, const ChainPtr& B, int lb) {
-    if (k == 0) return true;
-    return min_cross_over<kGlobal>(B.u, B.v, lb, ldi<kGlobal>(A.u + k - 1), ldi<kGlobal>(A.v + k - 1),
-                                   ldi<kGlobal>(A.u + k), ldi<kGlobal>(A.v + k)) > 0;
-}
-
-template <bool kGlobal>
-__device__ __forceinline__ bool keep_b(const ChainPtr& A, int la, const ChainPtr& B, int l, int lb) {
-    if (l == lb - 1) return true;
-    return min_cross_over<kGlobal>(A.u, A.v, la, ldi<kGlobal>(B.u + l), ldi<kGlobal>(B.v + l),
-                                   ldi<kGlobal>(B.u + l + 1), ldi<kGlobal>(B.v + l + 1)) > 0;
-}
-
-// Sequential bridge (one thread): last kept index of A, first kept of B.
-template <bool kGlobal>
-__device__ void bridge_seq(const ChainPtr& A, int la, const ChainPtr& B, int lb, int& is, int& js) {
-    int lo = 0, hi = la - 1;               // keep_a(lo) true
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (keep_a<kGlobal>(A, mid, B, lb)) lo = mid; else hi = mid - 1;
-    }
-    is = lo;
-    lo = 0; hi = lb - 1;                   // keep_b(hi) true
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (keep_b<kGlobal>(A, la, B, mid, lb)) hi = mid; else lo = mid + 1;
-    }
-    js = lo;
-}
-
 // Block-cooperative bridge: repeated 256-way probing of the monotone keep
 // predicates (each probe is a sequential binary search over the other chain).
 template <bool kGlobal>
@@ -154,26 +89,6 @@ struct HullBufs {
     int32_t* out_idx;
     int64_t* out_n;
 };
-
-// Merge chain B (at sb, length lb) into chain A (at sa, length la) in shared
-// memory, one thread.  Returns the new length of A.
-__device__ int merge_smem_seq(int* su, int* sv, int* si, int sa, int la, int sb, int lb) {
-    if (lb == 0) return la;
-    if (la == 0) {
-        for (int j = 0; j < lb; ++j) { su[sa + j] = su[sb + j]; sv[sa + j] = sv[sb + j]; si[sa + j] = si[sb + j]; }
-        return lb;
-    }
-    ChainPtr A{su + sa, sv + sa, si + sa}, B{su + sb, sv + sb, si + sb};
-    int is, js;
-    bridge_seq<false>(A, la, B, lb, is, js);
-    const int n = lb - js;
-    for (int j = 0; j < n; ++j) {
-        su[sa + is + 1 + j] = su[sb + js + j];
-        sv[sa + is + 1 + j] = sv[sb + js + j];
-        si[sa + is + 1 + j] = si[sb + js + j];
-    }
-    return is + 1 + n;
-}
 
 // Block-wide forward copy of n entries, dst <= src (possibly overlapping),
 // in chunks fully loaded before they are stored.

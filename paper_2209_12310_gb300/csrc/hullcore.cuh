@@ -10,6 +10,98 @@
 
 namespace ch {
 
+// ---------------------------------------------------------------------------
+// Lower convex chains in a queue frame (u strictly increasing).  Merging two
+// chains A, B with every u of A below every u of B: a_k (k > 0) stays iff every
+// b in B is strictly left of a_{k-1} -> a_k; b_l (l < |B| - 1) stays iff every
+// a in A is strictly left of b_l -> b_{l+1}.  Both predicates hold on a prefix
+// of A / a suffix of B, and "every b" reduces to the minimum of a linear
+// function over the convex chain B, found by binary search.
+struct ChainPtr {   // structure-of-arrays view of a chain (u, v, index)
+    int* u;
+    int* v;
+    int* i;
+};
+
+__device__ __forceinline__ long long cross_uv(int ou, int ov, int au, int av, int bu, int bv) {
+    return (long long)(au - ou) * (long long)(bv - ov) - (long long)(av - ov) * (long long)(bu - ou);
+}
+
+template <bool kGlobal>
+__device__ __forceinline__ int ldi(const int* p) {
+    if (kGlobal) return __ldcg(p);
+    return *p;
+}
+
+// Minimum over chain C[0..lc) of f(c) = cross(p, q, c), q.u > p.u.  Along a
+// lower convex chain the increments cross(q - p, c_{l+1} - c_l) change sign
+// once (negative, then >= 0), so f is minimal at the first l whose next edge
+// does not decrease it.
+template <bool kGlobal>
+__device__ long long min_cross_over(const int* cu, const int* cv, int lc, int pu, int pv, int qu,
+                                    int qv) {
+    int lo = 0, hi = lc - 1;   // answer in [lo, hi]
+    const long long du = qu - pu, dv = qv - pv;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        const long long eu = (long long)ldi<kGlobal>(cu + mid + 1) - ldi<kGlobal>(cu + mid);
+        const long long ev = (long long)ldi<kGlobal>(cv + mid + 1) - ldi<kGlobal>(cv + mid);
+        if (du * ev - dv * eu >= 0) hi = mid; else lo = mid + 1;
+    }
+    return cross_uv(pu, pv, qu, qv, ldi<kGlobal>(cu + lo), ldi<kGlobal>(cv + lo));
+}
+
+template <bool kGlobal>
+__device__ __forceinline__ bool keep_a(const ChainPtr& A, int k, const ChainPtr& B, int lb) {
+    if (k == 0) return true;
+    return min_cross_over<kGlobal>(B.u, B.v, lb, ldi<kGlobal>(A.u + k - 1), ldi<kGlobal>(A.v + k - 1),
+                                   ldi<kGlobal>(A.u + k), ldi<kGlobal>(A.v + k)) > 0;
+}
+
+template <bool kGlobal>
+__device__ __forceinline__ bool keep_b(const ChainPtr& A, int la, const ChainPtr& B, int l, int lb) {
+    if (l == lb - 1) return true;
+    return min_cross_over<kGlobal>(A.u, A.v, la, ldi<kGlobal>(B.u + l), ldi<kGlobal>(B.v + l),
+                                   ldi<kGlobal>(B.u + l + 1), ldi<kGlobal>(B.v + l + 1)) > 0;
+}
+
+// Sequential bridge (one thread): last kept index of A, first kept of B.
+template <bool kGlobal>
+__device__ void bridge_seq(const ChainPtr& A, int la, const ChainPtr& B, int lb, int& is, int& js) {
+    int lo = 0, hi = la - 1;               // keep_a(lo) true
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (keep_a<kGlobal>(A, mid, B, lb)) lo = mid; else hi = mid - 1;
+    }
+    is = lo;
+    lo = 0; hi = lb - 1;                   // keep_b(hi) true
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (keep_b<kGlobal>(A, la, B, mid, lb)) hi = mid; else lo = mid + 1;
+    }
+    js = lo;
+}
+
+// Merge chain B (at sb, length lb) into chain A (at sa, length la) in shared
+// memory, one thread.  Returns the new length of A.
+static __device__ int merge_smem_seq(int* su, int* sv, int* si, int sa, int la, int sb, int lb) {
+    if (lb == 0) return la;
+    if (la == 0) {
+        for (int j = 0; j < lb; ++j) { su[sa + j] = su[sb + j]; sv[sa + j] = sv[sb + j]; si[sa + j] = si[sb + j]; }
+        return lb;
+    }
+    ChainPtr A{su + sa, sv + sa, si + sa}, B{su + sb, sv + sb, si + sb};
+    int is, js;
+    bridge_seq<false>(A, la, B, lb, is, js);
+    const int n = lb - js;
+    for (int j = 0; j < n; ++j) {
+        su[sa + is + 1 + j] = su[sb + js + j];
+        sv[sa + is + 1 + j] = sv[sb + js + j];
+        si[sa + is + 1 + j] = si[sb + js + j];
+    }
+    return is + 1 + n;
+}
+
 template <typename T, typename Op>
 __device__ __forceinline__ T block_reduce(T v, Op op, T* s_tmp) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
@@ -157,93 +249,114 @@ static __device__ void stitch_core(const int* V, int m, int* flag, int* comp, co
     }
 }
 
-// Shared memory of tiny_hull (kTinyCap records).
-struct TinySmem {
-    uint32_t key[kTinyCap];
-    uint64_t val[kTinyCap];
-    int vert[kTinyCap];      // 1 = chain vertex
-    int rank[kTinyCap];
-    int V[kTinyCap];
-    int flag[kTinyCap];
-    int comp[kTinyCap];
-    int len[4];
-};
+// Dynamic shared memory of mid_hull: sort keys (kMidCap u64) followed by the
+// chain arrays u | queue, v, index (kMidCap ints each).
+constexpr size_t kMidSmemBytes = (size_t)kMidCap * 8 + (size_t)3 * kMidCap * 4;
 
-__device__ __forceinline__ int rec_u(uint32_t k) { return (int)(k & kKeyMask); }
-__device__ __forceinline__ int rec_v(uint64_t v) { return (int)(v >> 31); }
-
-// The hull stage for m <= kTinyCap sort records (queue | u, v | index) in one
-// block, without sorting: a record survives its queue's run reduction when no
-// record of equal (queue, u) has a smaller (v, index); a survivor is a chain
-// vertex when it is an end of its queue or strictly below the line through its
-// steepest left neighbour and its flattest right neighbour (Andrew's lower
-// chain in the queue frame); its position is its rank by u.
-static __device__ void tiny_hull(const uint32_t* keys, const uint64_t* vals, int m, const float* __restrict__ pts,
-                          long long n, Ctl* ctl, int32_t* out_idx, int64_t* out_n, TinySmem& sm) {
+// The whole hull stage for m <= kMidCap sort records (queue | u, v | index) in
+// one block: bitonic sort of (key, position) in shared memory, run reduction
+// (minimum (v, index) per key), the four queue chains built concurrently by a
+// quarter of the block each (per-thread chains, then pairwise merges), and the
+// stitch.  blockDim.x must be a multiple of 128.
+static __device__ void mid_hull(const uint32_t* keys, const uint64_t* vals, int m, const float* __restrict__ pts,
+                                long long n, Ctl* ctl, int32_t* out_idx, int64_t* out_n, char* smem) {
+    __shared__ int s_rs[5];
+    __shared__ int s_int[33];
+    __shared__ int s_clen[1024];
+    unsigned long long* sk = reinterpret_cast<unsigned long long*>(smem);
+    int* cu = reinterpret_cast<int*>(sk + kMidCap);
+    int* cv = cu + kMidCap;
+    int* ci = cv + kMidCap;
     const int tid = threadIdx.x, T = blockDim.x;
-    for (int i = tid; i < m; i += T) { sm.key[i] = keys[i]; sm.val[i] = vals[i]; }
-    if (tid < 4) sm.len[tid] = 0;
+    int P = 1;
+    while (P < m) P <<= 1;
+    for (int i = tid; i < P; i += T)
+        sk[i] = i < m ? (((unsigned long long)keys[i] << 13) | (unsigned long long)i) : ~0ull;
     __syncthreads();
-    // run reduction: keep the smallest (v, index) per (queue, u); first position on exact ties
-    for (int i = tid; i < m; i += T) {
-        const uint32_t ki = sm.key[i];
-        const uint64_t vi = sm.val[i];
-        int alive = 1;
-        for (int j = 0; j < m; ++j) {
-            if (sm.key[j] == ki && (sm.val[j] < vi || (sm.val[j] == vi && j < i))) { alive = 0; break; }
+    for (int k = 2; k <= P; k <<= 1) {          // bitonic sort, ascending
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = tid; i < P; i += T) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const unsigned long long a = sk[i], b = sk[l];
+                    if ((a > b) == ((i & k) == 0)) { sk[i] = b; sk[l] = a; }
+                }
+            }
+            __syncthreads();
         }
-        sm.vert[i] = alive;
     }
-    __syncthreads();
-    int vflag[(kTinyCap + 31) / 32];
-    int c = 0;
-    for (int i = tid; i < m; i += T, ++c) {
-        vflag[c] = 0;
-        if (!sm.vert[i]) continue;
-        const uint32_t qi = sm.key[i] >> kKeyBits;
-        const long long ui = rec_u(sm.key[i]), vi = rec_v(sm.val[i]);
-        bool has_l = false, has_r = false;
-        long long au = 0, av = 0, bu = 0, bv = 0;
-        for (int j = 0; j < m; ++j) {
-            if (!sm.vert[j] || (sm.key[j] >> kKeyBits) != qi) continue;
-            const long long uj = rec_u(sm.key[j]), vj = rec_v(sm.val[j]);
-            if (uj < ui) {   // steepest slope (a -> i)
-                if (!has_l || (vi - vj) * (ui - au) > (vi - av) * (ui - uj)) { au = uj; av = vj; }
-                has_l = true;
-            } else if (uj > ui) {   // flattest slope (i -> b)
-                if (!has_r || (vj - vi) * (bu - ui) < (bv - vi) * (uj - ui)) { bu = uj; bv = vj; }
-                has_r = true;
+    // run reduction: one point per (queue, u), the minimum (v, index)
+    int written = 0;
+    for (int base = 0; base < m; base += T) {
+        const int p = base + tid;
+        int f = 0;
+        unsigned key = 0u;
+        unsigned long long best = 0ull;
+        if (p < m) {
+            key = (unsigned)(sk[p] >> 13);
+            f = (p == 0) || (unsigned)(sk[p - 1] >> 13) != key;
+            if (f) {
+                best = vals[sk[p] & 8191ull];
+                for (int q = p + 1; q < m && (unsigned)(sk[q] >> 13) == key; ++q) {
+                    const unsigned long long w = vals[sk[q] & 8191ull];
+                    best = w < best ? w : best;
+                }
             }
         }
-        const bool is_v = !has_l || !has_r ||
-                          (ui - au) * (bv - av) - (vi - av) * (bu - au) > 0;
-        vflag[c] = is_v ? 1 : 0;
+        int tot;
+        const int ex = block_excl_scan(f, s_int, &tot);
+        if (f) {
+            cu[written + ex] = (int)key;                 // queue in bits 25..26, u below
+            cv[written + ex] = (int)(best >> 31);
+            ci[written + ex] = (int)(best & 0x7FFFFFFFull);
+        }
+        written += tot;
     }
     __syncthreads();
-    c = 0;
-    for (int i = tid; i < m; i += T, ++c) sm.vert[i] = vflag[c];
-    __syncthreads();
-    for (int i = tid; i < m; i += T) {
-        if (!sm.vert[i]) continue;
-        const uint32_t ki = sm.key[i];
-        int rk = 0;
-        for (int j = 0; j < m; ++j)
-            if (sm.vert[j] && (sm.key[j] >> kKeyBits) == (ki >> kKeyBits) && sm.key[j] < ki) ++rk;
-        sm.rank[i] = rk;
-        atomicAdd(&sm.len[ki >> kKeyBits], 1);
+    const int m2 = written;
+    for (int p = tid; p <= m2; p += T) {         // queue boundaries
+        const int prev = p == 0 ? -1 : (cu[p - 1] >> kKeyBits);
+        const int cur = p == m2 ? 4 : (cu[p] >> kKeyBits);
+        for (int r = prev + 1; r <= cur; ++r) s_rs[r] = p;
     }
     __syncthreads();
+    // four queues at once, a quarter of the block each; queue bits are equal
+    // within a queue, so cross products of cu differences are those of u
+    const int G = T / 4, g = tid / G, lt = tid % G;
+    const int qa = s_rs[g], qb = s_rs[g + 1];
+    const int chunk = (qb - qa + G - 1) / G;
+    const int my0 = qa + lt * chunk, my1 = min(qb, my0 + chunk);
+    {
+        int sp = 0;
+        for (int p = my0; p < my1; ++p) {
+            const int pu = cu[p], pv = cv[p], pi = ci[p];
+            while (sp >= 2 && cross_uv(cu[my0 + sp - 2], cv[my0 + sp - 2], cu[my0 + sp - 1], cv[my0 + sp - 1], pu, pv) <= 0)
+                --sp;
+            cu[my0 + sp] = pu; cv[my0 + sp] = pv; ci[my0 + sp] = pi;
+            ++sp;
+        }
+        s_clen[tid] = my1 > my0 ? sp : 0;
+    }
+    __syncthreads();
+    for (int l = 0; (1 << l) < G; ++l) {
+        const int gsz = 1 << l;
+        if ((lt & (2 * gsz - 1)) == 0 && lt + gsz < G) {
+            const int b0 = qa + (lt + gsz) * chunk;
+            if (b0 < qb)
+                s_clen[tid] = merge_smem_seq(cu, cv, ci, my0, s_clen[tid], b0, s_clen[tid + gsz]);
+        }
+        __syncthreads();
+    }
+    // stitch: V (in the sort buffer) = the queue chains without their last point
+    int* V = reinterpret_cast<int*>(sk);
+    int* flag = V + kMidCap;
     int off[5];
     off[0] = 0;
-    for (int r = 0; r < 4; ++r) off[r + 1] = off[r] + max(sm.len[r] - 1, 0);
-    const int mv = off[4];
-    for (int i = tid; i < m; i += T) {
-        if (!sm.vert[i]) continue;
-        const int r = (int)(sm.key[i] >> kKeyBits);
-        if (sm.rank[i] < sm.len[r] - 1) sm.V[off[r] + sm.rank[i]] = (int)(sm.val[i] & 0x7FFFFFFFull);
-    }
+    for (int r = 0; r < 4; ++r) off[r + 1] = off[r] + max(s_clen[r * G] - 1, 0);
+    for (int r = 0; r < 4; ++r)
+        for (int j = tid; j < off[r + 1] - off[r]; j += T) V[off[r] + j] = ci[s_rs[r] + j];
     __syncthreads();
-    stitch_core(sm.V, mv, sm.flag, sm.comp, pts, n, ctl, out_idx, out_n);
+    stitch_core(V, off[4], flag, cu, pts, n, ctl, out_idx, out_n);
 }
 
 }  // namespace ch

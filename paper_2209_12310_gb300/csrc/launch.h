@@ -29,6 +29,8 @@ void launch_chain(Ctl* ctl, const uint32_t* keys, const uint64_t* vals, int* cu,
                   int64_t* out_n, int grid, cudaStream_t s);
 size_t chain_smem_bytes();
 cudaError_t configure_hull_kernels();
+cudaError_t configure_filter_kernels();
+long long sample_tiles_host(long long ntiles);
 
 // Occupancy (resident blocks per SM at each kernel's launch shape).
 cudaError_t occupancy_filter(int* main_k, int* stagec, int* labels);
