@@ -27,6 +27,7 @@
 #include "hullcore.cuh"
 #include "launch.h"
 #include "octagon.cuh"
+#include "tma.cuh"
 
 #include <climits>
 
@@ -161,12 +162,14 @@ __global__ void __launch_bounds__(256) sample_kernel(const float* __restrict__ p
         if (m) atomicMax(&ctl->samp_packed[threadIdx.x], m);
     }
     if (!last_block(&ctl->blocks_done[0], &s_last)) return;
-    if (warp != 0) return;
-    int vx[8], vy[8], ext[8];
-    bool ok = nsamp > 0;
-    for (int d = 0; d < 8; ++d) {
+    __shared__ int s_v[2][8];
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) s_ok = nsamp > 0;
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        const int d = threadIdx.x;
         const unsigned long long p = *(volatile unsigned long long*)&ctl->samp_packed[d];
-        ok &= p != 0ull;
+        if (p == 0ull) atomicAnd(&s_ok, 0);
         const unsigned hk = (unsigned)(p >> 32), aux = (unsigned)p;
         const int key = dir_is_max(d) ? (int)hk : (int)(0xFFFFFFFFu - hk);
         int x, y;
@@ -176,20 +179,21 @@ __global__ void __launch_bounds__(256) sample_kernel(const float* __restrict__ p
             case SW: case NE: x = (int)aux; y = key - x; break;
             default: x = (int)aux; y = x - (key - kCoordLimit); break;
         }
-        vx[d] = x; vy[d] = y; ext[d] = -1;
+        s_v[0][d] = x;
+        s_v[1][d] = y;
     }
-    if (!ok) {   // too few points to sample: run the two-pass path
-        if (lane == 0) ctl->mode = 1;
+    __syncthreads();
+    if (!s_ok) {   // too few points to sample: run the two-pass path
+        if (threadIdx.x == 0) ctl->mode = 1;
         return;
     }
-    setup_octagon_warp(s_o, vx, vy, ext);
+    const int ext[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
+    setup_octagon_block(s_o, s_v[0], s_v[1], ext);
     if (s_o.discard_none) {
-        if (lane == 0) ctl->mode = 1;
+        if (threadIdx.x == 0) ctl->mode = 1;
         return;
     }
-    const int words = (int)(sizeof(Octagon) / 4);
-    for (int i = lane; i < words; i += 32)
-        reinterpret_cast<int*>(&ctl->oct_s)[i] = reinterpret_cast<const int*>(&s_o)[i];
+    copy_octagon(&ctl->oct_s, &s_o);
 }
 
 // ---------------------------------------------------------------------------
@@ -250,14 +254,16 @@ __device__ __forceinline__ void track_tile(Track& tr, const int (&tk)[8], unsign
 
 // Strictly inside the inner region of the sample octagon: the tile's key
 // extremes (or one point's keys) against the bounds, strict comparisons.
-__device__ __forceinline__ bool tile_in_inner(const int (&tk)[8], const int (&lo)[4], const int (&hi)[4]) {
-    return tk[W] > lo[0] && tk[E] < hi[0] && tk[S] > lo[1] && tk[N] < hi[1] &&
-           tk[SW] > lo[2] && tk[NE] < hi[2] && tk[NW] > lo[3] && tk[SE] < hi[3];
+// Bounds are read from shared memory (lo = in[0..3], hi = in[4..7]) to keep
+// them out of the streaming loop's registers.
+__device__ __forceinline__ bool tile_in_inner(const int (&tk)[8], const int* in) {
+    return tk[W] > in[0] && tk[E] < in[4] && tk[S] > in[1] && tk[N] < in[5] &&
+           tk[SW] > in[2] && tk[NE] < in[6] && tk[NW] > in[3] && tk[SE] < in[7];
 }
 
-__device__ __forceinline__ bool pt_in_inner(int X, int Y, const int (&lo)[4], const int (&hi)[4]) {
+__device__ __forceinline__ bool pt_in_inner(int X, int Y, const int* in) {
     const int S = X + Y, D = X - Y + kCoordLimit;
-    return X > lo[0] && X < hi[0] && Y > lo[1] && Y < hi[1] && S > lo[2] && S < hi[2] && D > lo[3] && D < hi[3];
+    return X > in[0] && X < in[4] && Y > in[1] && Y < in[5] && S > in[2] && S < in[6] && D > in[3] && D < in[7];
 }
 
 __device__ __forceinline__ unsigned long long pack_best(int d, int best, unsigned code) {
@@ -486,7 +492,6 @@ __device__ void finalize_block(const float* __restrict__ pts, long long n, int h
     __shared__ unsigned long long s_ext[8];
     __shared__ int s_G[8];
     __shared__ long long s_lo[8], s_hi[8];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x < 8) {
         const int d = threadIdx.x;
         const unsigned long long pk = *(volatile unsigned long long*)&ctl->ext_packed[d];
@@ -514,43 +519,43 @@ __device__ void finalize_block(const float* __restrict__ pts, long long n, int h
         if (threadIdx.x == 0) set_status(ctl, CH_ECUDA);
         return;
     }
-    if (warp == 0) {
-        int vx[8], vy[8], ext[8];
-        for (int d = 0; d < 8; ++d) {
-            const long long i = (long long)s_ext[d];
-            ext[d] = (int)i;
-            vx[d] = __float2int_rn(pts[2 * i]);
-            vy[d] = __float2int_rn(pts[2 * i + 1]);
+    __shared__ int s_vx[8], s_vy[8], s_id[8];
+    if (threadIdx.x < 8) {
+        const long long i = (long long)s_ext[threadIdx.x];
+        s_id[threadIdx.x] = (int)i;
+        s_vx[threadIdx.x] = __float2int_rn(pts[2 * i]);
+        s_vy[threadIdx.x] = __float2int_rn(pts[2 * i + 1]);
+    }
+    __syncthreads();
+    setup_octagon_block(s_o, s_vx, s_vy, s_id);
+    if (threadIdx.x < 12) {
+        // Threads 0..7: chain end points (queue r runs from quad vertex r to
+        // r+1).  Threads 8..11: the diagonal extreme of queue r, when it lies
+        // strictly right of the quad edge (the hull rule drops every point of
+        // the closed octagon, vertices included, so the vertices that can be
+        // hull vertices get their own record; on the edge it cannot be one).
+        const int lane = threadIdx.x;
+        int r, d;
+        bool emit = true;
+        if (lane < 8) {
+            r = lane >> 1;
+            d = (lane & 1) ? ((2 * r + 2) & 7) : 2 * r;
+        } else {
+            r = lane - 8;
+            d = 2 * r + 1;
+            const int a = 2 * r, b = (2 * r + 2) & 7;
+            emit = orient64(s_vx[a], s_vy[a], s_vx[b], s_vy[b], s_vx[d], s_vy[d]) < 0;
         }
-        setup_octagon_warp(s_o, vx, vy, ext);
-        if (lane < 12) {
-            // Lanes 0..7: chain end points (queue r runs from quad vertex r to
-            // r+1).  Lanes 8..11: the diagonal extreme of queue r, when it lies
-            // strictly right of the quad edge (the hull rule drops every point
-            // of the closed octagon, vertices included, so the vertices that
-            // can be hull vertices get their own record; on the edge it cannot).
-            int r, d;
-            bool emit = true;
-            if (lane < 8) {
-                r = lane >> 1;
-                d = (lane & 1) ? ((2 * r + 2) & 7) : 2 * r;
-            } else {
-                r = lane - 8;
-                d = 2 * r + 1;
-                const int a = 2 * r, b = (2 * r + 2) & 7;
-                emit = orient64(vx[a], vy[a], vx[b], vy[b], vx[d], vy[d]) < 0;
-            }
-            if (emit) {
-                uint32_t u, v;
-                queue_frame(r, vx[d], vy[d], u, v);
-                const uint32_t key = make_key(r, u);
-                const unsigned pos = lane < 8 ? (unsigned)lane : atomicAdd(&ctl->count, 1u);
-                keys[pos] = key;
-                vals[pos] = make_val(v, (uint32_t)ext[d]);
+        if (emit) {
+            uint32_t u, v;
+            queue_frame(r, s_vx[d], s_vy[d], u, v);
+            const uint32_t key = make_key(r, u);
+            const unsigned pos = lane < 8 ? (unsigned)lane : atomicAdd(&ctl->count, 1u);
+            keys[pos] = key;
+            vals[pos] = make_val(v, (uint32_t)s_id[d]);
 #pragma unroll
-                for (int p = 0; p < kSortPasses; ++p)
-                    atomicAdd(&ctl->digit_hist[p][(key >> (p * kDigitBits)) & (kDigits - 1)], 1u);
-            }
+            for (int p = 0; p < kSortPasses; ++p)
+                atomicAdd(&ctl->digit_hist[p][(key >> (p * kDigitBits)) & (kDigits - 1)], 1u);
         }
     }
     __syncthreads();
@@ -558,28 +563,27 @@ __device__ void finalize_block(const float* __restrict__ pts, long long n, int h
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(256, 3) main_kernel(const float* __restrict__ pts, long long n, int head,
+constexpr size_t kMainSmemBytes = (size_t)8 * kStages * kWarpTileF4 * sizeof(float4);
+
+__global__ void __launch_bounds__(256, 2) main_kernel(const float* __restrict__ pts, long long n, int head,
                                                       long long ntiles, Ctl* ctl, uint64_t* raw_xy,
                                                       uint32_t* raw_idx, unsigned switch_at) {
+    extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ int s_inner[8];
     __shared__ unsigned long long s_red[8][8];
     __shared__ int s_mode;
     __shared__ RawBuf s_buf[8];
+    __shared__ unsigned long long s_bar[8][kStages];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     if (threadIdx.x == 0) s_mode = *(volatile int*)&ctl->mode;   // one read: uniform per block
-    __syncthreads();
-    bool filt = s_mode == 0;
     if (threadIdx.x < 4) {
         s_inner[threadIdx.x] = ctl->oct_s.in_lo[threadIdx.x];
         s_inner[4 + threadIdx.x] = ctl->oct_s.in_hi[threadIdx.x];
     }
     __syncthreads();
-    int lo[4], hi[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) { lo[k] = s_inner[k]; hi[k] = s_inner[4 + k]; }
-
+    bool filt = s_mode == 0;
     RawBuf& wbuf = s_buf[warp];
     unsigned wcnt = 0u;
     Track tr;
@@ -599,7 +603,7 @@ __global__ void __launch_bounds__(256, 3) main_kernel(const float* __restrict__ 
                 convert_pt(x, y, X, Y, tr);
                 tile_keys2(tk, X, Y, X, Y, !any);
                 any = true;
-                if (filt && !pt_in_inner(X, Y, lo, hi)) keep = 1u;
+                if (filt && !pt_in_inner(X, Y, s_inner)) keep = 1u;
             }
             auto get = [&](int, long long& idx, float& px, float& py) { idx = i; px = x; py = y; };
             if (filt) emit_raw<1>(keep, get, wbuf, wcnt, ctl, raw_xy, raw_idx);
@@ -607,48 +611,53 @@ __global__ void __launch_bounds__(256, 3) main_kernel(const float* __restrict__ 
         if (any) track_tile(tr, tk, code);
     };
     if (gwarp == 0 && head) scalar_range(0, head, 0u);
-    const float4* p4 = reinterpret_cast<const float4*>(pts + 2 * head);
-    long long iter = 0;
-    for (long long t = gwarp; t < ntiles; t += nwarps, ++iter) {
-        const float4* base = p4 + t * kWarpTileF4 + lane;
-        float4 v[kLoadsPerLane];
-#pragma unroll
-        for (int j = 0; j < kLoadsPerLane; ++j) v[j] = ld_stream_f4(base + j * 32);
+
+    // Warp tiles t = gwarp + k * nwarps stream through a double-buffered
+    // shared-memory ring filled by bulk asynchronous copies (TMA).
+    WarpStream ws{reinterpret_cast<float4*>(dsm) + warp * kStages * kWarpTileF4, s_bar[warp],
+                  reinterpret_cast<const float4*>(pts + 2 * head), gwarp, nwarps, ntiles, lane};
+    ws.start();
+    for (long long k = 0;; ++k) {
+        const long long t = gwarp + k * nwarps;
+        if (t >= ntiles) break;
+        const float4* cur = ws.acquire(k, ctl);
+        if (!cur) {   // a copy never completed: status is CH_ETIMEOUT
+            ws.drain(k);
+            break;
+        }
         int tk[8];
 #pragma unroll
         for (int j = 0; j < kLoadsPerLane; ++j) {
+            const float4 v = cur[j * 32 + lane];
             int X0, Y0, X1, Y1;
-            convert_pt(v[j].x, v[j].y, X0, Y0, tr);
-            convert_pt(v[j].z, v[j].w, X1, Y1, tr);
+            convert_pt(v.x, v.y, X0, Y0, tr);
+            convert_pt(v.z, v.w, X1, Y1, tr);
             tile_keys2(tk, X0, Y0, X1, Y1, j == 0);
         }
         track_tile(tr, tk, (unsigned)(t + 1));
         if (filt) {
             // Points strictly inside the inner region of the sample octagon
-            // are strictly inside the hull; everything else is a raw survivor,
-            // classified against the true octagon once its extremes are known.
-            const bool inside = tile_in_inner(tk, lo, hi);
+            // are strictly inside the hull; every other point is a raw
+            // survivor, classified against the true octagon once its extremes
+            // are known.  Lanes with such points re-read them from the stage.
+            const bool inside = tile_in_inner(tk, s_inner);
             if (!__all_sync(0xFFFFFFFFu, inside)) {
-                // Reload the lane's points (just read, served by L2) rather than
-                // keeping them live across the tile: fewer registers in the
-                // streaming loop.
-                float4 w[kLoadsPerLane];
                 unsigned keep = 0u;
                 if (!inside) {
 #pragma unroll
-                    for (int j = 0; j < kLoadsPerLane; ++j) w[j] = __ldcg(base + j * 32);
-#pragma unroll
                     for (int j = 0; j < kLoadsPerLane; ++j) {
-                        if (!pt_in_inner(__float2int_rn(w[j].x), __float2int_rn(w[j].y), lo, hi)) keep |= 1u << (2 * j);
-                        if (!pt_in_inner(__float2int_rn(w[j].z), __float2int_rn(w[j].w), lo, hi)) keep |= 2u << (2 * j);
+                        const float4 v = cur[j * 32 + lane];
+                        if (!pt_in_inner(__float2int_rn(v.x), __float2int_rn(v.y), s_inner)) keep |= 1u << (2 * j);
+                        if (!pt_in_inner(__float2int_rn(v.z), __float2int_rn(v.w), s_inner)) keep |= 2u << (2 * j);
                     }
                 }
                 const long long i0 = head + 2 * (t * kWarpTileF4 + lane);
                 auto get = [&](int s, long long& idx, float& x, float& y) {
                     const int j = s >> 1;
+                    const float4 v = cur[j * 32 + lane];
                     idx = i0 + 64 * j + (s & 1);
-                    x = (s & 1) ? w[j].z : w[j].x;
-                    y = (s & 1) ? w[j].w : w[j].y;
+                    x = (s & 1) ? v.z : v.x;
+                    y = (s & 1) ? v.w : v.y;
                 };
                 const unsigned upto = emit_raw<2 * kLoadsPerLane>(keep, get, wbuf, wcnt, ctl, raw_xy, raw_idx);
                 if (upto > switch_at) {   // dense data: leave filtering to the second pass
@@ -656,12 +665,13 @@ __global__ void __launch_bounds__(256, 3) main_kernel(const float* __restrict__ 
                     filt = false;
                 }
             }
-            if ((iter & 7) == 7) {
+            if ((k & 7) == 7) {
                 int m = 0;
                 if (lane == 0) m = *(volatile int*)&ctl->mode;
                 filt = filt && __shfl_sync(0xFFFFFFFFu, m, 0) == 0;
             }
         }
+        ws.release(k);
     }
     if (gwarp == 0 && head + ntiles * kWarpTilePts < n)
         scalar_range(head + ntiles * kWarpTilePts, n, (unsigned)(ntiles + 1));
@@ -854,7 +864,7 @@ void launch_sample(const float* pts, long long n, int head, long long ntiles, Ct
 
 void launch_main(const float* pts, long long n, int head, long long ntiles, Ctl* ctl, uint64_t* raw_xy,
                  uint32_t* raw_idx, unsigned switch_at, int grid, cudaStream_t s) {
-    main_kernel<<<grid, 256, 0, s>>>(pts, n, head, ntiles, ctl, raw_xy, raw_idx, switch_at);
+    main_kernel<<<grid, 256, kMainSmemBytes, s>>>(pts, n, head, ntiles, ctl, raw_xy, raw_idx, switch_at);
 }
 
 void launch_tail(const float* pts, long long n, int head, Ctl* ctl, const uint64_t* raw_xy, const uint32_t* raw_idx,
@@ -880,11 +890,14 @@ void launch_filter_output(const Ctl* ctl, long long n, int32_t* out_ext8, int64_
 long long sample_tiles_host(long long ntiles) { return sample_tiles(ntiles); }
 
 cudaError_t configure_filter_kernels() {
-    return cudaFuncSetAttribute(tail_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMidSmemBytes);
+    cudaError_t e = cudaFuncSetAttribute(tail_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMidSmemBytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(main_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMainSmemBytes);
+    return e;
 }
 
 cudaError_t occupancy_filter(int* main_k, int* stagec, int* labels) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(main_k, main_kernel, 256, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(main_k, main_kernel, 256, kMainSmemBytes);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(stagec, stagec_kernel, 256, 0);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(labels, labels_kernel, 256, 0);
     return e;

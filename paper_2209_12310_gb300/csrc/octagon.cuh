@@ -163,11 +163,12 @@ __device__ __forceinline__ bool inner_fits(const Octagon& o, const int lo[4], co
     return true;
 }
 
-// Fills every field of o from the 8 vertices (one full warp calls this; lane 0
-// writes the scalar fields, all lanes search the inner region).
-static __device__ void setup_octagon_warp(Octagon& o, const int vx[8], const int vy[8], const int ext[8]) {
-    const int lane = threadIdx.x & 31;
-    if (lane == 0) {
+// Fills every field of o (in shared memory) from the 8 vertices.  The whole
+// block calls it (all threads, same arguments); thread 0 writes the scalar
+// fields and the threads search the inner region's scale t/1024 in parallel.
+static __device__ void setup_octagon_block(Octagon& o, const int vx[8], const int vy[8], const int ext[8]) {
+    __shared__ int s_best;
+    if (threadIdx.x == 0) {
         long long area2 = 0;
         for (int d = 0; d < 8; ++d) {
             o.vx[d] = vx[d];
@@ -184,27 +185,23 @@ static __device__ void setup_octagon_warp(Octagon& o, const int vx[8], const int
             o.quad[r] = make_edge(vx[a], vy[a], vx[b], vy[b]);
         }
         o.discard_none = (area2 == 0);
+        s_best = 0;
     }
-    __syncwarp();
+    __syncthreads();
     // 8-direction bounds of the octagon's vertices: x, y, x+y, x-y (biased).
     const int lo0[4] = {vx[W], vy[S], vx[SW] + vy[SW], vx[NW] - vy[NW] + kCoordLimit};
     const int hi0[4] = {vx[E], vy[N], vx[NE] + vy[NE], vx[SE] - vy[SE] + kCoordLimit};
-    int t1 = 0;
     if (!o.discard_none) {
-        int lo[4], hi[4];
-        inner_bounds(lo0, hi0, (lane + 1) * 32, lo, hi);
-        unsigned ok = __ballot_sync(0xFFFFFFFFu, inner_fits(o, lo, hi));
-        t1 = ok ? (32 - __clz(ok)) * 32 : 0;   // nested regions: passing lanes form a prefix
-        const int t2 = t1 + lane + 1;
-        bool f = false;
-        if (lane < 31 && t2 <= 1024) {
-            inner_bounds(lo0, hi0, t2, lo, hi);
-            f = inner_fits(o, lo, hi);
+        // every t in [1, 1024] is tested once, spread over the block
+        for (int t = 1 + (int)threadIdx.x; t <= 1024; t += blockDim.x) {
+            int lo[4], hi[4];
+            inner_bounds(lo0, hi0, t, lo, hi);
+            if (inner_fits(o, lo, hi)) atomicMax(&s_best, t);
         }
-        ok = __ballot_sync(0xFFFFFFFFu, f);
-        if (ok) t1 += 32 - __clz(ok);
     }
-    if (lane == 0) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int t1 = s_best;
         if (t1 > 0) {
             int lo[4], hi[4];
             inner_bounds(lo0, hi0, t1, lo, hi);
@@ -213,7 +210,7 @@ static __device__ void setup_octagon_warp(Octagon& o, const int vx[8], const int
             for (int k = 0; k < 4; ++k) { o.in_lo[k] = 1; o.in_hi[k] = 0; }   // empty
         }
     }
-    __syncwarp();
+    __syncthreads();
 }
 
 __device__ __forceinline__ void copy_octagon(Octagon* dst, const Octagon* src) {
