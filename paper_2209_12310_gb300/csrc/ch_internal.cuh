@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdio.h>
 
 #include "ch.h"
 
@@ -37,7 +38,7 @@ constexpr int kChainThreads = 256;
 constexpr int kChainItems = 16;
 constexpr int kChainTile = kChainThreads * kChainItems;
 constexpr int kMergeSmemCap = 8192;           // chain points a global merge keeps on chip
-constexpr int kSampleTiles = 2048;            // warp tiles read by the sample pass
+constexpr int kSampleTiles = 1024;            // warp tiles read by the sample pass (512k points)
 constexpr int kMaxLevels = 32;
 
 // Float edge-function error bound: |e_float - e_exact| < 2^28 for every edge
@@ -69,7 +70,7 @@ struct Octagon {
 
 // Small-path limits: the last block of a pass finishes the hull itself when
 // the survivors are few.
-constexpr unsigned kRawSmall = 32768;   // raw survivors one block re-classifies
+constexpr unsigned kRawSmall = 4096;    // raw survivors one block re-classifies
 constexpr int kMidCap = 8192;           // sort records one block turns into the hull
 
 // Per-call control block in device memory.
@@ -94,6 +95,21 @@ struct Ctl {
     Octagon oct;                        // octagon of the true extremes
     Octagon oct_s;                      // octagon of a sample's extremes
 };
+
+// Optional phase tracing of single-block kernels (debug builds with
+// -DCH_TRACE): thread 0 stamps %globaltimer and prints the deltas.
+#ifdef CH_TRACE
+#define CH_TRACE_DECL __shared__ unsigned long long s_trace_t[24]; __shared__ int s_trace_n; \
+    if (threadIdx.x == 0) s_trace_n = 0;
+#define CH_TRACE_MARK() do { if (threadIdx.x == 0 && s_trace_n < 24) { unsigned long long _t; \
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(_t)); s_trace_t[s_trace_n++] = _t; } } while (0)
+#define CH_TRACE_PRINT(tag) do { if (threadIdx.x == 0) { printf("[trace %s]", tag); \
+    for (int _i = 1; _i < s_trace_n; ++_i) printf(" %llu", s_trace_t[_i] - s_trace_t[_i - 1]); printf("\n"); } } while (0)
+#else
+#define CH_TRACE_DECL
+#define CH_TRACE_MARK() do { } while (0)
+#define CH_TRACE_PRINT(tag) do { } while (0)
+#endif
 
 // ---------------------------------------------------------------------------
 // Small helpers

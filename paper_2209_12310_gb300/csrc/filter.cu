@@ -96,7 +96,7 @@ __device__ __forceinline__ bool last_block(unsigned* counter, int* s_flag) {
 }
 
 // Warp tiles read by the sample pass: about 1/32 of the input, at most
-// kSampleTiles (a million points), at least min(ntiles, 64).
+// kSampleTiles, at least min(ntiles, 64).
 __host__ __device__ __forceinline__ long long sample_tiles(long long ntiles) {
     long long s = ntiles / 32;
     if (s < 64) s = ntiles < 64 ? ntiles : 64;
@@ -506,10 +506,28 @@ __device__ void finalize_block(const float* __restrict__ pts, long long n, int h
         s_ext[d] = ~0ull;
     }
     __syncthreads();
-    for (int d = 0; d < 8; ++d) {
-        for (long long i = s_lo[d] + threadIdx.x; i < s_hi[d]; i += blockDim.x) {
-            const int X = __float2int_rn(pts[2 * i]), Y = __float2int_rn(pts[2 * i + 1]);
-            if (dir_key(d, X, Y) == s_G[d]) atomicMin(&s_ext[d], (unsigned long long)i);
+    // One round of independent loads for all 8 directions (a tile has at
+    // most kWarpTilePts points; blockDim.x >= kWarpTilePts / 2).
+    {
+        float2 p[8][2];
+        bool valid[8][2];
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const long long i = s_lo[d] + threadIdx.x + (long long)h * blockDim.x;
+                valid[d][h] = i < s_hi[d];
+                p[d][h] = valid[d][h] ? reinterpret_cast<const float2*>(pts)[i] : make_float2(0.f, 0.f);
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const long long i = s_lo[d] + threadIdx.x + (long long)h * blockDim.x;
+                if (valid[d][h] && dir_key(d, __float2int_rn(p[d][h].x), __float2int_rn(p[d][h].y)) == s_G[d])
+                    atomicMin(&s_ext[d], (unsigned long long)i);
+            }
         }
     }
     __syncthreads();
@@ -563,6 +581,45 @@ __device__ void finalize_block(const float* __restrict__ pts, long long n, int h
     __syncthreads();
 }
 
+// Processes up to 32 queued lane tiles of a warp (one per lane): reloads the
+// lane tile's 16 points (just streamed, so served by L2) and keeps those not
+// strictly inside the inner region.  Entries are (warp tile << 5) | lane.
+// Warp-collective; returns emit_raw's count.
+__device__ __forceinline__ unsigned drain_queue(const float* __restrict__ pts, int head, unsigned* q, unsigned& qn,
+                                                const int* in, RawBuf& wbuf, unsigned& wcnt, Ctl* ctl,
+                                                uint64_t* raw_xy, uint32_t* raw_idx) {
+    const int lane = threadIdx.x & 31;
+    const unsigned take = qn < 32u ? qn : 32u;
+    float4 w[kLoadsPerLane];
+    unsigned keep = 0u;
+    long long i0 = 0;
+    if ((unsigned)lane < take) {
+        const unsigned e = q[lane];
+        const long long t = e >> 5;
+        const int ln = (int)(e & 31u);
+        const float4* base = reinterpret_cast<const float4*>(pts + 2 * head) + t * kWarpTileF4 + ln;
+#pragma unroll
+        for (int j = 0; j < kLoadsPerLane; ++j) w[j] = __ldcg(base + j * 32);
+#pragma unroll
+        for (int j = 0; j < kLoadsPerLane; ++j) {
+            if (!pt_in_inner(__float2int_rn(w[j].x), __float2int_rn(w[j].y), in)) keep |= 1u << (2 * j);
+            if (!pt_in_inner(__float2int_rn(w[j].z), __float2int_rn(w[j].w), in)) keep |= 2u << (2 * j);
+        }
+        i0 = head + 2 * (t * kWarpTileF4 + ln);
+    }
+    __syncwarp();
+    for (unsigned k = take + lane; k < qn; k += 32) q[k - take] = q[k];   // keep the rest
+    __syncwarp();
+    qn -= take;
+    auto get = [&](int s, long long& idx, float& x, float& y) {
+        const int j = s >> 1;
+        idx = i0 + 64 * j + (s & 1);
+        x = (s & 1) ? w[j].z : w[j].x;
+        y = (s & 1) ? w[j].w : w[j].y;
+    };
+    return emit_raw<2 * kLoadsPerLane>(keep, get, wbuf, wcnt, ctl, raw_xy, raw_idx);
+}
+
 constexpr size_t kMainSmemBytes = (size_t)8 * kStages * kWarpTileF4 * sizeof(float4);
 
 __global__ void __launch_bounds__(256, 2) main_kernel(const float* __restrict__ pts, long long n, int head,
@@ -574,6 +631,7 @@ __global__ void __launch_bounds__(256, 2) main_kernel(const float* __restrict__ 
     __shared__ int s_mode;
     __shared__ RawBuf s_buf[8];
     __shared__ unsigned long long s_bar[8][kStages];
+    __shared__ unsigned s_q[8][64];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -586,6 +644,7 @@ __global__ void __launch_bounds__(256, 2) main_kernel(const float* __restrict__ 
     bool filt = s_mode == 0;
     RawBuf& wbuf = s_buf[warp];
     unsigned wcnt = 0u;
+    unsigned qn = 0u;   // queued lane tiles of this warp (warp-uniform)
     Track tr;
     track_init(tr);
     // Scalar ranges (warp 0): the unaligned head point first and the ragged
@@ -639,30 +698,21 @@ __global__ void __launch_bounds__(256, 2) main_kernel(const float* __restrict__ 
             // Points strictly inside the inner region of the sample octagon
             // are strictly inside the hull; every other point is a raw
             // survivor, classified against the true octagon once its extremes
-            // are known.  Lanes with such points re-read them from the stage.
+            // are known.  Lanes whose 16 points are not all inside are queued
+            // and handled 32 at a time, one per lane, so outliers cost the
+            // warp a few instructions instead of a warp-wide slow path.
             const bool inside = tile_in_inner(tk, s_inner);
-            if (!__all_sync(0xFFFFFFFFu, inside)) {
-                unsigned keep = 0u;
-                if (!inside) {
-#pragma unroll
-                    for (int j = 0; j < kLoadsPerLane; ++j) {
-                        const float4 v = cur[j * 32 + lane];
-                        if (!pt_in_inner(__float2int_rn(v.x), __float2int_rn(v.y), s_inner)) keep |= 1u << (2 * j);
-                        if (!pt_in_inner(__float2int_rn(v.z), __float2int_rn(v.w), s_inner)) keep |= 2u << (2 * j);
+            const unsigned fail = __ballot_sync(0xFFFFFFFFu, !inside);
+            if (fail) {
+                if (!inside) s_q[warp][qn + __popc(fail & lanemask_lt())] = ((unsigned)t << 5) | (unsigned)lane;
+                qn += __popc(fail);
+                __syncwarp();
+                if (qn >= 32u) {
+                    const unsigned upto = drain_queue(pts, head, s_q[warp], qn, s_inner, wbuf, wcnt, ctl, raw_xy, raw_idx);
+                    if (upto > switch_at) {   // dense data: leave filtering to the second pass
+                        if (lane == 0) atomicExch(&ctl->mode, 1);
+                        filt = false;
                     }
-                }
-                const long long i0 = head + 2 * (t * kWarpTileF4 + lane);
-                auto get = [&](int s, long long& idx, float& x, float& y) {
-                    const int j = s >> 1;
-                    const float4 v = cur[j * 32 + lane];
-                    idx = i0 + 64 * j + (s & 1);
-                    x = (s & 1) ? v.z : v.x;
-                    y = (s & 1) ? v.w : v.y;
-                };
-                const unsigned upto = emit_raw<2 * kLoadsPerLane>(keep, get, wbuf, wcnt, ctl, raw_xy, raw_idx);
-                if (upto > switch_at) {   // dense data: leave filtering to the second pass
-                    if (lane == 0) atomicExch(&ctl->mode, 1);
-                    filt = false;
                 }
             }
             if ((k & 7) == 7) {
@@ -675,6 +725,7 @@ __global__ void __launch_bounds__(256, 2) main_kernel(const float* __restrict__ 
     }
     if (gwarp == 0 && head + ntiles * kWarpTilePts < n)
         scalar_range(head + ntiles * kWarpTilePts, n, (unsigned)(ntiles + 1));
+    while (qn > 0u) drain_queue(pts, head, s_q[warp], qn, s_inner, wbuf, wcnt, ctl, raw_xy, raw_idx);
     flush_raw(wbuf, wcnt, ctl, raw_xy, raw_idx);
 
     const bool err = tr.bad || (tr.orv >> kCoordBits) != 0u;
@@ -773,13 +824,18 @@ __global__ void __launch_bounds__(256, 3) stagec_kernel(const float* __restrict_
 //   phase 1 (after stagec_kernel): support-line end-point records, then with
 //     few records compute the hull.
 // Data errors found by the streaming pass end the call here: out_n = status.
-__global__ void __launch_bounds__(1024) tail_kernel(const float* __restrict__ pts, long long n, int head, Ctl* ctl,
+constexpr int kTailThreads = 256;
+constexpr size_t kTailSmemBytes = kMidSmemBytes > sizeof(WrapSmem) ? kMidSmemBytes : sizeof(WrapSmem);
+
+__global__ void __launch_bounds__(kTailThreads) tail_kernel(const float* __restrict__ pts, long long n, int head, Ctl* ctl,
                                                     const uint64_t* raw_xy, const uint32_t* raw_idx, uint32_t* keys,
                                                     uint64_t* vals, int phase, int hull, int32_t* out_idx,
                                                     int64_t* out_n) {
     extern __shared__ __align__(16) char dyn[];
     __shared__ Octagon s_o;
     __shared__ unsigned s_hist[kSortPasses][kDigits];
+    CH_TRACE_DECL
+    CH_TRACE_MARK();
     if (*(volatile int*)&ctl->done) return;
     if (read_status(ctl) != CH_OK) {
         if (hull && threadIdx.x == 0) { *out_n = read_status(ctl); ctl->done = 1; }
@@ -787,6 +843,7 @@ __global__ void __launch_bounds__(1024) tail_kernel(const float* __restrict__ pt
     }
     if (phase == 0) {
         finalize_block(pts, n, head, ctl, s_o, keys, vals);
+        CH_TRACE_MARK();
         if (read_status(ctl) != CH_OK) {
             if (hull && threadIdx.x == 0) { *out_n = read_status(ctl); ctl->done = 1; }
             return;
@@ -794,7 +851,7 @@ __global__ void __launch_bounds__(1024) tail_kernel(const float* __restrict__ pt
         if (!hull) return;
         const int mode = *(volatile int*)&ctl->mode;
         const unsigned nraw = *(volatile unsigned*)&ctl->count_raw;
-        if (mode != 0 || nraw > kRawSmall) return;
+        if (mode != 0 || nraw > kRawSmall) { CH_TRACE_PRINT("tail0-final"); return; }
         for (int i = threadIdx.x; i < kSortPasses * kDigits; i += blockDim.x) (&s_hist[0][0])[i] = 0u;
         __syncthreads();
         reclassify_raw(raw_xy, raw_idx, nraw, blockDim.x, (unsigned)threadIdx.x, s_o, ctl, keys, vals, s_hist);
@@ -802,6 +859,7 @@ __global__ void __launch_bounds__(1024) tail_kernel(const float* __restrict__ pt
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) ctl->records_ready = 1;
+        CH_TRACE_MARK();
     } else {
         if (*(volatile int*)&ctl->records_ready) return;   // phase 0 produced every record
         copy_octagon(&s_o, &ctl->oct);
@@ -810,11 +868,21 @@ __global__ void __launch_bounds__(1024) tail_kernel(const float* __restrict__ pt
     emit_line_records(s_o, ctl, keys, vals);
     __threadfence();
     __syncthreads();
+    CH_TRACE_MARK();
     const unsigned cnt = *(volatile unsigned*)&ctl->count;
     if (cnt <= (unsigned)kMidCap) {
-        mid_hull(keys, vals, (int)cnt, pts, n, ctl, out_idx, out_n, dyn);
+        // Few records: gift wrapping (few chain vertices), else sort-based.
+        if (!wrap_hull(keys, vals, (int)cnt, n, ctl, out_idx, out_n, *reinterpret_cast<WrapSmem*>(dyn))) {
+            __syncthreads();
+            mid_hull(keys, vals, (int)cnt, pts, n, ctl, out_idx, out_n, dyn);
+        }
         if (threadIdx.x == 0) ctl->done = 1;
     }
+    CH_TRACE_MARK();
+#ifdef CH_TRACE
+    if (threadIdx.x == 0) printf("[tail phase %d] records %u raw %u\n", phase, cnt, ctl->count_raw);
+#endif
+    CH_TRACE_PRINT("tail");
 }
 
 // ---------------------------------------------------------------------------
@@ -870,8 +938,8 @@ void launch_main(const float* pts, long long n, int head, long long ntiles, Ctl*
 void launch_tail(const float* pts, long long n, int head, Ctl* ctl, const uint64_t* raw_xy, const uint32_t* raw_idx,
                  uint32_t* keys, uint64_t* vals, int phase, int hull, int32_t* out_idx, int64_t* out_n,
                  cudaStream_t s) {
-    tail_kernel<<<1, 1024, kMidSmemBytes, s>>>(pts, n, head, ctl, raw_xy, raw_idx, keys, vals, phase, hull, out_idx,
-                                               out_n);
+    tail_kernel<<<1, kTailThreads, kTailSmemBytes, s>>>(pts, n, head, ctl, raw_xy, raw_idx, keys, vals, phase, hull,
+                                                        out_idx, out_n);
 }
 
 void launch_stagec(const float* pts, long long n, int head, long long ntiles, Ctl* ctl, const uint64_t* raw_xy,
@@ -890,7 +958,7 @@ void launch_filter_output(const Ctl* ctl, long long n, int32_t* out_ext8, int64_
 long long sample_tiles_host(long long ntiles) { return sample_tiles(ntiles); }
 
 cudaError_t configure_filter_kernels() {
-    cudaError_t e = cudaFuncSetAttribute(tail_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMidSmemBytes);
+    cudaError_t e = cudaFuncSetAttribute(tail_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemBytes);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(main_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMainSmemBytes);
     return e;

@@ -267,6 +267,8 @@ static __device__ void mid_hull(const uint32_t* keys, const uint64_t* vals, int 
     int* cu = reinterpret_cast<int*>(sk + kMidCap);
     int* cv = cu + kMidCap;
     int* ci = cv + kMidCap;
+    CH_TRACE_DECL
+    CH_TRACE_MARK();
     const int tid = threadIdx.x, T = blockDim.x;
     int P = 1;
     while (P < m) P <<= 1;
@@ -285,6 +287,7 @@ static __device__ void mid_hull(const uint32_t* keys, const uint64_t* vals, int 
             __syncthreads();
         }
     }
+    CH_TRACE_MARK();
     // run reduction: one point per (queue, u), the minimum (v, index)
     int written = 0;
     for (int base = 0; base < m; base += T) {
@@ -320,6 +323,7 @@ static __device__ void mid_hull(const uint32_t* keys, const uint64_t* vals, int 
         for (int r = prev + 1; r <= cur; ++r) s_rs[r] = p;
     }
     __syncthreads();
+    CH_TRACE_MARK();
     // four queues at once, a quarter of the block each; queue bits are equal
     // within a queue, so cross products of cu differences are those of u
     const int G = T / 4, g = tid / G, lt = tid % G;
@@ -347,6 +351,7 @@ static __device__ void mid_hull(const uint32_t* keys, const uint64_t* vals, int 
         }
         __syncthreads();
     }
+    CH_TRACE_MARK();
     // stitch: V (in the sort buffer) = the queue chains without their last point
     int* V = reinterpret_cast<int*>(sk);
     int* flag = V + kMidCap;
@@ -356,7 +361,222 @@ static __device__ void mid_hull(const uint32_t* keys, const uint64_t* vals, int 
     for (int r = 0; r < 4; ++r)
         for (int j = tid; j < off[r + 1] - off[r]; j += T) V[off[r] + j] = ci[s_rs[r] + j];
     __syncthreads();
+    CH_TRACE_MARK();
     stitch_core(V, off[4], flag, cu, pts, n, ctl, out_idx, out_n);
+    CH_TRACE_MARK();
+    CH_TRACE_PRINT("mid_hull");
+}
+
+// ---------------------------------------------------------------------------
+// Gift wrapping of the queues (Jarvis march, Table I), one warp per queue:
+// from the queue's start extreme (minimum u), the next chain vertex is the
+// point of larger u seen at the smallest slope; on equal slopes the farthest
+// (collinear points are not vertices), on equal coordinates the lowest index
+// (the representative of duplicates).  Each step is a warp argmin; it stops at
+// the end extreme (maximum u).  Steps = chain vertices, so it suits the few
+// vertices that remain after filtering; more than kWrapCap vertices in a queue
+// abandons it (the caller falls back to the sort-based path).
+constexpr int kWrapCap = 512;
+
+// Inverse of queue_frame.
+__device__ __forceinline__ void frame_to_xy(int r, int u, int v, int& x, int& y) {
+    const int off = kCoordLimit, top = 2 * kCoordLimit - 2;
+    switch (r) {
+        case 0: x = (u + v - off) / 2; y = (v - u + off) / 2; break;
+        case 1: x = (u - v + off) / 2; y = (u + v - off) / 2; break;
+        case 2: x = (top - v - u + off) / 2; y = (top - v + u - off) / 2; break;
+        default: x = (top - u + v - off) / 2; y = (top - u - v + off) / 2; break;
+    }
+}
+
+// "a is a better next vertex than b" seen from p (both of larger u than p).
+__device__ __forceinline__ bool wrap_better(int pu, int pv, int au, int av, int ai, int bu, int bv, int bi) {
+    const long long c = (long long)(au - pu) * (bv - pv) - (long long)(av - pv) * (bu - pu);
+    if (c != 0) return c > 0;
+    if (au != bu) return au > bu;
+    if (av != bv) return av < bv;
+    return ai < bi;
+}
+
+// Shared memory of wrap_hull (dynamic, placed by the caller).
+struct WrapSmem {
+    int qu[kMidCap], qv[kMidCap], qi[kMidCap];   // records grouped by queue
+    int cu[4][kWrapCap], cv[4][kWrapCap], ci[4][kWrapCap];   // queue chains
+};
+
+// Returns false (nothing written) when a queue has more than kWrapCap chain
+// vertices.  Needs blockDim.x >= 128; m <= kMidCap.
+static __device__ bool wrap_hull(const uint32_t* keys, const uint64_t* vals, int m, long long n, Ctl* ctl,
+                                 int32_t* out_idx, int64_t* out_n, WrapSmem& sm) {
+    __shared__ int s_cnt[4], s_base[5], s_len[4], s_fail;
+    __shared__ int s_V[2 * kWrapCap], s_X[2 * kWrapCap], s_Y[2 * kWrapCap];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < 4) s_cnt[tid] = 0;
+    if (tid == 0) s_fail = 0;
+    __syncthreads();
+    for (int i = tid; i < m; i += blockDim.x) atomicAdd(&s_cnt[keys[i] >> kKeyBits], 1);
+    __syncthreads();
+    if (tid == 0) {
+        s_base[0] = 0;
+        for (int r = 0; r < 4; ++r) s_base[r + 1] = s_base[r] + s_cnt[r];
+        for (int r = 0; r < 4; ++r) s_cnt[r] = s_base[r];
+    }
+    __syncthreads();
+    for (int i = tid; i < m; i += blockDim.x) {
+        const uint32_t k = keys[i];
+        const uint64_t w = vals[i];
+        const int pos = atomicAdd(&s_cnt[k >> kKeyBits], 1);
+        sm.qu[pos] = (int)(k & kKeyMask);
+        sm.qv[pos] = (int)(w >> 31);
+        sm.qi[pos] = (int)(w & 0x7FFFFFFFull);
+    }
+    __syncthreads();
+    if (warp < 4) {
+        const int r = warp, a = s_base[r], b = s_base[r + 1];
+        // start: minimum u (then v, index); end: maximum u
+        int su = INT_MAX, sv = INT_MAX, si = INT_MAX, eu = -1;
+        for (int i = a + lane; i < b; i += 32) {
+            const int u = sm.qu[i], v = sm.qv[i], id = sm.qi[i];
+            if (u < su || (u == su && (v < sv || (v == sv && id < si)))) { su = u; sv = v; si = id; }
+            eu = max(eu, sm.qu[i]);
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            const int ou = __shfl_xor_sync(0xFFFFFFFFu, su, o), ov = __shfl_xor_sync(0xFFFFFFFFu, sv, o);
+            const int oi = __shfl_xor_sync(0xFFFFFFFFu, si, o);
+            if (ou < su || (ou == su && (ov < sv || (ov == sv && oi < si)))) { su = ou; sv = ov; si = oi; }
+            eu = max(eu, __shfl_xor_sync(0xFFFFFFFFu, eu, o));
+        }
+        int len = 0;
+        int pu = su, pv = sv, pi = si;
+        if (lane == 0) { sm.cu[r][0] = pu; sm.cv[r][0] = pv; sm.ci[r][0] = pi; }
+        len = 1;
+        while (pu < eu) {
+            int bu = -1, bv = 0, bi = 0;
+            for (int i = a + lane; i < b; i += 32) {
+                const int u = sm.qu[i];
+                if (u <= pu) continue;
+                const int v = sm.qv[i], id = sm.qi[i];
+                if (bu < 0 || wrap_better(pu, pv, u, v, id, bu, bv, bi)) { bu = u; bv = v; bi = id; }
+            }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                const int ou = __shfl_xor_sync(0xFFFFFFFFu, bu, o), ov = __shfl_xor_sync(0xFFFFFFFFu, bv, o);
+                const int oi = __shfl_xor_sync(0xFFFFFFFFu, bi, o);
+                if (ou >= 0 && (bu < 0 || wrap_better(pu, pv, ou, ov, oi, bu, bv, bi))) { bu = ou; bv = ov; bi = oi; }
+            }
+            if (bu < 0 || len >= kWrapCap) { len = -1; break; }   // too many vertices (or inconsistent)
+            pu = bu; pv = bv; pi = bi;
+            if (lane == 0) { sm.cu[r][len] = pu; sm.cv[r][len] = pv; sm.ci[r][len] = pi; }
+            ++len;
+        }
+        if (lane == 0) {
+            s_len[r] = len;
+            if (len < 0) s_fail = 1;
+        }
+    }
+    __syncthreads();
+    if (s_fail) return false;
+    int off[5];
+    off[0] = 0;
+    for (int r = 0; r < 4; ++r) off[r + 1] = off[r] + s_len[r] - 1;
+    const int mv = off[4];
+    if (mv > 2 * kWrapCap) return false;
+    for (int r = 0; r < 4; ++r)
+        for (int j = tid; j < s_len[r] - 1; j += blockDim.x) {
+            int x, y;
+            frame_to_xy(r, sm.cu[r][j], sm.cv[r][j], x, y);
+            s_V[off[r] + j] = sm.ci[r][j];
+            s_X[off[r] + j] = x;
+            s_Y[off[r] + j] = y;
+        }
+    __syncthreads();
+    if (warp != 0) return true;
+    // ---- stitch on one warp ----
+    if (mv == 0) {   // all four quadrilateral vertices coincide
+        if (lane == 0) { out_idx[0] = ctl->oct.ext[W]; *out_n = 1; }
+        return true;
+    }
+    int npos = 0, nneg = 0;
+    for (int i = lane; i < mv; i += 32) {
+        const int p = (i + mv - 1) % mv, q = (i + 1) % mv;
+        const long long tr = orient64(s_X[p], s_Y[p], s_X[i], s_Y[i], s_X[q], s_Y[q]);
+        npos += tr > 0;
+        nneg += tr < 0;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        npos += __shfl_xor_sync(0xFFFFFFFFu, npos, o);
+        nneg += __shfl_xor_sync(0xFFFFFFFFu, nneg, o);
+    }
+    if (npos == 0) {   // degenerate: [lex-min, lex-max], lowest index per coordinate
+        unsigned long long lo = ~0ull, hi = 0ull;
+        for (int i = lane; i < mv; i += 32) {
+            const unsigned long long kxy = xy_key(s_X[i], s_Y[i]);
+            lo = kxy < lo ? kxy : lo;
+            hi = kxy > hi ? kxy : hi;
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            const unsigned long long a2 = __shfl_xor_sync(0xFFFFFFFFu, lo, o), b2 = __shfl_xor_sync(0xFFFFFFFFu, hi, o);
+            lo = a2 < lo ? a2 : lo;
+            hi = b2 > hi ? b2 : hi;
+        }
+        int ilo = INT_MAX, ihi = INT_MAX;
+        for (int i = lane; i < mv; i += 32) {
+            const unsigned long long kxy = xy_key(s_X[i], s_Y[i]);
+            if (kxy == lo) ilo = min(ilo, s_V[i]);
+            if (kxy == hi) ihi = min(ihi, s_V[i]);
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            ilo = min(ilo, __shfl_xor_sync(0xFFFFFFFFu, ilo, o));
+            ihi = min(ihi, __shfl_xor_sync(0xFFFFFFFFu, ihi, o));
+        }
+        if (lane == 0) {
+            out_idx[0] = ilo;
+            if (lo == hi) *out_n = 1;
+            else { out_idx[1] = ihi; *out_n = 2; }
+        }
+        return true;
+    }
+    if (nneg != 0 && lane == 0) set_status(ctl, CH_ECUDA);   // internal consistency check
+    // strictly convex vertices in order, the lexicographically smallest first
+    int h = 0;
+    unsigned long long best = ~0ull;
+    for (int base = 0; base < mv; base += 32) {
+        const int i = base + lane;
+        bool f = false;
+        if (i < mv) {
+            const int p = (i + mv - 1) % mv, q = (i + 1) % mv;
+            f = orient64(s_X[p], s_Y[p], s_X[i], s_Y[i], s_X[q], s_Y[q]) > 0;
+        }
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, f);
+        if (f) {
+            const int pos = h + __popc(bal & lanemask_lt());
+            const unsigned long long kxy = (xy_key(s_X[i], s_Y[i]) << 16) | (unsigned)pos;
+            best = kxy < best ? kxy : best;
+            sm.qu[pos] = s_V[i];   // reuse the record buffer for the output order
+        }
+        h += __popc(bal);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const unsigned long long a2 = __shfl_xor_sync(0xFFFFFFFFu, best, o);
+        best = a2 < best ? a2 : best;
+    }
+    __syncwarp();
+    if (h > n) {
+        if (lane == 0) { set_status(ctl, CH_ECUDA); *out_n = CH_ECUDA; }
+        return true;
+    }
+    const int start = (int)(best & 0xFFFFull);
+    for (int j = lane; j < h; j += 32) out_idx[j] = sm.qu[(start + j) % h];
+    if (lane == 0) {
+        const int st = read_status(ctl);
+        *out_n = (st == CH_OK) ? h : st;
+    }
+    return true;
 }
 
 }  // namespace ch

@@ -192,11 +192,39 @@ static __device__ void setup_octagon_block(Octagon& o, const int vx[8], const in
     const int lo0[4] = {vx[W], vy[S], vx[SW] + vy[SW], vx[NW] - vy[NW] + kCoordLimit};
     const int hi0[4] = {vx[E], vy[N], vx[NE] + vy[NE], vx[SE] - vy[SE] + kCoordLimit};
     if (!o.discard_none) {
-        // every t in [1, 1024] is tested once, spread over the block
-        for (int t = 1 + (int)threadIdx.x; t <= 1024; t += blockDim.x) {
-            int lo[4], hi[4];
-            inner_bounds(lo0, hi0, t, lo, hi);
-            if (inner_fits(o, lo, hi)) atomicMax(&s_best, t);
+        // Each warp tests one scale per round (its lanes split the 8 x 8
+        // candidate/edge checks); rounds refine the step by the warp count.
+        const int nw = (int)(blockDim.x >> 5), warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
+        int step = 1024 / nw;
+        if (step < 1) step = 1;
+        int base = 0;
+        for (;;) {
+            const int t = base + step * (warp + 1);
+            bool ok = t <= 1024;
+            if (ok) {
+                int lo[4], hi[4];
+                inner_bounds(lo0, hi0, t, lo, hi);
+                ok = !(lo[0] > hi[0] || lo[1] > hi[1] || lo[2] > hi[2] || lo[3] > hi[3]);
+                if (ok) {
+                    const long long xl = lo[0], xh = hi[0], yl = lo[1], yh = hi[1];
+                    const long long sl = lo[2], sh = hi[2], dl = lo[3] - kCoordLimit, dh = hi[3] - kCoordLimit;
+                    const long long px[8] = {xl, sl - yl, dh + yl, xh, xh, sh - yh, dl + yh, xl};
+                    const long long py[8] = {sl - xl, yl, yl, xh - dh, sh - xh, yh, yh, xl - dl};
+                    bool mine = true;
+                    for (int pair = lane; pair < 64; pair += 32) {   // (candidate, edge)
+                        const Edge& e = o.oct[pair & 7];
+                        const int c = pair >> 3;
+                        if ((e.dx | e.dy) != 0 && edge_exact(e, px[c], py[c]) < 0) mine = false;
+                    }
+                    ok = __all_sync(0xFFFFFFFFu, mine);
+                }
+            }
+            if (ok && lane == 0) atomicMax(&s_best, t);
+            __syncthreads();
+            if (step == 1) break;
+            base = s_best;
+            step = step / nw > 0 ? step / nw : 1;
+            __syncthreads();
         }
     }
     __syncthreads();
