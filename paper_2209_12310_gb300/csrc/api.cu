@@ -87,8 +87,11 @@ struct Workspace {
 
 static std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
 
-static int grow_workspace(Workspace& ws, long long n, cudaStream_t s) {
+void drop_graphs(int dev, cudaStream_t s);
+
+static int grow_workspace(Workspace& ws, long long n, cudaStream_t s, int dev) {
     if (n <= ws.n_cap) return CH_OK;
+    drop_graphs(dev, s);
     const long long want = std::max(n, (long long)(ws.n_cap > 0 ? ws.n_cap + ws.n_cap / 4 : n));
     const Layout L = make_layout(want);
     if (ws.base) {
@@ -116,7 +119,7 @@ static int grow_workspace(Workspace& ws, long long n, cudaStream_t s) {
 int get_workspace(int dev, cudaStream_t s, long long n, char** base, Layout* L) {
     std::lock_guard<std::mutex> lk(g_mu);
     Workspace& ws = g_ws[std::make_pair(dev, s)];
-    const int st = grow_workspace(ws, n, s);
+    const int st = grow_workspace(ws, n, s, dev);
     if (st != CH_OK) return st;
     *base = ws.base;
     *L = make_layout(ws.n_cap);
@@ -127,6 +130,7 @@ void release_stream_workspace(int dev, cudaStream_t s) {
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_ws.find(std::make_pair(dev, s));
     if (it == g_ws.end()) return;
+    drop_graphs(dev, s);
     cudaStreamSynchronize(s);
     if (it->second.base) cudaFree(it->second.base);
     if (it->second.stage) cudaFree(it->second.stage);
@@ -211,14 +215,10 @@ static void prof_drain() {
 
 // ---------------------------------------------------------------------------
 // The launch sequence of one hull (n >= 1) on an allocated workspace.
-int enqueue_hull(const float* pts, long long n, int32_t* out_idx, int64_t* out_n, cudaStream_t s,
-                 int dev) {
+static int enqueue_hull_direct(const float* pts, long long n, int32_t* out_idx, int64_t* out_n, cudaStream_t s,
+                               int dev, char* base, const Layout& L) {
     DevInfo di;
     int st = device_info(dev, &di);
-    if (st != CH_OK) return st;
-    char* base = nullptr;
-    Layout L;
-    st = get_workspace(dev, s, n, &base, &L);
     if (st != CH_OK) return st;
     Ctl* ctl = (Ctl*)(base + L.off_ctl);
     uint32_t* kA = (uint32_t*)(base + L.off_kA);
@@ -264,6 +264,112 @@ int enqueue_hull(const float* pts, long long n, int32_t* out_idx, int64_t* out_n
                      out_n, grid_chain, s);
     }
     return cudaGetLastError() == cudaSuccess ? CH_OK : CH_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// CUDA-graph cache.  A call repeated with the same (device, stream, points,
+// n, outputs, workspace) replays one captured graph instead of ~10 separate
+// launches.  The first call of a key runs directly; the second captures the
+// sequence on a private stream and instantiates it; later ones replay it.
+// Disabled while profiling (per-kernel events) and when the caller's stream
+// is itself being captured (the launches then become part of that graph).
+struct GraphKey {
+    int dev;
+    cudaStream_t s;
+    const void* pts;
+    long long n;
+    const void* out_idx;
+    const void* out_n;
+    const void* ws;
+    bool operator<(const GraphKey& o) const {
+        if (dev != o.dev) return dev < o.dev;
+        if (s != o.s) return s < o.s;
+        if (pts != o.pts) return pts < o.pts;
+        if (n != o.n) return n < o.n;
+        if (out_idx != o.out_idx) return out_idx < o.out_idx;
+        if (out_n != o.out_n) return out_n < o.out_n;
+        return ws < o.ws;
+    }
+};
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    int seen = 0;
+    unsigned long long last_use = 0;
+};
+static std::mutex g_graph_mu;
+static std::map<GraphKey, GraphEntry> g_graphs;
+static unsigned long long g_graph_clock = 0;
+static constexpr size_t kGraphCacheMax = 64;
+
+static void drop_graphs_locked(int dev, cudaStream_t s) {
+    for (auto it = g_graphs.begin(); it != g_graphs.end();) {
+        if (it->first.dev == dev && it->first.s == s) {
+            if (it->second.exec) cudaGraphExecDestroy(it->second.exec);
+            it = g_graphs.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
+void drop_graphs(int dev, cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    drop_graphs_locked(dev, s);
+}
+
+int enqueue_hull(const float* pts, long long n, int32_t* out_idx, int64_t* out_n, cudaStream_t s, int dev) {
+    DevInfo di;
+    int st = device_info(dev, &di);
+    if (st != CH_OK) return st;
+    // The workspace must exist (and keep its address) before a graph names it.
+    char* base = nullptr;
+    Layout L;
+    st = get_workspace(dev, s, n, &base, &L);
+    if (st != CH_OK) return st;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (g_prof || cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
+        return enqueue_hull_direct(pts, n, out_idx, out_n, s, dev, base, L);
+    const GraphKey key{dev, s, pts, n, out_idx, out_n, base};
+    cudaGraphExec_t exec = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_graph_mu);
+        GraphEntry& e = g_graphs[key];
+        e.last_use = ++g_graph_clock;
+        if (e.exec) exec = e.exec;
+        else if (e.seen++ == 0) return enqueue_hull_direct(pts, n, out_idx, out_n, s, dev, base, L);
+    }
+    if (exec) return cudaGraphLaunch(exec, s) == cudaSuccess ? CH_OK : CH_ECUDA;
+    // Second call of this key: capture on a private stream, then replay.
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return enqueue_hull_direct(pts, n, out_idx, out_n, s, dev, base, L);
+    }
+    cudaGraph_t graph = nullptr;
+    bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        st = enqueue_hull_direct(pts, n, out_idx, out_n, cs, dev, base, L);
+        ok = cudaStreamEndCapture(cs, &graph) == cudaSuccess && st == CH_OK && graph;
+    }
+    if (ok) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    if (!ok) {
+        cudaGetLastError();
+        return enqueue_hull_direct(pts, n, out_idx, out_n, s, dev, base, L);
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_graph_mu);
+        if (g_graphs.size() > kGraphCacheMax) {   // evict the least recently used entry
+            auto victim = g_graphs.begin();
+            for (auto it = g_graphs.begin(); it != g_graphs.end(); ++it)
+                if (it->second.last_use < victim->second.last_use) victim = it;
+            if (victim->second.exec) cudaGraphExecDestroy(victim->second.exec);
+            g_graphs.erase(victim);
+        }
+        g_graphs[key].exec = exec;
+    }
+    return cudaGraphLaunch(exec, s) == cudaSuccess ? CH_OK : CH_ECUDA;
 }
 
 int check_points_args(const float* pts, long long n) {
@@ -370,6 +476,12 @@ int ch_reserve(int64_t n, int32_t k, void* stream) {
 size_t ch_workspace_bytes(int64_t n) { return n < 0 ? 0 : make_layout(n).total; }
 
 int ch_release(void) {
+    {
+        std::lock_guard<std::mutex> lk(g_graph_mu);
+        for (auto& kv : g_graphs)
+            if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        g_graphs.clear();
+    }
     std::lock_guard<std::mutex> lk(g_mu);
     for (auto& kv : g_ws) {
         cudaStreamSynchronize(kv.first.second);

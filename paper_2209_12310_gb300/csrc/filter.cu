@@ -349,16 +349,29 @@ __device__ __forceinline__ unsigned emit_raw(unsigned keep, Get get, RawBuf& b, 
 // can be hull vertices.  They are reduced into ctl->line_ep (minimum and
 // maximum along the line, lowest index on ties) instead of becoming records;
 // emit_line_records turns the end points into records afterwards.
-__device__ __forceinline__ bool reduce_on_line(const Octagon& o, int X, int Y, unsigned idx, Ctl* ctl) {
+// Warp-collective: every lane passes its candidate (valid = false for none);
+// the warp reduces per line first and issues one atomic pair per line.
+__device__ __forceinline__ bool reduce_on_line(const Octagon& o, bool valid, int X, int Y, unsigned idx, Ctl* ctl) {
     bool on = false;
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
-        const bool hit = (l == 0) ? X == o.vx[W] : (l == 1) ? Y == o.vy[S] : (l == 2) ? X == o.vx[E] : Y == o.vy[N];
-        if (hit) {
+        const bool hit = valid && ((l == 0) ? X == o.vx[W] : (l == 1) ? Y == o.vy[S] : (l == 2) ? X == o.vx[E] : Y == o.vy[N]);
+        on |= hit;
+        if (__any_sync(0xFFFFFFFFu, hit)) {
             const unsigned along = (l & 1) ? (unsigned)X : (unsigned)Y;
-            atomicMin(&ctl->line_ep[2 * l], ((unsigned long long)along << 32) | idx);
-            atomicMax(&ctl->line_ep[2 * l + 1], ((unsigned long long)along << 32) | (0xFFFFFFFFu - idx));
-            on = true;
+            unsigned long long mn = hit ? ((unsigned long long)along << 32) | idx : ~0ull;
+            unsigned long long mx = hit ? ((unsigned long long)along << 32) | (0xFFFFFFFFu - idx) : 0ull;
+#pragma unroll
+            for (int o2 = 16; o2; o2 >>= 1) {
+                const unsigned long long a = __shfl_xor_sync(0xFFFFFFFFu, mn, o2);
+                const unsigned long long b = __shfl_xor_sync(0xFFFFFFFFu, mx, o2);
+                mn = a < mn ? a : mn;
+                mx = b > mx ? b : mx;
+            }
+            if ((threadIdx.x & 31) == 0) {
+                atomicMin(&ctl->line_ep[2 * l], mn);
+                atomicMax(&ctl->line_ep[2 * l + 1], mx);
+            }
         }
     }
     return on;
@@ -369,16 +382,16 @@ __device__ __forceinline__ void emit_records(unsigned keep, unsigned long long r
                                              uint32_t* keys, uint64_t* vals, unsigned (*s_hist)[kDigits],
                                              const Octagon* lines = nullptr) {
     const int lane = threadIdx.x & 31;
-    if (lines) {   // divert support-line points to the end-point reduction
+    if (lines) {   // divert support-line points to the end-point reduction (warp-collective)
 #pragma unroll
         for (int s = 0; s < kSlots; ++s) {
-            if ((keep >> s) & 1u) {
-                long long idx;
-                float x, y;
-                get(s, idx, x, y);
-                if (reduce_on_line(*lines, __float2int_rn(x), __float2int_rn(y), (unsigned)idx, ctl))
-                    keep &= ~(1u << s);
-            }
+            const bool kept = (keep >> s) & 1u;
+            if (!__any_sync(0xFFFFFFFFu, kept)) continue;
+            long long idx = 0;
+            float x = 0.0f, y = 0.0f;
+            if (kept) get(s, idx, x, y);
+            if (reduce_on_line(*lines, kept, __float2int_rn(x), __float2int_rn(y), (unsigned)idx, ctl))
+                keep &= ~(1u << s);
         }
     }
     const unsigned c = __popc(keep);

@@ -148,3 +148,27 @@ def test_full_size_workloads(lib, name):
     want = oracle.hull(pts)
     np.testing.assert_array_equal(got, want)
     check_hull(pts, got)
+
+
+def test_repeated_calls_replay_graph(lib):
+    """Calls repeated with the same buffers replay a cached CUDA graph; the
+    results must follow the current contents of the buffers, and a larger
+    call on the same stream (workspace regrowth) must stay correct."""
+    stream = torch.cuda.Stream()
+    a = W.normal(300_000, 21)
+    b = W.ring(300_000, 22)
+    pts = torch.from_numpy(a).cuda()
+    out_idx = torch.empty(pts.shape[0], dtype=torch.int32, device="cuda")
+    out_n = torch.empty(1, dtype=torch.int64, device="cuda")
+    want_a, want_b = oracle.hull(a), oracle.hull(b)
+    with torch.cuda.stream(stream):
+        for rep in range(6):
+            src = a if rep % 2 == 0 else b
+            pts.copy_(torch.from_numpy(src).cuda())
+            lib.ch_hull(pts.data_ptr(), pts.shape[0], out_idx.data_ptr(), out_n.data_ptr(), stream.cuda_stream)
+            stream.synchronize()
+            h = int(out_n.item())
+            np.testing.assert_array_equal(out_idx[:h].cpu().numpy(), want_a if rep % 2 == 0 else want_b)
+        big = W.uniform(2_000_000, 23)
+        got = lib.hull(torch.from_numpy(big).cuda(), stream=stream).cpu().numpy()
+        np.testing.assert_array_equal(got, oracle.hull(big))
