@@ -275,13 +275,12 @@ def run_ours(args):
     # Roofline of the dominant kernel (largest device time in the timed region).
     survivors = None
     peak, peak_src = peaks()
-    kern = max((k for k in prof if k in ("main_filter", "stagec_filter", "sort", "hull_chains")),
+    kern = max((k for k in prof if k in ("main_filter", "post", "sort", "hull_chains")),
                key=lambda k: prof[k][1])
     launches, tot = prof[kern]
     avg_s = tot / launches / 1e3
-    # main_filter streams every point once (8 bytes); stagec_filter streams them
-    # again in two-pass mode
-    algo = {"main_filter": 8.0 * n, "stagec_filter": 8.0 * n}.get(kern)
+    # main_filter streams every point once (8 bytes)
+    algo = {"main_filter": 8.0 * n}.get(kern)
     roof = None
     if algo is not None:
         achieved = algo / avg_s / 1e9

@@ -18,7 +18,7 @@ namespace ch {
 // Device information (SM count, resident blocks per SM of every kernel).
 struct DevInfo {
     int sms = 0;
-    int occ_main = 1, occ_c = 1, occ_lab = 1, occ_sort = 1, occ_chain = 1;
+    int occ_main = 1, occ_post = 1, occ_lab = 1, occ_sort = 1, occ_chain = 1;
 };
 
 static std::mutex g_mu;
@@ -32,11 +32,13 @@ static int device_info(int dev, DevInfo* out) {
     if (cudaDeviceGetAttribute(&di.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return CH_ECUDA;
     if (configure_hull_kernels() != cudaSuccess) return CH_ECUDA;
     if (configure_filter_kernels() != cudaSuccess) return CH_ECUDA;
-    if (occupancy_filter(&di.occ_main, &di.occ_c, &di.occ_lab) != cudaSuccess) return CH_ECUDA;
+    if (configure_post_kernel() != cudaSuccess) return CH_ECUDA;
+    if (occupancy_filter(&di.occ_main, &di.occ_lab) != cudaSuccess) return CH_ECUDA;
+    if (occupancy_post(&di.occ_post) != cudaSuccess) return CH_ECUDA;
     if (occupancy_sort(&di.occ_sort) != cudaSuccess) return CH_ECUDA;
     if (occupancy_chain(&di.occ_chain) != cudaSuccess) return CH_ECUDA;
     di.occ_main = std::max(1, di.occ_main);
-    di.occ_c = std::max(1, di.occ_c);
+    di.occ_post = std::max(1, di.occ_post);
     di.occ_lab = std::max(1, di.occ_lab);
     di.occ_sort = std::max(1, di.occ_sort);
     di.occ_chain = std::max(1, di.occ_chain);
@@ -237,21 +239,25 @@ static int enqueue_hull_direct(const float* pts, long long n, int32_t* out_idx, 
     const long long samples = sample_tiles_host(ntiles);
     const int grid_sample = (int)std::max<long long>(1, std::min<long long>(256, (samples + 7) / 8));
     const int grid_main = di.sms * di.occ_main;
-    const int grid_c = di.sms * di.occ_c;
+    const int grid_post = di.sms * di.occ_post;
     const int grid_sort = di.sms * di.occ_sort;
     const int grid_chain = di.sms * di.occ_chain;
-    // Raw survivors of the fused pass live in the B buffers until stage C
-    // has turned them into sort records in the A buffers.
+    // Raw survivors of the fused pass live in the B buffers until the post
+    // pass has turned them into sort records in the A buffers.
     uint64_t* raw_xy = vB;
     uint32_t* raw_idx = kB;
     const unsigned switch_at = (unsigned)std::max<long long>(1 << 16, n >> 5);
 
     { ProfScope p("init", s); launch_init(ctl, 0, s); }
     { ProfScope p("sample", s); launch_sample(pts, n, head, ntiles, ctl, grid_sample, s); }
-    { ProfScope p("main_filter", s); launch_main(pts, n, head, ntiles, ctl, raw_xy, raw_idx, switch_at, grid_main, s); }
-    { ProfScope p("tail", s); launch_tail(pts, n, head, ctl, raw_xy, raw_idx, kA, vA, 0, 1, out_idx, out_n, s); }
-    { ProfScope p("stagec_filter", s); launch_stagec(pts, n, head, ntiles, ctl, raw_xy, raw_idx, kA, vA, grid_c, s); }
-    { ProfScope p("tail", s); launch_tail(pts, n, head, ctl, raw_xy, raw_idx, kA, vA, 1, 1, out_idx, out_n, s); }
+    {
+        ProfScope p("main_filter", s);
+        launch_main(pts, n, head, ntiles, ctl, raw_xy, raw_idx, switch_at, kA, vA, grid_main, s);
+    }
+    {
+        ProfScope p("post", s);
+        launch_post(pts, n, head, ntiles, ctl, raw_xy, raw_idx, kA, vA, out_idx, out_n, grid_post, s);
+    }
     {
         ProfScope p("sort", s);
         launch_sort_pass(kA, vA, kB, vB, ctl, status, 0, grid_sort, s);
@@ -421,8 +427,10 @@ int ch_filter(const float* pts, int64_t n, int32_t* out_ext8, uint8_t* out_label
     uint32_t* kA = (uint32_t*)(base + L.off_kA);
     uint64_t* vA = (uint64_t*)(base + L.off_vA);
     { ProfScope p("init", s); launch_init(ctl, 1, s); }
-    { ProfScope p("main_filter", s); launch_main(pts, n, head, ntiles, ctl, nullptr, nullptr, 0xFFFFFFFFu, di.sms * di.occ_main, s); }
-    { ProfScope p("tail", s); launch_tail(pts, n, head, ctl, nullptr, nullptr, kA, vA, 0, 0, nullptr, nullptr, s); }
+    {
+        ProfScope p("main_filter", s);
+        launch_main(pts, n, head, ntiles, ctl, nullptr, nullptr, 0xFFFFFFFFu, kA, vA, di.sms * di.occ_main, s);
+    }
     if (out_labels || out_counts4) {
         ProfScope p("labels", s);
         launch_labels(pts, n, ctl, out_labels, di.sms * di.occ_lab, s);

@@ -99,8 +99,9 @@ struct Ctl {
 // Optional phase tracing of single-block kernels (debug builds with
 // -DCH_TRACE): thread 0 stamps %globaltimer and prints the deltas.
 #ifdef CH_TRACE
-#define CH_TRACE_DECL __shared__ unsigned long long s_trace_t[24]; __shared__ int s_trace_n; \
-    if (threadIdx.x == 0) s_trace_n = 0;
+__shared__ unsigned long long s_trace_t[24];
+__shared__ int s_trace_n;
+#define CH_TRACE_DECL if (threadIdx.x == 0) s_trace_n = 0;
 #define CH_TRACE_MARK() do { if (threadIdx.x == 0 && s_trace_n < 24) { unsigned long long _t; \
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(_t)); s_trace_t[s_trace_n++] = _t; } } while (0)
 #define CH_TRACE_PRINT(tag) do { if (threadIdx.x == 0) { printf("[trace %s]", tag); \
@@ -119,11 +120,20 @@ __device__ __forceinline__ long long orient64(long long ax, long long ay, long l
     return (bx - ax) * (py - ay) - (by - ay) * (px - ax);
 }
 
-__device__ __forceinline__ float4 ld_stream_f4(const float4* p) {
+// L2 policy for data read once per call (the input points): evicted first,
+// so streaming 100s of MB does not flush the workspace, the control block and
+// the kernels' code out of L2.
+__device__ __forceinline__ unsigned long long l2_evict_first() {
+    unsigned long long pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+__device__ __forceinline__ float4 ld_stream_f4(const float4* p, unsigned long long pol) {
     float4 r;
-    asm("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
         : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
-        : "l"(p));
+        : "l"(p), "l"(pol));
     return r;
 }
 
@@ -131,6 +141,19 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
+}
+
+// Last-arriver election: returns true in exactly one block, after every other
+// block of the grid has finished (and made its writes visible).
+__device__ __forceinline__ bool last_block(unsigned* counter, int* s_flag) {
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) *s_flag = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!*s_flag) return false;
+    __threadfence();
+    if (threadIdx.x == 0) *counter = 0u;
+    return true;
 }
 
 __device__ __forceinline__ void set_status(Ctl* ctl, int st) {

@@ -15,13 +15,9 @@
 //                   of two.  When the raw survivors grow past a threshold
 //                   (adversarial data such as points on a circle), the pass
 //                   stops filtering and the second pass does it (two-pass mode).
-//                   Its last block builds the octagon of the true extremes,
-//                   and when few raw survivors remain it re-classifies them,
-//                   and with few records left computes the hull itself.
-//   stagec_kernel   two-pass mode: the loop of Alg. 1/2 over every point
-//                   against the true octagon (findQueue by the quadrilateral
-//                   rule), or the re-classification of many raw survivors;
-//                   compaction into sort records (queue | u, v | index).
+//                   Its last block builds the octagon of the true extremes
+//                   and the records of the chain end points.
+//   (post.cu)       the classification of the survivors and the hull.
 //   labels_kernel   ch_filter: the label array Q of Alg. 2 (paper rule).
 #include "ch_internal.cuh"
 #include "hullcore.cuh"
@@ -82,19 +78,6 @@ __global__ void init_kernel(Ctl* ctl, int mode) {
     for (int i = t; i < kSortPasses * kDigits; i += blockDim.x) h[i] = 0u;
 }
 
-// Last-arriver election: returns true in exactly one block, after every other
-// block of the grid has finished (and made its writes visible).
-__device__ __forceinline__ bool last_block(unsigned* counter, int* s_flag) {
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) *s_flag = (atomicAdd(counter, 1u) == gridDim.x - 1);
-    __syncthreads();
-    if (!*s_flag) return false;
-    __threadfence();
-    if (threadIdx.x == 0) *counter = 0u;
-    return true;
-}
-
 // Warp tiles read by the sample pass: about 1/32 of the input, at most
 // kSampleTiles, at least min(ntiles, 64).
 __host__ __device__ __forceinline__ long long sample_tiles(long long ntiles) {
@@ -127,12 +110,13 @@ __global__ void __launch_bounds__(256) sample_kernel(const float* __restrict__ p
     for (int d = 0; d < 8; ++d) best[d] = 0ull;
     const long long nsamp = sample_tiles(ntiles);
     const float4* p4 = reinterpret_cast<const float4*>(pts + 2 * head);
+    const unsigned long long pol = l2_evict_first();
     for (long long k = gwarp; k < nsamp; k += nwarps) {
         const long long t = k * ntiles / nsamp;
         const float4* base = p4 + t * kWarpTileF4 + lane;
         float4 v[kLoadsPerLane];
 #pragma unroll
-        for (int j = 0; j < kLoadsPerLane; ++j) v[j] = ld_stream_f4(base + j * 32);
+        for (int j = 0; j < kLoadsPerLane; ++j) v[j] = ld_stream_f4(base + j * 32, pol);
 #pragma unroll
         for (int j = 0; j < kLoadsPerLane; ++j) {
             const int X0 = __float2int_rn(v[j].x), Y0 = __float2int_rn(v[j].y);
@@ -188,7 +172,7 @@ __global__ void __launch_bounds__(256) sample_kernel(const float* __restrict__ p
         return;
     }
     const int ext[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
-    setup_octagon_block(s_o, s_v[0], s_v[1], ext);
+    setup_octagon_block(s_o, s_v[0], s_v[1], ext, true);
     if (s_o.discard_none) {
         if (threadIdx.x == 0) ctl->mode = 1;
         return;
@@ -308,13 +292,20 @@ __device__ __forceinline__ unsigned emit_raw(unsigned keep, Get get, RawBuf& b, 
                                              uint64_t* raw_xy, uint32_t* raw_idx) {
     const int lane = threadIdx.x & 31;
     const unsigned c = __popc(keep);
-    unsigned incl = c;
+    unsigned incl, total;
+    if constexpr (kSlots == 1) {
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep != 0u);
+        incl = __popc(bal & lanemask_lt()) + c;
+        total = __popc(bal);
+    } else {
+        incl = c;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-        if (lane >= o) incl += t;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        total = __shfl_sync(0xFFFFFFFFu, incl, 31);
     }
-    const unsigned total = __shfl_sync(0xFFFFFFFFu, incl, 31);
     if (total == 0u) return 0u;
     unsigned after = 0u;
     if (cnt + total > (unsigned)kWarpBuf) after = flush_raw(b, cnt, ctl, raw_xy, raw_idx);
@@ -344,164 +335,14 @@ __device__ __forceinline__ unsigned emit_raw(unsigned keep, Get get, RawBuf& b, 
     return after;
 }
 
-// Survivors on an axis support line of the true octagon (x = xmin, y = ymin,
-// x = xmax, y = ymax) lie on a hull edge; only the two extreme ones per line
-// can be hull vertices.  They are reduced into ctl->line_ep (minimum and
-// maximum along the line, lowest index on ties) instead of becoming records;
-// emit_line_records turns the end points into records afterwards.
-// Warp-collective: every lane passes its candidate (valid = false for none);
-// the warp reduces per line first and issues one atomic pair per line.
-__device__ __forceinline__ bool reduce_on_line(const Octagon& o, bool valid, int X, int Y, unsigned idx, Ctl* ctl) {
-    bool on = false;
-#pragma unroll
-    for (int l = 0; l < 4; ++l) {
-        const bool hit = valid && ((l == 0) ? X == o.vx[W] : (l == 1) ? Y == o.vy[S] : (l == 2) ? X == o.vx[E] : Y == o.vy[N]);
-        on |= hit;
-        if (__any_sync(0xFFFFFFFFu, hit)) {
-            const unsigned along = (l & 1) ? (unsigned)X : (unsigned)Y;
-            unsigned long long mn = hit ? ((unsigned long long)along << 32) | idx : ~0ull;
-            unsigned long long mx = hit ? ((unsigned long long)along << 32) | (0xFFFFFFFFu - idx) : 0ull;
-#pragma unroll
-            for (int o2 = 16; o2; o2 >>= 1) {
-                const unsigned long long a = __shfl_xor_sync(0xFFFFFFFFu, mn, o2);
-                const unsigned long long b = __shfl_xor_sync(0xFFFFFFFFu, mx, o2);
-                mn = a < mn ? a : mn;
-                mx = b > mx ? b : mx;
-            }
-            if ((threadIdx.x & 31) == 0) {
-                atomicMin(&ctl->line_ep[2 * l], mn);
-                atomicMax(&ctl->line_ep[2 * l + 1], mx);
-            }
-        }
-    }
-    return on;
-}
-
-template <int kSlots, typename Get>
-__device__ __forceinline__ void emit_records(unsigned keep, unsigned long long regs, Get get, Ctl* ctl,
-                                             uint32_t* keys, uint64_t* vals, unsigned (*s_hist)[kDigits],
-                                             const Octagon* lines = nullptr) {
-    const int lane = threadIdx.x & 31;
-    if (lines) {   // divert support-line points to the end-point reduction (warp-collective)
-#pragma unroll
-        for (int s = 0; s < kSlots; ++s) {
-            const bool kept = (keep >> s) & 1u;
-            if (!__any_sync(0xFFFFFFFFu, kept)) continue;
-            long long idx = 0;
-            float x = 0.0f, y = 0.0f;
-            if (kept) get(s, idx, x, y);
-            if (reduce_on_line(*lines, kept, __float2int_rn(x), __float2int_rn(y), (unsigned)idx, ctl))
-                keep &= ~(1u << s);
-        }
-    }
-    const unsigned c = __popc(keep);
-    unsigned incl = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    const unsigned total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-    if (total == 0u) return;
-    unsigned base = 0u;
-    if (lane == 31) base = atomicAdd(&ctl->count, total);
-    base = __shfl_sync(0xFFFFFFFFu, base, 31);
-    unsigned pos = base + incl - c;
-#pragma unroll
-    for (int s = 0; s < kSlots; ++s) {
-        if ((keep >> s) & 1u) {
-            long long idx;
-            float x, y;
-            get(s, idx, x, y);
-            const int r = (int)((regs >> (2 * s)) & 3ull);
-            uint32_t u, v;
-            queue_frame(r, __float2int_rn(x), __float2int_rn(y), u, v);
-            const uint32_t key = make_key(r, u);
-            keys[pos] = key;
-            vals[pos] = make_val(v, (uint32_t)idx);
-            ++pos;
-#pragma unroll
-            for (int p = 0; p < kSortPasses; ++p)
-                atomicAdd(&s_hist[p][(key >> (p * kDigitBits)) & (kDigits - 1)], 1u);
-        }
-    }
-}
-
-__device__ __forceinline__ void flush_hist(unsigned (*s_hist)[kDigits], Ctl* ctl) {
-    __syncthreads();
-    for (int i = threadIdx.x; i < kSortPasses * kDigits; i += blockDim.x) {
-        const unsigned c = (&s_hist[0][0])[i];
-        if (c) atomicAdd(&(&ctl->digit_hist[0][0])[i], c);
-        (&s_hist[0][0])[i] = 0u;
-    }
-    __syncthreads();
-}
-
-// Hull-rule classification: -1 = dropped, else queue.
-__device__ __forceinline__ int classify_hull(float x, float y, const Octagon& o) {
-    const int X = __float2int_rn(x), Y = __float2int_rn(y);
-    if (in_inner(o, X, Y)) return -1;
-    return classify_hull_slow(x, y, &o);
-}
-
-// Re-classifies raw survivors [0, hi) against the true octagon into sort
-// records; thread `start` of `stride` cooperating threads, warp-uniform loop.
-__device__ void reclassify_raw(const uint64_t* raw_xy, const uint32_t* raw_idx, unsigned hi, unsigned stride,
-                               unsigned start, const Octagon& o, Ctl* ctl, uint32_t* keys, uint64_t* vals,
-                               unsigned (*s_hist)[kDigits]) {
-    const int lane = threadIdx.x & 31;
-    for (unsigned b = start - lane; b < hi; b += stride) {
-        const unsigned i = b + lane;
-        unsigned keep = 0u;
-        unsigned long long regs = 0ull;
-        float x = 0.0f, y = 0.0f;
-        unsigned idx = 0u;
-        if (i < hi) {
-            const unsigned long long xy = raw_xy[i];
-            x = (float)(unsigned)(xy >> 32);
-            y = (float)(unsigned)(xy & 0xFFFFFFFFull);
-            idx = raw_idx[i];
-            const int r = classify_hull(x, y, o);
-            if (r >= 0) { keep = 1u; regs = (unsigned long long)r; }
-        }
-        auto get = [&](int, long long& id, float& px, float& py) { id = idx; px = x; py = y; };
-        emit_records<1>(keep, regs, get, ctl, keys, vals, s_hist, &o);
-    }
-}
-
-// Records for the end points of the support-line survivors (one thread each).
-__device__ void emit_line_records(const Octagon& o, Ctl* ctl, uint32_t* keys, uint64_t* vals) {
-    const int t = threadIdx.x;
-    if (t >= 8) return;
-    const unsigned long long e = *(volatile unsigned long long*)&ctl->line_ep[t];
-    if ((t & 1) ? e == 0ull : e == ~0ull) return;   // no survivor on this line
-    const int l = t >> 1;
-    const int along = (int)(e >> 32);
-    const unsigned idx = (t & 1) ? 0xFFFFFFFFu - (unsigned)e : (unsigned)e;
-    int X, Y;
-    switch (l) {
-        case 0: X = o.vx[W]; Y = along; break;
-        case 1: X = along; Y = o.vy[S]; break;
-        case 2: X = o.vx[E]; Y = along; break;
-        default: X = along; Y = o.vy[N]; break;
-    }
-    const int r = classify_hull_slow((float)X, (float)Y, &o);
-    if (r < 0) return;   // cannot happen: it was a survivor
-    uint32_t u, v;
-    queue_frame(r, X, Y, u, v);
-    const uint32_t key = make_key(r, u);
-    const unsigned pos = atomicAdd(&ctl->count, 1u);
-    keys[pos] = key;
-    vals[pos] = make_val(v, idx);
-#pragma unroll
-    for (int p = 0; p < kSortPasses; ++p)
-        atomicAdd(&ctl->digit_hist[p][(key >> (p * kDigitBits)) & (kDigits - 1)], 1u);
-}
-
-// Finalize of the main pass (whole block): lowest-index tie-break, octagon of
-// the true extremes (-> s_o and ctl->oct), the 8 chain end-point records.
-__device__ void finalize_block(const float* __restrict__ pts, long long n, int head, Ctl* ctl, Octagon& s_o,
-                               uint32_t* keys, uint64_t* vals) {
+// Finalize of the main pass (whole block, the main pass's last block):
+// lowest-index tie-break, octagon of the true extremes (-> s_o and ctl->oct),
+// the chain end-point records.  The inner region of the true octagon is only
+// searched in two-pass mode, where it settles most points of the second pass;
+// raw survivors of the fused pass lie outside the sample octagon's inner
+// region, so for them it would almost never apply.
+__device__ __noinline__ void finalize_block(const float* __restrict__ pts, long long n, int head, Ctl* ctl,
+                                            Octagon& s_o, uint32_t* keys, uint64_t* vals) {
     __shared__ unsigned long long s_ext[8];
     __shared__ int s_G[8];
     __shared__ long long s_lo[8], s_hi[8];
@@ -519,6 +360,7 @@ __device__ void finalize_block(const float* __restrict__ pts, long long n, int h
         s_ext[d] = ~0ull;
     }
     __syncthreads();
+    CH_TRACE_MARK();
     // One round of independent loads for all 8 directions (a tile has at
     // most kWarpTilePts points; blockDim.x >= kWarpTilePts / 2).
     {
@@ -558,7 +400,9 @@ __device__ void finalize_block(const float* __restrict__ pts, long long n, int h
         s_vy[threadIdx.x] = __float2int_rn(pts[2 * i + 1]);
     }
     __syncthreads();
-    setup_octagon_block(s_o, s_vx, s_vy, s_id);
+    CH_TRACE_MARK();
+    setup_octagon_block(s_o, s_vx, s_vy, s_id, *(volatile int*)&ctl->mode != 0);
+    CH_TRACE_MARK();
     if (threadIdx.x < 12) {
         // Threads 0..7: chain end points (queue r runs from quad vertex r to
         // r+1).  Threads 8..11: the diagonal extreme of queue r, when it lies
@@ -594,57 +438,19 @@ __device__ void finalize_block(const float* __restrict__ pts, long long n, int h
     __syncthreads();
 }
 
-// Processes up to 32 queued lane tiles of a warp (one per lane): reloads the
-// lane tile's 16 points (just streamed, so served by L2) and keeps those not
-// strictly inside the inner region.  Entries are (warp tile << 5) | lane.
-// Warp-collective; returns emit_raw's count.
-__device__ __forceinline__ unsigned drain_queue(const float* __restrict__ pts, int head, unsigned* q, unsigned& qn,
-                                                const int* in, RawBuf& wbuf, unsigned& wcnt, Ctl* ctl,
-                                                uint64_t* raw_xy, uint32_t* raw_idx) {
-    const int lane = threadIdx.x & 31;
-    const unsigned take = qn < 32u ? qn : 32u;
-    float4 w[kLoadsPerLane];
-    unsigned keep = 0u;
-    long long i0 = 0;
-    if ((unsigned)lane < take) {
-        const unsigned e = q[lane];
-        const long long t = e >> 5;
-        const int ln = (int)(e & 31u);
-        const float4* base = reinterpret_cast<const float4*>(pts + 2 * head) + t * kWarpTileF4 + ln;
-#pragma unroll
-        for (int j = 0; j < kLoadsPerLane; ++j) w[j] = __ldcg(base + j * 32);
-#pragma unroll
-        for (int j = 0; j < kLoadsPerLane; ++j) {
-            if (!pt_in_inner(__float2int_rn(w[j].x), __float2int_rn(w[j].y), in)) keep |= 1u << (2 * j);
-            if (!pt_in_inner(__float2int_rn(w[j].z), __float2int_rn(w[j].w), in)) keep |= 2u << (2 * j);
-        }
-        i0 = head + 2 * (t * kWarpTileF4 + ln);
-    }
-    __syncwarp();
-    for (unsigned k = take + lane; k < qn; k += 32) q[k - take] = q[k];   // keep the rest
-    __syncwarp();
-    qn -= take;
-    auto get = [&](int s, long long& idx, float& x, float& y) {
-        const int j = s >> 1;
-        idx = i0 + 64 * j + (s & 1);
-        x = (s & 1) ? w[j].z : w[j].x;
-        y = (s & 1) ? w[j].w : w[j].y;
-    };
-    return emit_raw<2 * kLoadsPerLane>(keep, get, wbuf, wcnt, ctl, raw_xy, raw_idx);
-}
-
 constexpr size_t kMainSmemBytes = (size_t)8 * kStages * kWarpTileF4 * sizeof(float4);
 
 __global__ void __launch_bounds__(256, 2) main_kernel(const float* __restrict__ pts, long long n, int head,
                                                       long long ntiles, Ctl* ctl, uint64_t* raw_xy,
-                                                      uint32_t* raw_idx, unsigned switch_at) {
+                                                      uint32_t* raw_idx, unsigned switch_at, uint32_t* keys,
+                                                      uint64_t* vals) {
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ int s_inner[8];
     __shared__ unsigned long long s_red[8][8];
     __shared__ int s_mode;
     __shared__ RawBuf s_buf[8];
     __shared__ unsigned long long s_bar[8][kStages];
-    __shared__ unsigned s_q[8][64];
+    __shared__ unsigned char s_q[8][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -657,7 +463,6 @@ __global__ void __launch_bounds__(256, 2) main_kernel(const float* __restrict__ 
     bool filt = s_mode == 0;
     RawBuf& wbuf = s_buf[warp];
     unsigned wcnt = 0u;
-    unsigned qn = 0u;   // queued lane tiles of this warp (warp-uniform)
     Track tr;
     track_init(tr);
     // Scalar ranges (warp 0): the unaligned head point first and the ragged
@@ -711,21 +516,41 @@ __global__ void __launch_bounds__(256, 2) main_kernel(const float* __restrict__ 
             // Points strictly inside the inner region of the sample octagon
             // are strictly inside the hull; every other point is a raw
             // survivor, classified against the true octagon once its extremes
-            // are known.  Lanes whose 16 points are not all inside are queued
-            // and handled 32 at a time, one per lane, so outliers cost the
-            // warp a few instructions instead of a warp-wide slow path.
+            // are known.  The 16 points of each lane whose tile test failed
+            // are spread over the warp (two lane tiles per round) and tested
+            // one per lane from the ring slot, so an outlier costs the warp
+            // one round instead of a 16-point slow path on one lane.
             const bool inside = tile_in_inner(tk, s_inner);
             const unsigned fail = __ballot_sync(0xFFFFFFFFu, !inside);
             if (fail) {
-                if (!inside) s_q[warp][qn + __popc(fail & lanemask_lt())] = ((unsigned)t << 5) | (unsigned)lane;
-                qn += __popc(fail);
+                if (!inside) s_q[warp][__popc(fail & lanemask_lt())] = (unsigned char)lane;
                 __syncwarp();
-                if (qn >= 32u) {
-                    const unsigned upto = drain_queue(pts, head, s_q[warp], qn, s_inner, wbuf, wcnt, ctl, raw_xy, raw_idx);
-                    if (upto > switch_at) {   // dense data: leave filtering to the second pass
-                        if (lane == 0) atomicExch(&ctl->mode, 1);
-                        filt = false;
+                const unsigned slots = 16u * (unsigned)__popc(fail);
+                const float2* cur2 = reinterpret_cast<const float2*>(cur);
+                unsigned upto = 0u;
+                for (unsigned s0 = 0; s0 < slots; s0 += 32u) {
+                    const unsigned s = s0 + (unsigned)lane;
+                    unsigned keep = 0u;
+                    float x = 0.0f, y = 0.0f;
+                    long long idx = 0;
+                    if (s < slots) {
+                        // slot s: lane tile of rank s / 16, float4 (s / 2) % 8, half s % 2
+                        const int ln = s_q[warp][s >> 4];
+                        const int f2 = 2 * ((int)((s >> 1) & 7u) * 32 + ln) + (int)(s & 1u);
+                        const float2 v = cur2[f2];
+                        x = v.x;
+                        y = v.y;
+                        keep = pt_in_inner(__float2int_rn(x), __float2int_rn(y), s_inner) ? 0u : 1u;
+                        idx = head + t * kWarpTilePts + f2;
                     }
+                    auto get = [&](int, long long& id, float& px, float& py) { id = idx; px = x; py = y; };
+                    const unsigned a = emit_raw<1>(keep, get, wbuf, wcnt, ctl, raw_xy, raw_idx);
+                    upto = a > upto ? a : upto;
+                }
+                __syncwarp();
+                if (upto > switch_at) {   // dense data: leave filtering to the second pass
+                    if (lane == 0) atomicExch(&ctl->mode, 1);
+                    filt = false;
                 }
             }
             if ((k & 7) == 7) {
@@ -738,7 +563,6 @@ __global__ void __launch_bounds__(256, 2) main_kernel(const float* __restrict__ 
     }
     if (gwarp == 0 && head + ntiles * kWarpTilePts < n)
         scalar_range(head + ntiles * kWarpTilePts, n, (unsigned)(ntiles + 1));
-    while (qn > 0u) drain_queue(pts, head, s_q[warp], qn, s_inner, wbuf, wcnt, ctl, raw_xy, raw_idx);
     flush_raw(wbuf, wcnt, ctl, raw_xy, raw_idx);
 
     const bool err = tr.bad || (tr.orv >> kCoordBits) != 0u;
@@ -759,143 +583,15 @@ __global__ void __launch_bounds__(256, 2) main_kernel(const float* __restrict__ 
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = s_red[w][threadIdx.x] > m ? s_red[w][threadIdx.x] : m;
         if (m) atomicMax(&ctl->ext_packed[threadIdx.x], m);
     }
-
-}
-
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256, 3) stagec_kernel(const float* __restrict__ pts, long long n, int head,
-                                                        long long ntiles, Ctl* ctl, const uint64_t* raw_xy,
-                                                        const uint32_t* raw_idx, uint32_t* keys, uint64_t* vals) {
-    __shared__ Octagon s_o;
-    __shared__ unsigned s_hist[kSortPasses][kDigits];
-    if (*(volatile int*)&ctl->done || *(volatile int*)&ctl->records_ready) return;
-    const int mode = *(volatile int*)&ctl->mode;
-    copy_octagon(&s_o, &ctl->oct);
-    for (int i = threadIdx.x; i < kSortPasses * kDigits; i += blockDim.x) (&s_hist[0][0])[i] = 0u;
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    if (mode == 1) {   // second streaming pass over every point
-        const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-        const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-        const float4* p4 = reinterpret_cast<const float4*>(pts + 2 * head);
-        for (long long t = gwarp; t < ntiles; t += nwarps) {
-            const float4* base = p4 + t * kWarpTileF4 + lane;
-            float4 v[kLoadsPerLane];
-#pragma unroll
-            for (int j = 0; j < kLoadsPerLane; ++j) v[j] = ld_stream_f4(base + j * 32);
-            unsigned keep = 0u;
-            unsigned long long regs = 0ull;
-#pragma unroll
-            for (int j = 0; j < kLoadsPerLane; ++j) {
-                const int r0 = classify_hull(v[j].x, v[j].y, s_o);
-                const int r1 = classify_hull(v[j].z, v[j].w, s_o);
-                if (r0 >= 0) { keep |= 1u << (2 * j); regs |= (unsigned long long)r0 << (4 * j); }
-                if (r1 >= 0) { keep |= 1u << (2 * j + 1); regs |= (unsigned long long)r1 << (4 * j + 2); }
-            }
-            if (__any_sync(0xFFFFFFFFu, keep != 0u)) {
-                const long long i0 = head + 2 * (t * kWarpTileF4 + lane);
-                auto get = [&](int s, long long& idx, float& x, float& y) {
-                    const int j = s >> 1;
-                    idx = i0 + 64 * j + (s & 1);
-                    x = (s & 1) ? v[j].z : v[j].x;
-                    y = (s & 1) ? v[j].w : v[j].y;
-                };
-                emit_records<2 * kLoadsPerLane>(keep, regs, get, ctl, keys, vals, s_hist, &s_o);
-            }
-        }
-        if (gwarp == 0) {
-            const long long ranges[2][2] = {{0, head}, {head + ntiles * kWarpTilePts, n}};
-            for (int rg = 0; rg < 2; ++rg) {
-                for (long long b = ranges[rg][0]; b < ranges[rg][1]; b += 32) {
-                    const long long i = b + lane;
-                    unsigned keep = 0u;
-                    unsigned long long regs = 0ull;
-                    float x = 0.0f, y = 0.0f;
-                    if (i < ranges[rg][1]) {
-                        x = pts[2 * i]; y = pts[2 * i + 1];
-                        const int r = classify_hull(x, y, s_o);
-                        if (r >= 0) { keep = 1u; regs = (unsigned long long)r; }
-                    }
-                    auto get = [&](int, long long& idx, float& px, float& py) { idx = i; px = x; py = y; };
-                    emit_records<1>(keep, regs, get, ctl, keys, vals, s_hist, &s_o);
-                }
-            }
-        }
-    } else {   // many raw survivors of the fused pass: re-classify them
-        const unsigned nraw = *(volatile unsigned*)&ctl->count_raw;
-        reclassify_raw(raw_xy, raw_idx, nraw, gridDim.x * blockDim.x, blockIdx.x * blockDim.x + threadIdx.x,
-                       s_o, ctl, keys, vals, s_hist);
-    }
-    flush_hist(s_hist, ctl);
-}
-
-// ---------------------------------------------------------------------------
-// Single-block tail of a streaming pass.
-//   phase 0 (after main_kernel): octagon of the true extremes and the chain
-//     end-point records; in fused mode with few raw survivors, re-classify them
-//     here and, with few records, compute the hull (ctl->done).
-//   phase 1 (after stagec_kernel): support-line end-point records, then with
-//     few records compute the hull.
-// Data errors found by the streaming pass end the call here: out_n = status.
-constexpr int kTailThreads = 256;
-constexpr size_t kTailSmemBytes = kMidSmemBytes > sizeof(WrapSmem) ? kMidSmemBytes : sizeof(WrapSmem);
-
-__global__ void __launch_bounds__(kTailThreads) tail_kernel(const float* __restrict__ pts, long long n, int head, Ctl* ctl,
-                                                    const uint64_t* raw_xy, const uint32_t* raw_idx, uint32_t* keys,
-                                                    uint64_t* vals, int phase, int hull, int32_t* out_idx,
-                                                    int64_t* out_n) {
-    extern __shared__ __align__(16) char dyn[];
-    __shared__ Octagon s_o;
-    __shared__ unsigned s_hist[kSortPasses][kDigits];
+    // The block that finishes last builds the octagon of the true extremes.
+    // Every bulk copy of this block has completed (or was drained), so the
+    // ring's shared memory is free for it.
+    if (!last_block(&ctl->blocks_done[1], &s_mode)) return;
     CH_TRACE_DECL
     CH_TRACE_MARK();
-    if (*(volatile int*)&ctl->done) return;
-    if (read_status(ctl) != CH_OK) {
-        if (hull && threadIdx.x == 0) { *out_n = read_status(ctl); ctl->done = 1; }
-        return;
-    }
-    if (phase == 0) {
-        finalize_block(pts, n, head, ctl, s_o, keys, vals);
-        CH_TRACE_MARK();
-        if (read_status(ctl) != CH_OK) {
-            if (hull && threadIdx.x == 0) { *out_n = read_status(ctl); ctl->done = 1; }
-            return;
-        }
-        if (!hull) return;
-        const int mode = *(volatile int*)&ctl->mode;
-        const unsigned nraw = *(volatile unsigned*)&ctl->count_raw;
-        if (mode != 0 || nraw > kRawSmall) { CH_TRACE_PRINT("tail0-final"); return; }
-        for (int i = threadIdx.x; i < kSortPasses * kDigits; i += blockDim.x) (&s_hist[0][0])[i] = 0u;
-        __syncthreads();
-        reclassify_raw(raw_xy, raw_idx, nraw, blockDim.x, (unsigned)threadIdx.x, s_o, ctl, keys, vals, s_hist);
-        flush_hist(s_hist, ctl);
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) ctl->records_ready = 1;
-        CH_TRACE_MARK();
-    } else {
-        if (*(volatile int*)&ctl->records_ready) return;   // phase 0 produced every record
-        copy_octagon(&s_o, &ctl->oct);
-        __syncthreads();
-    }
-    emit_line_records(s_o, ctl, keys, vals);
-    __threadfence();
-    __syncthreads();
-    CH_TRACE_MARK();
-    const unsigned cnt = *(volatile unsigned*)&ctl->count;
-    if (cnt <= (unsigned)kMidCap) {
-        // Few records: gift wrapping (few chain vertices), else sort-based.
-        if (!wrap_hull(keys, vals, (int)cnt, n, ctl, out_idx, out_n, *reinterpret_cast<WrapSmem*>(dyn))) {
-            __syncthreads();
-            mid_hull(keys, vals, (int)cnt, pts, n, ctl, out_idx, out_n, dyn);
-        }
-        if (threadIdx.x == 0) ctl->done = 1;
-    }
-    CH_TRACE_MARK();
-#ifdef CH_TRACE
-    if (threadIdx.x == 0) printf("[tail phase %d] records %u raw %u\n", phase, cnt, ctl->count_raw);
-#endif
-    CH_TRACE_PRINT("tail");
+    if (__syncthreads_or(read_status(ctl) != CH_OK)) return;
+    finalize_block(pts, n, head, ctl, *reinterpret_cast<Octagon*>(dsm), keys, vals);
+    CH_TRACE_PRINT("finalize");
 }
 
 // ---------------------------------------------------------------------------
@@ -944,20 +640,8 @@ void launch_sample(const float* pts, long long n, int head, long long ntiles, Ct
 }
 
 void launch_main(const float* pts, long long n, int head, long long ntiles, Ctl* ctl, uint64_t* raw_xy,
-                 uint32_t* raw_idx, unsigned switch_at, int grid, cudaStream_t s) {
-    main_kernel<<<grid, 256, kMainSmemBytes, s>>>(pts, n, head, ntiles, ctl, raw_xy, raw_idx, switch_at);
-}
-
-void launch_tail(const float* pts, long long n, int head, Ctl* ctl, const uint64_t* raw_xy, const uint32_t* raw_idx,
-                 uint32_t* keys, uint64_t* vals, int phase, int hull, int32_t* out_idx, int64_t* out_n,
-                 cudaStream_t s) {
-    tail_kernel<<<1, kTailThreads, kTailSmemBytes, s>>>(pts, n, head, ctl, raw_xy, raw_idx, keys, vals, phase, hull,
-                                                        out_idx, out_n);
-}
-
-void launch_stagec(const float* pts, long long n, int head, long long ntiles, Ctl* ctl, const uint64_t* raw_xy,
-                   const uint32_t* raw_idx, uint32_t* keys, uint64_t* vals, int grid, cudaStream_t s) {
-    stagec_kernel<<<grid, 256, 0, s>>>(pts, n, head, ntiles, ctl, raw_xy, raw_idx, keys, vals);
+                 uint32_t* raw_idx, unsigned switch_at, uint32_t* keys, uint64_t* vals, int grid, cudaStream_t s) {
+    main_kernel<<<grid, 256, kMainSmemBytes, s>>>(pts, n, head, ntiles, ctl, raw_xy, raw_idx, switch_at, keys, vals);
 }
 
 void launch_labels(const float* pts, long long n, Ctl* ctl, uint8_t* labels, int grid, cudaStream_t s) {
@@ -971,15 +655,11 @@ void launch_filter_output(const Ctl* ctl, long long n, int32_t* out_ext8, int64_
 long long sample_tiles_host(long long ntiles) { return sample_tiles(ntiles); }
 
 cudaError_t configure_filter_kernels() {
-    cudaError_t e = cudaFuncSetAttribute(tail_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemBytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(main_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMainSmemBytes);
-    return e;
+    return cudaFuncSetAttribute(main_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMainSmemBytes);
 }
 
-cudaError_t occupancy_filter(int* main_k, int* stagec, int* labels) {
+cudaError_t occupancy_filter(int* main_k, int* labels) {
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(main_k, main_kernel, 256, kMainSmemBytes);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(stagec, stagec_kernel, 256, 0);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(labels, labels_kernel, 256, 0);
     return e;
 }

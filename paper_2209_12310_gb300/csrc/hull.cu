@@ -113,7 +113,12 @@ __global__ void __launch_bounds__(kChainThreads) chain_kernel(Ctl* ctl, HullBufs
     __shared__ int s_old;
     __shared__ unsigned s_qn[4], s_q0[5], s_tb[5];
 
-    if (*(volatile int*)&ctl->done || read_status(ctl) != CH_OK) return;
+    if (*(volatile int*)&ctl->done) return;
+    const int st0 = read_status(ctl);
+    if (st0 != CH_OK) {   // a sort pass gave up (timed-out wait): report it
+        if (blockIdx.x == 0 && threadIdx.x == 0) *hb.out_n = st0;
+        return;
+    }
     const int tid = threadIdx.x;
     // Queue boundaries in the sorted records: queue r holds the top-pass
     // digits [128 r, 128 (r + 1)), so its size is a sum of that histogram.

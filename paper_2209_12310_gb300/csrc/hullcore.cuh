@@ -368,15 +368,22 @@ static __device__ void mid_hull(const uint32_t* keys, const uint64_t* vals, int 
 }
 
 // ---------------------------------------------------------------------------
-// Gift wrapping of the queues (Jarvis march, Table I), one warp per queue:
-// from the queue's start extreme (minimum u), the next chain vertex is the
-// point of larger u seen at the smallest slope; on equal slopes the farthest
-// (collinear points are not vertices), on equal coordinates the lowest index
-// (the representative of duplicates).  Each step is a warp argmin; it stops at
-// the end extreme (maximum u).  Steps = chain vertices, so it suits the few
-// vertices that remain after filtering; more than kWrapCap vertices in a queue
-// abandons it (the caller falls back to the sort-based path).
-constexpr int kWrapCap = 512;
+// Quickhull rounds over the four queue chains at once (quickhull is among the
+// sequential algorithms of Table I; here every segment of every queue is
+// refined in the same round, so the rounds grow with the logarithm of the
+// chain length rather than with the vertex count).
+//
+// In queue r's frame the chain is the lower convex chain from S (minimum u,
+// then v, then index) to E (maximum u, then minimum v, then index).  A segment
+// a -> b of consecutive chain vertices owns the records with a.u < u < b.u.
+// Each round every segment takes the record farthest below it,
+// d = (b.v - a.v)(u - a.u) - (b.u - a.u)(v - a.v) > 0 largest, as a new vertex
+// between a and b; among records at that distance (a line parallel to a -> b)
+// the smallest u, then the lowest index: an end point of that line, hence a
+// vertex.  Records on or above their segment are dropped: they are no strict
+// vertices.  The round ends the process when no segment owns a record.
+constexpr int kQhCap = 1024;     // chain vertices of all four queues
+constexpr int kQhRounds = 64;
 
 // Inverse of queue_frame.
 __device__ __forceinline__ void frame_to_xy(int r, int u, int v, int& x, int& y) {
@@ -389,130 +396,188 @@ __device__ __forceinline__ void frame_to_xy(int r, int u, int v, int& x, int& y)
     }
 }
 
-// "a is a better next vertex than b" seen from p (both of larger u than p).
-__device__ __forceinline__ bool wrap_better(int pu, int pv, int au, int av, int ai, int bu, int bv, int bi) {
-    const long long c = (long long)(au - pu) * (bv - pv) - (long long)(av - pv) * (bu - pu);
-    if (c != 0) return c > 0;
-    if (au != bu) return au > bu;
-    if (av != bv) return av < bv;
-    return ai < bi;
-}
-
-// Shared memory of wrap_hull (dynamic, placed by the caller).
-struct WrapSmem {
-    int qu[kMidCap], qv[kMidCap], qi[kMidCap];   // records grouped by queue
-    int cu[4][kWrapCap], cv[4][kWrapCap], ci[4][kWrapCap];   // queue chains
+// Shared memory of the small hull (dynamic, placed by the caller).  After the
+// rounds the record arrays hold the joined cycle (x, y, index) and the output.
+struct QhSmem {
+    int ru[kMidCap], rv[kMidCap], ri[kMidCap];   // records: u, v, index
+    int rs[kMidCap];                             // queue (on entry), then segment (left vertex), -1 dropped
+    unsigned long long segmax[kQhCap], segarg[kQhCap];
+    int vu[kQhCap], vv[kQhCap], vi[kQhCap], vnext[kQhCap];
+    int splitu[kQhCap], child[kQhCap];
 };
 
-// Returns false (nothing written) when a queue has more than kWrapCap chain
-// vertices.  Needs blockDim.x >= 128; m <= kMidCap.
-static __device__ bool wrap_hull(const uint32_t* keys, const uint64_t* vals, int m, long long n, Ctl* ctl,
-                                 int32_t* out_idx, int64_t* out_n, WrapSmem& sm) {
-    __shared__ int s_cnt[4], s_base[5], s_len[4], s_fail;
-    __shared__ int s_V[2 * kWrapCap], s_X[2 * kWrapCap], s_Y[2 * kWrapCap];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid < 4) s_cnt[tid] = 0;
-    if (tid == 0) s_fail = 0;
+__device__ __forceinline__ long long qh_depth(const QhSmem& q, int a, int b, int u, int v) {
+    return (long long)(q.vv[b] - q.vv[a]) * (u - q.vu[a]) - (long long)(q.vu[b] - q.vu[a]) * (v - q.vv[a]);
+}
+
+// The four chains; on success the joined cycle (every chain without its end
+// vertex, which starts the next chain) is in q.ru / q.rv / q.ri as x, y,
+// index, and its length in *mv.  False when a limit is exceeded (the caller
+// falls back to the sort-based path).  Whole block; m records in q.
+static __device__ bool qh_chains(QhSmem& q, int m, int* mv) {
+    __shared__ unsigned long long s_s[4], s_e[4];
+    __shared__ int s_si[4], s_ei[4], s_len[4], s_nvert, s_changed, s_fail;
+    const int tid = threadIdx.x, T = blockDim.x;
+    constexpr int kVBits = kKeyBits;   // v < 2^25 in every frame
+    constexpr unsigned long long kVMask = (1ull << kVBits) - 1ull;
+    if (tid < 4) { s_s[tid] = ~0ull; s_e[tid] = 0ull; s_si[tid] = INT_MAX; s_ei[tid] = INT_MAX; }
+    if (tid == 0) { s_nvert = 8; s_fail = 0; s_changed = 0; }
+    for (int a = tid; a < kQhCap; a += T) { q.segmax[a] = 0ull; q.segarg[a] = ~0ull; q.splitu[a] = -1; }
     __syncthreads();
-    for (int i = tid; i < m; i += blockDim.x) atomicAdd(&s_cnt[keys[i] >> kKeyBits], 1);
-    __syncthreads();
-    if (tid == 0) {
-        s_base[0] = 0;
-        for (int r = 0; r < 4; ++r) s_base[r + 1] = s_base[r] + s_cnt[r];
-        for (int r = 0; r < 4; ++r) s_cnt[r] = s_base[r];
+    // S = minimum (u, v); E = maximum u, then minimum v; then lowest indices
+    for (int i = tid; i < m; i += T) {
+        const int r = q.rs[i];
+        const unsigned long long ks = ((unsigned long long)q.ru[i] << kVBits) | (unsigned)q.rv[i];
+        const unsigned long long ke = ((unsigned long long)q.ru[i] << kVBits) | (kVMask - (unsigned)q.rv[i]);
+        if (ks < *(volatile unsigned long long*)&s_s[r]) atomicMin(&s_s[r], ks);
+        if (ke > *(volatile unsigned long long*)&s_e[r]) atomicMax(&s_e[r], ke);
     }
     __syncthreads();
-    for (int i = tid; i < m; i += blockDim.x) {
-        const uint32_t k = keys[i];
-        const uint64_t w = vals[i];
-        const int pos = atomicAdd(&s_cnt[k >> kKeyBits], 1);
-        sm.qu[pos] = (int)(k & kKeyMask);
-        sm.qv[pos] = (int)(w >> 31);
-        sm.qi[pos] = (int)(w & 0x7FFFFFFFull);
+    for (int i = tid; i < m; i += T) {
+        const int r = q.rs[i];
+        const unsigned long long ks = ((unsigned long long)q.ru[i] << kVBits) | (unsigned)q.rv[i];
+        const unsigned long long ke = ((unsigned long long)q.ru[i] << kVBits) | (kVMask - (unsigned)q.rv[i]);
+        if (ks == s_s[r]) atomicMin(&s_si[r], q.ri[i]);
+        if (ke == s_e[r]) atomicMin(&s_ei[r], q.ri[i]);
     }
     __syncthreads();
-    if (warp < 4) {
-        const int r = warp, a = s_base[r], b = s_base[r + 1];
-        // start: minimum u (then v, index); end: maximum u
-        int su = INT_MAX, sv = INT_MAX, si = INT_MAX, eu = -1;
-        for (int i = a + lane; i < b; i += 32) {
-            const int u = sm.qu[i], v = sm.qv[i], id = sm.qi[i];
-            if (u < su || (u == su && (v < sv || (v == sv && id < si)))) { su = u; sv = v; si = id; }
-            eu = max(eu, sm.qu[i]);
-        }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            const int ou = __shfl_xor_sync(0xFFFFFFFFu, su, o), ov = __shfl_xor_sync(0xFFFFFFFFu, sv, o);
-            const int oi = __shfl_xor_sync(0xFFFFFFFFu, si, o);
-            if (ou < su || (ou == su && (ov < sv || (ov == sv && oi < si)))) { su = ou; sv = ov; si = oi; }
-            eu = max(eu, __shfl_xor_sync(0xFFFFFFFFu, eu, o));
-        }
-        int len = 0;
-        int pu = su, pv = sv, pi = si;
-        if (lane == 0) { sm.cu[r][0] = pu; sm.cv[r][0] = pv; sm.ci[r][0] = pi; }
-        len = 1;
-        while (pu < eu) {
-            int bu = -1, bv = 0, bi = 0;
-            for (int i = a + lane; i < b; i += 32) {
-                const int u = sm.qu[i];
-                if (u <= pu) continue;
-                const int v = sm.qv[i], id = sm.qi[i];
-                if (bu < 0 || wrap_better(pu, pv, u, v, id, bu, bv, bi)) { bu = u; bv = v; bi = id; }
-            }
-#pragma unroll
-            for (int o = 16; o; o >>= 1) {
-                const int ou = __shfl_xor_sync(0xFFFFFFFFu, bu, o), ov = __shfl_xor_sync(0xFFFFFFFFu, bv, o);
-                const int oi = __shfl_xor_sync(0xFFFFFFFFu, bi, o);
-                if (ou >= 0 && (bu < 0 || wrap_better(pu, pv, ou, ov, oi, bu, bv, bi))) { bu = ou; bv = ov; bi = oi; }
-            }
-            if (bu < 0 || len >= kWrapCap) { len = -1; break; }   // too many vertices (or inconsistent)
-            pu = bu; pv = bv; pi = bi;
-            if (lane == 0) { sm.cu[r][len] = pu; sm.cv[r][len] = pv; sm.ci[r][len] = pi; }
-            ++len;
-        }
-        if (lane == 0) {
-            s_len[r] = len;
-            if (len < 0) s_fail = 1;
-        }
+    if (tid < 4) {
+        const int r = tid;
+        if (s_si[r] == INT_MAX || s_ei[r] == INT_MAX) s_fail = 1;   // empty queue: cannot happen
+        q.vu[2 * r] = (int)(s_s[r] >> kVBits);
+        q.vv[2 * r] = (int)(s_s[r] & kVMask);
+        q.vi[2 * r] = s_si[r];
+        q.vu[2 * r + 1] = (int)(s_e[r] >> kVBits);
+        q.vv[2 * r + 1] = (int)(kVMask - (s_e[r] & kVMask));
+        q.vi[2 * r + 1] = s_ei[r];
+        q.vnext[2 * r] = q.vu[2 * r] < q.vu[2 * r + 1] ? 2 * r + 1 : -1;   // S == E: a one-point chain
+        q.vnext[2 * r + 1] = -1;
     }
     __syncthreads();
     if (s_fail) return false;
+    for (int i = tid; i < m; i += T) {
+        const int r = q.rs[i], u = q.ru[i];
+        q.rs[i] = (q.vu[2 * r] < u && u < q.vu[2 * r + 1]) ? 2 * r : -1;
+    }
+    for (int round = 0;; ++round) {
+        const int nv = s_nvert;
+        // depths; each segment's maximum
+        for (int i = tid; i < m; i += T) {
+            int a = q.rs[i];
+            if (a < 0) continue;
+            const int u = q.ru[i], v = q.rv[i];
+            const int su = q.splitu[a];
+            if (su >= 0) {   // split last round: stay left of the new vertex, or move right of it
+                if (u > su) a = q.child[a];
+                else if (u == su) a = -1;
+            }
+            const int b = a >= 0 ? q.vnext[a] : -1;
+            if (b < 0) {
+                a = -1;   // (a segment always has a right end; defensive)
+            } else {
+                const long long d = qh_depth(q, a, b, u, v);
+                if (d <= 0) a = -1;
+                else if ((unsigned long long)d > *(volatile unsigned long long*)&q.segmax[a])
+                    atomicMax(&q.segmax[a], (unsigned long long)d);
+            }
+            q.rs[i] = a;
+        }
+        __syncthreads();
+        if (tid == 0) s_changed = 0;
+        // the deepest record per segment: smallest u, then index
+        for (int i = tid; i < m; i += T) {
+            const int a = q.rs[i];
+            if (a < 0) continue;
+            const int u = q.ru[i];
+            const long long d = qh_depth(q, a, q.vnext[a], u, q.rv[i]);
+            if ((unsigned long long)d == q.segmax[a])
+                atomicMin(&q.segarg[a], ((unsigned long long)u << 31) | (unsigned)q.ri[i]);
+        }
+        __syncthreads();
+        // insert the new vertices
+        for (int a = tid; a < nv; a += T) {
+            q.splitu[a] = -1;
+            const unsigned long long dm = q.segmax[a];
+            if (dm == 0ull) continue;
+            const int b = q.vnext[a];
+            const unsigned long long key = q.segarg[a];
+            const int fu = (int)(key >> 31), fi = (int)(key & 0x7FFFFFFFull);
+            // v from the depth: exact (the quotient of an exact integer identity)
+            const long long num = (long long)(q.vv[b] - q.vv[a]) * (fu - q.vu[a]) - (long long)dm;
+            const int fv = q.vv[a] + (int)(num / (long long)(q.vu[b] - q.vu[a]));
+            const int f = atomicAdd(&s_nvert, 1);
+            if (f < kQhCap) {
+                q.vu[f] = fu;
+                q.vv[f] = fv;
+                q.vi[f] = fi;
+                q.vnext[f] = b;
+                q.vnext[a] = f;
+                q.child[a] = f;
+                q.splitu[a] = fu;
+            } else {
+                s_fail = 1;
+            }
+            q.segmax[a] = 0ull;
+            q.segarg[a] = ~0ull;
+            s_changed = 1;
+        }
+        __syncthreads();
+        if (s_fail || (s_changed && round + 1 >= kQhRounds)) return false;
+        if (!s_changed) break;
+    }
+    // chain lengths, then the joined cycle (chain r without its end vertex)
+    if (tid < 4) {
+        int len = 0;
+        for (int a = 2 * tid; a >= 0 && len <= kQhCap; a = q.vnext[a]) ++len;
+        s_len[tid] = len;
+    }
+    __syncthreads();
     int off[5];
     off[0] = 0;
-    for (int r = 0; r < 4; ++r) off[r + 1] = off[r] + s_len[r] - 1;
-    const int mv = off[4];
-    if (mv > 2 * kWrapCap) return false;
-    for (int r = 0; r < 4; ++r)
-        for (int j = tid; j < s_len[r] - 1; j += blockDim.x) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) off[r + 1] = off[r] + max(s_len[r] - 1, 0);
+    if (tid < 4) {
+        const int r = tid;
+        int pos = off[r];
+        for (int a = 2 * r; a >= 0 && pos < off[r + 1]; a = q.vnext[a], ++pos) {
             int x, y;
-            frame_to_xy(r, sm.cu[r][j], sm.cv[r][j], x, y);
-            s_V[off[r] + j] = sm.ci[r][j];
-            s_X[off[r] + j] = x;
-            s_Y[off[r] + j] = y;
+            frame_to_xy(r, q.vu[a], q.vv[a], x, y);
+            q.ru[pos] = x;
+            q.rv[pos] = y;
+            q.ri[pos] = q.vi[a];
         }
+    }
     __syncthreads();
-    if (warp != 0) return true;
-    // ---- stitch on one warp ----
+    *mv = off[4];
+    return true;
+}
+
+// Joins the cycle (x, y, index in X, Y, V; mv points) into the output: the
+// strictly convex vertices, counter-clockwise from the lexicographically
+// smallest; a degenerate cycle gives [lex-min, lex-max] (or one point).  One
+// warp (warp 0) works; tmp holds mv ints.
+static __device__ void stitch_cycle(const int* X, const int* Y, const int* V, int mv, int* tmp, Ctl* ctl,
+                                    long long n, int32_t* out_idx, int64_t* out_n) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp != 0) return;
     if (mv == 0) {   // all four quadrilateral vertices coincide
         if (lane == 0) { out_idx[0] = ctl->oct.ext[W]; *out_n = 1; }
-        return true;
+        return;
     }
     int npos = 0, nneg = 0;
     for (int i = lane; i < mv; i += 32) {
-        const int p = (i + mv - 1) % mv, q = (i + 1) % mv;
-        const long long tr = orient64(s_X[p], s_Y[p], s_X[i], s_Y[i], s_X[q], s_Y[q]);
+        const int p = i == 0 ? mv - 1 : i - 1, q = i + 1 == mv ? 0 : i + 1;
+        const long long tr = orient64(X[p], Y[p], X[i], Y[i], X[q], Y[q]);
         npos += tr > 0;
         nneg += tr < 0;
+        tmp[i] = tr > 0;
     }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-        npos += __shfl_xor_sync(0xFFFFFFFFu, npos, o);
-        nneg += __shfl_xor_sync(0xFFFFFFFFu, nneg, o);
-    }
+    npos = __reduce_add_sync(0xFFFFFFFFu, (unsigned)npos);
+    nneg = __reduce_add_sync(0xFFFFFFFFu, (unsigned)nneg);
     if (npos == 0) {   // degenerate: [lex-min, lex-max], lowest index per coordinate
         unsigned long long lo = ~0ull, hi = 0ull;
         for (int i = lane; i < mv; i += 32) {
-            const unsigned long long kxy = xy_key(s_X[i], s_Y[i]);
+            const unsigned long long kxy = xy_key(X[i], Y[i]);
             lo = kxy < lo ? kxy : lo;
             hi = kxy > hi ? kxy : hi;
         }
@@ -522,23 +587,20 @@ static __device__ bool wrap_hull(const uint32_t* keys, const uint64_t* vals, int
             lo = a2 < lo ? a2 : lo;
             hi = b2 > hi ? b2 : hi;
         }
-        int ilo = INT_MAX, ihi = INT_MAX;
+        unsigned ilo = 0xFFFFFFFFu, ihi = 0xFFFFFFFFu;
         for (int i = lane; i < mv; i += 32) {
-            const unsigned long long kxy = xy_key(s_X[i], s_Y[i]);
-            if (kxy == lo) ilo = min(ilo, s_V[i]);
-            if (kxy == hi) ihi = min(ihi, s_V[i]);
+            const unsigned long long kxy = xy_key(X[i], Y[i]);
+            if (kxy == lo) ilo = min(ilo, (unsigned)V[i]);
+            if (kxy == hi) ihi = min(ihi, (unsigned)V[i]);
         }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            ilo = min(ilo, __shfl_xor_sync(0xFFFFFFFFu, ilo, o));
-            ihi = min(ihi, __shfl_xor_sync(0xFFFFFFFFu, ihi, o));
-        }
+        ilo = __reduce_min_sync(0xFFFFFFFFu, ilo);
+        ihi = __reduce_min_sync(0xFFFFFFFFu, ihi);
         if (lane == 0) {
-            out_idx[0] = ilo;
+            out_idx[0] = (int)ilo;
             if (lo == hi) *out_n = 1;
-            else { out_idx[1] = ihi; *out_n = 2; }
+            else { out_idx[1] = (int)ihi; *out_n = 2; }
         }
-        return true;
+        return;
     }
     if (nneg != 0 && lane == 0) set_status(ctl, CH_ECUDA);   // internal consistency check
     // strictly convex vertices in order, the lexicographically smallest first
@@ -546,37 +608,33 @@ static __device__ bool wrap_hull(const uint32_t* keys, const uint64_t* vals, int
     unsigned long long best = ~0ull;
     for (int base = 0; base < mv; base += 32) {
         const int i = base + lane;
-        bool f = false;
-        if (i < mv) {
-            const int p = (i + mv - 1) % mv, q = (i + 1) % mv;
-            f = orient64(s_X[p], s_Y[p], s_X[i], s_Y[i], s_X[q], s_Y[q]) > 0;
-        }
+        const bool f = i < mv && tmp[i] != 0;
         const unsigned bal = __ballot_sync(0xFFFFFFFFu, f);
+        __syncwarp();
         if (f) {
             const int pos = h + __popc(bal & lanemask_lt());
-            const unsigned long long kxy = (xy_key(s_X[i], s_Y[i]) << 16) | (unsigned)pos;
+            const unsigned long long kxy = (xy_key(X[i], Y[i]) << 16) | (unsigned)pos;
             best = kxy < best ? kxy : best;
-            sm.qu[pos] = s_V[i];   // reuse the record buffer for the output order
+            tmp[pos] = V[i];   // pos <= i: entries still to be read are not overwritten
         }
         h += __popc(bal);
+        __syncwarp();
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
         const unsigned long long a2 = __shfl_xor_sync(0xFFFFFFFFu, best, o);
         best = a2 < best ? a2 : best;
     }
-    __syncwarp();
     if (h > n) {
         if (lane == 0) { set_status(ctl, CH_ECUDA); *out_n = CH_ECUDA; }
-        return true;
+        return;
     }
     const int start = (int)(best & 0xFFFFull);
-    for (int j = lane; j < h; j += 32) out_idx[j] = sm.qu[(start + j) % h];
-    if (lane == 0) {
-        const int st = read_status(ctl);
-        *out_n = (st == CH_OK) ? h : st;
+    for (int j = lane; j < h; j += 32) {
+        const int k = start + j;
+        out_idx[j] = tmp[k < h ? k : k - h];
     }
-    return true;
+    if (lane == 0) *out_n = nneg != 0 ? (int64_t)CH_ECUDA : (int64_t)h;
 }
 
 }  // namespace ch

@@ -12,12 +12,10 @@ struct Ctl;
 void launch_init(Ctl* ctl, int mode, cudaStream_t s);
 void launch_sample(const float* pts, long long n, int head, long long ntiles, Ctl* ctl, int grid, cudaStream_t s);
 void launch_main(const float* pts, long long n, int head, long long ntiles, Ctl* ctl, uint64_t* raw_xy,
-                 uint32_t* raw_idx, unsigned switch_at, int grid, cudaStream_t s);
-void launch_tail(const float* pts, long long n, int head, Ctl* ctl, const uint64_t* raw_xy, const uint32_t* raw_idx,
-                 uint32_t* keys, uint64_t* vals, int phase, int hull, int32_t* out_idx, int64_t* out_n,
-                 cudaStream_t s);
-void launch_stagec(const float* pts, long long n, int head, long long ntiles, Ctl* ctl, const uint64_t* raw_xy,
-                   const uint32_t* raw_idx, uint32_t* keys, uint64_t* vals, int grid, cudaStream_t s);
+                 uint32_t* raw_idx, unsigned switch_at, uint32_t* keys, uint64_t* vals, int grid, cudaStream_t s);
+void launch_post(const float* pts, long long n, int head, long long ntiles, Ctl* ctl, const uint64_t* raw_xy,
+                 const uint32_t* raw_idx, uint32_t* keys, uint64_t* vals, int32_t* out_idx, int64_t* out_n,
+                 int grid, cudaStream_t s);
 void launch_labels(const float* pts, long long n, Ctl* ctl, uint8_t* labels, int grid, cudaStream_t s);
 void launch_filter_output(const Ctl* ctl, long long n, int32_t* out_ext8, int64_t* out_counts4, cudaStream_t s);
 
@@ -30,10 +28,12 @@ void launch_chain(Ctl* ctl, const uint32_t* keys, const uint64_t* vals, int* cu,
 size_t chain_smem_bytes();
 cudaError_t configure_hull_kernels();
 cudaError_t configure_filter_kernels();
+cudaError_t configure_post_kernel();
 long long sample_tiles_host(long long ntiles);
 
 // Occupancy (resident blocks per SM at each kernel's launch shape).
-cudaError_t occupancy_filter(int* main_k, int* stagec, int* labels);
+cudaError_t occupancy_filter(int* main_k, int* labels);
+cudaError_t occupancy_post(int* post);
 cudaError_t occupancy_sort(int* sort);
 cudaError_t occupancy_chain(int* chain);
 

@@ -164,72 +164,56 @@ __device__ __forceinline__ bool inner_fits(const Octagon& o, const int lo[4], co
 }
 
 // Fills every field of o (in shared memory) from the 8 vertices.  The whole
-// block calls it (all threads, same arguments); thread 0 writes the scalar
-// fields and the threads search the inner region's scale t/1024 in parallel.
-static __device__ void setup_octagon_block(Octagon& o, const int vx[8], const int vy[8], const int ext[8]) {
+// block calls it (all threads, same arguments; blockDim.x >= 12).  Threads
+// 0..7 build the edges, 8..11 the quadrilateral; with with_inner, the threads
+// then search the inner region's scale t/1024 in parallel: each thread checks
+// one coarse scale, then the scales between the best coarse one and the next.
+// Without it the inner region is empty (every test takes the exact path).
+static __device__ void setup_octagon_block(Octagon& o, const int vx[8], const int vy[8], const int ext[8],
+                                           bool with_inner) {
     __shared__ int s_best;
-    if (threadIdx.x == 0) {
-        long long area2 = 0;
-        for (int d = 0; d < 8; ++d) {
-            o.vx[d] = vx[d];
-            o.vy[d] = vy[d];
-            o.ext[d] = ext[d];
-        }
-        for (int k = 0; k < 8; ++k) {
-            const int j = (k + 1) & 7;
-            area2 += (long long)vx[k] * vy[j] - (long long)vx[j] * vy[k];
-            o.oct[k] = make_edge(vx[k], vy[k], vx[j], vy[j]);
-        }
-        for (int r = 0; r < 4; ++r) {
-            const int a = 2 * r, b = (2 * r + 2) & 7;
-            o.quad[r] = make_edge(vx[a], vy[a], vx[b], vy[b]);
-        }
-        o.discard_none = (area2 == 0);
-        s_best = 0;
+    __shared__ long long s_area[8];
+    const int tid = (int)threadIdx.x;
+    if (tid < 8) {
+        const int j = (tid + 1) & 7;
+        o.vx[tid] = vx[tid];
+        o.vy[tid] = vy[tid];
+        o.ext[tid] = ext[tid];
+        o.oct[tid] = make_edge(vx[tid], vy[tid], vx[j], vy[j]);
+        s_area[tid] = (long long)vx[tid] * vy[j] - (long long)vx[j] * vy[tid];
+    } else if (tid < 12) {
+        const int r = tid - 8, a = 2 * r, b = (2 * r + 2) & 7;
+        o.quad[r] = make_edge(vx[a], vy[a], vx[b], vy[b]);
     }
+    if (tid == 0) s_best = 0;
     __syncthreads();
+    long long area2 = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) area2 += s_area[k];
+    const bool none = area2 == 0;
     // 8-direction bounds of the octagon's vertices: x, y, x+y, x-y (biased).
     const int lo0[4] = {vx[W], vy[S], vx[SW] + vy[SW], vx[NW] - vy[NW] + kCoordLimit};
     const int hi0[4] = {vx[E], vy[N], vx[NE] + vy[NE], vx[SE] - vy[SE] + kCoordLimit};
-    if (!o.discard_none) {
-        // Each warp tests one scale per round (its lanes split the 8 x 8
-        // candidate/edge checks); rounds refine the step by the warp count.
-        const int nw = (int)(blockDim.x >> 5), warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
-        int step = 1024 / nw;
-        if (step < 1) step = 1;
-        int base = 0;
-        for (;;) {
-            const int t = base + step * (warp + 1);
-            bool ok = t <= 1024;
-            if (ok) {
-                int lo[4], hi[4];
-                inner_bounds(lo0, hi0, t, lo, hi);
-                ok = !(lo[0] > hi[0] || lo[1] > hi[1] || lo[2] > hi[2] || lo[3] > hi[3]);
-                if (ok) {
-                    const long long xl = lo[0], xh = hi[0], yl = lo[1], yh = hi[1];
-                    const long long sl = lo[2], sh = hi[2], dl = lo[3] - kCoordLimit, dh = hi[3] - kCoordLimit;
-                    const long long px[8] = {xl, sl - yl, dh + yl, xh, xh, sh - yh, dl + yh, xl};
-                    const long long py[8] = {sl - xl, yl, yl, xh - dh, sh - xh, yh, yh, xl - dl};
-                    bool mine = true;
-                    for (int pair = lane; pair < 64; pair += 32) {   // (candidate, edge)
-                        const Edge& e = o.oct[pair & 7];
-                        const int c = pair >> 3;
-                        if ((e.dx | e.dy) != 0 && edge_exact(e, px[c], py[c]) < 0) mine = false;
-                    }
-                    ok = __all_sync(0xFFFFFFFFu, mine);
-                }
-            }
-            if (ok && lane == 0) atomicMax(&s_best, t);
-            __syncthreads();
-            if (step == 1) break;
-            base = s_best;
-            step = step / nw > 0 ? step / nw : 1;
-            __syncthreads();
+    if (with_inner && !none) {
+        const int nthr = (int)blockDim.x;
+        const int step = (1024 + nthr - 1) / nthr;
+        int lo[4], hi[4];
+        const int tc = step * (tid + 1);
+        if (tc <= 1024) {
+            inner_bounds(lo0, hi0, tc, lo, hi);
+            if (inner_fits(o, lo, hi)) atomicMax(&s_best, tc);
         }
+        __syncthreads();
+        const int tf = s_best + 1 + tid;
+        if (tid < step - 1 && tf <= 1024) {
+            inner_bounds(lo0, hi0, tf, lo, hi);
+            if (inner_fits(o, lo, hi)) atomicMax(&s_best, tf);
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const int t1 = s_best;
+    if (tid == 0) {
+        o.discard_none = none;
+        const int t1 = (with_inner && !none) ? s_best : 0;
         if (t1 > 0) {
             int lo[4], hi[4];
             inner_bounds(lo0, hi0, t1, lo, hi);

@@ -1,0 +1,337 @@
+// post.cu -- the loop of Alg. 1/2 after findExtremes, on the survivors.
+//
+// post_kernel classifies, against the octagon of the true extremes (hull
+// rule, findQueue by the quadrilateral rule), either the raw survivors of the
+// fused main pass or, in two-pass mode, every point; kept points become sort
+// records (queue | u, v | index).  The block that finishes last adds the
+// records of the support-line end points and, when the records are few,
+// computes the hull itself (quickhull rounds over the queues), so the
+// sort-based path that follows finds ctl->done set and exits at once.
+#include "ch_internal.cuh"
+#include "hullcore.cuh"
+#include "launch.h"
+#include "octagon.cuh"
+
+#include <climits>
+
+namespace ch {
+
+constexpr int kPostThreads = 512;
+static_assert(kPostThreads % 128 == 0, "mid_hull splits the block in four");
+
+// Hull-rule classification: -1 = dropped, else queue.
+__device__ __forceinline__ int classify_hull(float x, float y, const Octagon& o) {
+    const int X = __float2int_rn(x), Y = __float2int_rn(y);
+    if (in_inner(o, X, Y)) return -1;
+    return classify_hull_slow(x, y, &o);
+}
+
+// Survivors on an axis support line of the true octagon (x = xmin, y = ymin,
+// x = xmax, y = ymax) lie on a hull edge; only the two extreme ones per line
+// can be hull vertices.  They are reduced into ctl->line_ep (minimum and
+// maximum along the line, lowest index on ties) instead of becoming records;
+// the last block turns the end points into records.
+// Warp-collective: every lane passes its candidate (valid = false for none);
+// the warp reduces per line first and issues one atomic pair per line.
+// Returns whether this lane's point lies on a support line.
+__device__ __forceinline__ bool reduce_on_line(const Octagon& o, bool valid, int X, int Y, unsigned idx, Ctl* ctl) {
+    bool on = false;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        const bool hit = valid && ((l == 0) ? X == o.vx[W] : (l == 1) ? Y == o.vy[S] : (l == 2) ? X == o.vx[E] : Y == o.vy[N]);
+        on |= hit;
+        if (__any_sync(0xFFFFFFFFu, hit)) {
+            const unsigned along = (l & 1) ? (unsigned)X : (unsigned)Y;
+            unsigned long long mn = hit ? ((unsigned long long)along << 32) | idx : ~0ull;
+            unsigned long long mx = hit ? ((unsigned long long)along << 32) | (0xFFFFFFFFu - idx) : 0ull;
+#pragma unroll
+            for (int o2 = 16; o2; o2 >>= 1) {
+                const unsigned long long a = __shfl_xor_sync(0xFFFFFFFFu, mn, o2);
+                const unsigned long long b = __shfl_xor_sync(0xFFFFFFFFu, mx, o2);
+                mn = a < mn ? a : mn;
+                mx = b > mx ? b : mx;
+            }
+            if ((threadIdx.x & 31) == 0) {
+                atomicMin(&ctl->line_ep[2 * l], mn);
+                atomicMax(&ctl->line_ep[2 * l + 1], mx);
+            }
+        }
+    }
+    return on;
+}
+
+// Records are staged per warp in shared memory; a full buffer goes out with
+// one atomic on the record counter, and at the end the block's remainders go
+// out together with one atomic (a single counter hit once per warp batch
+// serialises at L2).
+constexpr int kRecBuf = 128;
+struct RecBuf {
+    unsigned long long val[kRecBuf];
+    unsigned key[kRecBuf];
+};
+
+__device__ __forceinline__ void rec_flush_warp(RecBuf& b, unsigned& cnt, Ctl* ctl, uint32_t* keys, uint64_t* vals) {
+    const int lane = threadIdx.x & 31;
+    unsigned base = 0u;
+    if (lane == 0) base = atomicAdd(&ctl->count, cnt);
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    for (unsigned i = lane; i < cnt; i += 32) {
+        keys[base + i] = b.key[i];
+        vals[base + i] = b.val[i];
+    }
+    __syncwarp();
+    cnt = 0u;
+}
+
+// Warp-collective: classifies one point per lane (valid = false for none) and
+// stages the kept ones.  Histograms of the three sort digits are counted in
+// shared memory.
+__device__ __forceinline__ void post_point(bool valid, float x, float y, unsigned idx, const Octagon& o, RecBuf& b,
+                                           unsigned& cnt, Ctl* ctl, uint32_t* keys, uint64_t* vals,
+                                           unsigned (*s_hist)[kDigits]) {
+    int r = -1, X = 0, Y = 0;
+    if (valid) {
+        X = __float2int_rn(x);
+        Y = __float2int_rn(y);
+        r = classify_hull(x, y, o);
+    }
+    bool keep = r >= 0;
+    if (!__any_sync(0xFFFFFFFFu, keep)) return;
+    if (reduce_on_line(o, keep, X, Y, idx, ctl)) keep = false;
+    const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
+    if (!bal) return;
+    if (cnt + (unsigned)__popc(bal) > (unsigned)kRecBuf) rec_flush_warp(b, cnt, ctl, keys, vals);
+    if (keep) {
+        uint32_t u, v;
+        queue_frame(r, X, Y, u, v);
+        const uint32_t key = make_key(r, u);
+        const unsigned pos = cnt + __popc(bal & lanemask_lt());
+        b.key[pos] = key;
+        b.val[pos] = make_val(v, idx);
+#pragma unroll
+        for (int p = 0; p < kSortPasses; ++p) atomicAdd(&s_hist[p][(key >> (p * kDigitBits)) & (kDigits - 1)], 1u);
+    }
+    cnt += __popc(bal);
+    __syncwarp();
+}
+
+// Whole block: the warps' staged records go out with one atomic.
+__device__ void rec_flush_block(RecBuf& b, unsigned cnt, Ctl* ctl, uint32_t* keys, uint64_t* vals) {
+    __shared__ unsigned s_off[kPostThreads / 32];
+    __shared__ unsigned s_base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s_off[warp] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned tot = 0u;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            const unsigned c = s_off[w];
+            s_off[w] = tot;
+            tot += c;
+        }
+        s_base = tot ? atomicAdd(&ctl->count, tot) : 0u;
+    }
+    __syncthreads();
+    const unsigned base = s_base + s_off[warp];
+    for (unsigned i = lane; i < cnt; i += 32) {
+        keys[base + i] = b.key[i];
+        vals[base + i] = b.val[i];
+    }
+}
+
+__device__ __forceinline__ void flush_hist(unsigned (*s_hist)[kDigits], Ctl* ctl) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < kSortPasses * kDigits; i += blockDim.x) {
+        const unsigned c = (&s_hist[0][0])[i];
+        if (c) atomicAdd(&(&ctl->digit_hist[0][0])[i], c);
+    }
+}
+
+// Record of support line l's end point (slot t = 2 l + {0: minimum, 1:
+// maximum}) from its packed reduction; false when the line has no survivor.
+__device__ __forceinline__ bool line_record(const Octagon& o, int t, unsigned long long e, uint32_t& key,
+                                            uint64_t& val) {
+    if ((t & 1) ? e == 0ull : e == ~0ull) return false;
+    const int l = t >> 1;
+    const int along = (int)(e >> 32);
+    const unsigned idx = (t & 1) ? 0xFFFFFFFFu - (unsigned)e : (unsigned)e;
+    int X, Y;
+    switch (l) {
+        case 0: X = o.vx[W]; Y = along; break;
+        case 1: X = along; Y = o.vy[S]; break;
+        case 2: X = o.vx[E]; Y = along; break;
+        default: X = along; Y = o.vy[N]; break;
+    }
+    const int r = classify_hull_slow((float)X, (float)Y, &o);
+    if (r < 0) return false;   // cannot happen: it was a survivor
+    uint32_t u, v;
+    queue_frame(r, X, Y, u, v);
+    key = make_key(r, u);
+    val = make_val(v, idx);
+    return true;
+}
+
+// The block that finished last: support-line records, then with at most
+// kMidCap records the hull (quickhull rounds, else the sort-based mid_hull).
+// Every other record is already in keys/vals and in the digit histograms.
+__device__ void post_last_block(const float* __restrict__ pts, long long n, Ctl* ctl, const Octagon& o,
+                                uint32_t* keys, uint64_t* vals, int32_t* out_idx, int64_t* out_n, char* dyn) {
+    __shared__ unsigned long long s_lep[8];
+    __shared__ uint64_t s_lval[8];
+    __shared__ unsigned s_lkey[8];
+    __shared__ int s_lpos[8];
+    __shared__ unsigned s_m, s_total;
+    __shared__ int s_mv;
+    const int tid = threadIdx.x;
+    CH_TRACE_DECL
+    CH_TRACE_MARK();
+    // one round of loads: line end points and the record count
+    if (tid < 8) s_lep[tid] = *(volatile unsigned long long*)&ctl->line_ep[tid];
+    if (tid == 8) s_m = *(volatile unsigned*)&ctl->count;
+    __syncthreads();
+    if (tid < 8) s_lpos[tid] = line_record(o, tid, s_lep[tid], s_lkey[tid], s_lval[tid]) ? 1 : -1;
+    __syncthreads();
+    if (tid == 0) {
+        unsigned m = s_m;
+        for (int t = 0; t < 8; ++t)
+            if (s_lpos[t] > 0) s_lpos[t] = (int)m++;
+        s_total = m;
+        ctl->count = m;
+    }
+    __syncthreads();
+    const unsigned total = s_total;
+    const bool small = total <= (unsigned)kMidCap;
+    if (tid < 8 && s_lpos[tid] >= 0) {
+        keys[s_lpos[tid]] = s_lkey[tid];
+        vals[s_lpos[tid]] = s_lval[tid];
+        if (!small) {
+#pragma unroll
+            for (int p = 0; p < kSortPasses; ++p)
+                atomicAdd(&ctl->digit_hist[p][(s_lkey[tid] >> (p * kDigitBits)) & (kDigits - 1)], 1u);
+        }
+    }
+    if (!small) return;   // the sort-based path follows
+    __syncthreads();      // also makes this block's line records visible to it
+    QhSmem& q = *reinterpret_cast<QhSmem*>(dyn);
+    for (unsigned i = tid; i < total; i += blockDim.x) {
+        const uint32_t k = __ldcg(keys + i);
+        const uint64_t w = __ldcg(vals + i);
+        q.ru[i] = (int)(k & kKeyMask);
+        q.rv[i] = (int)(w >> 31);
+        q.ri[i] = (int)(w & 0x7FFFFFFFull);
+        q.rs[i] = (int)(k >> kKeyBits);
+    }
+    __syncthreads();
+    CH_TRACE_MARK();
+    const bool ok = qh_chains(q, (int)total, &s_mv);
+    CH_TRACE_MARK();
+    if (ok) {
+        stitch_cycle(q.ru, q.rv, q.ri, s_mv, q.rs, ctl, n, out_idx, out_n);
+    } else {
+        __syncthreads();
+        mid_hull(keys, vals, (int)total, pts, n, ctl, out_idx, out_n, dyn);
+    }
+    if (tid == 0) ctl->done = 1;
+    CH_TRACE_MARK();
+#ifdef CH_TRACE
+    if (tid == 0) printf("[post] records %u raw %u mv %d ok %d\n", total, ctl->count_raw, s_mv, (int)ok);
+#endif
+    CH_TRACE_PRINT("post-last");
+}
+
+constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
+constexpr size_t kPostSmemBytes =
+    cmax(cmax(kMidSmemBytes, sizeof(QhSmem)), (size_t)(kPostThreads / 32) * sizeof(RecBuf));
+
+__global__ void __launch_bounds__(kPostThreads, 1) post_kernel(const float* __restrict__ pts, long long n, int head,
+                                                               long long ntiles, Ctl* ctl, const uint64_t* raw_xy,
+                                                               const uint32_t* raw_idx, uint32_t* keys,
+                                                               uint64_t* vals, int32_t* out_idx, int64_t* out_n) {
+    extern __shared__ __align__(16) char dyn[];
+    __shared__ Octagon s_o;
+    __shared__ unsigned s_hist[kSortPasses][kDigits];
+    __shared__ int s_flag, s_mode;
+    __shared__ unsigned s_nraw;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        s_flag = read_status(ctl);
+        s_mode = *(volatile int*)&ctl->mode;
+        s_nraw = *(volatile unsigned*)&ctl->count_raw;
+    }
+    copy_octagon(&s_o, &ctl->oct);
+    for (int i = tid; i < kSortPasses * kDigits; i += blockDim.x) (&s_hist[0][0])[i] = 0u;
+    __syncthreads();
+    if (s_flag != CH_OK) {   // data error or timeout of an earlier stage
+        if (blockIdx.x == 0 && tid == 0) { *out_n = s_flag; ctl->done = 1; }
+        return;
+    }
+    RecBuf& rb = reinterpret_cast<RecBuf*>(dyn)[warp];
+    unsigned rc = 0u;
+    if (s_mode == 1) {   // two-pass mode: every point
+        const long long gwarp = ((long long)blockIdx.x * blockDim.x + tid) >> 5;
+        const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+        const float4* p4 = reinterpret_cast<const float4*>(pts + 2 * head);
+        const unsigned long long pol = l2_evict_first();
+        for (long long t = gwarp; t < ntiles; t += nwarps) {
+            const float4* base = p4 + t * kWarpTileF4 + lane;
+            float4 v[kLoadsPerLane];
+#pragma unroll
+            for (int j = 0; j < kLoadsPerLane; ++j) v[j] = ld_stream_f4(base + j * 32, pol);
+            const long long i0 = head + t * kWarpTilePts + 2 * lane;
+#pragma unroll
+            for (int j = 0; j < kLoadsPerLane; ++j) {
+                post_point(true, v[j].x, v[j].y, (unsigned)(i0 + 64 * j), s_o, rb, rc, ctl, keys, vals, s_hist);
+                post_point(true, v[j].z, v[j].w, (unsigned)(i0 + 64 * j + 1), s_o, rb, rc, ctl, keys, vals, s_hist);
+            }
+        }
+        if (gwarp == 0) {   // the unaligned head point and the ragged tail
+            const long long ranges[2][2] = {{0, head}, {head + ntiles * kWarpTilePts, n}};
+            for (int rg = 0; rg < 2; ++rg)
+                for (long long b = ranges[rg][0]; b < ranges[rg][1]; b += 32) {
+                    const long long i = b + lane;
+                    const bool valid = i < ranges[rg][1];
+                    float x = 0.0f, y = 0.0f;
+                    if (valid) { x = pts[2 * i]; y = pts[2 * i + 1]; }
+                    post_point(valid, x, y, (unsigned)i, s_o, rb, rc, ctl, keys, vals, s_hist);
+                }
+        }
+    } else {   // fused mode: the raw survivors of the main pass
+        const unsigned nraw = s_nraw;
+        const unsigned stride = gridDim.x * blockDim.x;
+        for (unsigned b = blockIdx.x * blockDim.x + warp * 32; b < nraw; b += stride) {
+            const unsigned i = b + lane;
+            const bool valid = i < nraw;
+            float x = 0.0f, y = 0.0f;
+            unsigned idx = 0u;
+            if (valid) {
+                const unsigned long long xy = raw_xy[i];
+                x = (float)(unsigned)(xy >> 32);
+                y = (float)(unsigned)(xy & 0xFFFFFFFFull);
+                idx = raw_idx[i];
+            }
+            post_point(valid, x, y, idx, s_o, rb, rc, ctl, keys, vals, s_hist);
+        }
+    }
+    rec_flush_block(rb, rc, ctl, keys, vals);
+    flush_hist(s_hist, ctl);
+    if (!last_block(&ctl->blocks_done[2], &s_flag)) return;
+    post_last_block(pts, n, ctl, s_o, keys, vals, out_idx, out_n, dyn);
+}
+
+// ---------------------------------------------------------------------------
+void launch_post(const float* pts, long long n, int head, long long ntiles, Ctl* ctl, const uint64_t* raw_xy,
+                 const uint32_t* raw_idx, uint32_t* keys, uint64_t* vals, int32_t* out_idx, int64_t* out_n,
+                 int grid, cudaStream_t s) {
+    post_kernel<<<grid, kPostThreads, kPostSmemBytes, s>>>(pts, n, head, ntiles, ctl, raw_xy, raw_idx, keys, vals,
+                                                          out_idx, out_n);
+}
+
+cudaError_t configure_post_kernel() {
+    return cudaFuncSetAttribute(post_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPostSmemBytes);
+}
+
+cudaError_t occupancy_post(int* blocks) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, post_kernel, kPostThreads, kPostSmemBytes);
+}
+
+}  // namespace ch

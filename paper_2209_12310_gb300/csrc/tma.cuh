@@ -28,20 +28,17 @@ __device__ __forceinline__ void fence_proxy_async() {
 }
 
 __device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
-    unsigned long long state;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
-                 : "=l"(state)
-                 : "r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-    (void)state;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 
 // Bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) from
 // global to this CTA's shared memory, completing on `bar`.
-__device__ __forceinline__ void tma_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
+__device__ __forceinline__ void tma_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar,
+                                         unsigned long long pol) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
+        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+        : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
@@ -86,7 +83,7 @@ struct WarpStream {
             const int s = (int)(k % kStages);
             fence_proxy_async();
             mbar_expect_tx(&bar[s], kWarpTileF4 * 16);
-            tma_load(ring + s * kWarpTileF4, src + t * kWarpTileF4, kWarpTileF4 * 16, &bar[s]);
+            tma_load(ring + s * kWarpTileF4, src + t * kWarpTileF4, kWarpTileF4 * 16, &bar[s], l2_evict_first());
         }
     }
     __device__ __forceinline__ void start() {
