@@ -116,6 +116,32 @@ int ch_filter(const float* pts, int64_t n, int32_t* out_ext8, uint8_t* out_label
  */
 int ch_hull_host(const float* pts, int64_t n, int32_t* out_idx, int64_t* out_n, void* stream);
 
+/* Largest point count of ch_hull_noalloc. */
+#define CH_NOALLOC_MAX_POINTS ((int64_t)8000)
+
+/*
+ * ch_hull_noalloc -- ch_hull for at most CH_NOALLOC_MAX_POINTS points that
+ * allocates nothing.  The paper has no counterpart; it exists for callers
+ * that cannot let the library allocate device memory: code that must keep
+ * within a device-memory budget fixed up front, or a latency-critical loop
+ * that cannot pay the device-wide synchronisation cudaMalloc may imply
+ * (ch_hull grows its workspace the first time it sees a size).
+ *   pts      device, 8-byte aligned, n*2 float32 (same domain as ch_hull).
+ *   n        0 <= n <= CH_NOALLOC_MAX_POINTS; larger n returns CH_EINVAL and
+ *            enqueues nothing.
+ *   out_idx  device int32[n], 4-byte aligned; out_n device int64 (8-byte
+ *            aligned): the same result as ch_hull (h indices, CCW from the
+ *            lexicographically smallest vertex; or CH_ERANGE on bad data).
+ * The whole hull runs in one thread block.  Its global scratch (about 100 KB)
+ * is one fixed array in the library's static device memory; the first call on
+ * a device looks up that array's address and sets the kernel's shared-memory
+ * limit, so make that first call before any stream capture.  Nothing in the
+ * scratch needs to start at zero.  Calls that overlap in time (other streams
+ * or host threads) share the scratch and race: the caller orders them.
+ * Returns CH_OK when enqueued, CH_EINVAL or CH_ECUDA otherwise.
+ */
+int ch_hull_noalloc(const float* pts, int64_t n, int32_t* out_idx, int64_t* out_n, void* stream);
+
 /*
  * ch_reserve -- grow the workspace of `stream` on the current device for
  * hulls of up to n points (batched: n = total points, k sets).  Call it before

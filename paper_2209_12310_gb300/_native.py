@@ -38,6 +38,7 @@ SIGNATURES = {
     "ch_hull_batched": (_INT, [_P, _P, _I32, _P, _P, _P, _P]),
     "ch_filter": (_INT, [_P, _I64, _P, _P, _P, _P]),
     "ch_hull_host": (_INT, [_P, _I64, _P, _P, _P]),
+    "ch_hull_noalloc": (_INT, [_P, _I64, _P, _P, _P]),
     "ch_reserve": (_INT, [_I64, _I32, _P]),
     "ch_workspace_bytes": (_SZ, [_I64]),
     "ch_release": (_INT, []),
