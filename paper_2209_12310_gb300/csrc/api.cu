@@ -323,6 +323,15 @@ void drop_graphs(int dev, cudaStream_t s) {
     drop_graphs_locked(dev, s);
 }
 
+int enqueue_hull_nograph(const float* pts, long long n, int32_t* out_idx, int64_t* out_n, cudaStream_t s,
+                         int dev) {
+    char* base = nullptr;
+    Layout L;
+    const int st = get_workspace(dev, s, n, &base, &L);
+    if (st != CH_OK) return st;
+    return enqueue_hull_direct(pts, n, out_idx, out_n, s, dev, base, L);
+}
+
 int enqueue_hull(const float* pts, long long n, int32_t* out_idx, int64_t* out_n, cudaStream_t s, int dev) {
     DevInfo di;
     int st = device_info(dev, &di);

@@ -1,22 +1,414 @@
 // batched.cu -- k independent hulls packed back to back (ch_hull_batched).
 //
-// Every set runs the full single-hull launch sequence on the caller's stream,
-// in stream order, sharing that stream's workspace; each result is therefore
-// identical to ch_hull on the set alone.
+// The sets are cut into tiles of at most kBTile points (a tile never spans
+// two sets) and every launch covers all sets at once:
+//   bt_init      per-set control blocks and tile counts;
+//   bt_scan      tile offsets (exclusive prefix over the sets, one block);
+//   bt_extremes  tiles: validation and the 8 extremes of each set as packed
+//                (key, lowest local index) maxima (Alg. 2, findExtremes);
+//   bt_octagon   one block per set: octagon, inner region, the chain end
+//                point records;
+//   bt_filter    tiles: the hull-rule classification of every point against
+//                its set's octagon, records compacted into the set's region
+//                (the loop of Alg. 1/2), support-line end points reduced;
+//   bt_hull      one block per set: the hull of its records (quickhull rounds
+//                and the stitch, as in the single hull's last block).
+// A set whose records exceed what one block holds is flagged; after the
+// launches the host reads the flags and runs the single-hull path on those
+// sets.  Each result equals ch_hull on the set alone (local indices).
 #include "ch_internal.cuh"
 #include "host.h"
+#include "hullcore.cuh"
 #include "launch.h"
+#include "octagon.cuh"
+#include "records.cuh"
 
+#include <algorithm>
+#include <map>
+#include <mutex>
 #include <vector>
 
 namespace ch {
 
-int reserve_batched(int dev, cudaStream_t s, long long n, int k) {
-    (void)dev; (void)s; (void)n; (void)k;
+constexpr int kBTile = 4096;           // points per tile
+constexpr int kBThreads = 256;         // threads of the tile kernels
+constexpr int kBHullThreads = 512;     // threads of bt_hull (a multiple of 128)
+constexpr int kBOctThreads = 64;       // threads of bt_octagon
+
+struct BArgs {
+    const float* pts;
+    const int64_t* offsets;   // device, k + 1
+    int k;
+    Ctl* ctl;                 // k control blocks
+    uint32_t* keys;           // records: set i's region starts at offsets[i] + 16 i
+    uint64_t* vals;
+    int* tile_base;           // k + 1: first tile of each set
+    int32_t* out_idx;
+    int64_t* out_n;
+    unsigned char* big;       // k: the set needs the single-hull path
+};
+
+__device__ __forceinline__ long long region_base(const BArgs& a, int i) { return a.offsets[i] + 16ll * i; }
+
+// Set of tile t: the last i with tile_base[i] <= t.
+__device__ __forceinline__ int tile_set(const BArgs& a, int t) {
+    int lo = 0, hi = a.k - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.tile_base[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void bt_init(BArgs a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.k) return;
+    Ctl* c = a.ctl + i;
+    for (int d = 0; d < 8; ++d) {
+        c->ext_packed[d] = 0ull;
+        c->line_ep[d] = (d & 1) ? 0ull : ~0ull;
+    }
+    c->status = CH_OK;
+    c->abort = 0;
+    c->count = 8u;
+    c->done = 0;
+    a.big[i] = 0;
+    const long long ni = a.offsets[i + 1] - a.offsets[i];
+    a.tile_base[i] = (int)((ni + kBTile - 1) / kBTile);
+}
+
+// Exclusive prefix of the tile counts in place (one block of 1024 threads);
+// tile_base[k] = total tiles.
+__global__ void __launch_bounds__(1024) bt_scan(int* tile_base, int k) {
+    __shared__ int s_part[1024];
+    const int tid = threadIdx.x;
+    const int per = (k + 1023) / 1024;
+    const int lo = tid * per, hi = min(k, lo + per);
+    int sum = 0;
+    for (int i = lo; i < hi; ++i) sum += tile_base[i];
+    s_part[tid] = sum;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const int v = tid >= o ? s_part[tid - o] : 0;
+        __syncthreads();
+        s_part[tid] += v;
+        __syncthreads();
+    }
+    int run = s_part[tid] - sum;
+    for (int i = lo; i < hi; ++i) {
+        const int c = tile_base[i];
+        tile_base[i] = run;
+        run += c;
+    }
+    if (tid == 1023) tile_base[k] = s_part[1023];
+}
+
+__device__ __forceinline__ bool bt_dir_is_max(int d) { return d >= SE && d <= N; }
+
+__device__ __forceinline__ unsigned long long bt_pack(int d, int X, int Y, unsigned idx) {
+    int k;
+    switch (d) {
+        case W: case E: k = X; break;
+        case S: case N: k = Y; break;
+        case SW: case NE: k = X + Y; break;
+        default: k = X - Y + kCoordLimit; break;
+    }
+    const unsigned hk = bt_dir_is_max(d) ? (unsigned)k : 0xFFFFFFFFu - (unsigned)k;
+    return ((unsigned long long)hk << 32) | (unsigned long long)(0xFFFFFFFFu - idx);
+}
+
+__global__ void __launch_bounds__(kBThreads) bt_extremes(BArgs a, int ntiles) {
+    __shared__ unsigned long long s_red[kBThreads / 32][8];
+    __shared__ int s_set;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        if (tid == 0) s_set = tile_set(a, t);
+        __syncthreads();
+        const int i = s_set;
+        const long long base = a.offsets[i], ni = a.offsets[i + 1] - base;
+        const long long p0 = (long long)(t - a.tile_base[i]) * kBTile;
+        const long long p1 = min(ni, p0 + kBTile);
+        const float2* p2 = reinterpret_cast<const float2*>(a.pts) + base;
+        unsigned long long best[8];
+#pragma unroll
+        for (int d = 0; d < 8; ++d) best[d] = 0ull;
+        bool bad = false;
+        for (long long p = p0 + tid; p < p1; p += kBThreads) {
+            const float2 v = __ldcs(p2 + p);
+            const int X = __float2int_rn(v.x), Y = __float2int_rn(v.y);
+            bad |= (__int2float_rn(X) != v.x) | (__int2float_rn(Y) != v.y) |
+                   ((((unsigned)X | (unsigned)Y) >> kCoordBits) != 0u);
+#pragma unroll
+            for (int d = 0; d < 8; ++d) {
+                const unsigned long long q = bt_pack(d, X, Y, (unsigned)p);
+                best[d] = q > best[d] ? q : best[d];
+            }
+        }
+        if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) set_status(a.ctl + i, CH_ERANGE);
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            unsigned long long q = best[d];
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                const unsigned long long r = __shfl_xor_sync(0xFFFFFFFFu, q, o);
+                q = r > q ? r : q;
+            }
+            if (lane == 0) s_red[warp][d] = q;
+        }
+        __syncthreads();
+        if (tid < 8) {
+            unsigned long long m = 0ull;
+            for (int w = 0; w < kBThreads / 32; ++w) m = s_red[w][tid] > m ? s_red[w][tid] : m;
+            if (m) atomicMax(&a.ctl[i].ext_packed[tid], m);
+        }
+        __syncthreads();
+    }
+}
+
+// One block per set: octagon of its extremes (with the inner region, which
+// settles most points of bt_filter), the chain end-point records.
+__global__ void __launch_bounds__(kBOctThreads) bt_octagon(BArgs a) {
+    __shared__ Octagon s_o;
+    __shared__ int s_vx[8], s_vy[8], s_id[8], s_st;
+    const int i = blockIdx.x, tid = threadIdx.x;
+    Ctl* c = a.ctl + i;
+    const long long base = a.offsets[i], ni = a.offsets[i + 1] - base;
+    if (tid == 0) s_st = read_status(c);
+    __syncthreads();
+    if (ni == 0 || s_st != CH_OK) {
+        if (tid == 0) {
+            a.out_n[i] = ni == 0 ? 0 : s_st;
+            c->done = 1;
+        }
+        return;
+    }
+    if (tid < 8) {
+        const unsigned long long pk = c->ext_packed[tid];
+        const int id = (int)(0xFFFFFFFFu - (unsigned)(pk & 0xFFFFFFFFull));
+        s_id[tid] = id;
+        s_vx[tid] = __float2int_rn(a.pts[2 * (base + id)]);
+        s_vy[tid] = __float2int_rn(a.pts[2 * (base + id) + 1]);
+    }
+    __syncthreads();
+    setup_octagon_block(s_o, s_vx, s_vy, s_id, true);
+    copy_octagon(&c->oct, &s_o);
+    const long long rb = region_base(a, i);
+    if (tid < 12) {
+        int r, d;
+        bool emit = true;
+        if (tid < 8) {
+            r = tid >> 1;
+            d = (tid & 1) ? ((2 * r + 2) & 7) : 2 * r;
+        } else {
+            r = tid - 8;
+            d = 2 * r + 1;
+            const int qa = 2 * r, qb = (2 * r + 2) & 7;
+            emit = orient64(s_vx[qa], s_vy[qa], s_vx[qb], s_vy[qb], s_vx[d], s_vy[d]) < 0;
+        }
+        if (emit) {
+            uint32_t u, v;
+            queue_frame(r, s_vx[d], s_vy[d], u, v);
+            const unsigned pos = tid < 8 ? (unsigned)tid : atomicAdd(&c->count, 1u);
+            a.keys[rb + pos] = make_key(r, u);
+            a.vals[rb + pos] = make_val(v, (uint32_t)s_id[d]);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBThreads) bt_filter(BArgs a, int ntiles) {
+    __shared__ Octagon s_o;
+    __shared__ int s_set, s_skip;
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        if (tid == 0) {
+            const int i = tile_set(a, t);
+            s_set = i;
+            s_skip = *(volatile int*)&a.ctl[i].done;
+        }
+        __syncthreads();
+        const int i = s_set;
+        if (!s_skip) {
+            copy_octagon(&s_o, &a.ctl[i].oct);
+            __syncthreads();
+            Ctl* c = a.ctl + i;
+            const long long base = a.offsets[i], ni = a.offsets[i + 1] - base;
+            const long long p0 = (long long)(t - a.tile_base[i]) * kBTile;
+            const long long p1 = min(ni, p0 + kBTile);
+            const long long rb = region_base(a, i);
+            const float2* p2 = reinterpret_cast<const float2*>(a.pts) + base;
+            for (long long b0 = p0; b0 < p1; b0 += kBThreads) {   // uniform trip count
+                const long long p = b0 + tid;
+                const bool valid = p < p1;
+                int r = -1, X = 0, Y = 0;
+                if (valid) {
+                    const float2 v = __ldcs(p2 + p);
+                    X = __float2int_rn(v.x);
+                    Y = __float2int_rn(v.y);
+                    r = classify_hull(v.x, v.y, s_o);
+                }
+                bool keep = r >= 0;
+                if (!__any_sync(0xFFFFFFFFu, keep)) continue;
+                if (reduce_on_line(s_o, keep, X, Y, (unsigned)p, c)) keep = false;
+                const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
+                if (!bal) continue;
+                unsigned pos0 = 0u;
+                if (lane == 0) pos0 = atomicAdd(&c->count, (unsigned)__popc(bal));
+                pos0 = __shfl_sync(0xFFFFFFFFu, pos0, 0);
+                if (keep) {
+                    uint32_t u, v;
+                    queue_frame(r, X, Y, u, v);
+                    const long long pos = rb + pos0 + __popc(bal & lanemask_lt());
+                    a.keys[pos] = make_key(r, u);
+                    a.vals[pos] = make_val(v, (uint32_t)p);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+constexpr size_t bt_cmax(size_t x, size_t y) { return x > y ? x : y; }
+constexpr size_t kBHullSmem = bt_cmax(kMidSmemBytes, sizeof(QhSmem));
+
+// One block per set: support-line records, then the hull of the records when
+// one block can hold them (else the set is flagged for the single-hull path).
+__global__ void __launch_bounds__(kBHullThreads, 1) bt_hull(BArgs a) {
+    extern __shared__ __align__(16) char dyn[];
+    __shared__ unsigned long long s_lep[8];
+    __shared__ uint64_t s_lval[8];
+    __shared__ unsigned s_lkey[8];
+    __shared__ int s_lpos[8], s_done, s_mv;
+    __shared__ unsigned s_m, s_total;
+    __shared__ Octagon s_o;
+    const int i = blockIdx.x, tid = threadIdx.x;
+    Ctl* c = a.ctl + i;
+    if (tid == 0) s_done = *(volatile int*)&c->done;
+    __syncthreads();
+    if (s_done) return;
+    copy_octagon(&s_o, &c->oct);
+    if (tid < 8) s_lep[tid] = *(volatile unsigned long long*)&c->line_ep[tid];
+    if (tid == 8) s_m = *(volatile unsigned*)&c->count;
+    __syncthreads();
+    if (tid < 8) s_lpos[tid] = line_record(s_o, tid, s_lep[tid], s_lkey[tid], s_lval[tid]) ? 1 : -1;
+    __syncthreads();
+    if (tid == 0) {
+        unsigned m = s_m;
+        for (int t = 0; t < 8; ++t)
+            if (s_lpos[t] > 0) s_lpos[t] = (int)m++;
+        s_total = m;
+        c->count = m;
+    }
+    __syncthreads();
+    const unsigned total = s_total;
+    const long long rb = region_base(a, i);
+    const long long base = a.offsets[i], ni = a.offsets[i + 1] - base;
+    if (tid < 8 && s_lpos[tid] >= 0) {
+        a.keys[rb + s_lpos[tid]] = s_lkey[tid];
+        a.vals[rb + s_lpos[tid]] = s_lval[tid];
+    }
+    if (total > (unsigned)kMidCap) {
+        if (tid == 0) a.big[i] = 1;
+        return;
+    }
+    __syncthreads();
+    QhSmem& q = *reinterpret_cast<QhSmem*>(dyn);
+    for (unsigned j = tid; j < total; j += blockDim.x) {
+        const uint32_t k = __ldcg(a.keys + rb + j);
+        const uint64_t w = __ldcg(a.vals + rb + j);
+        q.ru[j] = (int)(k & kKeyMask);
+        q.rv[j] = (int)(w >> 31);
+        q.ri[j] = (int)(w & 0x7FFFFFFFull);
+        q.rs[j] = (int)(k >> kKeyBits);
+    }
+    __syncthreads();
+    if (qh_chains(q, (int)total, &s_mv)) {
+        stitch_cycle(q.ru, q.rv, q.ri, s_mv, q.rs, c, ni, a.out_idx + base, a.out_n + i);
+    } else {
+        __syncthreads();
+        mid_hull(a.keys + rb, a.vals + rb, (int)total, a.pts + 2 * base, ni, c, a.out_idx + base, a.out_n + i, dyn);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Workspace per (device, stream), grow-only.
+struct BWork {
+    char* base = nullptr;
+    size_t bytes = 0;
+};
+static std::mutex g_bmu;
+static std::map<std::pair<int, cudaStream_t>, BWork> g_bws;
+
+static size_t bt_align(size_t x) { return (x + 255) / 256 * 256; }
+
+struct BLayout {
+    size_t ctl, keys, vals, tiles, big, total;
+};
+
+static BLayout bt_layout(long long total, int k) {
+    BLayout L;
+    const long long cap = total + 16ll * k + 16;
+    L.ctl = 0;
+    L.keys = bt_align(L.ctl + sizeof(Ctl) * (size_t)k);
+    L.vals = bt_align(L.keys + sizeof(uint32_t) * (size_t)cap);
+    L.tiles = bt_align(L.vals + sizeof(uint64_t) * (size_t)cap);
+    L.big = bt_align(L.tiles + sizeof(int) * ((size_t)k + 1));
+    L.total = bt_align(L.big + (size_t)k);
+    return L;
+}
+
+static int bt_workspace(int dev, cudaStream_t s, long long total, int k, char** base, BLayout* L) {
+    std::lock_guard<std::mutex> lk(g_bmu);
+    *L = bt_layout(total, k);
+    BWork& w = g_bws[std::make_pair(dev, s)];
+    if (w.bytes < L->total) {
+        if (w.base) {
+            cudaStreamSynchronize(s);
+            cudaFree(w.base);
+            w.base = nullptr;
+            w.bytes = 0;
+        }
+        void* p = nullptr;
+        const size_t want = L->total + L->total / 8;
+        if (cudaMalloc(&p, want) != cudaSuccess) {
+            cudaGetLastError();
+            return CH_ENOMEM;
+        }
+        w.base = (char*)p;
+        w.bytes = want;
+    }
+    *base = w.base;
     return CH_OK;
 }
 
-void release_batched() {}
+int reserve_batched(int dev, cudaStream_t s, long long n, int k) {
+    char* base = nullptr;
+    BLayout L;
+    return bt_workspace(dev, s, n, std::max(k, 1), &base, &L);
+}
+
+void release_batched() {
+    std::lock_guard<std::mutex> lk(g_bmu);
+    for (auto& kv : g_bws) {
+        cudaStreamSynchronize(kv.first.second);
+        if (kv.second.base) cudaFree(kv.second.base);
+    }
+    g_bws.clear();
+}
+
+static int bt_configure(int dev, int* sms) {
+    static std::mutex mu;
+    static std::map<int, int> done;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = done.find(dev);
+    if (it != done.end()) { *sms = it->second; return CH_OK; }
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return CH_ECUDA;
+    if (cudaFuncSetAttribute(bt_hull, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBHullSmem) != cudaSuccess)
+        return CH_ECUDA;
+    done[dev] = n;
+    *sms = n;
+    return CH_OK;
+}
 
 }  // namespace ch
 
@@ -38,21 +430,58 @@ extern "C" int ch_hull_batched(const float* pts, const int64_t* offsets, int32_t
         if (cudaStreamSynchronize(s) != cudaSuccess) return CH_ECUDA;
     }
     if (off[0] != 0) return CH_EINVAL;
-    for (int i = 0; i < k; ++i)
+    long long tiles = 0;
+    for (int i = 0; i < k; ++i) {
         if (off[i + 1] < off[i] || off[i + 1] - off[i] > CH_MAX_POINTS) return CH_EINVAL;
+        tiles += (off[i + 1] - off[i] + kBTile - 1) / kBTile;
+    }
+    if (tiles > INT32_MAX) return CH_EINVAL;
     const int64_t total = off[k];
     int st = check_points_args(pts, total);
     if (st != CH_OK) return st;
     if (total > 0 && !out_idx) return CH_EINVAL;
-    int dev = 0;
+    int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return CH_ECUDA;
+    if ((st = bt_configure(dev, &sms)) != CH_OK) return st;
+    char* base = nullptr;
+    BLayout L;
+    if ((st = bt_workspace(dev, s, total, k, &base, &L)) != CH_OK) return st;
+    BArgs a;
+    a.pts = pts;
+    a.offsets = offsets;
+    a.k = k;
+    a.ctl = (Ctl*)(base + L.ctl);
+    a.keys = (uint32_t*)(base + L.keys);
+    a.vals = (uint64_t*)(base + L.vals);
+    a.tile_base = (int*)(base + L.tiles);
+    a.out_idx = out_idx;
+    a.out_n = out_n;
+    a.big = (unsigned char*)(base + L.big);
+    const int nt = (int)tiles;
+    const int grid_t = std::max(1, std::min(nt, sms * 8));
+    {
+        ProfScope p("batched_prep", s);
+        bt_init<<<(k + 255) / 256, 256, 0, s>>>(a);
+        bt_scan<<<1, 1024, 0, s>>>(a.tile_base, k);
+    }
+    if (nt > 0) {
+        ProfScope p("batched_extremes", s);
+        bt_extremes<<<grid_t, kBThreads, 0, s>>>(a, nt);
+    }
+    { ProfScope p("batched_octagon", s); bt_octagon<<<k, kBOctThreads, 0, s>>>(a); }
+    if (nt > 0) {
+        ProfScope p("batched_filter", s);
+        bt_filter<<<grid_t, kBThreads, 0, s>>>(a, nt);
+    }
+    { ProfScope p("batched_hull", s); bt_hull<<<k, kBHullThreads, kBHullSmem, s>>>(a); }
+    if (cudaGetLastError() != cudaSuccess) return CH_ECUDA;
+    // Sets with more records than one block holds: the single-hull path.
+    std::vector<unsigned char> big((size_t)k);
+    if (cudaMemcpyAsync(big.data(), a.big, (size_t)k, cudaMemcpyDeviceToHost, s) != cudaSuccess) return CH_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return CH_ECUDA;
     for (int i = 0; i < k; ++i) {
-        const int64_t ni = off[i + 1] - off[i];
-        if (ni == 0) {
-            if (cudaMemsetAsync(out_n + i, 0, sizeof(int64_t), s) != cudaSuccess) return CH_ECUDA;
-            continue;
-        }
-        st = enqueue_hull(pts + 2 * off[i], ni, out_idx + off[i], out_n + i, s, dev);
+        if (!big[i]) continue;
+        st = enqueue_hull_nograph(pts + 2 * off[i], off[i + 1] - off[i], out_idx + off[i], out_n + i, s, dev);
         if (st != CH_OK) return st;
     }
     return CH_OK;

@@ -17,6 +17,10 @@ struct Layout {
 Layout make_layout(long long n);
 int get_workspace(int dev, cudaStream_t s, long long n, char** base, Layout* L);
 int enqueue_hull(const float* pts, long long n, int32_t* out_idx, int64_t* out_n, cudaStream_t s, int dev);
+// The same launches without the CUDA-graph cache (callers with many distinct
+// argument sets, where capturing each would only thrash the cache).
+int enqueue_hull_nograph(const float* pts, long long n, int32_t* out_idx, int64_t* out_n, cudaStream_t s,
+                         int dev);
 int check_points_args(const float* pts, long long n);
 
 int reserve_batched(int dev, cudaStream_t s, long long n, int k);

@@ -11,6 +11,7 @@
 #include "hullcore.cuh"
 #include "launch.h"
 #include "octagon.cuh"
+#include "records.cuh"
 
 #include <climits>
 
@@ -18,47 +19,6 @@ namespace ch {
 
 constexpr int kPostThreads = 512;
 static_assert(kPostThreads % 128 == 0, "mid_hull splits the block in four");
-
-// Hull-rule classification: -1 = dropped, else queue.
-__device__ __forceinline__ int classify_hull(float x, float y, const Octagon& o) {
-    const int X = __float2int_rn(x), Y = __float2int_rn(y);
-    if (in_inner(o, X, Y)) return -1;
-    return classify_hull_slow(x, y, &o);
-}
-
-// Survivors on an axis support line of the true octagon (x = xmin, y = ymin,
-// x = xmax, y = ymax) lie on a hull edge; only the two extreme ones per line
-// can be hull vertices.  They are reduced into ctl->line_ep (minimum and
-// maximum along the line, lowest index on ties) instead of becoming records;
-// the last block turns the end points into records.
-// Warp-collective: every lane passes its candidate (valid = false for none);
-// the warp reduces per line first and issues one atomic pair per line.
-// Returns whether this lane's point lies on a support line.
-__device__ __forceinline__ bool reduce_on_line(const Octagon& o, bool valid, int X, int Y, unsigned idx, Ctl* ctl) {
-    bool on = false;
-#pragma unroll
-    for (int l = 0; l < 4; ++l) {
-        const bool hit = valid && ((l == 0) ? X == o.vx[W] : (l == 1) ? Y == o.vy[S] : (l == 2) ? X == o.vx[E] : Y == o.vy[N]);
-        on |= hit;
-        if (__any_sync(0xFFFFFFFFu, hit)) {
-            const unsigned along = (l & 1) ? (unsigned)X : (unsigned)Y;
-            unsigned long long mn = hit ? ((unsigned long long)along << 32) | idx : ~0ull;
-            unsigned long long mx = hit ? ((unsigned long long)along << 32) | (0xFFFFFFFFu - idx) : 0ull;
-#pragma unroll
-            for (int o2 = 16; o2; o2 >>= 1) {
-                const unsigned long long a = __shfl_xor_sync(0xFFFFFFFFu, mn, o2);
-                const unsigned long long b = __shfl_xor_sync(0xFFFFFFFFu, mx, o2);
-                mn = a < mn ? a : mn;
-                mx = b > mx ? b : mx;
-            }
-            if ((threadIdx.x & 31) == 0) {
-                atomicMin(&ctl->line_ep[2 * l], mn);
-                atomicMax(&ctl->line_ep[2 * l + 1], mx);
-            }
-        }
-    }
-    return on;
-}
 
 // Records are staged per warp in shared memory; a full buffer goes out with
 // one atomic on the record counter, and at the end the block's remainders go
@@ -145,30 +105,6 @@ __device__ __forceinline__ void flush_hist(unsigned (*s_hist)[kDigits], Ctl* ctl
         const unsigned c = (&s_hist[0][0])[i];
         if (c) atomicAdd(&(&ctl->digit_hist[0][0])[i], c);
     }
-}
-
-// Record of support line l's end point (slot t = 2 l + {0: minimum, 1:
-// maximum}) from its packed reduction; false when the line has no survivor.
-__device__ __forceinline__ bool line_record(const Octagon& o, int t, unsigned long long e, uint32_t& key,
-                                            uint64_t& val) {
-    if ((t & 1) ? e == 0ull : e == ~0ull) return false;
-    const int l = t >> 1;
-    const int along = (int)(e >> 32);
-    const unsigned idx = (t & 1) ? 0xFFFFFFFFu - (unsigned)e : (unsigned)e;
-    int X, Y;
-    switch (l) {
-        case 0: X = o.vx[W]; Y = along; break;
-        case 1: X = along; Y = o.vy[S]; break;
-        case 2: X = o.vx[E]; Y = along; break;
-        default: X = along; Y = o.vy[N]; break;
-    }
-    const int r = classify_hull_slow((float)X, (float)Y, &o);
-    if (r < 0) return false;   // cannot happen: it was a survivor
-    uint32_t u, v;
-    queue_frame(r, X, Y, u, v);
-    key = make_key(r, u);
-    val = make_val(v, idx);
-    return true;
 }
 
 // The block that finished last: support-line records, then with at most
