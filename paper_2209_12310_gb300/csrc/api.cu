@@ -33,6 +33,7 @@ static int device_info(int dev, DevInfo* out) {
     if (configure_hull_kernels() != cudaSuccess) return CH_ECUDA;
     if (configure_filter_kernels() != cudaSuccess) return CH_ECUDA;
     if (configure_post_kernel() != cudaSuccess) return CH_ECUDA;
+    if (configure_bucket_kernels() != cudaSuccess) return CH_ECUDA;
     if (occupancy_filter(&di.occ_main, &di.occ_lab) != cudaSuccess) return CH_ECUDA;
     if (occupancy_post(&di.occ_post) != cudaSuccess) return CH_ECUDA;
     if (occupancy_sort(&di.occ_sort) != cudaSuccess) return CH_ECUDA;
@@ -74,6 +75,14 @@ Layout make_layout(long long n) {
     L.off_ci = take(4 * (size_t)L.ctcap * kChainTile);
     L.off_clen = take(4 * (size_t)L.ctcap);
     L.off_counters = take(4 * (size_t)kMaxLevels * L.ctcap);
+    L.bmax = L.cap / kBkAvg + 8;
+    L.off_bcount = take(4 * (size_t)L.bmax);
+    L.off_bcur = take(4 * (size_t)L.bmax);
+    L.off_bstart = take(4 * (size_t)L.bmax);
+    L.off_blen = take(4 * (size_t)L.bmax);
+    L.off_bu = take(4 * (size_t)L.bmax * kBkChain);
+    L.off_bv = take(4 * (size_t)L.bmax * kBkChain);
+    L.off_bi = take(4 * (size_t)L.bmax * kBkChain);
     L.total = o;
     return L;
 }
@@ -259,6 +268,11 @@ static int enqueue_hull_direct(const float* pts, long long n, int32_t* out_idx, 
         launch_post(pts, n, head, ntiles, ctl, raw_xy, raw_idx, kA, vA, out_idx, out_n, grid_post, s);
     }
     {
+        launch_bucket_pass(ctl, kA, vA, kB, vB, (unsigned*)(base + L.off_bcount), (unsigned*)(base + L.off_bcur),
+                           (unsigned*)(base + L.off_bstart), (int*)(base + L.off_bu), (int*)(base + L.off_bv),
+                           (int*)(base + L.off_bi), (int*)(base + L.off_blen), (unsigned)L.bmax, di.sms, s);
+    }
+    {
         ProfScope p("sort", s);
         launch_sort_pass(kA, vA, kB, vB, ctl, status, 0, grid_sort, s);
         launch_sort_pass(kB, vB, kA, vA, ctl, status, 1, grid_sort, s);
@@ -266,8 +280,9 @@ static int enqueue_hull_direct(const float* pts, long long n, int32_t* out_idx, 
     }
     {
         ProfScope p("hull_chains", s);
-        launch_chain(ctl, kB, vB, cu, cv, ci, clen, counters, (int)L.ctcap, (int*)vA, (int*)kA, pts, n, out_idx,
-                     out_n, grid_chain, s);
+        launch_chain(ctl, kB, vB, (const int*)(base + L.off_bu), (const int*)(base + L.off_bv),
+                     (const int*)(base + L.off_bi), (const int*)(base + L.off_blen), cu, cv, ci, clen, counters,
+                     (int)L.ctcap, (int*)vA, (int*)kA, (int*)kB, (int*)vB, pts, n, out_idx, out_n, grid_chain, s);
     }
     return cudaGetLastError() == cudaSuccess ? CH_OK : CH_ECUDA;
 }

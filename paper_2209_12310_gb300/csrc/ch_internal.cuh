@@ -38,6 +38,11 @@ constexpr int kChainThreads = 256;
 constexpr int kChainItems = 16;
 constexpr int kChainTile = kChainThreads * kChainItems;
 constexpr int kMergeSmemCap = 8192;           // chain points a global merge keeps on chip
+// Bucketed large-survivor path (bucket.cu): records per bucket on average,
+// chain vertices a bucket may keep, bucket chains per chain-kernel tile.
+constexpr int kBkAvg = 256;
+constexpr int kBkChain = 32;
+constexpr int kBkGroup = kChainTile / kBkChain;
 constexpr int kSampleTiles = 1024;            // warp tiles read by the sample pass (512k points)
 constexpr int kMaxLevels = 32;
 
@@ -92,6 +97,12 @@ struct Ctl {
     unsigned int reg_tile_base[5];      // chain tiles of queue r: [base[r], base[r+1])
     unsigned int counts4[4];            // survivors per queue (ch_filter)
     unsigned long long line_ep[8];      // end points of survivors on the 4 axis support lines
+    int bk_state;                       // large-survivor path: 0 unused, 1 buckets, 2 full sort
+    unsigned int bk_cursor;             // bucket allocation cursor
+    unsigned int bk_nb[4];              // buckets of queue r
+    unsigned int bk_base[5];            // first bucket of queue r
+    int bk_lo[4];                       // u of queue r's first chain point
+    float bk_scale[4];                  // buckets per unit of u in queue r
     Octagon oct;                        // octagon of the true extremes
     Octagon oct_s;                      // octagon of a sample's extremes
 };

@@ -73,6 +73,8 @@ __global__ void init_kernel(Ctl* ctl, int mode) {
         ctl->mode = mode;
         ctl->done = 0;
         ctl->records_ready = 0;
+        ctl->bk_state = 0;
+        ctl->bk_cursor = 0u;
     }
     unsigned* h = &ctl->digit_hist[0][0];
     for (int i = t; i < kSortPasses * kDigits; i += blockDim.x) h[i] = 0u;

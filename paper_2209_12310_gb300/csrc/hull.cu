@@ -74,8 +74,12 @@ __device__ void bridge_block(const ChainPtr& A, int la, const ChainPtr& B, int l
 
 // ---------------------------------------------------------------------------
 struct HullBufs {
-    const uint32_t* keys;   // sorted records
+    const uint32_t* keys;   // sorted records (sort-based path)
     const uint64_t* vals;
+    const int* bu;          // bucket chains (bucketed path): bucket b at [b*kBkChain, ...)
+    const int* bv;
+    const int* bi;
+    const int* blen;
     int* cu;                // chain storage: tile c at [c*kChainTile, ...)
     int* cv;
     int* ci;
@@ -84,6 +88,8 @@ struct HullBufs {
     int ctcap;
     int* vbuf;              // stitch scratch (2 * records ints)
     int* kbuf;              // stitch scratch (records ints)
+    int* xbuf;              // stitch coordinates (records ints each)
+    int* ybuf;
     const float* pts;
     long long n;
     int32_t* out_idx;
@@ -112,6 +118,7 @@ __global__ void __launch_bounds__(kChainThreads) chain_kernel(Ctl* ctl, HullBufs
     __shared__ int s_red[4];
     __shared__ int s_old;
     __shared__ unsigned s_qn[4], s_q0[5], s_tb[5];
+    __shared__ int s_mv[kChainThreads / 2][3];   // per pair: destination, source, count
 
     if (*(volatile int*)&ctl->done) return;
     const int st0 = read_status(ctl);
@@ -120,28 +127,39 @@ __global__ void __launch_bounds__(kChainThreads) chain_kernel(Ctl* ctl, HullBufs
         return;
     }
     const int tid = threadIdx.x;
-    // Queue boundaries in the sorted records: queue r holds the top-pass
-    // digits [128 r, 128 (r + 1)), so its size is a sum of that histogram.
+    // Bucketed input: the leaves are bucket chains, kBkGroup per tile; queue
+    // r owns buckets [bk_base[r], bk_base[r+1]).  Sorted input: queue r holds
+    // the top-pass digits [128 r, 128 (r + 1)), so its size is a sum of that
+    // histogram.
+    const bool bk = *(volatile int*)&ctl->bk_state == 1;
     if (tid < 4) s_qn[tid] = 0u;
     __syncthreads();
-    for (int d = tid; d < kDigits; d += blockDim.x) {
-        const unsigned c = ctl->digit_hist[kSortPasses - 1][d];
-        if (c) atomicAdd(&s_qn[d >> (kDigitBits - 2)], c);
+    if (bk) {
+        if (tid < 4) s_qn[tid] = ctl->bk_base[tid + 1] - ctl->bk_base[tid];
+    } else {
+        for (int d = tid; d < kDigits; d += blockDim.x) {
+            const unsigned c = ctl->digit_hist[kSortPasses - 1][d];
+            if (c) atomicAdd(&s_qn[d >> (kDigitBits - 2)], c);
+        }
     }
     __syncthreads();
     if (tid == 0) {
+        const unsigned per = bk ? (unsigned)kBkGroup : (unsigned)kChainTile;
         unsigned q = 0, tb = 0;
         for (int r = 0; r < 4; ++r) {
             s_q0[r] = q;
             s_tb[r] = tb;
             q += s_qn[r];
-            tb += (s_qn[r] + kChainTile - 1) / kChainTile;
+            tb += (s_qn[r] + per - 1) / per;
         }
         s_q0[4] = q;
         s_tb[4] = tb;
     }
     __syncthreads();
     const unsigned total_tiles = s_tb[4];
+    const unsigned nrec = ctl->count;
+    const int seg = bk ? kBkChain : kChainItems;           // shared-memory slot per leaf chain
+    const int nseg = bk ? kBkGroup : kChainThreads;        // leaf chains per tile
 
     for (unsigned c = blockIdx.x; c < total_tiles; c += gridDim.x) {
         int r = 0;
@@ -150,9 +168,26 @@ __global__ void __launch_bounds__(kChainThreads) chain_kernel(Ctl* ctl, HullBufs
         const unsigned ct = s_tb[r + 1] - rb;
         const unsigned t_local = c - rb;
         const unsigned q0 = s_q0[r], q1 = s_q0[r + 1];
-        const unsigned ts = q0 + t_local * kChainTile;
-        const unsigned te = min(q1, ts + kChainTile);
+        const unsigned ts = q0 + t_local * (bk ? (unsigned)kBkGroup : (unsigned)kChainTile);
+        const unsigned te = min(q1, ts + (bk ? (unsigned)kBkGroup : (unsigned)kChainTile));
 
+        if (bk) {
+            // 1') the tile's bucket chains (buckets q0 + t_local * kBkGroup + tid)
+            int len = 0;
+            if (tid < kBkGroup) {
+                const unsigned b = ts + tid;
+                if (b < te) {
+                    len = __ldcg(hb.blen + b);
+                    const size_t o = (size_t)b * kBkChain;
+                    for (int j = 0; j < len; ++j) {
+                        su[tid * kBkChain + j] = __ldcg(hb.bu + o + j);
+                        sv[tid * kBkChain + j] = __ldcg(hb.bv + o + j);
+                        si[tid * kBkChain + j] = __ldcg(hb.bi + o + j);
+                    }
+                }
+            }
+            s_len[tid] = len;
+        } else {
         // 1) run reduction + per-thread chain (records [ts + 16 tid, +16)).
         {
             const int sbase = tid * kChainItems;
@@ -180,14 +215,52 @@ __global__ void __launch_bounds__(kChainThreads) chain_kernel(Ctl* ctl, HullBufs
             }
             s_len[tid] = sp;
         }
+        }
         __syncthreads();
-        // 2) pairwise merge of the 256 thread chains.
-        for (int l = 0; (1 << l) < kChainThreads; ++l) {
+        // 2) pairwise merge of the tile's leaf chains: the bridge of each pair
+        //    by its leader thread, then the kept part of the right chain moved
+        //    down by one warp per pair (a left shift, copied forward in chunks
+        //    of 32, never overwrites entries still to be read).
+        for (int l = 0; (1 << l) < nseg; ++l) {
             const int g = 1 << l;
-            if ((tid & (2 * g - 1)) == 0) {
-                const int b = tid + g;
-                s_len[tid] = merge_smem_seq(su, sv, si, tid * kChainItems, s_len[tid],
-                                            b * kChainItems, s_len[b]);
+            const int npairs = nseg >> (l + 1);
+            if (tid < nseg && (tid & (2 * g - 1)) == 0) {
+                const int b = tid + g, la = s_len[tid], lb = s_len[b];
+                int dst = tid * seg, src = b * seg, cnt = 0, len = la;
+                if (lb > 0) {
+                    if (la == 0) {
+                        cnt = lb;
+                        len = lb;
+                    } else {
+                        ChainPtr A{su + tid * seg, sv + tid * seg, si + tid * seg};
+                        ChainPtr B{su + b * seg, sv + b * seg, si + b * seg};
+                        int is, js;
+                        bridge_seq<false>(A, la, B, lb, is, js);
+                        dst += is + 1;
+                        src += js;
+                        cnt = lb - js;
+                        len = is + 1 + cnt;
+                    }
+                }
+                const int p = tid / (2 * g);
+                s_mv[p][0] = dst;
+                s_mv[p][1] = src;
+                s_mv[p][2] = cnt;
+                s_len[tid] = len;
+            }
+            __syncthreads();
+            const int lane = tid & 31;
+            for (int p = tid >> 5; p < npairs; p += kChainThreads / 32) {
+                const int dst = s_mv[p][0], src = s_mv[p][1], cnt = s_mv[p][2];
+                if (dst == src) continue;
+                for (int c = 0; c < cnt; c += 32) {
+                    const int j = c + lane;
+                    int a = 0, b2 = 0, d = 0;
+                    if (j < cnt) { a = su[src + j]; b2 = sv[src + j]; d = si[src + j]; }
+                    __syncwarp();
+                    if (j < cnt) { su[dst + j] = a; sv[dst + j] = b2; si[dst + j] = d; }
+                    __syncwarp();
+                }
             }
             __syncthreads();
         }
@@ -268,16 +341,28 @@ __global__ void __launch_bounds__(kChainThreads) chain_kernel(Ctl* ctl, HullBufs
         off[0] = 0;
         for (int q = 0; q < 4; ++q) off[q + 1] = off[q] + __ldcg(hb.clen + s_tb[q]) - 1;
         const int m = off[4];
-        if (m < 0 || m > (int)s_q0[4]) {   // inconsistent state: report, never read out of range
+        if (m < 0 || m > (int)nrec) {   // inconsistent state: report, never read out of range
             if (tid == 0) { set_status(ctl, CH_ECUDA); *hb.out_n = CH_ECUDA; }
             return;
         }
+        // the cycle's coordinates from the chains' frames (no reads of the
+        // points), into the sort/scatter buffers, free by now
         for (int q = 0; q < 4; ++q) {
             const size_t o = (size_t)s_tb[q] * kChainTile;
-            for (int j = tid; j < off[q + 1] - off[q]; j += blockDim.x) hb.vbuf[off[q] + j] = __ldcg(hb.ci + o + j);
+            for (int j = tid; j < off[q + 1] - off[q]; j += blockDim.x) {
+                int x, y;
+                frame_to_xy(q, __ldcg(hb.cu + o + j), __ldcg(hb.cv + o + j), x, y);
+                hb.vbuf[off[q] + j] = __ldcg(hb.ci + o + j);
+                hb.xbuf[off[q] + j] = x;
+                hb.ybuf[off[q] + j] = y;
+            }
         }
         __syncthreads();
-        stitch_core(hb.vbuf, m, hb.kbuf, hb.vbuf + m, hb.pts, hb.n, ctl, hb.out_idx, hb.out_n);
+        const int* X = hb.xbuf;
+        const int* Y = hb.ybuf;
+        stitch_core(hb.vbuf, m, hb.kbuf, hb.vbuf + m,
+                    [&](int p, long long& x, long long& y) { x = __ldcg(X + p); y = __ldcg(Y + p); }, hb.n, ctl,
+                    hb.out_idx, hb.out_n);
         return;
     }
 }
@@ -285,10 +370,12 @@ __global__ void __launch_bounds__(kChainThreads) chain_kernel(Ctl* ctl, HullBufs
 // ---------------------------------------------------------------------------
 size_t chain_smem_bytes() { return (size_t)3 * kMergeSmemCap * sizeof(int); }
 
-void launch_chain(Ctl* ctl, const uint32_t* keys, const uint64_t* vals, int* cu, int* cv, int* ci, int* clen,
-                  int* counters, int ctcap, int* vbuf, int* kbuf, const float* pts, long long n, int32_t* out_idx,
+void launch_chain(Ctl* ctl, const uint32_t* keys, const uint64_t* vals, const int* bu, const int* bv,
+                  const int* bi, const int* blen, int* cu, int* cv, int* ci, int* clen, int* counters, int ctcap,
+                  int* vbuf, int* kbuf, int* xbuf, int* ybuf, const float* pts, long long n, int32_t* out_idx,
                   int64_t* out_n, int grid, cudaStream_t s) {
-    HullBufs hb{keys, vals, cu, cv, ci, clen, counters, ctcap, vbuf, kbuf, pts, n, out_idx, out_n};
+    HullBufs hb{keys, vals, bu, bv, bi, blen, cu, cv, ci, clen, counters, ctcap, vbuf, kbuf, xbuf, ybuf, pts, n,
+                out_idx, out_n};
     chain_kernel<<<grid, kChainThreads, chain_smem_bytes(), s>>>(ctl, hb);
 }
 

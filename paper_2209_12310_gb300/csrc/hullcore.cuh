@@ -149,12 +149,14 @@ __device__ __forceinline__ unsigned long long xy_key(long long x, long long y) {
 }
 
 // V[0..m): point indices of the concatenated queue chains W..S, S..E, E..N,
-// N..W (each without its last point), a weakly convex cyclic polygon.  Writes
-// the strictly convex vertices counter-clockwise from the lexicographically
-// smallest one; all-collinear input gives [lex-min, lex-max], one distinct
-// point gives [it].  flag and comp are scratch arrays of m ints.
-static __device__ void stitch_core(const int* V, int m, int* flag, int* comp, const float* __restrict__ pts,
-                            long long n, Ctl* ctl, int32_t* out_idx, int64_t* out_n) {
+// N..W (each without its last point), a weakly convex cyclic polygon; xy(p,
+// x, y) gives the coordinates of cycle position p.  Writes the strictly
+// convex vertices counter-clockwise from the lexicographically smallest one;
+// all-collinear input gives [lex-min, lex-max], one distinct point gives
+// [it].  flag and comp are scratch arrays of m ints.
+template <typename XY>
+__device__ void stitch_core(const int* V, int m, int* flag, int* comp, XY xy, long long n, Ctl* ctl,
+                            int32_t* out_idx, int64_t* out_n) {
     __shared__ long long s_ll[32];
     __shared__ unsigned long long s_ull[32];
     __shared__ int s_int[33];
@@ -167,9 +169,9 @@ static __device__ void stitch_core(const int* V, int m, int* flag, int* comp, co
     long long npos = 0, nneg = 0;
     for (int i = tid; i < m; i += T) {
         long long ax, ay, bx, by, cx, cy;
-        pt_xy(pts, V[(i + m - 1) % m], ax, ay);
-        pt_xy(pts, V[i], bx, by);
-        pt_xy(pts, V[(i + 1) % m], cx, cy);
+        xy(i == 0 ? m - 1 : i - 1, ax, ay);
+        xy(i, bx, by);
+        xy(i + 1 == m ? 0 : i + 1, cx, cy);
         const long long tr = orient64(ax, ay, bx, by, cx, cy);
         flag[i] = tr > 0;
         npos += tr > 0;
@@ -184,7 +186,7 @@ static __device__ void stitch_core(const int* V, int m, int* flag, int* comp, co
         unsigned long long lo = ~0ull, hi = 0ull;
         for (int i = tid; i < m; i += T) {
             long long x, y;
-            pt_xy(pts, V[i], x, y);
+            xy(i, x, y);
             const unsigned long long k = xy_key(x, y);
             lo = k < lo ? k : lo;
             hi = k > hi ? k : hi;
@@ -195,7 +197,7 @@ static __device__ void stitch_core(const int* V, int m, int* flag, int* comp, co
         __syncthreads();
         for (int i = tid; i < m; i += T) {
             long long x, y;
-            pt_xy(pts, V[i], x, y);
+            xy(i, x, y);
             const unsigned long long k = xy_key(x, y);
             if (k == lo) atomicMin(&s_a, V[i]);
             if (k == hi) atomicMin(&s_b, V[i]);
@@ -219,11 +221,12 @@ static __device__ void stitch_core(const int* V, int m, int* flag, int* comp, co
         const int ex = block_excl_scan(f, s_int, &tot);
         if (f) {
             long long x, y;
-            pt_xy(pts, V[i], x, y);
+            xy(i, x, y);
             const unsigned long long k = xy_key(x, y);
             best = k < best ? k : best;
             comp[written + ex] = V[i];
         }
+        if (i < m) flag[i] = f ? written + ex : -1;   // compacted position
         written += tot;
     }
     best = block_reduce<unsigned long long>(best, mn, s_ull);
@@ -234,14 +237,18 @@ static __device__ void stitch_core(const int* V, int m, int* flag, int* comp, co
     }
     if (tid == 0) s_a = 0;
     __syncthreads();
-    for (int j = tid; j < h; j += T) {
+    for (int i = tid; i < m; i += T) {
+        if (flag[i] < 0) continue;
         long long x, y;
-        pt_xy(pts, comp[j], x, y);
-        if (xy_key(x, y) == best) s_a = j;
+        xy(i, x, y);
+        if (xy_key(x, y) == best) s_a = flag[i];
     }
     __syncthreads();
     const int start = s_a;
-    for (int j = tid; j < h; j += T) out_idx[j] = comp[(start + j) % h];
+    for (int j = tid; j < h; j += T) {
+        const int k = start + j;
+        out_idx[j] = comp[k < h ? k : k - h];
+    }
     __syncthreads();
     if (tid == 0) {
         const int st = read_status(ctl);
@@ -362,7 +369,8 @@ static __device__ void mid_hull(const uint32_t* keys, const uint64_t* vals, int 
         for (int j = tid; j < off[r + 1] - off[r]; j += T) V[off[r] + j] = ci[s_rs[r] + j];
     __syncthreads();
     CH_TRACE_MARK();
-    stitch_core(V, off[4], flag, cu, pts, n, ctl, out_idx, out_n);
+    stitch_core(V, off[4], flag, cu, [&](int p, long long& x, long long& y) { pt_xy(pts, V[p], x, y); }, n, ctl,
+                out_idx, out_n);
     CH_TRACE_MARK();
     CH_TRACE_PRINT("mid_hull");
 }

@@ -22,9 +22,14 @@ void launch_filter_output(const Ctl* ctl, long long n, int32_t* out_ext8, int64_
 void launch_sort_pass(const uint32_t* kin, const uint64_t* vin, uint32_t* kout, uint64_t* vout,
                       Ctl* ctl, unsigned long long* status, int pass, int grid, cudaStream_t s);
 
-void launch_chain(Ctl* ctl, const uint32_t* keys, const uint64_t* vals, int* cu, int* cv, int* ci, int* clen,
-                  int* counters, int ctcap, int* vbuf, int* kbuf, const float* pts, long long n, int32_t* out_idx,
+void launch_chain(Ctl* ctl, const uint32_t* keys, const uint64_t* vals, const int* bu, const int* bv,
+                  const int* bi, const int* blen, int* cu, int* cv, int* ci, int* clen, int* counters, int ctcap,
+                  int* vbuf, int* kbuf, int* xbuf, int* ybuf, const float* pts, long long n, int32_t* out_idx,
                   int64_t* out_n, int grid, cudaStream_t s);
+void launch_bucket_pass(Ctl* ctl, const uint32_t* kA, const uint64_t* vA, uint32_t* kB, uint64_t* vB,
+                        unsigned* bcount, unsigned* bcur, unsigned* bstart, int* bu, int* bv, int* bi, int* blen,
+                        unsigned bmax, int sms, cudaStream_t s);
+cudaError_t configure_bucket_kernels();
 size_t chain_smem_bytes();
 cudaError_t configure_hull_kernels();
 cudaError_t configure_filter_kernels();

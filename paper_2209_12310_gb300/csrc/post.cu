@@ -24,7 +24,7 @@ static_assert(kPostThreads % 128 == 0, "mid_hull splits the block in four");
 // one atomic on the record counter, and at the end the block's remainders go
 // out together with one atomic (a single counter hit once per warp batch
 // serialises at L2).
-constexpr int kRecBuf = 128;
+constexpr int kRecBuf = 512;
 struct RecBuf {
     unsigned long long val[kRecBuf];
     unsigned key[kRecBuf];

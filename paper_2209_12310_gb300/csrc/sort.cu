@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(
     __shared__ unsigned s_warp[kSortThreads / 32];
     __shared__ unsigned s_tile;
 
-    if (*(volatile int*)&ctl->done || read_status(ctl) != CH_OK) return;
+    if (*(volatile int*)&ctl->done || read_status(ctl) != CH_OK || *(volatile int*)&ctl->bk_state == 1) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned count = ctl->count;
     const unsigned ntiles = (count + kSortTile - 1) / kSortTile;
