@@ -225,66 +225,153 @@ static void prof_drain() {
 }
 
 // ---------------------------------------------------------------------------
-// The launch sequence of one hull (n >= 1) on an allocated workspace.
-static int enqueue_hull_direct(const float* pts, long long n, int32_t* out_idx, int64_t* out_n, cudaStream_t s,
-                               int dev, char* base, const Layout& L) {
+// The launch sequence of one hull (n >= 1) on an allocated workspace, in two
+// parts: the filter (init .. post), after which small survivor sets are done,
+// and the large-survivor path (buckets, the sort fallback, the chain merge).
+// `cond`, when non-zero, is a graph condition the post pass raises when the
+// second part has work (see the CUDA-graph cache below).
+struct HullLaunch {
     DevInfo di;
-    int st = device_info(dev, &di);
-    if (st != CH_OK) return st;
-    Ctl* ctl = (Ctl*)(base + L.off_ctl);
-    uint32_t* kA = (uint32_t*)(base + L.off_kA);
-    uint32_t* kB = (uint32_t*)(base + L.off_kB);
-    uint64_t* vA = (uint64_t*)(base + L.off_vA);
-    uint64_t* vB = (uint64_t*)(base + L.off_vB);
-    unsigned long long* status = (unsigned long long*)(base + L.off_status);
-    int* cu = (int*)(base + L.off_cu);
-    int* cv = (int*)(base + L.off_cv);
-    int* ci = (int*)(base + L.off_ci);
-    int* clen = (int*)(base + L.off_clen);
-    int* counters = (int*)(base + L.off_counters);
+    Ctl* ctl;
+    uint32_t *kA, *kB;
+    uint64_t *vA, *vB;
+    int head;
+    long long ntiles;
+};
 
-    const int head = (((uintptr_t)pts & 15u) != 0u && n > 0) ? 1 : 0;
-    const long long ntiles = (n - head) / kWarpTilePts;
-    const long long samples = sample_tiles_host(ntiles);
+static int hull_setup(const float* pts, long long n, int dev, char* base, const Layout& L, HullLaunch* h) {
+    int st = device_info(dev, &h->di);
+    if (st != CH_OK) return st;
+    h->ctl = (Ctl*)(base + L.off_ctl);
+    h->kA = (uint32_t*)(base + L.off_kA);
+    h->kB = (uint32_t*)(base + L.off_kB);
+    h->vA = (uint64_t*)(base + L.off_vA);
+    h->vB = (uint64_t*)(base + L.off_vB);
+    h->head = (((uintptr_t)pts & 15u) != 0u && n > 0) ? 1 : 0;
+    h->ntiles = (n - h->head) / kWarpTilePts;
+    return CH_OK;
+}
+
+static void enqueue_filter_part(const float* pts, long long n, int32_t* out_idx, int64_t* out_n, cudaStream_t s,
+                                const HullLaunch& h, unsigned long long cond) {
+    const long long samples = sample_tiles_host(h.ntiles);
     const int grid_sample = (int)std::max<long long>(1, std::min<long long>(256, (samples + 7) / 8));
-    const int grid_main = di.sms * di.occ_main;
-    const int grid_post = di.sms * di.occ_post;
-    const int grid_sort = di.sms * di.occ_sort;
-    const int grid_chain = di.sms * di.occ_chain;
     // Raw survivors of the fused pass live in the B buffers until the post
     // pass has turned them into sort records in the A buffers.
-    uint64_t* raw_xy = vB;
-    uint32_t* raw_idx = kB;
+    uint64_t* raw_xy = h.vB;
+    uint32_t* raw_idx = h.kB;
     const unsigned switch_at = (unsigned)std::max<long long>(1 << 16, n >> 5);
-
-    { ProfScope p("init", s); launch_init(ctl, 0, s); }
-    { ProfScope p("sample", s); launch_sample(pts, n, head, ntiles, ctl, grid_sample, s); }
+    { ProfScope p("init", s); launch_init(h.ctl, 0, s); }
+    { ProfScope p("sample", s); launch_sample(pts, n, h.head, h.ntiles, h.ctl, grid_sample, s); }
     {
         ProfScope p("main_filter", s);
-        launch_main(pts, n, head, ntiles, ctl, raw_xy, raw_idx, switch_at, kA, vA, grid_main, s);
+        launch_main(pts, n, h.head, h.ntiles, h.ctl, raw_xy, raw_idx, switch_at, h.kA, h.vA,
+                    h.di.sms * h.di.occ_main, s);
     }
     {
         ProfScope p("post", s);
-        launch_post(pts, n, head, ntiles, ctl, raw_xy, raw_idx, kA, vA, out_idx, out_n, grid_post, s);
+        launch_post(pts, n, h.head, h.ntiles, h.ctl, raw_xy, raw_idx, h.kA, h.vA, out_idx, out_n, cond,
+                    h.di.sms * h.di.occ_post, s);
     }
-    {
-        launch_bucket_pass(ctl, kA, vA, kB, vB, (unsigned*)(base + L.off_bcount), (unsigned*)(base + L.off_bcur),
-                           (unsigned*)(base + L.off_bstart), (int*)(base + L.off_bu), (int*)(base + L.off_bv),
-                           (int*)(base + L.off_bi), (int*)(base + L.off_blen), (unsigned)L.bmax, di.sms, s);
-    }
+}
+
+static void enqueue_large_part(const float* pts, long long n, int32_t* out_idx, int64_t* out_n, cudaStream_t s,
+                               char* base, const Layout& L, const HullLaunch& h) {
+    Ctl* ctl = h.ctl;
+    unsigned long long* status = (unsigned long long*)(base + L.off_status);
+    launch_bucket_pass(ctl, h.kA, h.vA, h.kB, h.vB, (unsigned*)(base + L.off_bcount), (unsigned*)(base + L.off_bcur),
+                       (unsigned*)(base + L.off_bstart), (int*)(base + L.off_bu), (int*)(base + L.off_bv),
+                       (int*)(base + L.off_bi), (int*)(base + L.off_blen), (unsigned)L.bmax, h.di.sms, s);
     {
         ProfScope p("sort", s);
-        launch_sort_pass(kA, vA, kB, vB, ctl, status, 0, grid_sort, s);
-        launch_sort_pass(kB, vB, kA, vA, ctl, status, 1, grid_sort, s);
-        launch_sort_pass(kA, vA, kB, vB, ctl, status, 2, grid_sort, s);
+        const int grid_sort = h.di.sms * h.di.occ_sort;
+        launch_sort_pass(h.kA, h.vA, h.kB, h.vB, ctl, status, 0, grid_sort, s);
+        launch_sort_pass(h.kB, h.vB, h.kA, h.vA, ctl, status, 1, grid_sort, s);
+        launch_sort_pass(h.kA, h.vA, h.kB, h.vB, ctl, status, 2, grid_sort, s);
     }
     {
         ProfScope p("hull_chains", s);
-        launch_chain(ctl, kB, vB, (const int*)(base + L.off_bu), (const int*)(base + L.off_bv),
-                     (const int*)(base + L.off_bi), (const int*)(base + L.off_blen), cu, cv, ci, clen, counters,
-                     (int)L.ctcap, (int*)vA, (int*)kA, (int*)kB, (int*)vB, pts, n, out_idx, out_n, grid_chain, s);
+        launch_chain(ctl, h.kB, h.vB, (const int*)(base + L.off_bu), (const int*)(base + L.off_bv),
+                     (const int*)(base + L.off_bi), (const int*)(base + L.off_blen), (int*)(base + L.off_cu),
+                     (int*)(base + L.off_cv), (int*)(base + L.off_ci), (int*)(base + L.off_clen),
+                     (int*)(base + L.off_counters), (int)L.ctcap, (int*)h.vA, (int*)h.kA, (int*)h.kB, (int*)h.vB,
+                     pts, n, out_idx, out_n, h.di.sms * h.di.occ_chain, s);
     }
+}
+
+static int enqueue_hull_direct(const float* pts, long long n, int32_t* out_idx, int64_t* out_n, cudaStream_t s,
+                               int dev, char* base, const Layout& L) {
+    HullLaunch h;
+    const int st = hull_setup(pts, n, dev, base, L, &h);
+    if (st != CH_OK) return st;
+    enqueue_filter_part(pts, n, out_idx, out_n, s, h, 0ull);
+    enqueue_large_part(pts, n, out_idx, out_n, s, base, L, h);
     return cudaGetLastError() == cudaSuccess ? CH_OK : CH_ECUDA;
+}
+
+// Captures the sequence on `cs` with the large-survivor part as the body of
+// a conditional (if) node whose condition the post pass raises; replays of
+// small-survivor calls then launch only the filter part.  False when any step
+// of the capture fails (the caller then captures the plain sequence).
+static bool capture_conditional(const float* pts, long long n, int32_t* out_idx, int64_t* out_n, cudaStream_t cs,
+                                int dev, char* base, const Layout& L, cudaGraph_t* out) {
+    HullLaunch h;
+    if (hull_setup(pts, n, dev, base, L, &h) != CH_OK) return false;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
+    bool ok = true;
+    cudaGraph_t graph = nullptr;
+    cudaGraphConditionalHandle cond = 0;
+    cudaStream_t bs = nullptr;
+    {
+        cudaStreamCaptureStatus stc;
+        unsigned long long id = 0;
+        const cudaGraphNode_t* deps = nullptr;
+        const cudaGraphEdgeData* edata = nullptr;
+        size_t ndeps = 0;
+        ok = cudaStreamGetCaptureInfo(cs, &stc, &id, &graph, &deps, &edata, &ndeps) == cudaSuccess && graph;
+        if (ok) ok = cudaGraphConditionalHandleCreate(&cond, graph, 0u, cudaGraphCondAssignDefault) == cudaSuccess;
+    }
+    if (ok) {
+        enqueue_filter_part(pts, n, out_idx, out_n, cs, h, (unsigned long long)cond);
+        cudaStreamCaptureStatus stc;
+        unsigned long long id = 0;
+        const cudaGraphNode_t* deps = nullptr;
+        const cudaGraphEdgeData* edata = nullptr;
+        size_t ndeps = 0;
+        ok = cudaStreamGetCaptureInfo(cs, &stc, &id, &graph, &deps, &edata, &ndeps) == cudaSuccess;
+        cudaGraphNode_t node = nullptr;
+        cudaGraphNodeParams np = {};
+        if (ok) {
+            np.type = cudaGraphNodeTypeConditional;
+            np.conditional.handle = cond;
+            np.conditional.type = cudaGraphCondTypeIf;
+            np.conditional.size = 1;
+            ok = cudaGraphAddNode(&node, graph, deps, edata, ndeps, &np) == cudaSuccess;
+        }
+        if (ok) ok = cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies) ==
+                     cudaSuccess;
+        if (ok) ok = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking) == cudaSuccess;
+        if (ok) {
+            cudaGraph_t body = np.conditional.phGraph_out[0];
+            ok = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+                 cudaSuccess;
+            if (ok) {
+                enqueue_large_part(pts, n, out_idx, out_n, bs, base, L, h);
+                cudaGraph_t tmp = nullptr;
+                ok = cudaStreamEndCapture(bs, &tmp) == cudaSuccess;
+            }
+        }
+    }
+    cudaGraph_t g = nullptr;
+    const bool ended = cudaStreamEndCapture(cs, &g) == cudaSuccess;
+    if (bs) cudaStreamDestroy(bs);
+    if (!ok || !ended || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return false;
+    }
+    *out = g;
+    return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -376,10 +463,13 @@ int enqueue_hull(const float* pts, long long n, int32_t* out_idx, int64_t* out_n
         return enqueue_hull_direct(pts, n, out_idx, out_n, s, dev, base, L);
     }
     cudaGraph_t graph = nullptr;
-    bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-    if (ok) {
-        st = enqueue_hull_direct(pts, n, out_idx, out_n, cs, dev, base, L);
-        ok = cudaStreamEndCapture(cs, &graph) == cudaSuccess && st == CH_OK && graph;
+    bool ok = capture_conditional(pts, n, out_idx, out_n, cs, dev, base, L, &graph);
+    if (!ok) {   // plain capture of the whole sequence
+        ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            st = enqueue_hull_direct(pts, n, out_idx, out_n, cs, dev, base, L);
+            ok = cudaStreamEndCapture(cs, &graph) == cudaSuccess && st == CH_OK && graph;
+        }
     }
     if (ok) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
     if (graph) cudaGraphDestroy(graph);

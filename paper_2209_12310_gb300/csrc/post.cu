@@ -111,7 +111,8 @@ __device__ __forceinline__ void flush_hist(unsigned (*s_hist)[kDigits], Ctl* ctl
 // kMidCap records the hull (quickhull rounds, else the sort-based mid_hull).
 // Every other record is already in keys/vals and in the digit histograms.
 __device__ void post_last_block(const float* __restrict__ pts, long long n, Ctl* ctl, const Octagon& o,
-                                uint32_t* keys, uint64_t* vals, int32_t* out_idx, int64_t* out_n, char* dyn) {
+                                uint32_t* keys, uint64_t* vals, int32_t* out_idx, int64_t* out_n, char* dyn,
+                                unsigned long long cond) {
     __shared__ unsigned long long s_lep[8];
     __shared__ uint64_t s_lval[8];
     __shared__ unsigned s_lkey[8];
@@ -146,7 +147,10 @@ __device__ void post_last_block(const float* __restrict__ pts, long long n, Ctl*
                 atomicAdd(&ctl->digit_hist[p][(s_lkey[tid] >> (p * kDigitBits)) & (kDigits - 1)], 1u);
         }
     }
-    if (!small) return;   // the sort-based path follows
+    if (!small) {   // the large-survivor path follows
+        if (cond && tid == 0) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, 1u);
+        return;
+    }
     __syncthreads();      // also makes this block's line records visible to it
     QhSmem& q = *reinterpret_cast<QhSmem*>(dyn);
     for (unsigned i = tid; i < total; i += blockDim.x) {
@@ -182,7 +186,8 @@ constexpr size_t kPostSmemBytes =
 __global__ void __launch_bounds__(kPostThreads, 1) post_kernel(const float* __restrict__ pts, long long n, int head,
                                                                long long ntiles, Ctl* ctl, const uint64_t* raw_xy,
                                                                const uint32_t* raw_idx, uint32_t* keys,
-                                                               uint64_t* vals, int32_t* out_idx, int64_t* out_n) {
+                                                               uint64_t* vals, int32_t* out_idx, int64_t* out_n,
+                                                               unsigned long long cond) {
     extern __shared__ __align__(16) char dyn[];
     __shared__ Octagon s_o;
     __shared__ unsigned s_hist[kSortPasses][kDigits];
@@ -251,15 +256,15 @@ __global__ void __launch_bounds__(kPostThreads, 1) post_kernel(const float* __re
     rec_flush_block(rb, rc, ctl, keys, vals);
     flush_hist(s_hist, ctl);
     if (!last_block(&ctl->blocks_done[2], &s_flag)) return;
-    post_last_block(pts, n, ctl, s_o, keys, vals, out_idx, out_n, dyn);
+    post_last_block(pts, n, ctl, s_o, keys, vals, out_idx, out_n, dyn, cond);
 }
 
 // ---------------------------------------------------------------------------
 void launch_post(const float* pts, long long n, int head, long long ntiles, Ctl* ctl, const uint64_t* raw_xy,
                  const uint32_t* raw_idx, uint32_t* keys, uint64_t* vals, int32_t* out_idx, int64_t* out_n,
-                 int grid, cudaStream_t s) {
+                 unsigned long long cond, int grid, cudaStream_t s) {
     post_kernel<<<grid, kPostThreads, kPostSmemBytes, s>>>(pts, n, head, ntiles, ctl, raw_xy, raw_idx, keys, vals,
-                                                          out_idx, out_n);
+                                                          out_idx, out_n, cond);
 }
 
 cudaError_t configure_post_kernel() {
