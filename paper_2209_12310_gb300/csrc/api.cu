@@ -56,26 +56,31 @@ Layout make_layout(long long n) {
     Layout L{};
     L.cap = n + 16;
     L.sort_tiles = (L.cap + kSortTile - 1) / kSortTile;
-    L.ctcap = (L.cap + kChainTile - 1) / kChainTile + 4;
+    L.bmax = L.cap / kBkAvg + 4 * kBkMinQ + 8;
+    // chain tiles: sorted records (one per kChainTile) or bucket chains (one
+    // per kBkGroup buckets of each queue), whichever needs more
+    L.ctcap = std::max((L.cap + kChainTile - 1) / kChainTile + 4, L.bmax / kBkGroup + 8);
     size_t o = 0;
     auto take = [&](size_t bytes) {
         const size_t r = o;
         o = align_up(o + bytes);
         return r;
     };
+    // zeroed at allocation: the control block, the sort's look-back status
+    // words and the merge tree's arrival counters (each kernel leaves them
+    // in that state for the next call)
     L.off_ctl = take(sizeof(Ctl));
+    L.off_status = take(8 * (size_t)kDigits * L.sort_tiles);
+    L.off_counters = take(4 * (size_t)kMaxLevels * L.ctcap);
+    L.zero_bytes = o;
     L.off_kA = take(4 * (size_t)L.cap);
     L.off_kB = take(4 * (size_t)L.cap);
     L.off_vA = take(8 * (size_t)L.cap);
     L.off_vB = take(8 * (size_t)L.cap);
-    L.off_status = take(8 * (size_t)kDigits * L.sort_tiles);
-    L.zero_bytes = o;   // control block and look-back status are zeroed at allocation
     L.off_cu = take(4 * (size_t)L.ctcap * kChainTile);
     L.off_cv = take(4 * (size_t)L.ctcap * kChainTile);
     L.off_ci = take(4 * (size_t)L.ctcap * kChainTile);
     L.off_clen = take(4 * (size_t)L.ctcap);
-    L.off_counters = take(4 * (size_t)kMaxLevels * L.ctcap);
-    L.bmax = L.cap / kBkAvg + 8;
     L.off_bcount = take(4 * (size_t)L.bmax);
     L.off_bcur = take(4 * (size_t)L.bmax);
     L.off_bstart = take(4 * (size_t)L.bmax);

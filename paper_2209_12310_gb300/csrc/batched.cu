@@ -13,9 +13,12 @@
 //                (the loop of Alg. 1/2), support-line end points reduced;
 //   bt_hull      one block per set: the hull of its records (quickhull rounds
 //                and the stitch, as in the single hull's last block).
-// A set whose records exceed what one block holds is flagged; after the
-// launches the host reads the flags and runs the single-hull path on those
-// sets.  Each result equals ch_hull on the set alone (local indices).
+// Sets whose records exceed what one block holds go through the bucketed
+// large-survivor path together (batched_large.cu); the rare set it cannot
+// finish (a bucket chain longer than kBkChain) is flagged and the host runs
+// the single-hull path on it.  Each result equals ch_hull on the set alone
+// (local indices).
+#include "batched_large.h"
 #include "ch_internal.cuh"
 #include "host.h"
 #include "hullcore.cuh"
@@ -72,6 +75,11 @@ __global__ void bt_init(BArgs a) {
     c->abort = 0;
     c->count = 8u;
     c->done = 0;
+    c->bk_state = 0;
+    for (int q = 0; q < 4; ++q) {
+        c->counts4[q] = 2u;   // the two chain end points of every queue
+        c->blocks_done[q] = 0u;
+    }
     a.big[i] = 0;
     const long long ni = a.offsets[i + 1] - a.offsets[i];
     a.tile_base[i] = (int)((ni + kBTile - 1) / kBTile);
@@ -209,6 +217,7 @@ __global__ void __launch_bounds__(kBOctThreads) bt_octagon(BArgs a) {
             uint32_t u, v;
             queue_frame(r, s_vx[d], s_vy[d], u, v);
             const unsigned pos = tid < 8 ? (unsigned)tid : atomicAdd(&c->count, 1u);
+            if (tid >= 8) atomicAdd(&c->counts4[r], 1u);
             a.keys[rb + pos] = make_key(r, u);
             a.vals[rb + pos] = make_val(v, (uint32_t)s_id[d]);
         }
@@ -254,6 +263,11 @@ __global__ void __launch_bounds__(kBThreads) bt_filter(BArgs a, int ntiles) {
                 unsigned pos0 = 0u;
                 if (lane == 0) pos0 = atomicAdd(&c->count, (unsigned)__popc(bal));
                 pos0 = __shfl_sync(0xFFFFFFFFu, pos0, 0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const unsigned bq = __ballot_sync(0xFFFFFFFFu, keep && r == q);
+                    if (bq && lane == 0) atomicAdd(&c->counts4[q], (unsigned)__popc(bq));
+                }
                 if (keep) {
                     uint32_t u, v;
                     queue_frame(r, X, Y, u, v);
@@ -305,6 +319,7 @@ __global__ void __launch_bounds__(kBHullThreads, 1) bt_hull(BArgs a) {
     if (tid < 8 && s_lpos[tid] >= 0) {
         a.keys[rb + s_lpos[tid]] = s_lkey[tid];
         a.vals[rb + s_lpos[tid]] = s_lval[tid];
+        atomicAdd(&c->counts4[s_lkey[tid] >> kKeyBits], 1u);
     }
     if (total > (unsigned)kMidCap) {
         if (tid == 0) a.big[i] = 1;
@@ -341,24 +356,68 @@ static std::map<std::pair<int, cudaStream_t>, BWork> g_bws;
 static size_t bt_align(size_t x) { return (x + 255) / 256 * 256; }
 
 struct BLayout {
-    size_t ctl, keys, vals, tiles, big, total;
+    size_t ctl, keys, vals, tiles, big, redo;
+    size_t seg_nb, seg_bbase, seg_lo, seg_scale, seg_tbase, rt_base, totals;
+    size_t bcount, bcur, bstart, blen, bu, bv, bi, kP, vP, cu, cv, ci, clen, counters;
+    size_t zero_from, zero_to;   // bucket counters: cleared before each batch
+    size_t total;
+    unsigned bcap, tcap;
 };
 
-static BLayout bt_layout(long long total, int k) {
+// big_pts: points of the sets that can exceed one block (more than kMidCap
+// points), big_sets: how many; they bound the buckets and chain tiles.
+static BLayout bt_layout(long long total, int k, long long big_pts, long long big_sets) {
     BLayout L;
     const long long cap = total + 16ll * k + 16;
-    L.ctl = 0;
-    L.keys = bt_align(L.ctl + sizeof(Ctl) * (size_t)k);
-    L.vals = bt_align(L.keys + sizeof(uint32_t) * (size_t)cap);
-    L.tiles = bt_align(L.vals + sizeof(uint64_t) * (size_t)cap);
-    L.big = bt_align(L.tiles + sizeof(int) * ((size_t)k + 1));
-    L.total = bt_align(L.big + (size_t)k);
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t r = o;
+        o = bt_align(o + bytes);
+        return r;
+    };
+    const size_t nseg = 4 * (size_t)k;
+    L.bcap = (unsigned)((big_pts + 16 * big_sets) / kBkAvg + big_sets * (4 * kBkMinQ + 4) + 8);
+    L.tcap = L.bcap / kBkGroup + (unsigned)(4 * big_sets) + 8;
+    L.ctl = take(sizeof(Ctl) * (size_t)k);
+    L.keys = take(sizeof(uint32_t) * (size_t)cap);
+    L.vals = take(sizeof(uint64_t) * (size_t)cap);
+    L.tiles = take(sizeof(int) * ((size_t)k + 1));
+    L.big = take((size_t)k);
+    L.redo = take((size_t)k);
+    L.seg_nb = take(4 * nseg);
+    L.seg_bbase = take(4 * (nseg + 1));
+    L.seg_lo = take(4 * nseg);
+    L.seg_scale = take(4 * nseg);
+    L.seg_tbase = take(4 * (nseg + 1));
+    L.rt_base = take(4 * ((size_t)k + 1));
+    L.totals = take(4 * 8);
+    // Cleared before every batch: bucket counters and the merge tree's
+    // arrival counters (the layout moves with the batch's sizes, so memory
+    // that held other data last time can land here).
+    L.zero_from = o;
+    L.bcount = take(4 * (size_t)L.bcap);
+    L.bcur = take(4 * (size_t)L.bcap);
+    L.counters = take(4 * (size_t)kMaxLevels * L.tcap);
+    L.zero_to = o;
+    L.bstart = take(4 * (size_t)L.bcap);
+    L.blen = take(4 * (size_t)L.bcap);
+    L.bu = take(4 * (size_t)L.bcap * kBkChain);
+    L.bv = take(4 * (size_t)L.bcap * kBkChain);
+    L.bi = take(4 * (size_t)L.bcap * kBkChain);
+    L.kP = take(sizeof(uint32_t) * (size_t)cap);
+    L.vP = take(sizeof(uint64_t) * (size_t)cap);
+    L.cu = take(4 * (size_t)L.tcap * kChainTile);
+    L.cv = take(4 * (size_t)L.tcap * kChainTile);
+    L.ci = take(4 * (size_t)L.tcap * kChainTile);
+    L.clen = take(4 * (size_t)L.tcap);
+    L.total = o;
     return L;
 }
 
-static int bt_workspace(int dev, cudaStream_t s, long long total, int k, char** base, BLayout* L) {
+static int bt_workspace(int dev, cudaStream_t s, long long total, int k, long long big_pts, long long big_sets,
+                        char** base, BLayout* L) {
     std::lock_guard<std::mutex> lk(g_bmu);
-    *L = bt_layout(total, k);
+    *L = bt_layout(total, k, big_pts, big_sets);
     BWork& w = g_bws[std::make_pair(dev, s)];
     if (w.bytes < L->total) {
         if (w.base) {
@@ -383,7 +442,7 @@ static int bt_workspace(int dev, cudaStream_t s, long long total, int k, char** 
 int reserve_batched(int dev, cudaStream_t s, long long n, int k) {
     char* base = nullptr;
     BLayout L;
-    return bt_workspace(dev, s, n, std::max(k, 1), &base, &L);
+    return bt_workspace(dev, s, n, std::max(k, 1), n, std::max(k, 1), &base, &L);
 }
 
 void release_batched() {
@@ -405,6 +464,7 @@ static int bt_configure(int dev, int* sms) {
     if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return CH_ECUDA;
     if (cudaFuncSetAttribute(bt_hull, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBHullSmem) != cudaSuccess)
         return CH_ECUDA;
+    if (configure_batched_large() != cudaSuccess) return CH_ECUDA;
     done[dev] = n;
     *sms = n;
     return CH_OK;
@@ -430,10 +490,14 @@ extern "C" int ch_hull_batched(const float* pts, const int64_t* offsets, int32_t
         if (cudaStreamSynchronize(s) != cudaSuccess) return CH_ECUDA;
     }
     if (off[0] != 0) return CH_EINVAL;
-    long long tiles = 0;
+    long long tiles = 0, big_pts = 0, big_sets = 0;
     for (int i = 0; i < k; ++i) {
         if (off[i + 1] < off[i] || off[i + 1] - off[i] > CH_MAX_POINTS) return CH_EINVAL;
         tiles += (off[i + 1] - off[i] + kBTile - 1) / kBTile;
+        if (off[i + 1] - off[i] + 12 > kMidCap) {
+            big_pts += off[i + 1] - off[i];
+            ++big_sets;
+        }
     }
     if (tiles > INT32_MAX) return CH_EINVAL;
     const int64_t total = off[k];
@@ -445,7 +509,7 @@ extern "C" int ch_hull_batched(const float* pts, const int64_t* offsets, int32_t
     if ((st = bt_configure(dev, &sms)) != CH_OK) return st;
     char* base = nullptr;
     BLayout L;
-    if ((st = bt_workspace(dev, s, total, k, &base, &L)) != CH_OK) return st;
+    if ((st = bt_workspace(dev, s, total, k, big_pts, big_sets, &base, &L)) != CH_OK) return st;
     BArgs a;
     a.pts = pts;
     a.offsets = offsets;
@@ -474,10 +538,49 @@ extern "C" int ch_hull_batched(const float* pts, const int64_t* offsets, int32_t
         bt_filter<<<grid_t, kBThreads, 0, s>>>(a, nt);
     }
     { ProfScope p("batched_hull", s); bt_hull<<<k, kBHullThreads, kBHullSmem, s>>>(a); }
+    // Sets with more records than one block holds: all together through the
+    // bucketed path.
+    BLArgs b;
+    b.pts = pts;
+    b.offsets = offsets;
+    b.k = k;
+    b.ctl = a.ctl;
+    b.keys = a.keys;
+    b.vals = a.vals;
+    b.big = a.big;
+    b.out_idx = out_idx;
+    b.out_n = out_n;
+    b.seg_nb = (unsigned*)(base + L.seg_nb);
+    b.seg_bbase = (unsigned*)(base + L.seg_bbase);
+    b.seg_lo = (int*)(base + L.seg_lo);
+    b.seg_scale = (float*)(base + L.seg_scale);
+    b.seg_tbase = (unsigned*)(base + L.seg_tbase);
+    b.rt_base = (unsigned*)(base + L.rt_base);
+    b.totals = (unsigned*)(base + L.totals);
+    b.bcount = (unsigned*)(base + L.bcount);
+    b.bcur = (unsigned*)(base + L.bcur);
+    b.bstart = (unsigned*)(base + L.bstart);
+    b.blen = (int*)(base + L.blen);
+    b.bu = (int*)(base + L.bu);
+    b.bv = (int*)(base + L.bv);
+    b.bi = (int*)(base + L.bi);
+    b.kP = (uint32_t*)(base + L.kP);
+    b.vP = (uint64_t*)(base + L.vP);
+    b.cu = (int*)(base + L.cu);
+    b.cv = (int*)(base + L.cv);
+    b.ci = (int*)(base + L.ci);
+    b.clen = (int*)(base + L.clen);
+    b.counters = (int*)(base + L.counters);
+    b.bcap = L.bcap;
+    b.tcap = L.tcap;
+    unsigned char* redo = (unsigned char*)(base + L.redo);
+    if (cudaMemsetAsync(base + L.zero_from, 0, L.zero_to - L.zero_from, s) != cudaSuccess) return CH_ECUDA;
+    launch_batched_large(b, redo, sms, s);
     if (cudaGetLastError() != cudaSuccess) return CH_ECUDA;
-    // Sets with more records than one block holds: the single-hull path.
+    // Sets the bucketed path could not finish (a bucket chain too long): the
+    // single-hull path, one by one.
     std::vector<unsigned char> big((size_t)k);
-    if (cudaMemcpyAsync(big.data(), a.big, (size_t)k, cudaMemcpyDeviceToHost, s) != cudaSuccess) return CH_ECUDA;
+    if (cudaMemcpyAsync(big.data(), redo, (size_t)k, cudaMemcpyDeviceToHost, s) != cudaSuccess) return CH_ECUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return CH_ECUDA;
     for (int i = 0; i < k; ++i) {
         if (!big[i]) continue;

@@ -22,14 +22,12 @@
 #include "hullcore.cuh"
 #include "host.h"
 #include "launch.h"
+#include "bkwarp.cuh"
 
 #include <climits>
 
 namespace ch {
 
-constexpr int kBkPer = 9;               // records per lane
-constexpr int kBkWCap = 32 * kBkPer;    // records a warp holds at once
-constexpr int kBkV = kBkChain + 2;      // quickhull vertices of one bucket
 constexpr int kBkWarps = 8;             // warps per bk_hull block
 constexpr int kBkAllocThreads = 1024;
 constexpr int kBkUnroll = 8;            // records per thread and step (hist, scatter)
@@ -77,8 +75,7 @@ __global__ void bk_prep(Ctl* ctl, unsigned* bcount, unsigned* bcur, unsigned bma
     if (tid == 0) {
         s_base[0] = 0u;
         for (int r = 0; r < 4; ++r) {
-            const unsigned nb = (s_q[r] + kBkAvg - 1) / kBkAvg;
-            s_base[r + 1] = s_base[r] + (nb > 0u ? nb : 1u);
+            s_base[r + 1] = s_base[r] + bk_buckets_for(s_q[r]);
         }
     }
     __syncthreads();
@@ -208,159 +205,6 @@ __global__ void __launch_bounds__(256) bk_scatter(Ctl* ctl, const uint32_t* kin,
 }
 
 // ---------------------------------------------------------------------------
-// One warp's quickhull over m <= kBkWCap records of one queue frame: the
-// lower chain from S (minimum u, v, index) to E (maximum u, then minimum v,
-// index); the same rounds and tie rules as qh_chains, synchronised within the
-// warp only.  The records live in registers (slot k of lane l is record
-// 32 k + l), so a round's loads are only of the few chain vertices.
-struct BkWarp {   // shared memory of one warp: the chain under construction
-    unsigned long long segmax[kBkV], segarg[kBkV];
-    int vu[kBkV], vv[kBkV], vi[kBkV], vnext[kBkV], splitu[kBkV], child[kBkV];
-    int cu[kBkV], cv[kBkV], ci[kBkV];   // the finished chain in order
-};
-
-struct BkRecs {
-    int u[kBkPer], v[kBkPer], i[kBkPer], s[kBkPer];
-};
-
-__device__ __forceinline__ long long bk_depth(const BkWarp& w, int a, int b, int u, int v) {
-    return (long long)(w.vv[b] - w.vv[a]) * (u - w.vu[a]) - (long long)(w.vu[b] - w.vu[a]) * (v - w.vv[a]);
-}
-
-// Returns the chain length, its vertices in order in w.cu / cv / ci; -1 when
-// the chain would exceed kBkV vertices.
-__device__ int bk_warp_chain(BkWarp& w, BkRecs& R, int m) {
-    const int lane = threadIdx.x & 31;
-    constexpr unsigned long long kVMask = (1ull << kKeyBits) - 1ull;
-    unsigned long long ks = ~0ull, ke = 0ull;
-#pragma unroll
-    for (int k = 0; k < kBkPer; ++k) {
-        if (k * 32 + lane < m) {
-            const unsigned long long a = ((unsigned long long)R.u[k] << kKeyBits) | (unsigned)R.v[k];
-            const unsigned long long b = ((unsigned long long)R.u[k] << kKeyBits) | (kVMask - (unsigned)R.v[k]);
-            ks = a < ks ? a : ks;
-            ke = b > ke ? b : ke;
-        }
-    }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-        const unsigned long long a = __shfl_xor_sync(0xFFFFFFFFu, ks, o), b = __shfl_xor_sync(0xFFFFFFFFu, ke, o);
-        ks = a < ks ? a : ks;
-        ke = b > ke ? b : ke;
-    }
-    unsigned is = 0xFFFFFFFFu, ie = 0xFFFFFFFFu;
-#pragma unroll
-    for (int k = 0; k < kBkPer; ++k) {
-        if (k * 32 + lane < m) {
-            const unsigned long long a = ((unsigned long long)R.u[k] << kKeyBits) | (unsigned)R.v[k];
-            const unsigned long long b = ((unsigned long long)R.u[k] << kKeyBits) | (kVMask - (unsigned)R.v[k]);
-            if (a == ks) is = min(is, (unsigned)R.i[k]);
-            if (b == ke) ie = min(ie, (unsigned)R.i[k]);
-        }
-    }
-    is = __reduce_min_sync(0xFFFFFFFFu, is);
-    ie = __reduce_min_sync(0xFFFFFFFFu, ie);
-    const int su = (int)(ks >> kKeyBits), eu = (int)(ke >> kKeyBits);
-    for (int a = lane; a < kBkV; a += 32) {
-        w.segmax[a] = 0ull;
-        w.segarg[a] = ~0ull;
-        w.splitu[a] = -1;
-    }
-    if (lane == 0) {
-        w.vu[0] = su;
-        w.vv[0] = (int)(ks & kVMask);
-        w.vi[0] = (int)is;
-        w.vu[1] = eu;
-        w.vv[1] = (int)(kVMask - (ke & kVMask));
-        w.vi[1] = (int)ie;
-        w.vnext[0] = su < eu ? 1 : -1;
-        w.vnext[1] = -1;
-    }
-#pragma unroll
-    for (int k = 0; k < kBkPer; ++k)
-        R.s[k] = (k * 32 + lane < m && su < R.u[k] && R.u[k] < eu) ? 0 : -1;
-    __syncwarp();
-    int nv = 2;
-    for (int round = 0;; ++round) {
-        // depths; each segment's maximum
-#pragma unroll
-        for (int k = 0; k < kBkPer; ++k) {
-            int a = R.s[k];
-            if (a >= 0) {
-                const int sp = w.splitu[a];
-                if (sp >= 0) {
-                    if (R.u[k] > sp) a = w.child[a];
-                    else if (R.u[k] == sp) a = -1;
-                }
-                const int b = a >= 0 ? w.vnext[a] : -1;
-                if (b < 0) {
-                    a = -1;
-                } else {
-                    const long long d = bk_depth(w, a, b, R.u[k], R.v[k]);
-                    if (d <= 0) a = -1;
-                    else if ((unsigned long long)d > *(volatile unsigned long long*)&w.segmax[a])
-                        atomicMax(&w.segmax[a], (unsigned long long)d);
-                }
-                R.s[k] = a;
-            }
-        }
-        __syncwarp();
-        // the deepest record per segment: smallest u, then index
-#pragma unroll
-        for (int k = 0; k < kBkPer; ++k) {
-            const int a = R.s[k];
-            if (a >= 0 && (unsigned long long)bk_depth(w, a, w.vnext[a], R.u[k], R.v[k]) == w.segmax[a])
-                atomicMin(&w.segarg[a], ((unsigned long long)R.u[k] << 31) | (unsigned)R.i[k]);
-        }
-        __syncwarp();
-        int added = 0;
-        bool over = false;
-        for (int a0 = 0; a0 < nv; a0 += 32) {
-            const int a = a0 + lane;
-            const unsigned long long dm = a < nv ? w.segmax[a] : 0ull;
-            const bool split = dm != 0ull;
-            const unsigned bal = __ballot_sync(0xFFFFFFFFu, split);
-            if (a < nv) w.splitu[a] = -1;
-            if (split) {
-                const int f = nv + added + __popc(bal & lanemask_lt());
-                if (f < kBkV) {
-                    const int b = w.vnext[a];
-                    const unsigned long long key = w.segarg[a];
-                    const int fu = (int)(key >> 31), fi = (int)(key & 0x7FFFFFFFull);
-                    const long long num = (long long)(w.vv[b] - w.vv[a]) * (fu - w.vu[a]) - (long long)dm;
-                    w.vu[f] = fu;
-                    w.vv[f] = w.vv[a] + (int)(num / (long long)(w.vu[b] - w.vu[a]));
-                    w.vi[f] = fi;
-                    w.vnext[f] = b;
-                    w.vnext[a] = f;
-                    w.child[a] = f;
-                    w.splitu[a] = fu;
-                } else {
-                    over = true;
-                }
-                w.segmax[a] = 0ull;
-                w.segarg[a] = ~0ull;
-            }
-            added += __popc(bal);
-        }
-        if (__any_sync(0xFFFFFFFFu, over)) return -1;
-        __syncwarp();
-        if (added == 0) break;
-        nv += added;
-        if (round + 1 >= kBkV) return -1;
-    }
-    int len = 0;
-    if (lane == 0)
-        for (int a = 0; a >= 0 && len < kBkV; a = w.vnext[a], ++len) {
-            w.cu[len] = w.vu[a];
-            w.cv[len] = w.vv[a];
-            w.ci[len] = w.vi[a];
-        }
-    len = __shfl_sync(0xFFFFFFFFu, len, 0);
-    __syncwarp();
-    return len;
-}
-
 __global__ void __launch_bounds__(kBkWarps * 32) bk_hull(Ctl* ctl, const uint32_t* keys, const uint64_t* vals,
                                                         const unsigned* bstart, const unsigned* bcount,
                                                         int* bu, int* bv, int* bi, int* blen) {
@@ -377,39 +221,8 @@ __global__ void __launch_bounds__(kBkWarps * 32) bk_hull(Ctl* ctl, const uint32_
     BkWarp& w = s_w[warp];
     const unsigned nwarps = gridDim.x * kBkWarps;
     for (unsigned b = blockIdx.x * kBkWarps + warp; b < s_nb; b += nwarps) {
-        const unsigned start = bstart[b], cnt = bcount[b];
-        int len = 0;   // chain vertices carried into the next chunk (w.cu / cv / ci)
-        bool fail = false;
-        for (unsigned c0 = 0; c0 < cnt;) {
-            const unsigned take = min(cnt - c0, (unsigned)(kBkWCap - len));
-            const int m = len + (int)take;
-            BkRecs R;
-#pragma unroll
-            for (int k = 0; k < kBkPer; ++k) {
-                const int j = k * 32 + lane;
-                R.u[k] = 0;
-                R.v[k] = 0;
-                R.i[k] = 0;
-                if (j < len) {
-                    R.u[k] = w.cu[j];
-                    R.v[k] = w.cv[j];
-                    R.i[k] = w.ci[j];
-                } else if (j < m) {
-                    const unsigned g = start + c0 + (unsigned)(j - len);
-                    const uint32_t kk = __ldcs(keys + g);
-                    const uint64_t vv = __ldcs(vals + g);
-                    R.u[k] = (int)(kk & kKeyMask);
-                    R.v[k] = (int)(vv >> 31);
-                    R.i[k] = (int)(vv & 0x7FFFFFFFull);
-                }
-            }
-            __syncwarp();
-            const int l2 = bk_warp_chain(w, R, m);
-            if (l2 < 0 || l2 > kBkChain) { fail = true; break; }
-            len = l2;
-            c0 += take;
-        }
-        if (fail) {
+        int len = bk_bucket_chain(w, keys, vals, bstart[b], bcount[b]);
+        if (len < 0) {
             if (lane == 0) ctl->bk_state = 2;   // the sort-based path takes over
             len = 0;
         }

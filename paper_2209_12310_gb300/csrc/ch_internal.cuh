@@ -43,6 +43,18 @@ constexpr int kMergeSmemCap = 8192;           // chain points a global merge kee
 constexpr int kBkAvg = 256;
 constexpr int kBkChain = 32;
 constexpr int kBkGroup = kChainTile / kBkChain;
+// At least this many buckets per queue (at most one per 8 records): a queue's
+// u-range cut this finely makes each bucket a nearly straight strip of the
+// hull boundary even for sets of a few thousand points on a circle, so
+// bucket chains stay short.
+constexpr int kBkMinQ = 1024;
+
+__host__ __device__ __forceinline__ unsigned bk_buckets_for(unsigned cnt) {
+    unsigned nb = (cnt + kBkAvg - 1) / kBkAvg;
+    const unsigned lo = (cnt / 8u < (unsigned)kBkMinQ) ? cnt / 8u : (unsigned)kBkMinQ;
+    nb = nb > lo ? nb : lo;
+    return nb > 0u ? nb : 1u;
+}
 constexpr int kSampleTiles = 1024;            // warp tiles read by the sample pass (512k points)
 constexpr int kMaxLevels = 32;
 

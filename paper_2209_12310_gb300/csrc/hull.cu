@@ -24,53 +24,11 @@
 #include "ch_internal.cuh"
 #include "hullcore.cuh"
 #include "launch.h"
+#include "merge.cuh"
 
 #include <climits>
 
 namespace ch {
-
-// Block-cooperative bridge: repeated 256-way probing of the monotone keep
-// predicates (each probe is a sequential binary search over the other chain).
-template <bool kGlobal>
-__device__ void bridge_block(const ChainPtr& A, int la, const ChainPtr& B, int lb, int& is, int& js,
-                             int* s_red) {
-    const int T = blockDim.x;
-    // A: largest k with keep_a(k); predicate true on [0, is]
-    int lo = 0, hi = la - 1;
-    while (lo < hi) {
-        const long long span = (long long)hi - lo;
-        const int k = lo + 1 + (int)(span * threadIdx.x / T);   // probes in (lo, hi]
-        const bool ok = (k <= hi) && keep_a<kGlobal>(A, k, B, lb);
-        if (threadIdx.x == 0) { s_red[0] = lo; s_red[1] = hi; }
-        __syncthreads();
-        if (k <= hi) {
-            if (ok) atomicMax(&s_red[0], k);
-            else atomicMin(&s_red[1], k - 1);
-        }
-        __syncthreads();
-        const int nlo = s_red[0], nhi = s_red[1];
-        __syncthreads();
-        lo = nlo; hi = max(nhi, nlo);
-    }
-    is = lo;
-    lo = 0; hi = lb - 1;   // smallest l with keep_b(l); true on [js, lb-1]
-    while (lo < hi) {
-        const long long span = (long long)hi - lo;
-        const int l = lo + (int)(span * threadIdx.x / T);       // probes in [lo, hi)
-        const bool ok = (l < hi) && keep_b<kGlobal>(A, la, B, l, lb);
-        if (threadIdx.x == 0) { s_red[0] = lo; s_red[1] = hi; }
-        __syncthreads();
-        if (l < hi) {
-            if (ok) atomicMin(&s_red[1], l);
-            else atomicMax(&s_red[0], l + 1);
-        }
-        __syncthreads();
-        const int nlo = s_red[0], nhi = s_red[1];
-        __syncthreads();
-        hi = nhi; lo = min(nlo, nhi);
-    }
-    js = lo;
-}
 
 // ---------------------------------------------------------------------------
 struct HullBufs {
@@ -95,19 +53,6 @@ struct HullBufs {
     int32_t* out_idx;
     int64_t* out_n;
 };
-
-// Block-wide forward copy of n entries, dst <= src (possibly overlapping),
-// in chunks fully loaded before they are stored.
-__device__ void copy_down(int* du, int* dv, int* di, const int* su, const int* sv, const int* si, int n) {
-    for (int base = 0; base < n; base += blockDim.x) {
-        const int j = base + threadIdx.x;
-        int a = 0, b = 0, c = 0;
-        if (j < n) { a = __ldcg(su + j); b = __ldcg(sv + j); c = __ldcg(si + j); }
-        __syncthreads();
-        if (j < n) { du[j] = a; dv[j] = b; di[j] = c; }
-        __syncthreads();
-    }
-}
 
 __global__ void __launch_bounds__(kChainThreads) chain_kernel(Ctl* ctl, HullBufs hb) {
     extern __shared__ int smem[];
@@ -217,116 +162,8 @@ __global__ void __launch_bounds__(kChainThreads) chain_kernel(Ctl* ctl, HullBufs
         }
         }
         __syncthreads();
-        // 2) pairwise merge of the tile's leaf chains: the bridge of each pair
-        //    by its leader thread, then the kept part of the right chain moved
-        //    down by one warp per pair (a left shift, copied forward in chunks
-        //    of 32, never overwrites entries still to be read).
-        for (int l = 0; (1 << l) < nseg; ++l) {
-            const int g = 1 << l;
-            const int npairs = nseg >> (l + 1);
-            if (tid < nseg && (tid & (2 * g - 1)) == 0) {
-                const int b = tid + g, la = s_len[tid], lb = s_len[b];
-                int dst = tid * seg, src = b * seg, cnt = 0, len = la;
-                if (lb > 0) {
-                    if (la == 0) {
-                        cnt = lb;
-                        len = lb;
-                    } else {
-                        ChainPtr A{su + tid * seg, sv + tid * seg, si + tid * seg};
-                        ChainPtr B{su + b * seg, sv + b * seg, si + b * seg};
-                        int is, js;
-                        bridge_seq<false>(A, la, B, lb, is, js);
-                        dst += is + 1;
-                        src += js;
-                        cnt = lb - js;
-                        len = is + 1 + cnt;
-                    }
-                }
-                const int p = tid / (2 * g);
-                s_mv[p][0] = dst;
-                s_mv[p][1] = src;
-                s_mv[p][2] = cnt;
-                s_len[tid] = len;
-            }
-            __syncthreads();
-            const int lane = tid & 31;
-            for (int p = tid >> 5; p < npairs; p += kChainThreads / 32) {
-                const int dst = s_mv[p][0], src = s_mv[p][1], cnt = s_mv[p][2];
-                if (dst == src) continue;
-                for (int c = 0; c < cnt; c += 32) {
-                    const int j = c + lane;
-                    int a = 0, b2 = 0, d = 0;
-                    if (j < cnt) { a = su[src + j]; b2 = sv[src + j]; d = si[src + j]; }
-                    __syncwarp();
-                    if (j < cnt) { su[dst + j] = a; sv[dst + j] = b2; si[dst + j] = d; }
-                    __syncwarp();
-                }
-            }
-            __syncthreads();
-        }
-        // 3) write the tile chain.
-        const int len = s_len[0];
-        {
-            const size_t o = (size_t)c * kChainTile;
-            for (int j = tid; j < len; j += blockDim.x) {
-                hb.cu[o + j] = su[j]; hb.cv[o + j] = sv[j]; hb.ci[o + j] = si[j];
-            }
-            if (tid == 0) hb.clen[c] = len;
-        }
-        // 4) climb the merge tree of queue r.
-        unsigned L = 0, k = t_local;
-        bool root = false;
-        for (;;) {
-            if (k == 0 && (1u << L) >= ct) { root = true; break; }   // root of queue r
-            const unsigned sib = k ^ 1u;
-            if ((sib << L) >= ct) { ++L; k >>= 1; continue; }  // no sibling: pass through
-            __threadfence();
-            __syncthreads();
-            if (tid == 0)
-                s_old = atomicAdd(&hb.counters[(size_t)L * hb.ctcap + rb + ((k >> 1) << (L + 1))], 1);
-            __syncthreads();
-            if (s_old == 0) break;                              // sibling merges later
-            __threadfence();
-            const unsigned left = rb + ((k & ~1u) << L), right = rb + ((k | 1u) << L);
-            const int la = __ldcg(hb.clen + left), lb = __ldcg(hb.clen + right);
-            const size_t oa = (size_t)left * kChainTile, ob = (size_t)right * kChainTile;
-            int is, js;
-            if (lb == 0) {
-                // nothing to add
-            } else if (la == 0) {
-                copy_down(hb.cu + oa, hb.cv + oa, hb.ci + oa, hb.cu + ob, hb.cv + ob, hb.ci + ob, lb);
-                if (tid == 0) hb.clen[left] = lb;
-            } else if (la + lb <= kMergeSmemCap) {
-                for (int j = tid; j < la; j += blockDim.x) {
-                    su[j] = __ldcg(hb.cu + oa + j); sv[j] = __ldcg(hb.cv + oa + j); si[j] = __ldcg(hb.ci + oa + j);
-                }
-                for (int j = tid; j < lb; j += blockDim.x) {
-                    su[la + j] = __ldcg(hb.cu + ob + j); sv[la + j] = __ldcg(hb.cv + ob + j);
-                    si[la + j] = __ldcg(hb.ci + ob + j);
-                }
-                __syncthreads();
-                ChainPtr A{su, sv, si}, B{su + la, sv + la, si + la};
-                bridge_block<false>(A, la, B, lb, is, js, s_red);
-                const int n = lb - js;
-                for (int j = tid; j < n; j += blockDim.x) {
-                    hb.cu[oa + is + 1 + j] = su[la + js + j];
-                    hb.cv[oa + is + 1 + j] = sv[la + js + j];
-                    hb.ci[oa + is + 1 + j] = si[la + js + j];
-                }
-                if (tid == 0) hb.clen[left] = is + 1 + n;
-            } else {
-                ChainPtr A{hb.cu + oa, hb.cv + oa, hb.ci + oa}, B{hb.cu + ob, hb.cv + ob, hb.ci + ob};
-                bridge_block<true>(A, la, B, lb, is, js, s_red);
-                const int n = lb - js;
-                copy_down(hb.cu + oa + is + 1, hb.cv + oa + is + 1, hb.ci + oa + is + 1,
-                          hb.cu + ob + js, hb.cv + ob + js, hb.ci + ob + js, n);
-                if (tid == 0) hb.clen[left] = is + 1 + n;
-            }
-            if (tid == 0) hb.counters[(size_t)L * hb.ctcap + rb + ((k >> 1) << (L + 1))] = 0;
-            __syncthreads();
-            ++L;
-            k >>= 1;
-        }
+        const TreeBufs tb{hb.cu, hb.cv, hb.ci, hb.clen, hb.counters, hb.ctcap};
+        const bool root = tile_merge_climb(su, sv, si, s_len, s_mv, seg, nseg, tb, c, rb, ct, t_local, s_red, &s_old);
         __syncthreads();
         if (!root) continue;
         // 5) the block completing the fourth queue root joins the chains.
