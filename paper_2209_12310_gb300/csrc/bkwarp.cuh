@@ -38,6 +38,7 @@ static __device__ int bk_warp_chain(BkWarp& w, BkRecs& R, int m) {
     unsigned long long ks = ~0ull, ke = 0ull;
 #pragma unroll
     for (int k = 0; k < kBkPer; ++k) {
+        if (k * 32 >= m) break;   // warp-uniform: slots past the records
         if (k * 32 + lane < m) {
             const unsigned long long a = ((unsigned long long)R.u[k] << kKeyBits) | (unsigned)R.v[k];
             const unsigned long long b = ((unsigned long long)R.u[k] << kKeyBits) | (kVMask - (unsigned)R.v[k]);
@@ -54,6 +55,7 @@ static __device__ int bk_warp_chain(BkWarp& w, BkRecs& R, int m) {
     unsigned is = 0xFFFFFFFFu, ie = 0xFFFFFFFFu;
 #pragma unroll
     for (int k = 0; k < kBkPer; ++k) {
+        if (k * 32 >= m) break;
         if (k * 32 + lane < m) {
             const unsigned long long a = ((unsigned long long)R.u[k] << kKeyBits) | (unsigned)R.v[k];
             const unsigned long long b = ((unsigned long long)R.u[k] << kKeyBits) | (kVMask - (unsigned)R.v[k]);
@@ -88,6 +90,7 @@ static __device__ int bk_warp_chain(BkWarp& w, BkRecs& R, int m) {
         // depths; each segment's maximum
 #pragma unroll
         for (int k = 0; k < kBkPer; ++k) {
+            if (k * 32 >= m) break;
             int a = R.s[k];
             if (a >= 0) {
                 const int sp = w.splitu[a];
@@ -111,6 +114,7 @@ static __device__ int bk_warp_chain(BkWarp& w, BkRecs& R, int m) {
         // the deepest record per segment: smallest u, then index
 #pragma unroll
         for (int k = 0; k < kBkPer; ++k) {
+            if (k * 32 >= m) break;
             const int a = R.s[k];
             if (a >= 0 && (unsigned long long)bk_depth(w, a, w.vnext[a], R.u[k], R.v[k]) == w.segmax[a])
                 atomicMin(&w.segarg[a], ((unsigned long long)R.u[k] << 31) | (unsigned)R.i[k]);
@@ -165,12 +169,13 @@ static __device__ int bk_warp_chain(BkWarp& w, BkRecs& R, int m) {
 }
 
 
-// The lower chain of bucket records [start, start + cnt) (one queue frame) by
-// one warp, kBkWCap records at a time: each chunk's chain is carried into the
-// next chunk as records.  Returns its length (<= kBkChain, the chain in
-// w.cu / cv / ci), or -1 when it has more than kBkChain vertices.
-__device__ __forceinline__ int bk_bucket_chain(BkWarp& w, const uint32_t* keys, const uint64_t* vals,
-                                               unsigned start, unsigned cnt) {
+// The lower chain of a stream of cnt records (one queue frame) by one warp,
+// kBkWCap records at a time: each chunk's chain is carried into the next
+// chunk as records.  load(j, u, v, i) reads record j of the stream.  Returns
+// the chain's length (<= kBkChain, the chain in w.cu / cv / ci), or -1 when
+// it has more than kBkChain vertices.
+template <typename Load>
+__device__ __forceinline__ int bk_stream_chain(BkWarp& w, unsigned cnt, Load load) {
     const int lane = threadIdx.x & 31;
     int len = 0;
     for (unsigned c0 = 0; c0 < cnt;) {
@@ -188,12 +193,7 @@ __device__ __forceinline__ int bk_bucket_chain(BkWarp& w, const uint32_t* keys, 
                 R.v[k] = w.cv[j];
                 R.i[k] = w.ci[j];
             } else if (j < m) {
-                const unsigned g = start + c0 + (unsigned)(j - len);
-                const uint32_t kk = __ldcs(keys + g);
-                const uint64_t vv = __ldcs(vals + g);
-                R.u[k] = (int)(kk & kKeyMask);
-                R.v[k] = (int)(vv >> 31);
-                R.i[k] = (int)(vv & 0x7FFFFFFFull);
+                load(c0 + (unsigned)(j - len), R.u[k], R.v[k], R.i[k]);
             }
         }
         __syncwarp();
@@ -203,6 +203,18 @@ __device__ __forceinline__ int bk_bucket_chain(BkWarp& w, const uint32_t* keys, 
         c0 += take;
     }
     return len;
+}
+
+// The lower chain of bucket records [start, start + cnt) of keys / vals.
+__device__ __forceinline__ int bk_bucket_chain(BkWarp& w, const uint32_t* keys, const uint64_t* vals,
+                                               unsigned start, unsigned cnt) {
+    return bk_stream_chain(w, cnt, [&](unsigned j, int& u, int& v, int& i) {
+        const uint32_t kk = __ldcs(keys + start + j);
+        const uint64_t vv = __ldcs(vals + start + j);
+        u = (int)(kk & kKeyMask);
+        v = (int)(vv >> 31);
+        i = (int)(vv & 0x7FFFFFFFull);
+    });
 }
 
 }  // namespace ch
