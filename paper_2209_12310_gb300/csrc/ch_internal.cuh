@@ -47,7 +47,7 @@ constexpr int kBkGroup = kChainTile / kBkChain;
 // u-range cut this finely makes each bucket a nearly straight strip of the
 // hull boundary even for sets of a few thousand points on a circle, so
 // bucket chains stay short.
-constexpr int kBkMinQ = 1024;
+constexpr int kBkMinQ = 256;
 
 __host__ __device__ __forceinline__ unsigned bk_buckets_for(unsigned cnt) {
     unsigned nb = (cnt + kBkAvg - 1) / kBkAvg;
