@@ -46,6 +46,7 @@ struct BArgs {
     uint32_t* keys;           // records: set i's region starts at offsets[i] + 16 i
     uint64_t* vals;
     int* tile_base;           // k + 1: first tile of each set
+    int* tile_map;            // set of every tile
     int32_t* out_idx;
     int64_t* out_n;
     unsigned char* big;       // k: the set needs the single-hull path
@@ -53,15 +54,8 @@ struct BArgs {
 
 __device__ __forceinline__ long long region_base(const BArgs& a, int i) { return a.offsets[i] + 16ll * i; }
 
-// Set of tile t: the last i with tile_base[i] <= t.
-__device__ __forceinline__ int tile_set(const BArgs& a, int t) {
-    int lo = 0, hi = a.k - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (a.tile_base[mid] <= t) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
+// Set of tile t (written by bt_scan).
+__device__ __forceinline__ int tile_set(const BArgs& a, int t) { return a.tile_map[t]; }
 
 __global__ void bt_init(BArgs a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -86,8 +80,8 @@ __global__ void bt_init(BArgs a) {
 }
 
 // Exclusive prefix of the tile counts in place (one block of 1024 threads);
-// tile_base[k] = total tiles.
-__global__ void __launch_bounds__(1024) bt_scan(int* tile_base, int k) {
+// tile_base[k] = total tiles; then the set of every tile.
+__global__ void __launch_bounds__(1024) bt_scan(int* tile_base, int* tile_map, int k) {
     __shared__ int s_part[1024];
     const int tid = threadIdx.x;
     const int per = (k + 1023) / 1024;
@@ -106,6 +100,7 @@ __global__ void __launch_bounds__(1024) bt_scan(int* tile_base, int k) {
     for (int i = lo; i < hi; ++i) {
         const int c = tile_base[i];
         tile_base[i] = run;
+        for (int t = 0; t < c; ++t) tile_map[run + t] = i;
         run += c;
     }
     if (tid == 1023) tile_base[k] = s_part[1023];
@@ -113,61 +108,121 @@ __global__ void __launch_bounds__(1024) bt_scan(int* tile_base, int k) {
 
 __device__ __forceinline__ bool bt_dir_is_max(int d) { return d >= SE && d <= N; }
 
-__device__ __forceinline__ unsigned long long bt_pack(int d, int X, int Y, unsigned idx) {
-    int k;
+__device__ __forceinline__ int bt_key(int d, int X, int Y) {
     switch (d) {
-        case W: case E: k = X; break;
-        case S: case N: k = Y; break;
-        case SW: case NE: k = X + Y; break;
-        default: k = X - Y + kCoordLimit; break;
+        case W: case E: return X;
+        case S: case N: return Y;
+        case SW: case NE: return X + Y;
+        default: return X - Y + kCoordLimit;
     }
-    const unsigned hk = bt_dir_is_max(d) ? (unsigned)k : 0xFFFFFFFFu - (unsigned)k;
-    return ((unsigned long long)hk << 32) | (unsigned long long)(0xFFFFFFFFu - idx);
 }
 
+// Three-input max / min of non-negative int keys through their float bit
+// patterns (below 2^26 the patterns are positive finite floats that order
+// like the integers; max.f32 without .ftz keeps subnormals exact).
+__device__ __forceinline__ int bt_max3(int a, int b, int c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(__int_as_float(a)), "f"(__int_as_float(b)), "f"(__int_as_float(c)));
+    return __float_as_int(r);
+}
+__device__ __forceinline__ int bt_min3(int a, int b, int c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(__int_as_float(a)), "f"(__int_as_float(b)), "f"(__int_as_float(c)));
+    return __float_as_int(r);
+}
+
+// Per tile: each thread holds its kBPer points in registers; the block first
+// finds the tile's 8 extreme keys (three-input min / max, two points per
+// instruction), then the lowest index reaching each of them (every thread
+// checks its own points), and one packed (key, lowest index) atomic per
+// direction carries it to the set's maximum.
+constexpr int kBPer = kBTile / kBThreads;   // points per thread and tile
+
 __global__ void __launch_bounds__(kBThreads) bt_extremes(BArgs a, int ntiles) {
-    __shared__ unsigned long long s_red[kBThreads / 32][8];
+    __shared__ int s_key[kBThreads / 32][8];
+    __shared__ int s_best[8];
+    __shared__ unsigned s_idx[8];
     __shared__ int s_set;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         if (tid == 0) s_set = tile_set(a, t);
+        if (tid < 8) s_idx[tid] = 0xFFFFFFFFu;
         __syncthreads();
         const int i = s_set;
         const long long base = a.offsets[i], ni = a.offsets[i + 1] - base;
         const long long p0 = (long long)(t - a.tile_base[i]) * kBTile;
-        const long long p1 = min(ni, p0 + kBTile);
-        const float2* p2 = reinterpret_cast<const float2*>(a.pts) + base;
-        unsigned long long best[8];
+        const int cnt = (int)min((long long)kBTile, ni - p0);   // >= 1
+        const float2* p2 = reinterpret_cast<const float2*>(a.pts) + base + p0;
+        float2 v[kBPer];
 #pragma unroll
-        for (int d = 0; d < 8; ++d) best[d] = 0ull;
+        for (int j = 0; j < kBPer; ++j) {
+            const int q = tid + j * kBThreads;
+            v[j] = __ldcs(p2 + (q < cnt ? q : 0));   // a missing point repeats point 0 of the tile
+        }
+        int tk[8];
         bool bad = false;
-        for (long long p = p0 + tid; p < p1; p += kBThreads) {
-            const float2 v = __ldcs(p2 + p);
-            const int X = __float2int_rn(v.x), Y = __float2int_rn(v.y);
-            bad |= (__int2float_rn(X) != v.x) | (__int2float_rn(Y) != v.y) |
-                   ((((unsigned)X | (unsigned)Y) >> kCoordBits) != 0u);
 #pragma unroll
-            for (int d = 0; d < 8; ++d) {
-                const unsigned long long q = bt_pack(d, X, Y, (unsigned)p);
-                best[d] = q > best[d] ? q : best[d];
+        for (int j = 0; j < kBPer; j += 2) {
+            const int X0 = __float2int_rn(v[j].x), Y0 = __float2int_rn(v[j].y);
+            const int X1 = __float2int_rn(v[j + 1].x), Y1 = __float2int_rn(v[j + 1].y);
+            bad |= (__int2float_rn(X0) != v[j].x) | (__int2float_rn(Y0) != v[j].y) |
+                   (__int2float_rn(X1) != v[j + 1].x) | (__int2float_rn(Y1) != v[j + 1].y) |
+                   (((unsigned)X0 | (unsigned)Y0 | (unsigned)X1 | (unsigned)Y1) >> kCoordBits) != 0u;
+            if (j == 0) {
+#pragma unroll
+                for (int d = 0; d < 8; ++d) {
+                    const int k0 = bt_key(d, X0, Y0), k1 = bt_key(d, X1, Y1);
+                    tk[d] = bt_dir_is_max(d) ? max(k0, k1) : min(k0, k1);
+                }
+            } else {
+#pragma unroll
+                for (int d = 0; d < 8; ++d) {
+                    const int k0 = bt_key(d, X0, Y0), k1 = bt_key(d, X1, Y1);
+                    tk[d] = bt_dir_is_max(d) ? bt_max3(tk[d], k0, k1) : bt_min3(tk[d], k0, k1);
+                }
             }
         }
         if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) set_status(a.ctl + i, CH_ERANGE);
 #pragma unroll
         for (int d = 0; d < 8; ++d) {
-            unsigned long long q = best[d];
+            int k = tk[d];
 #pragma unroll
             for (int o = 16; o; o >>= 1) {
-                const unsigned long long r = __shfl_xor_sync(0xFFFFFFFFu, q, o);
-                q = r > q ? r : q;
+                const int r = __shfl_xor_sync(0xFFFFFFFFu, k, o);
+                k = bt_dir_is_max(d) ? max(k, r) : min(k, r);
             }
-            if (lane == 0) s_red[warp][d] = q;
+            if (lane == 0) s_key[warp][d] = k;
         }
         __syncthreads();
         if (tid < 8) {
-            unsigned long long m = 0ull;
-            for (int w = 0; w < kBThreads / 32; ++w) m = s_red[w][tid] > m ? s_red[w][tid] : m;
-            if (m) atomicMax(&a.ctl[i].ext_packed[tid], m);
+            int k = s_key[0][tid];
+            for (int w = 1; w < kBThreads / 32; ++w) k = bt_dir_is_max(tid) ? max(k, s_key[w][tid]) : min(k, s_key[w][tid]);
+            s_best[tid] = k;
+        }
+        __syncthreads();
+        // lowest index reaching each extreme key (points in increasing index order per thread)
+        unsigned first[8];
+#pragma unroll
+        for (int d = 0; d < 8; ++d) first[d] = 0xFFFFFFFFu;
+#pragma unroll
+        for (int j = kBPer - 1; j >= 0; --j) {
+            const int q = tid + j * kBThreads;
+            const int X = __float2int_rn(v[j].x), Y = __float2int_rn(v[j].y);
+#pragma unroll
+            for (int d = 0; d < 8; ++d)
+                if (q < cnt && bt_key(d, X, Y) == s_best[d]) first[d] = (unsigned)(p0 + q);
+        }
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            const unsigned m = __reduce_min_sync(0xFFFFFFFFu, first[d]);
+            if (lane == 0 && m != 0xFFFFFFFFu) atomicMin(&s_idx[d], m);
+        }
+        __syncthreads();
+        if (tid < 8) {
+            const int d = tid;
+            const unsigned hk = bt_dir_is_max(d) ? (unsigned)s_best[d] : 0xFFFFFFFFu - (unsigned)s_best[d];
+            const unsigned long long pk = ((unsigned long long)hk << 32) | (unsigned long long)(0xFFFFFFFFu - s_idx[d]);
+            atomicMax(&a.ctl[i].ext_packed[d], pk);
         }
         __syncthreads();
     }
@@ -356,17 +411,17 @@ static std::map<std::pair<int, cudaStream_t>, BWork> g_bws;
 static size_t bt_align(size_t x) { return (x + 255) / 256 * 256; }
 
 struct BLayout {
-    size_t ctl, keys, vals, tiles, big, redo;
+    size_t ctl, keys, vals, tiles, tmap, rmap, big, redo;
     size_t seg_nb, seg_bbase, seg_lo, seg_scale, seg_tbase, rt_base, totals;
-    size_t bcount, bcur, bstart, blen, bu, bv, bi, kP, vP, cu, cv, ci, clen, counters;
+    size_t bcount, bcur, bstart, blen, bu, bv, bi, kP, vP, cu, cv, ci, clen, ctmap, counters;
     size_t zero_from, zero_to;   // bucket counters: cleared before each batch
     size_t total;
-    unsigned bcap, tcap;
+    unsigned bcap, tcap, rtcap;
 };
 
 // big_pts: points of the sets that can exceed one block (more than kMidCap
 // points), big_sets: how many; they bound the buckets and chain tiles.
-static BLayout bt_layout(long long total, int k, long long big_pts, long long big_sets) {
+static BLayout bt_layout(long long total, int k, long long big_pts, long long big_sets, long long tiles) {
     BLayout L;
     const long long cap = total + 16ll * k + 16;
     size_t o = 0;
@@ -382,6 +437,9 @@ static BLayout bt_layout(long long total, int k, long long big_pts, long long bi
     L.keys = take(sizeof(uint32_t) * (size_t)cap);
     L.vals = take(sizeof(uint64_t) * (size_t)cap);
     L.tiles = take(sizeof(int) * ((size_t)k + 1));
+    L.tmap = take(sizeof(int) * ((size_t)tiles + 1));
+    L.rtcap = (unsigned)((big_pts + 16 * big_sets) / kBTile + big_sets + 1);
+    L.rmap = take(sizeof(int) * (size_t)L.rtcap);
     L.big = take((size_t)k);
     L.redo = take((size_t)k);
     L.seg_nb = take(4 * nseg);
@@ -410,14 +468,15 @@ static BLayout bt_layout(long long total, int k, long long big_pts, long long bi
     L.cv = take(4 * (size_t)L.tcap * kChainTile);
     L.ci = take(4 * (size_t)L.tcap * kChainTile);
     L.clen = take(4 * (size_t)L.tcap);
+    L.ctmap = take(4 * (size_t)L.tcap);
     L.total = o;
     return L;
 }
 
 static int bt_workspace(int dev, cudaStream_t s, long long total, int k, long long big_pts, long long big_sets,
-                        char** base, BLayout* L) {
+                        long long tiles, char** base, BLayout* L) {
     std::lock_guard<std::mutex> lk(g_bmu);
-    *L = bt_layout(total, k, big_pts, big_sets);
+    *L = bt_layout(total, k, big_pts, big_sets, tiles);
     BWork& w = g_bws[std::make_pair(dev, s)];
     if (w.bytes < L->total) {
         if (w.base) {
@@ -442,7 +501,7 @@ static int bt_workspace(int dev, cudaStream_t s, long long total, int k, long lo
 int reserve_batched(int dev, cudaStream_t s, long long n, int k) {
     char* base = nullptr;
     BLayout L;
-    return bt_workspace(dev, s, n, std::max(k, 1), n, std::max(k, 1), &base, &L);
+    return bt_workspace(dev, s, n, std::max(k, 1), n, std::max(k, 1), n / kBTile + std::max(k, 1), &base, &L);
 }
 
 void release_batched() {
@@ -509,7 +568,7 @@ extern "C" int ch_hull_batched(const float* pts, const int64_t* offsets, int32_t
     if ((st = bt_configure(dev, &sms)) != CH_OK) return st;
     char* base = nullptr;
     BLayout L;
-    if ((st = bt_workspace(dev, s, total, k, big_pts, big_sets, &base, &L)) != CH_OK) return st;
+    if ((st = bt_workspace(dev, s, total, k, big_pts, big_sets, tiles, &base, &L)) != CH_OK) return st;
     BArgs a;
     a.pts = pts;
     a.offsets = offsets;
@@ -518,6 +577,7 @@ extern "C" int ch_hull_batched(const float* pts, const int64_t* offsets, int32_t
     a.keys = (uint32_t*)(base + L.keys);
     a.vals = (uint64_t*)(base + L.vals);
     a.tile_base = (int*)(base + L.tiles);
+    a.tile_map = (int*)(base + L.tmap);
     a.out_idx = out_idx;
     a.out_n = out_n;
     a.big = (unsigned char*)(base + L.big);
@@ -526,7 +586,7 @@ extern "C" int ch_hull_batched(const float* pts, const int64_t* offsets, int32_t
     {
         ProfScope p("batched_prep", s);
         bt_init<<<(k + 255) / 256, 256, 0, s>>>(a);
-        bt_scan<<<1, 1024, 0, s>>>(a.tile_base, k);
+        bt_scan<<<1, 1024, 0, s>>>(a.tile_base, a.tile_map, k);
     }
     if (nt > 0) {
         ProfScope p("batched_extremes", s);
@@ -555,7 +615,9 @@ extern "C" int ch_hull_batched(const float* pts, const int64_t* offsets, int32_t
     b.seg_lo = (int*)(base + L.seg_lo);
     b.seg_scale = (float*)(base + L.seg_scale);
     b.seg_tbase = (unsigned*)(base + L.seg_tbase);
+    b.ct_map = (int*)(base + L.ctmap);
     b.rt_base = (unsigned*)(base + L.rt_base);
+    b.rt_map = (int*)(base + L.rmap);
     b.totals = (unsigned*)(base + L.totals);
     b.bcount = (unsigned*)(base + L.bcount);
     b.bcur = (unsigned*)(base + L.bcur);
@@ -572,6 +634,7 @@ extern "C" int ch_hull_batched(const float* pts, const int64_t* offsets, int32_t
     b.clen = (int*)(base + L.clen);
     b.counters = (int*)(base + L.counters);
     b.bcap = L.bcap;
+    b.rtcap = L.rtcap;
     b.tcap = L.tcap;
     unsigned char* redo = (unsigned char*)(base + L.redo);
     if (cudaMemsetAsync(base + L.zero_from, 0, L.zero_to - L.zero_from, s) != cudaSuccess) return CH_ECUDA;

@@ -29,7 +29,8 @@ constexpr int kBLWarps = 8;
 
 // Exclusive prefix in place over n entries by one block of 1024 threads
 // (contiguous chunks per thread); returns the total in every thread.
-__device__ unsigned block_prefix_inplace(unsigned* a, int n, unsigned* s_part) {
+__device__ unsigned block_prefix_inplace(unsigned* a, int n, unsigned* s_part, int* map = nullptr,
+                                        unsigned map_cap = 0u) {
     const int tid = threadIdx.x;
     const int per = (n + 1023) / 1024;
     const int lo = tid * per, hi = min(n, lo + per);
@@ -47,6 +48,8 @@ __device__ unsigned block_prefix_inplace(unsigned* a, int n, unsigned* s_part) {
     for (int j = lo; j < hi; ++j) {
         const unsigned c = a[j];
         a[j] = run;
+        if (map)   // the entry owning each unit (never past the map's capacity)
+            for (unsigned t = 0; t < c && run + t < map_cap; ++t) map[run + t] = j;
         run += c;
     }
     const unsigned total = s_part[1023];
@@ -86,8 +89,8 @@ __global__ void __launch_bounds__(1024) btl_prep(BLArgs a) {
     }
     __syncthreads();
     const unsigned nb_total = block_prefix_inplace(a.seg_bbase, nseg, s_part);
-    const unsigned nt_total = block_prefix_inplace(a.seg_tbase, nseg, s_part);
-    const unsigned rt_total = block_prefix_inplace(a.rt_base, a.k, s_part);
+    const unsigned nt_total = block_prefix_inplace(a.seg_tbase, nseg, s_part, a.ct_map, a.tcap);
+    const unsigned rt_total = block_prefix_inplace(a.rt_base, a.k, s_part, a.rt_map, a.rtcap);
     if (tid == 0) {
         a.totals[4] = 0u;
         const bool fits = nb_total <= a.bcap && nt_total <= a.tcap;   // always, by the workspace bounds
@@ -101,16 +104,6 @@ __global__ void __launch_bounds__(1024) btl_prep(BLArgs a) {
     }
 }
 
-// Last index i in [0, n) with base[i] <= t (bases non-decreasing).
-__device__ __forceinline__ int btl_find(const unsigned* base, int n, unsigned t) {
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (base[mid] <= t) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
 struct BLTileCtx {
     int set;
     long long rb;   // region base of the set's records
@@ -121,7 +114,7 @@ struct BLTileCtx {
 };
 
 __device__ __forceinline__ void btl_tile_ctx(const BLArgs& a, unsigned t, BLTileCtx& x) {
-    const int i = btl_find(a.rt_base, a.k, t);
+    const int i = a.rt_map[t];
     x.set = i;
     x.rb = a.offsets[i] + 16ll * i;
     const unsigned cnt = a.ctl[i].count;
@@ -220,11 +213,10 @@ __global__ void __launch_bounds__(kChainThreads) btl_chain(BLArgs a) {
     __shared__ int s_mv[kChainThreads / 2][3];
     const int tid = threadIdx.x;
     const unsigned ntiles = a.totals[1];
-    const int nseg = 4 * a.k;
     const TreeBufs tb{a.cu, a.cv, a.ci, a.clen, a.counters, (int)a.tcap};
     for (unsigned c = blockIdx.x; c < ntiles; c += gridDim.x) {
         if (tid == 0) {
-            s_seg = btl_find(a.seg_tbase, nseg, c);
+            s_seg = a.ct_map[c];
             s_fail = 0;
         }
         __syncthreads();

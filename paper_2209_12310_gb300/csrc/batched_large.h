@@ -24,7 +24,9 @@ struct BLArgs {
     int* seg_lo;
     float* seg_scale;
     unsigned* seg_tbase;
+    int* ct_map;                   // segment of every chain tile
     unsigned* rt_base;             // k + 1: record tiles per set (prefix)
+    int* rt_map;                   // set of every record tile
     unsigned* totals;              // buckets, chain tiles, record tiles, fits, allocation cursor
     // buckets
     unsigned* bcount;
@@ -42,7 +44,7 @@ struct BLArgs {
     int* ci;
     int* clen;
     int* counters;
-    unsigned bcap, tcap;
+    unsigned bcap, tcap, rtcap;
 };
 
 void launch_batched_large(const BLArgs& a, unsigned char* redo, int sms, cudaStream_t s);

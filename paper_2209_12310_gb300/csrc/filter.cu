@@ -247,6 +247,18 @@ __device__ __forceinline__ bool tile_in_inner(const int (&tk)[8], const int* in)
            tk[SW] > in[2] && tk[NE] < in[6] && tk[NW] > in[3] && tk[SE] < in[7];
 }
 
+// Surely strictly inside the sample octagon: every edge function above the
+// float error bound (zero-length edges evaluate to a huge constant).  The
+// sample octagon's vertices are input points, so its interior lies in the
+// interior of the hull: such a point is no hull vertex, whatever the true
+// octagon turns out to be.  Edges as (A, B, C) triples in shared memory.
+__device__ __forceinline__ bool pt_in_sample(float x, float y, const float* e) {
+    float m = kHugePositive;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) m = fminf(m, fmaf(e[3 * k], x, fmaf(e[3 * k + 1], y, e[3 * k + 2])));
+    return m > kEdgeTol;
+}
+
 __device__ __forceinline__ bool pt_in_inner(int X, int Y, const int* in) {
     const int S = X + Y, D = X - Y + kCoordLimit;
     return X > in[0] && X < in[4] && Y > in[1] && Y < in[5] && S > in[2] && S < in[6] && D > in[3] && D < in[7];
@@ -448,6 +460,7 @@ __global__ void __launch_bounds__(256, 2) main_kernel(const float* __restrict__ 
                                                       uint64_t* vals) {
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ int s_inner[8];
+    __shared__ float s_edge[24];
     __shared__ unsigned long long s_red[8][8];
     __shared__ int s_mode;
     __shared__ RawBuf s_buf[8];
@@ -460,6 +473,11 @@ __global__ void __launch_bounds__(256, 2) main_kernel(const float* __restrict__ 
     if (threadIdx.x < 4) {
         s_inner[threadIdx.x] = ctl->oct_s.in_lo[threadIdx.x];
         s_inner[4 + threadIdx.x] = ctl->oct_s.in_hi[threadIdx.x];
+    }
+    if (threadIdx.x < 8) {
+        s_edge[3 * threadIdx.x] = ctl->oct_s.oct[threadIdx.x].A;
+        s_edge[3 * threadIdx.x + 1] = ctl->oct_s.oct[threadIdx.x].B;
+        s_edge[3 * threadIdx.x + 2] = ctl->oct_s.oct[threadIdx.x].C;
     }
     __syncthreads();
     bool filt = s_mode == 0;
@@ -482,7 +500,7 @@ __global__ void __launch_bounds__(256, 2) main_kernel(const float* __restrict__ 
                 convert_pt(x, y, X, Y, tr);
                 tile_keys2(tk, X, Y, X, Y, !any);
                 any = true;
-                if (filt && !pt_in_inner(X, Y, s_inner)) keep = 1u;
+                if (filt && !pt_in_inner(X, Y, s_inner) && !pt_in_sample(x, y, s_edge)) keep = 1u;
             }
             auto get = [&](int, long long& idx, float& px, float& py) { idx = i; px = x; py = y; };
             if (filt) emit_raw<1>(keep, get, wbuf, wcnt, ctl, raw_xy, raw_idx);
@@ -542,7 +560,8 @@ __global__ void __launch_bounds__(256, 2) main_kernel(const float* __restrict__ 
                         const float2 v = cur2[f2];
                         x = v.x;
                         y = v.y;
-                        keep = pt_in_inner(__float2int_rn(x), __float2int_rn(y), s_inner) ? 0u : 1u;
+                        keep = (pt_in_inner(__float2int_rn(x), __float2int_rn(y), s_inner) ||
+                                pt_in_sample(x, y, s_edge)) ? 0u : 1u;
                         idx = head + t * kWarpTilePts + f2;
                     }
                     auto get = [&](int, long long& id, float& px, float& py) { id = idx; px = x; py = y; };
