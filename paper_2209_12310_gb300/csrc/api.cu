@@ -84,6 +84,7 @@ Layout make_layout(long long n) {
     L.off_bcount = take(4 * (size_t)L.bmax);
     L.off_bcur = take(4 * (size_t)L.bmax);
     L.off_bstart = take(4 * (size_t)L.bmax);
+    L.off_bsum = take(4 * ((size_t)L.bmax / 1024 + 2 + 2 * (size_t)kBkCoarseMax + 1));   // block sums, cursors, tiles
     L.off_blen = take(4 * (size_t)L.bmax);
     L.off_bu = take(4 * (size_t)L.bmax * kBkChain);
     L.off_bv = take(4 * (size_t)L.bmax * kBkChain);
@@ -285,7 +286,7 @@ static void enqueue_large_part(const float* pts, long long n, int32_t* out_idx, 
     Ctl* ctl = h.ctl;
     unsigned long long* status = (unsigned long long*)(base + L.off_status);
     launch_bucket_pass(ctl, h.kA, h.vA, h.kB, h.vB, (unsigned*)(base + L.off_bcount), (unsigned*)(base + L.off_bcur),
-                       (unsigned*)(base + L.off_bstart), (int*)(base + L.off_bu), (int*)(base + L.off_bv),
+                       (unsigned*)(base + L.off_bstart), (unsigned*)(base + L.off_bsum), (int*)(base + L.off_bu), (int*)(base + L.off_bv),
                        (int*)(base + L.off_bi), (int*)(base + L.off_blen), (unsigned)L.bmax, h.di.sms, s);
     {
         ProfScope p("sort", s);

@@ -48,6 +48,7 @@ constexpr int kBkGroup = kChainTile / kBkChain;
 // hull boundary even for sets of a few thousand points on a circle, so
 // bucket chains stay short.
 constexpr int kBkMinQ = 256;
+constexpr int kBkCoarseMax = 4096;   // coarse bucket groups of the two-level partition at most
 
 __host__ __device__ __forceinline__ unsigned bk_buckets_for(unsigned cnt) {
     unsigned nb = (cnt + kBkAvg - 1) / kBkAvg;
@@ -110,11 +111,12 @@ struct Ctl {
     unsigned int counts4[4];            // survivors per queue (ch_filter)
     unsigned long long line_ep[8];      // end points of survivors on the 4 axis support lines
     int bk_state;                       // large-survivor path: 0 unused, 1 buckets, 2 full sort
-    unsigned int bk_cursor;             // bucket allocation cursor
+    unsigned int bk_cursor;             // tiles of the second partition level
     unsigned int bk_nb[4];              // buckets of queue r
     unsigned int bk_base[5];            // first bucket of queue r
     int bk_lo[4];                       // u of queue r's first chain point
     float bk_scale[4];                  // buckets per unit of u in queue r
+    int bk_shift;                       // fine buckets per coarse group: 1 << bk_shift
     Octagon oct;                        // octagon of the true extremes
     Octagon oct_s;                      // octagon of a sample's extremes
 };

@@ -26,8 +26,8 @@ void launch_chain(Ctl* ctl, const uint32_t* keys, const uint64_t* vals, const in
                   const int* bi, const int* blen, int* cu, int* cv, int* ci, int* clen, int* counters, int ctcap,
                   int* vbuf, int* kbuf, int* xbuf, int* ybuf, const float* pts, long long n, int32_t* out_idx,
                   int64_t* out_n, int grid, cudaStream_t s);
-void launch_bucket_pass(Ctl* ctl, const uint32_t* kA, const uint64_t* vA, uint32_t* kB, uint64_t* vB,
-                        unsigned* bcount, unsigned* bcur, unsigned* bstart, int* bu, int* bv, int* bi, int* blen,
+void launch_bucket_pass(Ctl* ctl, uint32_t* kA, uint64_t* vA, uint32_t* kB, uint64_t* vB, unsigned* bcount,
+                        unsigned* bcur, unsigned* bstart, unsigned* bsum, int* bu, int* bv, int* bi, int* blen,
                         unsigned bmax, int sms, cudaStream_t s);
 cudaError_t configure_bucket_kernels();
 size_t chain_smem_bytes();
