@@ -20,6 +20,7 @@ struct BkWarp {   // shared memory of one warp: the chain under construction
     unsigned long long segmax[kBkV], segarg[kBkV];
     int vu[kBkV], vv[kBkV], vi[kBkV], vnext[kBkV], splitu[kBkV], child[kBkV];
     int cu[kBkV], cv[kBkV], ci[kBkV];   // the finished chain in order
+    int tu[kBkWCap], tv[kBkWCap], ti[kBkWCap];   // live records between rounds (u | segment << 25)
 };
 
 struct BkRecs {
@@ -88,6 +89,7 @@ static __device__ int bk_warp_chain(BkWarp& w, BkRecs& R, int m) {
     int nv = 2;
     for (int round = 0;; ++round) {
         // depths; each segment's maximum
+        int live = 0;
 #pragma unroll
         for (int k = 0; k < kBkPer; ++k) {
             if (k * 32 >= m) break;
@@ -109,6 +111,41 @@ static __device__ int bk_warp_chain(BkWarp& w, BkRecs& R, int m) {
                 }
                 R.s[k] = a;
             }
+            live += __popc(__ballot_sync(0xFFFFFFFFu, R.s[k] >= 0));
+        }
+        // records below the chain only: packed to the first slots when that
+        // saves slots (each round keeps a small part of the records)
+        if (live + 31 < ((m + 31) & ~31)) {
+            int pos = 0;
+#pragma unroll
+            for (int k = 0; k < kBkPer; ++k) {
+                if (k * 32 >= m) break;
+                const bool keep = R.s[k] >= 0;
+                const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
+                if (keep) {
+                    const int p = pos + __popc(bal & lanemask_lt());
+                    w.tu[p] = R.u[k] | (R.s[k] << 25);
+                    w.tv[p] = R.v[k];
+                    w.ti[p] = R.i[k];
+                }
+                pos += __popc(bal);
+            }
+            __syncwarp();
+            m = live;
+#pragma unroll
+            for (int k = 0; k < kBkPer; ++k) {
+                if (k * 32 >= m) break;
+                const int j = k * 32 + lane;
+                R.s[k] = -1;
+                if (j < m) {
+                    const int t = w.tu[j];
+                    R.u[k] = t & 0x1FFFFFF;
+                    R.s[k] = t >> 25;
+                    R.v[k] = w.tv[j];
+                    R.i[k] = w.ti[j];
+                }
+            }
+            __syncwarp();
         }
         __syncwarp();
         // the deepest record per segment: smallest u, then index
