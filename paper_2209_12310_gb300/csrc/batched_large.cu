@@ -7,7 +7,7 @@
 //   btl_hist     record tiles: records per bucket;
 //   btl_alloc    bucket ranges in the scatter buffer;
 //   btl_scatter  record tiles: records into their bucket's range;
-//   btl_bucket   one warp per bucket: its lower chain;
+//   btl_bucket_hull  one warp per bucket: its lower chain;
 //   btl_chain    chain tiles: bucket chains merged up each segment's tree;
 //                the block completing a set's fourth root joins its chains.
 // A set whose bucket chains overflow is left to the single-hull path (the
@@ -93,6 +93,7 @@ __global__ void __launch_bounds__(1024) btl_prep(BLArgs a) {
     const unsigned rt_total = block_prefix_inplace(a.rt_base, a.k, s_part, a.rt_map, a.rtcap);
     if (tid == 0) {
         a.totals[4] = 0u;
+        a.totals[5] = 0u;   // next bucket for a btl_bucket warp
         const bool fits = nb_total <= a.bcap && nt_total <= a.tcap;   // always, by the workspace bounds
         a.seg_bbase[nseg] = fits ? nb_total : 0u;
         a.seg_tbase[nseg] = fits ? nt_total : 0u;
@@ -184,12 +185,16 @@ __global__ void __launch_bounds__(256) btl_scatter(BLArgs a) {
     }
 }
 
-__global__ void __launch_bounds__(kBLWarps * 32) btl_bucket(BLArgs a) {
+__global__ void __launch_bounds__(kBLWarps * 32) btl_bucket_hull(BLArgs a) {
     __shared__ BkWarp s_w[kBLWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     BkWarp& w = s_w[warp];
     const unsigned nb = a.totals[0];
-    for (unsigned b = blockIdx.x * kBLWarps + warp; b < nb; b += gridDim.x * kBLWarps) {
+    for (;;) {   // buckets taken one at a time: sizes differ
+        unsigned b = 0u;
+        if (lane == 0) b = atomicAdd(&a.totals[5], 1u);
+        b = __shfl_sync(0xFFFFFFFFu, b, 0);
+        if (b >= nb) break;
         const int len = bk_bucket_chain(w, a.kP, a.vP, a.bstart[b], a.bcount[b]);
         const size_t o = (size_t)b * kBkChain;
         for (int j = lane; j < len; j += 32) {
@@ -304,7 +309,13 @@ void launch_batched_large(const BLArgs& a, unsigned char* redo, int sms, cudaStr
     { ProfScope p("bl_hist", s); btl_hist<<<sms * 8, 256, 0, s>>>(a); }
     { ProfScope p("bl_alloc", s); btl_alloc<<<sms, 1024, 0, s>>>(a); }
     { ProfScope p("bl_scatter", s); btl_scatter<<<sms * 8, 256, 0, s>>>(a); }
-    { ProfScope p("bl_bucket", s); btl_bucket<<<sms * 4, kBLWarps * 32, 0, s>>>(a); }
+    {
+        ProfScope p("bl_bucket", s);
+        static int occ = 0;   // resident blocks per SM: one wave of warps that take buckets
+        if (occ == 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, btl_bucket_hull, kBLWarps * 32, 0) != cudaSuccess)
+            occ = 2;
+        btl_bucket_hull<<<sms * (occ > 0 ? occ : 1), kBLWarps * 32, 0, s>>>(a);
+    }
     { ProfScope p("bl_chain", s); btl_chain<<<sms * 2, kChainThreads, chain_smem_bytes(), s>>>(a); }
     btl_flags<<<(a.k + 255) / 256, 256, 0, s>>>(a, redo);
 }

@@ -17,8 +17,10 @@ constexpr int kBkV = kBkChain + 2;      // quickhull vertices of one bucket
 // warp only.  The records live in registers (slot k of lane l is record
 // 32 k + l), so a round's loads are only of the few chain vertices.
 struct BkWarp {   // shared memory of one warp: the chain under construction
+    int4 seg[kBkV];    // segment from vertex a to its successor: u_a, v_a, du, dv
+    int2 sc[kBkV];     // split of segment a in the last round: u of the new vertex (-1: none), new segment
     unsigned long long segmax[kBkV], segarg[kBkV];
-    int vu[kBkV], vv[kBkV], vi[kBkV], vnext[kBkV], splitu[kBkV], child[kBkV];
+    int vu[kBkV], vv[kBkV], vi[kBkV], vnext[kBkV];
     int cu[kBkV], cv[kBkV], ci[kBkV];   // the finished chain in order
     int tu[kBkWCap], tv[kBkWCap], ti[kBkWCap];   // live records between rounds (u | segment << 25)
 };
@@ -27,8 +29,9 @@ struct BkRecs {
     int u[kBkPer], v[kBkPer], i[kBkPer], s[kBkPer];
 };
 
-__device__ __forceinline__ long long bk_depth(const BkWarp& w, int a, int b, int u, int v) {
-    return (long long)(w.vv[b] - w.vv[a]) * (u - w.vu[a]) - (long long)(w.vu[b] - w.vu[a]) * (v - w.vv[a]);
+// Depth of (u, v) below segment g (positive: strictly below).
+__device__ __forceinline__ long long bk_depth(const int4 g, int u, int v) {
+    return (long long)g.w * (u - g.x) - (long long)g.z * (v - g.y);
 }
 
 // Returns the chain length, its vertices in order in w.cu / cv / ci; -1 when
@@ -67,44 +70,107 @@ static __device__ int bk_warp_chain(BkWarp& w, BkRecs& R, int m) {
     is = __reduce_min_sync(0xFFFFFFFFu, is);
     ie = __reduce_min_sync(0xFFFFFFFFu, ie);
     const int su = (int)(ks >> kKeyBits), eu = (int)(ke >> kKeyBits);
+    const int vs = (int)(ks & kVMask), ve = (int)(kVMask - (ke & kVMask));
     for (int a = lane; a < kBkV; a += 32) {
         w.segmax[a] = 0ull;
         w.segarg[a] = ~0ull;
-        w.splitu[a] = -1;
-    }
-    if (lane == 0) {
-        w.vu[0] = su;
-        w.vv[0] = (int)(ks & kVMask);
-        w.vi[0] = (int)is;
-        w.vu[1] = eu;
-        w.vv[1] = (int)(kVMask - (ke & kVMask));
-        w.vi[1] = (int)ie;
-        w.vnext[0] = su < eu ? 1 : -1;
-        w.vnext[1] = -1;
+        w.sc[a] = make_int2(-1, -1);
     }
 #pragma unroll
     for (int k = 0; k < kBkPer; ++k)
         R.s[k] = (k * 32 + lane < m && su < R.u[k] && R.u[k] < eu) ? 0 : -1;
+    // First round, on the chord S -> E with every record in registers: the
+    // deepest record below it (smallest u, then index, on ties) becomes F.
+    const long long cdu = (long long)(eu - su), cdv = (long long)(ve - vs);
+    unsigned long long dmax = 0ull;
+#pragma unroll
+    for (int k = 0; k < kBkPer; ++k) {
+        if (k * 32 >= m) break;
+        if (R.s[k] == 0) {
+            const long long d = cdv * (R.u[k] - su) - cdu * (R.v[k] - vs);
+            if (d <= 0) R.s[k] = -1;
+            else dmax = (unsigned long long)d > dmax ? (unsigned long long)d : dmax;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(0xFFFFFFFFu, dmax, o);
+        dmax = t > dmax ? t : dmax;
+    }
+    if (dmax == 0ull) {   // S, E (one vertex when every record has the same u)
+        if (lane == 0) {
+            w.cu[0] = su;
+            w.cv[0] = vs;
+            w.ci[0] = (int)is;
+            w.cu[1] = eu;
+            w.cv[1] = ve;
+            w.ci[1] = (int)ie;
+        }
+        __syncwarp();
+        return su < eu ? 2 : 1;
+    }
+    unsigned long long best = ~0ull;
+#pragma unroll
+    for (int k = 0; k < kBkPer; ++k) {
+        if (k * 32 >= m) break;
+        if (R.s[k] == 0 && (unsigned long long)(cdv * (R.u[k] - su) - cdu * (R.v[k] - vs)) == dmax) {
+            const unsigned long long key = ((unsigned long long)R.u[k] << 31) | (unsigned)R.i[k];
+            best = key < best ? key : best;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(0xFFFFFFFFu, best, o);
+        best = t < best ? t : best;
+    }
+    const int fu = (int)(best >> 31), fi = (int)(best & 0x7FFFFFFFull);
+    int fv = 0;
+    bool own = false;
+#pragma unroll
+    for (int k = 0; k < kBkPer; ++k) {
+        if (k * 32 >= m) break;
+        if (R.s[k] == 0 && R.u[k] == fu && R.i[k] == fi) {
+            own = true;
+            fv = R.v[k];
+        }
+    }
+    fv = __shfl_sync(0xFFFFFFFFu, fv, __ffs(__ballot_sync(0xFFFFFFFFu, own)) - 1);
+    if (lane == 0) {   // chain S -> F -> E; vertex 2 = F
+        w.vu[0] = su;
+        w.vv[0] = vs;
+        w.vi[0] = (int)is;
+        w.vu[1] = eu;
+        w.vv[1] = ve;
+        w.vi[1] = (int)ie;
+        w.vu[2] = fu;
+        w.vv[2] = fv;
+        w.vi[2] = fi;
+        w.vnext[0] = 2;
+        w.vnext[2] = 1;
+        w.vnext[1] = -1;
+        w.seg[0] = make_int4(su, vs, fu - su, fv - vs);
+        w.seg[2] = make_int4(fu, fv, eu - fu, ve - fv);
+    }
+#pragma unroll
+    for (int k = 0; k < kBkPer; ++k)
+        if (R.s[k] == 0) R.s[k] = R.u[k] < fu ? 0 : (R.u[k] > fu ? 2 : -1);
     __syncwarp();
-    int nv = 2;
-    for (int round = 0;; ++round) {
+    int nv = 3;
+    for (int round = 1;; ++round) {
         // depths; each segment's maximum
         int live = 0;
 #pragma unroll
         for (int k = 0; k < kBkPer; ++k) {
             if (k * 32 >= m) break;
             int a = R.s[k];
-            if (a >= 0) {
-                const int sp = w.splitu[a];
-                if (sp >= 0) {
-                    if (R.u[k] > sp) a = w.child[a];
-                    else if (R.u[k] == sp) a = -1;
+            if (a >= 0) {   // every live record's segment has a successor
+                const int2 sc = w.sc[a];
+                if (sc.x >= 0) {
+                    if (R.u[k] > sc.x) a = sc.y;
+                    else if (R.u[k] == sc.x) a = -1;
                 }
-                const int b = a >= 0 ? w.vnext[a] : -1;
-                if (b < 0) {
-                    a = -1;
-                } else {
-                    const long long d = bk_depth(w, a, b, R.u[k], R.v[k]);
+                if (a >= 0) {
+                    const long long d = bk_depth(w.seg[a], R.u[k], R.v[k]);
                     if (d <= 0) a = -1;
                     else if ((unsigned long long)d > *(volatile unsigned long long*)&w.segmax[a])
                         atomicMax(&w.segmax[a], (unsigned long long)d);
@@ -153,7 +219,7 @@ static __device__ int bk_warp_chain(BkWarp& w, BkRecs& R, int m) {
         for (int k = 0; k < kBkPer; ++k) {
             if (k * 32 >= m) break;
             const int a = R.s[k];
-            if (a >= 0 && (unsigned long long)bk_depth(w, a, w.vnext[a], R.u[k], R.v[k]) == w.segmax[a])
+            if (a >= 0 && (unsigned long long)bk_depth(w.seg[a], R.u[k], R.v[k]) == w.segmax[a])
                 atomicMin(&w.segarg[a], ((unsigned long long)R.u[k] << 31) | (unsigned)R.i[k]);
         }
         __syncwarp();
@@ -164,21 +230,25 @@ static __device__ int bk_warp_chain(BkWarp& w, BkRecs& R, int m) {
             const unsigned long long dm = a < nv ? w.segmax[a] : 0ull;
             const bool split = dm != 0ull;
             const unsigned bal = __ballot_sync(0xFFFFFFFFu, split);
-            if (a < nv) w.splitu[a] = -1;
+            if (a < nv) w.sc[a] = make_int2(-1, -1);
             if (split) {
                 const int f = nv + added + __popc(bal & lanemask_lt());
                 if (f < kBkV) {
                     const int b = w.vnext[a];
+                    const int4 g = w.seg[a];
                     const unsigned long long key = w.segarg[a];
                     const int fu = (int)(key >> 31), fi = (int)(key & 0x7FFFFFFFull);
-                    const long long num = (long long)(w.vv[b] - w.vv[a]) * (fu - w.vu[a]) - (long long)dm;
+                    // v of the new vertex from its depth (an exact quotient)
+                    const long long num = (long long)g.w * (fu - g.x) - (long long)dm;
+                    const int fv = g.y + (int)(num / (long long)g.z);
                     w.vu[f] = fu;
-                    w.vv[f] = w.vv[a] + (int)(num / (long long)(w.vu[b] - w.vu[a]));
+                    w.vv[f] = fv;
                     w.vi[f] = fi;
                     w.vnext[f] = b;
                     w.vnext[a] = f;
-                    w.child[a] = f;
-                    w.splitu[a] = fu;
+                    w.seg[a] = make_int4(g.x, g.y, fu - g.x, fv - g.y);
+                    w.seg[f] = make_int4(fu, fv, g.x + g.z - fu, g.y + g.w - fv);
+                    w.sc[a] = make_int2(fu, f);
                 } else {
                     over = true;
                 }

@@ -113,6 +113,7 @@ __global__ void bk_prep(Ctl* ctl, unsigned* bcount, unsigned bmax) {
             ctl->bk_shift = shift;
             ctl->bk_base[4] = nbk;
             ctl->bk_cursor = 0u;
+            ctl->bk_next = 0u;
             ctl->bk_state = shift <= kBkShiftMax && ((nbk + (1u << shift) - 1) >> shift) <= (unsigned)kBkCoarseMax ? 1 : 2;
         }
     }
@@ -328,8 +329,11 @@ __global__ void __launch_bounds__(kBkWarps * 32) bk_hull(Ctl* ctl, const uint32_
     if (!s_go) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     BkWarp& w = s_w[warp];
-    const unsigned nwarps = gridDim.x * kBkWarps;
-    for (unsigned b = blockIdx.x * kBkWarps + warp; b < s_nb; b += nwarps) {
+    for (;;) {   // buckets taken one at a time: sizes differ
+        unsigned b = 0u;
+        if (lane == 0) b = atomicAdd(&ctl->bk_next, 1u);
+        b = __shfl_sync(0xFFFFFFFFu, b, 0);
+        if (b >= s_nb) break;
         int len = bk_bucket_chain(w, keys, vals, bstart[b], bcount[b]);
         if (len < 0) {
             if (lane == 0) ctl->bk_state = 2;   // the sort-based path takes over
@@ -371,7 +375,10 @@ void launch_bucket_pass(Ctl* ctl, uint32_t* kA, uint64_t* vA, uint32_t* kB, uint
     }
     {
         ProfScope p("bk_hull", s);
-        bk_hull<<<sms * 4, kBkWarps * 32, 0, s>>>(ctl, kA, vA, bstart, bcount, bu, bv, bi, blen);
+        static int occ = 0;   // resident blocks per SM: one wave of warps that take buckets
+        if (occ == 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bk_hull, kBkWarps * 32, 0) != cudaSuccess)
+            occ = 2;
+        bk_hull<<<sms * (occ > 0 ? occ : 1), kBkWarps * 32, 0, s>>>(ctl, kA, vA, bstart, bcount, bu, bv, bi, blen);
     }
 }
 

@@ -117,6 +117,7 @@ struct Ctl {
     int bk_lo[4];                       // u of queue r's first chain point
     float bk_scale[4];                  // buckets per unit of u in queue r
     int bk_shift;                       // fine buckets per coarse group: 1 << bk_shift
+    unsigned int bk_next;               // next bucket for a bk_hull warp
     Octagon oct;                        // octagon of the true extremes
     Octagon oct_s;                      // octagon of a sample's extremes
 };
