@@ -85,10 +85,31 @@ int ch_hull(const float* pts, int64_t n, int32_t* out_idx, int64_t* out_n, void*
  *   host_offsets  optional HOST copy of offsets (NULL allowed): lets the
  *            library size its launches without reading the device array.
  * Each result equals ch_hull on that set alone.
+ * Tile shape of the per-point kernels (threads per block x points per thread
+ * = points per tile): picked by an autotuner per (device name, SM count,
+ * floor log2 of offsets[k], floor log2 of k).  The first call of such a size
+ * class times every compiled shape on that call's batch (the call blocks
+ * meanwhile); the result is kept in memory and, when the environment variable
+ * CH_TUNE_CACHE names a file, in that JSON file, read at the first lookup.
+ * CH_BLOCK and CH_PPT (or CH_TILE = CH_BLOCK x CH_PPT) name a shape directly;
+ * one that is not compiled makes the call return CH_EINVAL.  The device work
+ * is launched as a CUDA graph that is updated in place from call to call
+ * (per device and stream); the call reads a k-byte flag array back before it
+ * returns (it synchronises the stream).
  */
 int ch_hull_batched(const float* pts, const int64_t* offsets, int32_t k,
                     int32_t* out_idx, int64_t* out_n, const int64_t* host_offsets,
                     void* stream);
+
+/*
+ * ch_batched_config -- the tile shape ch_hull_batched uses on the current
+ * device for a batch of total_points points in k >= 1 sets: *threads and
+ * *per (points per thread) from CH_BLOCK / CH_PPT / CH_TILE, else from the
+ * autotuner's choice for that size class; both 0 when it has not been tuned
+ * yet.  CH_EINVAL for bad arguments or an environment shape that is not one
+ * of the compiled shapes (128x16, 256x8, 256x16, 256x32, 512x8, 512x16).
+ */
+int ch_batched_config(int64_t total_points, int32_t k, int32_t* threads, int32_t* per);
 
 /*
  * ch_filter -- the paper's GPUfilter (Alg. 2) on its own.

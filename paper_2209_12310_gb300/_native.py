@@ -39,6 +39,7 @@ SIGNATURES = {
     "ch_filter": (_INT, [_P, _I64, _P, _P, _P, _P]),
     "ch_hull_host": (_INT, [_P, _I64, _P, _P, _P]),
     "ch_hull_noalloc": (_INT, [_P, _I64, _P, _P, _P]),
+    "ch_batched_config": (_INT, [_I64, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "ch_reserve": (_INT, [_I64, _I32, _P]),
     "ch_workspace_bytes": (_SZ, [_I64]),
     "ch_release": (_INT, []),
@@ -100,6 +101,15 @@ def ch_hull(pts, n, out_idx, out_n, stream=0):
 def ch_hull_batched(pts, offsets, k, out_idx, out_n, host_offsets=None, stream=0):
     return _check(load().ch_hull_batched(pts, offsets, k, out_idx, out_n, host_offsets, stream),
                   "ch_hull_batched")
+
+
+def ch_batched_config(total_points, k):
+    """(threads, points per thread) of ch_hull_batched's tile kernels for this
+    size class on the current device; (0, 0) before it has been tuned."""
+    t, p = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(load().ch_batched_config(int(total_points), int(k), ctypes.byref(t), ctypes.byref(p)),
+           "ch_batched_config")
+    return t.value, p.value
 
 
 def ch_filter(pts, n, out_ext8, out_labels=None, out_counts4=None, stream=0):

@@ -146,6 +146,7 @@ int get_workspace(int dev, cudaStream_t s, long long n, char** base, Layout* L) 
 void release_stream_workspace(int dev, cudaStream_t s) {
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_ws.find(std::make_pair(dev, s));
+    drop_batched_graphs(dev, s);
     if (it == g_ws.end()) return;
     drop_graphs(dev, s);
     cudaStreamSynchronize(s);
@@ -189,6 +190,8 @@ static std::vector<ProfPending> g_pending;
 static std::vector<cudaEvent_t> g_event_pool;
 static std::map<std::string, std::pair<long long, double>> g_acc;
 static std::vector<std::string> g_names;   // stable storage for names returned to callers
+
+bool prof_enabled() { return g_prof; }
 
 static cudaEvent_t take_event() {
     if (!g_event_pool.empty()) {

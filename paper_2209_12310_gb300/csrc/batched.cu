@@ -1,7 +1,9 @@
 // batched.cu -- k independent hulls packed back to back (ch_hull_batched).
 //
-// The sets are cut into tiles of at most kBTile points (a tile never spans
-// two sets) and every launch covers all sets at once:
+// The sets are cut into tiles of at most `tile` points (a tile never spans
+// two sets; tile = threads x points per thread of the tile kernels, one of
+// the compiled shapes that the autotuner picks per device and batch size)
+// and every launch covers all sets at once:
 //   bt_init      per-set control blocks and tile counts;
 //   bt_scan      tile offsets (exclusive prefix over the sets, one block);
 //   bt_extremes  tiles: validation and the 8 extremes of each set as packed
@@ -17,7 +19,9 @@
 // large-survivor path together (batched_large.cu); the rare set it cannot
 // finish (a bucket chain longer than kBkChain) is flagged and the host runs
 // the single-hull path on it.  Each result equals ch_hull on the set alone
-// (local indices).
+// (local indices).  The device work of one call is captured into a CUDA graph
+// on a private stream; the executable graph of a (device, stream) is updated
+// in place from call to call and launched on the caller's stream.
 #include "batched_large.h"
 #include "ch_internal.cuh"
 #include "host.h"
@@ -27,14 +31,16 @@
 #include "records.cuh"
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <map>
 #include <mutex>
+#include <string>
 #include <vector>
 
 namespace ch {
 
-constexpr int kBTile = 4096;           // points per tile
-constexpr int kBThreads = 256;         // threads of the tile kernels
+constexpr int kBTileMin = 2048;        // smallest tile of the compiled shapes
 constexpr int kBHullThreads = 512;     // threads of bt_hull (a multiple of 128)
 constexpr int kBOctThreads = 64;       // threads of bt_octagon
 
@@ -50,6 +56,7 @@ struct BArgs {
     int32_t* out_idx;
     int64_t* out_n;
     unsigned char* big;       // k: the set needs the single-hull path
+    int tile;                 // points per tile (threads x points per thread of the tile kernels)
 };
 
 __device__ __forceinline__ long long region_base(const BArgs& a, int i) { return a.offsets[i] + 16ll * i; }
@@ -76,7 +83,7 @@ __global__ void bt_init(BArgs a) {
     }
     a.big[i] = 0;
     const long long ni = a.offsets[i + 1] - a.offsets[i];
-    a.tile_base[i] = (int)((ni + kBTile - 1) / kBTile);
+    a.tile_base[i] = (int)((ni + a.tile - 1) / a.tile);
 }
 
 // Exclusive prefix of the tile counts in place (one block of 1024 threads);
@@ -131,15 +138,16 @@ __device__ __forceinline__ int bt_min3(int a, int b, int c) {
     return __float_as_int(r);
 }
 
-// Per tile: each thread holds its kBPer points in registers; the block first
-// finds the tile's 8 extreme keys (three-input min / max, two points per
-// instruction), then the lowest index reaching each of them (every thread
-// checks its own points), and one packed (key, lowest index) atomic per
-// direction carries it to the set's maximum.
-constexpr int kBPer = kBTile / kBThreads;   // points per thread and tile
-
-__global__ void __launch_bounds__(kBThreads) bt_extremes(BArgs a, int ntiles) {
-    __shared__ int s_key[kBThreads / 32][8];
+// Per tile of T x P points: each thread holds its P points in registers; the
+// block first finds the tile's 8 extreme keys (three-input min / max, two
+// points per instruction), then the lowest index reaching each of them
+// (every thread checks its own points), and one packed (key, lowest index)
+// atomic per direction carries it to the set's maximum.
+template <int T, int P>
+__global__ void __launch_bounds__(T) bt_extremes(BArgs a, int ntiles) {
+    static_assert(P % 2 == 0 && T % 32 == 0, "tile shape");
+    constexpr int kBTile = T * P;
+    __shared__ int s_key[T / 32][8];
     __shared__ int s_best[8];
     __shared__ unsigned s_idx[8];
     __shared__ int s_set;
@@ -153,16 +161,16 @@ __global__ void __launch_bounds__(kBThreads) bt_extremes(BArgs a, int ntiles) {
         const long long p0 = (long long)(t - a.tile_base[i]) * kBTile;
         const int cnt = (int)min((long long)kBTile, ni - p0);   // >= 1
         const float2* p2 = reinterpret_cast<const float2*>(a.pts) + base + p0;
-        float2 v[kBPer];
+        float2 v[P];
 #pragma unroll
-        for (int j = 0; j < kBPer; ++j) {
-            const int q = tid + j * kBThreads;
+        for (int j = 0; j < P; ++j) {
+            const int q = tid + j * T;
             v[j] = __ldcs(p2 + (q < cnt ? q : 0));   // a missing point repeats point 0 of the tile
         }
         int tk[8];
         bool bad = false;
 #pragma unroll
-        for (int j = 0; j < kBPer; j += 2) {
+        for (int j = 0; j < P; j += 2) {
             const int X0 = __float2int_rn(v[j].x), Y0 = __float2int_rn(v[j].y);
             const int X1 = __float2int_rn(v[j + 1].x), Y1 = __float2int_rn(v[j + 1].y);
             bad |= (__int2float_rn(X0) != v[j].x) | (__int2float_rn(Y0) != v[j].y) |
@@ -196,7 +204,7 @@ __global__ void __launch_bounds__(kBThreads) bt_extremes(BArgs a, int ntiles) {
         __syncthreads();
         if (tid < 8) {
             int k = s_key[0][tid];
-            for (int w = 1; w < kBThreads / 32; ++w) k = bt_dir_is_max(tid) ? max(k, s_key[w][tid]) : min(k, s_key[w][tid]);
+            for (int w = 1; w < T / 32; ++w) k = bt_dir_is_max(tid) ? max(k, s_key[w][tid]) : min(k, s_key[w][tid]);
             s_best[tid] = k;
         }
         __syncthreads();
@@ -205,8 +213,8 @@ __global__ void __launch_bounds__(kBThreads) bt_extremes(BArgs a, int ntiles) {
 #pragma unroll
         for (int d = 0; d < 8; ++d) first[d] = 0xFFFFFFFFu;
 #pragma unroll
-        for (int j = kBPer - 1; j >= 0; --j) {
-            const int q = tid + j * kBThreads;
+        for (int j = P - 1; j >= 0; --j) {
+            const int q = tid + j * T;
             const int X = __float2int_rn(v[j].x), Y = __float2int_rn(v[j].y);
 #pragma unroll
             for (int d = 0; d < 8; ++d)
@@ -279,7 +287,12 @@ __global__ void __launch_bounds__(kBOctThreads) bt_octagon(BArgs a) {
     }
 }
 
-__global__ void __launch_bounds__(kBThreads) bt_filter(BArgs a, int ntiles) {
+// Per tile of T x P points: every thread loads its P points (a batch of at
+// most 8 at a time, all loads in flight together), then classifies them.
+template <int T, int P>
+__global__ void __launch_bounds__(T) bt_filter(BArgs a, int ntiles) {
+    constexpr int kBTile = T * P;
+    constexpr int kB = P < 8 ? P : 8;   // points loaded together
     __shared__ Octagon s_o;
     __shared__ int s_set, s_skip;
     const int tid = threadIdx.x, lane = tid & 31;
@@ -300,15 +313,22 @@ __global__ void __launch_bounds__(kBThreads) bt_filter(BArgs a, int ntiles) {
             const long long p1 = min(ni, p0 + kBTile);
             const long long rb = region_base(a, i);
             const float2* p2 = reinterpret_cast<const float2*>(a.pts) + base;
-            for (long long b0 = p0; b0 < p1; b0 += kBThreads) {   // uniform trip count
-                const long long p = b0 + tid;
+            for (long long b0 = p0; b0 < p1; b0 += (long long)T * kB) {   // uniform trip counts
+                float2 pv[kB];
+#pragma unroll
+                for (int j = 0; j < kB; ++j) {
+                    const long long p = b0 + (long long)j * T + tid;
+                    if (p < p1) pv[j] = __ldcs(p2 + p);
+                }
+#pragma unroll 1
+                for (int j = 0; j < kB; ++j) {
+                const long long p = b0 + (long long)j * T + tid;
                 const bool valid = p < p1;
                 int r = -1, X = 0, Y = 0;
                 if (valid) {
-                    const float2 v = __ldcs(p2 + p);
-                    X = __float2int_rn(v.x);
-                    Y = __float2int_rn(v.y);
-                    r = classify_hull(v.x, v.y, s_o);
+                    X = __float2int_rn(pv[j].x);
+                    Y = __float2int_rn(pv[j].y);
+                    r = classify_hull(pv[j].x, pv[j].y, s_o);
                 }
                 bool keep = r >= 0;
                 if (!__any_sync(0xFFFFFFFFu, keep)) continue;
@@ -329,6 +349,7 @@ __global__ void __launch_bounds__(kBThreads) bt_filter(BArgs a, int ntiles) {
                     const long long pos = rb + pos0 + __popc(bal & lanemask_lt());
                     a.keys[pos] = make_key(r, u);
                     a.vals[pos] = make_val(v, (uint32_t)p);
+                }
                 }
             }
         }
@@ -438,7 +459,7 @@ static BLayout bt_layout(long long total, int k, long long big_pts, long long bi
     L.vals = take(sizeof(uint64_t) * (size_t)cap);
     L.tiles = take(sizeof(int) * ((size_t)k + 1));
     L.tmap = take(sizeof(int) * ((size_t)tiles + 1));
-    L.rtcap = (unsigned)((big_pts + 16 * big_sets) / kBTile + big_sets + 1);
+    L.rtcap = (unsigned)((big_pts + 16 * big_sets) / kBLTile + big_sets + 1);
     L.rmap = take(sizeof(int) * (size_t)L.rtcap);
     L.big = take((size_t)k);
     L.redo = take((size_t)k);
@@ -501,10 +522,13 @@ static int bt_workspace(int dev, cudaStream_t s, long long total, int k, long lo
 int reserve_batched(int dev, cudaStream_t s, long long n, int k) {
     char* base = nullptr;
     BLayout L;
-    return bt_workspace(dev, s, n, std::max(k, 1), n, std::max(k, 1), n / kBTile + std::max(k, 1), &base, &L);
+    return bt_workspace(dev, s, n, std::max(k, 1), n, std::max(k, 1), n / kBTileMin + std::max(k, 1), &base, &L);
 }
 
+static void drop_all_batched_graphs();
+
 void release_batched() {
+    drop_all_batched_graphs();
     std::lock_guard<std::mutex> lk(g_bmu);
     for (auto& kv : g_bws) {
         cudaStreamSynchronize(kv.first.second);
@@ -513,32 +537,370 @@ void release_batched() {
     g_bws.clear();
 }
 
-static int bt_configure(int dev, int* sms) {
+// ---------------------------------------------------------------------------
+// Tile shapes of bt_extremes / bt_filter: threads per block x points per
+// thread (tile = their product).  The autotuner below picks one per device
+// and batch size.
+struct BtShape {
+    int threads, per;
+};
+constexpr BtShape kBtShapes[] = {{128, 16}, {256, 8}, {256, 16}, {256, 32}, {512, 8}, {512, 16}};
+constexpr int kNumBtShapes = (int)(sizeof(kBtShapes) / sizeof(kBtShapes[0]));
+
+template <int T, int P>
+static void bt_occupancy(int* occ) {
+    int a = 0, b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, bt_extremes<T, P>, T, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, bt_filter<T, P>, T, 0);
+    occ[0] = std::max(1, a);
+    occ[1] = std::max(1, b);
+}
+
+struct BtDevice {
+    int sms = 0;
+    std::string name;
+    int occ[kNumBtShapes][2] = {};
+};
+
+static int bt_configure(int dev, BtDevice* out) {
     static std::mutex mu;
-    static std::map<int, int> done;
+    static std::map<int, BtDevice> done;
     std::lock_guard<std::mutex> lk(mu);
     auto it = done.find(dev);
-    if (it != done.end()) { *sms = it->second; return CH_OK; }
-    int n = 0;
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return CH_ECUDA;
+    if (it != done.end()) { *out = it->second; return CH_OK; }
+    BtDevice d;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return CH_ECUDA;
+    d.sms = prop.multiProcessorCount;
+    d.name = prop.name;
     if (cudaFuncSetAttribute(bt_hull, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBHullSmem) != cudaSuccess)
         return CH_ECUDA;
     if (configure_batched_large() != cudaSuccess) return CH_ECUDA;
-    done[dev] = n;
-    *sms = n;
+    bt_occupancy<128, 16>(d.occ[0]);
+    bt_occupancy<256, 8>(d.occ[1]);
+    bt_occupancy<256, 16>(d.occ[2]);
+    bt_occupancy<256, 32>(d.occ[3]);
+    bt_occupancy<512, 8>(d.occ[4]);
+    bt_occupancy<512, 16>(d.occ[5]);
+    if (cudaGetLastError() != cudaSuccess) return CH_ECUDA;
+    done[dev] = d;
+    *out = d;
     return CH_OK;
 }
 
-}  // namespace ch
+static void launch_bt_tiles(int shape, bool filter, const BArgs& a, int nt, int grid, cudaStream_t s) {
+#define CH_BT_CASE(i, T, P)                                                   \
+    case i:                                                                   \
+        if (filter) bt_filter<T, P><<<grid, T, 0, s>>>(a, nt);                \
+        else bt_extremes<T, P><<<grid, T, 0, s>>>(a, nt);                     \
+        break;
+    switch (shape) {
+        CH_BT_CASE(0, 128, 16)
+        CH_BT_CASE(1, 256, 8)
+        CH_BT_CASE(2, 256, 16)
+        CH_BT_CASE(3, 256, 32)
+        CH_BT_CASE(4, 512, 8)
+        CH_BT_CASE(5, 512, 16)
+        default: break;
+    }
+#undef CH_BT_CASE
+}
 
-using namespace ch;
+// ---------------------------------------------------------------------------
+// Autotuner.  Key: device name, SM count, and the batch's size class
+// (floor log2 of its total points and of its set count).  On the first batch
+// of a key every shape runs the tile kernels (extremes, octagon, filter) on
+// that batch twice; the fastest by CUDA events is kept, in memory and, when
+// CH_TUNE_CACHE names a file, in that JSON file ({"key": [threads, per,
+// microseconds], ...}), read once at the first lookup.  CH_BLOCK with CH_PPT
+// (or CH_TILE = threads x per) names a shape directly; a pair that is not one
+// of the compiled shapes makes ch_hull_batched return CH_EINVAL.
+static std::mutex g_tune_mu;
+static std::map<std::string, std::pair<int, double>> g_tune;   // key -> (shape, microseconds)
+static bool g_tune_loaded = false;
+
+static int ilog2(long long x) {
+    int r = 0;
+    while (x > 1) { x >>= 1; ++r; }
+    return r;
+}
+
+static std::string tune_key(const BtDevice& d, long long total, int k) {
+    char buf[64];
+    snprintf(buf, sizeof(buf), "|%d|%d|%d", d.sms, ilog2(std::max(1ll, total)), ilog2(std::max(1, k)));
+    std::string name;
+    for (char c : d.name) name += (c == '"' || c == '\\' || c == '|') ? '_' : c;
+    return name + buf;
+}
+
+static int shape_index(int threads, int per) {
+    for (int i = 0; i < kNumBtShapes; ++i)
+        if (kBtShapes[i].threads == threads && kBtShapes[i].per == per) return i;
+    return -1;
+}
+
+// The shape named by the environment: index, -1 = none named, -2 = invalid.
+static int env_shape() {
+    const char* b = getenv("CH_BLOCK");
+    const char* p = getenv("CH_PPT");
+    const char* t = getenv("CH_TILE");
+    if (!b && !p && !t) return -1;
+    if (!b || (!p && !t)) return -2;
+    const int threads = atoi(b);
+    int per = p ? atoi(p) : 0;
+    if (!p && threads > 0) per = atoi(t) / threads;
+    if (p && t && atoi(t) != threads * per) return -2;
+    const int i = shape_index(threads, per);
+    return i >= 0 ? i : -2;
+}
+
+static void tune_load_locked() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char* path = getenv("CH_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE* f = fopen(path, "rb");
+    if (!f) return;
+    std::string txt;
+    char buf[4096];
+    size_t r;
+    while ((r = fread(buf, 1, sizeof(buf), f)) > 0) txt.append(buf, r);
+    fclose(f);
+    // entries "key": [threads, per, us]
+    size_t pos = 0;
+    while ((pos = txt.find('"', pos)) != std::string::npos) {
+        const size_t e = txt.find('"', pos + 1);
+        if (e == std::string::npos) break;
+        const std::string key = txt.substr(pos + 1, e - pos - 1);
+        int threads = 0, per = 0;
+        double us = 0.0;
+        const size_t lb = txt.find('[', e);
+        if (lb == std::string::npos) break;
+        if (sscanf(txt.c_str() + lb, "[%d,%d,%lf]", &threads, &per, &us) == 3 ||
+            sscanf(txt.c_str() + lb, "[ %d , %d , %lf ]", &threads, &per, &us) == 3) {
+            const int i = shape_index(threads, per);
+            if (i >= 0) g_tune[key] = {i, us};
+        }
+        pos = txt.find(']', lb);
+        if (pos == std::string::npos) break;
+    }
+}
+
+static void tune_save_locked() {
+    const char* path = getenv("CH_TUNE_CACHE");
+    if (!path || !*path) return;
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE* f = fopen(tmp.c_str(), "wb");
+    if (!f) return;
+    fprintf(f, "{\n");
+    size_t n = 0;
+    for (const auto& kv : g_tune) {
+        const BtShape& sh = kBtShapes[kv.second.first];
+        fprintf(f, "  \"%s\": [%d, %d, %.3f]%s\n", kv.first.c_str(), sh.threads, sh.per, kv.second.second,
+                ++n < g_tune.size() ? "," : "");
+    }
+    fprintf(f, "}\n");
+    fclose(f);
+    rename(tmp.c_str(), path);
+}
+
+static long long count_tiles(const std::vector<int64_t>& off, int k, int tile) {
+    long long t = 0;
+    for (int i = 0; i < k; ++i) t += (off[i + 1] - off[i] + tile - 1) / tile;
+    return t;
+}
+
+// ---------------------------------------------------------------------------
+// The device work of one call.
+struct BtCall {
+    BArgs a;
+    BLArgs b;
+    int nt, shape, grid_e, grid_f, sms;
+    char* base;
+    BLayout L;
+};
+
+static void bt_enqueue_tiles(const BtCall& c, cudaStream_t s) {
+    const BArgs& a = c.a;
+    {
+        ProfScope p("batched_prep", s);
+        bt_init<<<(a.k + 255) / 256, 256, 0, s>>>(a);
+        bt_scan<<<1, 1024, 0, s>>>(a.tile_base, a.tile_map, a.k);
+    }
+    {
+        ProfScope p("batched_extremes", s);
+        launch_bt_tiles(c.shape, false, a, c.nt, c.grid_e, s);
+    }
+    { ProfScope p("batched_octagon", s); bt_octagon<<<a.k, kBOctThreads, 0, s>>>(a); }
+    {
+        ProfScope p("batched_filter", s);
+        launch_bt_tiles(c.shape, true, a, c.nt, c.grid_f, s);
+    }
+}
+
+static int bt_enqueue(const BtCall& c, unsigned char* redo, cudaStream_t s) {
+    bt_enqueue_tiles(c, s);
+    { ProfScope p("batched_hull", s); bt_hull<<<c.a.k, kBHullThreads, kBHullSmem, s>>>(c.a); }
+    // Sets with more records than one block holds: all together through the
+    // bucketed path.
+    if (cudaMemsetAsync(c.base + c.L.zero_from, 0, c.L.zero_to - c.L.zero_from, s) != cudaSuccess) return CH_ECUDA;
+    launch_batched_large(c.b, redo, c.sms, s);
+    return cudaGetLastError() == cudaSuccess ? CH_OK : CH_ECUDA;
+}
+
+// One executable graph per (device, stream), updated in place per call.
+struct BtGraphKey {
+    int dev;
+    cudaStream_t s;
+    bool operator<(const BtGraphKey& o) const { return dev != o.dev ? dev < o.dev : s < o.s; }
+};
+static std::mutex g_bgraph_mu;
+static std::map<BtGraphKey, cudaGraphExec_t> g_bgraphs;
+
+static int bt_launch_graph(const BtCall& c, unsigned char* redo, int dev, cudaStream_t s) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (prof_enabled() || cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
+        return bt_enqueue(c, redo, s);
+    // capture on a stream of this thread's own (kept per device), so that
+    // concurrent callers never share a capture
+    thread_local std::map<int, cudaStream_t> t_capture;
+    cudaStream_t& cs = t_capture[dev];
+    if (!cs && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        cs = nullptr;
+        cudaGetLastError();
+        return bt_enqueue(c, redo, s);
+    }
+    cudaGraph_t graph = nullptr;
+    int st = CH_ECUDA;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        st = bt_enqueue(c, redo, cs);
+        if (cudaStreamEndCapture(cs, &graph) != cudaSuccess || !graph) st = CH_ECUDA;
+    }
+    if (st != CH_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return bt_enqueue(c, redo, s);
+    }
+    std::lock_guard<std::mutex> lk(g_bgraph_mu);
+    cudaGraphExec_t& exec = g_bgraphs[BtGraphKey{dev, s}];
+    if (exec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(exec, graph, &info) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(exec);
+            exec = nullptr;
+        }
+    }
+    if (!exec && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+        exec = nullptr;
+        cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return bt_enqueue(c, redo, s);
+    }
+    cudaGraphDestroy(graph);
+    return cudaGraphLaunch(exec, s) == cudaSuccess ? CH_OK : CH_ECUDA;
+}
+
+void drop_batched_graphs(int dev, cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(g_bgraph_mu);
+    auto it = g_bgraphs.find(BtGraphKey{dev, s});
+    if (it == g_bgraphs.end()) return;
+    if (it->second) cudaGraphExecDestroy(it->second);
+    g_bgraphs.erase(it);
+}
+
+static void drop_all_batched_graphs() {
+    std::lock_guard<std::mutex> lk(g_bgraph_mu);
+    for (auto& kv : g_bgraphs)
+        if (kv.second) cudaGraphExecDestroy(kv.second);
+    g_bgraphs.clear();
+}
+
+static void bt_set_shape(BtCall& c, const BtDevice& d, const std::vector<int64_t>& off, int shape) {
+    const BtShape& sh = kBtShapes[shape];
+    c.shape = shape;
+    c.a.tile = sh.threads * sh.per;
+    c.nt = (int)count_tiles(off, c.a.k, c.a.tile);
+    c.grid_e = std::max(1, std::min(c.nt, d.sms * d.occ[shape][0]));
+    c.grid_f = std::max(1, std::min(c.nt, d.sms * d.occ[shape][1]));
+}
+
+// Times every shape on this batch (tile kernels only, best of two runs).
+static int bt_tune(BtCall& c, const BtDevice& d, const std::vector<int64_t>& off, cudaStream_t s, int* best) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return CH_ECUDA;
+    double best_us = 1e30;
+    *best = 2;
+    int st = CH_OK;
+    for (int i = 0; i < kNumBtShapes && st == CH_OK; ++i) {
+        bt_set_shape(c, d, off, i);
+        double t_min = 1e30;
+        for (int rep = 0; rep < 2; ++rep) {
+            cudaEventRecord(e0, s);
+            bt_enqueue_tiles(c, s);
+            cudaEventRecord(e1, s);
+            float ms = 0.f;
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                st = CH_ECUDA;
+                break;
+            }
+            t_min = std::min(t_min, 1e3 * ms);
+        }
+        if (t_min < best_us) {
+            best_us = t_min;
+            *best = i;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st == CH_OK) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[tune_key(d, off[c.a.k], c.a.k)] = {*best, best_us};
+        tune_save_locked();
+    }
+    return st;
+}
+
+// The tuned shape of the nearest size class of this device (by the distance
+// of the log2 sizes), else the middle shape; for callers that must not block
+// on tuning (the server).
+static int nearest_tuned_locked(const BtDevice& d, long long total, int k) {
+    const std::string prefix = tune_key(d, 1, 1);
+    const std::string dev = prefix.substr(0, prefix.size() - 4);   // drops "|0|0"
+    const int lt = ilog2(std::max(1ll, total)), lk = ilog2(std::max(1, k));
+    int best = 2, best_d = 1 << 30;
+    for (const auto& kv : g_tune) {
+        if (kv.first.compare(0, dev.size(), dev) != 0) continue;
+        int t = 0, kk = 0;
+        if (sscanf(kv.first.c_str() + dev.size(), "|%d|%d", &t, &kk) != 2) continue;
+        const int dist = std::abs(t - lt) + std::abs(kk - lk);
+        if (dist < best_d) {
+            best_d = dist;
+            best = kv.second.first;
+        }
+    }
+    return best;
+}
+
+int hull_batched_impl(const float* pts, const int64_t* offsets, int32_t k, int32_t* out_idx, int64_t* out_n,
+                      const int64_t* host_offsets, cudaStream_t s, bool allow_tune);
+
+}  // namespace ch
 
 extern "C" int ch_hull_batched(const float* pts, const int64_t* offsets, int32_t k, int32_t* out_idx,
                                int64_t* out_n, const int64_t* host_offsets, void* stream) {
+    return ch::hull_batched_impl(pts, offsets, k, out_idx, out_n, host_offsets, (cudaStream_t)stream, true);
+}
+
+namespace ch {
+
+int hull_batched_impl(const float* pts, const int64_t* offsets, int32_t k, int32_t* out_idx, int64_t* out_n,
+                      const int64_t* host_offsets, cudaStream_t s, bool allow_tune) {
     if (k < 0 || k > (1 << 20)) return CH_EINVAL;
     if (k == 0) return CH_OK;
     if (!offsets || !out_n) return CH_EINVAL;
-    cudaStream_t s = (cudaStream_t)stream;
+    const int forced = env_shape();
+    if (forced == -2) return CH_EINVAL;
     std::vector<int64_t> off((size_t)k + 1);
     if (host_offsets) {
         for (int i = 0; i <= k; ++i) off[i] = host_offsets[i];
@@ -549,27 +911,30 @@ extern "C" int ch_hull_batched(const float* pts, const int64_t* offsets, int32_t
         if (cudaStreamSynchronize(s) != cudaSuccess) return CH_ECUDA;
     }
     if (off[0] != 0) return CH_EINVAL;
-    long long tiles = 0, big_pts = 0, big_sets = 0;
+    long long big_pts = 0, big_sets = 0;
     for (int i = 0; i < k; ++i) {
         if (off[i + 1] < off[i] || off[i + 1] - off[i] > CH_MAX_POINTS) return CH_EINVAL;
-        tiles += (off[i + 1] - off[i] + kBTile - 1) / kBTile;
         if (off[i + 1] - off[i] + 12 > kMidCap) {
             big_pts += off[i + 1] - off[i];
             ++big_sets;
         }
     }
-    if (tiles > INT32_MAX) return CH_EINVAL;
+    const long long max_tiles = count_tiles(off, k, kBTileMin);   // the most tiles of any shape
+    if (max_tiles > INT32_MAX) return CH_EINVAL;
     const int64_t total = off[k];
     int st = check_points_args(pts, total);
     if (st != CH_OK) return st;
     if (total > 0 && !out_idx) return CH_EINVAL;
-    int dev = 0, sms = 0;
+    int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return CH_ECUDA;
-    if ((st = bt_configure(dev, &sms)) != CH_OK) return st;
-    char* base = nullptr;
-    BLayout L;
-    if ((st = bt_workspace(dev, s, total, k, big_pts, big_sets, tiles, &base, &L)) != CH_OK) return st;
-    BArgs a;
+    BtDevice d;
+    if ((st = bt_configure(dev, &d)) != CH_OK) return st;
+    BtCall c;
+    if ((st = bt_workspace(dev, s, total, k, big_pts, big_sets, max_tiles, &c.base, &c.L)) != CH_OK) return st;
+    const BLayout& L = c.L;
+    char* base = c.base;
+    c.sms = d.sms;
+    BArgs& a = c.a;
     a.pts = pts;
     a.offsets = offsets;
     a.k = k;
@@ -581,26 +946,7 @@ extern "C" int ch_hull_batched(const float* pts, const int64_t* offsets, int32_t
     a.out_idx = out_idx;
     a.out_n = out_n;
     a.big = (unsigned char*)(base + L.big);
-    const int nt = (int)tiles;
-    const int grid_t = std::max(1, std::min(nt, sms * 8));
-    {
-        ProfScope p("batched_prep", s);
-        bt_init<<<(k + 255) / 256, 256, 0, s>>>(a);
-        bt_scan<<<1, 1024, 0, s>>>(a.tile_base, a.tile_map, k);
-    }
-    if (nt > 0) {
-        ProfScope p("batched_extremes", s);
-        bt_extremes<<<grid_t, kBThreads, 0, s>>>(a, nt);
-    }
-    { ProfScope p("batched_octagon", s); bt_octagon<<<k, kBOctThreads, 0, s>>>(a); }
-    if (nt > 0) {
-        ProfScope p("batched_filter", s);
-        bt_filter<<<grid_t, kBThreads, 0, s>>>(a, nt);
-    }
-    { ProfScope p("batched_hull", s); bt_hull<<<k, kBHullThreads, kBHullSmem, s>>>(a); }
-    // Sets with more records than one block holds: all together through the
-    // bucketed path.
-    BLArgs b;
+    BLArgs& b = c.b;
     b.pts = pts;
     b.offsets = offsets;
     b.k = k;
@@ -637,9 +983,18 @@ extern "C" int ch_hull_batched(const float* pts, const int64_t* offsets, int32_t
     b.rtcap = L.rtcap;
     b.tcap = L.tcap;
     unsigned char* redo = (unsigned char*)(base + L.redo);
-    if (cudaMemsetAsync(base + L.zero_from, 0, L.zero_to - L.zero_from, s) != cudaSuccess) return CH_ECUDA;
-    launch_batched_large(b, redo, sms, s);
-    if (cudaGetLastError() != cudaSuccess) return CH_ECUDA;
+    // tile shape: named by the environment, else tuned for this device and size class
+    int shape = forced;
+    if (shape < 0) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_load_locked();
+        auto it = g_tune.find(tune_key(d, total, k));
+        if (it != g_tune.end()) shape = it->second.first;
+        else if (!allow_tune) shape = nearest_tuned_locked(d, total, k);
+    }
+    if (shape < 0 && (st = bt_tune(c, d, off, s, &shape)) != CH_OK) return st;
+    bt_set_shape(c, d, off, shape);
+    if ((st = bt_launch_graph(c, redo, dev, s)) != CH_OK) return st;
     // Sets the bucketed path could not finish (a bucket chain too long): the
     // single-hull path, one by one.
     std::vector<unsigned char> big((size_t)k);
@@ -650,5 +1005,37 @@ extern "C" int ch_hull_batched(const float* pts, const int64_t* offsets, int32_t
         st = enqueue_hull_nograph(pts + 2 * off[i], off[i + 1] - off[i], out_idx + off[i], out_n + i, s, dev);
         if (st != CH_OK) return st;
     }
+    return CH_OK;
+}
+
+}  // namespace ch
+
+using namespace ch;
+
+// Tile shape that ch_hull_batched uses for a batch of this size class on the
+// current device: from the environment, else the tuned choice (0 when the
+// class has not been tuned yet).
+extern "C" int ch_batched_config(int64_t total_points, int32_t k, int32_t* threads, int32_t* per) {
+    if (!threads || !per || total_points < 0 || k < 1) return CH_EINVAL;
+    int shape = env_shape();
+    if (shape == -2) return CH_EINVAL;
+    if (shape < 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return CH_ECUDA;
+        BtDevice d;
+        const int st = bt_configure(dev, &d);
+        if (st != CH_OK) return st;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_load_locked();
+        auto it = g_tune.find(tune_key(d, total_points, k));
+        if (it == g_tune.end()) {
+            *threads = 0;
+            *per = 0;
+            return CH_OK;
+        }
+        shape = it->second.first;
+    }
+    *threads = kBtShapes[shape].threads;
+    *per = kBtShapes[shape].per;
     return CH_OK;
 }

@@ -24,7 +24,6 @@
 
 namespace ch {
 
-constexpr int kBLTile = 4096;   // records per record tile
 constexpr int kBLWarps = 8;
 
 // Exclusive prefix in place over n entries by one block of 1024 threads
@@ -304,6 +303,8 @@ __global__ void btl_flags(BLArgs a, unsigned char* redo) {
     redo[i] = (a.big[i] && (*(volatile int*)&a.ctl[i].bk_state == 2 || a.totals[3] == 0u)) ? 1 : 0;
 }
 
+static int g_occ_bucket_hull = 1;   // resident btl_bucket_hull blocks per SM (set by configure_batched_large)
+
 void launch_batched_large(const BLArgs& a, unsigned char* redo, int sms, cudaStream_t s) {
     { ProfScope p("bl_prep", s); btl_prep<<<1, 1024, 0, s>>>(a); }
     { ProfScope p("bl_hist", s); btl_hist<<<sms * 8, 256, 0, s>>>(a); }
@@ -311,16 +312,18 @@ void launch_batched_large(const BLArgs& a, unsigned char* redo, int sms, cudaStr
     { ProfScope p("bl_scatter", s); btl_scatter<<<sms * 8, 256, 0, s>>>(a); }
     {
         ProfScope p("bl_bucket", s);
-        static int occ = 0;   // resident blocks per SM: one wave of warps that take buckets
-        if (occ == 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, btl_bucket_hull, kBLWarps * 32, 0) != cudaSuccess)
-            occ = 2;
-        btl_bucket_hull<<<sms * (occ > 0 ? occ : 1), kBLWarps * 32, 0, s>>>(a);
+        // one wave of resident warps that take buckets from a counter
+        btl_bucket_hull<<<sms * g_occ_bucket_hull, kBLWarps * 32, 0, s>>>(a);
     }
     { ProfScope p("bl_chain", s); btl_chain<<<sms * 2, kChainThreads, chain_smem_bytes(), s>>>(a); }
     btl_flags<<<(a.k + 255) / 256, 256, 0, s>>>(a, redo);
 }
 
 cudaError_t configure_batched_large() {
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, btl_bucket_hull, kBLWarps * 32, 0);
+    if (e != cudaSuccess) return e;
+    g_occ_bucket_hull = occ > 0 ? occ : 1;
     return cudaFuncSetAttribute(btl_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chain_smem_bytes());
 }
 

@@ -8,6 +8,8 @@ namespace ch {
 
 struct Ctl;
 
+constexpr int kBLTile = 4096;   // records per record tile of the large-survivor path
+
 struct BLArgs {
     const float* pts;
     const int64_t* offsets;        // device, k + 1

@@ -351,6 +351,8 @@ __global__ void __launch_bounds__(kBkWarps * 32) bk_hull(Ctl* ctl, const uint32_
 }
 
 // ---------------------------------------------------------------------------
+static int g_occ_bk_hull = 1;   // resident bk_hull blocks per SM (set by configure_bucket_kernels)
+
 void launch_bucket_pass(Ctl* ctl, uint32_t* kA, uint64_t* vA, uint32_t* kB, uint64_t* vB, unsigned* bcount,
                         unsigned* bcur, unsigned* bstart, unsigned* bsum, int* bu, int* bv, int* bi, int* blen,
                         unsigned bmax, int sms, cudaStream_t s) {
@@ -375,15 +377,17 @@ void launch_bucket_pass(Ctl* ctl, uint32_t* kA, uint64_t* vA, uint32_t* kB, uint
     }
     {
         ProfScope p("bk_hull", s);
-        static int occ = 0;   // resident blocks per SM: one wave of warps that take buckets
-        if (occ == 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bk_hull, kBkWarps * 32, 0) != cudaSuccess)
-            occ = 2;
-        bk_hull<<<sms * (occ > 0 ? occ : 1), kBkWarps * 32, 0, s>>>(ctl, kA, vA, bstart, bcount, bu, bv, bi, blen);
+        // one wave of resident warps that take buckets from a counter
+        bk_hull<<<sms * g_occ_bk_hull, kBkWarps * 32, 0, s>>>(ctl, kA, vA, bstart, bcount, bu, bv, bi, blen);
     }
 }
 
 cudaError_t configure_bucket_kernels() {
-    cudaError_t e = cudaFuncSetAttribute(bk_part1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PartSmem));
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bk_hull, kBkWarps * 32, 0);
+    if (e != cudaSuccess) return e;
+    g_occ_bk_hull = occ > 0 ? occ : 1;
+    e = cudaFuncSetAttribute(bk_part1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PartSmem));
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(bk_part2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PartSmem));
 }

@@ -25,6 +25,12 @@ int enqueue_hull_nograph(const float* pts, long long n, int32_t* out_idx, int64_
 int check_points_args(const float* pts, long long n);
 
 int reserve_batched(int dev, cudaStream_t s, long long n, int k);
+void drop_batched_graphs(int dev, cudaStream_t s);
+// ch_hull_batched; allow_tune = false takes the nearest tuned size class
+// instead of tuning a new one (for callers that must not block).
+int hull_batched_impl(const float* pts, const int64_t* offsets, int32_t k, int32_t* out_idx, int64_t* out_n,
+                      const int64_t* host_offsets, cudaStream_t s, bool allow_tune);
+bool prof_enabled();
 void release_stream_workspace(int dev, cudaStream_t s);
 void release_batched();
 

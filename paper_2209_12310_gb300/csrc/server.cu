@@ -254,7 +254,7 @@ bool Server::launch(Slot& sl) {
         cudaMemcpyAsync(d_pts + 2 * sl.off[i], batch[i]->host, 8 * (size_t)batch[i]->n, cudaMemcpyHostToDevice,
                         sl.s);
     cudaMemcpyAsync(d_off, sl.h_off, 8 * (k + 1), cudaMemcpyHostToDevice, sl.s);
-    const int st = ch_hull_batched(d_pts, d_off, (int32_t)k, d_idx, d_n, sl.h_off, sl.s);
+    const int st = hull_batched_impl(d_pts, d_off, (int32_t)k, d_idx, d_n, sl.h_off, sl.s, false);
     if (st != CH_OK) cudaMemsetAsync(d_n, 0xFF, 8 * k, sl.s);   // -1 = CH_EINVAL per set
     cudaMemcpyAsync(sl.h_n, d_n, 8 * k, cudaMemcpyDeviceToHost, sl.s);
     cudaEventRecord(sl.ev, sl.s);

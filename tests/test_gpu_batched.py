@@ -104,3 +104,94 @@ def test_batched_repeated_and_odd_offsets(lib):
     for a, b, s in zip(first[1], second[1], sets):
         np.testing.assert_array_equal(a, b)
         np.testing.assert_array_equal(a, oracle.hull(s))
+
+
+# --- tile shapes and the autotuner ------------------------------------------
+
+SHAPES = [(128, 16), (256, 8), (256, 16), (256, 32), (512, 8), (512, 16)]
+
+
+def _shape_sets():
+    """Sets that span several tiles of every shape with ragged tails (tile
+    sizes 2048 .. 8192), plus empty, one-point and large-survivor sets."""
+    sizes = [0, 1, 2047, 2048, 2049, 8191, 8193, 20_000, 70_001]
+    kinds = ["uniform", "normal", "ring"]
+    sets = [W.make(kinds[i % 3], n, 50 + i) if n else np.zeros((0, 2), np.float32) for i, n in enumerate(sizes)]
+    sets.append(W.ring(40_000, 77))   # records beyond one block: the bucketed path
+    return sets
+
+
+@pytest.mark.parametrize("threads,per", SHAPES)
+def test_batched_every_tile_shape_matches_oracle(lib, monkeypatch, threads, per):
+    monkeypatch.setenv("CH_BLOCK", str(threads))
+    monkeypatch.setenv("CH_PPT", str(per))
+    sets = _shape_sets()
+    assert lib.ch_batched_config(sum(s.shape[0] for s in sets), len(sets)) == (threads, per)
+    for got, s in zip(_run(lib, sets), sets):
+        np.testing.assert_array_equal(got, oracle.hull(s))
+
+
+def test_batched_tile_env_and_invalid_shape(lib, monkeypatch):
+    monkeypatch.setenv("CH_BLOCK", "256")
+    monkeypatch.setenv("CH_TILE", "8192")
+    assert lib.ch_batched_config(10_000, 4) == (256, 32)
+    monkeypatch.setenv("CH_PPT", "7")   # CH_TILE and CH_PPT disagree
+    with pytest.raises(lib.CHError) as e:
+        lib.ch_batched_config(10_000, 4)
+    assert e.value.status == lib.CH_EINVAL
+    sets = [W.uniform(3000, 1), W.normal(5000, 2)]
+    with pytest.raises(lib.CHError) as e:
+        _run(lib, sets)
+    assert e.value.status == lib.CH_EINVAL
+    monkeypatch.delenv("CH_PPT")
+    monkeypatch.delenv("CH_TILE")
+    with pytest.raises(lib.CHError):   # a block size without points per thread
+        lib.ch_batched_config(10_000, 4)
+
+
+_TUNE_CHILD = r"""
+import json, sys
+import numpy as np
+import torch
+import paper_2209_12310_gb300 as ch
+sys.path.insert(0, sys.argv[2])
+from synth import workloads as W
+total, k = int(sys.argv[3]), int(sys.argv[4])
+if sys.argv[1] == "tune":
+    assert ch.ch_batched_config(total, k) == (0, 0)
+    sets = [W.make(("uniform", "normal", "ring")[i % 3], total // k, 100 + i) for i in range(k)]
+    off = np.zeros(k + 1, np.int64); off[1:] = np.cumsum([s.shape[0] for s in sets])
+    ch.hull_batched(torch.from_numpy(np.concatenate(sets)).cuda(), torch.from_numpy(off))
+print(json.dumps(ch.ch_batched_config(total, k)))
+"""
+
+
+def test_batched_autotuner_cache_file(lib, tmp_path):
+    """First batch of a size class tunes and writes the JSON cache; a new
+    process reads its choice from the file (edited here to another shape)."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cache = tmp_path / "tune.json"
+    env = {k: v for k, v in os.environ.items() if k not in ("CH_BLOCK", "CH_PPT", "CH_TILE")}
+    env["CH_TUNE_CACHE"] = str(cache)
+    env["PYTHONPATH"] = root + os.pathsep + env.get("PYTHONPATH", "")
+    total, k = 60_000, 6
+
+    def child(mode):
+        out = subprocess.run([sys.executable, "-c", _TUNE_CHILD, mode, root, str(total), str(k)], env=env,
+                             capture_output=True, text=True, timeout=300)
+        assert out.returncode == 0, out.stderr
+        return tuple(json.loads(out.stdout.strip().splitlines()[-1]))
+
+    tuned = child("tune")
+    assert tuned in SHAPES
+    table = json.loads(cache.read_text())
+    assert len(table) == 1
+    (key, (threads, per, us)), = table.items()
+    assert (threads, per) == tuned and us > 0
+    other = next(s for s in SHAPES if s != tuned)
+    cache.write_text(json.dumps({key: [other[0], other[1], us]}))
+    assert child("read") == other
