@@ -882,20 +882,31 @@ static int nearest_tuned_locked(const BtDevice& d, long long total, int k) {
     return best;
 }
 
-int hull_batched_impl(const float* pts, const int64_t* offsets, int32_t k, int32_t* out_idx, int64_t* out_n,
-                      const int64_t* host_offsets, cudaStream_t s, bool allow_tune);
-
 }  // namespace ch
 
 extern "C" int ch_hull_batched(const float* pts, const int64_t* offsets, int32_t k, int32_t* out_idx,
                                int64_t* out_n, const int64_t* host_offsets, void* stream) {
-    return ch::hull_batched_impl(pts, offsets, k, out_idx, out_n, host_offsets, (cudaStream_t)stream, true);
+    return ch::hull_batched_impl(pts, offsets, k, out_idx, out_n, host_offsets, (cudaStream_t)stream, true,
+                                 nullptr);
 }
 
 namespace ch {
 
+int hull_batched_redo(const float* pts, const int64_t* host_offsets, int32_t k, int32_t* out_idx, int64_t* out_n,
+                      const unsigned char* flags, cudaStream_t s) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CH_ECUDA;
+    for (int i = 0; i < k; ++i) {
+        if (!flags[i]) continue;
+        const int64_t o = host_offsets[i];
+        const int st = enqueue_hull_nograph(pts + 2 * o, host_offsets[i + 1] - o, out_idx + o, out_n + i, s, dev);
+        if (st != CH_OK) return st;
+    }
+    return CH_OK;
+}
+
 int hull_batched_impl(const float* pts, const int64_t* offsets, int32_t k, int32_t* out_idx, int64_t* out_n,
-                      const int64_t* host_offsets, cudaStream_t s, bool allow_tune) {
+                      const int64_t* host_offsets, cudaStream_t s, bool allow_tune, unsigned char* redo_host) {
     if (k < 0 || k > (1 << 20)) return CH_EINVAL;
     if (k == 0) return CH_OK;
     if (!offsets || !out_n) return CH_EINVAL;
@@ -996,16 +1007,14 @@ int hull_batched_impl(const float* pts, const int64_t* offsets, int32_t k, int32
     bt_set_shape(c, d, off, shape);
     if ((st = bt_launch_graph(c, redo, dev, s)) != CH_OK) return st;
     // Sets the bucketed path could not finish (a bucket chain too long): the
-    // single-hull path, one by one.
+    // single-hull path, one by one, once their flags are on the host.
+    if (redo_host)
+        return cudaMemcpyAsync(redo_host, redo, (size_t)k, cudaMemcpyDeviceToHost, s) == cudaSuccess ? CH_OK
+                                                                                                    : CH_ECUDA;
     std::vector<unsigned char> big((size_t)k);
     if (cudaMemcpyAsync(big.data(), redo, (size_t)k, cudaMemcpyDeviceToHost, s) != cudaSuccess) return CH_ECUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return CH_ECUDA;
-    for (int i = 0; i < k; ++i) {
-        if (!big[i]) continue;
-        st = enqueue_hull_nograph(pts + 2 * off[i], off[i + 1] - off[i], out_idx + off[i], out_n + i, s, dev);
-        if (st != CH_OK) return st;
-    }
-    return CH_OK;
+    return hull_batched_redo(pts, off.data(), k, out_idx, out_n, big.data(), s);
 }
 
 }  // namespace ch

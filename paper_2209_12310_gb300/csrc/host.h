@@ -27,9 +27,15 @@ int check_points_args(const float* pts, long long n);
 int reserve_batched(int dev, cudaStream_t s, long long n, int k);
 void drop_batched_graphs(int dev, cudaStream_t s);
 // ch_hull_batched; allow_tune = false takes the nearest tuned size class
-// instead of tuning a new one (for callers that must not block).
+// instead of tuning a new one (for callers that must not block).  With
+// redo_host (pinned, k bytes) nothing synchronises: the per-set flags of sets
+// left to the single-hull path are copied there asynchronously, and the
+// caller runs hull_batched_redo on them once they have arrived (host_offsets
+// is then required).
 int hull_batched_impl(const float* pts, const int64_t* offsets, int32_t k, int32_t* out_idx, int64_t* out_n,
-                      const int64_t* host_offsets, cudaStream_t s, bool allow_tune);
+                      const int64_t* host_offsets, cudaStream_t s, bool allow_tune, unsigned char* redo_host);
+int hull_batched_redo(const float* pts, const int64_t* host_offsets, int32_t k, int32_t* out_idx, int64_t* out_n,
+                      const unsigned char* flags, cudaStream_t s);
 bool prof_enabled();
 void release_stream_workspace(int dev, cudaStream_t s);
 void release_batched();

@@ -94,6 +94,8 @@ struct Slot {
     std::vector<int64_t> off;       // host copy of the batch offsets
     int64_t* h_off = nullptr;       // pinned offsets (k + 1)
     int64_t* h_n = nullptr;         // pinned result counts (k)
+    unsigned char* h_redo = nullptr;  // pinned flags of sets left to the single-hull path (k)
+    bool redone = false;
     int32_t* h_idx = nullptr;       // pinned result indices
     size_t h_idx_cap = 0;
     size_t cap_k = 0;
@@ -151,6 +153,21 @@ bool Server::retire(Slot& sl) {
     char* base = arena_base + sl.arena_off;
     const int64_t total = sl.off[k];
     int32_t* d_idx = (int32_t*)(base + align256(8 * (size_t)total));
+    if (sl.phase == 1 && !sl.redone) {   // sets the batched kernels left to the single-hull path
+        sl.redone = true;
+        bool any = false;
+        for (size_t i = 0; i < k; ++i) any |= sl.h_redo[i] != 0;
+        if (any) {
+            float* d_pts = (float*)base;
+            int64_t* d_n = (int64_t*)(base + align256(8 * (size_t)total) + align256(4 * (size_t)total) +
+                                      align256(8 * (k + 1)));
+            if (hull_batched_redo(d_pts, sl.h_off, (int32_t)k, d_idx, d_n, sl.h_redo, sl.s) != CH_OK)
+                cudaMemsetAsync(d_n, 0xFF, 8 * k, sl.s);
+            cudaMemcpyAsync(sl.h_n, d_n, 8 * k, cudaMemcpyDeviceToHost, sl.s);
+            cudaEventRecord(sl.ev, sl.s);
+            return true;
+        }
+    }
     if (sl.phase == 1) {
         size_t hsum = 0;
         for (size_t i = 0; i < k; ++i) hsum += sl.h_n[i] > 0 ? (size_t)sl.h_n[i] : 0;
@@ -238,9 +255,11 @@ bool Server::launch(Slot& sl) {
     if (sl.cap_k < k) {
         if (sl.h_off) cudaFreeHost(sl.h_off);
         if (sl.h_n) cudaFreeHost(sl.h_n);
+        if (sl.h_redo) cudaFreeHost(sl.h_redo);
         sl.cap_k = std::max<size_t>(k, 256);
         cudaMallocHost((void**)&sl.h_off, 8 * (sl.cap_k + 1));
         cudaMallocHost((void**)&sl.h_n, 8 * sl.cap_k);
+        cudaMallocHost((void**)&sl.h_redo, sl.cap_k);
     }
     sl.off.assign(k + 1, 0);
     for (size_t i = 0; i < k; ++i) sl.off[i + 1] = sl.off[i] + batch[i]->n;
@@ -254,7 +273,10 @@ bool Server::launch(Slot& sl) {
         cudaMemcpyAsync(d_pts + 2 * sl.off[i], batch[i]->host, 8 * (size_t)batch[i]->n, cudaMemcpyHostToDevice,
                         sl.s);
     cudaMemcpyAsync(d_off, sl.h_off, 8 * (k + 1), cudaMemcpyHostToDevice, sl.s);
-    const int st = hull_batched_impl(d_pts, d_off, (int32_t)k, d_idx, d_n, sl.h_off, sl.s, false);
+    std::memset(sl.h_redo, 0, k);
+    sl.redone = false;
+    // no host synchronisation: the batch overlaps with the other slot's
+    const int st = hull_batched_impl(d_pts, d_off, (int32_t)k, d_idx, d_n, sl.h_off, sl.s, false, sl.h_redo);
     if (st != CH_OK) cudaMemsetAsync(d_n, 0xFF, 8 * k, sl.s);   // -1 = CH_EINVAL per set
     cudaMemcpyAsync(sl.h_n, d_n, 8 * k, cudaMemcpyDeviceToHost, sl.s);
     cudaEventRecord(sl.ev, sl.s);
@@ -411,6 +433,7 @@ int ch_server_destroy(void* srv) {
         if (sl.ev) cudaEventDestroy(sl.ev);
         if (sl.h_off) cudaFreeHost(sl.h_off);
         if (sl.h_n) cudaFreeHost(sl.h_n);
+        if (sl.h_redo) cudaFreeHost(sl.h_redo);
         if (sl.h_idx) cudaFreeHost(sl.h_idx);
         for (Req* r : sl.reqs) S->reqs.erase(r->ticket), delete r;
     }

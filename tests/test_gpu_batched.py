@@ -195,3 +195,16 @@ def test_batched_autotuner_cache_file(lib, tmp_path):
     other = next(s for s in SHAPES if s != tuned)
     cache.write_text(json.dumps({key: [other[0], other[1], us]}))
     assert child("read") == other
+
+
+def test_batched_set_left_to_single_hull_path(lib):
+    """Sets in convex position overflow their bucket chains; ch_hull_batched
+    finishes them with the single-hull path, beside ordinary sets."""
+    m = 5000
+    x = np.arange(m, dtype=np.int64)
+    conv = np.stack([x * 64, x * (x + 1) // 2], 1)
+    conv = conv[np.random.default_rng(4).permutation(m)].astype(np.float32)
+    assert oracle.hull(conv).size == m
+    sets = [W.uniform(30_000, 1), conv, W.ring(50_000, 2), conv[: m // 2].copy()]
+    for got, s in zip(_run(lib, sets), sets):
+        np.testing.assert_array_equal(got, oracle.hull(s))

@@ -81,3 +81,34 @@ def test_server_errors(lib):
         assert st == lib.CH_ERANGE and n == lib.CH_ERANGE
     finally:
         lib.ch_server_destroy(srv)
+
+
+def _convex_position(m, seed):
+    """m lattice points that are all hull vertices (a strictly convex arc),
+    shuffled: bucket chains overflow and the set takes the single-hull path."""
+    x = np.arange(m, dtype=np.int64)
+    y = x * (x + 1) // 2   # strictly convex: the slopes x + 1 increase (m <= 5792 keeps y < 2^24)
+    pts = np.stack([x * 64, y], 1)
+    rng = np.random.default_rng(seed)
+    return np.ascontiguousarray(pts[rng.permutation(m)].astype(np.float32))
+
+
+def test_server_set_left_to_single_hull_path(lib):
+    """A request whose bucket chains overflow is finished by the single-hull
+    path after the batch (no host wait inside the batch), in a mix."""
+    srv = lib.ch_server_create(2 << 30, 0)
+    try:
+        conv = _convex_position(5000, 3)
+        assert oracle.hull(conv).size == conv.shape[0]
+        reqs = [np.ascontiguousarray(W.normal(20_000, 5)), conv, np.ascontiguousarray(W.ring(30_000, 6)), conv]
+        tickets, caps = [], {}
+        for p in reqs:
+            st, t = lib.ch_submit(srv, p.ctypes.data, p.shape[0])
+            assert st == lib.CH_OK
+            tickets.append(t)
+            caps[t] = p.shape[0]
+        res = _wait(lib, srv, tickets, caps)
+        for t, p in zip(tickets, reqs):
+            np.testing.assert_array_equal(res[t], oracle.hull(p))
+    finally:
+        lib.ch_server_destroy(srv)
