@@ -177,6 +177,30 @@ def cpu_baseline(kind, seed, seconds):
                       f"single-threaded C Andrew monotone chain, {el:.1f} s"}
 
 
+def cpu_heaphull(kind, seed, seconds):
+    """The CPU heaphull comparator (oracle/heaphull_cpu.c: parallel extremes and
+    octagon filter, parallel sort, Andrew's chains) on one thread and on every
+    host core, on the same bounded sample as the CPU baseline."""
+    import oracle
+    from synth import workloads as W
+    n = 2_000_000
+    pts = W.make(kind, n, seed)
+    cores = os.cpu_count() or 1
+    out = {"unit": "points/s", "cores": cores, "kind": "CPU heaphull (POSIX threads)"}
+    for label, threads in (("value_1_thread", 1), ("value_all_cores", cores)):
+        oracle.heaphull_cpu(pts[:1000], threads)
+        reps, t0 = 0, time.perf_counter()
+        while True:
+            oracle.heaphull_cpu(pts, threads)
+            reps += 1
+            el = time.perf_counter() - t0
+            if el >= seconds:
+                break
+        out[label] = n * reps / el
+    out["sample"] = f"{n} points of the same {kind} distribution (seed {seed}), about {seconds:.1f} s per setting"
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -343,6 +367,7 @@ def run_ours(args):
 
     if rank == 0:
         cpu = cpu_baseline(kind, seed, args.cpu_seconds) if world == 1 else None
+        cpu_hh = cpu_heaphull(kind, seed, max(0.5, args.cpu_seconds / 4)) if world == 1 else None
         line = {
             "metric": "points/s (filter+hull, device-timed)", "value": value, "unit": "points/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -354,7 +379,7 @@ def run_ours(args):
                               "(256 MB write) before each step, steps timed one by one") if in_l2 else
                              f"inputs {8 * n / 1e6:.0f} MB per step > 129 MB L2 (no flush needed)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-            "roofline": roof, "kernels": kernels, "e2e": e2e, "cpu_baseline": cpu,
+            "roofline": roof, "kernels": kernels, "e2e": e2e, "cpu_baseline": cpu, "cpu_heaphull": cpu_hh,
             "gpu_launches": launches_per_step * args.steps, "clocks": clk,
         }
         if batched is not None:

@@ -15,6 +15,11 @@ Contents
                          four-queue labelling.
 * ``brute``           -- an O(n^3) edge-test hull for tiny inputs, used to
                          pin ``hull`` itself.
+* ``heaphull_cpu(pts, threads)`` -- the paper's heaphull on the host's cores
+                         (``heaphull_cpu.c``: parallel extremes and octagon
+                         filter, parallel sort, Andrew's chains): the CPU
+                         comparator the benchmark times; checked against
+                         ``hull`` by the tests, not a definition itself.
 """
 from __future__ import annotations
 
@@ -26,7 +31,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "andrew.c")
+_SRCS = [os.path.join(_HERE, "andrew.c"), os.path.join(_HERE, "heaphull_cpu.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
@@ -36,13 +41,13 @@ ORACLE_ERANGE = -2
 
 
 def build(force: bool = False) -> str:
-    """Compile ``andrew.c`` with gcc into ``oracle/_build/liboracle.so``."""
+    """Compile ``andrew.c`` and ``heaphull_cpu.c`` with gcc into ``oracle/_build/liboracle.so``."""
     os.makedirs(_BUILD, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(src) for src in _SRCS)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread", "-o", tmp, *_SRCS, "-lm"])
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -56,6 +61,8 @@ def _load():
             lib.oracle_hull.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
             lib.oracle_check.restype = ctypes.c_int
             lib.oracle_check.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+            lib.cpu_heaphull.restype = ctypes.c_int64
+            lib.cpu_heaphull.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int]
             _lib = lib
     return _lib
 
@@ -82,6 +89,20 @@ def hull(pts) -> np.ndarray:
         raise ValueError("coordinate outside the integer domain [0, 2**24)")
     if h < 0:
         raise MemoryError("oracle allocation failed")
+    return out[:h].copy()
+
+
+def heaphull_cpu(pts, threads: int = 1) -> np.ndarray:
+    """The CPU heaphull comparator on ``threads`` POSIX threads; same output
+    convention and errors as ``hull``."""
+    a = _as_points(pts)
+    n = a.shape[0]
+    out = np.empty(max(n, 1), dtype=np.int32)
+    h = _load().cpu_heaphull(a.ctypes.data, n, out.ctypes.data, int(threads))
+    if h == ORACLE_ERANGE:
+        raise ValueError("coordinate outside the integer domain [0, 2**24)")
+    if h < 0:
+        raise MemoryError("heaphull_cpu allocation failed")
     return out[:h].copy()
 
 
