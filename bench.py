@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 # on the bucketed path, the chain merge) only when the post pass raised its
 # graph condition.
 FILTER_LAUNCHES = 4
-LARGE_LAUNCHES = 12   # bk_prep, bk_hist, bk_bsum, bk_bstart, bk_items, bk_part1, bk_part2, bk_hull, 3 sort passes, chain
+LARGE_LAUNCHES = 13   # bk_prep, bk_hist, bk_bsum, bk_bstart, bk_items, bk_part1, bk_part2, bk_hull, sort_hist, 3 sort passes, chain
 L2_BYTES = 129 * 1024 * 1024
 
 

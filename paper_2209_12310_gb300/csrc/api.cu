@@ -294,6 +294,7 @@ static void enqueue_large_part(const float* pts, long long n, int32_t* out_idx, 
     {
         ProfScope p("sort", s);
         const int grid_sort = h.di.sms * h.di.occ_sort;
+        launch_sort_hist(h.kA, ctl, h.di.sms, s);
         launch_sort_pass(h.kA, h.vA, h.kB, h.vB, ctl, status, 0, grid_sort, s);
         launch_sort_pass(h.kB, h.vB, h.kA, h.vA, ctl, status, 1, grid_sort, s);
         launch_sort_pass(h.kA, h.vA, h.kB, h.vB, ctl, status, 2, grid_sort, s);
@@ -605,6 +606,22 @@ int ch_reserve(int64_t n, int32_t k, void* stream) {
 }
 
 size_t ch_workspace_bytes(int64_t n) { return n < 0 ? 0 : make_layout(n).total; }
+
+#if defined(CH_TRACE) || defined(CH_TIMELINE)
+// Debug builds: the phase timeline of the most recent call on the first
+// workspace (ns since the init kernel).
+int ch_trace_timeline(unsigned long long* out16) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (g_ws.empty() || !g_ws.begin()->second.base) return CH_EINVAL;
+    Ctl c;
+    if (cudaMemcpy(&c, g_ws.begin()->second.base, sizeof(Ctl), cudaMemcpyDeviceToHost) != cudaSuccess) return CH_ECUDA;
+    for (int i = 0; i < 8; ++i) {
+        out16[2 * i] = c.tl[i][0];
+        out16[2 * i + 1] = c.tl[i][1];
+    }
+    return CH_OK;
+}
+#endif
 
 int ch_release(void) {
     {

@@ -76,10 +76,7 @@ __global__ void bk_prep(Ctl* ctl, unsigned* bcount, unsigned bmax) {
     if (tid < 4) s_q[tid] = 0u;
     __syncthreads();
     if (!s_go) return;
-    for (int d = tid; d < kDigits; d += blockDim.x) {
-        const unsigned c = ctl->digit_hist[kSortPasses - 1][d];
-        if (c) atomicAdd(&s_q[d >> (kDigitBits - 2)], c);
-    }
+    if (tid < 4) s_q[tid] = ctl->rec_q[tid];
     __syncthreads();
     if (tid == 0) {
         s_base[0] = 0u;

@@ -105,7 +105,8 @@ struct Ctl {
     int records_ready;                  // sort records complete before the re-classify stage
     unsigned int blocks_done[4];        // last-arriver counters (sample, main, stage C, roots)
     unsigned int tile_ctr[4];           // onesweep tile claim counters
-    unsigned int digit_hist[kSortPasses][kDigits];
+    unsigned int digit_hist[kSortPasses][kDigits];   // sort fallback only (sort_hist_kernel)
+    unsigned int rec_q[4];              // records per queue
     unsigned int reg_start[4], reg_end[4];
     unsigned int reg_tile_base[5];      // chain tiles of queue r: [base[r], base[r+1])
     unsigned int counts4[4];            // survivors per queue (ch_filter)
@@ -120,6 +121,9 @@ struct Ctl {
     unsigned int bk_next;               // next bucket for a bk_hull warp
     Octagon oct;                        // octagon of the true extremes
     Octagon oct_s;                      // octagon of a sample's extremes
+#if defined(CH_TRACE) || defined(CH_TIMELINE)
+    unsigned long long tl[8][2];        // debug builds: first start / last end per phase (%globaltimer)
+#endif
 };
 
 // Optional phase tracing of single-block kernels (debug builds with
@@ -128,7 +132,7 @@ struct Ctl {
 __shared__ unsigned long long s_trace_t[24];
 __shared__ int s_trace_n;
 #define CH_TRACE_DECL if (threadIdx.x == 0) s_trace_n = 0;
-#define CH_TRACE_MARK() do { if (threadIdx.x == 0 && s_trace_n < 24) { unsigned long long _t; \
+#define CH_TRACE_MARK() do { if (threadIdx.x == 0 && s_trace_n >= 0 && s_trace_n < 24) { unsigned long long _t; \
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(_t)); s_trace_t[s_trace_n++] = _t; } } while (0)
 #define CH_TRACE_PRINT(tag) do { if (threadIdx.x == 0) { printf("[trace %s]", tag); \
     for (int _i = 1; _i < s_trace_n; ++_i) printf(" %llu", s_trace_t[_i] - s_trace_t[_i - 1]); printf("\n"); } } while (0)
@@ -136,6 +140,15 @@ __shared__ int s_trace_n;
 #define CH_TRACE_DECL
 #define CH_TRACE_MARK() do { } while (0)
 #define CH_TRACE_PRINT(tag) do { } while (0)
+#endif
+// Debug builds (-DCH_TRACE or -DCH_TIMELINE): grid-wide phase timeline, the
+// first start and the last end of each phase in ctl->tl.
+#if defined(CH_TRACE) || defined(CH_TIMELINE)
+#define CH_TL(ctl, slot, end) do { if (threadIdx.x == 0) { unsigned long long _t; \
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(_t)); \
+    if (end) atomicMax(&(ctl)->tl[slot][1], _t); else atomicMin(&(ctl)->tl[slot][0], _t); } } while (0)
+#else
+#define CH_TL(ctl, slot, end) do { } while (0)
 #endif
 
 // ---------------------------------------------------------------------------

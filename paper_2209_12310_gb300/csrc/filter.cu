@@ -63,7 +63,7 @@ __global__ void init_kernel(Ctl* ctl, int mode) {
         ctl->samp_packed[t] = 0ull;
         ctl->line_ep[t] = (t & 1) ? 0ull : ~0ull;   // even: minimum slot, odd: maximum slot
     }
-    if (t < 4) { ctl->tile_ctr[t] = 0u; ctl->counts4[t] = 0u; ctl->blocks_done[t] = 0u; }
+    if (t < 4) { ctl->tile_ctr[t] = 0u; ctl->counts4[t] = 0u; ctl->blocks_done[t] = 0u; ctl->rec_q[t] = 0u; }
     if (t == 0) {
         ctl->status = CH_OK;
         ctl->abort = 0;
@@ -78,6 +78,12 @@ __global__ void init_kernel(Ctl* ctl, int mode) {
     }
     unsigned* h = &ctl->digit_hist[0][0];
     for (int i = t; i < kSortPasses * kDigits; i += blockDim.x) h[i] = 0u;
+#if defined(CH_TRACE) || defined(CH_TIMELINE)
+    if (t < 8) { ctl->tl[t][0] = ~0ull; ctl->tl[t][1] = 0ull; }
+    __syncthreads();
+    CH_TL(ctl, 0, 0);
+    CH_TL(ctl, 0, 1);
+#endif
 }
 
 // Warp tiles read by the sample pass: about 1/32 of the input, at most
@@ -107,6 +113,7 @@ __global__ void __launch_bounds__(256) sample_kernel(const float* __restrict__ p
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    CH_TL(ctl, 1, 0);
     unsigned long long best[8];
 #pragma unroll
     for (int d = 0; d < 8; ++d) best[d] = 0ull;
@@ -147,7 +154,11 @@ __global__ void __launch_bounds__(256) sample_kernel(const float* __restrict__ p
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = s_red[w][threadIdx.x] > m ? s_red[w][threadIdx.x] : m;
         if (m) atomicMax(&ctl->samp_packed[threadIdx.x], m);
     }
+    CH_TL(ctl, 1, 1);
     if (!last_block(&ctl->blocks_done[0], &s_last)) return;
+    CH_TL(ctl, 2, 0);
+    CH_TRACE_DECL
+    CH_TRACE_MARK();
     __shared__ int s_v[2][8];
     __shared__ int s_ok;
     if (threadIdx.x == 0) s_ok = nsamp > 0;
@@ -169,17 +180,23 @@ __global__ void __launch_bounds__(256) sample_kernel(const float* __restrict__ p
         s_v[1][d] = y;
     }
     __syncthreads();
+    CH_TRACE_MARK();
     if (!s_ok) {   // too few points to sample: run the two-pass path
         if (threadIdx.x == 0) ctl->mode = 1;
         return;
     }
     const int ext[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
     setup_octagon_block(s_o, s_v[0], s_v[1], ext, true);
+    CH_TRACE_MARK();
+
     if (s_o.discard_none) {
         if (threadIdx.x == 0) ctl->mode = 1;
         return;
     }
     copy_octagon(&ctl->oct_s, &s_o);
+    CH_TRACE_MARK();
+    CH_TL(ctl, 2, 1);
+    CH_TRACE_PRINT("sample-last");
 }
 
 // ---------------------------------------------------------------------------
@@ -442,9 +459,7 @@ __device__ __noinline__ void finalize_block(const float* __restrict__ pts, long 
             const unsigned pos = lane < 8 ? (unsigned)lane : atomicAdd(&ctl->count, 1u);
             keys[pos] = key;
             vals[pos] = make_val(v, (uint32_t)s_id[d]);
-#pragma unroll
-            for (int p = 0; p < kSortPasses; ++p)
-                atomicAdd(&ctl->digit_hist[p][(key >> (p * kDigitBits)) & (kDigits - 1)], 1u);
+            atomicAdd(&ctl->rec_q[r], 1u);
         }
     }
     __syncthreads();
@@ -469,6 +484,7 @@ __global__ void __launch_bounds__(256, 2) main_kernel(const float* __restrict__ 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    CH_TL(ctl, 3, 0);
     if (threadIdx.x == 0) s_mode = *(volatile int*)&ctl->mode;   // one read: uniform per block
     if (threadIdx.x < 4) {
         s_inner[threadIdx.x] = ctl->oct_s.in_lo[threadIdx.x];
@@ -607,12 +623,15 @@ __global__ void __launch_bounds__(256, 2) main_kernel(const float* __restrict__ 
     // The block that finishes last builds the octagon of the true extremes.
     // Every bulk copy of this block has completed (or was drained), so the
     // ring's shared memory is free for it.
+    CH_TL(ctl, 3, 1);
     if (!last_block(&ctl->blocks_done[1], &s_mode)) return;
+    CH_TL(ctl, 4, 0);
     CH_TRACE_DECL
     CH_TRACE_MARK();
     if (__syncthreads_or(read_status(ctl) != CH_OK)) return;
     finalize_block(pts, n, head, ctl, *reinterpret_cast<Octagon*>(dsm), keys, vals);
     CH_TRACE_PRINT("finalize");
+    CH_TL(ctl, 4, 1);
 }
 
 // ---------------------------------------------------------------------------

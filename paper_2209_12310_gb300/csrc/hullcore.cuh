@@ -467,6 +467,7 @@ static __device__ bool qh_chains(QhSmem& q, int m, int* mv) {
         const int r = q.rs[i], u = q.ru[i];
         q.rs[i] = (q.vu[2 * r] < u && u < q.vu[2 * r + 1]) ? 2 * r : -1;
     }
+    CH_TRACE_MARK();
     for (int round = 0;; ++round) {
         const int nv = s_nvert;
         // depths; each segment's maximum
@@ -491,6 +492,7 @@ static __device__ bool qh_chains(QhSmem& q, int m, int* mv) {
             q.rs[i] = a;
         }
         __syncthreads();
+        CH_TRACE_MARK();
         if (tid == 0) s_changed = 0;
         // the deepest record per segment: smallest u, then index
         for (int i = tid; i < m; i += T) {
@@ -502,6 +504,7 @@ static __device__ bool qh_chains(QhSmem& q, int m, int* mv) {
                 atomicMin(&q.segarg[a], ((unsigned long long)u << 31) | (unsigned)q.ri[i]);
         }
         __syncthreads();
+        CH_TRACE_MARK();
         // insert the new vertices
         for (int a = tid; a < nv; a += T) {
             q.splitu[a] = -1;
@@ -530,6 +533,7 @@ static __device__ bool qh_chains(QhSmem& q, int m, int* mv) {
             s_changed = 1;
         }
         __syncthreads();
+        CH_TRACE_MARK();
         if (s_fail || (s_changed && round + 1 >= kQhRounds)) return false;
         if (!s_changed) break;
     }

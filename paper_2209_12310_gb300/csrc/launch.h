@@ -19,6 +19,7 @@ void launch_post(const float* pts, long long n, int head, long long ntiles, Ctl*
 void launch_labels(const float* pts, long long n, Ctl* ctl, uint8_t* labels, int grid, cudaStream_t s);
 void launch_filter_output(const Ctl* ctl, long long n, int32_t* out_ext8, int64_t* out_counts4, cudaStream_t s);
 
+void launch_sort_hist(const uint32_t* keys, Ctl* ctl, int grid, cudaStream_t s);
 void launch_sort_pass(const uint32_t* kin, const uint64_t* vin, uint32_t* kout, uint64_t* vout,
                       Ctl* ctl, unsigned long long* status, int pass, int grid, cudaStream_t s);
 

@@ -150,29 +150,47 @@ __device__ __forceinline__ void inner_bounds(const int lo0[4], const int hi0[4],
     }
 }
 
-__device__ __forceinline__ bool inner_fits(const Octagon& o, const int lo[4], const int hi[4]) {
-    if (lo[0] > hi[0] || lo[1] > hi[1] || lo[2] > hi[2] || lo[3] > hi[3]) return false;
+// Candidate vertex k of the region with bounds lo / hi: the intersection of
+// consecutive bounding lines x=xl, x+y=sl, y=yl, x-y=dh, x=xh, x+y=sh, y=yh,
+// x-y=dl (in that order).
+__device__ __forceinline__ void inner_corner(const int lo[4], const int hi[4], int k, long long& px, long long& py) {
     const long long xl = lo[0], xh = hi[0], yl = lo[1], yh = hi[1];
     const long long sl = lo[2], sh = hi[2], dl = lo[3] - kCoordLimit, dh = hi[3] - kCoordLimit;
-    // consecutive lines: x=xl, x+y=sl, y=yl, x-y=dh, x=xh, x+y=sh, y=yh, x-y=dl
-    const long long px[8] = {xl, sl - yl, dh + yl, xh, xh, sh - yh, dl + yh, xl};
-    const long long py[8] = {sl - xl, yl, yl, xh - dh, sh - xh, yh, yh, xl - dl};
+    switch (k) {
+        case 0: px = xl; py = sl - xl; break;
+        case 1: px = sl - yl; py = yl; break;
+        case 2: px = dh + yl; py = yl; break;
+        case 3: px = xh; py = xh - dh; break;
+        case 4: px = xh; py = sh - xh; break;
+        case 5: px = sh - yh; py = yh; break;
+        case 6: px = dl + yh; py = yh; break;
+        default: px = xl; py = xl - dl; break;
+    }
+}
+
+__device__ __forceinline__ bool inner_fits(const Octagon& o, const int lo[4], const int hi[4]) {
+    if (lo[0] > hi[0] || lo[1] > hi[1] || lo[2] > hi[2] || lo[3] > hi[3]) return false;
 #pragma unroll
-    for (int k = 0; k < 8; ++k)
-        if (!in_closed_octagon_exact(o, px[k], py[k])) return false;
+    for (int k = 0; k < 8; ++k) {
+        long long px, py;
+        inner_corner(lo, hi, k, px, py);
+        if (!in_closed_octagon_exact(o, px, py)) return false;
+    }
     return true;
 }
 
 // Fills every field of o (in shared memory) from the 8 vertices.  The whole
-// block calls it (all threads, same arguments; blockDim.x >= 12).  Threads
-// 0..7 build the edges, 8..11 the quadrilateral; with with_inner, the threads
-// then search the inner region's scale t/1024 in parallel: each thread checks
-// one coarse scale, then the scales between the best coarse one and the next.
-// Without it the inner region is empty (every test takes the exact path).
+// block calls it (all threads, same arguments; blockDim.x >= 64).  Threads
+// 0..7 build the edges, 8..11 the quadrilateral; with with_inner, the block
+// then searches the inner region's scale t/1024: rounds of a 4-way search in
+// which each of up to 3 candidate scales has its 64 (corner, edge) exact
+// tests done by 64 threads at once.  Only scales whose test passed are kept,
+// so the region is verified whatever the search finds.  Without with_inner
+// the inner region is empty (every test takes the exact path).
 static __device__ void setup_octagon_block(Octagon& o, const int vx[8], const int vy[8], const int ext[8],
                                            bool with_inner) {
-    __shared__ int s_best;
     __shared__ long long s_area[8];
+    __shared__ int s_lo, s_hi, s_bad[3];
     const int tid = (int)threadIdx.x;
     if (tid < 8) {
         const int j = (tid + 1) & 7;
@@ -185,7 +203,10 @@ static __device__ void setup_octagon_block(Octagon& o, const int vx[8], const in
         const int r = tid - 8, a = 2 * r, b = (2 * r + 2) & 7;
         o.quad[r] = make_edge(vx[a], vy[a], vx[b], vy[b]);
     }
-    if (tid == 0) s_best = 0;
+    if (tid == 0) {
+        s_lo = 0;      // the largest scale verified so far (0: none)
+        s_hi = 1025;   // a scale known not to fit
+    }
     __syncthreads();
     long long area2 = 0;
 #pragma unroll
@@ -195,25 +216,50 @@ static __device__ void setup_octagon_block(Octagon& o, const int vx[8], const in
     const int lo0[4] = {vx[W], vy[S], vx[SW] + vy[SW], vx[NW] - vy[NW] + kCoordLimit};
     const int hi0[4] = {vx[E], vy[N], vx[NE] + vy[NE], vx[SE] - vy[SE] + kCoordLimit};
     if (with_inner && !none) {
-        const int nthr = (int)blockDim.x;
-        const int step = (1024 + nthr - 1) / nthr;
-        int lo[4], hi[4];
-        const int tc = step * (tid + 1);
-        if (tc <= 1024) {
-            inner_bounds(lo0, hi0, tc, lo, hi);
-            if (inner_fits(o, lo, hi)) atomicMax(&s_best, tc);
+        // thread: candidate j = tid / 64, corner k = (tid / 8) % 8, edge e = tid % 8;
+        // nc = 3 (or 1 for blocks below 192 threads) candidates split (lo, hi)
+        // into nc + 1 = 2^sh parts (32-bit arithmetic, shifts only)
+        const int j = tid >> 6, k = (tid >> 3) & 7, e = tid & 7;
+        const int nc = blockDim.x >= 192 ? 3 : 1, sh = blockDim.x >= 192 ? 2 : 1;
+        const Edge ed = o.oct[e];
+        for (int round = 0; round < 12; ++round) {
+            const int lo = s_lo, hi = s_hi;
+            if (hi - lo <= 1) break;
+            if (tid < 3) s_bad[tid] = 0;
+            __syncthreads();
+            const int t = lo + (((hi - lo) * (j + 1)) >> sh);
+            if (j < nc && t > lo && t < hi) {
+                int bl[4], bh[4];
+                inner_bounds(lo0, hi0, t, bl, bh);
+                bool bad = bl[0] > bh[0] || bl[1] > bh[1] || bl[2] > bh[2] || bl[3] > bh[3];
+                if (!bad && (ed.dx | ed.dy) != 0) {
+                    long long px, py;
+                    inner_corner(bl, bh, k, px, py);
+                    bad = edge_exact(ed, px, py) < 0;
+                }
+                if (bad) s_bad[j] = 1;
+            }
+            __syncthreads();
+            if (tid == 0) {   // the largest passing candidate; the next failing one above it
+                int nlo = lo, nhi = hi;
+                for (int c = 0; c < nc; ++c) {
+                    const int tc = lo + (((hi - lo) * (c + 1)) >> sh);
+                    if (tc <= lo || tc >= hi) continue;
+                    if (!s_bad[c]) nlo = tc > nlo ? tc : nlo;
+                }
+                for (int c = nc - 1; c >= 0; --c) {
+                    const int tc = lo + (((hi - lo) * (c + 1)) >> sh);
+                    if (tc > nlo && tc < nhi && s_bad[c]) nhi = tc;
+                }
+                s_lo = nlo;
+                s_hi = nhi;
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        const int tf = s_best + 1 + tid;
-        if (tid < step - 1 && tf <= 1024) {
-            inner_bounds(lo0, hi0, tf, lo, hi);
-            if (inner_fits(o, lo, hi)) atomicMax(&s_best, tf);
-        }
-        __syncthreads();
     }
     if (tid == 0) {
         o.discard_none = none;
-        const int t1 = (with_inner && !none) ? s_best : 0;
+        const int t1 = (with_inner && !none) ? s_lo : 0;
         if (t1 > 0) {
             int lo[4], hi[4];
             inner_bounds(lo0, hi0, t1, lo, hi);

@@ -44,11 +44,10 @@ __device__ __forceinline__ void rec_flush_warp(RecBuf& b, unsigned& cnt, Ctl* ct
 }
 
 // Warp-collective: classifies one point per lane (valid = false for none) and
-// stages the kept ones.  Histograms of the three sort digits are counted in
-// shared memory.
+// stages the kept ones.  Records per queue are counted per warp (lane 0's qn).
 __device__ __forceinline__ void post_point(bool valid, float x, float y, unsigned idx, const Octagon& o, RecBuf& b,
                                            unsigned& cnt, Ctl* ctl, uint32_t* keys, uint64_t* vals,
-                                           unsigned (*s_hist)[kDigits]) {
+                                           unsigned (&qn)[4]) {
     int r = -1, X = 0, Y = 0;
     if (valid) {
         X = __float2int_rn(x);
@@ -61,15 +60,14 @@ __device__ __forceinline__ void post_point(bool valid, float x, float y, unsigne
     const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
     if (!bal) return;
     if (cnt + (unsigned)__popc(bal) > (unsigned)kRecBuf) rec_flush_warp(b, cnt, ctl, keys, vals);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) qn[q] += __popc(__ballot_sync(0xFFFFFFFFu, keep && r == q));
     if (keep) {
         uint32_t u, v;
         queue_frame(r, X, Y, u, v);
-        const uint32_t key = make_key(r, u);
         const unsigned pos = cnt + __popc(bal & lanemask_lt());
-        b.key[pos] = key;
+        b.key[pos] = make_key(r, u);
         b.val[pos] = make_val(v, idx);
-#pragma unroll
-        for (int p = 0; p < kSortPasses; ++p) atomicAdd(&s_hist[p][(key >> (p * kDigitBits)) & (kDigits - 1)], 1u);
     }
     cnt += __popc(bal);
     __syncwarp();
@@ -99,17 +97,22 @@ __device__ void rec_flush_block(RecBuf& b, unsigned cnt, Ctl* ctl, uint32_t* key
     }
 }
 
-__device__ __forceinline__ void flush_hist(unsigned (*s_hist)[kDigits], Ctl* ctl) {
+// The block's records per queue (warp counts) into ctl->rec_q.
+__device__ __forceinline__ void flush_queue_counts(const unsigned (&qn)[4], Ctl* ctl) {
+    __shared__ unsigned s_q[4];
+    if (threadIdx.x < 4) s_q[threadIdx.x] = 0u;
     __syncthreads();
-    for (int i = threadIdx.x; i < kSortPasses * kDigits; i += blockDim.x) {
-        const unsigned c = (&s_hist[0][0])[i];
-        if (c) atomicAdd(&(&ctl->digit_hist[0][0])[i], c);
-    }
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (qn[q]) atomicAdd(&s_q[q], qn[q]);
+    __syncthreads();
+    if (threadIdx.x < 4 && s_q[threadIdx.x]) atomicAdd(&ctl->rec_q[threadIdx.x], s_q[threadIdx.x]);
 }
 
 // The block that finished last: support-line records, then with at most
 // kMidCap records the hull (quickhull rounds, else the sort-based mid_hull).
-// Every other record is already in keys/vals and in the digit histograms.
+// Every other record is already in keys/vals and in the per-queue counts.
 __device__ void post_last_block(const float* __restrict__ pts, long long n, Ctl* ctl, const Octagon& o,
                                 uint32_t* keys, uint64_t* vals, int32_t* out_idx, int64_t* out_n, char* dyn,
                                 unsigned long long cond) {
@@ -141,11 +144,7 @@ __device__ void post_last_block(const float* __restrict__ pts, long long n, Ctl*
     if (tid < 8 && s_lpos[tid] >= 0) {
         keys[s_lpos[tid]] = s_lkey[tid];
         vals[s_lpos[tid]] = s_lval[tid];
-        if (!small) {
-#pragma unroll
-            for (int p = 0; p < kSortPasses; ++p)
-                atomicAdd(&ctl->digit_hist[p][(s_lkey[tid] >> (p * kDigitBits)) & (kDigits - 1)], 1u);
-        }
+        if (!small) atomicAdd(&ctl->rec_q[s_lkey[tid] >> kKeyBits], 1u);
     }
     if (!small) {   // the large-survivor path follows
         if (cond && tid == 0) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, 1u);
@@ -190,17 +189,16 @@ __global__ void __launch_bounds__(kPostThreads, 1) post_kernel(const float* __re
                                                                unsigned long long cond) {
     extern __shared__ __align__(16) char dyn[];
     __shared__ Octagon s_o;
-    __shared__ unsigned s_hist[kSortPasses][kDigits];
     __shared__ int s_flag, s_mode;
     __shared__ unsigned s_nraw;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    CH_TL(ctl, 5, 0);
     if (tid == 0) {
         s_flag = read_status(ctl);
         s_mode = *(volatile int*)&ctl->mode;
         s_nraw = *(volatile unsigned*)&ctl->count_raw;
     }
     copy_octagon(&s_o, &ctl->oct);
-    for (int i = tid; i < kSortPasses * kDigits; i += blockDim.x) (&s_hist[0][0])[i] = 0u;
     __syncthreads();
     if (s_flag != CH_OK) {   // data error or timeout of an earlier stage
         if (blockIdx.x == 0 && tid == 0) { *out_n = s_flag; ctl->done = 1; }
@@ -208,6 +206,7 @@ __global__ void __launch_bounds__(kPostThreads, 1) post_kernel(const float* __re
     }
     RecBuf& rb = reinterpret_cast<RecBuf*>(dyn)[warp];
     unsigned rc = 0u;
+    unsigned qn[4] = {0u, 0u, 0u, 0u};
     if (s_mode == 1) {   // two-pass mode: every point
         const long long gwarp = ((long long)blockIdx.x * blockDim.x + tid) >> 5;
         const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -221,8 +220,8 @@ __global__ void __launch_bounds__(kPostThreads, 1) post_kernel(const float* __re
             const long long i0 = head + t * kWarpTilePts + 2 * lane;
 #pragma unroll
             for (int j = 0; j < kLoadsPerLane; ++j) {
-                post_point(true, v[j].x, v[j].y, (unsigned)(i0 + 64 * j), s_o, rb, rc, ctl, keys, vals, s_hist);
-                post_point(true, v[j].z, v[j].w, (unsigned)(i0 + 64 * j + 1), s_o, rb, rc, ctl, keys, vals, s_hist);
+                post_point(true, v[j].x, v[j].y, (unsigned)(i0 + 64 * j), s_o, rb, rc, ctl, keys, vals, qn);
+                post_point(true, v[j].z, v[j].w, (unsigned)(i0 + 64 * j + 1), s_o, rb, rc, ctl, keys, vals, qn);
             }
         }
         if (gwarp == 0) {   // the unaligned head point and the ragged tail
@@ -233,7 +232,7 @@ __global__ void __launch_bounds__(kPostThreads, 1) post_kernel(const float* __re
                     const bool valid = i < ranges[rg][1];
                     float x = 0.0f, y = 0.0f;
                     if (valid) { x = pts[2 * i]; y = pts[2 * i + 1]; }
-                    post_point(valid, x, y, (unsigned)i, s_o, rb, rc, ctl, keys, vals, s_hist);
+                    post_point(valid, x, y, (unsigned)i, s_o, rb, rc, ctl, keys, vals, qn);
                 }
         }
     } else {   // fused mode: the raw survivors of the main pass
@@ -250,13 +249,16 @@ __global__ void __launch_bounds__(kPostThreads, 1) post_kernel(const float* __re
                 y = (float)(unsigned)(xy & 0xFFFFFFFFull);
                 idx = raw_idx[i];
             }
-            post_point(valid, x, y, idx, s_o, rb, rc, ctl, keys, vals, s_hist);
+            post_point(valid, x, y, idx, s_o, rb, rc, ctl, keys, vals, qn);
         }
     }
     rec_flush_block(rb, rc, ctl, keys, vals);
-    flush_hist(s_hist, ctl);
+    flush_queue_counts(qn, ctl);
+    CH_TL(ctl, 5, 1);
     if (!last_block(&ctl->blocks_done[2], &s_flag)) return;
+    CH_TL(ctl, 6, 0);
     post_last_block(pts, n, ctl, s_o, keys, vals, out_idx, out_n, dyn, cond);
+    CH_TL(ctl, 6, 1);
 }
 
 // ---------------------------------------------------------------------------

@@ -176,6 +176,30 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(
     }
 }
 
+// Digit histograms of the records for the three passes (the sort-based
+// fallback only: the bucketed path needs none and leaves bk_state == 1).
+__global__ void __launch_bounds__(kSortThreads) sort_hist_kernel(const uint32_t* __restrict__ keys, Ctl* ctl) {
+    __shared__ unsigned s_h[kSortPasses][kDigits];
+    if (*(volatile int*)&ctl->done || read_status(ctl) != CH_OK || *(volatile int*)&ctl->bk_state == 1) return;
+    for (int i = threadIdx.x; i < kSortPasses * kDigits; i += blockDim.x) (&s_h[0][0])[i] = 0u;
+    __syncthreads();
+    const unsigned count = ctl->count;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        const uint32_t k = keys[i];
+#pragma unroll
+        for (int p = 0; p < kSortPasses; ++p) atomicAdd(&s_h[p][(k >> (p * kDigitBits)) & (kDigits - 1)], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kSortPasses * kDigits; i += blockDim.x) {
+        const unsigned c = (&s_h[0][0])[i];
+        if (c) atomicAdd(&(&ctl->digit_hist[0][0])[i], c);
+    }
+}
+
+void launch_sort_hist(const uint32_t* keys, Ctl* ctl, int grid, cudaStream_t s) {
+    sort_hist_kernel<<<grid, kSortThreads, 0, s>>>(keys, ctl);
+}
+
 void launch_sort_pass(const uint32_t* kin, const uint64_t* vin, uint32_t* kout, uint64_t* vout,
                       Ctl* ctl, unsigned long long* status, int pass, int grid, cudaStream_t s) {
     onesweep_kernel<<<grid, kSortThreads, 0, s>>>(kin, vin, kout, vout, ctl, status, pass);

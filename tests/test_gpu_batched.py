@@ -205,6 +205,9 @@ def test_batched_set_left_to_single_hull_path(lib):
     conv = np.stack([x * 64, x * (x + 1) // 2], 1)
     conv = conv[np.random.default_rng(4).permutation(m)].astype(np.float32)
     assert oracle.hull(conv).size == m
-    sets = [W.uniform(30_000, 1), conv, W.ring(50_000, 2), conv[: m // 2].copy()]
+    i = np.arange(11_000, dtype=np.int64)   # a narrow U in convex position: bucket chains overflow
+    y = np.concatenate([[0], np.cumsum(i[:-1] - 5500)])
+    u_arc = np.stack([i * 1500, y - y.min() + 5], 1)[np.random.default_rng(6).permutation(11_000)].astype(np.float32)
+    sets = [W.uniform(30_000, 1), conv, W.ring(50_000, 2), conv[: m // 2].copy(), u_arc]
     for got, s in zip(_run(lib, sets), sets):
         np.testing.assert_array_equal(got, oracle.hull(s))

@@ -172,3 +172,23 @@ def test_repeated_calls_replay_graph(lib):
         big = W.uniform(2_000_000, 23)
         got = lib.hull(torch.from_numpy(big).cuda(), stream=stream).cpu().numpy()
         np.testing.assert_array_equal(got, oracle.hull(big))
+
+
+def _u_arc(m, seed):
+    """m lattice points in strictly convex position forming a narrow U (slopes
+    -m/2 .. m/2): near the bottom the points crowd into a few u-buckets, whose
+    chains overflow, so the call takes the radix-sort fallback."""
+    i = np.arange(m, dtype=np.int64)
+    s = i - m // 2
+    y = np.concatenate([[0], np.cumsum(s[:-1])])
+    pts = np.stack([i * 1500, y - y.min() + 5], 1)
+    rng = np.random.default_rng(seed)
+    return pts[rng.permutation(m)].astype(np.float32)
+
+
+def test_sort_fallback_when_bucket_chains_overflow(lib):
+    pts = _u_arc(11_000, 1)
+    assert oracle.hull(pts).size == pts.shape[0]
+    assert_same(lib, pts)
+    # a repeat replays the captured graph, through its conditional node
+    assert_same(lib, pts)
