@@ -7,10 +7,27 @@
 
 namespace ch {
 
-// Hull-rule classification: -1 = dropped, else queue.
+// Hull-rule classification: -1 = dropped, else queue.  Fast paths: the inner
+// region (dropped), and a point that float edge functions put surely beyond
+// quad edge r (the first quad edge it is not surely left of) and surely
+// outside octagon edge 2r or 2r+1 (the two octagon edges over quad edge r):
+// no closed-octagon point is strictly outside an edge, so the point is queue
+// r's.  Everything else takes the exact slow path.
 __device__ __forceinline__ int classify_hull(float x, float y, const Octagon& o) {
     const int X = __float2int_rn(x), Y = __float2int_rn(y);
     if (in_inner(o, X, Y)) return -1;
+    float e[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) e[r] = edge_float(o.quad[r], x, y);
+    const int r = e[0] <= kEdgeTol ? 0 : e[1] <= kEdgeTol ? 1 : e[2] <= kEdgeTol ? 2 : e[3] <= kEdgeTol ? 3 : 4;
+    if (r < 4) {
+        const float er = r == 0 ? e[0] : r == 1 ? e[1] : r == 2 ? e[2] : e[3];
+        if (er < -kEdgeTol) {
+            if (o.discard_none) return r;
+            const float a = edge_float(o.oct[2 * r], x, y), b = edge_float(o.oct[2 * r + 1], x, y);
+            if (fminf(a, b) < -kEdgeTol) return r;
+        }
+    }
     return classify_hull_slow(x, y, &o);
 }
 
