@@ -66,6 +66,7 @@ def workload_config(name, n):
         "normal": "isotropic normal, centre (2^23, 2^23), sigma 2^21, rounded, clamped to [0, 2^24)",
         "ring": "ring: angle U[0, 2pi), radius 2^23 - U[0, 64), rounded, clamped",
         "uniform": "uniform integers in [0, 2^24)^2",
+        "distorted": "circumference with 2% distortion: angle U[0, 2pi), radius 2^23 (1 - 0.02 U[0, 1)), rounded, clamped",
     }[kind]
     return kind, (n or n0), seed, desc
 

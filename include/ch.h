@@ -177,6 +177,19 @@ size_t ch_workspace_bytes(int64_t n);
 /* Free every workspace of every device (synchronises the streams involved). */
 int ch_release(void);
 
+/*
+ * ch_selftest_timeout -- test support for failure detection: runs one of the
+ * library's bounded device waits on a condition that never comes true
+ * (which = 0: the radix-sort look-back poll on a flag nothing sets; 1: the
+ * bulk-copy barrier wait with no copy issued).  The wait gives up after its
+ * limit (well under a second) and the kernel returns; nothing traps or
+ * faults and the context stays usable.  Returns the status the device
+ * recorded, CH_ETIMEOUT when the wait gave up as designed; CH_EINVAL for a
+ * bad `which`; CH_ENOMEM / CH_ECUDA for allocation or launch failures.
+ * Synchronises `stream`.
+ */
+int ch_selftest_timeout(int which, void* stream);
+
 /* Static text for a status code. */
 const char* ch_strerror(int status);
 

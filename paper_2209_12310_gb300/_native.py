@@ -43,6 +43,7 @@ SIGNATURES = {
     "ch_reserve": (_INT, [_I64, _I32, _P]),
     "ch_workspace_bytes": (_SZ, [_I64]),
     "ch_release": (_INT, []),
+    "ch_selftest_timeout": (_INT, [_INT, _P]),
     "ch_strerror": (ctypes.c_char_p, [_INT]),
     "ch_profile_enable": (_INT, [_INT]),
     "ch_profile_reset": (_INT, []),

@@ -199,6 +199,20 @@ __device__ __forceinline__ void set_status(Ctl* ctl, int st) {
     atomicCAS(&ctl->status, CH_OK, st);
 }
 
+// One poll of a bounded wait on a flag another block sets: false to poll
+// again (after a short sleep); true to give up, after kSpinLimit polls or
+// when another wait already gave up (then status CH_ETIMEOUT and the abort
+// flag are set, and the caller leaves the wait).
+__device__ __forceinline__ bool spin_give_up(unsigned& spins, Ctl* ctl) {
+    if (++spins > kSpinLimit || ((spins & 63u) == 0u && *(volatile int*)&ctl->abort)) {
+        set_status(ctl, CH_ETIMEOUT);
+        atomicExch(&ctl->abort, 1);
+        return true;
+    }
+    __nanosleep(64);
+    return false;
+}
+
 __device__ __forceinline__ int read_status(const Ctl* ctl) {
     return *(volatile const int*)&ctl->status;
 }

@@ -147,12 +147,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_kernel(
                         --tp;
                         continue;
                     }
-                    if (++spins > kSpinLimit || ((spins & 63u) == 0u && *(volatile int*)&ctl->abort)) {
-                        set_status(ctl, CH_ETIMEOUT);
-                        atomicExch(&ctl->abort, 1);
-                        break;
-                    }
-                    __nanosleep(64);
+                    if (spin_give_up(spins, ctl)) break;
                 }
                 st_volatile(my + d, pack_status(epoch, true, excl + tot[h]));
             }

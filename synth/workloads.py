@@ -19,6 +19,8 @@ stand-ins:
             half-to-even and clamped to [0, 2**24 - 1]
 * ring:     angle uniform in [0, 2 pi), radius 2**23 - u with u uniform in
             [0, 64), centred at (2**23, 2**23), rounded and clamped
+* distorted: the circumference with "2% distortion": radius 2**23 (1 - 0.02 u),
+            u uniform in [0, 1), otherwise as ring
 * batched:  4096 instances, sizes log-uniform in [100, 1e6], each drawn from
             one of the three generators above
 * serving:  Poisson arrivals at 20,000 req/s, sizes log-uniform in
@@ -77,6 +79,27 @@ def ring(n: int, seed: int) -> np.ndarray:
     return out
 
 
+DISTORTION = 0.02
+
+
+def distorted(n: int, seed: int) -> np.ndarray:
+    """The paper's worst case with "2% distortion" (Sec. 4; parameters not
+    given): points near the circle of radius 2**23 about (2**23, 2**23), the
+    radius jittered inward by up to 2% of it (angle uniform in [0, 2 pi),
+    radius R (1 - 0.02 U[0, 1))), rounded and clamped."""
+    rng = np.random.default_rng(seed)
+    theta = rng.uniform(0.0, 2.0 * math.pi, size=n)
+    f = rng.uniform(0.0, 1.0, size=n)
+    out = np.empty((n, 2), dtype=np.float32)
+    step = 1 << 22
+    for s in range(0, n, step):
+        e = min(n, s + step)
+        r = RING_RADIUS * (1.0 - DISTORTION * f[s:e])
+        out[s:e, 0] = _clip_round(CENTER + r * np.cos(theta[s:e]))
+        out[s:e, 1] = _clip_round(CENTER + r * np.sin(theta[s:e]))
+    return out
+
+
 def make(kind: str, n: int, seed: int) -> np.ndarray:
     if kind == "uniform":
         return uniform(n, seed)
@@ -84,6 +107,8 @@ def make(kind: str, n: int, seed: int) -> np.ndarray:
         return normal(n, seed)
     if kind == "ring":
         return ring(n, seed)
+    if kind == "distorted":
+        return distorted(n, seed)
     raise ValueError(f"unknown generator {kind!r}")
 
 
@@ -92,6 +117,7 @@ SINGLE = {
     "uniform_1e6": ("uniform", 1_000_000, 0),
     "normal_1e8": ("normal", 100_000_000, 1),
     "ring_1e8": ("ring", 100_000_000, 2),
+    "distorted_1e8": ("distorted", 100_000_000, 5),
 }
 
 

@@ -44,6 +44,8 @@ def assert_same(ch, pts, offset_points=0):
     ("uniform", 513, 7),
     ("uniform", 511, 8),
     ("ring", 4096 * 3 + 17, 9),
+    ("distorted", 1_000_003, 5),         # the circumference with 2% distortion
+    ("distorted", 30_000, 10),
 ])
 def test_hull_matches_oracle(lib, kind, n, seed):
     assert_same(lib, W.make(kind, n, seed))
@@ -139,9 +141,9 @@ def test_tensor_helper(lib):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("name", ["normal_1e8", "ring_1e8"])
+@pytest.mark.parametrize("name", ["normal_1e8", "ring_1e8", "distorted_1e8"])
 def test_full_size_workloads(lib, name):
-    """The 1e8-point normal and ring workloads in the benchmark's launch shape,
+    """The 1e8-point normal, ring and distorted workloads in the benchmark's launch shape,
     checked bit-exactly against the oracle and by the defining invariants."""
     pts = W.single(name)
     h, got = gpu_hull(lib, pts)

@@ -87,7 +87,7 @@ def test_oracle_matches_scipy_on_general_position():
         np.testing.assert_array_equal(got, ref)
 
 
-@pytest.mark.parametrize("kind", ["uniform", "normal", "ring"])
+@pytest.mark.parametrize("kind", ["uniform", "normal", "ring", "distorted"])
 def test_oracle_invariants_on_workloads(kind):
     pts = W.make(kind, 200_000, seed=11)
     check_hull(pts, oracle.hull(pts))
@@ -134,3 +134,15 @@ def test_oracle_accepts_domain_edges():
     pts = np.array([[0, 0], [16777215, 0], [16777215, 16777215], [0, 16777215], [-0.0, 5]],
                    np.float32)
     np.testing.assert_array_equal(oracle.hull(pts), [0, 1, 2, 3])
+
+
+def test_distorted_workload_shape():
+    """The 2%-distortion stand-in: integer points in the domain, within 2% of
+    the radius inside the circle (plus rounding), angles spread round it."""
+    pts = W.distorted(100_000, 5).astype(np.float64)
+    assert pts.min() >= 0 and pts.max() < (1 << 24)
+    assert np.all(pts == np.rint(pts))
+    r = np.hypot(pts[:, 0] - (1 << 23), pts[:, 1] - (1 << 23)) / float(1 << 23)
+    assert r.max() <= 1.0 + 1e-6 and r.min() >= 0.98 - 1e-6
+    ang = np.arctan2(pts[:, 1] - (1 << 23), pts[:, 0] - (1 << 23))
+    assert np.histogram(ang, bins=8)[0].min() > 10_000
