@@ -212,17 +212,34 @@ __global__ void __launch_bounds__(kPostThreads, 1) post_kernel(const float* __re
         const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
         const float4* p4 = reinterpret_cast<const float4*>(pts + 2 * head);
         const unsigned long long pol = l2_evict_first();
-        for (long long t = gwarp; t < ntiles; t += nwarps) {
-            const float4* base = p4 + t * kWarpTileF4 + lane;
-            float4 v[kLoadsPerLane];
+        // one float4 (two points) per step with the loads of the next kAhead
+        // steps in flight: a rolled loop keeps the classification code small.
+        // Steps run over this warp's tiles, kLoadsPerLane float4 per tile.
+        constexpr int kAhead = 4;
+        const long long total = ntiles * kLoadsPerLane;
+        const long long sstep = nwarps * kLoadsPerLane;
+        auto next_step = [&](long long st) {
+            return (st % kLoadsPerLane == kLoadsPerLane - 1) ? st + sstep - (kLoadsPerLane - 1) : st + 1;
+        };
+        long long s = gwarp * kLoadsPerLane, sl = s;   // sl: the step of the newest load
+        float4 q[kAhead];
 #pragma unroll
-            for (int j = 0; j < kLoadsPerLane; ++j) v[j] = ld_stream_f4(base + j * 32, pol);
-            const long long i0 = head + t * kWarpTilePts + 2 * lane;
+        for (int a = 0; a < kAhead; ++a) {
+            q[a] = sl < total ? ld_stream_f4(p4 + sl * 32 + lane, pol) : make_float4(0.f, 0.f, 0.f, 0.f);
+            sl = next_step(sl);
+        }
+#pragma unroll 1
+        while (s < total) {
+            const float4 v = q[0];
 #pragma unroll
-            for (int j = 0; j < kLoadsPerLane; ++j) {
-                post_point(true, v[j].x, v[j].y, (unsigned)(i0 + 64 * j), s_o, rb, rc, ctl, keys, vals, qn);
-                post_point(true, v[j].z, v[j].w, (unsigned)(i0 + 64 * j + 1), s_o, rb, rc, ctl, keys, vals, qn);
-            }
+            for (int a = 0; a + 1 < kAhead; ++a) q[a] = q[a + 1];
+            q[kAhead - 1] = sl < total ? ld_stream_f4(p4 + sl * 32 + lane, pol) : make_float4(0.f, 0.f, 0.f, 0.f);
+            sl = next_step(sl);
+            const long long t = s / kLoadsPerLane, j = s % kLoadsPerLane;
+            const long long i0 = head + t * kWarpTilePts + 64 * j + 2 * lane;
+            post_point(true, v.x, v.y, (unsigned)i0, s_o, rb, rc, ctl, keys, vals, qn);
+            post_point(true, v.z, v.w, (unsigned)(i0 + 1), s_o, rb, rc, ctl, keys, vals, qn);
+            s = next_step(s);
         }
         if (gwarp == 0) {   // the unaligned head point and the ragged tail
             const long long ranges[2][2] = {{0, head}, {head + ntiles * kWarpTilePts, n}};
