@@ -7,6 +7,20 @@
 
 namespace ch {
 
+// Debug builds (-DCH_PHASEPROF): cycles per phase of the warp chain, summed
+// over all warps (lane 0 adds each phase's clock delta).
+#ifdef CH_PHASEPROF
+static __device__ unsigned long long g_bk_phase[16];
+#define CH_PH_DECL unsigned long long _ph_t = clock64();
+#define CH_PH(k) do { const unsigned long long _t = clock64(); \
+    if ((threadIdx.x & 31) == 0) atomicAdd(&g_bk_phase[k], _t - _ph_t); _ph_t = _t; } while (0)
+#define CH_PH_COUNT(k) do { if ((threadIdx.x & 31) == 0) atomicAdd(&g_bk_phase[k], 1ull); } while (0)
+#else
+#define CH_PH_DECL
+#define CH_PH(k) do { } while (0)
+#define CH_PH_COUNT(k) do { } while (0)
+#endif
+
 constexpr int kBkPer = 9;               // records per lane
 constexpr int kBkWCap = 32 * kBkPer;    // records a warp holds at once
 constexpr int kBkV = kBkChain + 2;      // quickhull vertices of one bucket
@@ -38,6 +52,8 @@ __device__ __forceinline__ long long bk_depth(const int4 g, int u, int v) {
 // the chain would exceed kBkV vertices.
 static __device__ int bk_warp_chain(BkWarp& w, BkRecs& R, int m) {
     const int lane = threadIdx.x & 31;
+    CH_PH_DECL
+    CH_PH_COUNT(15);
     constexpr unsigned long long kVMask = (1ull << kKeyBits) - 1ull;
     unsigned long long ks = ~0ull, ke = 0ull;
 #pragma unroll
@@ -71,6 +87,7 @@ static __device__ int bk_warp_chain(BkWarp& w, BkRecs& R, int m) {
     ie = __reduce_min_sync(0xFFFFFFFFu, ie);
     const int su = (int)(ks >> kKeyBits), eu = (int)(ke >> kKeyBits);
     const int vs = (int)(ks & kVMask), ve = (int)(kVMask - (ke & kVMask));
+    CH_PH(1);
     for (int a = lane; a < kBkV; a += 32) {
         w.segmax[a] = 0ull;
         w.segarg[a] = ~0ull;
@@ -155,8 +172,10 @@ static __device__ int bk_warp_chain(BkWarp& w, BkRecs& R, int m) {
     for (int k = 0; k < kBkPer; ++k)
         if (R.s[k] == 0) R.s[k] = R.u[k] < fu ? 0 : (R.u[k] > fu ? 2 : -1);
     __syncwarp();
+    CH_PH(2);
     int nv = 3;
     for (int round = 1;; ++round) {
+        CH_PH_COUNT(14);
         // depths; each segment's maximum
         int live = 0;
 #pragma unroll
@@ -179,6 +198,7 @@ static __device__ int bk_warp_chain(BkWarp& w, BkRecs& R, int m) {
             }
             live += __popc(__ballot_sync(0xFFFFFFFFu, R.s[k] >= 0));
         }
+        CH_PH(3);
         // records below the chain only: packed to the first slots when that
         // saves slots (each round keeps a small part of the records)
         if (live + 31 < ((m + 31) & ~31)) {
@@ -214,6 +234,7 @@ static __device__ int bk_warp_chain(BkWarp& w, BkRecs& R, int m) {
             __syncwarp();
         }
         __syncwarp();
+        CH_PH(4);
         // the deepest record per segment: smallest u, then index
 #pragma unroll
         for (int k = 0; k < kBkPer; ++k) {
@@ -223,6 +244,7 @@ static __device__ int bk_warp_chain(BkWarp& w, BkRecs& R, int m) {
                 atomicMin(&w.segarg[a], ((unsigned long long)R.u[k] << 31) | (unsigned)R.i[k]);
         }
         __syncwarp();
+        CH_PH(5);
         int added = 0;
         bool over = false;
         for (int a0 = 0; a0 < nv; a0 += 32) {
@@ -259,6 +281,7 @@ static __device__ int bk_warp_chain(BkWarp& w, BkRecs& R, int m) {
         }
         if (__any_sync(0xFFFFFFFFu, over)) return -1;
         __syncwarp();
+        CH_PH(6);
         if (added == 0) break;
         nv += added;
         if (round + 1 >= kBkV) return -1;
@@ -272,6 +295,7 @@ static __device__ int bk_warp_chain(BkWarp& w, BkRecs& R, int m) {
         }
     len = __shfl_sync(0xFFFFFFFFu, len, 0);
     __syncwarp();
+    CH_PH(7);
     return len;
 }
 
@@ -286,24 +310,34 @@ __device__ __forceinline__ int bk_stream_chain(BkWarp& w, unsigned cnt, Load loa
     const int lane = threadIdx.x & 31;
     int len = 0;
     for (unsigned c0 = 0; c0 < cnt;) {
+        CH_PH_DECL
         const unsigned take = min(cnt - c0, (unsigned)(kBkWCap - len));
         const int m = len + (int)take;
         BkRecs R;
+        // every slot loads (an index clamped into this chunk, take >= 1), so
+        // the loads of all slots are in flight together; then the carried
+        // chain and the empty slots override
 #pragma unroll
         for (int k = 0; k < kBkPer; ++k) {
             const int j = k * 32 + lane;
-            R.u[k] = 0;
-            R.v[k] = 0;
-            R.i[k] = 0;
+            const int g = min(max(j - len, 0), (int)take - 1);
+            load(c0 + (unsigned)g, R.u[k], R.v[k], R.i[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < kBkPer; ++k) {
+            const int j = k * 32 + lane;
             if (j < len) {
                 R.u[k] = w.cu[j];
                 R.v[k] = w.cv[j];
                 R.i[k] = w.ci[j];
-            } else if (j < m) {
-                load(c0 + (unsigned)(j - len), R.u[k], R.v[k], R.i[k]);
+            } else if (j >= m) {
+                R.u[k] = 0;
+                R.v[k] = 0;
+                R.i[k] = 0;
             }
         }
         __syncwarp();
+        CH_PH(0);
         const int l2 = bk_warp_chain(w, R, m);
         if (l2 < 0 || l2 > kBkChain) return -1;
         len = l2;

@@ -379,6 +379,18 @@ void launch_bucket_pass(Ctl* ctl, uint32_t* kA, uint64_t* vA, uint32_t* kB, uint
     }
 }
 
+#ifdef CH_PHASEPROF
+}  // namespace ch
+extern "C" int ch_phase_read(unsigned long long* out16) {
+    return cudaMemcpyFromSymbol(out16, ch::g_bk_phase, sizeof(unsigned long long) * 16) == cudaSuccess ? 0 : -4;
+}
+extern "C" int ch_phase_reset(void) {
+    unsigned long long z[16] = {};
+    return cudaMemcpyToSymbol(ch::g_bk_phase, z, sizeof(z)) == cudaSuccess ? 0 : -4;
+}
+namespace ch {
+#endif
+
 cudaError_t configure_bucket_kernels() {
     int occ = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bk_hull, kBkWarps * 32, 0);
