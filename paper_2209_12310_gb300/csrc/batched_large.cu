@@ -229,20 +229,22 @@ __global__ void __launch_bounds__(kChainThreads) btl_chain(BLArgs a) {
         const unsigned b0 = a.seg_bbase[sg] + t_local * kBkGroup, b1 = a.seg_bbase[sg + 1];
         int len = 0;
         if (tid < kBkGroup && b0 + tid < b1) {
-            const unsigned b = b0 + tid;
-            len = __ldcg(a.blen + b);
+            len = __ldcg(a.blen + b0 + tid);
             if (len < 0) {
                 s_fail = 1;
                 len = 0;
             }
-            const size_t o = (size_t)b * kBkChain;
-            for (int j = 0; j < len; ++j) {
-                su[tid * kBkChain + j] = __ldcg(a.bu + o + j);
-                sv[tid * kBkChain + j] = __ldcg(a.bv + o + j);
-                si[tid * kBkChain + j] = __ldcg(a.bi + o + j);
-            }
         }
         s_len[tid] = len;
+        {   // the tile's bucket chain slots are contiguous: coalesced block copy
+            const unsigned nb_t = b1 > b0 ? min(b1 - b0, (unsigned)kBkGroup) : 0u;
+            const size_t o0 = (size_t)b0 * kBkChain;
+            for (unsigned e = tid; e < nb_t * kBkChain; e += blockDim.x) {
+                su[e] = __ldcg(a.bu + o0 + e);
+                sv[e] = __ldcg(a.bv + o0 + e);
+                si[e] = __ldcg(a.bi + o0 + e);
+            }
+        }
         __syncthreads();
         if (s_fail && tid == 0) atomicExch(&a.ctl[i].bk_state, 2);
         const bool root = tile_merge_climb(su, sv, si, s_len, s_mv, kBkChain, kBkGroup, tb, c, rb, ct, t_local,

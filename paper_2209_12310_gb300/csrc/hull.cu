@@ -107,6 +107,7 @@ __global__ void __launch_bounds__(kChainThreads) chain_kernel(Ctl* ctl, HullBufs
     const int nseg = bk ? kBkGroup : kChainThreads;        // leaf chains per tile
 
     for (unsigned c = blockIdx.x; c < total_tiles; c += gridDim.x) {
+        CH_MG_DECL
         int r = 0;
         while (r < 3 && c >= s_tb[r + 1]) ++r;
         const unsigned rb = s_tb[r];
@@ -117,21 +118,15 @@ __global__ void __launch_bounds__(kChainThreads) chain_kernel(Ctl* ctl, HullBufs
         const unsigned te = min(q1, ts + (bk ? (unsigned)kBkGroup : (unsigned)kChainTile));
 
         if (bk) {
-            // 1') the tile's bucket chains (buckets q0 + t_local * kBkGroup + tid)
-            int len = 0;
-            if (tid < kBkGroup) {
-                const unsigned b = ts + tid;
-                if (b < te) {
-                    len = __ldcg(hb.blen + b);
-                    const size_t o = (size_t)b * kBkChain;
-                    for (int j = 0; j < len; ++j) {
-                        su[tid * kBkChain + j] = __ldcg(hb.bu + o + j);
-                        sv[tid * kBkChain + j] = __ldcg(hb.bv + o + j);
-                        si[tid * kBkChain + j] = __ldcg(hb.bi + o + j);
-                    }
-                }
+            // 1') the tile's bucket chains (buckets ts .. te): their slots are
+            // contiguous, so the whole block copies them with coalesced loads
+            s_len[tid] = (tid < kBkGroup && ts + tid < te) ? __ldcg(hb.blen + ts + tid) : 0;
+            const size_t o0 = (size_t)ts * kBkChain;
+            for (unsigned e = tid; e < (te - ts) * kBkChain; e += blockDim.x) {
+                su[e] = __ldcg(hb.bu + o0 + e);
+                sv[e] = __ldcg(hb.bv + o0 + e);
+                si[e] = __ldcg(hb.bi + o0 + e);
             }
-            s_len[tid] = len;
         } else {
         // 1) run reduction + per-thread chain (records [ts + 16 tid, +16)).
         {
@@ -162,6 +157,7 @@ __global__ void __launch_bounds__(kChainThreads) chain_kernel(Ctl* ctl, HullBufs
         }
         }
         __syncthreads();
+        CH_MG(0);
         const TreeBufs tb{hb.cu, hb.cv, hb.ci, hb.clen, hb.counters, hb.ctcap};
         const bool root = tile_merge_climb(su, sv, si, s_len, s_mv, seg, nseg, tb, c, rb, ct, t_local, s_red, &s_old);
         __syncthreads();
@@ -197,14 +193,28 @@ __global__ void __launch_bounds__(kChainThreads) chain_kernel(Ctl* ctl, HullBufs
         __syncthreads();
         const int* X = hb.xbuf;
         const int* Y = hb.ybuf;
+        CH_MG(7);
         stitch_core(hb.vbuf, m, hb.kbuf, hb.vbuf + m,
                     [&](int p, long long& x, long long& y) { x = __ldcg(X + p); y = __ldcg(Y + p); }, hb.n, ctl,
                     hb.out_idx, hb.out_n);
+        CH_MG(8);
         return;
     }
 }
 
 // ---------------------------------------------------------------------------
+#ifdef CH_PHASEPROF
+}  // namespace ch
+extern "C" int ch_phase_read_merge(unsigned long long* out16) {
+    return cudaMemcpyFromSymbol(out16, ch::g_mg_phase, sizeof(unsigned long long) * 16) == cudaSuccess ? 0 : -4;
+}
+extern "C" int ch_phase_reset_merge(void) {
+    unsigned long long z[16] = {};
+    return cudaMemcpyToSymbol(ch::g_mg_phase, z, sizeof(z)) == cudaSuccess ? 0 : -4;
+}
+namespace ch {
+#endif
+
 size_t chain_smem_bytes() { return (size_t)3 * kMergeSmemCap * sizeof(int); }
 
 void launch_chain(Ctl* ctl, const uint32_t* keys, const uint64_t* vals, const int* bu, const int* bv,

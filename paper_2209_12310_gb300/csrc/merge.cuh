@@ -13,6 +13,18 @@
 
 namespace ch {
 
+// Debug builds (-DCH_PHASEPROF): cycles per phase of the merge tree, summed
+// over blocks (thread 0 adds each phase's clock delta).
+#ifdef CH_PHASEPROF
+static __device__ unsigned long long g_mg_phase[16];
+#define CH_MG_DECL unsigned long long _mg_t = clock64();
+#define CH_MG(k) do { const unsigned long long _t = clock64(); \
+    if (threadIdx.x == 0) atomicAdd(&g_mg_phase[k], _t - _mg_t); _mg_t = _t; } while (0)
+#else
+#define CH_MG_DECL
+#define CH_MG(k) do { } while (0)
+#endif
+
 // Block-cooperative bridge: repeated 256-way probing of the monotone keep
 // predicates (each probe is a sequential binary search over the other chain).
 template <bool kGlobal>
@@ -92,6 +104,7 @@ static __device__ bool tile_merge_climb(int* su, int* sv, int* si, int* s_len, i
                                         int* s_red, int* s_old_p) {
     const int tid = threadIdx.x;
     int& s_old = *s_old_p;
+    CH_MG_DECL
         // 2) pairwise merge of the tile's leaf chains: the bridge of each pair
         //    by its leader thread, then the kept part of the right chain moved
         //    down by one warp per pair (a left shift, copied forward in chunks
@@ -139,6 +152,7 @@ static __device__ bool tile_merge_climb(int* su, int* sv, int* si, int* s_len, i
             }
             __syncthreads();
         }
+        CH_MG(1);
         // 3) write the tile chain.
         const int len = s_len[0];
         {
@@ -148,6 +162,7 @@ static __device__ bool tile_merge_climb(int* su, int* sv, int* si, int* s_len, i
             }
             if (tid == 0) hb.clen[c] = len;
         }
+        CH_MG(2);
         // 4) climb the merge tree of queue r.
         unsigned L = 0, k = t_local;
         bool root = false;
@@ -199,9 +214,11 @@ static __device__ bool tile_merge_climb(int* su, int* sv, int* si, int* s_len, i
             }
             if (tid == 0) hb.counters[(size_t)L * hb.ctcap + rb + ((k >> 1) << (L + 1))] = 0;
             __syncthreads();
+            CH_MG(L < 4 ? 3 : (L < 8 ? 4 : 5));
             ++L;
             k >>= 1;
         }
+        CH_MG(6);
     return root;
 }
 
