@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(256) btl_scatter(BLArgs a) {
     }
 }
 
-__global__ void __launch_bounds__(kBLWarps * 32) btl_bucket_hull(BLArgs a) {
+__global__ void __launch_bounds__(kBLWarps * 32, 4) btl_bucket_hull(BLArgs a) {
     __shared__ BkWarp s_w[kBLWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     BkWarp& w = s_w[warp];

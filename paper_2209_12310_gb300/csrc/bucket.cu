@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(kPtThreads, 1) bk_part2(Ctl* ctl, const uint32
     }
 }
 
-__global__ void __launch_bounds__(kBkWarps * 32) bk_hull(Ctl* ctl, const uint32_t* keys, const uint64_t* vals,
+__global__ void __launch_bounds__(kBkWarps * 32, 4) bk_hull(Ctl* ctl, const uint32_t* keys, const uint64_t* vals,
                                                         const unsigned* bstart, const unsigned* bcount,
                                                         int* bu, int* bv, int* bi, int* blen) {
     __shared__ BkWarp s_w[kBkWarps];
