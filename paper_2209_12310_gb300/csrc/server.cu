@@ -228,11 +228,15 @@ bool Server::launch(Slot& sl) {
     {
         std::lock_guard<std::mutex> lk(mu);
         // FIFO admission: take queue-head requests while the batch still fits
-        // the workspace and a contiguous arena block exists for it.
+        // the workspace and a contiguous arena block exists for it.  A batch
+        // takes at most half the arena's points (a single request may take
+        // more), so that the other slot's batch fits beside it: one batch's
+        // copies then overlap the other's kernels.
+        const int64_t cap = std::max<int64_t>(max_points / kSlots, 1);
         while (!queue.empty() && (int)batch.size() < kMaxBatch) {
             Req* r = queue.front();
             const int64_t np = points + r->n;
-            if (np > max_points) break;
+            if (np > max_points || (!batch.empty() && np > cap)) break;
             if (batch_bytes(np, batch.size() + 1) > arena.size()) break;
             batch.push_back(r);
             points = np;
