@@ -43,16 +43,21 @@ constexpr int kMergeSmemCap = 8192;           // chain points a global merge kee
 constexpr int kBkAvg = 256;
 constexpr int kBkChain = 32;
 constexpr int kBkGroup = kChainTile / kBkChain;
-// At least this many buckets per queue (at most one per 8 records): a queue's
-// u-range cut this finely makes each bucket a nearly straight strip of the
-// hull boundary even for sets of a few thousand points on a circle, so
-// bucket chains stay short.
+// Buckets of a queue of cnt records: about kBkAvg records each, and at least
+// 7 cnt^(1/3) (at most one per 8 records).  The queue chain of cnt records
+// on a thin ring (the ring workload: width 64 at radius 2^23) has about
+// 54 cnt^(1/3) vertices, so a bucket holds about 8 of them and its chain
+// stays within kBkChain; a queue whose chains still overflow takes the
+// radix-sort path.  kBkMinQ bounds the floor (7 cnt^(1/3) - cnt / kBkAvg
+// stays below 115), for the workspace bounds.
 constexpr int kBkMinQ = 256;
 constexpr int kBkCoarseMax = 4096;   // coarse bucket groups of the two-level partition at most
 
 __host__ __device__ __forceinline__ unsigned bk_buckets_for(unsigned cnt) {
     unsigned nb = (cnt + kBkAvg - 1) / kBkAvg;
-    const unsigned lo = (cnt / 8u < (unsigned)kBkMinQ) ? cnt / 8u : (unsigned)kBkMinQ;
+    unsigned ring = (unsigned)(7.0f * cbrtf((float)cnt)) + 1u;
+    ring = ring < (unsigned)kBkMinQ ? ring : (unsigned)kBkMinQ;
+    const unsigned lo = (cnt / 8u < ring) ? cnt / 8u : ring;
     nb = nb > lo ? nb : lo;
     return nb > 0u ? nb : 1u;
 }
