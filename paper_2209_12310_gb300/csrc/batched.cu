@@ -289,13 +289,38 @@ __global__ void __launch_bounds__(kBOctThreads) bt_octagon(BArgs a) {
 
 // Per tile of T x P points: every thread loads its P points (a batch of at
 // most 8 at a time, all loads in flight together), then classifies them.
+// Survivors are staged per warp (kBtWarpRecs records) and written out in
+// batches: one returning atomic per batch instead of one per 32 points.
+constexpr int kBtWarpRecs = 128;
+struct BtWarpBuf {
+    uint64_t val[kBtWarpRecs];
+    uint32_t key[kBtWarpRecs];
+};
+
+__device__ __forceinline__ void bt_flush(BtWarpBuf& b, unsigned& cnt, Ctl* c, uint32_t* keys, uint64_t* vals,
+                                         long long rb) {
+    const int lane = threadIdx.x & 31;
+    if (cnt == 0u) return;
+    unsigned base = 0u;
+    if (lane == 0) base = atomicAdd(&c->count, cnt);
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    for (unsigned j = lane; j < cnt; j += 32) {
+        keys[rb + base + j] = b.key[j];
+        vals[rb + base + j] = b.val[j];
+    }
+    __syncwarp();
+    cnt = 0u;
+}
+
 template <int T, int P>
 __global__ void __launch_bounds__(T) bt_filter(BArgs a, int ntiles) {
     constexpr int kBTile = T * P;
     constexpr int kB = P < 8 ? P : 8;   // points loaded together
     __shared__ Octagon s_o;
     __shared__ int s_set, s_skip;
+    __shared__ BtWarpBuf s_wb[T / 32];
     const int tid = threadIdx.x, lane = tid & 31;
+    BtWarpBuf& wb = s_wb[tid >> 5];
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         if (tid == 0) {
             const int i = tile_set(a, t);
@@ -313,6 +338,8 @@ __global__ void __launch_bounds__(T) bt_filter(BArgs a, int ntiles) {
             const long long p1 = min(ni, p0 + kBTile);
             const long long rb = region_base(a, i);
             const float2* p2 = reinterpret_cast<const float2*>(a.pts) + base;
+            unsigned wcnt = 0u;                      // records staged in wb
+            unsigned qn[4] = {0u, 0u, 0u, 0u};       // records per queue (lane 0)
             for (long long b0 = p0; b0 < p1; b0 += (long long)T * kB) {   // uniform trip counts
                 float2 pv[kB];
 #pragma unroll
@@ -335,23 +362,26 @@ __global__ void __launch_bounds__(T) bt_filter(BArgs a, int ntiles) {
                 if (reduce_on_line(s_o, keep, X, Y, (unsigned)p, c)) keep = false;
                 const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
                 if (!bal) continue;
-                unsigned pos0 = 0u;
-                if (lane == 0) pos0 = atomicAdd(&c->count, (unsigned)__popc(bal));
-                pos0 = __shfl_sync(0xFFFFFFFFu, pos0, 0);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const unsigned bq = __ballot_sync(0xFFFFFFFFu, keep && r == q);
-                    if (bq && lane == 0) atomicAdd(&c->counts4[q], (unsigned)__popc(bq));
-                }
+                for (int q = 0; q < 4; ++q) qn[q] += __popc(__ballot_sync(0xFFFFFFFFu, keep && r == q));
+                if (wcnt + (unsigned)__popc(bal) > (unsigned)kBtWarpRecs) bt_flush(wb, wcnt, c, a.keys, a.vals, rb);
                 if (keep) {
                     uint32_t u, v;
                     queue_frame(r, X, Y, u, v);
-                    const long long pos = rb + pos0 + __popc(bal & lanemask_lt());
-                    a.keys[pos] = make_key(r, u);
-                    a.vals[pos] = make_val(v, (uint32_t)p);
+                    const unsigned pos = wcnt + __popc(bal & lanemask_lt());
+                    wb.key[pos] = make_key(r, u);
+                    wb.val[pos] = make_val(v, (uint32_t)p);
                 }
+                wcnt += __popc(bal);
+                __syncwarp();
                 }
             }
+            // the tile's records and queue counts (a tile never spans two sets)
+            bt_flush(wb, wcnt, c, a.keys, a.vals, rb);
+            if (lane == 0)
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (qn[q]) atomicAdd(&c->counts4[q], qn[q]);
         }
         __syncthreads();
     }
