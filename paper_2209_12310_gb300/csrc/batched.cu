@@ -387,13 +387,19 @@ __global__ void __launch_bounds__(T) bt_filter(BArgs a, int ntiles) {
     }
 }
 
-constexpr size_t bt_cmax(size_t x, size_t y) { return x > y ? x : y; }
-constexpr size_t kBHullSmem = bt_cmax(kMidSmemBytes, sizeof(QhSmem));
+// One block per set, in two kernels.  bt_hull_small (every set): the
+// support-line records, then the hull of a set of at most kBSmallRec records
+// in a small shared-memory footprint (several blocks per SM).  bt_hull (the
+// other sets): the hull when one block can hold the records, else the set is
+// flagged for the bucketed path.  A small set whose quickhull rounds exceed
+// their vertex capacity is flagged the same way.
+constexpr int kBSmallRec = 2048;        // records of a small set
+constexpr int kBSmallVert = 256;        // quickhull vertices of a small set
+constexpr int kBSmallThreads = 256;
+using QhSmall = QhSmemT<kBSmallRec, kBSmallVert>;
 
-// One block per set: support-line records, then the hull of the records when
-// one block can hold them (else the set is flagged for the single-hull path).
-__global__ void __launch_bounds__(kBHullThreads, 1) bt_hull(BArgs a) {
-    extern __shared__ __align__(16) char dyn[];
+__global__ void __launch_bounds__(kBSmallThreads) bt_hull_small(BArgs a) {
+    __shared__ QhSmall q;
     __shared__ unsigned long long s_lep[8];
     __shared__ uint64_t s_lval[8];
     __shared__ unsigned s_lkey[8];
@@ -427,11 +433,44 @@ __global__ void __launch_bounds__(kBHullThreads, 1) bt_hull(BArgs a) {
         a.vals[rb + s_lpos[tid]] = s_lval[tid];
         atomicAdd(&c->counts4[s_lkey[tid] >> kKeyBits], 1u);
     }
+    if (total > (unsigned)kBSmallRec) return;   // bt_hull's
+    __syncthreads();   // also makes this block's line records visible to it
+    for (unsigned j = tid; j < total; j += blockDim.x) {
+        const uint32_t k = __ldcg(a.keys + rb + j);
+        const uint64_t w = __ldcg(a.vals + rb + j);
+        q.ru[j] = (int)(k & kKeyMask);
+        q.rv[j] = (int)(w >> 31);
+        q.ri[j] = (int)(w & 0x7FFFFFFFull);
+        q.rs[j] = (int)(k >> kKeyBits);
+    }
+    __syncthreads();
+    if (qh_chains(q, (int)total, &s_mv)) {
+        stitch_cycle(q.ru, q.rv, q.ri, s_mv, q.rs, c, ni, a.out_idx + base, a.out_n + i);
+        if (tid == 0) c->done = 1;
+    } else if (tid == 0) {
+        a.big[i] = 1;   // too many chain vertices for the small footprint: the bucketed path
+        c->done = 1;
+    }
+}
+
+constexpr size_t bt_cmax(size_t x, size_t y) { return x > y ? x : y; }
+constexpr size_t kBHullSmem = bt_cmax(kMidSmemBytes, sizeof(QhSmem));
+
+__global__ void __launch_bounds__(kBHullThreads, 1) bt_hull(BArgs a) {
+    extern __shared__ __align__(16) char dyn[];
+    __shared__ int s_done, s_mv;
+    const int i = blockIdx.x, tid = threadIdx.x;
+    Ctl* c = a.ctl + i;
+    if (tid == 0) s_done = *(volatile int*)&c->done;
+    __syncthreads();
+    if (s_done) return;   // empty or failed, or done by bt_hull_small
+    const unsigned total = *(volatile unsigned*)&c->count;   // with the line records
+    const long long rb = region_base(a, i);
+    const long long base = a.offsets[i], ni = a.offsets[i + 1] - base;
     if (total > (unsigned)kMidCap) {
         if (tid == 0) a.big[i] = 1;
         return;
     }
-    __syncthreads();
     QhSmem& q = *reinterpret_cast<QhSmem*>(dyn);
     for (unsigned j = tid; j < total; j += blockDim.x) {
         const uint32_t k = __ldcg(a.keys + rb + j);
@@ -770,7 +809,11 @@ static void bt_enqueue_tiles(const BtCall& c, cudaStream_t s) {
 
 static int bt_enqueue(const BtCall& c, unsigned char* redo, cudaStream_t s) {
     bt_enqueue_tiles(c, s);
-    { ProfScope p("batched_hull", s); bt_hull<<<c.a.k, kBHullThreads, kBHullSmem, s>>>(c.a); }
+    {
+        ProfScope p("batched_hull", s);
+        bt_hull_small<<<c.a.k, kBSmallThreads, 0, s>>>(c.a);
+        bt_hull<<<c.a.k, kBHullThreads, kBHullSmem, s>>>(c.a);
+    }
     // Sets with more records than one block holds: all together through the
     // bucketed path.
     if (cudaMemsetAsync(c.base + c.L.zero_from, 0, c.L.zero_to - c.L.zero_from, s) != cudaSuccess) return CH_ECUDA;

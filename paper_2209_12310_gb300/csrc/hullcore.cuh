@@ -406,15 +406,20 @@ __device__ __forceinline__ void frame_to_xy(int r, int u, int v, int& x, int& y)
 
 // Shared memory of the small hull (dynamic, placed by the caller).  After the
 // rounds the record arrays hold the joined cycle (x, y, index) and the output.
-struct QhSmem {
-    int ru[kMidCap], rv[kMidCap], ri[kMidCap];   // records: u, v, index
-    int rs[kMidCap];                             // queue (on entry), then segment (left vertex), -1 dropped
-    unsigned long long segmax[kQhCap], segarg[kQhCap];
-    int vu[kQhCap], vv[kQhCap], vi[kQhCap], vnext[kQhCap];
-    int splitu[kQhCap], child[kQhCap];
+// RCAP records, VCAP chain vertices of all four queues.
+template <int RCAP, int VCAP>
+struct QhSmemT {
+    static constexpr int kRecords = RCAP, kVertices = VCAP;
+    int ru[RCAP], rv[RCAP], ri[RCAP];            // records: u, v, index
+    int rs[RCAP];                                // queue (on entry), then segment (left vertex), -1 dropped
+    unsigned long long segmax[VCAP], segarg[VCAP];
+    int vu[VCAP], vv[VCAP], vi[VCAP], vnext[VCAP];
+    int splitu[VCAP], child[VCAP];
 };
+using QhSmem = QhSmemT<kMidCap, kQhCap>;
 
-__device__ __forceinline__ long long qh_depth(const QhSmem& q, int a, int b, int u, int v) {
+template <class Q>
+__device__ __forceinline__ long long qh_depth(const Q& q, int a, int b, int u, int v) {
     return (long long)(q.vv[b] - q.vv[a]) * (u - q.vu[a]) - (long long)(q.vu[b] - q.vu[a]) * (v - q.vv[a]);
 }
 
@@ -422,7 +427,9 @@ __device__ __forceinline__ long long qh_depth(const QhSmem& q, int a, int b, int
 // vertex, which starts the next chain) is in q.ru / q.rv / q.ri as x, y,
 // index, and its length in *mv.  False when a limit is exceeded (the caller
 // falls back to the sort-based path).  Whole block; m records in q.
-static __device__ bool qh_chains(QhSmem& q, int m, int* mv) {
+template <class Q>
+static __device__ bool qh_chains(Q& q, int m, int* mv) {
+    constexpr int kQhCap = Q::kVertices;
     __shared__ unsigned long long s_s[4], s_e[4];
     __shared__ int s_si[4], s_ei[4], s_len[4], s_nvert, s_changed, s_fail;
     const int tid = threadIdx.x, T = blockDim.x;
