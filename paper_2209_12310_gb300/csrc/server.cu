@@ -1,18 +1,22 @@
 // server.cu -- continuous-batching hull server (ch_server_* / ch_submit / ch_poll).
 //
 // A server owns one device arena carved from its memory budget, an engine
-// thread and two CUDA streams.  ch_submit only appends a request to the
+// thread and kSlots (3) CUDA streams.  ch_submit only appends a request to the
 // admission queue (O(1), never touches the GPU).  The engine thread repeatedly
 //   1. retires finished batches (result counts first, then the index lists,
 //      both copied back asynchronously and observed through CUDA events),
 //   2. forms a new batch from the queue head while a free stream slot exists
 //      and the arena has a contiguous block for the batch (admission by
 //      memory: a request waits until memory frees up),
-//   3. copies the batch's points in and launches ch_hull_batched on it.
-// Two batch slots on two streams let a new batch start while the previous
-// one is still on the GPU, so requests that arrive during a batch overlap
-// with it instead of waiting for it.  Every request's result is computed by
-// the same kernels as ch_hull on that request alone.
+//   3. copies the batch's points in and enqueues the batched hull on it (no
+//      host wait; sets the batched kernels leave to the single-hull path are
+//      finished when the batch retires).
+// Batch slots on separate streams let new batches start while earlier ones
+// are still on the GPU, so one batch's copies overlap another's kernels and
+// requests that arrive during a batch do not wait for it; a batch takes at
+// most 1 / kSlots of the arena's points so that the slots' batches fit side
+// by side.  Every request's result is computed by the same kernels as
+// ch_hull on that request alone.
 #include "ch_internal.cuh"
 #include "host.h"
 
@@ -104,7 +108,7 @@ struct Slot {
 
 constexpr size_t kMaxQueue = 1u << 17;
 constexpr int kMaxBatch = 4096;
-constexpr int kSlots = 2;
+constexpr int kSlots = 3;
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 size_t batch_bytes(int64_t points, size_t k) {
@@ -229,9 +233,8 @@ bool Server::launch(Slot& sl) {
         std::lock_guard<std::mutex> lk(mu);
         // FIFO admission: take queue-head requests while the batch still fits
         // the workspace and a contiguous arena block exists for it.  A batch
-        // takes at most half the arena's points (a single request may take
-        // more), so that the other slot's batch fits beside it: one batch's
-        // copies then overlap the other's kernels.
+        // takes at most 1 / kSlots of the arena's points (a single request
+        // may take more), so that the other slots' batches fit beside it.
         const int64_t cap = std::max<int64_t>(max_points / kSlots, 1);
         while (!queue.empty() && (int)batch.size() < kMaxBatch) {
             Req* r = queue.front();
@@ -322,10 +325,9 @@ int ch_server_create(size_t budget_bytes, int device, void** srv) {
     S->device = device;
     S->budget = budget_bytes;
     // Split of the budget: per point a batch needs 12 bytes of arena (points
-    // in, indices out) and about ws bytes of workspace on each of the two slot
-    // streams.
+    // in, indices out) and about ws bytes of workspace on each slot stream.
     const double ws_pp = (double)ch_workspace_bytes(1 << 20) / (double)(1 << 20);
-    const double per_point = 12.0 + 2.0 * ws_pp;
+    const double per_point = 12.0 + (double)kSlots * ws_pp;
     S->max_points = (int64_t)((double)budget_bytes / per_point);
     const size_t arena_bytes = align256((size_t)(12.0 * (double)S->max_points) + (size_t)kMaxBatch * 64 + (1u << 20));
     int st = CH_OK;
