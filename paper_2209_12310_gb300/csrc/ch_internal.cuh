@@ -93,7 +93,6 @@ struct Octagon {
 
 // Small-path limits: the last block of a pass finishes the hull itself when
 // the survivors are few.
-constexpr unsigned kRawSmall = 4096;    // raw survivors one block re-classifies
 constexpr int kMidCap = 8192;           // sort records one block turns into the hull
 
 // Per-call control block in device memory.
