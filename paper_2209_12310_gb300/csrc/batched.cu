@@ -935,8 +935,8 @@ static int bt_tune(BtCall& c, const BtDevice& d, const std::vector<int64_t>& off
 }
 
 // The tuned shape of the nearest size class of this device (by the distance
-// of the log2 sizes), else the middle shape; for callers that must not block
-// on tuning (the server).
+// of the log2 sizes) when one lies within two steps, else the middle shape;
+// for callers that must not block on tuning (the server).
 static int nearest_tuned_locked(const BtDevice& d, long long total, int k) {
     const std::string prefix = tune_key(d, 1, 1);
     const std::string dev = prefix.substr(0, prefix.size() - 4);   // drops "|0|0"
@@ -947,7 +947,7 @@ static int nearest_tuned_locked(const BtDevice& d, long long total, int k) {
         int t = 0, kk = 0;
         if (sscanf(kv.first.c_str() + dev.size(), "|%d|%d", &t, &kk) != 2) continue;
         const int dist = std::abs(t - lt) + std::abs(kk - lk);
-        if (dist < best_d) {
+        if (dist <= 2 && dist < best_d) {
             best_d = dist;
             best = kv.second.first;
         }
