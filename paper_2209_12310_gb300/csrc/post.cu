@@ -43,25 +43,18 @@ __device__ __forceinline__ void rec_flush_warp(RecBuf& b, unsigned& cnt, Ctl* ct
     cnt = 0u;
 }
 
-// Warp-collective: classifies one point per lane (valid = false for none) and
-// stages the kept ones.  Records per queue are counted per warp (lane 0's qn).
-__device__ __forceinline__ void post_point(bool valid, float x, float y, unsigned idx, const Octagon& o, RecBuf& b,
+// Warp-collective: stages one classified point per lane (r = -1 for none).
+// Records per queue are counted per lane in `tally`.
+__device__ __forceinline__ void post_stage(int r, int X, int Y, unsigned idx, const Octagon& o, RecBuf& b,
                                            unsigned& cnt, Ctl* ctl, uint32_t* keys, uint64_t* vals,
-                                           unsigned (&qn)[4]) {
-    int r = -1, X = 0, Y = 0;
-    if (valid) {
-        X = __float2int_rn(x);
-        Y = __float2int_rn(y);
-        r = classify_hull(x, y, o);
-    }
+                                           QueueTally& tally) {
     bool keep = r >= 0;
     if (!__any_sync(0xFFFFFFFFu, keep)) return;
     if (reduce_on_line(o, keep, X, Y, idx, ctl)) keep = false;
     const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
     if (!bal) return;
     if (cnt + (unsigned)__popc(bal) > (unsigned)kRecBuf) rec_flush_warp(b, cnt, ctl, keys, vals);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) qn[q] += __popc(__ballot_sync(0xFFFFFFFFu, keep && r == q));
+    tally.add(keep, r);
     if (keep) {
         uint32_t u, v;
         queue_frame(r, X, Y, u, v);
@@ -71,6 +64,21 @@ __device__ __forceinline__ void post_point(bool valid, float x, float y, unsigne
     }
     cnt += __popc(bal);
     __syncwarp();
+}
+
+// Warp-collective: classifies one point per lane (valid = false for none) and
+// stages it; folds the tally (one add per lane and call).
+__device__ __forceinline__ void post_point(bool valid, float x, float y, unsigned idx, const Octagon& o, RecBuf& b,
+                                           unsigned& cnt, Ctl* ctl, uint32_t* keys, uint64_t* vals,
+                                           QueueTally& tally) {
+    int r = -1, X = 0, Y = 0;
+    if (valid) {
+        X = __float2int_rn(x);
+        Y = __float2int_rn(y);
+        r = classify_hull(x, y, o);
+    }
+    post_stage(r, X, Y, idx, o, b, cnt, ctl, keys, vals, tally);
+    tally.fold();
 }
 
 // Whole block: the warps' staged records go out with one atomic.
@@ -97,15 +105,17 @@ __device__ void rec_flush_block(RecBuf& b, unsigned cnt, Ctl* ctl, uint32_t* key
     }
 }
 
-// The block's records per queue (warp counts) into ctl->rec_q.
-__device__ __forceinline__ void flush_queue_counts(const unsigned (&qn)[4], Ctl* ctl) {
+// The block's records per queue (lane tallies) into ctl->rec_q.
+__device__ __forceinline__ void flush_queue_counts(QueueTally& tally, Ctl* ctl) {
     __shared__ unsigned s_q[4];
     if (threadIdx.x < 4) s_q[threadIdx.x] = 0u;
     __syncthreads();
-    if ((threadIdx.x & 31) == 0)
+    tally.fold();
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (qn[q]) atomicAdd(&s_q[q], qn[q]);
+    for (int q = 0; q < 4; ++q) {
+        const unsigned w = tally.warp_total(q);
+        if ((threadIdx.x & 31) == 0 && w) atomicAdd(&s_q[q], w);
+    }
     __syncthreads();
     if (threadIdx.x < 4 && s_q[threadIdx.x]) atomicAdd(&ctl->rec_q[threadIdx.x], s_q[threadIdx.x]);
 }
@@ -206,22 +216,24 @@ __global__ void __launch_bounds__(kPostThreads, 1) post_kernel(const float* __re
     }
     RecBuf& rb = reinterpret_cast<RecBuf*>(dyn)[warp];
     unsigned rc = 0u;
-    unsigned qn[4] = {0u, 0u, 0u, 0u};
+    QueueTally tally;
     if (s_mode == 1) {   // two-pass mode: every point
-        const long long gwarp = ((long long)blockIdx.x * blockDim.x + tid) >> 5;
-        const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+        // n < 2^31, so step and point numbers fit in 32 bits
+        const unsigned gwarp = (blockIdx.x * blockDim.x + tid) >> 5;
+        const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
         const float4* p4 = reinterpret_cast<const float4*>(pts + 2 * head);
         const unsigned long long pol = l2_evict_first();
-        // one float4 (two points) per step with the loads of the next kAhead
-        // steps in flight: a rolled loop keeps the classification code small.
-        // Steps run over this warp's tiles, kLoadsPerLane float4 per tile.
+        // one float4 (two points, classified together) per step with the
+        // loads of the next kAhead steps in flight: a rolled loop keeps the
+        // classification code small.  Steps run over this warp's tiles,
+        // kLoadsPerLane float4 per tile.
         constexpr int kAhead = 4;
-        const long long total = ntiles * kLoadsPerLane;
-        const long long sstep = nwarps * kLoadsPerLane;
-        auto next_step = [&](long long st) {
+        const unsigned total = (unsigned)ntiles * kLoadsPerLane;
+        const unsigned sstep = nwarps * kLoadsPerLane;
+        auto next_step = [&](unsigned st) {
             return (st % kLoadsPerLane == kLoadsPerLane - 1) ? st + sstep - (kLoadsPerLane - 1) : st + 1;
         };
-        long long s = gwarp * kLoadsPerLane, sl = s;   // sl: the step of the newest load
+        unsigned s = gwarp * kLoadsPerLane, sl = s;   // sl: the step of the newest load
         float4 q[kAhead];
 #pragma unroll
         for (int a = 0; a < kAhead; ++a) {
@@ -235,10 +247,17 @@ __global__ void __launch_bounds__(kPostThreads, 1) post_kernel(const float* __re
             for (int a = 0; a + 1 < kAhead; ++a) q[a] = q[a + 1];
             q[kAhead - 1] = sl < total ? ld_stream_f4(p4 + sl * 32 + lane, pol) : make_float4(0.f, 0.f, 0.f, 0.f);
             sl = next_step(sl);
-            const long long t = s / kLoadsPerLane, j = s % kLoadsPerLane;
-            const long long i0 = head + t * kWarpTilePts + 64 * j + 2 * lane;
-            post_point(true, v.x, v.y, (unsigned)i0, s_o, rb, rc, ctl, keys, vals, qn);
-            post_point(true, v.z, v.w, (unsigned)(i0 + 1), s_o, rb, rc, ctl, keys, vals, qn);
+            const unsigned i0 = (unsigned)head + (s / kLoadsPerLane) * kWarpTilePts + 64u * (s % kLoadsPerLane) +
+                                2u * lane;
+            const int X0 = __float2int_rn(v.x), Y0 = __float2int_rn(v.y);
+            const int X1 = __float2int_rn(v.z), Y1 = __float2int_rn(v.w);
+            int r0 = classify_hull_fast(v.x, v.y, X0, Y0, s_o);
+            int r1 = classify_hull_fast(v.z, v.w, X1, Y1, s_o);
+            if (r0 == kUndecided) r0 = classify_hull_slow(v.x, v.y, &s_o);
+            if (r1 == kUndecided) r1 = classify_hull_slow(v.z, v.w, &s_o);
+            post_stage(r0, X0, Y0, i0, s_o, rb, rc, ctl, keys, vals, tally);
+            post_stage(r1, X1, Y1, i0 + 1u, s_o, rb, rc, ctl, keys, vals, tally);
+            if (s % kLoadsPerLane == kLoadsPerLane - 1) tally.fold();   // at most 2 kLoadsPerLane adds
             s = next_step(s);
         }
         if (gwarp == 0) {   // the unaligned head point and the ragged tail
@@ -249,7 +268,7 @@ __global__ void __launch_bounds__(kPostThreads, 1) post_kernel(const float* __re
                     const bool valid = i < ranges[rg][1];
                     float x = 0.0f, y = 0.0f;
                     if (valid) { x = pts[2 * i]; y = pts[2 * i + 1]; }
-                    post_point(valid, x, y, (unsigned)i, s_o, rb, rc, ctl, keys, vals, qn);
+                    post_point(valid, x, y, (unsigned)i, s_o, rb, rc, ctl, keys, vals, tally);
                 }
         }
     } else {   // fused mode: the raw survivors of the main pass
@@ -266,11 +285,11 @@ __global__ void __launch_bounds__(kPostThreads, 1) post_kernel(const float* __re
                 y = (float)(unsigned)(xy & 0xFFFFFFFFull);
                 idx = raw_idx[i];
             }
-            post_point(valid, x, y, idx, s_o, rb, rc, ctl, keys, vals, qn);
+            post_point(valid, x, y, idx, s_o, rb, rc, ctl, keys, vals, tally);
         }
     }
     rec_flush_block(rb, rc, ctl, keys, vals);
-    flush_queue_counts(qn, ctl);
+    flush_queue_counts(tally, ctl);
     CH_TL(ctl, 5, 1);
     if (!last_block(&ctl->blocks_done[2], &s_flag)) return;
     CH_TL(ctl, 6, 0);
