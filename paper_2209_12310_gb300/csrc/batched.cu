@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(T) bt_filter(BArgs a, int ntiles) {
             const long long rb = region_base(a, i);
             const float2* p2 = reinterpret_cast<const float2*>(a.pts) + base;
             unsigned wcnt = 0u;                      // records staged in wb
-            QueueTally tally;                        // records per queue (per lane)
+            unsigned qn[4] = {0u, 0u, 0u, 0u};       // records per queue (lane 0)
             for (long long b0 = p0; b0 < p1; b0 += (long long)T * kB) {   // uniform trip counts
                 float2 pv[kB];
 #pragma unroll
@@ -362,7 +362,8 @@ __global__ void __launch_bounds__(T) bt_filter(BArgs a, int ntiles) {
                 if (reduce_on_line(s_o, keep, X, Y, (unsigned)p, c)) keep = false;
                 const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
                 if (!bal) continue;
-                tally.add(keep, r);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) qn[q] += __popc(__ballot_sync(0xFFFFFFFFu, keep && r == q));
                 if (wcnt + (unsigned)__popc(bal) > (unsigned)kBtWarpRecs) bt_flush(wb, wcnt, c, a.keys, a.vals, rb);
                 if (keep) {
                     uint32_t u, v;
@@ -374,15 +375,13 @@ __global__ void __launch_bounds__(T) bt_filter(BArgs a, int ntiles) {
                 wcnt += __popc(bal);
                 __syncwarp();
                 }
-                tally.fold();   // at most kB adds per lane since the last fold
             }
             // the tile's records and queue counts (a tile never spans two sets)
             bt_flush(wb, wcnt, c, a.keys, a.vals, rb);
+            if (lane == 0)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const unsigned w = tally.warp_total(q);
-                if (lane == 0 && w) atomicAdd(&c->counts4[q], w);
-            }
+                for (int q = 0; q < 4; ++q)
+                    if (qn[q]) atomicAdd(&c->counts4[q], qn[q]);
         }
         __syncthreads();
     }
