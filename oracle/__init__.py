@@ -13,6 +13,9 @@ Contents
 * ``filter_ref``      -- the paper's filtering stage (Alg. 2) written out in
                          numpy int64: the 8 extremes, the octagon test and the
                          four-queue labelling.
+* ``filter16_ref``    -- the same filter with a 16-direction polygon (the 8
+                         octagon directions and the 8 integer directions
+                         between them), in numpy int64.
 * ``brute``           -- an O(n^3) edge-test hull for tiny inputs, used to
                          pin ``hull`` itself.
 * ``heaphull_cpu(pts, threads)`` -- the paper's heaphull on the host's cores
@@ -112,4 +115,4 @@ def check(pts) -> bool:
     return _load().oracle_check(a.ctypes.data, a.shape[0]) == 0
 
 
-from . import brute, filter_ref  # noqa: E402,F401
+from . import brute, filter16_ref, filter_ref  # noqa: E402,F401

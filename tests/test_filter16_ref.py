@@ -1,0 +1,122 @@
+"""Pins of the 16-direction filter polygon (oracle/filter16_ref.py): the
+octagon definition (already pinned) for the even directions, a polygon with
+known extremes, the C hull oracle (a different algorithm) for the strict
+interior, and the properties the filter relies on."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import filter16_ref as G
+from oracle import filter_ref as F
+from synth import workloads as W
+from tests.test_filter_ref import SETS, _strictly_inside_hull_of
+
+
+@pytest.mark.parametrize("k", range(len(SETS)))
+def test_even_directions_are_the_octagon(k):
+    """V_0, V_2, ..., V_14 are Alg. 2's W, SW, S, SE, E, NE, N, NW."""
+    pts = SETS[k]
+    np.testing.assert_array_equal(G.extremes16(pts)[0::2], F.extremes(pts))
+
+
+def _circle16(rng, n_inner, dup=()):
+    """Interior points (radius < R/2), then one point on a circle of radius R
+    at the angle of each direction of DIRS, then copies of some of them."""
+    c, R = float(1 << 23), float(1 << 20)
+    ang = rng.uniform(0, 2 * math.pi, n_inner)
+    rad = rng.uniform(0, R / 2, n_inner)
+    inner = np.stack([np.rint(c + rad * np.cos(ang)), np.rint(c + rad * np.sin(ang))], 1)
+    ring = []
+    for a, b in G.DIRS:
+        t = math.atan2(b, a)
+        ring.append((round(c + R * math.cos(t)), round(c + R * math.sin(t))))
+    ring = np.array(ring, np.float64)
+    pts = np.concatenate([inner, ring, ring[list(dup)]]).astype(np.float32)
+    return pts, n_inner
+
+
+def test_known_extremes_on_a_circle():
+    """On a circle, the point at direction k's own angle is the unique
+    maximiser of that direction among the circle points (the next direction is
+    at least 18.4 degrees away: a margin of 0.05 R against rounding of 1), and
+    every interior point lies below it.  Later copies never win a tie."""
+    rng = np.random.default_rng(16)
+    pts, base = _circle16(rng, 3000, dup=(3, 9, 14))
+    np.testing.assert_array_equal(G.extremes16(pts), base + np.arange(16))
+    lab = G.labels16(pts)
+    assert (lab[:base] == 0).all()            # strictly inside the 16-gon
+    # vertices are on its boundary: W, S, E, N lie on the quadrilateral (no
+    # queue); the three between two of them are in that arc's queue
+    np.testing.assert_array_equal(lab[base:base + 16], [0, 1, 1, 1, 0, 2, 2, 2, 0, 3, 3, 3, 0, 4, 4, 4])
+
+
+def test_ties_take_the_lowest_index():
+    """A copy of a circle point placed BEFORE the original wins its direction."""
+    rng = np.random.default_rng(17)
+    pts, base = _circle16(rng, 100)
+    pts = np.concatenate([pts[base + 5:base + 6], pts])   # copy of V_5 at index 0
+    ext = G.extremes16(pts)
+    assert ext[5] == 0
+    np.testing.assert_array_equal(np.delete(ext, 5), np.delete(base + 1 + np.arange(16), 5))
+
+
+@pytest.mark.parametrize("k", range(len(SETS)))
+def test_inside16_matches_hull_of_the_16_extremes(k):
+    """The polygon V_0..V_15 taken in direction order has the strict interior
+    of the convex hull of the 16 points (C oracle): the order is
+    counter-clockwise and the polygon convex."""
+    pts = SETS[k]
+    ext = G.extremes16(pts)
+    np.testing.assert_array_equal(G.inside16(pts, ext), _strictly_inside_hull_of(pts, ext))
+
+
+@pytest.mark.parametrize("k", range(len(SETS)))
+def test_16gon_contains_the_octagon(k):
+    pts = SETS[k]
+    assert not (F.inside_octagon(pts) & ~G.inside16(pts)).any()
+
+
+@pytest.mark.parametrize("k", range(len(SETS)))
+def test_filter16_keeps_every_hull_vertex(k):
+    """No hull vertex is discarded, and the hull of the kept points plus the
+    16 extremes is the hull of all points."""
+    pts = SETS[k]
+    full = oracle.hull(pts)
+    lab = G.labels16(pts)
+    kept = lab > 0
+    kept[G.extremes16(pts)] = True
+    assert kept[full].all()
+    sel = np.flatnonzero(kept)
+    np.testing.assert_array_equal(sel[oracle.hull(pts[sel])], full)
+
+
+def test_degenerate_polygon_discards_nothing():
+    pts = np.array([[0, 0], [10, 3], [5, 1], [4, 1]], np.float32)   # extremes on one line
+    _, area2 = G.polygon16(pts)
+    assert area2 == 0
+    assert not G.inside16(pts).any()
+    np.testing.assert_array_equal(G.labels16(pts), F.labels(pts))
+
+
+def test_survivors_fewer_on_normal_and_distorted():
+    """The point of a wider polygon: fewer survivors where the hull is round
+    and the octagon leaves a rim (1e6-point samples; the octagon keeps 380 and
+    934,941 of them)."""
+    n = G.region_counts16(W.normal(1_000_000, 1)).sum()
+    assert 0 < n <= 0.5 * F.region_counts(W.normal(1_000_000, 1)).sum()
+    d16 = (G.labels16(W.distorted(1_000_000, 5)) > 0).sum()
+    d8 = (F.labels(W.distorted(1_000_000, 5)) > 0).sum()
+    assert d16 <= 0.75 * d8
+
+
+def test_planted_direction_error_is_caught(monkeypatch):
+    """A plausible mistake planted in the oracle (one direction with a flipped
+    sign, which breaks the counter-clockwise order) fails the hull pin."""
+    pts = W.normal(20_000, 3)
+    dirs = list(G.DIRS)
+    dirs[9] = (2, -1)
+    monkeypatch.setattr(G, "DIRS", tuple(dirs))
+    ext = G.extremes16(pts)
+    assert not np.array_equal(G.inside16(pts, ext), _strictly_inside_hull_of(pts, ext))
