@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--n", type=int, default=None, help="override the point count (testing)")
+    ap.add_argument("--filter-steps", type=int, default=20,
+                    help="timed ch_filter / ch_filter16 calls on the same input (0: skip)")
     ap.add_argument("--batched-sets", type=int, default=4096, help="sets of the batched workload (0: skip)")
     ap.add_argument("--batched-reps", type=int, default=5)
     ap.add_argument("--serve-requests", type=int, default=200000,
@@ -344,6 +346,7 @@ def run_ours(args):
     large = kernels.get("bk_hull", {}).get("avg_ms", 0.0) > 5 * kernels.get("bk_prep", {}).get("avg_ms", 1.0)
     launches_per_step = FILTER_LAUNCHES + (LARGE_LAUNCHES if large else 0)
 
+    filters = run_filters(ch, torch, args, pts, n, sp, peak) if (args.filter_steps > 0 and world == 1) else None
     batched = run_batched(ch, torch, args, sp) if (args.batched_sets > 0 and world == 1) else None
     serving = run_serving(ch, torch, args) if (args.serve_requests > 0 and world == 1) else None
 
@@ -384,6 +387,8 @@ def run_ours(args):
             "roofline": roof, "kernels": kernels, "e2e": e2e, "cpu_baseline": cpu, "cpu_heaphull": cpu_hh,
             "gpu_launches": launches_per_step * args.steps, "clocks": clk,
         }
+        if filters is not None:
+            line["filters"] = filters
         if batched is not None:
             line["batched"] = batched
         if serving is not None:
@@ -391,6 +396,51 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_filters(ch, torch, args, pts, n, sp, peak):
+    """The filter on its own (labels and queue sizes) with the octagon
+    (ch_filter) and with the 16-direction polygon (ch_filter16), on the
+    resident input: device time per call, points kept, and the HBM fraction
+    of each pass (8 bytes a point read; the label pass also writes 1)."""
+    labels = torch.empty(max(n, 1), dtype=torch.uint8, device="cuda")
+    counts = torch.empty(4, dtype=torch.int64, device="cuda")
+    ext = torch.empty(16, dtype=torch.int32, device="cuda")
+    out = {}
+    for name, fn, passes in (("octagon", ch.ch_filter, {"main_filter": 8.0, "labels": 9.0}),
+                             ("16-gon", ch.ch_filter16, {"filter16_extremes": 8.0, "filter16_labels": 9.0})):
+        def call():
+            fn(pts.data_ptr(), n, ext.data_ptr(), labels.data_ptr(), counts.data_ptr(), sp)
+        for _ in range(3):
+            call()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.filter_steps):
+            call()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.filter_steps
+        ch.ch_profile_reset()
+        ch.ch_profile_enable(True)
+        for _ in range(args.filter_steps):
+            call()
+        torch.cuda.synchronize()
+        ch.ch_profile_enable(False)
+        prof = ch.ch_profile_read()
+        kept = int(counts.sum().item())
+        per = {}
+        for k, bpp in passes.items():
+            if k in prof and prof[k][0]:
+                avg_ms = prof[k][1] / prof[k][0]
+                gbs = bpp * n / (avg_ms / 1e3) / 1e9
+                per[k] = {"avg_ms": avg_ms, "achieved_gbs": gbs, "frac_of_measured_hbm": gbs / peak}
+        out[name] = {"ms_per_call": ms, "points_per_s": n / (ms / 1e3), "kept": kept,
+                     "kept_fraction": kept / max(n, 1), "passes": per}
+    out["note"] = ("labels + queue sizes of every point; octagon = ch_filter, 16-gon = ch_filter16 "
+                   f"(same input, {args.filter_steps} calls each, CUDA events)")
+    return out
 
 
 def _pct(xs, q):

@@ -130,6 +130,34 @@ int ch_filter(const float* pts, int64_t n, int32_t* out_ext8, uint8_t* out_label
               int64_t* out_counts4, void* stream);
 
 /*
+ * ch_filter16 -- ch_filter with a 16-direction polygon in place of the
+ * octagon: the filter over a convex polygon of 16 extreme points that the
+ * paper cites among related work (Sec. 2), with Alg. 2's rules.  The paper
+ * gives no directions; they are the octagon's 8 and the 8 integer directions
+ * between them, in counter-clockwise order from W:
+ *   (-1,0) W, (-2,-1), (-1,-1) SW, (-1,-2), (0,-1) S, (1,-2), (1,-1) SE,
+ *   (2,-1), (1,0) E, (2,1), (1,1) NE, (1,2), (0,1) N, (-1,2), (-1,1) NW,
+ *   (-2,1).
+ *   pts          as ch_filter (device, 8-byte aligned, integers in [0, 2^24)).
+ *   out_ext16    device int32[16]: for direction k = (a, b) the index of the
+ *                point maximising a x + b y, lowest index on ties (the even
+ *                entries equal ch_filter's W, SW, ..., NW).  All -1 when
+ *                n == 0 or on a data error.
+ *   out_labels   device uint8[n] or NULL: 0 when the point is strictly inside
+ *                the polygon of those 16 points (strictly left of every edge
+ *                of non-zero length; a polygon of zero area discards nothing)
+ *                or in no queue, else its queue 1..4 by ch_filter's
+ *                quadrilateral rule over W, S, E, N.
+ *   out_counts4  device int64[4] or NULL: points per queue, or all four set
+ *                to CH_ERANGE when a coordinate is outside the domain.
+ * Stream-ordered, no host synchronisation; uses the stream's workspace (as
+ * ch_hull).  Returns CH_OK on enqueue or a negative status for bad arguments
+ * (CH_EINVAL) or a launch error (CH_ECUDA).
+ */
+int ch_filter16(const float* pts, int64_t n, int32_t* out_ext16, uint8_t* out_labels,
+                int64_t* out_counts4, void* stream);
+
+/*
  * ch_hull_host -- ch_hull on HOST buffers: copies pts (host, n*2 float32) to
  * the device, computes the hull, copies the result back and waits for it.
  * Writes h (or a negative status) to *out_n and the indices to out_idx (host,

@@ -9,7 +9,8 @@ stream to them.  There is no CPU fallback.
 from __future__ import annotations
 
 from ._native import (CH_EBUSY, CH_ECUDA, CH_EINVAL, CH_ENOMEM, CH_ERANGE, CH_ETIMEOUT, CH_OK,  # noqa: F401
-                      CH_PENDING, CHError, LIB_PATH, ch_batched_config, ch_filter, ch_hull, ch_hull_batched, ch_hull_host,
+                      CH_PENDING, CHError, LIB_PATH, ch_batched_config, ch_filter, ch_filter16, ch_hull,
+                      ch_hull_batched, ch_hull_host,
                       ch_poll, ch_profile_enable, ch_profile_read, ch_profile_reset, ch_release,
                       ch_reserve, ch_server_create, ch_server_destroy, ch_server_stats, ch_strerror,
                       ch_submit, ch_workspace_bytes, load, strerror)
@@ -93,4 +94,18 @@ def filter_labels(pts, labels=True, stream=None):
     cnt = torch.empty(4, dtype=torch.int64, device=pts.device)
     ch_filter(pts.data_ptr(), n, ext.data_ptr(), lab.data_ptr() if lab is not None else None,
               cnt.data_ptr(), _stream(stream))
+    return ext, (lab[:n] if lab is not None else None), cnt
+
+
+def filter16_labels(pts, labels=True, stream=None):
+    """The filter with the 16-direction polygon: (ext16 int32[16], labels
+    uint8[n] or None, counts int64[4])."""
+    import torch
+    pts = _points(pts)
+    n = pts.shape[0]
+    ext = torch.empty(16, dtype=torch.int32, device=pts.device)
+    lab = torch.empty(max(n, 1), dtype=torch.uint8, device=pts.device) if labels else None
+    cnt = torch.empty(4, dtype=torch.int64, device=pts.device)
+    ch_filter16(pts.data_ptr(), n, ext.data_ptr(), lab.data_ptr() if lab is not None else None,
+                cnt.data_ptr(), _stream(stream))
     return ext, (lab[:n] if lab is not None else None), cnt
