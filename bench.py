@@ -28,9 +28,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 # Kernels per replayed hull: the filter part (init, sample, main, post) always;
-# the large-survivor part (5 bucket kernels, 3 sort passes that return at once
-# on the bucketed path, the chain merge) only when the post pass raised its
-# graph condition.
+# the large-survivor part (8 bucket kernels, the sort's histogram and 3 passes,
+# which return at once on the bucketed path, and the chain merge) only when the
+# post pass raised its graph condition.
 FILTER_LAUNCHES = 4
 LARGE_LAUNCHES = 13   # bk_prep, bk_hist, bk_bsum, bk_bstart, bk_items, bk_part1, bk_part2, bk_hull, sort_hist, 3 sort passes, chain
 L2_BYTES = 129 * 1024 * 1024

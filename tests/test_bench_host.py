@@ -1,0 +1,99 @@
+"""Host logic of bench.py, without a GPU: the reference arm's JSON line, the
+traffic figure's staleness rule, the clock-sample parser and percentiles."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_reference_arm_prints_one_json_line():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
+                        "--warmup", "1", "--workload", "uniform_1e6"],
+                       capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert r.returncode == 0, r.stderr
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "dtype", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["steps"] == 2 and d["value"] > 0
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+
+
+def test_reference_arm_other_ranks_print_nothing():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], capture_output=True, text=True, timeout=120, cwd=ROOT, env=env)
+    assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_workload_configs_cover_every_single_hull_workload():
+    from synth import workloads as W
+    for name in W.SINGLE:
+        kind, n, seed, desc = bench.workload_config(name, None)
+        assert n > 0 and desc
+        assert bench.workload_config(name, 1234)[1] == 1234
+
+
+def test_traffic_comes_from_the_committed_profile_while_its_source_is_unchanged():
+    t = bench.traffic_from_profile("main_filter", "normal_1e8", 100_000_000)
+    assert t == pytest.approx(810.3e6)
+    assert bench.traffic_from_profile("main_filter", "normal_1e8", 50_000_000) == pytest.approx(405.15e6)
+    assert bench.traffic_from_profile("no_such_kernel", "normal_1e8", 1) is None
+
+
+def test_traffic_is_null_once_the_source_changed(tmp_path, monkeypatch):
+    src = tmp_path / "k.cu"
+    src.write_text("// kernel\n")
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    sha = bench.source_sha(str(src))
+    body = "traffic_bytes_per_launch: 1.5e6\npoints_per_launch: 1e6\nsource_file: k.cu\nsource_sha: {}\n"
+    (prof / "kern_w.md").write_text(body.format(sha))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.traffic_from_profile("kern", "w", 2_000_000) == pytest.approx(3.0e6)
+    src.write_text("// kernel, changed\n")
+    assert bench.traffic_from_profile("kern", "w", 2_000_000) is None
+
+
+class _FakeProc:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def test_clock_samples_median_and_reasons():
+    c = bench.ClockSampler(0)
+    c.proc = _FakeProc()
+    c.lines = [
+        "0, 2070, 2070, 900.5, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, 2055, 2070, 1200.0, 0x4, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1250.0, 0x4, Not Active, Not Active, Not Active, Active",
+        "garbage line",
+    ]
+    out = c.stop()
+    assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0 and out["samples"] == 3
+    assert out["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_sampler_without_nvidia_smi():
+    c = bench.ClockSampler(0)
+    assert c.stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_percentiles():
+    xs = list(range(1, 101))
+    assert bench._pct(xs, 50) == 51 or bench._pct(xs, 50) == 50
+    assert bench._pct(xs, 99) == 99
+    assert bench._pct([], 50) is None
+    assert bench._pct([7.0], 99) == 7.0
