@@ -16,8 +16,14 @@
  *   3. "CH <- union of hull(Q_i)": the survivors hold every hull vertex and
  *      every repetition of its coordinates, so Andrew's monotone chain
  *      (Table I) over them gives the hull of all points.  They are ordered
- *      by (x, y, index) with a parallel sort (per-chunk qsort, then pairwise
- *      merges in parallel rounds); the chains themselves are sequential.
+ *      by (x, y, index): stable LSD radix passes on the 48-bit key
+ *      x * 2^24 + y, every chunk counting and scattering its share of each
+ *      pass (the survivors arrive in index order, so equal coordinates stay
+ *      in index order); the first of each run of equal coordinates stays.
+ *   4. Andrew's chains: each chunk of the sorted points builds its lower and
+ *      upper chain, and one pass over the concatenated chunk chains gives
+ *      the hull (the hull of a sorted list is the hull of its pieces' hulls,
+ *      in order).
  * Output convention as andrew.c: strictly convex vertices, counter-clockwise
  * from the lexicographically smallest, the lowest index per coordinate.
  */
@@ -32,34 +38,30 @@
 #define HH_ENOMEM (-3)
 #define HH_MAX_THREADS 256
 
+/* a survivor: key = x * 2^24 + y (orders by x, then y), and its index */
 typedef struct {
-    int64_t x, y, idx;
+    uint64_t key;
+    int64_t idx;
 } hpt;
+
+static int64_t px(const hpt* p) { return (int64_t)(p->key >> 24); }
+static int64_t py(const hpt* p) { return (int64_t)(p->key & 0xFFFFFFu); }
 
 /* direction order W, SW, S, SE, E, NE, N, NW (counter-clockwise around the
  * hull); key d is minimised for W, SW, S, NW and maximised for SE, E, NE, N */
-static int64_t dir_key(int d, int64_t x, int64_t y) {
-    switch (d) {
-        case 0: case 4: return x;
-        case 2: case 6: return y;
-        case 1: case 5: return x + y;
-        default: return x - y;
-    }
-}
 static int dir_max(int d) { return d >= 3 && d <= 6; }
 
-static int coord_ok(float v) { return v >= 0.0f && v < 16777216.0f && v == floorf(v); }
+/* an integer in [0, 2^24): the truncation is exact only for integers; NaN
+ * fails the range test */
+static int coord_ok(float v) { return v >= 0.0f && v < 16777216.0f && (float)(int32_t)v == v; }
 
 static int64_t cross3(int64_t ox, int64_t oy, int64_t ax, int64_t ay, int64_t bx, int64_t by) {
     return (ax - ox) * (by - oy) - (ay - oy) * (bx - ox);
 }
 
-static int cmp_pt(const void* pa, const void* pb) {
-    const hpt* a = (const hpt*)pa;
-    const hpt* b = (const hpt*)pb;
-    if (a->x != b->x) return a->x < b->x ? -1 : 1;
-    if (a->y != b->y) return a->y < b->y ? -1 : 1;
-    return a->idx < b->idx ? -1 : (a->idx > b->idx);
+/* cross3 of three survivors */
+static int64_t turn(const hpt* o, const hpt* a, const hpt* b) {
+    return cross3(px(o), py(o), px(a), py(a), px(b), py(b));
 }
 
 /* ---------------------------------------------------------------------- */
@@ -68,36 +70,51 @@ typedef struct {
     int64_t lo, hi;
     int bad;
     int64_t key[8], arg[8];   /* step 1 */
-    const int64_t* ox;        /* step 2: octagon vertices (8), NULL = keep all */
-    const int64_t* oy;
+    const int64_t* ea;        /* step 2: live octagon edges a x + b y + c (> 0: strictly left) */
+    const int64_t* eb;
+    const int64_t* ec;
+    int ne;                   /*   their number; -1 = keep every point */
     hpt* surv;                /* step 2: this chunk's survivors */
     int64_t nsurv;
-    hpt* a;                   /* step 3: sort / merge ranges */
-    hpt* b;
-    int64_t m0, m1, m2;
+    const hpt* src;           /* step 3: one radix pass over src[m0, m1) into dst */
+    hpt* dst;
+    int sh;                   /*   digit shift */
+    int64_t* cnt;             /*   this chunk's digit counts, then its scatter cursors */
+    hpt* low;                 /* step 4: lower / upper chain of src[m0, m1) */
+    hpt* up;
+    int64_t nl, nu;
+    int64_t m0, m1;
 } job;
 
 static void* run_extremes(void* arg) {
     job* j = (job*)arg;
     j->bad = 0;
-    for (int d = 0; d < 8; ++d) {
-        j->key[d] = dir_max(d) ? INT64_MIN : INT64_MAX;
-        j->arg[d] = -1;
-    }
+    /* minima of x, x + y, y, x - y and maxima of x - y, x, x + y, y */
+    int32_t wx = INT32_MAX, sws = INT32_MAX, sy = INT32_MAX, nwd = INT32_MAX;
+    int32_t sed = INT32_MIN, ex = INT32_MIN, nes = INT32_MIN, ny = INT32_MIN;
+    int64_t aw = -1, asw = -1, as = -1, anw = -1, ase = -1, ae = -1, ane = -1, an = -1;
     for (int64_t i = j->lo; i < j->hi; ++i) {
         const float fx = j->pts[2 * i], fy = j->pts[2 * i + 1];
         if (!coord_ok(fx) || !coord_ok(fy)) {
             j->bad = 1;
             return NULL;
         }
-        const int64_t x = (int64_t)fx, y = (int64_t)fy;
-        for (int d = 0; d < 8; ++d) {   /* strict improvement keeps the lowest index */
-            const int64_t k = dir_key(d, x, y);
-            if (dir_max(d) ? k > j->key[d] : k < j->key[d]) {
-                j->key[d] = k;
-                j->arg[d] = i;
-            }
-        }
+        const int32_t x = (int32_t)fx, y = (int32_t)fy, s = x + y, d = x - y;
+        /* strict improvement keeps the lowest index */
+        if (x < wx) { wx = x; aw = i; }
+        if (s < sws) { sws = s; asw = i; }
+        if (y < sy) { sy = y; as = i; }
+        if (d > sed) { sed = d; ase = i; }
+        if (x > ex) { ex = x; ae = i; }
+        if (s > nes) { nes = s; ane = i; }
+        if (y > ny) { ny = y; an = i; }
+        if (d < nwd) { nwd = d; anw = i; }
+    }
+    const int32_t k[8] = {wx, sws, sy, sed, ex, nes, ny, nwd};
+    const int64_t a[8] = {aw, asw, as, ase, ae, ane, an, anw};
+    for (int d = 0; d < 8; ++d) {
+        j->key[d] = j->hi > j->lo ? (int64_t)k[d] : (dir_max(d) ? INT64_MIN : INT64_MAX);
+        j->arg[d] = a[d];
     }
     return NULL;
 }
@@ -107,15 +124,10 @@ static void* run_filter(void* arg) {
     int64_t m = 0;
     for (int64_t i = j->lo; i < j->hi; ++i) {
         const int64_t x = (int64_t)j->pts[2 * i], y = (int64_t)j->pts[2 * i + 1];
-        int inside = j->ox != NULL;
-        for (int e = 0; e < 8 && inside; ++e) {
-            const int f = (e + 1) & 7;
-            if (j->ox[e] == j->ox[f] && j->oy[e] == j->oy[f]) continue;   /* zero-length edge */
-            if (cross3(j->ox[e], j->oy[e], j->ox[f], j->oy[f], x, y) <= 0) inside = 0;
-        }
+        int inside = j->ne >= 0;
+        for (int e = 0; e < j->ne; ++e) inside &= j->ea[e] * x + j->eb[e] * y + j->ec[e] > 0;
         if (inside) continue;
-        j->surv[m].x = x;
-        j->surv[m].y = y;
+        j->surv[m].key = ((uint64_t)x << 24) | (uint64_t)y;
         j->surv[m].idx = i;
         ++m;
     }
@@ -123,19 +135,43 @@ static void* run_filter(void* arg) {
     return NULL;
 }
 
-static void* run_sort(void* arg) {
+/* Step 3: stable LSD radix sort by key, RADIX_BITS per pass over the 48-bit
+ * key, all chunks at once: each counts its digits, the counts become
+ * (digit, chunk)-major offsets, and each chunk scatters its records in
+ * order, so a pass is stable */
+#define RADIX_BITS 12
+#define RADIX_BUCKETS (1 << RADIX_BITS)
+#define RADIX_PASSES ((48 + RADIX_BITS - 1) / RADIX_BITS)
+
+static void* run_count(void* arg) {
     job* j = (job*)arg;
-    qsort(j->a + j->m0, (size_t)(j->m1 - j->m0), sizeof(hpt), cmp_pt);
+    memset(j->cnt, 0, RADIX_BUCKETS * sizeof(int64_t));
+    for (int64_t i = j->m0; i < j->m1; ++i) j->cnt[(j->src[i].key >> j->sh) & (RADIX_BUCKETS - 1)]++;
     return NULL;
 }
 
-/* merges a[m0, m1) and a[m1, m2) into b[m0, m2) */
-static void* run_merge(void* arg) {
+static void* run_scatter(void* arg) {
     job* j = (job*)arg;
-    int64_t p = j->m0, q = j->m1, o = j->m0;
-    while (p < j->m1 && q < j->m2) j->b[o++] = cmp_pt(&j->a[q], &j->a[p]) < 0 ? j->a[q++] : j->a[p++];
-    while (p < j->m1) j->b[o++] = j->a[p++];
-    while (q < j->m2) j->b[o++] = j->a[q++];
+    for (int64_t i = j->m0; i < j->m1; ++i) j->dst[j->cnt[(j->src[i].key >> j->sh) & (RADIX_BUCKETS - 1)]++] = j->src[i];
+    return NULL;
+}
+
+/* Step 4: Andrew's lower chain (pop while not a left turn) and upper chain
+ * (pop while not a right turn) of the sorted, distinct points src[m0, m1),
+ * both in ascending order.  The hull of a sorted list is the hull of the
+ * concatenated chains of its pieces, so the final pass runs over these. */
+static void* run_chains(void* arg) {
+    job* j = (job*)arg;
+    int64_t nl = 0, nu = 0;
+    for (int64_t i = j->m0; i < j->m1; ++i) {
+        const hpt* p = &j->src[i];
+        while (nl >= 2 && turn(&j->low[nl - 2], &j->low[nl - 1], p) <= 0) --nl;
+        j->low[nl++] = *p;
+        while (nu >= 2 && turn(&j->up[nu - 2], &j->up[nu - 1], p) >= 0) --nu;
+        j->up[nu++] = *p;
+    }
+    j->nl = nl;
+    j->nu = nu;
     return NULL;
 }
 
@@ -163,6 +199,9 @@ int64_t cpu_heaphull(const float* pts, int64_t n, int32_t* out_idx, int threads)
     job* jobs = (job*)calloc((size_t)t, sizeof(job));
     hpt* surv = (hpt*)malloc((size_t)n * sizeof(hpt));
     hpt* tmp = NULL;
+    hpt* up = NULL;
+    hpt* h = NULL;
+    int64_t* cnt = NULL;
     int64_t result = HH_ENOMEM;
     if (!jobs || !surv) goto done;
     for (int i = 0; i < t; ++i) {
@@ -196,9 +235,24 @@ int64_t cpu_heaphull(const float* pts, int64_t n, int32_t* out_idx, int threads)
         oy[d] = (int64_t)pts[2 * ext[d] + 1];
     }
     for (int d = 0; d < 8; ++d) area2 += ox[d] * oy[(d + 1) & 7] - ox[(d + 1) & 7] * oy[d];
+    /* edge V_d -> V_d+1 as a x + b y + c = orient(V_d, V_d+1, p); zero-length
+     * edges are skipped, an octagon of zero area keeps everything */
+    int64_t ea[8], eb[8], ec[8];
+    int ne = 0;
+    for (int d = 0; d < 8; ++d) {
+        const int f = (d + 1) & 7;
+        const int64_t dx = ox[f] - ox[d], dy = oy[f] - oy[d];
+        if (dx == 0 && dy == 0) continue;
+        ea[ne] = -dy;
+        eb[ne] = dx;
+        ec[ne] = dy * ox[d] - dx * oy[d];
+        ++ne;
+    }
     for (int i = 0; i < t; ++i) {
-        jobs[i].ox = area2 > 0 ? ox : NULL;
-        jobs[i].oy = area2 > 0 ? oy : NULL;
+        jobs[i].ea = ea;
+        jobs[i].eb = eb;
+        jobs[i].ec = ec;
+        jobs[i].ne = area2 > 0 ? ne : -1;
         jobs[i].surv = surv + jobs[i].lo;
     }
     run_all(run_filter, jobs, t);
@@ -207,41 +261,42 @@ int64_t cpu_heaphull(const float* pts, int64_t n, int32_t* out_idx, int threads)
         if (surv + m != jobs[i].surv) memmove(surv + m, jobs[i].surv, (size_t)jobs[i].nsurv * sizeof(hpt));
         m += jobs[i].nsurv;
     }
-    /* 3. order by (x, y, index): per-chunk sorts, then pairwise merges */
+    /* 3. order by (x, y, index): parallel stable radix passes over the key
+     * (the survivors are in index order, so ties stay in index order) */
     tmp = (hpt*)malloc((size_t)(m > 0 ? m : 1) * sizeof(hpt));
-    if (!tmp) goto done;
+    cnt = (int64_t*)malloc((size_t)t * RADIX_BUCKETS * sizeof(int64_t));
+    if (!tmp || !cnt) goto done;
     int64_t bound[HH_MAX_THREADS + 1];
     int parts = (int64_t)t > m ? (int)(m > 0 ? m : 1) : t;
     for (int i = 0; i <= parts; ++i) bound[i] = m * i / parts;
-    for (int i = 0; i < parts; ++i) {
-        jobs[i].a = surv;
-        jobs[i].m0 = bound[i];
-        jobs[i].m1 = bound[i + 1];
-    }
-    run_all(run_sort, jobs, parts);
     hpt* src = surv;
     hpt* dst = tmp;
-    for (int width = 1; width < parts; width *= 2) {
-        int nj = 0;
-        for (int i = 0; i < parts; i += 2 * width) {
-            const int mid = i + width < parts ? i + width : parts;
-            const int end = i + 2 * width < parts ? i + 2 * width : parts;
-            jobs[nj].a = src;
-            jobs[nj].b = dst;
-            jobs[nj].m0 = bound[i];
-            jobs[nj].m1 = bound[mid];
-            jobs[nj].m2 = bound[end];
-            ++nj;
+    for (int pass = 0; pass < RADIX_PASSES; ++pass) {
+        for (int i = 0; i < parts; ++i) {
+            jobs[i].src = src;
+            jobs[i].dst = dst;
+            jobs[i].sh = RADIX_BITS * pass;
+            jobs[i].cnt = cnt + (size_t)i * RADIX_BUCKETS;
+            jobs[i].m0 = bound[i];
+            jobs[i].m1 = bound[i + 1];
         }
-        run_all(run_merge, jobs, nj);
-        hpt* s = src;
+        run_all(run_count, jobs, parts);
+        int64_t run = 0;
+        for (int d = 0; d < RADIX_BUCKETS; ++d)
+            for (int i = 0; i < parts; ++i) {
+                const int64_t c = jobs[i].cnt[d];
+                jobs[i].cnt[d] = run;
+                run += c;
+            }
+        run_all(run_scatter, jobs, parts);
+        hpt* sw = src;
         src = dst;
-        dst = s;
+        dst = sw;
     }
     /* the first of each equal-(x, y) run has the lowest index */
     int64_t u = 0;
     for (int64_t i = 0; i < m; ++i) {
-        if (u > 0 && src[u - 1].x == src[i].x && src[u - 1].y == src[i].y) continue;
+        if (u > 0 && src[u - 1].key == src[i].key) continue;
         src[u++] = src[i];
     }
     if (u <= 2) {
@@ -249,24 +304,45 @@ int64_t cpu_heaphull(const float* pts, int64_t n, int32_t* out_idx, int threads)
         result = u;
         goto done;
     }
-    /* Andrew's chains (the lower and the upper chain together hold at most 2u points) */
-    hpt* h = (hpt*)malloc((size_t)(2 * u + 1) * sizeof(hpt));
-    if (!h) goto done;
+    /* 4. Andrew's chains: per chunk in parallel, then one pass over the
+     * concatenated chunk chains (dst is free scratch now) */
+    up = (hpt*)malloc((size_t)u * sizeof(hpt));
+    h = (hpt*)malloc((size_t)(2 * u + 1) * sizeof(hpt));
+    if (!up || !h) goto done;
+    parts = (int64_t)t > u ? (int)u : t;
+    for (int i = 0; i <= parts; ++i) bound[i] = u * i / parts;
+    for (int i = 0; i < parts; ++i) {
+        jobs[i].src = src;
+        jobs[i].low = dst + bound[i];
+        jobs[i].up = up + bound[i];
+        jobs[i].m0 = bound[i];
+        jobs[i].m1 = bound[i + 1];
+    }
+    run_all(run_chains, jobs, parts);
+    int64_t nl = 0, nu = 0;   /* compact the chunk chains, in chunk order */
+    for (int i = 0; i < parts; ++i) {
+        memmove(dst + nl, jobs[i].low, (size_t)jobs[i].nl * sizeof(hpt));
+        memmove(up + nu, jobs[i].up, (size_t)jobs[i].nu * sizeof(hpt));
+        nl += jobs[i].nl;
+        nu += jobs[i].nu;
+    }
     int64_t k = 0;
-    for (int64_t i = 0; i < u; ++i) {   /* lower chain */
-        while (k >= 2 && cross3(h[k - 2].x, h[k - 2].y, h[k - 1].x, h[k - 1].y, src[i].x, src[i].y) <= 0) --k;
-        h[k++] = src[i];
+    for (int64_t i = 0; i < nl; ++i) {   /* lower chain, lexicographic minimum to maximum */
+        while (k >= 2 && turn(&h[k - 2], &h[k - 1], &dst[i]) <= 0) --k;
+        h[k++] = dst[i];
     }
     const int64_t lower_len = k + 1;
-    for (int64_t i = u - 2; i >= 0; --i) {   /* upper chain */
-        while (k >= lower_len && cross3(h[k - 2].x, h[k - 2].y, h[k - 1].x, h[k - 1].y, src[i].x, src[i].y) <= 0) --k;
-        h[k++] = src[i];
+    for (int64_t i = nu - 2; i >= 0; --i) {   /* upper chain, back to the minimum */
+        while (k >= lower_len && turn(&h[k - 2], &h[k - 1], &up[i]) <= 0) --k;
+        h[k++] = up[i];
     }
     --k;   /* the last point repeats the first */
     for (int64_t i = 0; i < k; ++i) out_idx[i] = (int32_t)h[i].idx;
-    free(h);
     result = k;
 done:
+    free(h);
+    free(up);
+    free(cnt);
     free(tmp);
     free(surv);
     free(jobs);

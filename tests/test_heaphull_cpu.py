@@ -37,3 +37,21 @@ def test_heaphull_cpu_more_threads_than_points_and_bad_input():
     bad[57, 1] = 0.5
     with pytest.raises(ValueError):
         oracle.heaphull_cpu(bad, 4)
+
+
+@pytest.mark.parametrize("threads", [2, 5, 16])
+def test_heaphull_cpu_chunk_boundaries(threads):
+    """Chunks of the sorted survivors split runs of equal coordinates and
+    collinear stretches; the per-chunk chains and the final pass over them
+    must still give the oracle's hull."""
+    rng = np.random.default_rng(threads)
+    cases = [
+        W.distorted(120_000, 11),
+        rng.integers(0, 64, (100_000, 2)).astype(np.float32),                 # heavy duplicates
+        np.repeat(np.stack([np.arange(3000), np.full(3000, 5)], 1), 3, axis=0).astype(np.float32),
+        np.concatenate([np.stack([np.full(5000, 7), np.arange(5000)], 1),      # vertical line
+                        np.array([[3, 2500], [11, 100]])]).astype(np.float32),
+    ]
+    cases += [v for v in W.degenerate_suite().values() if v.shape[0] > 0]
+    for pts in cases:
+        np.testing.assert_array_equal(oracle.heaphull_cpu(pts, threads), oracle.hull(pts))
