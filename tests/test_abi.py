@@ -50,6 +50,10 @@ def test_host_side_checks_without_gpu(native):
     assert native.ch_hull(8, 10, 0, 0, None) == ch.CH_EINVAL          # null outputs
     assert native.ch_hull(12, 10, 64, 64, None) == ch.CH_EINVAL        # pts not 8-byte aligned
     assert native.ch_filter(None, -5, None, None, None, None) == ch.CH_EINVAL
+    assert native.ch_filter16(None, -5, None, None, None, None) == ch.CH_EINVAL
+    assert native.ch_filter16(8, 10, None, None, None, None) == ch.CH_EINVAL      # null out_ext16
+    assert native.ch_filter16(12, 10, 64, None, None, None) == ch.CH_EINVAL       # pts not 8-byte aligned
+    assert native.ch_filter16(None, 10, 64, None, None, None) == ch.CH_EINVAL     # null pts, n > 0
     assert native.ch_hull_batched(None, None, -1, None, None, None, None) == ch.CH_EINVAL
     assert native.ch_hull_batched(None, None, 0, None, None, None, None) == ch.CH_OK
     assert native.ch_poll(None, 1, None, 0, None) == ch.CH_EINVAL
