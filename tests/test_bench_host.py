@@ -97,3 +97,12 @@ def test_percentiles():
     assert bench._pct(xs, 99) == 99
     assert bench._pct([], 50) is None
     assert bench._pct([7.0], 99) == 7.0
+
+
+def test_roofline_entry_arithmetic():
+    r = bench.roofline_entry("main_filter", 800e6, 137.5e-6, 6682.5, "measured", 810.3e6)
+    assert r["achieved"] == pytest.approx(800e6 / 137.5e-6 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6682.5)
+    assert r["frac_of_nominal"] == pytest.approx(r["achieved"] / 7900.0)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["traffic"] == 810.3e6
+    assert r["avg_launch_ms"] == pytest.approx(0.1375)
