@@ -92,3 +92,51 @@ def labels16(pts) -> np.ndarray:
 def region_counts16(pts) -> np.ndarray:
     lab = labels16(pts)
     return np.array([(lab == r).sum() for r in range(1, 5)], dtype=np.int64)
+
+
+def sample_tiles(n, tile=512, every=32):
+    """Indices of a strided sample: the first of every `every` tiles of `tile`
+    consecutive points (about n / every points)."""
+    starts = np.arange(0, n, tile * every)
+    if starts.size == 0:
+        return np.zeros(0, np.int64)
+    return np.concatenate([np.arange(s, min(s + tile, n)) for s in starts]).astype(np.int64)
+
+
+def hull_drop_sampled16(pts, sample_idx) -> np.ndarray:
+    """Points the hull stage may drop given the 16-direction polygon P of a
+    sample's extremes (vertices V_k = extremes16 of the sample, as indices
+    into pts): every point strictly inside P, and every point on P's boundary
+    whose coordinates are not those of a vertex.
+
+    Why this is safe: P's vertices are input points, so P lies in the hull.
+    A point strictly inside P is strictly inside the hull.  A point on an
+    edge of P at no vertex lies strictly between two input points, so it is
+    no strictly convex hull vertex, and neither is any point sharing its
+    coordinates.  Copies of a vertex's coordinates are kept: the sample's
+    vertex has the lowest index within the sample only, and the hull must
+    report the lowest index of all copies.  A polygon of zero area drops
+    nothing."""
+    x, y = _ints(pts)
+    drop = np.zeros(x.size, bool)
+    sample_idx = np.asarray(sample_idx, np.int64)
+    if x.size == 0 or sample_idx.size == 0:
+        return drop
+    ext = sample_idx[extremes16(np.asarray(pts, np.float32).reshape(-1, 2)[sample_idx])]
+    v, area2 = polygon16(pts, ext)
+    if area2 == 0:
+        return drop
+    closed = np.ones(x.size, bool)
+    strict = np.ones(x.size, bool)
+    for k in range(16):
+        ax, ay = v[k]
+        bx, by = v[(k + 1) % 16]
+        if ax == bx and ay == by:
+            continue
+        o = filter_ref.orient(ax, ay, bx, by, x, y)
+        closed &= o >= 0
+        strict &= o > 0
+    at_vertex = np.zeros(x.size, bool)
+    for vx, vy in {(int(a), int(b)) for a, b in v}:
+        at_vertex |= (x == vx) & (y == vy)
+    return strict | (closed & ~at_vertex)

@@ -120,3 +120,45 @@ def test_planted_direction_error_is_caught(monkeypatch):
     monkeypatch.setattr(G, "DIRS", tuple(dirs))
     ext = G.extremes16(pts)
     assert not np.array_equal(G.inside16(pts, ext), _strictly_inside_hull_of(pts, ext))
+
+
+@pytest.mark.parametrize("k", range(len(SETS)))
+def test_sampled16_drop_keeps_the_hull(k):
+    """The drop rule for a sample's 16-gon removes no output point (the
+    lowest-index copy of each hull vertex), so the hull of what is left is the
+    hull of all points; several samples per set, including one that is a
+    single tile and one that is every point."""
+    pts = SETS[k]
+    n = pts.shape[0]
+    full = oracle.hull(pts)
+    rng = np.random.default_rng(k)
+    samples = [G.sample_tiles(n), G.sample_tiles(n, tile=7, every=3), np.arange(min(n, 512)),
+               np.arange(n), np.sort(rng.choice(n, size=max(1, n // 10), replace=False))]
+    for s in samples:
+        drop = G.hull_drop_sampled16(pts, s)
+        assert not drop[full].any()
+        sel = np.flatnonzero(~drop)
+        np.testing.assert_array_equal(sel[oracle.hull(pts[sel])], full)
+
+
+def test_sampled16_drop_keeps_every_copy_of_a_vertex():
+    """A copy of a sample vertex that comes before the sample (lower index)
+    is the hull's choice; the rule must not drop it."""
+    rng = np.random.default_rng(21)
+    pts, base = _circle16(rng, 2000)
+    pts = np.concatenate([pts[base + 9:base + 10], pts])   # copy of V_9 at index 0
+    sample = np.arange(1 + base, 1 + base + 16)             # the circle points only
+    drop = G.hull_drop_sampled16(pts, sample)
+    assert not drop[0] and not drop[1 + base + 9]
+    assert drop[1:1 + base].all()                          # interior points go
+    full = oracle.hull(pts)
+    assert 0 in full and (1 + base + 9) not in full
+
+
+def test_sampled16_drops_most_of_the_distorted_rim():
+    """Every 32nd tile of 512 points is enough: with the octagon the hull
+    stage keeps about 0.64 of the distorted points (0.935 with the octagon
+    alone)."""
+    pts = W.distorted(1_000_000, 5)
+    keep = ~(F.inside_octagon(pts) | G.hull_drop_sampled16(pts, G.sample_tiles(pts.shape[0])))
+    assert 0.6 < keep.mean() < 0.68
