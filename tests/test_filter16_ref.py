@@ -162,3 +162,31 @@ def test_sampled16_drops_most_of_the_distorted_rim():
     pts = W.distorted(1_000_000, 5)
     keep = ~(F.inside_octagon(pts) | G.hull_drop_sampled16(pts, G.sample_tiles(pts.shape[0])))
     assert 0.6 < keep.mean() < 0.68
+
+
+@pytest.mark.parametrize("offset", [1000, W.COORD_LIMIT - 100])
+def test_known_extremes_on_the_lattice_circle(offset):
+    """The twelve lattice points of x^2 + y^2 = 25 (tests/golden), worked by
+    hand: in each (+-2, +-1) and (+-1, +-2) direction one of (+-4, +-3),
+    (+-3, +-4) is the unique maximum (value 11; the disk interior reaches at
+    most 10), the axis directions hit (+-5, 0) and (0, +-5), and each
+    diagonal ties between two points (value 7), which goes to the lower index
+    (the fixture repeats every vertex later, never earlier)."""
+    from tests import golden_io
+    pts, _ = golden_io.load("lattice_circle25.txt", offset=offset)
+    first = {}
+    for i, (a, b) in enumerate(pts.astype(np.int64).tolist()):
+        first.setdefault((a - offset, b - offset), i)
+    f = first.__getitem__
+    want = [f((-5, 0)), f((-4, -3)), min(f((-4, -3)), f((-3, -4))), f((-3, -4)),
+            f((0, -5)), f((3, -4)), min(f((3, -4)), f((4, -3))), f((4, -3)),
+            f((5, 0)), f((4, 3)), min(f((4, 3)), f((3, 4))), f((3, 4)),
+            f((0, 5)), f((-3, 4)), min(f((-3, 4)), f((-4, 3))), f((-4, 3))]
+    np.testing.assert_array_equal(G.extremes16(pts), want)
+    # every disk-interior point is strictly inside the 16-gon (the twelve
+    # circle points span it), the circle points and their copies are not
+    lab_in = G.inside16(pts)
+    circle = {(5, 0), (4, 3), (3, 4), (0, 5), (-3, 4), (-4, 3), (-5, 0), (-4, -3), (-3, -4), (0, -5),
+              (3, -4), (4, -3)}
+    on = np.array([(a - offset, b - offset) in circle for a, b in pts.astype(np.int64).tolist()])
+    assert not lab_in[on].any() and lab_in[~on].all()
