@@ -381,7 +381,8 @@ def run_ours(args):
 
     if rank == 0:
         cpu = cpu_baseline(kind, seed, args.cpu_seconds) if world == 1 else None
-        cpu_hh = cpu_heaphull(kind, seed, max(0.5, args.cpu_seconds / 4)) if world == 1 else None
+        if cpu is not None:   # the multi-core comparator, part of the same CPU-baseline leg
+            cpu["heaphull_comparator"] = cpu_heaphull(kind, seed, max(0.5, args.cpu_seconds / 4))
         line = {
             "metric": "points/s (filter+hull, device-timed)", "value": value, "unit": "points/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -393,7 +394,7 @@ def run_ours(args):
                               "(256 MB write) before each step, steps timed one by one") if in_l2 else
                              f"inputs {8 * n / 1e6:.0f} MB per step > 129 MB L2 (no flush needed)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-            "roofline": roof, "kernels": kernels, "e2e": e2e, "cpu_baseline": cpu, "cpu_heaphull": cpu_hh,
+            "roofline": roof, "kernels": kernels, "e2e": e2e, "cpu_baseline": cpu,
             "gpu_launches": launches_per_step * args.steps, "clocks": clk,
         }
         if filters is not None:

@@ -106,3 +106,13 @@ def test_roofline_entry_arithmetic():
     assert r["frac_of_nominal"] == pytest.approx(r["achieved"] / 7900.0)
     assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["traffic"] == 810.3e6
     assert r["avg_launch_ms"] == pytest.approx(0.1375)
+
+
+def test_cpu_baseline_and_comparator_legs():
+    """The CPU-baseline leg's two parts run on the host alone: the oracle on
+    one core, and the multi-core comparator on one thread and on every core."""
+    base = bench.cpu_baseline("normal", 1, 0.05)
+    assert base["kind"] == "oracle" and base["cores"] == 1 and base["value"] > 0
+    hh = bench.cpu_heaphull("normal", 1, 0.05)
+    assert hh["cores"] == (os.cpu_count() or 1)
+    assert hh["value_1_thread"] > 0 and hh["value_all_cores"] > 0
