@@ -18,9 +18,13 @@
  * - "device" pointers are CUDA device (or managed) memory of the current
  *   device; "host" pointers are ordinary or pinned host memory.
  * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
- *   Device entry points are stream-ordered and return as soon as the work is
- *   enqueued; they never synchronise the host with the device, so a sequence
- *   of calls can be captured in a CUDA graph (after ch_reserve, see below).
+ *   ch_hull, ch_filter, ch_filter16 and ch_hull_noalloc are stream-ordered:
+ *   they return as soon as the work is enqueued and never synchronise the
+ *   host with the device, so a sequence of them can be captured in a CUDA
+ *   graph (after ch_reserve, see below).  The calls that do wait for the
+ *   device say so in their own comments: ch_hull_batched (it reads a k-byte
+ *   flag array back, and the offsets when no host copy is given), ch_hull_host,
+ *   ch_reserve, ch_release, ch_selftest_timeout and ch_profile_read.
  * - Return value: CH_OK when the work was enqueued, or a negative ch_status
  *   for an error the host can see at call time (null pointer, bad size or
  *   alignment, allocation or launch failure).  No C++ exception crosses the ABI.
@@ -67,8 +71,11 @@ typedef enum {
  *   out_n    device int64*: the device writes h, or a negative ch_status when
  *            the input holds a value outside the domain (CH_ERANGE) or a
  *            device wait timed out (CH_ETIMEOUT).
- * Returns CH_OK on enqueue.  Pass 1 and pass 2 of the filter each stream the
- * points once (8 bytes per point); the hull stage touches only survivors.
+ * Returns CH_OK on enqueue.  On sparse data (few points outside the octagon)
+ * the points are streamed once (8 bytes per point): the extremes and the
+ * filter share one pass.  When most points survive that pass's filter (points
+ * near a circle, Table V) a second streaming pass classifies every point.  The
+ * hull stage touches only the survivors.
  */
 int ch_hull(const float* pts, int64_t n, int32_t* out_idx, int64_t* out_n, void* stream);
 
@@ -184,7 +191,9 @@ int ch_hull_host(const float* pts, int64_t n, int32_t* out_idx, int64_t* out_n, 
  * The whole hull runs in one thread block.  Its global scratch (about 100 KB)
  * is one fixed array in the library's static device memory; the first call on
  * a device looks up that array's address and sets the kernel's shared-memory
- * limit, so make that first call before any stream capture.  Nothing in the
+ * limit, so make that first call before any stream capture.  The look-up is
+ * kept per device and CUDA context: after the context is re-created (e.g. by
+ * cudaDeviceReset) the next call repeats it.  Nothing in the
  * scratch needs to start at zero.  Calls that overlap in time (other streams
  * or host threads) share the scratch and race: the caller orders them.
  * Returns CH_OK when enqueued, CH_EINVAL or CH_ECUDA otherwise.
@@ -198,6 +207,24 @@ int ch_hull_noalloc(const float* pts, int64_t n, int32_t* out_idx, int64_t* out_
  * allowed during capture.  Blocking (may synchronise `stream`).
  */
 int ch_reserve(int64_t n, int32_t k, void* stream);
+
+/*
+ * ch_hull_counters -- what the most recent ch_hull on `stream` (current
+ * device) did, for measurement and tests (ch_filter shares the control block
+ * these come from, so after it they describe the filter): writes up to `cap` of
+ *   out[0]  raw survivors of the fused streaming pass (points it could not
+ *           discard against the sample's polygon),
+ *   out[1]  sort records handed to the hull stage (the chain end points
+ *           included): the survivors of the filter,
+ *   out[2]  0 when one streaming pass did the extremes and the filter, 1 when
+ *           a second pass classified every point,
+ *   out[3]  hull stage: 0 finished by one block (few records), 1 bucketed
+ *           chains, 2 the radix-sort fallback,
+ *   out[4]  the call's status (CH_OK or the negative code it reported)
+ * and returns how many counters exist (5).  Synchronises the stream.
+ * CH_EINVAL when no hull ran on that stream (or out is NULL).
+ */
+int ch_hull_counters(void* stream, int64_t* out, int cap);
 
 /* Bytes of workspace ch_hull needs for n points. */
 size_t ch_workspace_bytes(int64_t n);

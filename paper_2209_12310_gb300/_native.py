@@ -43,6 +43,7 @@ SIGNATURES = {
     "ch_batched_config": (_INT, [_I64, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     "ch_reserve": (_INT, [_I64, _I32, _P]),
     "ch_workspace_bytes": (_SZ, [_I64]),
+    "ch_hull_counters": (_INT, [_P, ctypes.POINTER(_I64), _INT]),
     "ch_release": (_INT, []),
     "ch_selftest_timeout": (_INT, [_INT, _P]),
     "ch_strerror": (ctypes.c_char_p, [_INT]),
@@ -128,6 +129,16 @@ def ch_hull_host(pts, n, out_idx, out_n, stream=0):
 
 def ch_reserve(n, k=1, stream=0):
     return _check(load().ch_reserve(n, k, stream), "ch_reserve")
+
+
+def ch_hull_counters(stream=0):
+    """Counters of the most recent ch_hull on `stream`: raw survivors, records,
+    mode (two streaming passes), hull stage (0 one block, 1 buckets, 2 sort),
+    status."""
+    out = (_I64 * 8)()
+    k = _check(load().ch_hull_counters(stream, out, 8), "ch_hull_counters")
+    names = ("raw", "records", "two_pass", "stage", "status")
+    return {names[i]: int(out[i]) for i in range(min(k, 8, len(names)))}
 
 
 def ch_workspace_bytes(n):

@@ -607,6 +607,33 @@ int ch_reserve(int64_t n, int32_t k, void* stream) {
 
 size_t ch_workspace_bytes(int64_t n) { return n < 0 ? 0 : make_layout(n).total; }
 
+int ch_hull_counters(void* stream, int64_t* out, int cap) {
+    if (!out || cap < 0) return CH_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CH_ECUDA;
+    char* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_ws.find(std::make_pair(dev, s));
+        if (it == g_ws.end() || !it->second.base) return CH_EINVAL;
+        base = it->second.base;
+    }
+    Ctl c;
+    if (cudaMemcpyAsync(&c, base, sizeof(Ctl), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CH_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return CH_ECUDA;
+    const int64_t v[] = {
+        (int64_t)c.count_raw,
+        (int64_t)c.count,
+        (int64_t)c.mode,
+        (int64_t)(c.bk_state == 2 ? 2 : c.bk_state == 1 ? 1 : 0),
+        (int64_t)c.status,
+    };
+    const int nv = (int)(sizeof(v) / sizeof(v[0]));
+    for (int i = 0; i < nv && i < cap; ++i) out[i] = v[i];
+    return nv;
+}
+
 #if defined(CH_TRACE) || defined(CH_TIMELINE)
 // Debug builds: the phase timeline of the most recent call on the first
 // workspace (ns since the init kernel).

@@ -174,7 +174,37 @@ __global__ void __launch_bounds__(kNoAllocThreads, 1)
 }
 
 std::mutex g_mu;
-void* g_ptr[64];   // scratch address per device, found once
+void* g_ptr[64];                   // scratch address per device
+unsigned long long g_ctx[64];      // id of the context that address belongs to
+
+// Id of the calling thread's current CUDA context (unique for the life of
+// the process), 0 when there is none yet or the driver cannot say.  A new id
+// for a device means its context was destroyed and re-created (for example
+// by cudaDeviceReset): the static array then has a new address and the
+// kernel attribute must be set again.  The driver calls are looked up
+// through the runtime, so the library needs no link to the driver library.
+unsigned long long current_context_id() {
+    typedef int (*GetCurrentFn)(void**);
+    typedef int (*GetIdFn)(void*, unsigned long long*);
+    static GetCurrentFn get_current = nullptr;
+    static GetIdFn get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        looked_up = true;
+        cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", (void**)&get_current, 12000, cudaEnableDefault,
+                                             &q1) != cudaSuccess || q1 != cudaDriverEntryPointSuccess)
+            get_current = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", (void**)&get_id, 12000, cudaEnableDefault, &q2) !=
+                cudaSuccess || q2 != cudaDriverEntryPointSuccess)
+            get_id = nullptr;
+        cudaGetLastError();
+    }
+    void* ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current && get_id && get_current(&ctx) == 0 && ctx && get_id(ctx, &id) == 0) return id;
+    return 0;
+}
 
 }  // namespace
 }  // namespace ch
@@ -190,7 +220,10 @@ extern "C" int ch_hull_noalloc(const float* pts, int64_t n, int32_t* out_idx, in
     void* sc = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_ptr[dev]) {   // set-up, once per device (that device current)
+        const unsigned long long ctx = current_context_id();
+        if (!g_ptr[dev] || ctx == 0 || ctx != g_ctx[dev]) {
+            // set-up, once per device and context (that device current); a
+            // thread whose context is not current yet redoes the lookup once
             void* p = nullptr;
             if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) {
                 cudaGetLastError();
@@ -202,6 +235,7 @@ extern "C" int ch_hull_noalloc(const float* pts, int64_t n, int32_t* out_idx, in
                 return CH_ECUDA;
             }
             g_ptr[dev] = p;
+            g_ctx[dev] = current_context_id();
         }
         sc = g_ptr[dev];
     }

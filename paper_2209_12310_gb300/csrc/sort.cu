@@ -7,9 +7,9 @@
 // three 9-bit digit passes of a single-pass ("onesweep") radix sort: each
 // pass ranks a 4096-record tile in shared memory, publishes its per-digit
 // counts, resolves its global offsets by decoupled look-back over the
-// preceding tiles, and scatters.  The digit histograms of all passes were
-// accumulated while the records were produced (pass 2 of the filter), so no
-// separate counting pass over the records is needed.
+// preceding tiles, and scatters.  The digit histograms of all three passes
+// come from one counting pass over the records (sort_hist_kernel) before the
+// first scatter; the post pass keeps only per-queue counts.
 //
 // Look-back waits are bounded (kSpinLimit polls with back-off); a wait that
 // gives up raises CH_ETIMEOUT and the abort flag, after which every other

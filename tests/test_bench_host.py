@@ -24,6 +24,7 @@ def test_reference_arm_prints_one_json_line():
                 "higher_is_better", "scaling", "dtype", "config", "cpu_baseline", "e2e"):
         assert key in d, key
     assert d["impl"] == "reference" and d["steps"] == 2 and d["value"] > 0
+    assert d["metric"] == bench.METRIC   # the same metric name as the GPU arm's line
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
 
@@ -116,3 +117,23 @@ def test_cpu_baseline_and_comparator_legs():
     hh = bench.cpu_heaphull("normal", 1, 0.05)
     assert hh["cores"] == (os.cpu_count() or 1)
     assert hh["value_1_thread"] > 0 and hh["value_all_cores"] > 0
+
+
+def test_algorithmic_bytes_follow_the_counters():
+    sparse = {"raw": 1000, "records": 900, "two_pass": 0, "stage": 0}
+    a = bench.algorithmic_bytes(10_000, sparse)
+    assert a == {"main_filter": 8 * 10_000 + 12 * 1000, "post": 12 * 1000 + 12 * 900}
+    dense = {"raw": 70_000, "records": 9_000, "two_pass": 1, "stage": 1}
+    b = bench.algorithmic_bytes(10_000, dense)
+    assert b["post"] == 8 * 10_000 + 12 * 9_000
+    assert b["bk_part1"] == b["bk_part2"] == 24 * 9_000 and b["bk_hist"] == 4 * 9_000 and b["bk_hull"] == 12 * 9_000
+
+
+def test_kernel_rooflines_pick_the_slowest_kernel_with_bytes():
+    prof = {"main_filter": (10, 1.0), "post": (10, 3.0), "hull_chains": (10, 9.0)}
+    algo = {"main_filter": 8e6, "post": 2e6}
+    per, roof = bench.kernel_rooflines(prof, algo, 1000.0, "measured", "nowhere", 1_000_000)
+    assert roof["kernel"] == "post"   # hull_chains has no byte count
+    assert roof["achieved"] == pytest.approx(2e6 / 0.3e-3 / 1e9)
+    assert per["main_filter"]["achieved_gbs"] == pytest.approx(8e6 / 0.1e-3 / 1e9)
+    assert roof["traffic"] is None

@@ -46,6 +46,41 @@ def test_two_calls_in_a_row_match_ch_hull(lib):
     np.testing.assert_array_equal(hb[1], oracle.hull(b))
 
 
+def _u_arc(m, seed):
+    """m lattice points in strictly convex position (a narrow U, slopes -m/2 ..
+    m/2, x step 1500), shuffled: every point is a hull vertex."""
+    i = np.arange(m, dtype=np.int64)
+    y = np.concatenate([[0], np.cumsum(i[:-1] - m // 2)])
+    pts = np.stack([i * 1500, y - y.min() + 5], 1)
+    return pts[np.random.default_rng(seed).permutation(m)].astype(np.float32)
+
+
+def _parabola(m, seed):
+    """m points of y = x (x + 1) / 2, x step 64 (m <= 5792 keeps y < 2^24),
+    shuffled, plus a copy of every tenth point at the end: all hull vertices,
+    each duplicate named by its first index."""
+    x = np.arange(m, dtype=np.int64)
+    pts = np.stack([x * 64, x * (x + 1) // 2], 1)[np.random.default_rng(seed).permutation(m)]
+    return np.concatenate([pts, pts[::10]]).astype(np.float32)
+
+
+def test_all_points_on_the_hull_take_the_sort_fallback(lib):
+    """Sets whose hull has thousands of vertices overflow the one-block
+    quickhull's chain capacity, so the kernel sorts its records in the static
+    scratch and joins the chains from there (the branch no smaller hull
+    reaches).  Two different such sets in a row, each against ch_hull and the
+    oracle."""
+    native = lib.load()
+    a = _u_arc(MAX_POINTS, 41)
+    b = _parabola(5000, 42)
+    assert b.shape[0] <= MAX_POINTS
+    for pts in (a, b, a):
+        want = oracle.hull(pts)
+        assert want.size >= 5000
+        got = _same_as_ch_hull(native, pts)
+        np.testing.assert_array_equal(got[1], want)
+
+
 @pytest.mark.parametrize("n", [0, 1, 2, 3, 17, 512, 4097, MAX_POINTS])
 def test_sizes_match_ch_hull(lib, n):
     rng = np.random.default_rng(n + 5)
