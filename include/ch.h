@@ -220,8 +220,10 @@ int ch_reserve(int64_t n, int32_t k, void* stream);
  *           a second pass classified every point,
  *   out[3]  hull stage: 0 finished by one block (few records), 1 bucketed
  *           chains, 2 the radix-sort fallback,
- *   out[4]  the call's status (CH_OK or the negative code it reported)
- * and returns how many counters exist (5).  Synchronises the stream.
+ *   out[4]  the call's status (CH_OK or the negative code it reported),
+ *   out[5]  vertices of the star polygon that filtered dense data (0 when
+ *           the call built none)
+ * and returns how many counters exist (6).  Synchronises the stream.
  * CH_EINVAL when no hull ran on that stream (or out is NULL).
  */
 int ch_hull_counters(void* stream, int64_t* out, int cap);

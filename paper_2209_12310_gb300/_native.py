@@ -134,10 +134,10 @@ def ch_reserve(n, k=1, stream=0):
 def ch_hull_counters(stream=0):
     """Counters of the most recent ch_hull on `stream`: raw survivors, records,
     mode (two streaming passes), hull stage (0 one block, 1 buckets, 2 sort),
-    status."""
+    status, vertices of the star polygon (0: none built)."""
     out = (_I64 * 8)()
     k = _check(load().ch_hull_counters(stream, out, 8), "ch_hull_counters")
-    names = ("raw", "records", "two_pass", "stage", "status")
+    names = ("raw", "records", "two_pass", "stage", "status", "star_vertices")
     return {names[i]: int(out[i]) for i in range(min(k, 8, len(names)))}
 
 

@@ -72,7 +72,10 @@ Layout make_layout(long long n) {
     L.off_ctl = take(sizeof(Ctl));
     L.off_status = take(8 * (size_t)kDigits * L.sort_tiles);
     L.off_counters = take(4 * (size_t)kMaxLevels * L.ctcap);
+    L.off_star_bins = take(star_bins_bytes());   // the star pass leaves them at zero
     L.zero_bytes = o;
+    L.off_star_poly = take(star_poly_bytes());
+    L.off_star_work = take(star_work_bytes());
     L.off_kA = take(4 * (size_t)L.cap);
     L.off_kB = take(4 * (size_t)L.cap);
     L.off_vA = take(8 * (size_t)L.cap);
@@ -100,6 +103,10 @@ struct Workspace {
     // staging for the host-buffer entry point
     char* stage = nullptr;
     size_t stage_bytes = 0;
+    // the star pass's branch: a stream of its own, forked from and joined
+    // back into the caller's stream by two events
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 static std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
@@ -113,6 +120,7 @@ static int grow_workspace(Workspace& ws, long long n, cudaStream_t s, int dev) {
     const Layout L = make_layout(want);
     if (ws.base) {
         cudaStreamSynchronize(s);
+        if (ws.side) cudaStreamSynchronize(ws.side);
         cudaFree(ws.base);
         ws.base = nullptr;
         ws.bytes = 0;
@@ -143,16 +151,52 @@ int get_workspace(int dev, cudaStream_t s, long long n, char** base, Layout* L) 
     return CH_OK;
 }
 
+static void free_workspace(Workspace& w, cudaStream_t s) {
+    cudaStreamSynchronize(s);
+    if (w.side) cudaStreamSynchronize(w.side);
+    if (w.base) cudaFree(w.base);
+    if (w.stage) cudaFree(w.stage);
+    if (w.ev_fork) cudaEventDestroy(w.ev_fork);
+    if (w.ev_join) cudaEventDestroy(w.ev_join);
+    if (w.side) cudaStreamDestroy(w.side);
+    w = Workspace();
+}
+
 void release_stream_workspace(int dev, cudaStream_t s) {
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_ws.find(std::make_pair(dev, s));
     drop_batched_graphs(dev, s);
+    release_batched_stream(dev, s);
     if (it == g_ws.end()) return;
     drop_graphs(dev, s);
-    cudaStreamSynchronize(s);
-    if (it->second.base) cudaFree(it->second.base);
-    if (it->second.stage) cudaFree(it->second.stage);
+    free_workspace(it->second, s);
     g_ws.erase(it);
+}
+
+// The star pass's stream and events of (dev, s), created on first use;
+// false when they cannot be (the hull then runs without the star pass).
+static bool get_side(int dev, cudaStream_t s, cudaStream_t* side, cudaEvent_t* fork, cudaEvent_t* join) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    Workspace& ws = g_ws[std::make_pair(dev, s)];
+    if (!ws.side) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t a = nullptr, b = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&a, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b, cudaEventDisableTiming) != cudaSuccess) {
+            if (st) cudaStreamDestroy(st);
+            if (a) cudaEventDestroy(a);
+            cudaGetLastError();
+            return false;
+        }
+        ws.side = st;
+        ws.ev_fork = a;
+        ws.ev_join = b;
+    }
+    *side = ws.side;
+    *fork = ws.ev_fork;
+    *join = ws.ev_join;
+    return true;
 }
 
 static int get_stage(int dev, cudaStream_t s, size_t bytes, char** out) {
@@ -246,9 +290,19 @@ struct HullLaunch {
     uint64_t *vA, *vB;
     int head;
     long long ntiles;
+    // the star pass (dense data): its branch and its buffers; side is null
+    // when the input is too small for it
+    cudaStream_t side;
+    cudaEvent_t ev_fork, ev_join;
+    void *star_bins, *star_poly, *star_work;
 };
 
-static int hull_setup(const float* pts, long long n, int dev, char* base, const Layout& L, HullLaunch* h) {
+// Inputs below this many warp tiles skip the star pass.
+constexpr long long kStarMinTiles = 256;
+
+// owner: the caller's stream, whose workspace (and star branch) the launches use.
+static int hull_setup(const float* pts, long long n, int dev, cudaStream_t owner, char* base, const Layout& L,
+                      HullLaunch* h) {
     int st = device_info(dev, &h->di);
     if (st != CH_OK) return st;
     h->ctl = (Ctl*)(base + L.off_ctl);
@@ -258,6 +312,12 @@ static int hull_setup(const float* pts, long long n, int dev, char* base, const 
     h->vB = (uint64_t*)(base + L.off_vB);
     h->head = (((uintptr_t)pts & 15u) != 0u && n > 0) ? 1 : 0;
     h->ntiles = (n - h->head) / kWarpTilePts;
+    h->star_bins = base + L.off_star_bins;
+    h->star_poly = base + L.off_star_poly;
+    h->star_work = base + L.off_star_work;
+    h->side = nullptr;
+    h->ev_fork = h->ev_join = nullptr;
+    if (h->ntiles >= kStarMinTiles && !get_side(dev, owner, &h->side, &h->ev_fork, &h->ev_join)) h->side = nullptr;
     return CH_OK;
 }
 
@@ -272,15 +332,28 @@ static void enqueue_filter_part(const float* pts, long long n, int32_t* out_idx,
     const unsigned switch_at = (unsigned)std::max<long long>(1 << 16, n >> 5);
     { ProfScope p("init", s); launch_init(h.ctl, 0, s); }
     { ProfScope p("sample", s); launch_sample(pts, n, h.head, h.ntiles, h.ctl, grid_sample, s); }
+    // The star pass needs only the sample octagon: it runs on its own branch
+    // beside the main pass, and the post pass waits for both.
+    const bool star = h.side != nullptr;
+    if (star) {
+        cudaEventRecord(h.ev_fork, s);
+        cudaStreamWaitEvent(h.side, h.ev_fork, 0);
+        {
+            ProfScope p("star", h.side);
+            launch_star(pts, n, h.head, h.ntiles, h.ctl, h.star_bins, h.star_poly, h.star_work, h.di.sms, h.side);
+        }
+        cudaEventRecord(h.ev_join, h.side);
+    }
     {
         ProfScope p("main_filter", s);
         launch_main(pts, n, h.head, h.ntiles, h.ctl, raw_xy, raw_idx, switch_at, h.kA, h.vA,
                     h.di.sms * h.di.occ_main, s);
     }
+    if (star) cudaStreamWaitEvent(s, h.ev_join, 0);
     {
         ProfScope p("post", s);
-        launch_post(pts, n, h.head, h.ntiles, h.ctl, raw_xy, raw_idx, h.kA, h.vA, out_idx, out_n, cond,
-                    h.di.sms * h.di.occ_post, s);
+        launch_post(pts, n, h.head, h.ntiles, h.ctl, raw_xy, raw_idx, h.kA, h.vA, out_idx, out_n,
+                    star ? h.star_poly : nullptr, cond, h.di.sms * h.di.occ_post, s);
     }
 }
 
@@ -310,9 +383,9 @@ static void enqueue_large_part(const float* pts, long long n, int32_t* out_idx, 
 }
 
 static int enqueue_hull_direct(const float* pts, long long n, int32_t* out_idx, int64_t* out_n, cudaStream_t s,
-                               int dev, char* base, const Layout& L) {
+                               int dev, char* base, const Layout& L, cudaStream_t owner) {
     HullLaunch h;
-    const int st = hull_setup(pts, n, dev, base, L, &h);
+    const int st = hull_setup(pts, n, dev, owner, base, L, &h);
     if (st != CH_OK) return st;
     enqueue_filter_part(pts, n, out_idx, out_n, s, h, 0ull);
     enqueue_large_part(pts, n, out_idx, out_n, s, base, L, h);
@@ -324,9 +397,9 @@ static int enqueue_hull_direct(const float* pts, long long n, int32_t* out_idx, 
 // small-survivor calls then launch only the filter part.  False when any step
 // of the capture fails (the caller then captures the plain sequence).
 static bool capture_conditional(const float* pts, long long n, int32_t* out_idx, int64_t* out_n, cudaStream_t cs,
-                                int dev, char* base, const Layout& L, cudaGraph_t* out) {
+                                int dev, char* base, const Layout& L, cudaStream_t owner, cudaGraph_t* out) {
     HullLaunch h;
-    if (hull_setup(pts, n, dev, base, L, &h) != CH_OK) return false;
+    if (hull_setup(pts, n, dev, owner, base, L, &h) != CH_OK) return false;
     if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
     bool ok = true;
     cudaGraph_t graph = nullptr;
@@ -441,7 +514,7 @@ int enqueue_hull_nograph(const float* pts, long long n, int32_t* out_idx, int64_
     Layout L;
     const int st = get_workspace(dev, s, n, &base, &L);
     if (st != CH_OK) return st;
-    return enqueue_hull_direct(pts, n, out_idx, out_n, s, dev, base, L);
+    return enqueue_hull_direct(pts, n, out_idx, out_n, s, dev, base, L, s);
 }
 
 int enqueue_hull(const float* pts, long long n, int32_t* out_idx, int64_t* out_n, cudaStream_t s, int dev) {
@@ -455,7 +528,7 @@ int enqueue_hull(const float* pts, long long n, int32_t* out_idx, int64_t* out_n
     if (st != CH_OK) return st;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (g_prof || cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
-        return enqueue_hull_direct(pts, n, out_idx, out_n, s, dev, base, L);
+        return enqueue_hull_direct(pts, n, out_idx, out_n, s, dev, base, L, s);
     const GraphKey key{dev, s, pts, n, out_idx, out_n, base};
     cudaGraphExec_t exec = nullptr;
     {
@@ -463,21 +536,21 @@ int enqueue_hull(const float* pts, long long n, int32_t* out_idx, int64_t* out_n
         GraphEntry& e = g_graphs[key];
         e.last_use = ++g_graph_clock;
         if (e.exec) exec = e.exec;
-        else if (e.seen++ == 0) return enqueue_hull_direct(pts, n, out_idx, out_n, s, dev, base, L);
+        else if (e.seen++ == 0) return enqueue_hull_direct(pts, n, out_idx, out_n, s, dev, base, L, s);
     }
     if (exec) return cudaGraphLaunch(exec, s) == cudaSuccess ? CH_OK : CH_ECUDA;
     // Second call of this key: capture on a private stream, then replay.
     cudaStream_t cs = nullptr;
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
-        return enqueue_hull_direct(pts, n, out_idx, out_n, s, dev, base, L);
+        return enqueue_hull_direct(pts, n, out_idx, out_n, s, dev, base, L, s);
     }
     cudaGraph_t graph = nullptr;
-    bool ok = capture_conditional(pts, n, out_idx, out_n, cs, dev, base, L, &graph);
+    bool ok = capture_conditional(pts, n, out_idx, out_n, cs, dev, base, L, s, &graph);
     if (!ok) {   // plain capture of the whole sequence
         ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
         if (ok) {
-            st = enqueue_hull_direct(pts, n, out_idx, out_n, cs, dev, base, L);
+            st = enqueue_hull_direct(pts, n, out_idx, out_n, cs, dev, base, L, s);
             ok = cudaStreamEndCapture(cs, &graph) == cudaSuccess && st == CH_OK && graph;
         }
     }
@@ -486,7 +559,7 @@ int enqueue_hull(const float* pts, long long n, int32_t* out_idx, int64_t* out_n
     cudaStreamDestroy(cs);
     if (!ok) {
         cudaGetLastError();
-        return enqueue_hull_direct(pts, n, out_idx, out_n, s, dev, base, L);
+        return enqueue_hull_direct(pts, n, out_idx, out_n, s, dev, base, L, s);
     }
     {
         std::lock_guard<std::mutex> lk(g_graph_mu);
@@ -628,6 +701,7 @@ int ch_hull_counters(void* stream, int64_t* out, int cap) {
         (int64_t)c.mode,
         (int64_t)(c.bk_state == 2 ? 2 : c.bk_state == 1 ? 1 : 0),
         (int64_t)c.status,
+        (int64_t)(c.star_ok ? c.star_k : 0),
     };
     const int nv = (int)(sizeof(v) / sizeof(v[0]));
     for (int i = 0; i < nv && i < cap; ++i) out[i] = v[i];
@@ -658,11 +732,7 @@ int ch_release(void) {
         g_graphs.clear();
     }
     std::lock_guard<std::mutex> lk(g_mu);
-    for (auto& kv : g_ws) {
-        cudaStreamSynchronize(kv.first.second);
-        if (kv.second.base) cudaFree(kv.second.base);
-        if (kv.second.stage) cudaFree(kv.second.stage);
-    }
+    for (auto& kv : g_ws) free_workspace(kv.second, kv.first.second);
     g_ws.clear();
     release_batched();
     return CH_OK;

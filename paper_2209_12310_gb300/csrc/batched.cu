@@ -594,6 +594,15 @@ int reserve_batched(int dev, cudaStream_t s, long long n, int k) {
     return bt_workspace(dev, s, n, std::max(k, 1), n, std::max(k, 1), n / kBTileMin + std::max(k, 1), &base, &L);
 }
 
+void release_batched_stream(int dev, cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(g_bmu);
+    auto it = g_bws.find(std::make_pair(dev, s));
+    if (it == g_bws.end()) return;
+    cudaStreamSynchronize(s);
+    if (it->second.base) cudaFree(it->second.base);
+    g_bws.erase(it);
+}
+
 static void drop_all_batched_graphs();
 
 void release_batched() {

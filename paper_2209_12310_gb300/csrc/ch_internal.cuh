@@ -62,7 +62,19 @@ __host__ __device__ __forceinline__ unsigned bk_buckets_for(unsigned cnt) {
     return nb > 0u ? nb : 1u;
 }
 constexpr int kSampleTiles = 1024;            // warp tiles read by the sample pass (512k points)
+// Star polygon of dense data (star.cu): angular bins around the sample
+// octagon's centre, extra warp tiles read when the sample is dense.
+constexpr int kStarBins = 8192;
+constexpr int kStarExtraTiles = 3072;
 constexpr int kMaxLevels = 32;
+
+// Warp tiles read by the sample pass: about 1/32 of the input, at most
+// kSampleTiles, at least min(ntiles, 64).
+__host__ __device__ __forceinline__ long long sample_tiles(long long ntiles) {
+    long long s = ntiles / 32;
+    if (s < 64) s = ntiles < 64 ? ntiles : 64;
+    return s < kSampleTiles ? s : kSampleTiles;
+}
 
 // Float edge-function error bound: |e_float - e_exact| < 2^28 for every edge
 // and query point of the domain (see octagon setup in filter.cu).
@@ -123,6 +135,12 @@ struct Ctl {
     float bk_scale[4];                  // buckets per unit of u in queue r
     int bk_shift;                       // fine buckets per coarse group: 1 << bk_shift
     unsigned int bk_next;               // next bucket for a bk_hull warp
+    int samp_ok;                        // oct_s holds this call's sample octagon
+    int star_ok;                        // the star polygon of this call is ready (star.cu)
+    int star_k;                         // its vertices
+    int star_cx, star_cy;               // its centre (vertices are stored relative to it)
+    unsigned int star_pts, star_out;    // points the star pass read / found outside the sample octagon
+    unsigned int star_done;             // last-arriver counter of the star pass
     Octagon oct;                        // octagon of the true extremes
     Octagon oct_s;                      // octagon of a sample's extremes
 #if defined(CH_TRACE) || defined(CH_TIMELINE)

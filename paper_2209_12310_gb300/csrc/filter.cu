@@ -75,6 +75,12 @@ __global__ void init_kernel(Ctl* ctl, int mode) {
         ctl->records_ready = 0;
         ctl->bk_state = 0;
         ctl->bk_cursor = 0u;
+        ctl->samp_ok = 0;
+        ctl->star_ok = 0;
+        ctl->star_k = 0;
+        ctl->star_pts = 0u;
+        ctl->star_out = 0u;
+        ctl->star_done = 0u;
     }
     unsigned* h = &ctl->digit_hist[0][0];
     for (int i = t; i < kSortPasses * kDigits; i += blockDim.x) h[i] = 0u;
@@ -86,13 +92,6 @@ __global__ void init_kernel(Ctl* ctl, int mode) {
 #endif
 }
 
-// Warp tiles read by the sample pass: about 1/32 of the input, at most
-// kSampleTiles, at least min(ntiles, 64).
-__host__ __device__ __forceinline__ long long sample_tiles(long long ntiles) {
-    long long s = ntiles / 32;
-    if (s < 64) s = ntiles < 64 ? ntiles : 64;
-    return s < kSampleTiles ? s : kSampleTiles;
-}
 
 // ---------------------------------------------------------------------------
 // Sample pass: packed (key, other coordinate) maxima per direction; the other
@@ -194,6 +193,11 @@ __global__ void __launch_bounds__(256) sample_kernel(const float* __restrict__ p
         return;
     }
     copy_octagon(&ctl->oct_s, &s_o);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        ctl->samp_ok = 1;
+    }
     CH_TRACE_MARK();
     CH_TL(ctl, 2, 1);
     CH_TRACE_PRINT("sample-last");
@@ -264,22 +268,6 @@ __device__ __forceinline__ bool tile_in_inner(const int (&tk)[8], const int* in)
            tk[SW] > in[2] && tk[NE] < in[6] && tk[NW] > in[3] && tk[SE] < in[7];
 }
 
-// Surely strictly inside the sample octagon: every edge function above the
-// float error bound (zero-length edges evaluate to a huge constant).  The
-// sample octagon's vertices are input points, so its interior lies in the
-// interior of the hull: such a point is no hull vertex, whatever the true
-// octagon turns out to be.  Edges as (A, B, C) triples in shared memory.
-__device__ __forceinline__ bool pt_in_sample(float x, float y, const float* e) {
-    float m = kHugePositive;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) m = fminf(m, fmaf(e[3 * k], x, fmaf(e[3 * k + 1], y, e[3 * k + 2])));
-    return m > kEdgeTol;
-}
-
-__device__ __forceinline__ bool pt_in_inner(int X, int Y, const int* in) {
-    const int S = X + Y, D = X - Y + kCoordLimit;
-    return X > in[0] && X < in[4] && Y > in[1] && Y < in[5] && S > in[2] && S < in[6] && D > in[3] && D < in[7];
-}
 
 __device__ __forceinline__ unsigned long long pack_best(int d, int best, unsigned code) {
     if (best == INT_MIN || best == INT_MAX) return 0ull;

@@ -12,6 +12,7 @@ struct Layout {
     size_t off_ctl, off_kA, off_kB, off_vA, off_vB, off_status, zero_bytes;
     size_t off_cu, off_cv, off_ci, off_clen, off_counters;
     size_t off_bcount, off_bcur, off_bstart, off_bsum, off_blen, off_bu, off_bv, off_bi, total;
+    size_t off_star_bins, off_star_poly, off_star_work;
     long long cap, sort_tiles, ctcap, bmax;
 };
 
@@ -39,6 +40,8 @@ int hull_batched_redo(const float* pts, const int64_t* host_offsets, int32_t k, 
 bool prof_enabled();
 void release_stream_workspace(int dev, cudaStream_t s);
 void release_batched();
+// The batched workspace of one stream (freed with the stream's other workspace).
+void release_batched_stream(int dev, cudaStream_t s);
 
 // Records a CUDA event pair around a scope when profiling is enabled.
 class ProfScope {

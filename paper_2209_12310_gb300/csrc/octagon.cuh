@@ -271,6 +271,25 @@ static __device__ void setup_octagon_block(Octagon& o, const int vx[8], const in
     __syncthreads();
 }
 
+// Surely strictly inside the sample octagon: every edge function above the
+// float error bound (zero-length edges evaluate to a huge constant).  The
+// sample octagon's vertices are input points, so its interior lies in the
+// interior of the hull: such a point is no hull vertex, whatever the true
+// octagon turns out to be.  Edges as (A, B, C) triples in shared memory.
+__device__ __forceinline__ bool pt_in_sample(float x, float y, const float* e) {
+    float m = kHugePositive;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) m = fminf(m, fmaf(e[3 * k], x, fmaf(e[3 * k + 1], y, e[3 * k + 2])));
+    return m > kEdgeTol;
+}
+
+// Strictly inside an inner region given as lo = in[0..3], hi = in[4..7]
+// (bounds of x, y, x+y, x-y+2^24).
+__device__ __forceinline__ bool pt_in_inner(int X, int Y, const int* in) {
+    const int S = X + Y, D = X - Y + kCoordLimit;
+    return X > in[0] && X < in[4] && Y > in[1] && Y < in[5] && S > in[2] && S < in[6] && D > in[3] && D < in[7];
+}
+
 __device__ __forceinline__ void copy_octagon(Octagon* dst, const Octagon* src) {
     const int words = (int)(sizeof(Octagon) / 4);
     const int* s = reinterpret_cast<const int*>(src);

@@ -12,6 +12,7 @@
 #include "launch.h"
 #include "octagon.cuh"
 #include "records.cuh"
+#include "star.cuh"
 
 #include <climits>
 
@@ -66,16 +67,27 @@ __device__ __forceinline__ void post_stage(int r, int X, int Y, unsigned idx, co
     __syncwarp();
 }
 
+// The star polygon in shared memory (null when this call has none) and its
+// centre; points strictly inside it are dropped before the octagon test.
+struct StarView {
+    const int2* v;
+    const unsigned short* tbl;
+    int cx, cy;
+    __device__ __forceinline__ bool inside(int X, int Y) const {
+        return v != nullptr && star_inside(X - cx, Y - cy, v, tbl);
+    }
+};
+
 // Warp-collective: classifies one point per lane (valid = false for none) and
 // stages it; folds the tally (one add per lane and call).
-__device__ __forceinline__ void post_point(bool valid, float x, float y, unsigned idx, const Octagon& o, RecBuf& b,
-                                           unsigned& cnt, Ctl* ctl, uint32_t* keys, uint64_t* vals,
-                                           QueueTally& tally) {
+__device__ __forceinline__ void post_point(bool valid, float x, float y, unsigned idx, const Octagon& o,
+                                           const StarView& sv, RecBuf& b, unsigned& cnt, Ctl* ctl, uint32_t* keys,
+                                           uint64_t* vals, QueueTally& tally) {
     int r = -1, X = 0, Y = 0;
     if (valid) {
         X = __float2int_rn(x);
         Y = __float2int_rn(y);
-        r = classify_hull(x, y, o);
+        if (!sv.inside(X, Y)) r = classify_hull(x, y, o);
     }
     post_stage(r, X, Y, idx, o, b, cnt, ctl, keys, vals, tally);
     tally.fold();
@@ -189,17 +201,23 @@ __device__ void post_last_block(const float* __restrict__ pts, long long n, Ctl*
 }
 
 constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
-constexpr size_t kPostSmemBytes =
-    cmax(cmax(kMidSmemBytes, sizeof(QhSmem)), (size_t)(kPostThreads / 32) * sizeof(RecBuf));
+// Dynamic shared memory: the warps' record buffers, then the star polygon
+// (vertices and bin table) while points are classified; afterwards the last
+// block's hull reuses all of it.
+constexpr size_t kRecBufBytes = (size_t)(kPostThreads / 32) * sizeof(RecBuf);
+constexpr size_t kStarSmemBytes = sizeof(int2) * (kStarBins + 2) + sizeof(unsigned short) * kStarBins;
+constexpr size_t kPostSmemBytes = cmax(cmax(kMidSmemBytes, sizeof(QhSmem)), kRecBufBytes + kStarSmemBytes);
+static_assert(kRecBufBytes % 16 == 0, "the star polygon starts 16-byte aligned");
 
 __global__ void __launch_bounds__(kPostThreads, 1) post_kernel(const float* __restrict__ pts, long long n, int head,
                                                                long long ntiles, Ctl* ctl, const uint64_t* raw_xy,
                                                                const uint32_t* raw_idx, uint32_t* keys,
                                                                uint64_t* vals, int32_t* out_idx, int64_t* out_n,
+                                                               const StarPoly* __restrict__ star,
                                                                unsigned long long cond) {
     extern __shared__ __align__(16) char dyn[];
     __shared__ Octagon s_o;
-    __shared__ int s_flag, s_mode;
+    __shared__ int s_flag, s_mode, s_star, s_sk, s_scx, s_scy;
     __shared__ unsigned s_nraw;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     CH_TL(ctl, 5, 0);
@@ -207,12 +225,28 @@ __global__ void __launch_bounds__(kPostThreads, 1) post_kernel(const float* __re
         s_flag = read_status(ctl);
         s_mode = *(volatile int*)&ctl->mode;
         s_nraw = *(volatile unsigned*)&ctl->count_raw;
+        s_star = star != nullptr && *(volatile int*)&ctl->star_ok;
+        s_sk = ctl->star_k;
+        s_scx = ctl->star_cx;
+        s_scy = ctl->star_cy;
     }
     copy_octagon(&s_o, &ctl->oct);
     __syncthreads();
     if (s_flag != CH_OK) {   // data error or timeout of an earlier stage
         if (blockIdx.x == 0 && tid == 0) { *out_n = s_flag; ctl->done = 1; }
         return;
+    }
+    StarView sv{nullptr, nullptr, s_scx, s_scy};
+    if (s_star) {   // the star pass built a polygon: copy it next to the record buffers
+        int2* v = reinterpret_cast<int2*>(dyn + kRecBufBytes);
+        unsigned short* tb = reinterpret_cast<unsigned short*>(v + (kStarBins + 2));
+        for (int i = tid; i < s_sk + 2; i += blockDim.x) v[i] = star->v[i];
+        const uint4* t4 = reinterpret_cast<const uint4*>(star->tbl);
+        for (int i = tid; i < (int)(kStarBins * sizeof(unsigned short) / 16); i += blockDim.x)
+            reinterpret_cast<uint4*>(tb)[i] = t4[i];
+        sv.v = v;
+        sv.tbl = tb;
+        __syncthreads();
     }
     RecBuf& rb = reinterpret_cast<RecBuf*>(dyn)[warp];
     unsigned rc = 0u;
@@ -251,10 +285,23 @@ __global__ void __launch_bounds__(kPostThreads, 1) post_kernel(const float* __re
                                 2u * lane;
             const int X0 = __float2int_rn(v.x), Y0 = __float2int_rn(v.y);
             const int X1 = __float2int_rn(v.z), Y1 = __float2int_rn(v.w);
-            int r0 = classify_hull_fast(v.x, v.y, X0, Y0, s_o);
-            int r1 = classify_hull_fast(v.z, v.w, X1, Y1, s_o);
-            if (r0 == kUndecided) r0 = classify_hull_slow(v.x, v.y, &s_o);
-            if (r1 == kUndecided) r1 = classify_hull_slow(v.z, v.w, &s_o);
+            int r0 = -1, r1 = -1;
+            if (sv.v) {   // most points of dense data fall inside the star polygon
+                const bool in0 = sv.inside(X0, Y0), in1 = sv.inside(X1, Y1);
+                if (!in0) {
+                    r0 = classify_hull_fast(v.x, v.y, X0, Y0, s_o);
+                    if (r0 == kUndecided) r0 = classify_hull_slow(v.x, v.y, &s_o);
+                }
+                if (!in1) {
+                    r1 = classify_hull_fast(v.z, v.w, X1, Y1, s_o);
+                    if (r1 == kUndecided) r1 = classify_hull_slow(v.z, v.w, &s_o);
+                }
+            } else {
+                r0 = classify_hull_fast(v.x, v.y, X0, Y0, s_o);
+                r1 = classify_hull_fast(v.z, v.w, X1, Y1, s_o);
+                if (r0 == kUndecided) r0 = classify_hull_slow(v.x, v.y, &s_o);
+                if (r1 == kUndecided) r1 = classify_hull_slow(v.z, v.w, &s_o);
+            }
             post_stage(r0, X0, Y0, i0, s_o, rb, rc, ctl, keys, vals, tally);
             post_stage(r1, X1, Y1, i0 + 1u, s_o, rb, rc, ctl, keys, vals, tally);
             if (s % kLoadsPerLane == kLoadsPerLane - 1) tally.fold();   // at most 2 kLoadsPerLane adds
@@ -268,7 +315,7 @@ __global__ void __launch_bounds__(kPostThreads, 1) post_kernel(const float* __re
                     const bool valid = i < ranges[rg][1];
                     float x = 0.0f, y = 0.0f;
                     if (valid) { x = pts[2 * i]; y = pts[2 * i + 1]; }
-                    post_point(valid, x, y, (unsigned)i, s_o, rb, rc, ctl, keys, vals, tally);
+                    post_point(valid, x, y, (unsigned)i, s_o, sv, rb, rc, ctl, keys, vals, tally);
                 }
         }
     } else {   // fused mode: the raw survivors of the main pass
@@ -285,7 +332,7 @@ __global__ void __launch_bounds__(kPostThreads, 1) post_kernel(const float* __re
                 y = (float)(unsigned)(xy & 0xFFFFFFFFull);
                 idx = raw_idx[i];
             }
-            post_point(valid, x, y, idx, s_o, rb, rc, ctl, keys, vals, tally);
+            post_point(valid, x, y, idx, s_o, sv, rb, rc, ctl, keys, vals, tally);
         }
     }
     rec_flush_block(rb, rc, ctl, keys, vals);
@@ -300,9 +347,9 @@ __global__ void __launch_bounds__(kPostThreads, 1) post_kernel(const float* __re
 // ---------------------------------------------------------------------------
 void launch_post(const float* pts, long long n, int head, long long ntiles, Ctl* ctl, const uint64_t* raw_xy,
                  const uint32_t* raw_idx, uint32_t* keys, uint64_t* vals, int32_t* out_idx, int64_t* out_n,
-                 unsigned long long cond, int grid, cudaStream_t s) {
+                 const void* star_poly, unsigned long long cond, int grid, cudaStream_t s) {
     post_kernel<<<grid, kPostThreads, kPostSmemBytes, s>>>(pts, n, head, ntiles, ctl, raw_xy, raw_idx, keys, vals,
-                                                          out_idx, out_n, cond);
+                                                          out_idx, out_n, (const StarPoly*)star_poly, cond);
 }
 
 cudaError_t configure_post_kernel() {

@@ -325,7 +325,10 @@ int ch_server_create(size_t budget_bytes, int device, void** srv) {
     S->device = device;
     S->budget = budget_bytes;
     // Split of the budget: per point a batch needs 12 bytes of arena (points
-    // in, indices out) and about ws bytes of workspace on each slot stream.
+    // in, indices out) and about ws bytes of single-hull workspace on each
+    // slot stream (sets left to that path).  Each slot's batched workspace,
+    // reserved below for batches of up to max_points points in kMaxBatch sets,
+    // comes on top of the budget.
     const double ws_pp = (double)ch_workspace_bytes(1 << 20) / (double)(1 << 20);
     const double per_point = 12.0 + (double)kSlots * ws_pp;
     S->max_points = (int64_t)((double)budget_bytes / per_point);

@@ -45,9 +45,18 @@ def test_workload_configs_cover_every_single_hull_workload():
 
 
 def test_traffic_comes_from_the_committed_profile_while_its_source_is_unchanged():
+    import re
+    text = open(os.path.join(ROOT, "profiles", "main_filter_normal_1e8.md")).read()
+    per_launch = float(re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text).group(1))
+    pts = float(re.search(r"points_per_launch:\s*([0-9.eE+]+)", text).group(1))
+    src = re.search(r"source_file:\s*(\S+)", text).group(1)
+    sha = re.search(r"source_sha:\s*([0-9a-f]+)", text).group(1)
     t = bench.traffic_from_profile("main_filter", "normal_1e8", 100_000_000)
-    assert t == pytest.approx(810.3e6)
-    assert bench.traffic_from_profile("main_filter", "normal_1e8", 50_000_000) == pytest.approx(405.15e6)
+    if bench.source_sha(os.path.join(ROOT, src)) == sha:
+        assert t == pytest.approx(per_launch * 1e8 / pts)
+        assert bench.traffic_from_profile("main_filter", "normal_1e8", 50_000_000) == pytest.approx(t / 2)
+    else:   # the kernel changed since the capture: no traffic figure
+        assert t is None
     assert bench.traffic_from_profile("no_such_kernel", "normal_1e8", 1) is None
 
 
