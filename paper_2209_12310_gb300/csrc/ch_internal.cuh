@@ -136,8 +136,9 @@ struct Ctl {
     int bk_shift;                       // fine buckets per coarse group: 1 << bk_shift
     unsigned int bk_next;               // next bucket for a bk_hull warp
     int samp_ok;                        // oct_s holds this call's sample octagon
-    int star_ok;                        // the star polygon of this call is ready (star.cu)
+    int star_ok;                        // the star pass gathered this call's vertex list (star.cu)
     int star_k;                         // its vertices
+    int star_final;                     // the post pass finished and accepted the polygon
     int star_cx, star_cy;               // its centre (vertices are stored relative to it)
     unsigned int star_pts, star_out;    // points the star pass read / found outside the sample octagon
     unsigned int star_done;             // last-arriver counter of the star pass

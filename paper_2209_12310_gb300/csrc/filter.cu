@@ -78,6 +78,7 @@ __global__ void init_kernel(Ctl* ctl, int mode) {
         ctl->samp_ok = 0;
         ctl->star_ok = 0;
         ctl->star_k = 0;
+        ctl->star_final = 0;
         ctl->star_pts = 0u;
         ctl->star_out = 0u;
         ctl->star_done = 0u;

@@ -70,11 +70,10 @@ __device__ __forceinline__ void post_stage(int r, int X, int Y, unsigned idx, co
 // The star polygon in shared memory (null when this call has none) and its
 // centre; points strictly inside it are dropped before the octagon test.
 struct StarView {
-    const int2* v;
-    const unsigned short* tbl;
+    const StarPoly* P;
     int cx, cy;
     __device__ __forceinline__ bool inside(int X, int Y) const {
-        return v != nullptr && star_inside(X - cx, Y - cy, v, tbl);
+        return P != nullptr && star_inside(X - cx, Y - cy, *P);
     }
 };
 
@@ -202,18 +201,19 @@ __device__ void post_last_block(const float* __restrict__ pts, long long n, Ctl*
 
 constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
 // Dynamic shared memory: the warps' record buffers, then the star polygon
-// (vertices and bin table) while points are classified; afterwards the last
-// block's hull reuses all of it.
+// while points are classified (the polygon is finished first, with the
+// record buffers as its work area); afterwards the last block's hull reuses
+// all of it.
 constexpr size_t kRecBufBytes = (size_t)(kPostThreads / 32) * sizeof(RecBuf);
-constexpr size_t kStarSmemBytes = sizeof(int2) * (kStarBins + 2) + sizeof(unsigned short) * kStarBins;
-constexpr size_t kPostSmemBytes = cmax(cmax(kMidSmemBytes, sizeof(QhSmem)), kRecBufBytes + kStarSmemBytes);
+constexpr size_t kPostSmemBytes = cmax(cmax(kMidSmemBytes, sizeof(QhSmem)), kRecBufBytes + sizeof(StarPoly));
 static_assert(kRecBufBytes % 16 == 0, "the star polygon starts 16-byte aligned");
+static_assert(kRecBufBytes >= (sizeof(int2) + sizeof(unsigned short)) * kStarBins, "work area A fits");
 
 __global__ void __launch_bounds__(kPostThreads, 1) post_kernel(const float* __restrict__ pts, long long n, int head,
                                                                long long ntiles, Ctl* ctl, const uint64_t* raw_xy,
                                                                const uint32_t* raw_idx, uint32_t* keys,
                                                                uint64_t* vals, int32_t* out_idx, int64_t* out_n,
-                                                               const StarPoly* __restrict__ star,
+                                                               const StarList* __restrict__ star,
                                                                unsigned long long cond) {
     extern __shared__ __align__(16) char dyn[];
     __shared__ Octagon s_o;
@@ -236,16 +236,13 @@ __global__ void __launch_bounds__(kPostThreads, 1) post_kernel(const float* __re
         if (blockIdx.x == 0 && tid == 0) { *out_n = s_flag; ctl->done = 1; }
         return;
     }
-    StarView sv{nullptr, nullptr, s_scx, s_scy};
-    if (s_star) {   // the star pass built a polygon: copy it next to the record buffers
-        int2* v = reinterpret_cast<int2*>(dyn + kRecBufBytes);
-        unsigned short* tb = reinterpret_cast<unsigned short*>(v + (kStarBins + 2));
-        for (int i = tid; i < s_sk + 2; i += blockDim.x) v[i] = star->v[i];
-        const uint4* t4 = reinterpret_cast<const uint4*>(star->tbl);
-        for (int i = tid; i < (int)(kStarBins * sizeof(unsigned short) / 16); i += blockDim.x)
-            reinterpret_cast<uint4*>(tb)[i] = t4[i];
-        sv.v = v;
-        sv.tbl = tb;
+    StarView sv{nullptr, s_scx, s_scy};
+    if (s_star) {   // the star pass gathered a vertex list: finish the polygon here
+        StarPoly* P = reinterpret_cast<StarPoly*>(dyn + kRecBufBytes);
+        int2* va = reinterpret_cast<int2*>(dyn);
+        unsigned short* ba = reinterpret_cast<unsigned short*>(dyn + sizeof(int2) * kStarBins);
+        if (star_finish<kPostThreads>(star, s_sk, va, ba, *P)) sv.P = P;
+        if (blockIdx.x == 0 && tid == 0) ctl->star_final = sv.P ? 1 : 0;
         __syncthreads();
     }
     RecBuf& rb = reinterpret_cast<RecBuf*>(dyn)[warp];
@@ -286,7 +283,7 @@ __global__ void __launch_bounds__(kPostThreads, 1) post_kernel(const float* __re
             const int X0 = __float2int_rn(v.x), Y0 = __float2int_rn(v.y);
             const int X1 = __float2int_rn(v.z), Y1 = __float2int_rn(v.w);
             int r0 = -1, r1 = -1;
-            if (sv.v) {   // most points of dense data fall inside the star polygon
+            if (sv.P) {   // most points of dense data fall inside the star polygon
                 const bool in0 = sv.inside(X0, Y0), in1 = sv.inside(X1, Y1);
                 if (!in0) {
                     r0 = classify_hull_fast(v.x, v.y, X0, Y0, s_o);
@@ -347,9 +344,9 @@ __global__ void __launch_bounds__(kPostThreads, 1) post_kernel(const float* __re
 // ---------------------------------------------------------------------------
 void launch_post(const float* pts, long long n, int head, long long ntiles, Ctl* ctl, const uint64_t* raw_xy,
                  const uint32_t* raw_idx, uint32_t* keys, uint64_t* vals, int32_t* out_idx, int64_t* out_n,
-                 const void* star_poly, unsigned long long cond, int grid, cudaStream_t s) {
+                 const void* star_list, unsigned long long cond, int grid, cudaStream_t s) {
     post_kernel<<<grid, kPostThreads, kPostSmemBytes, s>>>(pts, n, head, ntiles, ctl, raw_xy, raw_idx, keys, vals,
-                                                          out_idx, out_n, (const StarPoly*)star_poly, cond);
+                                                          out_idx, out_n, (const StarList*)star_list, cond);
 }
 
 cudaError_t configure_post_kernel() {

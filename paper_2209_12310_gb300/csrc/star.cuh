@@ -1,43 +1,55 @@
-// star.cuh -- a star-shaped filter polygon for dense data, and its point test.
+// star.cuh -- a star-shaped filter polygon for dense data, and its point tests.
 //
 // When most points survive the octagon (points near a circle, the worst case
 // of Table V), the octagon leaves a rim of width ~0.08 R that holds almost
 // every point.  A polygon with thousands of vertices that are input points
-// hugs the hull far closer.  It is built from a sample (star.cu): around a
-// centre c strictly inside it, the sample is split into kStarBins angular
-// bins and each bin keeps its point farthest from c; the kept points, in
-// angular order, are the polygon's vertices (some reflex vertices are then
-// dropped, which only enlarges it).
+// hugs the hull far closer.  It is built from a sample: around a centre c,
+// the sample is split into kStarBins angular bins and each bin keeps its point
+// farthest from c (star.cu gathers those points into a vertex list); every
+// post-pass block then finishes the polygon in shared memory (star_finish):
+// it drops some reflex vertices, which only enlarges it, checks it exactly,
+// and builds the lookup tables of the point tests.
 //
 // Why dropping points strictly inside it is exact: every vertex is an input
 // point, and the polygon is star-shaped around c with every wedge
 // (c, V_j, V_j+1) turning counter-clockwise by less than pi and the wedges
-// winding once around c (checked exactly when it is built).  So it is the
-// union of the triangles (c, V_j, V_j+1), each inside the hull of the input;
-// a point in its interior is in the interior of the hull, no hull vertex,
-// and so are all its duplicates.  The test below drops a point only when it
-// proves, with exact integer orientations, that the point lies in a closed
-// wedge and strictly on c's side of that wedge's edge; any doubt keeps it.
+// winding once around c (checked exactly).  So it is the union of the
+// triangles (c, V_j, V_j+1), each inside the hull of the input; a point in its
+// interior is in the interior of the hull, no hull vertex, and so are all its
+// duplicates.  The tests below drop a point only when they prove that it lies
+// strictly inside; any doubt keeps it.
 #pragma once
 
 #include "ch_internal.cuh"
 
 namespace ch {
 
-// The polygon as the post pass reads it: vertices relative to c (|.| < 2^24,
-// so every orientation below is exact in int64), counter-clockwise, with the
-// first two repeated after the last so that j + 2 needs no wrap; per angular
-// bin, the last vertex whose bin comes before it (K - 1 when none does).
+// The gathered vertices (global memory, written by the star pass): relative
+// to c, in bin order, with their bins; their number is ctl->star_k.
+struct StarList {
+    int2 v[kStarBins];
+    unsigned short b[kStarBins];
+    int2 park[kStarBins];   // the star pass's scratch: each kept point by bin
+};
+
+// The finished polygon (shared memory of a post-pass block):
+//   v    vertices relative to c (|.| < 2^24: every orientation is exact in
+//        int64), counter-clockwise, the first two repeated after the last;
+//   tbl  per bin, the last vertex whose bin comes before it (K - 1 if none);
+//   rin  per bin, a lower bound on the squared distance from c to the line
+//        of every edge whose wedge meets the bin or its two neighbours on
+//        either side: a point of the bin closer to c than that is strictly
+//        inside (0 when no bound was found).
 struct StarPoly {
     int2 v[kStarBins + 2];
     unsigned short tbl[kStarBins];
+    float rin[kStarBins];
 };
-constexpr size_t kStarPolyBytes = sizeof(StarPoly);
 
 // Angular bin of an offset (dx, dy) from c: a pseudo-angle in [0, 4) that
 // grows with the angle (|dy| / (|dx| + |dy|) per quadrant), scaled to
-// kStarBins bins.  Float rounding may move a point near a bin boundary to
-// the neighbouring bin; the test never relies on the bin being right.
+// kStarBins bins.  Float rounding may move a point near a bin boundary to the
+// neighbouring bin; no test relies on the bin being right to within one bin.
 __device__ __forceinline__ int star_bin(int dx, int dy) {
     const float fx = (float)dx, fy = (float)dy;   // exact: |d| < 2^24
     const float ax = fabsf(fx), ay = fabsf(fy), s = ax + ay;
@@ -51,21 +63,172 @@ __device__ __forceinline__ long long star_orient_c(int2 v, int px, int py) {
     return (long long)v.x * py - (long long)v.y * px;
 }
 
-// True only when p = c + (px, py) is strictly inside the polygon.  The bin's
+// Exact test: true only when p = c + (px, py) is strictly inside.  The bin's
 // table entry j names the last vertex before the bin; p lies in wedge j
 // (V_j, V_j+1) or, when it is past V_j+1, in wedge j+1 (V_j+1's bin may be
 // p's own).  The chosen wedge is verified on both spokes, then p must be
 // strictly left of the wedge's edge.
-__device__ __forceinline__ bool star_inside(int px, int py, const int2* __restrict__ v,
-                                            const unsigned short* __restrict__ tbl) {
-    const int j = tbl[star_bin(px, py)];
-    const int2 a = v[j], m = v[j + 1], z = v[j + 2];
+__device__ __forceinline__ bool star_inside_exact(int px, int py, int b, const StarPoly& P) {
+    const int j = P.tbl[b];
+    const int2 a = P.v[j], m = P.v[j + 1], z = P.v[j + 2];
     const bool past_m = star_orient_c(m, px, py) > 0;
     const bool spoke_ok = past_m ? star_orient_c(z, px, py) <= 0 : star_orient_c(a, px, py) >= 0;
     const int2 e0 = past_m ? m : a, e1 = past_m ? z : m;
     const long long side =
         (long long)(e1.x - e0.x) * (py - e0.y) - (long long)(e1.y - e0.y) * (px - e0.x);
     return spoke_ok && side > 0;
+}
+
+// Full test: first the bin's distance bound (one float compare; the bound
+// carries a margin larger than the rounding of both sides), then the exact
+// wedge test.
+__device__ __forceinline__ bool star_inside(int px, int py, const StarPoly& P) {
+    const int b = star_bin(px, py);
+    const float fx = (float)px, fy = (float)py;
+    if (fmaf(fy, fy, fx * fx) < P.rin[b]) return true;
+    return star_inside_exact(px, py, b, P);
+}
+
+// Block-wide exclusive scan of one count per thread (warp shuffles, then the
+// warp totals in s, one word per warp); returns the thread's offset and
+// leaves the total in *total.
+template <int T>
+__device__ __forceinline__ int star_scan(int c, unsigned* s, int* total) {
+    constexpr int kWarps = T / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned incl = (unsigned)c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned u = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) s[warp] = incl;
+    __syncthreads();
+    unsigned before = 0u, all = 0u;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+        const unsigned x = s[w];
+        before += w < warp ? x : 0u;
+        all += x;
+    }
+    if (threadIdx.x == 0) *total = (int)all;
+    __syncthreads();
+    return (int)(before + incl - (unsigned)c);
+}
+
+constexpr int kStarSweeps = 8;   // reflex-removal sweeps (alternately even and odd positions)
+
+// Finishes the polygon from the gathered list (K vertices) in shared memory,
+// all T threads of the block: work area A (va, ba) and the polygon P, whose
+// first bytes double as work area B (vb, bb).  Returns true (the same in
+// every thread) when the polygon passed its checks and P is ready.
+//
+// Sweeps: a vertex at an even (then odd) position is dropped when it is
+// reflex or flat, orient(V_j-1, V_j, V_j+1) <= 0, and its neighbours still
+// turn by less than pi around c, orient(c, V_j-1, V_j+1) > 0; same-parity
+// vertices are never neighbours (with K odd, the last vertex sits out the
+// even sweeps), so every drop sees its neighbours unchanged.  Dropping a
+// reflex vertex adds the triangle (V_j-1, V_j, V_j+1) to the polygon.
+template <int T>
+__device__ bool star_finish(const StarList* __restrict__ list, int K, int2* va, unsigned short* ba, StarPoly& P) {
+    static_assert(T % 32 == 0 && T <= 1024, "block size");
+    static_assert(sizeof(StarPoly) >= sizeof(int2) * kStarBins + sizeof(unsigned short) * kStarBins,
+                  "work area B fits in the polygon");
+    int2* vb = P.v;
+    unsigned short* bb = reinterpret_cast<unsigned short*>(reinterpret_cast<char*>(P.v) +
+                                                           sizeof(int2) * kStarBins);
+    __shared__ unsigned s_scan[T / 32];
+    __shared__ int s_K, s_bad, s_cross;
+    const int t = threadIdx.x;
+    if (K < 3 || K > kStarBins) return false;
+    for (int i = t; i < K; i += T) {
+        va[i] = list->v[i];
+        ba[i] = list->b[i];
+    }
+    if (t == 0) { s_K = K; s_bad = 0; s_cross = 0; }
+    __syncthreads();
+    int2* src = va; int2* dst = vb;
+    unsigned short* bsrc = ba; unsigned short* bdst = bb;
+    int idle = 0;   // consecutive sweeps that dropped nothing
+    for (int sweep = 0; sweep < kStarSweeps && idle < 2; ++sweep) {
+        const int k = s_K;
+        if (k <= 3) break;
+        const int par = sweep & 1;
+        const int chunk = (k + T - 1) / T;
+        const int lo = min(k, t * chunk), hi = min(k, lo + chunk);
+        unsigned keep = 0u;   // chunk <= kStarBins / T <= 32 for T >= 256
+        for (int j = lo; j < hi; ++j) {
+            bool drop = (j & 1) == par && !((k & 1) && j == k - 1);
+            if (drop) {
+                const int2 a = src[j == 0 ? k - 1 : j - 1], m = src[j], z = src[j + 1 == k ? 0 : j + 1];
+                const long long turn = (long long)(m.x - a.x) * (z.y - a.y) - (long long)(m.y - a.y) * (z.x - a.x);
+                drop = turn <= 0 && star_orient_c(a, z.x, z.y) > 0;
+            }
+            if (!drop) keep |= 1u << (j - lo);
+        }
+        __syncthreads();   // every read of s_K and src of this sweep is done
+        int o = star_scan<T>(__popc(keep), s_scan, &s_K);
+        idle = s_K == k ? idle + 1 : 0;
+        for (int j = lo; j < hi; ++j) {
+            if ((keep >> (j - lo)) & 1u) {
+                dst[o] = src[j];
+                bdst[o] = bsrc[j];
+                ++o;
+            }
+        }
+        __syncthreads();
+        int2* tv = src; src = dst; dst = tv;
+        unsigned short* tb = bsrc; bsrc = bdst; bdst = tb;
+    }
+    K = s_K;
+    if (src != va) {   // the list must sit in A before P is written over B
+        for (int i = t; i < K; i += T) {
+            va[i] = vb[i];
+            ba[i] = bb[i];
+        }
+        __syncthreads();
+    }
+    // checks: every wedge turns counter-clockwise by less than pi, and exactly
+    // one edge crosses the ray from c along +x (the wedges wind once)
+    int bad = 0, cross = 0;
+    for (int j = t; j < K; j += T) {
+        const int2 a = va[j], b = va[j + 1 == K ? 0 : j + 1];
+        bad |= star_orient_c(a, b.x, b.y) <= 0;
+        cross += (a.y < 0 && b.y >= 0) ? 1 : 0;
+    }
+    if (bad) atomicOr(&s_bad, 1);
+    if (cross) atomicAdd(&s_cross, cross);
+    __syncthreads();
+    const bool ok = K >= 3 && !s_bad && s_cross == 1;
+    if (!ok) return false;
+    // the polygon: vertices, then the bin table, then the distance bounds
+    for (int j = t; j < K + 2; j += T) P.v[j] = va[j < K ? j : j - K];
+    for (int j = t; j < K; j += T) {
+        const int b0 = ba[j];
+        const int b1 = j + 1 < K ? (int)ba[j + 1] : (int)ba[0] + kStarBins;
+        for (int b = b0 + 1; b <= b1; ++b) P.tbl[b & (kStarBins - 1)] = (unsigned short)j;
+    }
+    __syncthreads();
+    for (int b = t; b < kStarBins; b += T) {
+        const int first = P.tbl[(b - 2) & (kStarBins - 1)];
+        const int last = P.tbl[(b + 2) & (kStarBins - 1)] + 1;   // an edge index in [1, K]
+        float m = 3.0e38f;
+        int e = first, steps = 0;
+        for (;;) {
+            const int2 a = P.v[e], c2 = P.v[e + 1];
+            const long long o = (long long)a.x * c2.y - (long long)a.y * c2.x;   // orient(c, V_e, V_e+1) > 0
+            const long long dx = (long long)c2.x - a.x, dy = (long long)c2.y - a.y;
+            const float of = (float)o, lf = (float)(dx * dx + dy * dy);
+            m = fminf(m, of * of / lf);
+            if ((e % K) == (last % K) || ++steps > 8) break;
+            e = e + 1 == K ? 0 : e + 1;
+        }
+        // squared distances of edges [first, last] in float: within 5 roundings
+        // of 2^-24 of the exact values; the bound keeps a margin of 2^-18
+        P.rin[b] = steps > 8 ? 0.0f : m * (1.0f - 3.814697265625e-6f);
+    }
+    __syncthreads();
+    return true;
 }
 
 }  // namespace ch
