@@ -34,6 +34,7 @@ static int device_info(int dev, DevInfo* out) {
     if (configure_filter_kernels() != cudaSuccess) return CH_ECUDA;
     if (configure_post_kernel() != cudaSuccess) return CH_ECUDA;
     if (configure_bucket_kernels() != cudaSuccess) return CH_ECUDA;
+    if (configure_star_kernel() != cudaSuccess) return CH_ECUDA;
     if (occupancy_filter(&di.occ_main, &di.occ_lab) != cudaSuccess) return CH_ECUDA;
     if (occupancy_post(&di.occ_post) != cudaSuccess) return CH_ECUDA;
     if (occupancy_sort(&di.occ_sort) != cudaSuccess) return CH_ECUDA;
@@ -331,23 +332,24 @@ static void enqueue_filter_part(const float* pts, long long n, int32_t* out_idx,
     { ProfScope p("init", s); launch_init(h.ctl, 0, s); }
     { ProfScope p("sample", s); launch_sample(pts, n, h.head, h.ntiles, h.ctl, grid_sample, s); }
     // The star pass needs only the sample octagon: it runs on its own branch
-    // beside the main pass, and the post pass waits for both.
+    // beside the main pass, and the post pass waits for both.  The main pass
+    // is enqueued first, so that its blocks are placed before the star pass's.
     const bool star = h.side != nullptr;
+    if (star) cudaEventRecord(h.ev_fork, s);
+    {
+        ProfScope p("main_filter", s);
+        launch_main(pts, n, h.head, h.ntiles, h.ctl, raw_xy, raw_idx, switch_at, h.kA, h.vA,
+                    h.di.sms * h.di.occ_main, s);
+    }
     if (star) {
-        cudaEventRecord(h.ev_fork, s);
         cudaStreamWaitEvent(h.side, h.ev_fork, 0);
         {
             ProfScope p("star", h.side);
             launch_star(pts, n, h.head, h.ntiles, h.ctl, h.star_bins, h.star_list, h.di.sms, h.side);
         }
         cudaEventRecord(h.ev_join, h.side);
+        cudaStreamWaitEvent(s, h.ev_join, 0);
     }
-    {
-        ProfScope p("main_filter", s);
-        launch_main(pts, n, h.head, h.ntiles, h.ctl, raw_xy, raw_idx, switch_at, h.kA, h.vA,
-                    h.di.sms * h.di.occ_main, s);
-    }
-    if (star) cudaStreamWaitEvent(s, h.ev_join, 0);
     {
         ProfScope p("post", s);
         launch_post(pts, n, h.head, h.ntiles, h.ctl, raw_xy, raw_idx, h.kA, h.vA, out_idx, out_n,
@@ -708,15 +710,15 @@ int ch_hull_counters(void* stream, int64_t* out, int cap) {
 
 #if defined(CH_TRACE) || defined(CH_TIMELINE)
 // Debug builds: the phase timeline of the most recent call on the first
-// workspace (ns since the init kernel).
-int ch_trace_timeline(unsigned long long* out16) {
+// workspace (%globaltimer ns; 10 phases, first start and last end of each).
+int ch_trace_timeline(unsigned long long* out20) {
     std::lock_guard<std::mutex> lk(g_mu);
     if (g_ws.empty() || !g_ws.begin()->second.base) return CH_EINVAL;
     Ctl c;
     if (cudaMemcpy(&c, g_ws.begin()->second.base, sizeof(Ctl), cudaMemcpyDeviceToHost) != cudaSuccess) return CH_ECUDA;
-    for (int i = 0; i < 8; ++i) {
-        out16[2 * i] = c.tl[i][0];
-        out16[2 * i + 1] = c.tl[i][1];
+    for (int i = 0; i < 10; ++i) {
+        out20[2 * i] = c.tl[i][0];
+        out20[2 * i + 1] = c.tl[i][1];
     }
     return CH_OK;
 }

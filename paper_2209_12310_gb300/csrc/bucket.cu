@@ -79,9 +79,24 @@ __global__ void bk_prep(Ctl* ctl, unsigned* bcount, unsigned bmax) {
     if (tid < 4) s_q[tid] = ctl->rec_q[tid];
     __syncthreads();
     if (tid == 0) {
+        // Records that a star polygon left are mostly near the hull, so a
+        // bucket of kBkAvg of them would hold too many chain vertices: then
+        // at most kBkNearHull records per bucket, when that fits the
+        // workspace's bucket capacity.
+        const bool near_hull = *(volatile int*)&ctl->star_final != 0;
+        unsigned tot_near = 0u;
+        for (int r = 0; r < 4; ++r) {
+            const unsigned nb = bk_buckets_for(s_q[r]);
+            const unsigned nh = (s_q[r] + kBkNearHull - 1) / kBkNearHull;
+            tot_near += nb > nh ? nb : nh;
+        }
+        const bool use_near = near_hull && tot_near <= bmax;
         s_base[0] = 0u;
         for (int r = 0; r < 4; ++r) {
-            s_base[r + 1] = s_base[r] + bk_buckets_for(s_q[r]);
+            unsigned nb = bk_buckets_for(s_q[r]);
+            const unsigned nh = (s_q[r] + kBkNearHull - 1) / kBkNearHull;
+            if (use_near && nh > nb) nb = nh;
+            s_base[r + 1] = s_base[r] + nb;
         }
     }
     __syncthreads();

@@ -41,6 +41,7 @@ constexpr int kMergeSmemCap = 8192;           // chain points a global merge kee
 // Bucketed large-survivor path (bucket.cu): records per bucket on average,
 // chain vertices a bucket may keep, bucket chains per chain-kernel tile.
 constexpr int kBkAvg = 256;
+constexpr int kBkNearHull = 64;   // records per bucket when a star polygon filtered them
 constexpr int kBkChain = 32;
 constexpr int kBkGroup = kChainTile / kBkChain;
 // Buckets of a queue of cnt records: about kBkAvg records each, and at least
@@ -145,7 +146,7 @@ struct Ctl {
     Octagon oct;                        // octagon of the true extremes
     Octagon oct_s;                      // octagon of a sample's extremes
 #if defined(CH_TRACE) || defined(CH_TIMELINE)
-    unsigned long long tl[8][2];        // debug builds: first start / last end per phase (%globaltimer)
+    unsigned long long tl[10][2];       // debug builds: first start / last end per phase (%globaltimer)
 #endif
 };
 

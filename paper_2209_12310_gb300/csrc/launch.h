@@ -20,6 +20,7 @@ void launch_labels(const float* pts, long long n, Ctl* ctl, uint8_t* labels, int
 // The star pass (star.cu): its bins and vertex list live in the workspace.
 void launch_star(const float* pts, long long n, int head, long long ntiles, Ctl* ctl, void* bins, void* list,
                  int grid, cudaStream_t s);
+cudaError_t configure_star_kernel();
 size_t star_bins_bytes();
 size_t star_list_bytes();
 void launch_filter_output(const Ctl* ctl, long long n, int32_t* out_ext8, int64_t* out_counts4, cudaStream_t s);

@@ -25,7 +25,7 @@ static_assert(kPostThreads % 128 == 0, "mid_hull splits the block in four");
 // one atomic on the record counter, and at the end the block's remainders go
 // out together with one atomic (a single counter hit once per warp batch
 // serialises at L2).
-constexpr int kRecBuf = 512;
+constexpr int kRecBuf = 256;
 struct RecBuf {
     unsigned long long val[kRecBuf];
     unsigned key[kRecBuf];
@@ -200,14 +200,39 @@ __device__ void post_last_block(const float* __restrict__ pts, long long n, Ctl*
 }
 
 constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
-// Dynamic shared memory: the warps' record buffers, then the star polygon
-// while points are classified (the polygon is finished first, with the
-// record buffers as its work area); afterwards the last block's hull reuses
-// all of it.
-constexpr size_t kRecBufBytes = (size_t)(kPostThreads / 32) * sizeof(RecBuf);
-constexpr size_t kPostSmemBytes = cmax(cmax(kMidSmemBytes, sizeof(QhSmem)), kRecBufBytes + sizeof(StarPoly));
-static_assert(kRecBufBytes % 16 == 0, "the star polygon starts 16-byte aligned");
-static_assert(kRecBufBytes >= (sizeof(int2) + sizeof(unsigned short)) * kStarBins, "work area A fits");
+
+// Points of dense data that the star polygon's radius test leaves undecided,
+// queued per warp and taken 32 at a time through the exact tests, so that a
+// few such points do not hold a whole warp in the slow path.
+constexpr int kQueueCap = 96;   // < 32 waiting + 64 added per step
+struct WarpQueue {
+    int x[kQueueCap], y[kQueueCap];
+    unsigned idx[kQueueCap];
+};
+
+// Dynamic shared memory while points are classified: the star polygon, the
+// warps' record buffers, the warps' queues.  The polygon is finished first,
+// with the region from the record buffers on as its work area A; afterwards
+// the last block's hull reuses all of it.
+constexpr size_t kRecBufOff = (sizeof(StarPoly) + 15) / 16 * 16;
+constexpr size_t kQueueOff = kRecBufOff + (size_t)(kPostThreads / 32) * sizeof(RecBuf);
+constexpr size_t kClassifyBytes = kQueueOff + (size_t)(kPostThreads / 32) * sizeof(WarpQueue);
+constexpr size_t kWorkABytes = (sizeof(int2) + sizeof(unsigned short)) * kStarBins;
+constexpr size_t kPostSmemBytes =
+    cmax(cmax(kMidSmemBytes, sizeof(QhSmem)), cmax(kClassifyBytes, kRecBufOff + kWorkABytes));
+
+// Warp-collective: the exact star test and the octagon classification of one
+// queued point per lane (valid = false for none), then staging.
+__device__ __forceinline__ void post_queued(bool valid, int X, int Y, unsigned idx, const Octagon& o,
+                                            const StarView& sv, RecBuf& b, unsigned& cnt, Ctl* ctl, uint32_t* keys,
+                                            uint64_t* vals, QueueTally& tally) {
+    int r = -1;
+    if (valid) {
+        const int px = X - sv.cx, py = Y - sv.cy;
+        if (!star_inside_exact(px, py, star_bin(px, py), *sv.P)) r = classify_hull((float)X, (float)Y, o);
+    }
+    post_stage(r, X, Y, idx, o, b, cnt, ctl, keys, vals, tally);
+}
 
 __global__ void __launch_bounds__(kPostThreads, 1) post_kernel(const float* __restrict__ pts, long long n, int head,
                                                                long long ntiles, Ctl* ctl, const uint64_t* raw_xy,
@@ -238,14 +263,16 @@ __global__ void __launch_bounds__(kPostThreads, 1) post_kernel(const float* __re
     }
     StarView sv{nullptr, s_scx, s_scy};
     if (s_star) {   // the star pass gathered a vertex list: finish the polygon here
-        StarPoly* P = reinterpret_cast<StarPoly*>(dyn + kRecBufBytes);
-        int2* va = reinterpret_cast<int2*>(dyn);
-        unsigned short* ba = reinterpret_cast<unsigned short*>(dyn + sizeof(int2) * kStarBins);
+        StarPoly* P = reinterpret_cast<StarPoly*>(dyn);
+        int2* va = reinterpret_cast<int2*>(dyn + kRecBufOff);
+        unsigned short* ba = reinterpret_cast<unsigned short*>(dyn + kRecBufOff + sizeof(int2) * kStarBins);
+        CH_TL(ctl, 8, 0);
         if (star_finish<kPostThreads>(star, s_sk, va, ba, *P)) sv.P = P;
+        CH_TL(ctl, 8, 1);
         if (blockIdx.x == 0 && tid == 0) ctl->star_final = sv.P ? 1 : 0;
         __syncthreads();
     }
-    RecBuf& rb = reinterpret_cast<RecBuf*>(dyn)[warp];
+    RecBuf& rb = reinterpret_cast<RecBuf*>(dyn + kRecBufOff)[warp];
     unsigned rc = 0u;
     QueueTally tally;
     if (s_mode == 1) {   // two-pass mode: every point
@@ -265,6 +292,8 @@ __global__ void __launch_bounds__(kPostThreads, 1) post_kernel(const float* __re
             return (st % kLoadsPerLane == kLoadsPerLane - 1) ? st + sstep - (kLoadsPerLane - 1) : st + 1;
         };
         unsigned s = gwarp * kLoadsPerLane, sl = s;   // sl: the step of the newest load
+        WarpQueue& wq = reinterpret_cast<WarpQueue*>(dyn + kQueueOff)[warp];
+        unsigned qn = 0u;   // points waiting in wq (warp-uniform)
         float4 q[kAhead];
 #pragma unroll
         for (int a = 0; a < kAhead; ++a) {
@@ -282,27 +311,51 @@ __global__ void __launch_bounds__(kPostThreads, 1) post_kernel(const float* __re
                                 2u * lane;
             const int X0 = __float2int_rn(v.x), Y0 = __float2int_rn(v.y);
             const int X1 = __float2int_rn(v.z), Y1 = __float2int_rn(v.w);
-            int r0 = -1, r1 = -1;
-            if (sv.P) {   // most points of dense data fall inside the star polygon
-                const bool in0 = sv.inside(X0, Y0), in1 = sv.inside(X1, Y1);
-                if (!in0) {
-                    r0 = classify_hull_fast(v.x, v.y, X0, Y0, s_o);
-                    if (r0 == kUndecided) r0 = classify_hull_slow(v.x, v.y, &s_o);
-                }
-                if (!in1) {
-                    r1 = classify_hull_fast(v.z, v.w, X1, Y1, s_o);
-                    if (r1 == kUndecided) r1 = classify_hull_slow(v.z, v.w, &s_o);
+            if (sv.P) {
+                // most points of dense data are inside the star polygon's
+                // radius bound of their bin; the rest wait in the queue
+                const int px0 = X0 - sv.cx, py0 = Y0 - sv.cy, px1 = X1 - sv.cx, py1 = Y1 - sv.cy;
+                const bool d0 = star_inside_fast(px0, py0, star_bin(px0, py0), *sv.P);
+                const bool d1 = star_inside_fast(px1, py1, star_bin(px1, py1), *sv.P);
+                const unsigned m0 = __ballot_sync(0xFFFFFFFFu, !d0), m1 = __ballot_sync(0xFFFFFFFFu, !d1);
+                if (m0 | m1) {
+                    const unsigned lt = lanemask_lt();
+                    if (!d0) {
+                        const unsigned pos = qn + __popc(m0 & lt);
+                        wq.x[pos] = X0; wq.y[pos] = Y0; wq.idx[pos] = i0;
+                    }
+                    if (!d1) {
+                        const unsigned pos = qn + __popc(m0) + __popc(m1 & lt);
+                        wq.x[pos] = X1; wq.y[pos] = Y1; wq.idx[pos] = i0 + 1u;
+                    }
+                    qn += __popc(m0) + __popc(m1);
+                    __syncwarp();
+                    while (qn >= 32u) {
+                        qn -= 32u;
+                        const int X = wq.x[qn + lane], Y = wq.y[qn + lane];
+                        const unsigned id = wq.idx[qn + lane];
+                        __syncwarp();
+                        post_queued(true, X, Y, id, s_o, sv, rb, rc, ctl, keys, vals, tally);
+                    }
                 }
             } else {
-                r0 = classify_hull_fast(v.x, v.y, X0, Y0, s_o);
-                r1 = classify_hull_fast(v.z, v.w, X1, Y1, s_o);
+                int r0 = classify_hull_fast(v.x, v.y, X0, Y0, s_o);
+                int r1 = classify_hull_fast(v.z, v.w, X1, Y1, s_o);
                 if (r0 == kUndecided) r0 = classify_hull_slow(v.x, v.y, &s_o);
                 if (r1 == kUndecided) r1 = classify_hull_slow(v.z, v.w, &s_o);
+                post_stage(r0, X0, Y0, i0, s_o, rb, rc, ctl, keys, vals, tally);
+                post_stage(r1, X1, Y1, i0 + 1u, s_o, rb, rc, ctl, keys, vals, tally);
             }
-            post_stage(r0, X0, Y0, i0, s_o, rb, rc, ctl, keys, vals, tally);
-            post_stage(r1, X1, Y1, i0 + 1u, s_o, rb, rc, ctl, keys, vals, tally);
             if (s % kLoadsPerLane == kLoadsPerLane - 1) tally.fold();   // at most 2 kLoadsPerLane adds
             s = next_step(s);
+        }
+        if (qn) {   // the queue's remainder
+            const bool valid = (unsigned)lane < qn;
+            const int X = valid ? wq.x[lane] : 0, Y = valid ? wq.y[lane] : 0;
+            const unsigned id = valid ? wq.idx[lane] : 0u;
+            __syncwarp();
+            post_queued(valid, X, Y, id, s_o, sv, rb, rc, ctl, keys, vals, tally);
+            tally.fold();
         }
         if (gwarp == 0) {   // the unaligned head point and the ragged tail
             const long long ranges[2][2] = {{0, head}, {head + ntiles * kWarpTilePts, n}};

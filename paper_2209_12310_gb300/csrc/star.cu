@@ -51,20 +51,33 @@ __device__ __forceinline__ void star_tile_pass(const float4* __restrict__ p4, lo
         float4 v[kHalf];
 #pragma unroll
         for (int j = 0; j < kHalf; ++j) v[j] = ld_stream_f4(base + (j0 + j) * 32, pol);
+        // the keys of the points outside the sample octagon, then one load of
+        // each point's bin: only a point that beats the bin's current value
+        // issues the atomicMax (after a bin's first few points that is rare,
+        // so far fewer atomics meet at each bin)
+        unsigned long long key[2 * kHalf];
+        int bin[2 * kHalf];
 #pragma unroll
         for (int j = 0; j < kHalf; ++j) {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const float x = h ? v[j].z : v[j].x, y = h ? v[j].w : v[j].y;
                 const int X = __float2int_rn(x), Y = __float2int_rn(y);
-                if (pt_in_inner(X, Y, s_in) || pt_in_sample(x, y, s_edge)) continue;
+                const bool out = !pt_in_inner(X, Y, s_in) && !pt_in_sample(x, y, s_edge);
                 const int dx = X - cx, dy = Y - cy;
                 const unsigned long long d2 = (unsigned long long)((long long)dx * dx + (long long)dy * dy);
                 const unsigned idx = (unsigned)(head + t * kWarpTilePts + 2 * ((j0 + j) * 32 + lane) + h);
-                atomicMax(&bins[star_bin(dx, dy)], ((d2 >> 17) << 32) | idx);
-                ++nout;
+                key[2 * j + h] = out ? ((d2 >> 17) << 32) | idx : 0ull;
+                bin[2 * j + h] = star_bin(dx, dy);
+                nout += out ? 1u : 0u;
             }
         }
+        unsigned long long cur[2 * kHalf];
+#pragma unroll
+        for (int i = 0; i < 2 * kHalf; ++i) cur[i] = key[i] ? __ldcg(bins + bin[i]) : ~0ull;
+#pragma unroll
+        for (int i = 0; i < 2 * kHalf; ++i)
+            if (key[i] > cur[i]) atomicMax(&bins[bin[i]], key[i]);
     }
 }
 
@@ -127,6 +140,7 @@ __global__ void __launch_bounds__(kStarThreads, 8) star_kernel(const float* __re
     __shared__ unsigned s_pts, s_out;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int kWarps = kStarThreads / 32;
+    CH_TL(ctl, 7, 0);
     if (threadIdx.x == 0) {
         s_go = *(volatile int*)&ctl->samp_ok;
         s_pts = 0u;
@@ -184,6 +198,7 @@ __global__ void __launch_bounds__(kStarThreads, 8) star_kernel(const float* __re
         atomicAdd(&ctl->star_pts, s_pts);
         atomicAdd(&ctl->star_out, s_out);
     }
+    CH_TL(ctl, 7, 1);
     if (!last_block(&ctl->star_done, &s_last)) return;
     const unsigned tot_pts = *(volatile unsigned*)&ctl->star_pts;
     const unsigned tot_out = *(volatile unsigned*)&ctl->star_out;
@@ -192,12 +207,21 @@ __global__ void __launch_bounds__(kStarThreads, 8) star_kernel(const float* __re
     } else if (tot_out > 0u) {   // a few points were binned: clear the bins for the next call
         for (int b = threadIdx.x; b < kStarBins; b += kStarThreads) bins[b] = 0ull;
     }
+    CH_TL(ctl, 7, 1);
 }
 
 void launch_star(const float* pts, long long n, int head, long long ntiles, Ctl* ctl, void* bins, void* list,
                  int grid, cudaStream_t s) {
     star_kernel<<<grid, kStarThreads, 0, s>>>(pts, n, head, ntiles, ctl, (unsigned long long*)bins,
                                              (StarList*)list);
+}
+
+// The star pass shares SMs with the main pass: an SM that takes a star block
+// first must keep its shared memory at the maximum split, or the main pass's
+// blocks (91 KB each) cannot join it until the star block has left.
+cudaError_t configure_star_kernel() {
+    return cudaFuncSetAttribute(star_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared);
 }
 
 size_t star_bins_bytes() { return sizeof(unsigned long long) * kStarBins; }

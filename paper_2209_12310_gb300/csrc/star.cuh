@@ -36,14 +36,14 @@ struct StarList {
 //   v    vertices relative to c (|.| < 2^24: every orientation is exact in
 //        int64), counter-clockwise, the first two repeated after the last;
 //   tbl  per bin, the last vertex whose bin comes before it (K - 1 if none);
-//   rin  per bin, a lower bound on the squared distance from c to the line
-//        of every edge whose wedge meets the bin or its two neighbours on
-//        either side: a point of the bin closer to c than that is strictly
-//        inside (0 when no bound was found).
+//   rin  per bin, an integer radius no larger than the distance from c to
+//        the line of any edge whose wedge meets the bin or its two
+//        neighbours on either side: a point of the bin closer to c than that
+//        is strictly inside (0 when no bound was found).
 struct StarPoly {
     int2 v[kStarBins + 2];
     unsigned short tbl[kStarBins];
-    float rin[kStarBins];
+    unsigned rin[kStarBins];
 };
 
 // Angular bin of an offset (dx, dy) from c: a pseudo-angle in [0, 4) that
@@ -79,14 +79,52 @@ __device__ __forceinline__ bool star_inside_exact(int px, int py, int b, const S
     return spoke_ok && side > 0;
 }
 
-// Full test: first the bin's distance bound (one float compare; the bound
-// carries a margin larger than the rounding of both sides), then the exact
-// wedge test.
+// Fast test, exact in int64: true when p = c + (px, py) lies closer to c than
+// its bin's radius bound, hence strictly inside; false says nothing.
+__device__ __forceinline__ bool star_inside_fast(int px, int py, int b, const StarPoly& P) {
+    const long long r = (long long)P.rin[b];
+    return (long long)px * px + (long long)py * py < r * r;
+}
+
+// Full test: the bin's radius bound, then the exact wedge test.
 __device__ __forceinline__ bool star_inside(int px, int py, const StarPoly& P) {
     const int b = star_bin(px, py);
-    const float fx = (float)px, fy = (float)py;
-    if (fmaf(fy, fy, fx * fx) < P.rin[b]) return true;
-    return star_inside_exact(px, py, b, P);
+    return star_inside_fast(px, py, b, P) || star_inside_exact(px, py, b, P);
+}
+
+__device__ __forceinline__ float star_u128_to_float(unsigned __int128 x) {
+    return (float)(unsigned long long)(x >> 64) * 18446744073709551616.0f + (float)(unsigned long long)x;
+}
+
+// A radius r <= the distance from c to an edge line with orient(c, A, B) = o
+// and |B - A|^2 = l2 (0 < o < 2^50, 0 < l2 < 2^52; the distance is below
+// 2^25), at most 1 below floor(distance): floor(o^2 / l2) from a float
+// estimate corrected with exact 128-bit residues, then its integer square
+// root.  Every loop is bounded; leaving one early only lowers the result.
+__device__ __forceinline__ unsigned star_line_radius(long long o, long long l2) {
+    typedef unsigned __int128 u128;
+    const unsigned long long uo = (unsigned long long)o, ul = (unsigned long long)l2;
+    const u128 oo = (u128)uo * uo;
+    unsigned long long q = (unsigned long long)(((float)o * (float)o) / (float)l2);
+    for (int it = 0; it < 4; ++it) {   // the estimate is within about 2^28 of the quotient
+        const u128 ql = (u128)q * ul;
+        if (ql > oo) {
+            const unsigned long long back = (unsigned long long)(star_u128_to_float(ql - oo) / (float)ul) + 1ull;
+            q = q > back ? q - back : 0ull;
+        } else {
+            const unsigned long long fwd = (unsigned long long)(star_u128_to_float(oo - ql) / (float)ul);
+            if (fwd == 0ull) break;
+            q += fwd;
+        }
+    }
+    for (int it = 0; it < 64 && q > 0ull && (u128)q * ul > oo; ++it) --q;
+    if ((u128)q * ul > oo) return 0u;   // not settled: no bound
+    for (int it = 0; it < 64 && (u128)(q + 1ull) * ul <= oo; ++it) ++q;
+    unsigned r = (unsigned)sqrtf((float)q);
+    for (int it = 0; it < 16 && r > 0u && (unsigned long long)r * r > q; ++it) --r;
+    if ((unsigned long long)r * r > q) return 0u;
+    for (int it = 0; it < 16 && (unsigned long long)(r + 1u) * (r + 1u) <= q; ++it) ++r;
+    return r;
 }
 
 // Block-wide exclusive scan of one count per thread (warp shuffles, then the
@@ -116,7 +154,7 @@ __device__ __forceinline__ int star_scan(int c, unsigned* s, int* total) {
     return (int)(before + incl - (unsigned)c);
 }
 
-constexpr int kStarSweeps = 8;   // reflex-removal sweeps (alternately even and odd positions)
+constexpr int kStarSweeps = 4;   // reflex-removal sweeps (alternately even and odd positions)
 
 // Finishes the polygon from the gathered list (K vertices) in shared memory,
 // all T threads of the block: work area A (va, ba) and the polygon P, whose
@@ -209,23 +247,29 @@ __device__ bool star_finish(const StarList* __restrict__ list, int K, int2* va, 
         for (int b = b0 + 1; b <= b1; ++b) P.tbl[b & (kStarBins - 1)] = (unsigned short)j;
     }
     __syncthreads();
+    // each edge's line radius (work area A is free again), then per bin the
+    // smallest over the edges whose wedges can hold its points: from the last
+    // vertex before bin b - 2 to the first vertex from bin b + 2 on
+    unsigned* er = reinterpret_cast<unsigned*>(va);
+    for (int e = t; e < K; e += T) {
+        const int2 a = P.v[e], c2 = P.v[e + 1];
+        const long long o = (long long)a.x * c2.y - (long long)a.y * c2.x;   // > 0 (checked above)
+        const long long dx = (long long)c2.x - a.x, dy = (long long)c2.y - a.y;
+        er[e] = star_line_radius(o, dx * dx + dy * dy);
+    }
+    __syncthreads();
     for (int b = t; b < kStarBins; b += T) {
-        const int first = P.tbl[(b - 2) & (kStarBins - 1)];
-        const int last = P.tbl[(b + 2) & (kStarBins - 1)] + 1;   // an edge index in [1, K]
-        float m = 3.0e38f;
-        int e = first, steps = 0;
-        for (;;) {
-            const int2 a = P.v[e], c2 = P.v[e + 1];
-            const long long o = (long long)a.x * c2.y - (long long)a.y * c2.x;   // orient(c, V_e, V_e+1) > 0
-            const long long dx = (long long)c2.x - a.x, dy = (long long)c2.y - a.y;
-            const float of = (float)o, lf = (float)(dx * dx + dy * dy);
-            m = fminf(m, of * of / lf);
-            if ((e % K) == (last % K) || ++steps > 8) break;
+        int e = P.tbl[(b - 2) & (kStarBins - 1)];
+        int last = P.tbl[(b + 2) & (kStarBins - 1)] + 1;
+        if (last == K) last = 0;
+        unsigned m = er[e];
+        int steps = 0;
+        while (e != last && steps < 8) {
             e = e + 1 == K ? 0 : e + 1;
+            m = min(m, er[e]);
+            ++steps;
         }
-        // squared distances of edges [first, last] in float: within 5 roundings
-        // of 2^-24 of the exact values; the bound keeps a margin of 2^-18
-        P.rin[b] = steps > 8 ? 0.0f : m * (1.0f - 3.814697265625e-6f);
+        P.rin[b] = e == last ? m : 0u;   // a window longer than 8 edges gets no bound
     }
     __syncthreads();
     return true;
