@@ -73,9 +73,8 @@ Layout make_layout(long long n) {
     L.off_ctl = take(sizeof(Ctl));
     L.off_status = take(8 * (size_t)kDigits * L.sort_tiles);
     L.off_counters = take(4 * (size_t)kMaxLevels * L.ctcap);
-    L.off_star_bins = take(star_bins_bytes());   // the star pass leaves them at zero
+    L.off_star_bins = take(star_bins_bytes());   // the star and post passes leave them at zero
     L.zero_bytes = o;
-    L.off_star_list = take(star_list_bytes());
     L.off_kA = take(4 * (size_t)L.cap);
     L.off_kB = take(4 * (size_t)L.cap);
     L.off_vA = take(8 * (size_t)L.cap);
@@ -294,7 +293,7 @@ struct HullLaunch {
     // when the input is too small for it
     cudaStream_t side;
     cudaEvent_t ev_fork, ev_join;
-    void *star_bins, *star_list;
+    void* star_bins;
 };
 
 // Inputs below this many warp tiles skip the star pass.
@@ -313,7 +312,6 @@ static int hull_setup(const float* pts, long long n, int dev, cudaStream_t owner
     h->head = (((uintptr_t)pts & 15u) != 0u && n > 0) ? 1 : 0;
     h->ntiles = (n - h->head) / kWarpTilePts;
     h->star_bins = base + L.off_star_bins;
-    h->star_list = base + L.off_star_list;
     h->side = nullptr;
     h->ev_fork = h->ev_join = nullptr;
     if (h->ntiles >= kStarMinTiles && !get_side(dev, owner, &h->side, &h->ev_fork, &h->ev_join)) h->side = nullptr;
@@ -345,7 +343,7 @@ static void enqueue_filter_part(const float* pts, long long n, int32_t* out_idx,
         cudaStreamWaitEvent(h.side, h.ev_fork, 0);
         {
             ProfScope p("star", h.side);
-            launch_star(pts, n, h.head, h.ntiles, h.ctl, h.star_bins, h.star_list, h.di.sms, h.side);
+            launch_star(pts, n, h.head, h.ntiles, h.ctl, h.star_bins, h.di.sms, h.side);
         }
         cudaEventRecord(h.ev_join, h.side);
         cudaStreamWaitEvent(s, h.ev_join, 0);
@@ -353,7 +351,7 @@ static void enqueue_filter_part(const float* pts, long long n, int32_t* out_idx,
     {
         ProfScope p("post", s);
         launch_post(pts, n, h.head, h.ntiles, h.ctl, raw_xy, raw_idx, h.kA, h.vA, out_idx, out_n,
-                    star ? h.star_list : nullptr, cond, h.di.sms * h.di.occ_post, s);
+                    star ? h.star_bins : nullptr, cond, h.di.sms * h.di.occ_post, s);
     }
 }
 

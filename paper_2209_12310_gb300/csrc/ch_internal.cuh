@@ -66,7 +66,7 @@ constexpr int kSampleTiles = 1024;            // warp tiles read by the sample p
 // Star polygon of dense data (star.cu): angular bins around the sample
 // octagon's centre, extra warp tiles read when the sample is dense.
 constexpr int kStarBins = 8192;
-constexpr int kStarExtraTiles = 3072;
+constexpr int kStarExtraTiles = 2048;
 constexpr int kMaxLevels = 32;
 
 // Warp tiles read by the sample pass: about 1/32 of the input, at most
@@ -137,9 +137,9 @@ struct Ctl {
     int bk_shift;                       // fine buckets per coarse group: 1 << bk_shift
     unsigned int bk_next;               // next bucket for a bk_hull warp
     int samp_ok;                        // oct_s holds this call's sample octagon
-    int star_ok;                        // the star pass gathered this call's vertex list (star.cu)
-    int star_k;                         // its vertices
-    int star_final;                     // the post pass finished and accepted the polygon
+    int star_ok;                        // the star pass found dense data: the post pass builds the polygon
+    int star_k;                         // the polygon's vertices (post pass)
+    int star_final;                     // the post pass built and accepted the polygon
     int star_cx, star_cy;               // its centre (vertices are stored relative to it)
     unsigned int star_pts, star_out;    // points the star pass read / found outside the sample octagon
     unsigned int star_done;             // last-arriver counter of the star pass

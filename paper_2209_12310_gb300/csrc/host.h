@@ -12,7 +12,7 @@ struct Layout {
     size_t off_ctl, off_kA, off_kB, off_vA, off_vB, off_status, zero_bytes;
     size_t off_cu, off_cv, off_ci, off_clen, off_counters;
     size_t off_bcount, off_bcur, off_bstart, off_bsum, off_blen, off_bu, off_bv, off_bi, total;
-    size_t off_star_bins, off_star_list;
+    size_t off_star_bins;
     long long cap, sort_tiles, ctcap, bmax;
 };
 

@@ -15,14 +15,13 @@ void launch_main(const float* pts, long long n, int head, long long ntiles, Ctl*
                  uint32_t* raw_idx, unsigned switch_at, uint32_t* keys, uint64_t* vals, int grid, cudaStream_t s);
 void launch_post(const float* pts, long long n, int head, long long ntiles, Ctl* ctl, const uint64_t* raw_xy,
                  const uint32_t* raw_idx, uint32_t* keys, uint64_t* vals, int32_t* out_idx, int64_t* out_n,
-                 const void* star_list, unsigned long long cond, int grid, cudaStream_t s);
+                 void* star_bins, unsigned long long cond, int grid, cudaStream_t s);
 void launch_labels(const float* pts, long long n, Ctl* ctl, uint8_t* labels, int grid, cudaStream_t s);
-// The star pass (star.cu): its bins and vertex list live in the workspace.
-void launch_star(const float* pts, long long n, int head, long long ntiles, Ctl* ctl, void* bins, void* list,
-                 int grid, cudaStream_t s);
+// The star pass (star.cu): its angular bins live in the workspace.
+void launch_star(const float* pts, long long n, int head, long long ntiles, Ctl* ctl, void* bins, int grid,
+                 cudaStream_t s);
 cudaError_t configure_star_kernel();
 size_t star_bins_bytes();
-size_t star_list_bytes();
 void launch_filter_output(const Ctl* ctl, long long n, int32_t* out_ext8, int64_t* out_counts4, cudaStream_t s);
 
 void launch_sort_hist(const uint32_t* keys, Ctl* ctl, int grid, cudaStream_t s);

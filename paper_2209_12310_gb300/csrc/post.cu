@@ -238,11 +238,11 @@ __global__ void __launch_bounds__(kPostThreads, 1) post_kernel(const float* __re
                                                                long long ntiles, Ctl* ctl, const uint64_t* raw_xy,
                                                                const uint32_t* raw_idx, uint32_t* keys,
                                                                uint64_t* vals, int32_t* out_idx, int64_t* out_n,
-                                                               const StarList* __restrict__ star,
+                                                               unsigned long long* star_bins,
                                                                unsigned long long cond) {
     extern __shared__ __align__(16) char dyn[];
     __shared__ Octagon s_o;
-    __shared__ int s_flag, s_mode, s_star, s_sk, s_scx, s_scy;
+    __shared__ int s_flag, s_mode, s_star, s_scx, s_scy;
     __shared__ unsigned s_nraw;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     CH_TL(ctl, 5, 0);
@@ -250,8 +250,7 @@ __global__ void __launch_bounds__(kPostThreads, 1) post_kernel(const float* __re
         s_flag = read_status(ctl);
         s_mode = *(volatile int*)&ctl->mode;
         s_nraw = *(volatile unsigned*)&ctl->count_raw;
-        s_star = star != nullptr && *(volatile int*)&ctl->star_ok;
-        s_sk = ctl->star_k;
+        s_star = star_bins != nullptr && *(volatile int*)&ctl->star_ok;
         s_scx = ctl->star_cx;
         s_scy = ctl->star_cy;
     }
@@ -259,6 +258,8 @@ __global__ void __launch_bounds__(kPostThreads, 1) post_kernel(const float* __re
     __syncthreads();
     if (s_flag != CH_OK) {   // data error or timeout of an earlier stage
         if (blockIdx.x == 0 && tid == 0) { *out_n = s_flag; ctl->done = 1; }
+        if (blockIdx.x == 0 && s_star)   // leave the star bins clear for the next call
+            for (int b = tid; b < kStarBins; b += blockDim.x) star_bins[b] = 0ull;
         return;
     }
     StarView sv{nullptr, s_scx, s_scy};
@@ -267,9 +268,13 @@ __global__ void __launch_bounds__(kPostThreads, 1) post_kernel(const float* __re
         int2* va = reinterpret_cast<int2*>(dyn + kRecBufOff);
         unsigned short* ba = reinterpret_cast<unsigned short*>(dyn + kRecBufOff + sizeof(int2) * kStarBins);
         CH_TL(ctl, 8, 0);
-        if (star_finish<kPostThreads>(star, s_sk, va, ba, *P)) sv.P = P;
+        const int k = star_finish<kPostThreads>(star_bins, pts, n, s_scx, s_scy, va, ba, *P);
+        if (k) sv.P = P;
         CH_TL(ctl, 8, 1);
-        if (blockIdx.x == 0 && tid == 0) ctl->star_final = sv.P ? 1 : 0;
+        if (blockIdx.x == 0 && tid == 0) {
+            ctl->star_final = k ? 1 : 0;
+            ctl->star_k = k;
+        }
         __syncthreads();
     }
     RecBuf& rb = reinterpret_cast<RecBuf*>(dyn + kRecBufOff)[warp];
@@ -390,6 +395,8 @@ __global__ void __launch_bounds__(kPostThreads, 1) post_kernel(const float* __re
     CH_TL(ctl, 5, 1);
     if (!last_block(&ctl->blocks_done[2], &s_flag)) return;
     CH_TL(ctl, 6, 0);
+    if (s_star)   // every block has built its polygon: clear the bins for the next call
+        for (int b = tid; b < kStarBins; b += blockDim.x) star_bins[b] = 0ull;
     post_last_block(pts, n, ctl, s_o, keys, vals, out_idx, out_n, dyn, cond);
     CH_TL(ctl, 6, 1);
 }
@@ -397,9 +404,9 @@ __global__ void __launch_bounds__(kPostThreads, 1) post_kernel(const float* __re
 // ---------------------------------------------------------------------------
 void launch_post(const float* pts, long long n, int head, long long ntiles, Ctl* ctl, const uint64_t* raw_xy,
                  const uint32_t* raw_idx, uint32_t* keys, uint64_t* vals, int32_t* out_idx, int64_t* out_n,
-                 const void* star_list, unsigned long long cond, int grid, cudaStream_t s) {
+                 void* star_bins, unsigned long long cond, int grid, cudaStream_t s) {
     post_kernel<<<grid, kPostThreads, kPostSmemBytes, s>>>(pts, n, head, ntiles, ctl, raw_xy, raw_idx, keys, vals,
-                                                          out_idx, out_n, (const StarList*)star_list, cond);
+                                                          out_idx, out_n, (unsigned long long*)star_bins, cond);
 }
 
 cudaError_t configure_post_kernel() {

@@ -1,4 +1,4 @@
-// star.cu -- the star pass: the vertex list of the star polygon (star.cuh).
+// star.cu -- the star pass: the angular bins of the star polygon (star.cuh).
 //
 // star_kernel runs on a branch of its own beside the main pass (it needs only
 // the sample octagon) and is small enough to share the SMs with it.  Each warp
@@ -7,17 +7,14 @@
 // points outside the sample octagon), kStarExtraTiles more tiles spread over
 // the input.  Every point outside the sample octagon goes to its angular bin
 // around the sample octagon's centre c, where a 64-bit atomicMax keeps the
-// point farthest from c (its squared distance, truncated, above its index).
+// point farthest from c (its squared distance, truncated, above its index);
+// a point first reads its bin and issues the atomic only if it beats it.
 //
 // The block that finishes last decides: when the points seen outside the
 // sample octagon are more than 1/32 of those read (the main pass's own
-// threshold for dense data), it re-reads each non-empty bin's point from the
-// input by its index (so every vertex is an input point of this call,
-// whatever the bins held), keeps it if it is a valid coordinate and falls in
-// that bin again, and writes the kept points in bin order (relative to c)
-// with their bins: the vertex list.  Each post-pass block finishes the
-// polygon from it (star_finish).  The bins are left at zero for the next
-// call; nothing here waits for another block.
+// threshold for dense data), it publishes c and the post pass builds the
+// polygon from the bins (star_finish) and clears them; otherwise it clears
+// the bins itself.  Nothing here waits for another block.
 #include "ch_internal.cuh"
 #include "launch.h"
 #include "octagon.cuh"
@@ -27,8 +24,6 @@
 namespace ch {
 
 constexpr int kStarThreads = 128;
-constexpr int kStarPer = kStarBins / kStarThreads;   // bins per thread of the gathering block
-constexpr int kStarBatch = 4;                        // independent loads in flight per thread
 
 // Warp tile of the star pass's k-th read: the sample pass's tiles first, then
 // the extra tiles, half a stride away from an even spread.
@@ -81,59 +76,8 @@ __device__ __forceinline__ void star_tile_pass(const float4* __restrict__ p4, lo
     }
 }
 
-// The gathering block (the last to finish): the vertex list of c = (cx, cy).
-__device__ void star_gather(const float* __restrict__ pts, long long n, Ctl* ctl, unsigned long long* bins,
-                            StarList* list, int cx, int cy) {
-    __shared__ unsigned s_scan[kStarThreads / 32];
-    __shared__ int s_K;
-    const int t = threadIdx.x;
-    unsigned long long kept = 0ull;   // bit i: bin t * kStarPer + i holds a vertex
-    for (int i0 = 0; i0 < kStarPer; i0 += kStarBatch) {
-        unsigned long long key[kStarBatch];
-#pragma unroll
-        for (int i = 0; i < kStarBatch; ++i) key[i] = __ldcg(bins + t * kStarPer + i0 + i);
-        float2 p[kStarBatch];
-#pragma unroll
-        for (int i = 0; i < kStarBatch; ++i) {
-            const long long idx = (long long)(unsigned)key[i];
-            p[i] = (key[i] != 0ull && idx < n) ? __ldcg(reinterpret_cast<const float2*>(pts) + idx)
-                                               : make_float2(-1.0f, -1.0f);
-        }
-#pragma unroll
-        for (int i = 0; i < kStarBatch; ++i) {
-            const int b = t * kStarPer + i0 + i;
-            if (key[i] != 0ull) bins[b] = 0ull;
-            const int X = __float2int_rn(p[i].x), Y = __float2int_rn(p[i].y);
-            const bool valid = __int2float_rn(X) == p[i].x && __int2float_rn(Y) == p[i].y &&
-                               ((unsigned)(X | Y) >> kCoordBits) == 0u;
-            if (key[i] != 0ull && valid && star_bin(X - cx, Y - cy) == b) {
-                kept |= 1ull << (i0 + i);
-                list->park[b] = make_int2(X - cx, Y - cy);
-            }
-        }
-    }
-    int off = star_scan<kStarThreads>(__popcll(kept), s_scan, &s_K);
-    for (int i = 0; i < kStarPer; ++i) {
-        if ((kept >> i) & 1ull) {
-            const int b = t * kStarPer + i;
-            list->v[off] = list->park[b];
-            list->b[off] = (unsigned short)b;
-            ++off;
-        }
-    }
-    __syncthreads();
-    if (t == 0) {
-        ctl->star_k = s_K;
-        ctl->star_cx = cx;
-        ctl->star_cy = cy;
-        __threadfence();
-        ctl->star_ok = 1;
-    }
-}
-
 __global__ void __launch_bounds__(kStarThreads, 8) star_kernel(const float* __restrict__ pts, long long n, int head,
-                                                               long long ntiles, Ctl* ctl, unsigned long long* bins,
-                                                               StarList* list) {
+                                                               long long ntiles, Ctl* ctl, unsigned long long* bins) {
     __shared__ int s_in[8];
     __shared__ float s_edge[24];
     __shared__ int s_go, s_cx, s_cy, s_last;
@@ -203,17 +147,21 @@ __global__ void __launch_bounds__(kStarThreads, 8) star_kernel(const float* __re
     const unsigned tot_pts = *(volatile unsigned*)&ctl->star_pts;
     const unsigned tot_out = *(volatile unsigned*)&ctl->star_out;
     if (tot_out * 32ull > (unsigned long long)tot_pts && tot_out >= 1024u) {
-        star_gather(pts, n, ctl, bins, list, s_cx, s_cy);
+        if (threadIdx.x == 0) {   // dense: the post pass builds the polygon (and clears the bins)
+            ctl->star_cx = s_cx;
+            ctl->star_cy = s_cy;
+            __threadfence();
+            ctl->star_ok = 1;
+        }
     } else if (tot_out > 0u) {   // a few points were binned: clear the bins for the next call
         for (int b = threadIdx.x; b < kStarBins; b += kStarThreads) bins[b] = 0ull;
     }
     CH_TL(ctl, 7, 1);
 }
 
-void launch_star(const float* pts, long long n, int head, long long ntiles, Ctl* ctl, void* bins, void* list,
-                 int grid, cudaStream_t s) {
-    star_kernel<<<grid, kStarThreads, 0, s>>>(pts, n, head, ntiles, ctl, (unsigned long long*)bins,
-                                             (StarList*)list);
+void launch_star(const float* pts, long long n, int head, long long ntiles, Ctl* ctl, void* bins, int grid,
+                 cudaStream_t s) {
+    star_kernel<<<grid, kStarThreads, 0, s>>>(pts, n, head, ntiles, ctl, (unsigned long long*)bins);
 }
 
 // The star pass shares SMs with the main pass: an SM that takes a star block
@@ -225,6 +173,5 @@ cudaError_t configure_star_kernel() {
 }
 
 size_t star_bins_bytes() { return sizeof(unsigned long long) * kStarBins; }
-size_t star_list_bytes() { return sizeof(StarList); }
 
 }  // namespace ch

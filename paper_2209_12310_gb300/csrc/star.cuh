@@ -5,10 +5,10 @@
 // every point.  A polygon with thousands of vertices that are input points
 // hugs the hull far closer.  It is built from a sample: around a centre c,
 // the sample is split into kStarBins angular bins and each bin keeps its point
-// farthest from c (star.cu gathers those points into a vertex list); every
-// post-pass block then finishes the polygon in shared memory (star_finish):
-// it drops some reflex vertices, which only enlarges it, checks it exactly,
-// and builds the lookup tables of the point tests.
+// farthest from c (star.cu); every post-pass block then builds the polygon
+// in shared memory (star_finish): it gathers the bins' points, drops some
+// reflex vertices, which only enlarges the polygon, checks it exactly, and
+// builds the lookup tables of the point tests.
 //
 // Why dropping points strictly inside it is exact: every vertex is an input
 // point, and the polygon is star-shaped around c with every wedge
@@ -23,14 +23,6 @@
 #include "ch_internal.cuh"
 
 namespace ch {
-
-// The gathered vertices (global memory, written by the star pass): relative
-// to c, in bin order, with their bins; their number is ctl->star_k.
-struct StarList {
-    int2 v[kStarBins];
-    unsigned short b[kStarBins];
-    int2 park[kStarBins];   // the star pass's scratch: each kept point by bin
-};
 
 // The finished polygon (shared memory of a post-pass block):
 //   v    vertices relative to c (|.| < 2^24: every orientation is exact in
@@ -156,10 +148,17 @@ __device__ __forceinline__ int star_scan(int c, unsigned* s, int* total) {
 
 constexpr int kStarSweeps = 4;   // reflex-removal sweeps (alternately even and odd positions)
 
-// Finishes the polygon from the gathered list (K vertices) in shared memory,
-// all T threads of the block: work area A (va, ba) and the polygon P, whose
-// first bytes double as work area B (vb, bb).  Returns true (the same in
-// every thread) when the polygon passed its checks and P is ready.
+// Builds the polygon in shared memory, all T threads of the block, from the
+// star pass's bins (bins[b]: the packed farthest point of bin b, or 0) around
+// c = (cx, cy): work area A (va, ba) and the polygon P, whose first bytes
+// double as work area B (vb, bb).  Returns the polygon's vertex count (the
+// same in every thread) when it passed its checks and P is ready, else 0;
+// leaves the bins as they are.
+//
+// Gather: each non-empty bin's point is re-read from the input by its index
+// (so every vertex is an input point of this call, whatever the bins held)
+// and kept if it is a valid coordinate and falls in that bin again; the kept
+// points, in bin order, are the vertices.
 //
 // Sweeps: a vertex at an even (then odd) position is dropped when it is
 // reflex or flat, orient(V_j-1, V_j, V_j+1) <= 0, and its neighbours still
@@ -167,9 +166,15 @@ constexpr int kStarSweeps = 4;   // reflex-removal sweeps (alternately even and 
 // vertices are never neighbours (with K odd, the last vertex sits out the
 // even sweeps), so every drop sees its neighbours unchanged.  Dropping a
 // reflex vertex adds the triangle (V_j-1, V_j, V_j+1) to the polygon.
+//
+// Threads own contiguous chunks of the vertex list (the compaction keeps the
+// order); each lane walks its chunk from a different start, so that the
+// lanes of a warp touch different shared-memory banks.
 template <int T>
-__device__ bool star_finish(const StarList* __restrict__ list, int K, int2* va, unsigned short* ba, StarPoly& P) {
-    static_assert(T % 32 == 0 && T <= 1024, "block size");
+__device__ int star_finish(const unsigned long long* __restrict__ bins, const float* __restrict__ pts, long long n,
+                            int cx, int cy, int2* va, unsigned short* ba, StarPoly& P) {
+    static_assert(T % 32 == 0 && T >= 256 && T <= 1024, "block size");
+    constexpr int kPer = kStarBins / T;   // bins per thread: at most 32
     static_assert(sizeof(StarPoly) >= sizeof(int2) * kStarBins + sizeof(unsigned short) * kStarBins,
                   "work area B fits in the polygon");
     int2* vb = P.v;
@@ -177,14 +182,48 @@ __device__ bool star_finish(const StarList* __restrict__ list, int K, int2* va, 
                                                            sizeof(int2) * kStarBins);
     __shared__ unsigned s_scan[T / 32];
     __shared__ int s_K, s_bad, s_cross;
-    const int t = threadIdx.x;
-    if (K < 3 || K > kStarBins) return false;
-    for (int i = t; i < K; i += T) {
-        va[i] = list->v[i];
-        ba[i] = list->b[i];
+    const int t = threadIdx.x, lane = t & 31;
+    if (t == 0) { s_bad = 0; s_cross = 0; }
+    // 1. gather: bins [t kPer, (t + 1) kPer), their points parked in B by bin
+    unsigned kept = 0u;
+    for (int i0 = 0; i0 < kPer; i0 += 8) {
+        unsigned long long key[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) key[i] = __ldcg(bins + t * kPer + i0 + i);
+        float2 p[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const long long idx = (long long)(unsigned)key[i];
+            p[i] = (key[i] != 0ull && idx < n) ? __ldcg(reinterpret_cast<const float2*>(pts) + idx)
+                                               : make_float2(-1.0f, -1.0f);
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int b = t * kPer + i0 + i;
+            const int X = __float2int_rn(p[i].x), Y = __float2int_rn(p[i].y);
+            const bool valid = key[i] != 0ull && __int2float_rn(X) == p[i].x && __int2float_rn(Y) == p[i].y &&
+                               ((unsigned)(X | Y) >> kCoordBits) == 0u;
+            if (valid && star_bin(X - cx, Y - cy) == b) {
+                kept |= 1u << (i0 + i);
+                vb[b] = make_int2(X - cx, Y - cy);
+            }
+        }
     }
-    if (t == 0) { s_K = K; s_bad = 0; s_cross = 0; }
+    {
+        const int off = star_scan<T>(__popc(kept), s_scan, &s_K);
+        const int rot = lane % kPer;
+        for (int i = 0; i < kPer; ++i) {
+            int jj = i + rot;
+            if (jj >= kPer) jj -= kPer;
+            if (!((kept >> jj) & 1u)) continue;
+            const int o = off + __popc(kept & ((1u << jj) - 1u));
+            va[o] = vb[t * kPer + jj];
+            ba[o] = (unsigned short)(t * kPer + jj);
+        }
+    }
     __syncthreads();
+    if (s_K < 3) return 0;
+    // 2. sweeps, A -> B -> A ...
     int2* src = va; int2* dst = vb;
     unsigned short* bsrc = ba; unsigned short* bdst = bb;
     int idle = 0;   // consecutive sweeps that dropped nothing
@@ -192,33 +231,38 @@ __device__ bool star_finish(const StarList* __restrict__ list, int K, int2* va, 
         const int k = s_K;
         if (k <= 3) break;
         const int par = sweep & 1;
-        const int chunk = (k + T - 1) / T;
-        const int lo = min(k, t * chunk), hi = min(k, lo + chunk);
-        unsigned keep = 0u;   // chunk <= kStarBins / T <= 32 for T >= 256
-        for (int j = lo; j < hi; ++j) {
+        const int chunk = (k + T - 1) / T;   // <= kPer
+        const int lo = min(k, t * chunk), hi = min(k, lo + chunk), len = hi - lo;
+        const int rot = len > 0 ? lane % len : 0;
+        unsigned keep = 0u;
+        for (int i = 0; i < len; ++i) {
+            int jj = i + rot;
+            if (jj >= len) jj -= len;
+            const int j = lo + jj;
             bool drop = (j & 1) == par && !((k & 1) && j == k - 1);
             if (drop) {
                 const int2 a = src[j == 0 ? k - 1 : j - 1], m = src[j], z = src[j + 1 == k ? 0 : j + 1];
                 const long long turn = (long long)(m.x - a.x) * (z.y - a.y) - (long long)(m.y - a.y) * (z.x - a.x);
                 drop = turn <= 0 && star_orient_c(a, z.x, z.y) > 0;
             }
-            if (!drop) keep |= 1u << (j - lo);
+            if (!drop) keep |= 1u << jj;
         }
         __syncthreads();   // every read of s_K and src of this sweep is done
-        int o = star_scan<T>(__popc(keep), s_scan, &s_K);
+        const int off = star_scan<T>(__popc(keep), s_scan, &s_K);
         idle = s_K == k ? idle + 1 : 0;
-        for (int j = lo; j < hi; ++j) {
-            if ((keep >> (j - lo)) & 1u) {
-                dst[o] = src[j];
-                bdst[o] = bsrc[j];
-                ++o;
-            }
+        for (int i = 0; i < len; ++i) {
+            int jj = i + rot;
+            if (jj >= len) jj -= len;
+            if (!((keep >> jj) & 1u)) continue;
+            const int o = off + __popc(keep & ((1u << jj) - 1u));
+            dst[o] = src[lo + jj];
+            bdst[o] = bsrc[lo + jj];
         }
         __syncthreads();
         int2* tv = src; src = dst; dst = tv;
         unsigned short* tb = bsrc; bsrc = bdst; bdst = tb;
     }
-    K = s_K;
+    int K = s_K;
     if (src != va) {   // the list must sit in A before P is written over B
         for (int i = t; i < K; i += T) {
             va[i] = vb[i];
@@ -226,8 +270,8 @@ __device__ bool star_finish(const StarList* __restrict__ list, int K, int2* va, 
         }
         __syncthreads();
     }
-    // checks: every wedge turns counter-clockwise by less than pi, and exactly
-    // one edge crosses the ray from c along +x (the wedges wind once)
+    // 3. checks: every wedge turns counter-clockwise by less than pi, and
+    // exactly one edge crosses the ray from c along +x (the wedges wind once)
     int bad = 0, cross = 0;
     for (int j = t; j < K; j += T) {
         const int2 a = va[j], b = va[j + 1 == K ? 0 : j + 1];
@@ -238,8 +282,8 @@ __device__ bool star_finish(const StarList* __restrict__ list, int K, int2* va, 
     if (cross) atomicAdd(&s_cross, cross);
     __syncthreads();
     const bool ok = K >= 3 && !s_bad && s_cross == 1;
-    if (!ok) return false;
-    // the polygon: vertices, then the bin table, then the distance bounds
+    if (!ok) return 0;
+    // 4. the polygon: vertices, the bin table, then the radius bounds
     for (int j = t; j < K + 2; j += T) P.v[j] = va[j < K ? j : j - K];
     for (int j = t; j < K; j += T) {
         const int b0 = ba[j];
@@ -272,7 +316,7 @@ __device__ bool star_finish(const StarList* __restrict__ list, int K, int2* va, 
         P.rin[b] = e == last ? m : 0u;   // a window longer than 8 edges gets no bound
     }
     __syncthreads();
-    return true;
+    return K;
 }
 
 }  // namespace ch
