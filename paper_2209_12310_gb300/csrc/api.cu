@@ -708,15 +708,15 @@ int ch_hull_counters(void* stream, int64_t* out, int cap) {
 
 #if defined(CH_TRACE) || defined(CH_TIMELINE)
 // Debug builds: the phase timeline of the most recent call on the first
-// workspace (%globaltimer ns; 10 phases, first start and last end of each).
-int ch_trace_timeline(unsigned long long* out20) {
+// workspace (%globaltimer ns; 14 phases, first start and last end of each).
+int ch_trace_timeline(unsigned long long* out28) {
     std::lock_guard<std::mutex> lk(g_mu);
     if (g_ws.empty() || !g_ws.begin()->second.base) return CH_EINVAL;
     Ctl c;
     if (cudaMemcpy(&c, g_ws.begin()->second.base, sizeof(Ctl), cudaMemcpyDeviceToHost) != cudaSuccess) return CH_ECUDA;
-    for (int i = 0; i < 10; ++i) {
-        out20[2 * i] = c.tl[i][0];
-        out20[2 * i + 1] = c.tl[i][1];
+    for (int i = 0; i < 14; ++i) {
+        out28[2 * i] = c.tl[i][0];
+        out28[2 * i + 1] = c.tl[i][1];
     }
     return CH_OK;
 }

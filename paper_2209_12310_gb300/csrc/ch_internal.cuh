@@ -146,7 +146,7 @@ struct Ctl {
     Octagon oct;                        // octagon of the true extremes
     Octagon oct_s;                      // octagon of a sample's extremes
 #if defined(CH_TRACE) || defined(CH_TIMELINE)
-    unsigned long long tl[10][2];       // debug builds: first start / last end per phase (%globaltimer)
+    unsigned long long tl[14][2];       // debug builds: first start / last end per phase (%globaltimer)
 #endif
 };
 

@@ -86,7 +86,7 @@ __global__ void init_kernel(Ctl* ctl, int mode) {
     unsigned* h = &ctl->digit_hist[0][0];
     for (int i = t; i < kSortPasses * kDigits; i += blockDim.x) h[i] = 0u;
 #if defined(CH_TRACE) || defined(CH_TIMELINE)
-    if (t < 10) { ctl->tl[t][0] = ~0ull; ctl->tl[t][1] = 0ull; }
+    if (t < 14) { ctl->tl[t][0] = ~0ull; ctl->tl[t][1] = 0ull; }
     __syncthreads();
     CH_TL(ctl, 0, 0);
     CH_TL(ctl, 0, 1);

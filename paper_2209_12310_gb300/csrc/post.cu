@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(kPostThreads, 1) post_kernel(const float* __re
         int2* va = reinterpret_cast<int2*>(dyn + kRecBufOff);
         unsigned short* ba = reinterpret_cast<unsigned short*>(dyn + kRecBufOff + sizeof(int2) * kStarBins);
         CH_TL(ctl, 8, 0);
-        const int k = star_finish<kPostThreads>(star_bins, pts, n, s_scx, s_scy, va, ba, *P);
+        const int k = star_finish<kPostThreads>(star_bins, pts, n, s_scx, s_scy, va, ba, *P, ctl);
         if (k) sv.P = P;
         CH_TL(ctl, 8, 1);
         if (blockIdx.x == 0 && tid == 0) {
@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(kPostThreads, 1) post_kernel(const float* __re
         // loads of the next kAhead steps in flight: a rolled loop keeps the
         // classification code small.  Steps run over this warp's tiles,
         // kLoadsPerLane float4 per tile.
-        constexpr int kAhead = 4;
+        constexpr int kAhead = 8;
         const unsigned total = (unsigned)ntiles * kLoadsPerLane;
         const unsigned sstep = nwarps * kLoadsPerLane;
         auto next_step = [&](unsigned st) {

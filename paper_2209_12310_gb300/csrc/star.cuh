@@ -84,39 +84,23 @@ __device__ __forceinline__ bool star_inside(int px, int py, const StarPoly& P) {
     return star_inside_fast(px, py, b, P) || star_inside_exact(px, py, b, P);
 }
 
-__device__ __forceinline__ float star_u128_to_float(unsigned __int128 x) {
-    return (float)(unsigned long long)(x >> 64) * 18446744073709551616.0f + (float)(unsigned long long)x;
-}
-
-// A radius r <= the distance from c to an edge line with orient(c, A, B) = o
-// and |B - A|^2 = l2 (0 < o < 2^50, 0 < l2 < 2^52; the distance is below
-// 2^25), at most 1 below floor(distance): floor(o^2 / l2) from a float
-// estimate corrected with exact 128-bit residues, then its integer square
-// root.  Every loop is bounded; leaving one early only lowers the result.
+// The largest integer r with r^2 <= o^2 / l2: the distance from c to an edge
+// line with orient(c, A, B) = o and |B - A|^2 = l2 (0 < o < 2^50,
+// 0 < l2 < 2^52; the distance is below 2^25), rounded down.  A float
+// estimate (four roundings of 2^-24 each: off by less than 8) less 8 is
+// raised step by step while (r + 1)^2 l2 <= o^2 holds in exact 128-bit
+// arithmetic.  Every loop is bounded; leaving one early only lowers the
+// result, and 0 means no bound.
 __device__ __forceinline__ unsigned star_line_radius(long long o, long long l2) {
     typedef unsigned __int128 u128;
-    const unsigned long long uo = (unsigned long long)o, ul = (unsigned long long)l2;
-    const u128 oo = (u128)uo * uo;
-    unsigned long long q = (unsigned long long)(((float)o * (float)o) / (float)l2);
-    for (int it = 0; it < 4; ++it) {   // the estimate is within about 2^28 of the quotient
-        const u128 ql = (u128)q * ul;
-        if (ql > oo) {
-            const unsigned long long back = (unsigned long long)(star_u128_to_float(ql - oo) / (float)ul) + 1ull;
-            q = q > back ? q - back : 0ull;
-        } else {
-            const unsigned long long fwd = (unsigned long long)(star_u128_to_float(oo - ql) / (float)ul);
-            if (fwd == 0ull) break;
-            q += fwd;
-        }
-    }
-    for (int it = 0; it < 64 && q > 0ull && (u128)q * ul > oo; ++it) --q;
-    if ((u128)q * ul > oo) return 0u;   // not settled: no bound
-    for (int it = 0; it < 64 && (u128)(q + 1ull) * ul <= oo; ++it) ++q;
-    unsigned r = (unsigned)sqrtf((float)q);
-    for (int it = 0; it < 16 && r > 0u && (unsigned long long)r * r > q; ++it) --r;
-    if ((unsigned long long)r * r > q) return 0u;
-    for (int it = 0; it < 16 && (unsigned long long)(r + 1u) * (r + 1u) <= q; ++it) ++r;
-    return r;
+    const unsigned long long ul = (unsigned long long)l2;
+    const u128 oo = (u128)(unsigned long long)o * (unsigned long long)o;
+    const float rf = (float)o / sqrtf((float)l2);
+    unsigned long long r = rf > 8.0f ? (unsigned long long)rf - 8ull : 0ull;
+    for (int it = 0; it < 8 && r > 0ull && (u128)(r * r) * ul > oo; ++it) --r;
+    if ((u128)(r * r) * ul > oo) return 0u;
+    for (int it = 0; it < 24 && (u128)((r + 1ull) * (r + 1ull)) * ul <= oo; ++it) ++r;
+    return (unsigned)r;
 }
 
 // Block-wide exclusive scan of one count per thread (warp shuffles, then the
@@ -172,7 +156,8 @@ constexpr int kStarSweeps = 4;   // reflex-removal sweeps (alternately even and 
 // lanes of a warp touch different shared-memory banks.
 template <int T>
 __device__ int star_finish(const unsigned long long* __restrict__ bins, const float* __restrict__ pts, long long n,
-                            int cx, int cy, int2* va, unsigned short* ba, StarPoly& P) {
+                            int cx, int cy, int2* va, unsigned short* ba, StarPoly& P, Ctl* ctl) {
+    (void)ctl;   // debug timeline only
     static_assert(T % 32 == 0 && T >= 256 && T <= 1024, "block size");
     constexpr int kPer = kStarBins / T;   // bins per thread: at most 32
     static_assert(sizeof(StarPoly) >= sizeof(int2) * kStarBins + sizeof(unsigned short) * kStarBins,
@@ -184,44 +169,44 @@ __device__ int star_finish(const unsigned long long* __restrict__ bins, const fl
     __shared__ int s_K, s_bad, s_cross;
     const int t = threadIdx.x, lane = t & 31;
     if (t == 0) { s_bad = 0; s_cross = 0; }
-    // 1. gather: bins [t kPer, (t + 1) kPer), their points parked in B by bin
+    // 1. gather: bins [t kPer, (t + 1) kPer); all their keys, then all their
+    // points, in flight at once
+    static_assert(kPer <= 16, "gather registers");
     unsigned kept = 0u;
-    for (int i0 = 0; i0 < kPer; i0 += 8) {
-        unsigned long long key[8];
+    int2 d[kPer];
+    {
+        unsigned long long key[kPer];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) key[i] = __ldcg(bins + t * kPer + i0 + i);
-        float2 p[8];
+        for (int i = 0; i < kPer; ++i) key[i] = __ldcg(bins + t * kPer + i);
+        float2 p[kPer];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
+        for (int i = 0; i < kPer; ++i) {
             const long long idx = (long long)(unsigned)key[i];
             p[i] = (key[i] != 0ull && idx < n) ? __ldcg(reinterpret_cast<const float2*>(pts) + idx)
                                                : make_float2(-1.0f, -1.0f);
         }
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int b = t * kPer + i0 + i;
+        for (int i = 0; i < kPer; ++i) {
+            const int b = t * kPer + i;
             const int X = __float2int_rn(p[i].x), Y = __float2int_rn(p[i].y);
             const bool valid = key[i] != 0ull && __int2float_rn(X) == p[i].x && __int2float_rn(Y) == p[i].y &&
                                ((unsigned)(X | Y) >> kCoordBits) == 0u;
-            if (valid && star_bin(X - cx, Y - cy) == b) {
-                kept |= 1u << (i0 + i);
-                vb[b] = make_int2(X - cx, Y - cy);
-            }
+            d[i] = make_int2(X - cx, Y - cy);
+            if (valid && star_bin(X - cx, Y - cy) == b) kept |= 1u << i;
         }
     }
     {
         const int off = star_scan<T>(__popc(kept), s_scan, &s_K);
-        const int rot = lane % kPer;
+#pragma unroll
         for (int i = 0; i < kPer; ++i) {
-            int jj = i + rot;
-            if (jj >= kPer) jj -= kPer;
-            if (!((kept >> jj) & 1u)) continue;
-            const int o = off + __popc(kept & ((1u << jj) - 1u));
-            va[o] = vb[t * kPer + jj];
-            ba[o] = (unsigned short)(t * kPer + jj);
+            if (!((kept >> i) & 1u)) continue;
+            const int o = off + __popc(kept & ((1u << i) - 1u));
+            va[o] = d[i];
+            ba[o] = (unsigned short)(t * kPer + i);
         }
     }
     __syncthreads();
+    CH_TL(ctl, 9, 1);
     if (s_K < 3) return 0;
     // 2. sweeps, A -> B -> A ...
     int2* src = va; int2* dst = vb;
@@ -262,6 +247,7 @@ __device__ int star_finish(const unsigned long long* __restrict__ bins, const fl
         int2* tv = src; src = dst; dst = tv;
         unsigned short* tb = bsrc; bsrc = bdst; bdst = tb;
     }
+    CH_TL(ctl, 10, 1);
     int K = s_K;
     if (src != va) {   // the list must sit in A before P is written over B
         for (int i = t; i < K; i += T) {
@@ -291,6 +277,7 @@ __device__ int star_finish(const unsigned long long* __restrict__ bins, const fl
         for (int b = b0 + 1; b <= b1; ++b) P.tbl[b & (kStarBins - 1)] = (unsigned short)j;
     }
     __syncthreads();
+    CH_TL(ctl, 11, 1);
     // each edge's line radius (work area A is free again), then per bin the
     // smallest over the edges whose wedges can hold its points: from the last
     // vertex before bin b - 2 to the first vertex from bin b + 2 on
@@ -302,6 +289,7 @@ __device__ int star_finish(const unsigned long long* __restrict__ bins, const fl
         er[e] = star_line_radius(o, dx * dx + dy * dy);
     }
     __syncthreads();
+    CH_TL(ctl, 12, 1);
     for (int b = t; b < kStarBins; b += T) {
         int e = P.tbl[(b - 2) & (kStarBins - 1)];
         int last = P.tbl[(b + 2) & (kStarBins - 1)] + 1;
