@@ -263,11 +263,16 @@ int ch_profile_read(const char** names, int64_t* launches, double* total_ms, int
 
 /*
  * Serving (continuous batching).  A server owns a device memory pool of
- * budget_bytes on `device` and an engine thread with its own stream.
- * ch_submit copies the request (host points) in, without blocking; it returns
- * CH_OK with a ticket, or CH_EBUSY when the admission queue is full, or
- * CH_ENOMEM when the request can never fit the budget.  Requests that arrive
- * while others run are admitted as memory frees up and batched together.
+ * budget_bytes on `device` (its arena and the single-hull workspaces of its
+ * batch streams; each stream's batched workspace comes on top) and an engine
+ * thread with its own streams.  ch_submit queues the request without blocking
+ * and without copying it: it returns CH_OK with a ticket, or CH_EBUSY when
+ * the admission queue is full, or CH_ENOMEM when the request can never fit
+ * the budget.  The server copies the points to the device when the request
+ * is admitted into a batch (as memory frees up, together with the requests
+ * that arrived meanwhile), so the host buffer pts_host must stay valid and
+ * unchanged until ch_poll has answered for the ticket with anything but
+ * CH_PENDING; pinned host memory avoids a staging copy in the driver.
  * ch_poll returns CH_PENDING, or CH_OK after copying the h result indices to
  * out_idx_host (capacity cap) and setting *out_n (the request's ticket is
  * then retired), or a negative status (CH_EINVAL for an unknown ticket).

@@ -2,7 +2,9 @@
 //
 // A server owns one device arena carved from its memory budget, an engine
 // thread and kSlots (3) CUDA streams.  ch_submit only appends a request to the
-// admission queue (O(1), never touches the GPU).  The engine thread repeatedly
+// admission queue (O(1), never touches the GPU, never copies: the caller's
+// buffer is read when the request is admitted into a batch and must stay
+// valid until ch_poll answers for it).  The engine thread repeatedly
 //   1. retires finished batches (result counts first, then the index lists,
 //      both copied back asynchronously and observed through CUDA events),
 //   2. forms a new batch from the queue head while a free stream slot exists

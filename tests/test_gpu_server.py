@@ -112,3 +112,24 @@ def test_server_set_left_to_single_hull_path(lib):
             np.testing.assert_array_equal(res[t], oracle.hull(p))
     finally:
         lib.ch_server_destroy(srv)
+
+
+def test_submit_reads_the_buffer_until_poll_answers(lib):
+    """ch_submit does not copy: the buffer is read when the request joins a
+    batch.  Once ch_poll has answered, the caller may reuse the buffer: the
+    same buffer refilled with other points gives that set's hull."""
+    srv = lib.ch_server_create(1 << 30, 0)
+    try:
+        buf = np.ascontiguousarray(W.ring(200_000, 31))
+        first = buf.copy()
+        st, t = lib.ch_submit(srv, buf.ctypes.data, buf.shape[0])
+        assert st == lib.CH_OK
+        got1 = _wait(lib, srv, [t], {t: buf.shape[0]})[t]
+        buf[:] = W.normal(200_000, 32)   # reuse after the answer
+        st, t2 = lib.ch_submit(srv, buf.ctypes.data, buf.shape[0])
+        assert st == lib.CH_OK
+        got2 = _wait(lib, srv, [t2], {t2: buf.shape[0]})[t2]
+        np.testing.assert_array_equal(got1, oracle.hull(first))
+        np.testing.assert_array_equal(got2, oracle.hull(buf))
+    finally:
+        lib.ch_server_destroy(srv)
