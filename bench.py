@@ -542,6 +542,8 @@ def run_filters(ch, torch, args, pts, n, sp, peak):
     ext = torch.empty(16, dtype=torch.int32, device="cuda")
     out = {}
     for name, fn, passes in (("octagon", ch.ch_filter, {"main_filter": 8.0, "labels": 9.0}),
+                             ("octagon, two-kernel Manhattan extremes", ch.ch_filter_manhattan,
+                              {"manhattan_axis": 8.0, "manhattan_corner": 8.0, "labels": 9.0}),
                              ("16-gon", ch.ch_filter16, {"filter16_extremes": 8.0, "filter16_labels": 9.0})):
         def call():
             fn(pts.data_ptr(), n, ext.data_ptr(), labels.data_ptr(), counts.data_ptr(), sp)
@@ -572,7 +574,9 @@ def run_filters(ch, torch, args, pts, n, sp, peak):
                 per[k] = {"avg_ms": avg_ms, "achieved_gbs": gbs, "frac_of_measured_hbm": gbs / peak}
         out[name] = {"ms_per_call": ms, "points_per_s": n / (ms / 1e3), "kept": kept,
                      "kept_fraction": kept / max(n, 1), "passes": per}
-    out["note"] = ("labels + queue sizes of every point; octagon = ch_filter, 16-gon = ch_filter16 "
+    out["note"] = ("labels + queue sizes of every point; octagon = ch_filter (extremes fused in one pass), "
+                   "two-kernel Manhattan = ch_filter_manhattan (the paper's Sec. 3 form: axis extremes, then "
+                   "minimum Manhattan distance to the box corners), 16-gon = ch_filter16 "
                    f"(same input, {args.filter_steps} calls each, CUDA events)")
     return out
 

@@ -137,6 +137,20 @@ int ch_filter(const float* pts, int64_t n, int32_t* out_ext8, uint8_t* out_label
               int64_t* out_counts4, void* stream);
 
 /*
+ * ch_filter_manhattan -- ch_filter with the extremes found the way Sec. 3
+ * finds them: a first streaming kernel reduces the axis extremes (W, E, S,
+ * N, i.e. the bounding box), a second one the point of minimum Manhattan
+ * distance to each corner of that box (SW, SE, NE, NW); lowest index on
+ * ties.  Every point lies in the box, so those are the argmin / argmax of
+ * x + y and x - y that ch_filter takes in its single pass: the outputs are
+ * identical (same arguments, layouts and errors as ch_filter), but the input
+ * is read twice before the labels.  Kept to measure the fused pass against
+ * the paper's two-kernel form.
+ */
+int ch_filter_manhattan(const float* pts, int64_t n, int32_t* out_ext8, uint8_t* out_labels,
+                        int64_t* out_counts4, void* stream);
+
+/*
  * ch_filter16 -- ch_filter with a 16-direction polygon in place of the
  * octagon: the filter over a convex polygon of 16 extreme points that the
  * paper cites among related work (Sec. 2), with Alg. 2's rules.  The paper

@@ -38,6 +38,7 @@ SIGNATURES = {
     "ch_hull_batched": (_INT, [_P, _P, _I32, _P, _P, _P, _P]),
     "ch_filter": (_INT, [_P, _I64, _P, _P, _P, _P]),
     "ch_filter16": (_INT, [_P, _I64, _P, _P, _P, _P]),
+    "ch_filter_manhattan": (_INT, [_P, _I64, _P, _P, _P, _P]),
     "ch_hull_host": (_INT, [_P, _I64, _P, _P, _P]),
     "ch_hull_noalloc": (_INT, [_P, _I64, _P, _P, _P]),
     "ch_batched_config": (_INT, [_I64, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
@@ -117,6 +118,11 @@ def ch_batched_config(total_points, k):
 
 def ch_filter(pts, n, out_ext8, out_labels=None, out_counts4=None, stream=0):
     return _check(load().ch_filter(pts, n, out_ext8, out_labels, out_counts4, stream), "ch_filter")
+
+
+def ch_filter_manhattan(pts, n, out_ext8, out_labels=None, out_counts4=None, stream=0):
+    return _check(load().ch_filter_manhattan(pts, n, out_ext8, out_labels, out_counts4, stream),
+                  "ch_filter_manhattan")
 
 
 def ch_filter16(pts, n, out_ext16, out_labels=None, out_counts4=None, stream=0):
