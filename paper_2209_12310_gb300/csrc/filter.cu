@@ -653,6 +653,78 @@ __global__ void __launch_bounds__(256) labels_kernel(const float* __restrict__ p
     if (threadIdx.x < 4 && s_cnt[threadIdx.x]) atomicAdd(&ctl->counts4[threadIdx.x], s_cnt[threadIdx.x]);
 }
 
+// The same label array, 4 points per thread per step: two 16-byte loads and
+// one 32-bit store of 4 labels, when pts is 16-byte and labels 4-byte
+// aligned (the launcher checks).  The inner-region test settles most points
+// inline; only the others take the exact classifier.  The last n % 4 points
+// are labelled one per thread.
+constexpr int kLab4Unroll = 2;   // groups of 4 points in flight per thread
+
+__device__ __forceinline__ int label_of(float x, float y, const Octagon& o) {
+    const int X = __float2int_rn(x), Y = __float2int_rn(y);
+    return in_inner_strict(o, X, Y) ? -1 : classify_paper_slow(x, y, &o);
+}
+
+__global__ void __launch_bounds__(256) labels4_kernel(const float4* __restrict__ pts4, long long n, Ctl* ctl,
+                                                      uint32_t* labels4) {
+    __shared__ Octagon s_o;
+    __shared__ unsigned s_cnt[4];
+    if (read_status(ctl) != CH_OK) return;
+    copy_octagon(&s_o, &ctl->oct);
+    if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0u;
+    __syncthreads();
+    unsigned c[4] = {0u, 0u, 0u, 0u};
+    const long long groups = n >> 2;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const unsigned long long pol = l2_evict_first();
+    for (long long g0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; g0 < groups; g0 += stride * kLab4Unroll) {
+        float4 v[kLab4Unroll][2];
+#pragma unroll
+        for (int u = 0; u < kLab4Unroll; ++u) {
+            const long long g = g0 + u * stride;
+            if (g < groups) {
+                v[u][0] = ld_stream_f4(pts4 + 2 * g, pol);
+                v[u][1] = ld_stream_f4(pts4 + 2 * g + 1, pol);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kLab4Unroll; ++u) {
+            const long long g = g0 + u * stride;
+            if (g >= groups) continue;
+            const float xs[4] = {v[u][0].x, v[u][0].z, v[u][1].x, v[u][1].z};
+            const float ys[4] = {v[u][0].y, v[u][0].w, v[u][1].y, v[u][1].w};
+            uint32_t word = 0u;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int X = __float2int_rn(xs[k]), Y = __float2int_rn(ys[k]);
+                int r = -1;
+                if (!in_inner_strict(s_o, X, Y)) r = classify_paper_slow(xs[k], ys[k], &s_o);
+                word |= (uint32_t)(r + 1) << (8 * k);
+                c[0] += r == 0; c[1] += r == 1; c[2] += r == 2; c[3] += r == 3;
+            }
+            if (labels4) labels4[g] = word;
+        }
+    }
+    // the last n % 4 points
+    const long long tail = groups << 2;
+    if (blockIdx.x == 0 && threadIdx.x < (n & 3)) {
+        const long long i = tail + threadIdx.x;
+        const float2 p = reinterpret_cast<const float2*>(pts4)[i];
+        const int r = label_of(p.x, p.y, s_o);
+        if (labels4) reinterpret_cast<uint8_t*>(labels4)[i] = (uint8_t)(r + 1);
+        if (r >= 0) c[r]++;
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        unsigned v = c[r];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&s_cnt[r], v);
+    }
+    __syncthreads();
+    if (threadIdx.x < 4 && s_cnt[threadIdx.x]) atomicAdd(&ctl->counts4[threadIdx.x], s_cnt[threadIdx.x]);
+}
+
 __global__ void filter_output_kernel(const Ctl* ctl, long long n, int32_t* out_ext8, int64_t* out_counts4) {
     const int t = threadIdx.x;
     const int st = read_status(ctl);
@@ -674,7 +746,11 @@ void launch_main(const float* pts, long long n, int head, long long ntiles, Ctl*
 }
 
 void launch_labels(const float* pts, long long n, Ctl* ctl, uint8_t* labels, int grid, cudaStream_t s) {
-    labels_kernel<<<grid, 256, 0, s>>>(pts, n, ctl, labels);
+    if (((uintptr_t)pts & 15u) == 0u && ((uintptr_t)labels & 3u) == 0u)
+        labels4_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<const float4*>(pts), n, ctl,
+                                            reinterpret_cast<uint32_t*>(labels));
+    else
+        labels_kernel<<<grid, 256, 0, s>>>(pts, n, ctl, labels);
 }
 
 void launch_filter_output(const Ctl* ctl, long long n, int32_t* out_ext8, int64_t* out_counts4, cudaStream_t s) {
