@@ -658,7 +658,7 @@ __global__ void __launch_bounds__(256) labels_kernel(const float* __restrict__ p
 // aligned (the launcher checks).  The inner-region test settles most points
 // inline; only the others take the exact classifier.  The last n % 4 points
 // are labelled one per thread.
-constexpr int kLab4Unroll = 2;   // groups of 4 points in flight per thread
+constexpr int kLab4Unroll = 4;   // groups of 4 points in flight per thread
 
 __device__ __forceinline__ int label_of(float x, float y, const Octagon& o) {
     const int X = __float2int_rn(x), Y = __float2int_rn(y);
@@ -765,7 +765,10 @@ cudaError_t configure_filter_kernels() {
 
 cudaError_t occupancy_filter(int* main_k, int* labels) {
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(main_k, main_kernel, 256, kMainSmemBytes);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(labels, labels_kernel, 256, 0);
+    int a = 0, b = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, labels_kernel, 256, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, labels4_kernel, 256, 0);
+    *labels = a < b ? a : b;   // one grid size for both label kernels
     return e;
 }
 
