@@ -653,73 +653,78 @@ __global__ void __launch_bounds__(256) labels_kernel(const float* __restrict__ p
     if (threadIdx.x < 4 && s_cnt[threadIdx.x]) atomicAdd(&ctl->counts4[threadIdx.x], s_cnt[threadIdx.x]);
 }
 
-// The same label array, 4 points per thread per step: two 16-byte loads and
-// one 32-bit store of 4 labels, when pts is 16-byte and labels 4-byte
-// aligned (the launcher checks).  The inner-region test settles most points
-// inline; only the others take the exact classifier.  The last n % 4 points
-// are labelled one per thread.
-constexpr int kLab4Unroll = 4;   // groups of 4 points in flight per thread
-
+// The label of one point by the paper rule: -1 inside the octagon's inner
+// region or the octagon, else its queue.
 __device__ __forceinline__ int label_of(float x, float y, const Octagon& o) {
     const int X = __float2int_rn(x), Y = __float2int_rn(y);
     return in_inner_strict(o, X, Y) ? -1 : classify_paper_slow(x, y, &o);
 }
 
-__global__ void __launch_bounds__(256) labels4_kernel(const float4* __restrict__ pts4, long long n, Ctl* ctl,
-                                                      uint32_t* labels4) {
+// The label pass fed by bulk copies, for 16-byte aligned points and a 4-byte
+// aligned label array: each warp streams its warp tiles (512 points) through
+// a double-buffered shared-memory ring, as the main pass does, and labels 4
+// consecutive points per lane and round (one 32-bit store of 4 labels; a
+// tile is 4 rounds).  The ragged tail (fewer than 512 points) is labelled
+// point by point by the first warp.
+constexpr size_t kLabStreamSmemBytes = (size_t)8 * kStages * kWarpTileF4 * sizeof(float4);
+
+__global__ void __launch_bounds__(256) labels_stream_kernel(const float4* __restrict__ p4, long long n,
+                                                            long long ntiles, Ctl* ctl, uint32_t* labels4) {
+    extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ Octagon s_o;
     __shared__ unsigned s_cnt[4];
+    __shared__ unsigned long long s_bar[8][kStages];
     if (read_status(ctl) != CH_OK) return;
     copy_octagon(&s_o, &ctl->oct);
     if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0u;
     __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     unsigned c[4] = {0u, 0u, 0u, 0u};
-    const long long groups = n >> 2;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    const unsigned long long pol = l2_evict_first();
-    for (long long g0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; g0 < groups; g0 += stride * kLab4Unroll) {
-        float4 v[kLab4Unroll][2];
-#pragma unroll
-        for (int u = 0; u < kLab4Unroll; ++u) {
-            const long long g = g0 + u * stride;
-            if (g < groups) {
-                v[u][0] = ld_stream_f4(pts4 + 2 * g, pol);
-                v[u][1] = ld_stream_f4(pts4 + 2 * g + 1, pol);
-            }
+    WarpStream ws{reinterpret_cast<float4*>(dsm) + warp * kStages * kWarpTileF4, s_bar[warp], p4, gwarp, nwarps,
+                  ntiles, lane};
+    ws.start();
+    for (long long k = 0;; ++k) {
+        const long long t = gwarp + k * nwarps;
+        if (t >= ntiles) break;
+        const float4* cur = ws.acquire(k, ctl);
+        if (!cur) {   // a copy never completed: status is CH_ETIMEOUT
+            ws.drain(k);
+            break;
         }
 #pragma unroll
-        for (int u = 0; u < kLab4Unroll; ++u) {
-            const long long g = g0 + u * stride;
-            if (g >= groups) continue;
-            const float xs[4] = {v[u][0].x, v[u][0].z, v[u][1].x, v[u][1].z};
-            const float ys[4] = {v[u][0].y, v[u][0].w, v[u][1].y, v[u][1].w};
+        for (int r = 0; r < kWarpTilePts / 128; ++r) {
+            const int q = r * 32 + lane;   // 4 points: float4 2q and 2q + 1 of the tile
+            const float4 a = cur[2 * q], b = cur[2 * q + 1];
+            const float xs[4] = {a.x, a.z, b.x, b.z}, ys[4] = {a.y, a.w, b.y, b.w};
             uint32_t word = 0u;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int X = __float2int_rn(xs[k]), Y = __float2int_rn(ys[k]);
-                int r = -1;
-                if (!in_inner_strict(s_o, X, Y)) r = classify_paper_slow(xs[k], ys[k], &s_o);
-                word |= (uint32_t)(r + 1) << (8 * k);
-                c[0] += r == 0; c[1] += r == 1; c[2] += r == 2; c[3] += r == 3;
+            for (int m = 0; m < 4; ++m) {
+                const int X = __float2int_rn(xs[m]), Y = __float2int_rn(ys[m]);
+                int lab = -1;
+                if (!in_inner_strict(s_o, X, Y)) lab = classify_paper_slow(xs[m], ys[m], &s_o);
+                word |= (uint32_t)(lab + 1) << (8 * m);
+                c[0] += lab == 0; c[1] += lab == 1; c[2] += lab == 2; c[3] += lab == 3;
             }
-            if (labels4) labels4[g] = word;
+            if (labels4) labels4[t * (kWarpTilePts / 4) + q] = word;
         }
+        ws.release(k);
     }
-    // the last n % 4 points
-    const long long tail = groups << 2;
-    if (blockIdx.x == 0 && threadIdx.x < (n & 3)) {
-        const long long i = tail + threadIdx.x;
-        const float2 p = reinterpret_cast<const float2*>(pts4)[i];
-        const int r = label_of(p.x, p.y, s_o);
-        if (labels4) reinterpret_cast<uint8_t*>(labels4)[i] = (uint8_t)(r + 1);
-        if (r >= 0) c[r]++;
+    if (gwarp == 0) {   // the ragged tail
+        for (long long i = ntiles * kWarpTilePts + lane; i < n; i += 32) {
+            const float2 p = reinterpret_cast<const float2*>(p4)[i];
+            const int lab = label_of(p.x, p.y, s_o);
+            if (labels4) reinterpret_cast<uint8_t*>(labels4)[i] = (uint8_t)(lab + 1);
+            if (lab >= 0) c[lab]++;
+        }
     }
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
         unsigned v = c[r];
 #pragma unroll
         for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&s_cnt[r], v);
+        if (lane == 0 && v) atomicAdd(&s_cnt[r], v);
     }
     __syncthreads();
     if (threadIdx.x < 4 && s_cnt[threadIdx.x]) atomicAdd(&ctl->counts4[threadIdx.x], s_cnt[threadIdx.x]);
@@ -746,11 +751,13 @@ void launch_main(const float* pts, long long n, int head, long long ntiles, Ctl*
 }
 
 void launch_labels(const float* pts, long long n, Ctl* ctl, uint8_t* labels, int grid, cudaStream_t s) {
-    if (((uintptr_t)pts & 15u) == 0u && ((uintptr_t)labels & 3u) == 0u)
-        labels4_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<const float4*>(pts), n, ctl,
-                                            reinterpret_cast<uint32_t*>(labels));
-    else
+    if (((uintptr_t)pts & 15u) == 0u && ((uintptr_t)labels & 3u) == 0u) {
+        const long long ntiles = n / kWarpTilePts;
+        labels_stream_kernel<<<grid, 256, kLabStreamSmemBytes, s>>>(reinterpret_cast<const float4*>(pts), n, ntiles,
+                                                                    ctl, reinterpret_cast<uint32_t*>(labels));
+    } else {
         labels_kernel<<<grid, 256, 0, s>>>(pts, n, ctl, labels);
+    }
 }
 
 void launch_filter_output(const Ctl* ctl, long long n, int32_t* out_ext8, int64_t* out_counts4, cudaStream_t s) {
@@ -760,14 +767,19 @@ void launch_filter_output(const Ctl* ctl, long long n, int32_t* out_ext8, int64_
 long long sample_tiles_host(long long ntiles) { return sample_tiles(ntiles); }
 
 cudaError_t configure_filter_kernels() {
-    return cudaFuncSetAttribute(main_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMainSmemBytes);
+    cudaError_t e = cudaFuncSetAttribute(main_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMainSmemBytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(labels_stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kLabStreamSmemBytes);
+    return e;
 }
 
 cudaError_t occupancy_filter(int* main_k, int* labels) {
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(main_k, main_kernel, 256, kMainSmemBytes);
     int a = 0, b = 0;
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, labels_kernel, 256, 0);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, labels4_kernel, 256, 0);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, labels_stream_kernel, 256, kLabStreamSmemBytes);
     *labels = a < b ? a : b;   // one grid size for both label kernels
     return e;
 }

@@ -19,7 +19,8 @@
 // read), f16_output.  On 16-byte aligned input the extremes are tiled
 // (f16_extremes_tiled: min / max of 8 linear forms per warp tile, the
 // winning tile rescanned for the lowest index) and the labels take 4 points
-// per thread with the octagon's inner region as a fast path (f16_labels4);
+// per lane from a bulk-copy-fed shared-memory ring, with the octagon's inner
+// region as a fast path (f16_labels_stream);
 // otherwise per-point maxima (f16_extremes) and exact labels (f16_labels).
 // Everything is exact: |a x + b y| < 3 * 2^24 fits int32 and every
 // orientation product (< 2^48) int64.
@@ -83,11 +84,13 @@ __device__ __forceinline__ unsigned long long max_u64(unsigned long long a, unsi
     return a > b ? a : b;
 }
 
-__global__ void f16_init(F16Ctl* c) {
+// ctl: the stream workspace's control block, whose status and abort flag
+// the bounded waits of the streamed label pass use.
+__global__ void f16_init(F16Ctl* c, Ctl* ctl) {
     const int t = threadIdx.x;
     if (t < 16) { c->packed[t] = 0ull; c->tile_packed[t] = 0ull; }
     if (t < 4) c->counts[t] = 0u;
-    if (t == 0) { c->status = CH_OK; c->done = 0u; c->ready = 0; }
+    if (t == 0) { c->status = CH_OK; c->done = 0u; c->ready = 0; ctl->status = CH_OK; ctl->abort = 0; }
 }
 
 // ---------------------------------------------------------------------------
@@ -285,9 +288,12 @@ __global__ void __launch_bounds__(kF16Threads, 2) f16_extremes_tiled(const float
 }
 
 // The label pass on 16-byte aligned points with a 4-byte aligned label
-// array: 4 points per thread (two 16-byte loads, one 32-bit store), points
-// strictly inside the octagon's inner region settled inline (that octagon
-// lies inside the 16-gon), the others by the exact 16-edge test.
+// array, fed by bulk copies as ch_filter's: each warp streams its warp tiles
+// through a double-buffered shared-memory ring and labels 4 consecutive
+// points per lane and round (one 32-bit store).  Points strictly inside the
+// octagon's inner region are settled inline (that octagon lies inside the
+// 16-gon), the others by the exact 16-edge test; the ragged tail is labelled
+// point by point by the first warp.
 __device__ __forceinline__ int f16_label_exact(int X, int Y, const int* vx, const int* vy, const int* live,
                                                bool none) {
     bool inside = !none;
@@ -307,66 +313,70 @@ __device__ __forceinline__ int f16_label_exact(int X, int Y, const int* vx, cons
     return r;
 }
 
-constexpr int kF16LabUnroll = 4;
+constexpr size_t kF16StreamSmemBytes = (size_t)(kF16Threads / 32) * kStages * kWarpTileF4 * sizeof(float4);
 
-__global__ void __launch_bounds__(kF16Threads) f16_labels4(const float4* __restrict__ p4, long long n, F16Ctl* c,
-                                                           uint32_t* labels4) {
+__global__ void __launch_bounds__(kF16Threads) f16_labels_stream(const float4* __restrict__ p4, long long n,
+                                                                 long long ntiles, F16Ctl* c, Ctl* ctl,
+                                                                 uint32_t* labels4) {
+    extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ int s_vx[16], s_vy[16], s_live[16];
     __shared__ Octagon s_o;
     __shared__ unsigned s_cnt[4];
+    __shared__ unsigned long long s_bar[kF16Threads / 32][kStages];
     if (*(volatile int*)&c->status != CH_OK) return;
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     if (t < 16) { s_vx[t] = c->vx[t]; s_vy[t] = c->vy[t]; s_live[t] = c->live[t]; }
     if (t < 4) s_cnt[t] = 0u;
     copy_octagon(&s_o, &c->oct);
     __syncthreads();
     const bool none = c->none != 0;
+    const long long gwarp = ((long long)blockIdx.x * blockDim.x + t) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     unsigned cnt[4] = {0u, 0u, 0u, 0u};
-    const long long groups = n >> 2;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    const unsigned long long pol = l2_evict_first();
-    for (long long g0 = (long long)blockIdx.x * blockDim.x + t; g0 < groups; g0 += stride * kF16LabUnroll) {
-        float4 v[kF16LabUnroll][2];
-#pragma unroll
-        for (int u = 0; u < kF16LabUnroll; ++u) {
-            const long long g = g0 + u * stride;
-            if (g < groups) {
-                v[u][0] = ld_stream_f4(p4 + 2 * g, pol);
-                v[u][1] = ld_stream_f4(p4 + 2 * g + 1, pol);
-            }
+    WarpStream ws{reinterpret_cast<float4*>(dsm) + warp * kStages * kWarpTileF4, s_bar[warp], p4, gwarp, nwarps,
+                  ntiles, lane};
+    ws.start();
+    for (long long k = 0;; ++k) {
+        const long long tile = gwarp + k * nwarps;
+        if (tile >= ntiles) break;
+        const float4* cur = ws.acquire(k, ctl);
+        if (!cur) {   // a copy never completed: the workspace status is CH_ETIMEOUT
+            ws.drain(k);
+            break;
         }
 #pragma unroll
-        for (int u = 0; u < kF16LabUnroll; ++u) {
-            const long long g = g0 + u * stride;
-            if (g >= groups) continue;
-            const float xs[4] = {v[u][0].x, v[u][0].z, v[u][1].x, v[u][1].z};
-            const float ys[4] = {v[u][0].y, v[u][0].w, v[u][1].y, v[u][1].w};
+        for (int r = 0; r < kWarpTilePts / 128; ++r) {
+            const int q = r * 32 + lane;   // 4 points: float4 2q and 2q + 1 of the tile
+            const float4 a = cur[2 * q], b = cur[2 * q + 1];
+            const float xs[4] = {a.x, a.z, b.x, b.z}, ys[4] = {a.y, a.w, b.y, b.w};
             uint32_t word = 0u;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int X = __float2int_rn(xs[k]), Y = __float2int_rn(ys[k]);
-                int r = -1;
-                if (!in_inner_strict(s_o, X, Y)) r = f16_label_exact(X, Y, s_vx, s_vy, s_live, none);
-                word |= (uint32_t)(r + 1) << (8 * k);
-                if (r >= 0) cnt[r]++;
+            for (int m = 0; m < 4; ++m) {
+                const int X = __float2int_rn(xs[m]), Y = __float2int_rn(ys[m]);
+                int lab = -1;
+                if (!in_inner_strict(s_o, X, Y)) lab = f16_label_exact(X, Y, s_vx, s_vy, s_live, none);
+                word |= (uint32_t)(lab + 1) << (8 * m);
+                if (lab >= 0) cnt[lab]++;
             }
-            if (labels4) labels4[g] = word;
+            if (labels4) labels4[tile * (kWarpTilePts / 4) + q] = word;
+        }
+        ws.release(k);
+    }
+    if (gwarp == 0) {   // the ragged tail
+        for (long long i = ntiles * kWarpTilePts + lane; i < n; i += 32) {
+            const float2 p = reinterpret_cast<const float2*>(p4)[i];
+            const int X = __float2int_rn(p.x), Y = __float2int_rn(p.y);
+            const int lab = in_inner_strict(s_o, X, Y) ? -1 : f16_label_exact(X, Y, s_vx, s_vy, s_live, none);
+            if (labels4) reinterpret_cast<uint8_t*>(labels4)[i] = (uint8_t)(lab + 1);
+            if (lab >= 0) cnt[lab]++;
         }
     }
-    if (blockIdx.x == 0 && t < (n & 3)) {   // the last n % 4 points
-        const long long i = (groups << 2) + t;
-        const float2 p = reinterpret_cast<const float2*>(p4)[i];
-        const int X = __float2int_rn(p.x), Y = __float2int_rn(p.y);
-        const int r = in_inner_strict(s_o, X, Y) ? -1 : f16_label_exact(X, Y, s_vx, s_vy, s_live, none);
-        if (labels4) reinterpret_cast<uint8_t*>(labels4)[i] = (uint8_t)(r + 1);
-        if (r >= 0) cnt[r]++;
-    }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        unsigned v = cnt[q];
+    for (int qd = 0; qd < 4; ++qd) {
+        unsigned v = cnt[qd];
 #pragma unroll
         for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-        if ((t & 31) == 0 && v) atomicAdd(&s_cnt[q], v);
+        if (lane == 0 && v) atomicAdd(&s_cnt[qd], v);
     }
     __syncthreads();
     if (t < 4 && s_cnt[t]) atomicAdd(&c->counts[t], s_cnt[t]);
@@ -480,9 +490,9 @@ __global__ void __launch_bounds__(kF16Threads) f16_labels(const float2* __restri
     if (t < 4 && s_cnt[t]) atomicAdd(&c->counts[t], s_cnt[t]);
 }
 
-__global__ void f16_output(const F16Ctl* c, int32_t* out_ext16, int64_t* out_counts4) {
+__global__ void f16_output(const F16Ctl* c, const Ctl* ctl, int32_t* out_ext16, int64_t* out_counts4) {
     const int t = threadIdx.x;
-    const int st = c->status;
+    const int st = c->status != CH_OK ? c->status : ctl->status;
     if (t < 16) out_ext16[t] = st != CH_OK ? -1 : (int32_t)(0xFFFFFFFFu - (unsigned)(c->packed[t] & 0xFFFFFFFFull));
     if (t < 4 && out_counts4) out_counts4[t] = st != CH_OK ? (int64_t)st : (int64_t)c->counts[t];
 }
@@ -510,10 +520,22 @@ extern "C" int ch_filter16(const float* pts, int64_t n, int32_t* out_ext16, uint
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_e, f16_extremes, kF16Threads, 0) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_l, f16_labels, kF16Threads, 0) != cudaSuccess)
         return CH_ECUDA;
+    static bool s_configured = false;   // the streamed label pass's shared memory (idempotent)
+    if (!s_configured) {
+        if (cudaFuncSetAttribute(f16_labels_stream, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kF16StreamSmemBytes) != cudaSuccess)
+            return CH_ECUDA;
+        s_configured = true;
+    }
+    int occ_s = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_s, f16_labels_stream, kF16Threads, kF16StreamSmemBytes) !=
+        cudaSuccess)
+        return CH_ECUDA;
     char* base = nullptr;
     Layout L;
     if ((st = get_workspace(dev, s, n, &base, &L)) != CH_OK) return st;
     F16Ctl* c = reinterpret_cast<F16Ctl*>(base + L.off_cu);
+    Ctl* ctl = reinterpret_cast<Ctl*>(base + L.off_ctl);
     const float2* p2 = reinterpret_cast<const float2*>(pts);
     const long long blocks = (n + kF16Threads - 1) / kF16Threads;
     const int grid_e = (int)std::min<long long>(blocks, (long long)sms * std::max(1, occ_e));
@@ -522,7 +544,7 @@ extern "C" int ch_filter16(const float* pts, int64_t n, int32_t* out_ext16, uint
     // aligned label array, the 4-points-per-thread label pass
     const bool aligned = ((uintptr_t)pts & 15u) == 0u;
     const bool lab4 = aligned && ((uintptr_t)out_labels & 3u) == 0u;
-    f16_init<<<1, 32, 0, s>>>(c);
+    f16_init<<<1, 32, 0, s>>>(c, ctl);
     {
         ProfScope p("filter16_extremes", s);
         if (aligned) {
@@ -540,12 +562,14 @@ extern "C" int ch_filter16(const float* pts, int64_t n, int32_t* out_ext16, uint
     }
     if (out_labels || out_counts4) {
         ProfScope p("filter16_labels", s);
-        if (lab4)
-            f16_labels4<<<grid_l, kF16Threads, 0, s>>>(reinterpret_cast<const float4*>(pts), n, c,
-                                                      reinterpret_cast<uint32_t*>(out_labels));
-        else
+        if (lab4) {
+            const int grid_s = (int)std::min<long long>(blocks, (long long)sms * std::max(1, occ_s));
+            f16_labels_stream<<<grid_s, kF16Threads, kF16StreamSmemBytes, s>>>(
+                reinterpret_cast<const float4*>(pts), n, n / kWarpTilePts, c, ctl,
+                reinterpret_cast<uint32_t*>(out_labels));
+        } else
             f16_labels<<<grid_l, kF16Threads, 0, s>>>(p2, n, c, out_labels);
     }
-    f16_output<<<1, 32, 0, s>>>(c, out_ext16, out_counts4);
+    f16_output<<<1, 32, 0, s>>>(c, ctl, out_ext16, out_counts4);
     return cudaGetLastError() == cudaSuccess ? CH_OK : CH_ECUDA;
 }
