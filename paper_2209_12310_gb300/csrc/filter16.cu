@@ -294,8 +294,10 @@ __global__ void __launch_bounds__(kF16Threads, 2) f16_extremes_tiled(const float
 // octagon's inner region are settled inline (that octagon lies inside the
 // 16-gon), the others by the exact 16-edge test; the ragged tail is labelled
 // point by point by the first warp.
-__device__ __forceinline__ int f16_label_exact(int X, int Y, const int* vx, const int* vy, const int* live,
-                                               bool none) {
+// Out of line: the inner-region test settles most points, and the streaming
+// loop stays small.
+static __device__ __noinline__ int f16_label_exact(int X, int Y, const int* vx, const int* vy, const int* live,
+                                                   bool none) {
     bool inside = !none;
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
