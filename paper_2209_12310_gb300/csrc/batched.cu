@@ -7,14 +7,12 @@
 //   bt_init      per-set control blocks and tile counts;
 //   bt_scan      tile offsets (exclusive prefix over the sets, one block);
 //   bt_extremes  tiles: validation and the 8 extremes of each set as packed
-//                (key, lowest local index) maxima (Alg. 2, findExtremes), and
-//                the points outside each tile's own octagon ("raw");
+//                (key, lowest local index) maxima (Alg. 2, findExtremes);
 //   bt_octagon   one block per set: octagon, inner region, the chain end
 //                point records;
-//   bt_filter    tiles: the hull-rule classification of the raw points (or of
-//                every point of a dense tile) against its set's octagon,
-//                records compacted into the set's region (the loop of Alg.
-//                1/2), support-line end points reduced;
+//   bt_filter    tiles: the hull-rule classification of every point against
+//                its set's octagon, records compacted into the set's region
+//                (the loop of Alg. 1/2), support-line end points reduced;
 //   bt_hull      one block per set: the hull of its records (quickhull rounds
 //                and the stitch, as in the single hull's last block).
 // Sets whose records exceed what one block holds go through the bucketed
@@ -59,15 +57,7 @@ struct BArgs {
     int64_t* out_n;
     unsigned char* big;       // k: the set needs the single-hull path
     int tile;                 // points per tile (threads x points per thread of the tile kernels)
-    // raw survivors of each tile's own octagon (bt_extremes), in the tile's
-    // slot [region_base + tile start, ...) of these two arrays (free until the
-    // bucketed path), and their number per tile (kBtDense: the tile is read
-    // again whole by bt_filter)
-    uint64_t* raw_xy;
-    uint32_t* raw_idx;
-    unsigned* tile_cnt;
 };
-constexpr unsigned kBtDense = 0xFFFFFFFFu;
 
 __device__ __forceinline__ long long region_base(const BArgs& a, int i) { return a.offsets[i] + 16ll * i; }
 
@@ -153,27 +143,14 @@ __device__ __forceinline__ int bt_min3(int a, int b, int c) {
 // points per instruction), then the lowest index reaching each of them
 // (every thread checks its own points), and one packed (key, lowest index)
 // atomic per direction carries it to the set's maximum.
-//
-// The same pass filters the tile against the tile's own octagon: its 8
-// extreme points are input points of the set, so a point strictly inside
-// that octagon is strictly inside the set's hull (no hull vertex, whatever
-// the set's octagon turns out to be).  Points a conservative float test
-// (every edge function above kEdgeTol) puts strictly inside are dropped; the
-// others are written, compacted, to the tile's slot of raw_xy / raw_idx, for
-// bt_filter to classify against the set's octagon.  A tile where more than a
-// quarter of the points remain (data near a circle) writes nothing and is
-// marked kBtDense: bt_filter reads its points again.
 template <int T, int P>
 __global__ void __launch_bounds__(T) bt_extremes(BArgs a, int ntiles) {
-    static_assert(P % 2 == 0 && T % 32 == 0 && P <= 32, "tile shape");
+    static_assert(P % 2 == 0 && T % 32 == 0, "tile shape");
     constexpr int kBTile = T * P;
     __shared__ int s_key[T / 32][8];
     __shared__ int s_best[8];
     __shared__ unsigned s_idx[8];
     __shared__ int s_set;
-    __shared__ int s_tvx[8], s_tvy[8], s_tnone;
-    __shared__ float s_te[24];
-    __shared__ unsigned s_wsum[T / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         if (tid == 0) s_set = tile_set(a, t);
@@ -254,76 +231,6 @@ __global__ void __launch_bounds__(T) bt_extremes(BArgs a, int ntiles) {
             const unsigned hk = bt_dir_is_max(d) ? (unsigned)s_best[d] : 0xFFFFFFFFu - (unsigned)s_best[d];
             const unsigned long long pk = ((unsigned long long)hk << 32) | (unsigned long long)(0xFFFFFFFFu - s_idx[d]);
             atomicMax(&a.ctl[i].ext_packed[d], pk);
-        }
-        // the tile's octagon: the threads holding its 8 extreme points publish them
-#pragma unroll
-        for (int j = 0; j < P; ++j) {
-            const int q = tid + j * T;
-            const unsigned gi = (unsigned)(p0 + q);
-#pragma unroll
-            for (int d = 0; d < 8; ++d)
-                if (q < cnt && gi == s_idx[d]) {
-                    s_tvx[d] = __float2int_rn(v[j].x);
-                    s_tvy[d] = __float2int_rn(v[j].y);
-                }
-        }
-        __syncthreads();
-        if (tid < 8) {
-            const int j = (tid + 1) & 7;
-            const Edge e = make_edge(s_tvx[tid], s_tvy[tid], s_tvx[j], s_tvy[j]);
-            s_te[3 * tid] = e.A;
-            s_te[3 * tid + 1] = e.B;
-            s_te[3 * tid + 2] = e.C;
-        }
-        if (tid == 0) {
-            long long area2 = 0;
-            for (int d = 0; d < 8; ++d) {
-                const int j = (d + 1) & 7;
-                area2 += (long long)s_tvx[d] * s_tvy[j] - (long long)s_tvx[j] * s_tvy[d];
-            }
-            s_tnone = area2 == 0;
-        }
-        __syncthreads();
-        unsigned keep = 0u;   // bit j: point j of this thread is a raw survivor
-#pragma unroll
-        for (int j = 0; j < P; ++j) {
-            const int q = tid + j * T;
-            if (q >= cnt) continue;
-            float m = kHugePositive;
-#pragma unroll
-            for (int e = 0; e < 8; ++e) m = fminf(m, fmaf(s_te[3 * e], v[j].x, fmaf(s_te[3 * e + 1], v[j].y, s_te[3 * e + 2])));
-            if (s_tnone || !(m > kEdgeTol)) keep |= 1u << j;
-        }
-        // block-wide exclusive scan of the survivors per thread
-        const unsigned mine = (unsigned)__popc(keep);
-        unsigned incl = mine;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned u = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-            if (lane >= o) incl += u;
-        }
-        if (lane == 31) s_wsum[warp] = incl;
-        __syncthreads();
-        unsigned before = 0u, total = 0u;
-#pragma unroll
-        for (int w = 0; w < T / 32; ++w) {
-            const unsigned x = s_wsum[w];
-            before += w < warp ? x : 0u;
-            total += x;
-        }
-        const bool dense = total * 4u > (unsigned)cnt;
-        if (tid == 0) a.tile_cnt[t] = dense ? kBtDense : total;
-        if (!dense && keep) {
-            const long long slot = region_base(a, i) + p0;
-            unsigned pos = before + incl - mine;
-#pragma unroll
-            for (int j = 0; j < P; ++j) {
-                if (!((keep >> j) & 1u)) continue;
-                const unsigned X = (unsigned)__float2int_rn(v[j].x), Y = (unsigned)__float2int_rn(v[j].y);
-                a.raw_xy[slot + pos] = ((unsigned long long)X << 32) | Y;
-                a.raw_idx[slot + pos] = (uint32_t)(p0 + tid + j * T);
-                ++pos;
-            }
         }
         __syncthreads();
     }
@@ -433,19 +340,28 @@ __global__ void __launch_bounds__(T) bt_filter(BArgs a, int ntiles) {
             const float2* p2 = reinterpret_cast<const float2*>(a.pts) + base;
             unsigned wcnt = 0u;                      // records staged in wb
             unsigned qn[4] = {0u, 0u, 0u, 0u};       // records per queue (lane 0)
-            // warp-collective: classify one point per lane (valid = false for none) and stage it
-            auto process = [&](bool valid, float fx, float fy, unsigned p) {
+            for (long long b0 = p0; b0 < p1; b0 += (long long)T * kB) {   // uniform trip counts
+                float2 pv[kB];
+#pragma unroll
+                for (int j = 0; j < kB; ++j) {
+                    const long long p = b0 + (long long)j * T + tid;
+                    if (p < p1) pv[j] = __ldcs(p2 + p);
+                }
+#pragma unroll 1
+                for (int j = 0; j < kB; ++j) {
+                const long long p = b0 + (long long)j * T + tid;
+                const bool valid = p < p1;
                 int r = -1, X = 0, Y = 0;
                 if (valid) {
-                    X = __float2int_rn(fx);
-                    Y = __float2int_rn(fy);
-                    r = classify_hull(fx, fy, s_o);
+                    X = __float2int_rn(pv[j].x);
+                    Y = __float2int_rn(pv[j].y);
+                    r = classify_hull(pv[j].x, pv[j].y, s_o);
                 }
                 bool keep = r >= 0;
-                if (!__any_sync(0xFFFFFFFFu, keep)) return;
-                if (reduce_on_line(s_o, keep, X, Y, p, c)) keep = false;
+                if (!__any_sync(0xFFFFFFFFu, keep)) continue;
+                if (reduce_on_line(s_o, keep, X, Y, (unsigned)p, c)) keep = false;
                 const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
-                if (!bal) return;
+                if (!bal) continue;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) qn[q] += __popc(__ballot_sync(0xFFFFFFFFu, keep && r == q));
                 if (wcnt + (unsigned)__popc(bal) > (unsigned)kBtWarpRecs) bt_flush(wb, wcnt, c, a.keys, a.vals, rb);
@@ -454,40 +370,10 @@ __global__ void __launch_bounds__(T) bt_filter(BArgs a, int ntiles) {
                     queue_frame(r, X, Y, u, v);
                     const unsigned pos = wcnt + __popc(bal & lanemask_lt());
                     wb.key[pos] = make_key(r, u);
-                    wb.val[pos] = make_val(v, p);
+                    wb.val[pos] = make_val(v, (uint32_t)p);
                 }
                 wcnt += __popc(bal);
                 __syncwarp();
-            };
-            const unsigned tc = a.tile_cnt[t];
-            if (tc == kBtDense) {   // the tile's points again
-                for (long long b0 = p0; b0 < p1; b0 += (long long)T * kB) {   // uniform trip counts
-                    float2 pv[kB];
-#pragma unroll
-                    for (int j = 0; j < kB; ++j) {
-                        const long long p = b0 + (long long)j * T + tid;
-                        if (p < p1) pv[j] = __ldcs(p2 + p);
-                    }
-#pragma unroll 1
-                    for (int j = 0; j < kB; ++j) {
-                        const long long p = b0 + (long long)j * T + tid;
-                        process(p < p1, pv[j].x, pv[j].y, (unsigned)p);
-                    }
-                }
-            } else {   // the survivors of the tile's own octagon
-                const long long slot = rb + p0;
-                for (unsigned b0 = 0; b0 < tc; b0 += T) {
-                    const unsigned j = b0 + tid;
-                    const bool valid = j < tc;
-                    float fx = 0.0f, fy = 0.0f;
-                    unsigned p = 0u;
-                    if (valid) {
-                        const unsigned long long xy = a.raw_xy[slot + j];
-                        fx = (float)(unsigned)(xy >> 32);
-                        fy = (float)(unsigned)(xy & 0xFFFFFFFFull);
-                        p = a.raw_idx[slot + j];
-                    }
-                    process(valid, fx, fy, p);
                 }
             }
             // the tile's records and queue counts (a tile never spans two sets)
@@ -615,7 +501,7 @@ static std::map<std::pair<int, cudaStream_t>, BWork> g_bws;
 static size_t bt_align(size_t x) { return (x + 255) / 256 * 256; }
 
 struct BLayout {
-    size_t ctl, keys, vals, tiles, tmap, tcnt, rmap, big, redo;
+    size_t ctl, keys, vals, tiles, tmap, rmap, big, redo;
     size_t seg_nb, seg_bbase, seg_lo, seg_scale, seg_tbase, rt_base, totals;
     size_t bcount, bcur, bstart, blen, bu, bv, bi, kP, vP, cu, cv, ci, clen, ctmap, counters;
     size_t zero_from, zero_to;   // bucket counters: cleared before each batch
@@ -642,7 +528,6 @@ static BLayout bt_layout(long long total, int k, long long big_pts, long long bi
     L.vals = take(sizeof(uint64_t) * (size_t)cap);
     L.tiles = take(sizeof(int) * ((size_t)k + 1));
     L.tmap = take(sizeof(int) * ((size_t)tiles + 1));
-    L.tcnt = take(sizeof(unsigned) * ((size_t)tiles + 1));
     L.rtcap = (unsigned)((big_pts + 16 * big_sets) / kBLTile + big_sets + 1);
     L.rmap = take(sizeof(int) * (size_t)L.rtcap);
     L.big = take((size_t)k);
@@ -1154,9 +1039,6 @@ int hull_batched_impl(const float* pts, const int64_t* offsets, int32_t k, int32
     a.out_idx = out_idx;
     a.out_n = out_n;
     a.big = (unsigned char*)(base + L.big);
-    a.raw_xy = (uint64_t*)(base + L.vP);
-    a.raw_idx = (uint32_t*)(base + L.kP);
-    a.tile_cnt = (unsigned*)(base + L.tcnt);
     BLArgs& b = c.b;
     b.pts = pts;
     b.offsets = offsets;
