@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 # the large-survivor part (8 bucket kernels, the sort's histogram and 3 passes,
 # which return at once on the bucketed path, and the chain merge) only when the
 # post pass raised its graph condition.
-FILTER_LAUNCHES = 4
+FILTER_LAUNCHES = 4   # init, sample, main, post (the star pass adds one on large inputs)
 LARGE_LAUNCHES = 13   # bk_prep, bk_hist, bk_bsum, bk_bstart, bk_items, bk_part1, bk_part2, bk_hull, sort_hist, 3 sort passes, chain
 L2_BYTES = 129 * 1024 * 1024
 HBM_NOMINAL_GBS = 7900.0   # GB300 HBM3e, nominal (context beside the measured copy bandwidth)
@@ -384,10 +384,12 @@ def run_ours(args):
     kernels["_region"] = f"{prof_steps} profiled steps after the timed region"
     for k, v in per_kernel.items():
         kernels[k].update({kk: v[kk] for kk in ("algorithmic_bytes", "achieved_gbs", "frac_of_measured_hbm")})
-    # Whether the large-survivor part does work on this input (its kernels
-    # only return at once otherwise): then a replayed step runs it too.
-    large = kernels.get("bk_hull", {}).get("avg_ms", 0.0) > 5 * kernels.get("bk_prep", {}).get("avg_ms", 1.0)
-    launches_per_step = FILTER_LAUNCHES + (LARGE_LAUNCHES if large else 0)
+    # Kernels of a replayed step: the filter part, the star pass on its side
+    # branch when the input has enough tiles for it, and the large-survivor
+    # part when the call's counters say it ran (its graph node is skipped
+    # otherwise).
+    large = counters.get("stage", 0) >= 1
+    launches_per_step = FILTER_LAUNCHES + (1 if "star" in prof else 0) + (LARGE_LAUNCHES if large else 0)
 
     step_bytes = sum(v["algorithmic_bytes"] for v in per_kernel.values())
     step_roof = {"algorithmic_bytes": step_bytes, "achieved_gbs": step_bytes / (ms / args.steps / 1e3) / 1e9,
