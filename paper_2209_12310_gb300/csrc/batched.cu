@@ -13,6 +13,11 @@
 //   bt_filter    tiles: the hull-rule classification of every point against
 //                its set's octagon, records compacted into the set's region
 //                (the loop of Alg. 1/2), support-line end points reduced;
+//   bt_hull_small  one block per set: the support-line records, then the
+//                hull of a set with few records in a small footprint;
+//   bt_star      sets with more records than one block holds: the star
+//                polygon of the set's records (star.cuh) drops the records
+//                strictly inside it (points near a circle, Table V);
 //   bt_hull      one block per set: the hull of its records (quickhull rounds
 //                and the stitch, as in the single hull's last block).
 // Sets whose records exceed what one block holds go through the bucketed
@@ -29,6 +34,7 @@
 #include "launch.h"
 #include "octagon.cuh"
 #include "records.cuh"
+#include "star.cuh"
 
 #include <algorithm>
 #include <cstdio>
@@ -57,7 +63,15 @@ struct BArgs {
     int64_t* out_n;
     unsigned char* big;       // k: the set needs the single-hull path
     int tile;                 // points per tile (threads x points per thread of the tile kernels)
+    unsigned* star_ctr;       // bt_star's work list: [0] sets from the front, [1] from the back, [2] taken
+    int* star_list;           // k entries
+    uint32_t* kP;             // the bucketed path's scatter buffer (set regions as keys / vals)
+    uint64_t* vP;
 };
+
+// Sets with more records than this go through bt_star first (the others of
+// its list come after them).
+constexpr unsigned kBStarHuge = 1u << 18;
 
 __device__ __forceinline__ long long region_base(const BArgs& a, int i) { return a.offsets[i] + 16ll * i; }
 
@@ -77,6 +91,7 @@ __global__ void bt_init(BArgs a) {
     c->count = 8u;
     c->done = 0;
     c->bk_state = 0;
+    c->star_k = 0;
     for (int q = 0; q < 4; ++q) {
         c->counts4[q] = 2u;   // the two chain end points of every queue
         c->blocks_done[q] = 0u;
@@ -84,6 +99,7 @@ __global__ void bt_init(BArgs a) {
     a.big[i] = 0;
     const long long ni = a.offsets[i + 1] - a.offsets[i];
     a.tile_base[i] = (int)((ni + a.tile - 1) / a.tile);
+    if (i == 0) a.star_ctr[0] = a.star_ctr[1] = a.star_ctr[2] = 0u;
 }
 
 // Exclusive prefix of the tile counts in place (one block of 1024 threads);
@@ -433,7 +449,13 @@ __global__ void __launch_bounds__(kBSmallThreads) bt_hull_small(BArgs a) {
         a.vals[rb + s_lpos[tid]] = s_lval[tid];
         atomicAdd(&c->counts4[s_lkey[tid] >> kKeyBits], 1u);
     }
-    if (total > (unsigned)kBSmallRec) return;   // bt_hull's
+    if (total > (unsigned)kBSmallRec) {   // bt_hull's, after bt_star's when one block cannot hold them
+        if (tid == 0 && total > (unsigned)kMidCap) {
+            if (total > kBStarHuge) a.star_list[atomicAdd(&a.star_ctr[0], 1u)] = i;
+            else a.star_list[a.k - 1 - (int)atomicAdd(&a.star_ctr[1], 1u)] = i;
+        }
+        return;
+    }
     __syncthreads();   // also makes this block's line records visible to it
     for (unsigned j = tid; j < total; j += blockDim.x) {
         const uint32_t k = __ldcg(a.keys + rb + j);
@@ -450,6 +472,192 @@ __global__ void __launch_bounds__(kBSmallThreads) bt_hull_small(BArgs a) {
     } else if (tid == 0) {
         a.big[i] = 1;   // too many chain vertices for the small footprint: the bucketed path
         c->done = 1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The star polygon of a set whose records one block cannot hold (points near
+// a circle, where the octagon keeps almost all of them).  One block per such
+// set, persistent over the list that bt_hull_small builds (the sets with
+// more than kBStarHuge records first):
+//   1. bins: the set's first kBStarBinRec records go to their angular bins
+//      around the centre of the octagon's box, in shared memory; each bin
+//      keeps its point farthest from the centre.  A set's records come in
+//      the order of its points, so these are a sample of them when the
+//      points are in random order; any other order only makes the polygon
+//      smaller;
+//   2. the polygon (star_finish, star.cuh): its vertices are re-read from
+//      the input by index and it is checked exactly; without one the set is
+//      left as it is;
+//   3. the records whose point is not strictly inside the polygon are
+//      copied to the set's region of the scatter buffer (free until the
+//      bucketed path), then back, with the per-queue counts recounted.
+// A point strictly inside the polygon is an interior point of the set's hull
+// (star.cuh), so the records left have the same hull.  The sets then take
+// bt_hull's one-block path, or the bucketed path when still too many.
+//
+// Each warp streams a contiguous range of the records with the loads of its
+// next step in flight while it works on the current one; no step waits for
+// the other warps.
+constexpr int kBStarThreads = 512;
+constexpr int kBStarU = 8;                    // records per lane and step
+constexpr unsigned kBStarBinRec = 1u << 19;   // records binned (64 per bin)
+constexpr size_t kBStarAOff = (sizeof(StarPoly) + 15) / 16 * 16;
+constexpr size_t kBStarSmem = kBStarAOff + (sizeof(int2) + sizeof(unsigned short)) * kStarBins;
+static_assert(sizeof(unsigned long long) * kStarBins <= (sizeof(int2) + sizeof(unsigned short)) * kStarBins,
+              "the bins fit in work area A");
+
+// One step of a warp: records [r, r + 32 kBStarU) of a range ending at hi,
+// record r + 32 u + lane in slot u.
+__device__ __forceinline__ void bt_star_load(const uint32_t* __restrict__ keys, const uint64_t* __restrict__ vals,
+                                             long long rb, unsigned r, unsigned hi, uint32_t (&kk)[kBStarU],
+                                             uint64_t (&vv)[kBStarU]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int u = 0; u < kBStarU; ++u) {
+        const unsigned j = r + 32u * u + lane;
+        kk[u] = j < hi ? __ldcg(keys + rb + j) : 0u;
+        vv[u] = j < hi ? __ldcg(vals + rb + j) : 0ull;
+    }
+}
+
+__device__ __forceinline__ void bt_record_xy(uint32_t k, uint64_t v, int& X, int& Y) {
+    frame_to_xy((int)(k >> kKeyBits), (int)(k & kKeyMask), (int)(v >> 31), X, Y);
+}
+
+__global__ void __launch_bounds__(kBStarThreads, 1) bt_star(BArgs a) {
+    extern __shared__ __align__(16) char dyn[];
+    StarPoly& P = *reinterpret_cast<StarPoly*>(dyn);
+    unsigned long long* bins = reinterpret_cast<unsigned long long*>(dyn + kBStarAOff);
+    int2* va = reinterpret_cast<int2*>(dyn + kBStarAOff);
+    unsigned short* ba = reinterpret_cast<unsigned short*>(dyn + kBStarAOff + sizeof(int2) * kStarBins);
+    constexpr int kWarps = kBStarThreads / 32;
+    constexpr unsigned kStep = 32u * kBStarU;
+    __shared__ unsigned s_kept, s_q[4];
+    __shared__ int s_set, s_cx, s_cy;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned n_front = a.star_ctr[0], n_back = a.star_ctr[1];
+    for (;;) {
+        if (tid == 0) {
+            const unsigned g = atomicAdd(&a.star_ctr[2], 1u);
+            s_set = g < n_front ? a.star_list[g]
+                                : (g - n_front < n_back ? a.star_list[a.k - 1 - (int)(g - n_front)] : -1);
+        }
+        __syncthreads();
+        const int i = s_set;
+        if (i < 0) return;
+        Ctl* c = a.ctl + i;
+        const long long base = a.offsets[i], ni = a.offsets[i + 1] - base;
+        const long long rb = region_base(a, i);
+        const unsigned m = c->count;
+        if (tid == 0) {
+            s_cx = (c->oct.vx[W] + c->oct.vx[E]) / 2;
+            s_cy = (c->oct.vy[S] + c->oct.vy[N]) / 2;
+            s_kept = 0u;
+        }
+        if (tid < 4) s_q[tid] = 0u;
+        for (int b = tid; b < kStarBins; b += kBStarThreads) bins[b] = 0ull;
+        __syncthreads();
+        const int cx = s_cx, cy = s_cy;
+        // 1. bins: warp w takes [w per, (w + 1) per) of the first mb records
+        {
+            const unsigned mb = min(m, kBStarBinRec);
+            const unsigned per = ((mb + kWarps - 1) / kWarps + kStep - 1) / kStep * kStep;
+            const unsigned lo = min(mb, warp * per), hi = min(mb, lo + per);
+            uint32_t kk[kBStarU];
+            uint64_t vv[kBStarU];
+            bt_star_load(a.keys, a.vals, rb, lo, hi, kk, vv);
+            for (unsigned r = lo; r < hi; r += kStep) {
+                uint32_t nk[kBStarU];
+                uint64_t nv[kBStarU];
+                bt_star_load(a.keys, a.vals, rb, r + kStep, hi, nk, nv);
+#pragma unroll
+                for (int u = 0; u < kBStarU; ++u) {
+                    if (r + 32u * u + lane >= hi) continue;
+                    int X, Y;
+                    bt_record_xy(kk[u], vv[u], X, Y);
+                    const int dx = X - cx, dy = Y - cy;
+                    const unsigned long long d2 = (unsigned long long)((long long)dx * dx + (long long)dy * dy);
+                    const unsigned long long key = ((d2 >> 17) << 32) | (vv[u] & 0x7FFFFFFFull);
+                    const int b = star_bin(dx, dy);
+                    if (key > bins[b]) atomicMax(&bins[b], key);
+                }
+#pragma unroll
+                for (int u = 0; u < kBStarU; ++u) {
+                    kk[u] = nk[u];
+                    vv[u] = nv[u];
+                }
+            }
+        }
+        __syncthreads();
+        // 2. the polygon
+        const int K = star_finish<kBStarThreads, true>(bins, a.pts + 2 * base, ni, cx, cy, va, ba, P, c);
+        if (tid == 0) c->star_k = K;
+        if (K == 0) {
+            __syncthreads();
+            continue;
+        }
+        // 3. the records not strictly inside go to the scatter buffer
+        unsigned t0 = 0u, t1 = 0u, t2 = 0u, t3 = 0u;   // kept per queue (lane counts)
+        {
+            const unsigned per = ((m + kWarps - 1) / kWarps + kStep - 1) / kStep * kStep;
+            const unsigned lo = min(m, warp * per), hi = min(m, lo + per);
+            uint32_t kk[kBStarU];
+            uint64_t vv[kBStarU];
+            bt_star_load(a.keys, a.vals, rb, lo, hi, kk, vv);
+            for (unsigned r = lo; r < hi; r += kStep) {
+                uint32_t nk[kBStarU];
+                uint64_t nv[kBStarU];
+                bt_star_load(a.keys, a.vals, rb, r + kStep, hi, nk, nv);
+#pragma unroll
+                for (int u = 0; u < kBStarU; ++u) {
+                    bool keep = r + 32u * u + lane < hi;
+                    if (keep) {
+                        int X, Y;
+                        bt_record_xy(kk[u], vv[u], X, Y);
+                        keep = !star_inside(X - cx, Y - cy, P);
+                    }
+                    const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
+                    if (bal == 0u) continue;
+                    unsigned pos = 0u;
+                    if (lane == 0) pos = atomicAdd(&s_kept, (unsigned)__popc(bal));
+                    pos = __shfl_sync(0xFFFFFFFFu, pos, 0) + (unsigned)__popc(bal & lanemask_lt());
+                    if (keep) {
+                        a.kP[rb + pos] = kk[u];
+                        a.vP[rb + pos] = vv[u];
+                        const unsigned q = kk[u] >> kKeyBits;
+                        t0 += q == 0u;
+                        t1 += q == 1u;
+                        t2 += q == 2u;
+                        t3 += q == 3u;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kBStarU; ++u) {
+                    kk[u] = nk[u];
+                    vv[u] = nv[u];
+                }
+            }
+        }
+        t0 = __reduce_add_sync(0xFFFFFFFFu, t0);
+        t1 = __reduce_add_sync(0xFFFFFFFFu, t1);
+        t2 = __reduce_add_sync(0xFFFFFFFFu, t2);
+        t3 = __reduce_add_sync(0xFFFFFFFFu, t3);
+        if (lane == 0) {
+            atomicAdd(&s_q[0], t0);
+            atomicAdd(&s_q[1], t1);
+            atomicAdd(&s_q[2], t2);
+            atomicAdd(&s_q[3], t3);
+        }
+        __syncthreads();
+        const unsigned w = s_kept;
+        for (unsigned j = tid; j < w; j += kBStarThreads) {   // back into the set's records
+            a.keys[rb + j] = __ldcg(a.kP + rb + j);
+            a.vals[rb + j] = __ldcg(a.vP + rb + j);
+        }
+        if (tid < 4) c->counts4[tid] = s_q[tid];
+        if (tid == 0) c->count = w;
+        __syncthreads();
     }
 }
 
@@ -501,7 +709,7 @@ static std::map<std::pair<int, cudaStream_t>, BWork> g_bws;
 static size_t bt_align(size_t x) { return (x + 255) / 256 * 256; }
 
 struct BLayout {
-    size_t ctl, keys, vals, tiles, tmap, rmap, big, redo;
+    size_t ctl, keys, vals, tiles, tmap, rmap, big, redo, star_ctr, star_list;
     size_t seg_nb, seg_bbase, seg_lo, seg_scale, seg_tbase, rt_base, totals;
     size_t bcount, bcur, bstart, blen, bu, bv, bi, kP, vP, cu, cv, ci, clen, ctmap, counters;
     size_t zero_from, zero_to;   // bucket counters: cleared before each batch
@@ -532,6 +740,8 @@ static BLayout bt_layout(long long total, int k, long long big_pts, long long bi
     L.rmap = take(sizeof(int) * (size_t)L.rtcap);
     L.big = take((size_t)k);
     L.redo = take((size_t)k);
+    L.star_ctr = take(4 * 4);
+    L.star_list = take(sizeof(int) * (size_t)k);
     L.seg_nb = take(4 * nseg);
     L.seg_bbase = take(4 * (nseg + 1));
     L.seg_lo = take(4 * nseg);
@@ -652,6 +862,8 @@ static int bt_configure(int dev, BtDevice* out) {
     d.sms = prop.multiProcessorCount;
     d.name = prop.name;
     if (cudaFuncSetAttribute(bt_hull, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBHullSmem) != cudaSuccess)
+        return CH_ECUDA;
+    if (cudaFuncSetAttribute(bt_star, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBStarSmem) != cudaSuccess)
         return CH_ECUDA;
     if (configure_batched_large() != cudaSuccess) return CH_ECUDA;
     bt_occupancy<128, 16>(d.occ[0]);
@@ -818,11 +1030,9 @@ static void bt_enqueue_tiles(const BtCall& c, cudaStream_t s) {
 
 static int bt_enqueue(const BtCall& c, unsigned char* redo, cudaStream_t s) {
     bt_enqueue_tiles(c, s);
-    {
-        ProfScope p("batched_hull", s);
-        bt_hull_small<<<c.a.k, kBSmallThreads, 0, s>>>(c.a);
-        bt_hull<<<c.a.k, kBHullThreads, kBHullSmem, s>>>(c.a);
-    }
+    { ProfScope p("batched_hull_small", s); bt_hull_small<<<c.a.k, kBSmallThreads, 0, s>>>(c.a); }
+    { ProfScope p("batched_star", s); bt_star<<<c.sms, kBStarThreads, kBStarSmem, s>>>(c.a); }
+    { ProfScope p("batched_hull", s); bt_hull<<<c.a.k, kBHullThreads, kBHullSmem, s>>>(c.a); }
     // Sets with more records than one block holds: all together through the
     // bucketed path.
     if (cudaMemsetAsync(c.base + c.L.zero_from, 0, c.L.zero_to - c.L.zero_from, s) != cudaSuccess) return CH_ECUDA;
@@ -1039,6 +1249,10 @@ int hull_batched_impl(const float* pts, const int64_t* offsets, int32_t k, int32
     a.out_idx = out_idx;
     a.out_n = out_n;
     a.big = (unsigned char*)(base + L.big);
+    a.star_ctr = (unsigned*)(base + L.star_ctr);
+    a.star_list = (int*)(base + L.star_list);
+    a.kP = (uint32_t*)(base + L.kP);
+    a.vP = (uint64_t*)(base + L.vP);
     BLArgs& b = c.b;
     b.pts = pts;
     b.offsets = offsets;

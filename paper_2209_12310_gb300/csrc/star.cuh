@@ -137,7 +137,9 @@ constexpr int kStarSweeps = 4;   // reflex-removal sweeps (alternately even and 
 // c = (cx, cy): work area A (va, ba) and the polygon P, whose first bytes
 // double as work area B (vb, bb).  Returns the polygon's vertex count (the
 // same in every thread) when it passed its checks and P is ready, else 0;
-// leaves the bins as they are.
+// leaves the bins as they are.  With kSharedBins the bins are in this
+// block's shared memory, and they may share their bytes with work area A:
+// every bin is read before the first write to A.
 //
 // Gather: each non-empty bin's point is re-read from the input by its index
 // (so every vertex is an input point of this call, whatever the bins held)
@@ -154,8 +156,8 @@ constexpr int kStarSweeps = 4;   // reflex-removal sweeps (alternately even and 
 // Threads own contiguous chunks of the vertex list (the compaction keeps the
 // order); each lane walks its chunk from a different start, so that the
 // lanes of a warp touch different shared-memory banks.
-template <int T>
-__device__ int star_finish(const unsigned long long* __restrict__ bins, const float* __restrict__ pts, long long n,
+template <int T, bool kSharedBins = false>
+__device__ int star_finish(const unsigned long long* bins, const float* __restrict__ pts, long long n,
                             int cx, int cy, int2* va, unsigned short* ba, StarPoly& P, Ctl* ctl) {
     (void)ctl;   // debug timeline only
     static_assert(T % 32 == 0 && T >= 256 && T <= 1024, "block size");
@@ -177,7 +179,7 @@ __device__ int star_finish(const unsigned long long* __restrict__ bins, const fl
     {
         unsigned long long key[kPer];
 #pragma unroll
-        for (int i = 0; i < kPer; ++i) key[i] = __ldcg(bins + t * kPer + i);
+        for (int i = 0; i < kPer; ++i) key[i] = kSharedBins ? bins[t * kPer + i] : __ldcg(bins + t * kPer + i);
         float2 p[kPer];
 #pragma unroll
         for (int i = 0; i < kPer; ++i) {
