@@ -29,12 +29,14 @@
 // in place from call to call and launched on the caller's stream.
 #include "batched_large.h"
 #include "ch_internal.cuh"
+#include "extremes.cuh"
 #include "host.h"
 #include "hullcore.cuh"
 #include "launch.h"
 #include "octagon.cuh"
 #include "records.cuh"
 #include "star.cuh"
+#include "tma.cuh"
 
 #include <algorithm>
 #include <cstdio>
@@ -48,7 +50,7 @@ namespace ch {
 
 constexpr int kBTileMin = 2048;        // smallest tile of the compiled shapes
 constexpr int kBHullThreads = 512;     // threads of bt_hull (a multiple of 128)
-constexpr int kBOctThreads = 64;       // threads of bt_octagon
+constexpr int kBOctThreads = 256;      // threads of bt_octagon: a warp per direction
 
 struct BArgs {
     const float* pts;
@@ -63,6 +65,10 @@ struct BArgs {
     int64_t* out_n;
     unsigned char* big;       // k: the set needs the single-hull path
     int tile;                 // points per tile (threads x points per thread of the tile kernels)
+    long long total;          // points of the batch
+    long long nwt;            // warp tiles of the streamed body (bt_extremes)
+    int head;                 // points before the body's first 16-byte boundary (0 or 1)
+    int wtile;                // points per warp tile of bt_extremes (32 x points per lane)
     unsigned* star_ctr;       // bt_star's work list: [0] sets from the front, [1] from the back, [2] taken
     int* star_list;           // k entries
     uint32_t* kP;             // the bucketed path's scatter buffer (set regions as keys / vals)
@@ -129,138 +135,190 @@ __global__ void __launch_bounds__(1024) bt_scan(int* tile_base, int* tile_map, i
     if (tid == 1023) tile_base[k] = s_part[1023];
 }
 
-__device__ __forceinline__ bool bt_dir_is_max(int d) { return d >= SE && d <= N; }
+// ---------------------------------------------------------------------------
+// Extremes of every set, streamed (findExtremes, Alg. 2).  The batch's points
+// are one array; its 16-byte aligned body is cut into warp tiles of 32 P
+// points (P per lane), whatever the sets.  Each block takes a contiguous
+// chunk of warp tiles and its warps take the chunk's tiles in turn, so they
+// move through the same sets together; each warp streams its tiles through a
+// double-buffered shared-memory ring filled by bulk copies.  A tile inside
+// one set goes through the single hull's per-lane tracking (extremes.cuh:
+// three-input min / max of the keys, the first tile code reaching each
+// extreme); when the set changes, the warp folds its lanes and raises the
+// set's packed (key, ~tile code) maxima.  A tile that meets a set boundary
+// is folded set by set.  The unaligned head point and the ragged tail go
+// point by point.  bt_octagon then rescans each set's winning tiles for the
+// lowest index.
+// Tile codes: 0 = head, t + 1 = body tile t, nwt + 1 = tail.
 
-__device__ __forceinline__ int bt_key(int d, int X, int Y) {
-    switch (d) {
-        case W: case E: return X;
-        case S: case N: return Y;
-        case SW: case NE: return X + Y;
-        default: return X - Y + kCoordLimit;
+// Set holding point p (warp-uniform): a 32-way search over the offsets.
+__device__ __forceinline__ int bt_find_set(const BArgs& a, long long p) {
+    const int lane = threadIdx.x & 31;
+    int lo = 0, hi = a.k;   // offsets[lo] <= p < offsets[hi]
+    while (hi - lo > 1) {
+        const int step = (hi - lo + 31) / 32;
+        const int probe = lo + lane * step;
+        const bool le = probe < hi && __ldg(a.offsets + probe) <= p;
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, le);   // a prefix of the lanes (lane 0 always)
+        const int last = 31 - __clz((int)m);
+        lo = lo + last * step;
+        hi = min(hi, lo + step);
+    }
+    return lo;
+}
+
+// The warp's lanes folded into the set's packed maxima; validity into its status.
+__device__ __forceinline__ void bt_flush_track(const Track& tr, Ctl* c) {
+    const int lane = threadIdx.x & 31;
+    const bool err = tr.bad || (tr.orv >> kCoordBits) != 0u;
+    if (__any_sync(0xFFFFFFFFu, err) && lane == 0) set_status(c, CH_ERANGE);
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+        unsigned long long p = pack_best(d, tr.best[d], tr.code[d]);
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            const unsigned long long q = __shfl_xor_sync(0xFFFFFFFFu, p, o);
+            p = q > p ? q : p;
+        }
+        if (lane == 0 && p) atomicMax(&c->ext_packed[d], p);
     }
 }
 
-// Three-input max / min of non-negative int keys through their float bit
-// patterns (below 2^26 the patterns are positive finite floats that order
-// like the integers; max.f32 without .ftz keeps subnormals exact).
-__device__ __forceinline__ int bt_max3(int a, int b, int c) {
-    float r;
-    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(__int_as_float(a)), "f"(__int_as_float(b)), "f"(__int_as_float(c)));
-    return __float_as_int(r);
-}
-__device__ __forceinline__ int bt_min3(int a, int b, int c) {
-    float r;
-    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(__int_as_float(a)), "f"(__int_as_float(b)), "f"(__int_as_float(c)));
-    return __float_as_int(r);
-}
-
-// Per tile of T x P points: each thread holds its P points in registers; the
-// block first finds the tile's 8 extreme keys (three-input min / max, two
-// points per instruction), then the lowest index reaching each of them
-// (every thread checks its own points), and one packed (key, lowest index)
-// atomic per direction carries it to the set's maximum.
-template <int T, int P>
-__global__ void __launch_bounds__(T) bt_extremes(BArgs a, int ntiles) {
-    static_assert(P % 2 == 0 && T % 32 == 0, "tile shape");
-    constexpr int kBTile = T * P;
-    __shared__ int s_key[T / 32][8];
-    __shared__ int s_best[8];
-    __shared__ unsigned s_idx[8];
-    __shared__ int s_set;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        if (tid == 0) s_set = tile_set(a, t);
-        if (tid < 8) s_idx[tid] = 0xFFFFFFFFu;
-        __syncthreads();
-        const int i = s_set;
-        const long long base = a.offsets[i], ni = a.offsets[i + 1] - base;
-        const long long p0 = (long long)(t - a.tile_base[i]) * kBTile;
-        const int cnt = (int)min((long long)kBTile, ni - p0);   // >= 1
-        const float2* p2 = reinterpret_cast<const float2*>(a.pts) + base + p0;
-        float2 v[P];
-#pragma unroll
-        for (int j = 0; j < P; ++j) {
-            const int q = tid + j * T;
-            v[j] = __ldcs(p2 + (q < cnt ? q : 0));   // a missing point repeats point 0 of the tile
-        }
+// A warp tile meeting a set boundary (point p0 + 2 (32 j + lane) + h in
+// float4 j, half h), set by set from set s on.
+template <int P>
+__device__ __noinline__ void bt_tile_straddle(const BArgs& a, const float4* cur, long long p0, int s, unsigned code) {
+    const int lane = threadIdx.x & 31;
+    const long long p1 = p0 + 32ll * P;
+    for (int q = s; q < a.k; ++q) {
+        const long long qb = __ldg(a.offsets + q), qe = __ldg(a.offsets + q + 1);
+        Track tr;
+        track_init(tr);
         int tk[8];
-        bool bad = false;
 #pragma unroll
-        for (int j = 0; j < P; j += 2) {
-            const int X0 = __float2int_rn(v[j].x), Y0 = __float2int_rn(v[j].y);
-            const int X1 = __float2int_rn(v[j + 1].x), Y1 = __float2int_rn(v[j + 1].y);
-            bad |= (__int2float_rn(X0) != v[j].x) | (__int2float_rn(Y0) != v[j].y) |
-                   (__int2float_rn(X1) != v[j + 1].x) | (__int2float_rn(Y1) != v[j + 1].y) |
-                   (((unsigned)X0 | (unsigned)Y0 | (unsigned)X1 | (unsigned)Y1) >> kCoordBits) != 0u;
-            if (j == 0) {
+        for (int d = 0; d < 8; ++d) tk[d] = dir_is_max(d) ? INT_MIN : INT_MAX;
+#pragma unroll 1
+        for (int j = 0; j < P / 2; ++j) {
+            const float4 v = cur[j * 32 + lane];
 #pragma unroll
-                for (int d = 0; d < 8; ++d) {
-                    const int k0 = bt_key(d, X0, Y0), k1 = bt_key(d, X1, Y1);
-                    tk[d] = bt_dir_is_max(d) ? max(k0, k1) : min(k0, k1);
-                }
-            } else {
+            for (int h = 0; h < 2; ++h) {
+                const long long i = p0 + 2 * (j * 32 + lane) + h;
+                if (i < qb || i >= qe) continue;
+                int X, Y;
+                convert_pt(h ? v.z : v.x, h ? v.w : v.y, X, Y, tr);
 #pragma unroll
                 for (int d = 0; d < 8; ++d) {
-                    const int k0 = bt_key(d, X0, Y0), k1 = bt_key(d, X1, Y1);
-                    tk[d] = bt_dir_is_max(d) ? bt_max3(tk[d], k0, k1) : bt_min3(tk[d], k0, k1);
+                    const int key = dir_key(d, X, Y);
+                    tk[d] = dir_is_max(d) ? max(tk[d], key) : min(tk[d], key);
                 }
             }
         }
-        if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) set_status(a.ctl + i, CH_ERANGE);
-#pragma unroll
-        for (int d = 0; d < 8; ++d) {
-            int k = tk[d];
-#pragma unroll
-            for (int o = 16; o; o >>= 1) {
-                const int r = __shfl_xor_sync(0xFFFFFFFFu, k, o);
-                k = bt_dir_is_max(d) ? max(k, r) : min(k, r);
-            }
-            if (lane == 0) s_key[warp][d] = k;
-        }
-        __syncthreads();
-        if (tid < 8) {
-            int k = s_key[0][tid];
-            for (int w = 1; w < T / 32; ++w) k = bt_dir_is_max(tid) ? max(k, s_key[w][tid]) : min(k, s_key[w][tid]);
-            s_best[tid] = k;
-        }
-        __syncthreads();
-        // lowest index reaching each extreme key (points in increasing index order per thread)
-        unsigned first[8];
-#pragma unroll
-        for (int d = 0; d < 8; ++d) first[d] = 0xFFFFFFFFu;
-#pragma unroll
-        for (int j = P - 1; j >= 0; --j) {
-            const int q = tid + j * T;
-            const int X = __float2int_rn(v[j].x), Y = __float2int_rn(v[j].y);
-#pragma unroll
-            for (int d = 0; d < 8; ++d)
-                if (q < cnt && bt_key(d, X, Y) == s_best[d]) first[d] = (unsigned)(p0 + q);
-        }
-#pragma unroll
-        for (int d = 0; d < 8; ++d) {
-            const unsigned m = __reduce_min_sync(0xFFFFFFFFu, first[d]);
-            if (lane == 0 && m != 0xFFFFFFFFu) atomicMin(&s_idx[d], m);
-        }
-        __syncthreads();
-        if (tid < 8) {
-            const int d = tid;
-            const unsigned hk = bt_dir_is_max(d) ? (unsigned)s_best[d] : 0xFFFFFFFFu - (unsigned)s_best[d];
-            const unsigned long long pk = ((unsigned long long)hk << 32) | (unsigned long long)(0xFFFFFFFFu - s_idx[d]);
-            atomicMax(&a.ctl[i].ext_packed[d], pk);
-        }
-        __syncthreads();
+        track_tile(tr, tk, code);
+        bt_flush_track(tr, a.ctl + q);
+        if (qe >= p1) break;
     }
 }
 
-// One block per set: octagon of its extremes (with the inner region, which
-// settles most points of bt_filter), the chain end-point records.
+// Points [lo, hi) one per lane, each with its own set (head and tail).
+__device__ void bt_points_scalar(const BArgs& a, long long lo, long long hi, unsigned code) {
+    const int lane = threadIdx.x & 31;
+    for (long long b = lo; b < hi; b += 32) {
+        const long long i = b + lane;
+        if (i >= hi) continue;
+        int l = 0, r = a.k;   // offsets[l] <= i < offsets[r]
+        while (r - l > 1) {
+            const int mid = (l + r) >> 1;
+            if (__ldg(a.offsets + mid) <= i) l = mid;
+            else r = mid;
+        }
+        Ctl* c = a.ctl + l;
+        const float x = a.pts[2 * i], y = a.pts[2 * i + 1];
+        const int X = __float2int_rn(x), Y = __float2int_rn(y);
+        if (__int2float_rn(X) != x || __int2float_rn(Y) != y || (((unsigned)X | (unsigned)Y) >> kCoordBits) != 0u) {
+            set_status(c, CH_ERANGE);
+            continue;
+        }
+#pragma unroll
+        for (int d = 0; d < 8; ++d) atomicMax(&c->ext_packed[d], pack_best(d, dir_key(d, X, Y), code));
+    }
+}
+
+template <int T, int P>
+__global__ void __launch_bounds__(T) bt_extremes(BArgs a) {
+    constexpr int kWarps = T / 32, kF4 = 16 * P;
+    constexpr long long kPts = 32ll * P;
+    extern __shared__ __align__(128) unsigned char dsm[];
+    __shared__ unsigned long long s_bar[kWarps][kStages];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long nwt = a.nwt;
+    const long long per = (nwt + gridDim.x - 1) / gridDim.x;
+    const long long c0 = min(nwt, (long long)blockIdx.x * per), c1 = min(nwt, c0 + per);
+    if (blockIdx.x == 0 && warp == 0) {
+        bt_points_scalar(a, 0, a.head, 0u);
+        bt_points_scalar(a, a.head + nwt * kPts, a.total, (unsigned)(nwt + 1));
+    }
+    if (c0 + warp >= c1) return;
+    WarpStreamT<kF4> ws{reinterpret_cast<float4*>(dsm) + warp * kStages * kF4, s_bar[warp],
+                        reinterpret_cast<const float4*>(a.pts + 2 * a.head), c0 + warp, kWarps, c1, lane};
+    int s = bt_find_set(a, a.head + (c0 + warp) * kPts);
+    int ts = -1;   // the set the lanes' tracks belong to
+    Track tr;
+    track_init(tr);
+    ws.start();
+    for (long long k = 0;; ++k) {
+        const long long t = c0 + warp + k * kWarps;
+        if (t >= c1) break;
+        const long long p0 = a.head + t * kPts;
+        while (__ldg(a.offsets + s + 1) <= p0) ++s;
+        const float4* cur = ws.acquire(k, a.ctl + s);
+        if (!cur) {   // a copy never completed: every set of the rest of the chunk fails
+            ws.drain(k);
+            const long long pend = a.head + c1 * kPts;
+            for (int q = s + lane; q < a.k && __ldg(a.offsets + q) < pend; q += 32) set_status(a.ctl + q, CH_ETIMEOUT);
+            if (ts >= 0 && lane == 0) set_status(a.ctl + ts, CH_ETIMEOUT);
+            return;
+        }
+        if (__ldg(a.offsets + s + 1) >= p0 + kPts) {   // inside set s
+            if (s != ts) {
+                if (ts >= 0) bt_flush_track(tr, a.ctl + ts);
+                track_init(tr);
+                ts = s;
+            }
+            int tk[8];
+#pragma unroll
+            for (int j = 0; j < P / 2; ++j) {
+                const float4 v = cur[j * 32 + lane];
+                int X0, Y0, X1, Y1;
+                convert_pt(v.x, v.y, X0, Y0, tr);
+                convert_pt(v.z, v.w, X1, Y1, tr);
+                tile_keys2(tk, X0, Y0, X1, Y1, j == 0);
+            }
+            track_tile(tr, tk, (unsigned)(t + 1));
+        } else {
+            if (ts >= 0) bt_flush_track(tr, a.ctl + ts);
+            track_init(tr);
+            ts = -1;
+            bt_tile_straddle<P>(a, cur, p0, s, (unsigned)(t + 1));
+        }
+        ws.release(k);
+    }
+    if (ts >= 0) bt_flush_track(tr, a.ctl + ts);
+}
+
+// One block per set: the lowest index of each extreme (warp d rescans the
+// winning tile of direction d within the set), the octagon of the extremes
+// (with the inner region, which settles most points of bt_filter), the chain
+// end-point records.
 __global__ void __launch_bounds__(kBOctThreads) bt_octagon(BArgs a) {
     __shared__ Octagon s_o;
-    __shared__ int s_vx[8], s_vy[8], s_id[8], s_st;
-    const int i = blockIdx.x, tid = threadIdx.x;
+    __shared__ int s_vx[8], s_vy[8], s_id[8], s_st, s_bad;
+    const int i = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     Ctl* c = a.ctl + i;
     const long long base = a.offsets[i], ni = a.offsets[i + 1] - base;
-    if (tid == 0) s_st = read_status(c);
+    if (tid == 0) {
+        s_st = read_status(c);
+        s_bad = 0;
+    }
     __syncthreads();
     if (ni == 0 || s_st != CH_OK) {
         if (tid == 0) {
@@ -269,14 +327,49 @@ __global__ void __launch_bounds__(kBOctThreads) bt_octagon(BArgs a) {
         }
         return;
     }
-    if (tid < 8) {
-        const unsigned long long pk = c->ext_packed[tid];
-        const int id = (int)(0xFFFFFFFFu - (unsigned)(pk & 0xFFFFFFFFull));
-        s_id[tid] = id;
-        s_vx[tid] = __float2int_rn(a.pts[2 * (base + id)]);
-        s_vy[tid] = __float2int_rn(a.pts[2 * (base + id) + 1]);
+    {
+        const int d = warp;
+        const unsigned long long pk = c->ext_packed[d];
+        const unsigned code = 0xFFFFFFFFu - (unsigned)(pk & 0xFFFFFFFFull);
+        const unsigned hk = (unsigned)(pk >> 32);
+        const int best = dir_is_max(d) ? (int)hk : (int)(0xFFFFFFFFu - hk);
+        long long lo, hi;   // the tile's points, within the set
+        if (code == 0u) { lo = 0; hi = a.head; }
+        else if ((long long)code <= a.nwt) { lo = a.head + (long long)(code - 1u) * a.wtile; hi = lo + a.wtile; }
+        else { lo = a.head + a.nwt * a.wtile; hi = a.total; }
+        lo = max(lo, base);
+        hi = min(hi, base + ni);
+        long long first = LLONG_MAX;
+#pragma unroll 4
+        for (long long j = lo + lane; j < hi; j += 32) {
+            const float2 p = __ldg(reinterpret_cast<const float2*>(a.pts) + j);
+            if (j < first && dir_key(d, __float2int_rn(p.x), __float2int_rn(p.y)) == best) first = j;
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            const long long q = __shfl_xor_sync(0xFFFFFFFFu, first, o);
+            first = q < first ? q : first;
+        }
+        if (lane == 0) {
+            if (pk == 0ull || first == LLONG_MAX) {   // cannot happen for a valid set; fail safe
+                s_bad = 1;
+                first = base;
+            }
+            s_id[d] = (int)(first - base);
+            const float2 p = reinterpret_cast<const float2*>(a.pts)[first];
+            s_vx[d] = __float2int_rn(p.x);
+            s_vy[d] = __float2int_rn(p.y);
+        }
     }
     __syncthreads();
+    if (s_bad) {
+        if (tid == 0) {
+            set_status(c, CH_ECUDA);
+            a.out_n[i] = CH_ECUDA;
+            c->done = 1;
+        }
+        return;
+    }
     setup_octagon_block(s_o, s_vx, s_vy, s_id, true);
     copy_octagon(&c->oct, &s_o);
     const long long rb = region_base(a, i);
@@ -835,10 +928,14 @@ struct BtShape {
 constexpr BtShape kBtShapes[] = {{128, 16}, {256, 8}, {256, 16}, {256, 32}, {512, 8}, {512, 16}};
 constexpr int kNumBtShapes = (int)(sizeof(kBtShapes) / sizeof(kBtShapes[0]));
 
+// Dynamic shared memory of bt_extremes: a two-stage ring of warp tiles per warp.
+constexpr size_t bt_ext_smem(int threads, int per) { return (size_t)(threads / 32) * kStages * 16 * per * 16; }
+
 template <int T, int P>
 static void bt_occupancy(int* occ) {
     int a = 0, b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, bt_extremes<T, P>, T, 0);
+    cudaFuncSetAttribute(bt_extremes<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt_ext_smem(T, P));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, bt_extremes<T, P>, T, bt_ext_smem(T, P));
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, bt_filter<T, P>, T, 0);
     occ[0] = std::max(1, a);
     occ[1] = std::max(1, b);
@@ -882,7 +979,7 @@ static void launch_bt_tiles(int shape, bool filter, const BArgs& a, int nt, int 
 #define CH_BT_CASE(i, T, P)                                                   \
     case i:                                                                   \
         if (filter) bt_filter<T, P><<<grid, T, 0, s>>>(a, nt);                \
-        else bt_extremes<T, P><<<grid, T, 0, s>>>(a, nt);                     \
+        else bt_extremes<T, P><<<grid, T, bt_ext_smem(T, P), s>>>(a);         \
         break;
     switch (shape) {
         CH_BT_CASE(0, 128, 16)
@@ -1113,7 +1210,9 @@ static void bt_set_shape(BtCall& c, const BtDevice& d, const std::vector<int64_t
     c.shape = shape;
     c.a.tile = sh.threads * sh.per;
     c.nt = (int)count_tiles(off, c.a.k, c.a.tile);
-    c.grid_e = std::max(1, std::min(c.nt, d.sms * d.occ[shape][0]));
+    c.a.wtile = 32 * sh.per;
+    c.a.nwt = (c.a.total - c.a.head) / c.a.wtile;
+    c.grid_e = (int)std::max(1ll, std::min(c.a.nwt, (long long)d.sms * d.occ[shape][0]));
     c.grid_f = std::max(1, std::min(c.nt, d.sms * d.occ[shape][1]));
 }
 
@@ -1249,6 +1348,9 @@ int hull_batched_impl(const float* pts, const int64_t* offsets, int32_t k, int32
     a.out_idx = out_idx;
     a.out_n = out_n;
     a.big = (unsigned char*)(base + L.big);
+    a.total = total;
+    // the streamed body starts at the first 16-byte boundary (pts is 8-byte aligned)
+    a.head = (total > 0 && (reinterpret_cast<uintptr_t>(pts) & 15u) != 0u) ? 1 : 0;
     a.star_ctr = (unsigned*)(base + L.star_ctr);
     a.star_list = (int*)(base + L.star_list);
     a.kP = (uint32_t*)(base + L.kP);

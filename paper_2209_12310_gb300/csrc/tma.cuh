@@ -66,12 +66,14 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
 }
 
 // A warp's double-buffered stream of its warp tiles t = first + k * stride
-// (k = 0, 1, ...), each kWarpTileF4 float4 copied by one bulk copy issued by
-// lane 0.  Usage: for (k...) { cur = acquire(k); ...read cur...; release(k); }
+// (k = 0, 1, ...) below ntiles, each kF4 float4 copied by one bulk copy
+// issued by lane 0.  Usage: for (k...) { cur = acquire(k); ...read cur...;
+// release(k); }
 constexpr int kStages = 2;
 
-struct WarpStream {
-    float4* ring;                 // kStages * kWarpTileF4 float4 of shared memory
+template <int kF4>
+struct WarpStreamT {
+    float4* ring;                 // kStages * kF4 float4 of shared memory
     unsigned long long* bar;      // kStages barriers
     const float4* src;            // 16-byte aligned body of the point array
     long long first, stride, ntiles;
@@ -82,8 +84,8 @@ struct WarpStream {
         if (t < ntiles && lane == 0) {
             const int s = (int)(k % kStages);
             fence_proxy_async();
-            mbar_expect_tx(&bar[s], kWarpTileF4 * 16);
-            tma_load(ring + s * kWarpTileF4, src + t * kWarpTileF4, kWarpTileF4 * 16, &bar[s], l2_evict_first());
+            mbar_expect_tx(&bar[s], kF4 * 16);
+            tma_load(ring + s * kF4, src + t * kF4, kF4 * 16, &bar[s], l2_evict_first());
         }
     }
     __device__ __forceinline__ void start() {
@@ -99,7 +101,7 @@ struct WarpStream {
         const int s = (int)(k % kStages);
         const unsigned parity = (unsigned)((k / kStages) & 1);
         if (!mbar_wait(&bar[s], parity, ctl)) return nullptr;
-        return ring + s * kWarpTileF4;
+        return ring + s * kF4;
     }
     // Every lane is done reading tile k: refill its stage with tile k + kStages.
     __device__ __forceinline__ void release(long long k) {
@@ -120,5 +122,7 @@ struct WarpStream {
         __syncwarp();
     }
 };
+
+using WarpStream = WarpStreamT<kWarpTileF4>;
 
 }  // namespace ch

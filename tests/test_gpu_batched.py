@@ -106,6 +106,35 @@ def test_batched_repeated_and_odd_offsets(lib):
         np.testing.assert_array_equal(a, oracle.hull(s))
 
 
+def test_batched_unaligned_base_tiny_sets_and_ties(lib):
+    """The batch starts 8 bytes past a 16-byte boundary (one head point before
+    the streamed body), many tiny sets meet inside one warp tile, and extreme
+    keys repeat across tiles and sets (lowest index wins)."""
+    rng = np.random.default_rng(21)
+    sets = [rng.integers(0, 7, (int(rng.integers(1, 60)), 2)).astype(np.float32) for _ in range(300)]
+    sets += [np.repeat(W.uniform(50, 3), 40, axis=0), W.normal(30_001, 4),
+             rng.integers(0, 1 << 24, (5000, 2)).astype(np.float32), W.ring(20_000, 5)]
+    offsets = np.zeros(len(sets) + 1, np.int64)
+    offsets[1:] = np.cumsum([s.shape[0] for s in sets])
+    pts = np.concatenate(sets)
+    buf = torch.zeros((pts.shape[0] + 1, 2), dtype=torch.float32, device="cuda")
+    buf[1:] = torch.from_numpy(pts).cuda()
+    d_pts = buf[1:]
+    assert d_pts.data_ptr() % 16 == 8
+    d_off = torch.from_numpy(offsets).cuda()
+    out_idx = torch.full((int(offsets[-1]),), -7, dtype=torch.int32, device="cuda")
+    out_n = torch.full((len(sets),), -99, dtype=torch.int64, device="cuda")
+    st = lib.load().ch_hull_batched(d_pts.data_ptr(), d_off.data_ptr(), len(sets), out_idx.data_ptr(),
+                                    out_n.data_ptr(), None, torch.cuda.current_stream().cuda_stream)
+    assert st == 0
+    ns = out_n.cpu().tolist()
+    idx = out_idx.cpu().numpy()
+    for i, s in enumerate(sets):
+        want = oracle.hull(s)
+        assert ns[i] == want.size, i
+        np.testing.assert_array_equal(idx[offsets[i]:offsets[i] + ns[i]], want, err_msg=str(i))
+
+
 # --- tile shapes and the autotuner ------------------------------------------
 
 SHAPES = [(128, 16), (256, 8), (256, 16), (256, 32), (512, 8), (512, 16)]
