@@ -109,6 +109,23 @@ int ch_hull_batched(const float* pts, const int64_t* offsets, int32_t k,
                     void* stream);
 
 /*
+ * ch_batched_counters -- what the most recent ch_hull_batched on `stream`
+ * (current device) did per set, for measurement and tests: for set i,
+ *   out[4 i]      records handed to the hull stage (the filter's survivors,
+ *                 the chain end points included),
+ *   out[4 i + 1]  vertices of the star polygon that filtered the set (0 when
+ *                 none: a sparse set, a set under 32768 points, or a polygon
+ *                 that failed its checks),
+ *   out[4 i + 2]  the set's status (CH_OK or a negative ch_status),
+ *   out[4 i + 3]  hull stage: 0 one block, 1 the bucketed path, 2 the
+ *                 single-hull path.
+ * k must equal that call's k; out holds 4 k values.  Returns 4 (values per
+ * set).  Synchronises the stream.  CH_EINVAL when no batched call of k sets
+ * ran on that stream (or out is NULL).
+ */
+int ch_batched_counters(void* stream, int32_t k, int64_t* out);
+
+/*
  * ch_batched_config -- the tile shape ch_hull_batched uses on the current
  * device for a batch of total_points points in k >= 1 sets: *threads and
  * *per (points per thread) from CH_BLOCK / CH_PPT / CH_TILE, else from the

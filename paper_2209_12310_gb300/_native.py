@@ -45,6 +45,7 @@ SIGNATURES = {
     "ch_reserve": (_INT, [_I64, _I32, _P]),
     "ch_workspace_bytes": (_SZ, [_I64]),
     "ch_hull_counters": (_INT, [_P, ctypes.POINTER(_I64), _INT]),
+    "ch_batched_counters": (_INT, [_P, _I32, ctypes.POINTER(_I64)]),
     "ch_release": (_INT, []),
     "ch_selftest_timeout": (_INT, [_INT, _P]),
     "ch_strerror": (ctypes.c_char_p, [_INT]),
@@ -135,6 +136,15 @@ def ch_hull_host(pts, n, out_idx, out_n, stream=0):
 
 def ch_reserve(n, k=1, stream=0):
     return _check(load().ch_reserve(n, k, stream), "ch_reserve")
+
+
+def ch_batched_counters(k, stream=0):
+    """Per-set counters of the most recent ch_hull_batched of k sets on
+    `stream`: a list of dicts (records, star vertices, status, hull stage)."""
+    out = (_I64 * (4 * max(k, 1)))()
+    _check(load().ch_batched_counters(stream, k, out), "ch_batched_counters")
+    return [{"records": int(out[4 * i]), "star_vertices": int(out[4 * i + 1]), "status": int(out[4 * i + 2]),
+             "stage": int(out[4 * i + 3])} for i in range(k)]
 
 
 def ch_hull_counters(stream=0):

@@ -48,9 +48,20 @@
 
 namespace ch {
 
-constexpr int kBTileMin = 2048;        // smallest tile of the compiled shapes
 constexpr int kBHullThreads = 512;     // threads of bt_hull (a multiple of 128)
+constexpr int kBWarpTileMin = 256;     // points of the smallest warp tile of the compiled shapes
 constexpr int kBOctThreads = 256;      // threads of bt_octagon: a warp per direction
+
+// Star polygon of dense sets (star.cuh): a set of at least kBStarMinPts
+// points has a slot of angular bins and a polygon.  The bins are taken
+// around the centre of the box of the set's extremes, over a sample of
+// kBStarParts evenly spread runs of the set (up to kBStarRun points each).
+constexpr long long kBStarMinPts = 32768;
+constexpr int kBStarParts = 16;
+constexpr int kBStarRun = 65536;
+constexpr int kBDenseSample = 2048;   // points of a set's density test
+static_assert(kBDenseSample <= kBStarMinPts, "the density sample is spread over the set");
+
 
 struct BArgs {
     const float* pts;
@@ -59,64 +70,60 @@ struct BArgs {
     Ctl* ctl;                 // k control blocks
     uint32_t* keys;           // records: set i's region starts at offsets[i] + 16 i
     uint64_t* vals;
-    int* tile_base;           // k + 1: first tile of each set
-    int* tile_map;            // set of every tile
     int32_t* out_idx;
     int64_t* out_n;
     unsigned char* big;       // k: the set needs the single-hull path
-    int tile;                 // points per tile (threads x points per thread of the tile kernels)
     long long total;          // points of the batch
-    long long nwt;            // warp tiles of the streamed body (bt_extremes)
+    long long nwt;            // warp tiles of the streamed body
     int head;                 // points before the body's first 16-byte boundary (0 or 1)
-    int wtile;                // points per warp tile of bt_extremes (32 x points per lane)
-    unsigned* star_ctr;       // bt_star's work list: [0] sets from the front, [1] from the back, [2] taken
+    int wtile;                // points per warp tile (32 x points per lane)
+    int* star_slot;           // k: the set's star slot, or -1
+    unsigned long long* star_bins;   // kStarBins per slot (zeroed before every batch)
+    StarPoly* star_polys;     // one per slot
+    unsigned* star_ctr;       // bt_star_build's work list: [0] dense sets listed, [1] taken
     int* star_list;           // k entries
-    uint32_t* kP;             // the bucketed path's scatter buffer (set regions as keys / vals)
-    uint64_t* vP;
 };
-
-// Sets with more records than this go through bt_star first (the others of
-// its list come after them).
-constexpr unsigned kBStarHuge = 1u << 18;
 
 __device__ __forceinline__ long long region_base(const BArgs& a, int i) { return a.offsets[i] + 16ll * i; }
 
-// Set of tile t (written by bt_scan).
-__device__ __forceinline__ int tile_set(const BArgs& a, int t) { return a.tile_map[t]; }
-
-__global__ void bt_init(BArgs a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+// One warp per set: the control block.
+__global__ void __launch_bounds__(256) bt_init(BArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (i >= a.k) return;
     Ctl* c = a.ctl + i;
-    for (int d = 0; d < 8; ++d) {
-        c->ext_packed[d] = 0ull;
-        c->line_ep[d] = (d & 1) ? 0ull : ~0ull;
+    if (lane < 8) {
+        c->ext_packed[lane] = 0ull;
+        c->line_ep[lane] = (lane & 1) ? 0ull : ~0ull;
     }
-    c->status = CH_OK;
-    c->abort = 0;
-    c->count = 8u;
-    c->done = 0;
-    c->bk_state = 0;
-    c->star_k = 0;
-    for (int q = 0; q < 4; ++q) {
-        c->counts4[q] = 2u;   // the two chain end points of every queue
-        c->blocks_done[q] = 0u;
+    if (lane < 4) {
+        c->counts4[lane] = 2u;   // the two chain end points of every queue
+        c->blocks_done[lane] = 0u;
     }
-    a.big[i] = 0;
-    const long long ni = a.offsets[i + 1] - a.offsets[i];
-    a.tile_base[i] = (int)((ni + a.tile - 1) / a.tile);
-    if (i == 0) a.star_ctr[0] = a.star_ctr[1] = a.star_ctr[2] = 0u;
+    if (lane == 0) {
+        c->status = CH_OK;
+        c->abort = 0;
+        c->count = 8u;
+        c->done = 0;
+        c->bk_state = 0;
+        c->star_ok = 0;
+        c->star_k = 0;
+        c->star_cx = 0;
+        c->star_cy = 0;
+        a.big[i] = 0;
+    }
+    if (i == 0 && lane == 0) a.star_ctr[0] = a.star_ctr[1] = 0u;
 }
 
-// Exclusive prefix of the tile counts in place (one block of 1024 threads);
-// tile_base[k] = total tiles; then the set of every tile.
-__global__ void __launch_bounds__(1024) bt_scan(int* tile_base, int* tile_map, int k) {
+// Star slots (one block of 1024 threads): the sets of at least kBStarMinPts
+// points numbered in set order, -1 for the others.
+__global__ void __launch_bounds__(1024) bt_slots(BArgs a) {
     __shared__ int s_part[1024];
     const int tid = threadIdx.x;
-    const int per = (k + 1023) / 1024;
-    const int lo = tid * per, hi = min(k, lo + per);
+    const int per = (a.k + 1023) / 1024;
+    const int lo = tid * per, hi = min(a.k, lo + per);
     int sum = 0;
-    for (int i = lo; i < hi; ++i) sum += tile_base[i];
+    for (int i = lo; i < hi; ++i) sum += (a.offsets[i + 1] - a.offsets[i] >= kBStarMinPts) ? 1 : 0;
     s_part[tid] = sum;
     __syncthreads();
     for (int o = 1; o < 1024; o <<= 1) {
@@ -127,12 +134,10 @@ __global__ void __launch_bounds__(1024) bt_scan(int* tile_base, int* tile_map, i
     }
     int run = s_part[tid] - sum;
     for (int i = lo; i < hi; ++i) {
-        const int c = tile_base[i];
-        tile_base[i] = run;
-        for (int t = 0; t < c; ++t) tile_map[run + t] = i;
-        run += c;
+        const bool has = a.offsets[i + 1] - a.offsets[i] >= kBStarMinPts;
+        a.star_slot[i] = has ? run : -1;
+        run += has ? 1 : 0;
     }
-    if (tid == 1023) tile_base[k] = s_part[1023];
 }
 
 // ---------------------------------------------------------------------------
@@ -394,104 +399,418 @@ __global__ void __launch_bounds__(kBOctThreads) bt_octagon(BArgs a) {
             a.vals[rb + pos] = make_val(v, (uint32_t)s_id[d]);
         }
     }
+    // A set with a star slot whose sample (kBDenseSample points spread over
+    // it) has more than 1 / 16 outside the inner region is dense: bt_star_bin
+    // and bt_star_build make its star polygon.
+    if (a.star_slot[i] >= 0) {
+        __shared__ unsigned s_out;
+        if (tid == 0) s_out = 0u;
+        __syncthreads();
+        const long long step = ni / kBDenseSample;   // >= 1: ni >= kBStarMinPts
+        unsigned out = 0u;
+        for (int j = tid; j < kBDenseSample; j += kBOctThreads) {
+            const float2 p = __ldg(reinterpret_cast<const float2*>(a.pts) + base + j * step);
+            out += in_inner(s_o, __float2int_rn(p.x), __float2int_rn(p.y)) ? 0u : 1u;
+        }
+        out = __reduce_add_sync(0xFFFFFFFFu, out);
+        if (lane == 0 && out) atomicAdd(&s_out, out);
+        __syncthreads();
+        if (tid == 0 && s_out * 16u > (unsigned)kBDenseSample) {
+            c->star_ok = 1;
+            c->star_cx = (s_vx[W] + s_vx[E]) / 2;   // the centre of the extremes' box
+            c->star_cy = (s_vy[S] + s_vy[N]) / 2;
+            a.star_list[atomicAdd(&a.star_ctr[0], 1u)] = i;
+        }
+    }
 }
 
-// Per tile of T x P points: every thread loads its P points (a batch of at
-// most 8 at a time, all loads in flight together), then classifies them.
-// Survivors are staged per warp (kBtWarpRecs records) and written out in
-// batches: one returning atomic per batch instead of one per 32 points.
+// ---------------------------------------------------------------------------
+// The filter of every set, streamed (the loop of Alg. 1/2): the warp tiles
+// and block chunks of bt_extremes.  A warp keeps the octagon of its current
+// set in shared memory; the set's star polygon, when bt_star_build made one,
+// stays in global memory, where the warps of a block (on the same set) share
+// it through L1.  Per point: the octagon's inner region drops it (a whole
+// lane's points at once when their key extremes lie in the region); the star
+// polygon's radius bound of the point's bin drops most points of a dense set
+// (the bounds of a lane's points are loaded together); the points it leaves
+// wait in a per-warp queue and go 32 at a time through the exact wedge test
+// and the hull-rule classification, and the kept ones become records of
+// their queue, staged per warp and written to the set's region with one
+// atomic per batch.  Survivors on a support line of the octagon reduce to
+// the lines' end points (reduce_on_line).
 constexpr int kBtWarpRecs = 128;
-struct BtWarpBuf {
-    uint64_t val[kBtWarpRecs];
+constexpr int kBtQueue = 64;   // < 32 waiting + 32 added per step
+struct BtWarpSmem {
+    Octagon o;                       // the warp's set's octagon
+    uint64_t val[kBtWarpRecs];       // records staged
     uint32_t key[kBtWarpRecs];
+    float qx[kBtQueue], qy[kBtQueue];   // points waiting for the exact tests
+    unsigned qi[kBtQueue];
+    unsigned char lanes[32];         // lanes whose tile the inner region did not settle
 };
 
-__device__ __forceinline__ void bt_flush(BtWarpBuf& b, unsigned& cnt, Ctl* c, uint32_t* keys, uint64_t* vals,
-                                         long long rb) {
+// A warp's current set (warp-uniform registers).
+struct BtWarpSet {
+    int set = -1;
+    Ctl* c = nullptr;
+    long long base = 0, rb = 0;
+    const StarPoly* P = nullptr;   // the set's star polygon, if any
+    int cx = 0, cy = 0;
+    unsigned rmin = 0u;            // its inscribed radius
+    bool skip = true;              // empty or failed: nothing to classify
+    unsigned cnt = 0u;             // records staged
+    unsigned qn = 0u;              // points queued
+    unsigned nq[4] = {0u, 0u, 0u, 0u};   // records per queue since the last flush
+};
+
+__device__ __forceinline__ void bt_flush_recs(BtWarpSmem& m, BtWarpSet& w, uint32_t* keys, uint64_t* vals) {
     const int lane = threadIdx.x & 31;
-    if (cnt == 0u) return;
+    if (w.cnt == 0u) return;
     unsigned base = 0u;
-    if (lane == 0) base = atomicAdd(&c->count, cnt);
+    if (lane == 0) base = atomicAdd(&w.c->count, w.cnt);
     base = __shfl_sync(0xFFFFFFFFu, base, 0);
-    for (unsigned j = lane; j < cnt; j += 32) {
-        keys[rb + base + j] = b.key[j];
-        vals[rb + base + j] = b.val[j];
+    for (unsigned j = lane; j < w.cnt; j += 32) {
+        keys[w.rb + base + j] = m.key[j];
+        vals[w.rb + base + j] = m.val[j];
     }
     __syncwarp();
-    cnt = 0u;
+    w.cnt = 0u;
+}
+
+// Warp-collective: one point per lane of the warp's set (valid = false for
+// none), local index li; fast_done: its star radius test already failed.
+__device__ __forceinline__ void bt_filter_point(const BArgs& a, BtWarpSet& w, BtWarpSmem& m, bool valid,
+                                                bool fast_done, float x, float y, unsigned li) {
+    const Octagon& so = m.o;
+    int r = -1, X = 0, Y = 0;
+    if (valid) {
+        X = __float2int_rn(x);
+        Y = __float2int_rn(y);
+        if (!in_inner(so, X, Y)) {
+            bool drop = false;
+            if (w.P) {
+                const int px = X - w.cx, py = Y - w.cy, bn = star_bin(px, py);
+                drop = (!fast_done && star_inside_fast(px, py, bn, *w.P)) || star_inside_exact(px, py, bn, *w.P);
+            }
+            if (!drop) r = classify_hull(x, y, so);
+        }
+    }
+    bool keep = r >= 0;
+    if (!__any_sync(0xFFFFFFFFu, keep)) return;
+    if (reduce_on_line(so, keep, X, Y, li, w.c)) keep = false;
+    const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
+    if (!bal) return;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) w.nq[q] += (unsigned)__popc(__ballot_sync(0xFFFFFFFFu, keep && r == q));
+    if (w.cnt + (unsigned)__popc(bal) > (unsigned)kBtWarpRecs) bt_flush_recs(m, w, a.keys, a.vals);
+    if (keep) {
+        uint32_t u, v;
+        queue_frame(r, X, Y, u, v);
+        const unsigned pos = w.cnt + (unsigned)__popc(bal & lanemask_lt());
+        m.key[pos] = make_key(r, u);
+        m.val[pos] = make_val(v, li);
+    }
+    w.cnt += (unsigned)__popc(bal);
+    __syncwarp();
+}
+
+// Warp-collective: queues the lanes' points with need = true; full rounds of
+// 32 go through bt_filter_point.
+__device__ __forceinline__ void bt_queue_push(const BArgs& a, BtWarpSet& w, BtWarpSmem& m, bool need, float x, float y,
+                                              unsigned li) {
+    const int lane = threadIdx.x & 31;
+    const unsigned bal = __ballot_sync(0xFFFFFFFFu, need);
+    if (!bal) return;
+    if (need) {
+        const unsigned pos = w.qn + (unsigned)__popc(bal & lanemask_lt());
+        m.qx[pos] = x;
+        m.qy[pos] = y;
+        m.qi[pos] = li;
+    }
+    w.qn += (unsigned)__popc(bal);
+    __syncwarp();
+    while (w.qn >= 32u) {
+        w.qn -= 32u;
+        const float qx = m.qx[w.qn + lane], qy = m.qy[w.qn + lane];
+        const unsigned qi = m.qi[w.qn + lane];
+        __syncwarp();
+        bt_filter_point(a, w, m, true, true, qx, qy, qi);
+    }
+}
+
+// Warp-collective: finishes the warp's set (queue, records, queue counts).
+__device__ __forceinline__ void bt_warp_done(const BArgs& a, BtWarpSmem& m, BtWarpSet& w) {
+    const int lane = threadIdx.x & 31;
+    if (w.set < 0) return;
+    if (w.qn) {
+        const bool valid = (unsigned)lane < w.qn;
+        const float qx = valid ? m.qx[lane] : 0.0f, qy = valid ? m.qy[lane] : 0.0f;
+        const unsigned qi = valid ? m.qi[lane] : 0u;
+        __syncwarp();
+        w.qn = 0u;
+        bt_filter_point(a, w, m, valid, true, qx, qy, qi);
+    }
+    bt_flush_recs(m, w, a.keys, a.vals);
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (w.nq[q]) atomicAdd(&w.c->counts4[q], w.nq[q]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) w.nq[q] = 0u;
+    w.set = -1;
+}
+
+// Warp-collective: makes set q the warp's set (the previous one finished).
+__device__ __forceinline__ void bt_warp_set(const BArgs& a, int q, BtWarpSet& w, BtWarpSmem& m) {
+    const int lane = threadIdx.x & 31;
+    bt_warp_done(a, m, w);
+    w.set = q;
+    w.c = a.ctl + q;
+    w.base = a.offsets[q];
+    w.rb = region_base(a, q);
+    w.skip = *(volatile int*)&w.c->done != 0;   // bt_octagon's verdict on empty and failed sets
+    const int slot = a.star_slot[q];
+    w.P = (slot >= 0 && w.c->star_k > 0) ? a.star_polys + slot : nullptr;
+    w.rmin = w.P ? w.P->rmin : 0u;
+    w.cx = w.c->star_cx;
+    w.cy = w.c->star_cy;
+    if (!w.skip) {
+        const int* src = reinterpret_cast<const int*>(&w.c->oct);
+        int* dst = reinterpret_cast<int*>(&m.o);
+        for (int j = lane; j < (int)(sizeof(Octagon) / 4); j += 32) dst[j] = src[j];
+    }
+    __syncwarp();
+}
+
+// Points [lo, hi) of the batch read from global memory, set by set from the
+// set holding lo (head and tail).
+__device__ void bt_filter_global(const BArgs& a, long long lo, long long hi, BtWarpSet& w, BtWarpSmem& m) {
+    const int lane = threadIdx.x & 31;
+    if (lo >= hi) return;
+    for (int q = bt_find_set(a, lo); q < a.k; ++q) {
+        const long long qb = a.offsets[q], qe = a.offsets[q + 1];
+        if (qb >= hi) break;
+        if (qe <= lo) continue;
+        bt_warp_set(a, q, w, m);
+        if (w.skip) continue;
+        const long long e = min(hi, qe);
+        for (long long j0 = max(lo, qb); j0 < e; j0 += 32) {
+            const long long j = j0 + lane;
+            const bool valid = j < e;
+            const float2 p = valid ? reinterpret_cast<const float2*>(a.pts)[j] : make_float2(0.0f, 0.0f);
+            bt_filter_point(a, w, m, valid, false, p.x, p.y, (unsigned)(j - qb));
+        }
+    }
 }
 
 template <int T, int P>
-__global__ void __launch_bounds__(T) bt_filter(BArgs a, int ntiles) {
-    constexpr int kBTile = T * P;
-    constexpr int kB = P < 8 ? P : 8;   // points loaded together
-    __shared__ Octagon s_o;
-    __shared__ int s_set, s_skip;
-    __shared__ BtWarpBuf s_wb[T / 32];
-    const int tid = threadIdx.x, lane = tid & 31;
-    BtWarpBuf& wb = s_wb[tid >> 5];
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+__global__ void __launch_bounds__(T) bt_filter(BArgs a) {
+    constexpr int kWarps = T / 32, kF4 = 16 * P;
+    constexpr long long kPts = 32ll * P;
+    extern __shared__ __align__(128) unsigned char dsm[];
+    __shared__ unsigned long long s_bar[kWarps][kStages];
+    __shared__ BtWarpSmem s_w[kWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    BtWarpSmem& m = s_w[warp];
+    BtWarpSet w;
+    const long long nwt = a.nwt;
+    const long long per = (nwt + gridDim.x - 1) / gridDim.x;
+    const long long c0 = min(nwt, (long long)blockIdx.x * per), c1 = min(nwt, c0 + per);
+    if (blockIdx.x == 0 && warp == 0) {
+        bt_filter_global(a, 0, a.head, w, m);
+        bt_filter_global(a, a.head + nwt * kPts, a.total, w, m);
+    }
+    if (c0 + warp < c1) {
+        WarpStreamT<kF4> ws{reinterpret_cast<float4*>(dsm) + warp * kStages * kF4, s_bar[warp],
+                            reinterpret_cast<const float4*>(a.pts + 2 * a.head), c0 + warp, kWarps, c1, lane};
+        int s = bt_find_set(a, a.head + (c0 + warp) * kPts);
+        ws.start();
+        for (long long k = 0;; ++k) {
+            const long long t = c0 + warp + k * kWarps;
+            if (t >= c1) break;
+            const long long p0 = a.head + t * kPts;
+            while (__ldg(a.offsets + s + 1) <= p0) ++s;
+            const float4* cur = ws.acquire(k, a.ctl + s);
+            if (!cur) {   // a copy never completed: every set of the rest of the chunk fails
+                ws.drain(k);
+                const long long pend = a.head + c1 * kPts;
+                for (int q = s + lane; q < a.k && __ldg(a.offsets + q) < pend; q += 32)
+                    set_status(a.ctl + q, CH_ETIMEOUT);
+                break;
+            }
+            const float2* cur2 = reinterpret_cast<const float2*>(cur);
+            if (__ldg(a.offsets + s + 1) >= p0 + kPts) {   // inside set s
+                if (s != w.set) bt_warp_set(a, s, w, m);
+                if (!w.skip) {
+                    const Octagon& so = m.o;
+                    int tk[8];
+#pragma unroll
+                    for (int j = 0; j < P / 2; ++j) {
+                        const float4 v = cur[j * 32 + lane];
+                        tile_keys2(tk, __float2int_rn(v.x), __float2int_rn(v.y), __float2int_rn(v.z),
+                                   __float2int_rn(v.w), j == 0);
+                    }
+                    const bool inside = tk[W] >= so.in_lo[0] && tk[E] <= so.in_hi[0] && tk[S] >= so.in_lo[1] &&
+                                        tk[N] <= so.in_hi[1] && tk[SW] >= so.in_lo[2] && tk[NE] <= so.in_hi[2] &&
+                                        tk[NW] >= so.in_lo[3] && tk[SE] <= so.in_hi[3];
+                    // The points of the lanes whose tile failed are spread over
+                    // the warp, 32 at a time (slot s: failing lane of rank
+                    // s / P, its point s % P, in float4 (s % P) / 2, half s % 2).
+                    // A point needs the exact tests unless the inner region or,
+                    // with a star polygon, its inscribed radius or the bound of
+                    // the point's bin settles it.
+                    const unsigned fail = __ballot_sync(0xFFFFFFFFu, !inside);
+                    if (fail) {
+                        if (!inside) m.lanes[__popc(fail & lanemask_lt())] = (unsigned char)lane;
+                        __syncwarp();
+                        const unsigned slots = (unsigned)P * (unsigned)__popc(fail);
+                        const long long r0 = w.rmin;
+#pragma unroll 1
+                        for (unsigned s0 = 0; s0 < slots; s0 += 32u) {
+                            const unsigned sl = s0 + (unsigned)lane;
+                            bool need = false;
+                            float x = 0.0f, y = 0.0f;
+                            unsigned li = 0u;
+                            if (sl < slots) {
+                                const int ln = m.lanes[sl / P], j = (int)(sl % P);
+                                const int f2 = 2 * ((j >> 1) * 32 + ln) + (j & 1);
+                                const float2 p = cur2[f2];
+                                x = p.x;
+                                y = p.y;
+                                li = (unsigned)(p0 - w.base) + (unsigned)f2;
+                                const int X = __float2int_rn(x), Y = __float2int_rn(y);
+                                if (w.P) {   // the inscribed radius first: it settles most points of dense data
+                                    const long long px = X - w.cx, py = Y - w.cy, d2 = px * px + py * py;
+                                    if (d2 >= r0 * r0 && !in_inner(so, X, Y)) {
+                                        const long long r = __ldg(&w.P->rin[star_bin((int)px, (int)py)]);
+                                        need = d2 >= r * r;
+                                    }
+                                } else {
+                                    need = !in_inner(so, X, Y);
+                                }
+                            }
+                            bt_queue_push(a, w, m, need, x, y, li);
+                        }
+                        __syncwarp();
+                    }
+                }
+            } else {   // the tile meets a set boundary: set by set
+                for (int q = s; q < a.k; ++q) {
+                    const long long qb = __ldg(a.offsets + q), qe = __ldg(a.offsets + q + 1);
+                    if (qb >= p0 + kPts) break;
+                    if (qe <= p0) continue;
+                    if (q != w.set) bt_warp_set(a, q, w, m);
+                    if (w.skip) continue;
+#pragma unroll 1
+                    for (int j = 0; j < P; ++j) {
+                        const long long i = p0 + 2 * ((j >> 1) * 32 + lane) + (j & 1);
+                        const float2 p = cur2[2 * ((j >> 1) * 32 + lane) + (j & 1)];
+                        bt_filter_point(a, w, m, i >= qb && i < qe, false, p.x, p.y, (unsigned)(i - qb));
+                    }
+                }
+            }
+            ws.release(k);
+        }
+    }
+    bt_warp_done(a, m, w);
+}
+
+// ---------------------------------------------------------------------------
+// Bins of the dense sets (bt_octagon's list).  Chunk ch of the work is run
+// ch % kBStarParts of listed set ch / kBStarParts: the points
+// [base + part * (n / kBStarParts), + min(n / kBStarParts, kBStarRun)).
+// Every point outside the octagon's inner region goes to its angular bin
+// around the set's centre, where a 64-bit atomicMax keeps the point farthest
+// from the centre, packed (squared distance >> 17, local index); a point
+// reads its bin first and issues the atomic only when it beats it.
+constexpr int kBStarBinThreads = 256;
+constexpr int kBStarBinU = 8;   // points per thread in flight
+
+__global__ void __launch_bounds__(kBStarBinThreads) bt_star_bin(BArgs a) {
+    const int tid = threadIdx.x;
+    const unsigned nchunks = a.star_ctr[0] * (unsigned)kBStarParts;
+    for (unsigned ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        const int i = a.star_list[ch / kBStarParts];
+        const int part = (int)(ch % kBStarParts);
+        const Ctl* c = a.ctl + i;
+        const long long base = a.offsets[i], ni = a.offsets[i + 1] - base;
+        const long long step = ni / kBStarParts;
+        const long long lo = (long long)part * step;   // local index of the run
+        const int len = (int)min(step, (long long)kBStarRun);
+        const int cx = c->star_cx, cy = c->star_cy;
+        const int xl = c->oct.in_lo[0], yl = c->oct.in_lo[1], sl = c->oct.in_lo[2], dl = c->oct.in_lo[3];
+        const int xh = c->oct.in_hi[0], yh = c->oct.in_hi[1], sh = c->oct.in_hi[2], dh = c->oct.in_hi[3];
+        unsigned long long* bins = a.star_bins + (size_t)a.star_slot[i] * kStarBins;
+        const float2* p2 = reinterpret_cast<const float2*>(a.pts) + base + lo;
+        for (int j0 = 0; j0 < len; j0 += kBStarBinThreads * kBStarBinU) {
+            float2 p[kBStarBinU];
+#pragma unroll
+            for (int u = 0; u < kBStarBinU; ++u) {
+                const int j = j0 + u * kBStarBinThreads + tid;
+                p[u] = j < len ? __ldcs(p2 + j) : make_float2(-1.0f, -1.0f);
+            }
+            unsigned long long key[kBStarBinU];
+            int bin[kBStarBinU];
+#pragma unroll
+            for (int u = 0; u < kBStarBinU; ++u) {
+                const int X = __float2int_rn(p[u].x), Y = __float2int_rn(p[u].y);
+                const int S = X + Y, D = X - Y + kCoordLimit;
+                const bool inner = X >= xl && X <= xh && Y >= yl && Y <= yh && S >= sl && S <= sh && D >= dl && D <= dh;
+                const bool ok = ((unsigned)(X | Y) >> kCoordBits) == 0u && !inner;   // the set's points are valid
+                const int dx = X - cx, dy = Y - cy;
+                const unsigned long long d2 = (unsigned long long)((long long)dx * dx + (long long)dy * dy);
+                const long long li = lo + j0 + u * kBStarBinThreads + tid;
+                key[u] = ok ? ((d2 >> 17) << 32) | (unsigned long long)li : 0ull;
+                bin[u] = star_bin(dx, dy);
+            }
+            unsigned long long cur[kBStarBinU];
+#pragma unroll
+            for (int u = 0; u < kBStarBinU; ++u) cur[u] = key[u] ? __ldcg(bins + bin[u]) : ~0ull;
+#pragma unroll
+            for (int u = 0; u < kBStarBinU; ++u)
+                if (key[u] > cur[u]) atomicMax(&bins[bin[u]], key[u]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Star polygons of the dense sets (bt_octagon's list), one block per set,
+// persistent over the list: the polygon of the set's bins (star_finish,
+// star.cuh: vertices re-read from the input by index, checked exactly) is
+// built in shared memory and copied to the set's slot, for bt_filter.  A
+// set without one keeps star_k = 0 and is filtered by its octagon alone.
+constexpr int kBStarThreads = 512;
+constexpr size_t kBStarAOff = (sizeof(StarPoly) + 15) / 16 * 16;
+constexpr size_t kBStarSmem = kBStarAOff + (sizeof(int2) + sizeof(unsigned short)) * kStarBins;
+static_assert(sizeof(StarPoly) % 16 == 0, "the polygon is copied in 16-byte words");
+
+__global__ void __launch_bounds__(kBStarThreads, 1) bt_star_build(BArgs a) {
+    extern __shared__ __align__(16) char dyn[];
+    StarPoly& P = *reinterpret_cast<StarPoly*>(dyn);
+    int2* va = reinterpret_cast<int2*>(dyn + kBStarAOff);
+    unsigned short* ba = reinterpret_cast<unsigned short*>(dyn + kBStarAOff + sizeof(int2) * kStarBins);
+    __shared__ int s_set;
+    const int tid = threadIdx.x;
+    const unsigned listed = a.star_ctr[0];
+    for (;;) {
         if (tid == 0) {
-            const int i = tile_set(a, t);
-            s_set = i;
-            s_skip = *(volatile int*)&a.ctl[i].done;
+            const unsigned g = atomicAdd(&a.star_ctr[1], 1u);
+            s_set = g < listed ? a.star_list[g] : -1;
         }
         __syncthreads();
         const int i = s_set;
-        if (!s_skip) {
-            copy_octagon(&s_o, &a.ctl[i].oct);
-            __syncthreads();
-            Ctl* c = a.ctl + i;
-            const long long base = a.offsets[i], ni = a.offsets[i + 1] - base;
-            const long long p0 = (long long)(t - a.tile_base[i]) * kBTile;
-            const long long p1 = min(ni, p0 + kBTile);
-            const long long rb = region_base(a, i);
-            const float2* p2 = reinterpret_cast<const float2*>(a.pts) + base;
-            unsigned wcnt = 0u;                      // records staged in wb
-            unsigned qn[4] = {0u, 0u, 0u, 0u};       // records per queue (lane 0)
-            for (long long b0 = p0; b0 < p1; b0 += (long long)T * kB) {   // uniform trip counts
-                float2 pv[kB];
-#pragma unroll
-                for (int j = 0; j < kB; ++j) {
-                    const long long p = b0 + (long long)j * T + tid;
-                    if (p < p1) pv[j] = __ldcs(p2 + p);
-                }
-#pragma unroll 1
-                for (int j = 0; j < kB; ++j) {
-                const long long p = b0 + (long long)j * T + tid;
-                const bool valid = p < p1;
-                int r = -1, X = 0, Y = 0;
-                if (valid) {
-                    X = __float2int_rn(pv[j].x);
-                    Y = __float2int_rn(pv[j].y);
-                    r = classify_hull(pv[j].x, pv[j].y, s_o);
-                }
-                bool keep = r >= 0;
-                if (!__any_sync(0xFFFFFFFFu, keep)) continue;
-                if (reduce_on_line(s_o, keep, X, Y, (unsigned)p, c)) keep = false;
-                const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
-                if (!bal) continue;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) qn[q] += __popc(__ballot_sync(0xFFFFFFFFu, keep && r == q));
-                if (wcnt + (unsigned)__popc(bal) > (unsigned)kBtWarpRecs) bt_flush(wb, wcnt, c, a.keys, a.vals, rb);
-                if (keep) {
-                    uint32_t u, v;
-                    queue_frame(r, X, Y, u, v);
-                    const unsigned pos = wcnt + __popc(bal & lanemask_lt());
-                    wb.key[pos] = make_key(r, u);
-                    wb.val[pos] = make_val(v, (uint32_t)p);
-                }
-                wcnt += __popc(bal);
-                __syncwarp();
-                }
-            }
-            // the tile's records and queue counts (a tile never spans two sets)
-            bt_flush(wb, wcnt, c, a.keys, a.vals, rb);
-            if (lane == 0)
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (qn[q]) atomicAdd(&c->counts4[q], qn[q]);
+        if (i < 0) return;
+        Ctl* c = a.ctl + i;
+        const long long base = a.offsets[i], ni = a.offsets[i + 1] - base;
+        const int slot = a.star_slot[i];
+        const int K = star_finish<kBStarThreads>(a.star_bins + (size_t)slot * kStarBins, a.pts + 2 * base, ni,
+                                                 c->star_cx, c->star_cy, va, ba, P, c);
+        if (K) {
+            const int4* src = reinterpret_cast<const int4*>(&P);
+            int4* dst = reinterpret_cast<int4*>(a.star_polys + slot);
+            for (int j = tid; j < (int)(sizeof(StarPoly) / 16); j += kBStarThreads) dst[j] = src[j];
         }
+        if (tid == 0) c->star_k = K;
         __syncthreads();
     }
 }
@@ -542,13 +861,7 @@ __global__ void __launch_bounds__(kBSmallThreads) bt_hull_small(BArgs a) {
         a.vals[rb + s_lpos[tid]] = s_lval[tid];
         atomicAdd(&c->counts4[s_lkey[tid] >> kKeyBits], 1u);
     }
-    if (total > (unsigned)kBSmallRec) {   // bt_hull's, after bt_star's when one block cannot hold them
-        if (tid == 0 && total > (unsigned)kMidCap) {
-            if (total > kBStarHuge) a.star_list[atomicAdd(&a.star_ctr[0], 1u)] = i;
-            else a.star_list[a.k - 1 - (int)atomicAdd(&a.star_ctr[1], 1u)] = i;
-        }
-        return;
-    }
+    if (total > (unsigned)kBSmallRec) return;   // bt_hull's
     __syncthreads();   // also makes this block's line records visible to it
     for (unsigned j = tid; j < total; j += blockDim.x) {
         const uint32_t k = __ldcg(a.keys + rb + j);
@@ -565,192 +878,6 @@ __global__ void __launch_bounds__(kBSmallThreads) bt_hull_small(BArgs a) {
     } else if (tid == 0) {
         a.big[i] = 1;   // too many chain vertices for the small footprint: the bucketed path
         c->done = 1;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// The star polygon of a set whose records one block cannot hold (points near
-// a circle, where the octagon keeps almost all of them).  One block per such
-// set, persistent over the list that bt_hull_small builds (the sets with
-// more than kBStarHuge records first):
-//   1. bins: the set's first kBStarBinRec records go to their angular bins
-//      around the centre of the octagon's box, in shared memory; each bin
-//      keeps its point farthest from the centre.  A set's records come in
-//      the order of its points, so these are a sample of them when the
-//      points are in random order; any other order only makes the polygon
-//      smaller;
-//   2. the polygon (star_finish, star.cuh): its vertices are re-read from
-//      the input by index and it is checked exactly; without one the set is
-//      left as it is;
-//   3. the records whose point is not strictly inside the polygon are
-//      copied to the set's region of the scatter buffer (free until the
-//      bucketed path), then back, with the per-queue counts recounted.
-// A point strictly inside the polygon is an interior point of the set's hull
-// (star.cuh), so the records left have the same hull.  The sets then take
-// bt_hull's one-block path, or the bucketed path when still too many.
-//
-// Each warp streams a contiguous range of the records with the loads of its
-// next step in flight while it works on the current one; no step waits for
-// the other warps.
-constexpr int kBStarThreads = 512;
-constexpr int kBStarU = 8;                    // records per lane and step
-constexpr unsigned kBStarBinRec = 1u << 19;   // records binned (64 per bin)
-constexpr size_t kBStarAOff = (sizeof(StarPoly) + 15) / 16 * 16;
-constexpr size_t kBStarSmem = kBStarAOff + (sizeof(int2) + sizeof(unsigned short)) * kStarBins;
-static_assert(sizeof(unsigned long long) * kStarBins <= (sizeof(int2) + sizeof(unsigned short)) * kStarBins,
-              "the bins fit in work area A");
-
-// One step of a warp: records [r, r + 32 kBStarU) of a range ending at hi,
-// record r + 32 u + lane in slot u.
-__device__ __forceinline__ void bt_star_load(const uint32_t* __restrict__ keys, const uint64_t* __restrict__ vals,
-                                             long long rb, unsigned r, unsigned hi, uint32_t (&kk)[kBStarU],
-                                             uint64_t (&vv)[kBStarU]) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int u = 0; u < kBStarU; ++u) {
-        const unsigned j = r + 32u * u + lane;
-        kk[u] = j < hi ? __ldcg(keys + rb + j) : 0u;
-        vv[u] = j < hi ? __ldcg(vals + rb + j) : 0ull;
-    }
-}
-
-__device__ __forceinline__ void bt_record_xy(uint32_t k, uint64_t v, int& X, int& Y) {
-    frame_to_xy((int)(k >> kKeyBits), (int)(k & kKeyMask), (int)(v >> 31), X, Y);
-}
-
-__global__ void __launch_bounds__(kBStarThreads, 1) bt_star(BArgs a) {
-    extern __shared__ __align__(16) char dyn[];
-    StarPoly& P = *reinterpret_cast<StarPoly*>(dyn);
-    unsigned long long* bins = reinterpret_cast<unsigned long long*>(dyn + kBStarAOff);
-    int2* va = reinterpret_cast<int2*>(dyn + kBStarAOff);
-    unsigned short* ba = reinterpret_cast<unsigned short*>(dyn + kBStarAOff + sizeof(int2) * kStarBins);
-    constexpr int kWarps = kBStarThreads / 32;
-    constexpr unsigned kStep = 32u * kBStarU;
-    __shared__ unsigned s_kept, s_q[4];
-    __shared__ int s_set, s_cx, s_cy;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const unsigned n_front = a.star_ctr[0], n_back = a.star_ctr[1];
-    for (;;) {
-        if (tid == 0) {
-            const unsigned g = atomicAdd(&a.star_ctr[2], 1u);
-            s_set = g < n_front ? a.star_list[g]
-                                : (g - n_front < n_back ? a.star_list[a.k - 1 - (int)(g - n_front)] : -1);
-        }
-        __syncthreads();
-        const int i = s_set;
-        if (i < 0) return;
-        Ctl* c = a.ctl + i;
-        const long long base = a.offsets[i], ni = a.offsets[i + 1] - base;
-        const long long rb = region_base(a, i);
-        const unsigned m = c->count;
-        if (tid == 0) {
-            s_cx = (c->oct.vx[W] + c->oct.vx[E]) / 2;
-            s_cy = (c->oct.vy[S] + c->oct.vy[N]) / 2;
-            s_kept = 0u;
-        }
-        if (tid < 4) s_q[tid] = 0u;
-        for (int b = tid; b < kStarBins; b += kBStarThreads) bins[b] = 0ull;
-        __syncthreads();
-        const int cx = s_cx, cy = s_cy;
-        // 1. bins: warp w takes [w per, (w + 1) per) of the first mb records
-        {
-            const unsigned mb = min(m, kBStarBinRec);
-            const unsigned per = ((mb + kWarps - 1) / kWarps + kStep - 1) / kStep * kStep;
-            const unsigned lo = min(mb, warp * per), hi = min(mb, lo + per);
-            uint32_t kk[kBStarU];
-            uint64_t vv[kBStarU];
-            bt_star_load(a.keys, a.vals, rb, lo, hi, kk, vv);
-            for (unsigned r = lo; r < hi; r += kStep) {
-                uint32_t nk[kBStarU];
-                uint64_t nv[kBStarU];
-                bt_star_load(a.keys, a.vals, rb, r + kStep, hi, nk, nv);
-#pragma unroll
-                for (int u = 0; u < kBStarU; ++u) {
-                    if (r + 32u * u + lane >= hi) continue;
-                    int X, Y;
-                    bt_record_xy(kk[u], vv[u], X, Y);
-                    const int dx = X - cx, dy = Y - cy;
-                    const unsigned long long d2 = (unsigned long long)((long long)dx * dx + (long long)dy * dy);
-                    const unsigned long long key = ((d2 >> 17) << 32) | (vv[u] & 0x7FFFFFFFull);
-                    const int b = star_bin(dx, dy);
-                    if (key > bins[b]) atomicMax(&bins[b], key);
-                }
-#pragma unroll
-                for (int u = 0; u < kBStarU; ++u) {
-                    kk[u] = nk[u];
-                    vv[u] = nv[u];
-                }
-            }
-        }
-        __syncthreads();
-        // 2. the polygon
-        const int K = star_finish<kBStarThreads, true>(bins, a.pts + 2 * base, ni, cx, cy, va, ba, P, c);
-        if (tid == 0) c->star_k = K;
-        if (K == 0) {
-            __syncthreads();
-            continue;
-        }
-        // 3. the records not strictly inside go to the scatter buffer
-        unsigned t0 = 0u, t1 = 0u, t2 = 0u, t3 = 0u;   // kept per queue (lane counts)
-        {
-            const unsigned per = ((m + kWarps - 1) / kWarps + kStep - 1) / kStep * kStep;
-            const unsigned lo = min(m, warp * per), hi = min(m, lo + per);
-            uint32_t kk[kBStarU];
-            uint64_t vv[kBStarU];
-            bt_star_load(a.keys, a.vals, rb, lo, hi, kk, vv);
-            for (unsigned r = lo; r < hi; r += kStep) {
-                uint32_t nk[kBStarU];
-                uint64_t nv[kBStarU];
-                bt_star_load(a.keys, a.vals, rb, r + kStep, hi, nk, nv);
-#pragma unroll
-                for (int u = 0; u < kBStarU; ++u) {
-                    bool keep = r + 32u * u + lane < hi;
-                    if (keep) {
-                        int X, Y;
-                        bt_record_xy(kk[u], vv[u], X, Y);
-                        keep = !star_inside(X - cx, Y - cy, P);
-                    }
-                    const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
-                    if (bal == 0u) continue;
-                    unsigned pos = 0u;
-                    if (lane == 0) pos = atomicAdd(&s_kept, (unsigned)__popc(bal));
-                    pos = __shfl_sync(0xFFFFFFFFu, pos, 0) + (unsigned)__popc(bal & lanemask_lt());
-                    if (keep) {
-                        a.kP[rb + pos] = kk[u];
-                        a.vP[rb + pos] = vv[u];
-                        const unsigned q = kk[u] >> kKeyBits;
-                        t0 += q == 0u;
-                        t1 += q == 1u;
-                        t2 += q == 2u;
-                        t3 += q == 3u;
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < kBStarU; ++u) {
-                    kk[u] = nk[u];
-                    vv[u] = nv[u];
-                }
-            }
-        }
-        t0 = __reduce_add_sync(0xFFFFFFFFu, t0);
-        t1 = __reduce_add_sync(0xFFFFFFFFu, t1);
-        t2 = __reduce_add_sync(0xFFFFFFFFu, t2);
-        t3 = __reduce_add_sync(0xFFFFFFFFu, t3);
-        if (lane == 0) {
-            atomicAdd(&s_q[0], t0);
-            atomicAdd(&s_q[1], t1);
-            atomicAdd(&s_q[2], t2);
-            atomicAdd(&s_q[3], t3);
-        }
-        __syncthreads();
-        const unsigned w = s_kept;
-        for (unsigned j = tid; j < w; j += kBStarThreads) {   // back into the set's records
-            a.keys[rb + j] = __ldcg(a.kP + rb + j);
-            a.vals[rb + j] = __ldcg(a.vP + rb + j);
-        }
-        if (tid < 4) c->counts4[tid] = s_q[tid];
-        if (tid == 0) c->count = w;
-        __syncthreads();
     }
 }
 
@@ -795,6 +922,8 @@ __global__ void __launch_bounds__(kBHullThreads, 1) bt_hull(BArgs a) {
 struct BWork {
     char* base = nullptr;
     size_t bytes = 0;
+    int k = -1;                           // the last call's sets, and where its
+    size_t ctl = 0, big = 0, redo = 0;    // control blocks and flags are
 };
 static std::mutex g_bmu;
 static std::map<std::pair<int, cudaStream_t>, BWork> g_bws;
@@ -802,17 +931,18 @@ static std::map<std::pair<int, cudaStream_t>, BWork> g_bws;
 static size_t bt_align(size_t x) { return (x + 255) / 256 * 256; }
 
 struct BLayout {
-    size_t ctl, keys, vals, tiles, tmap, rmap, big, redo, star_ctr, star_list;
+    size_t ctl, keys, vals, rmap, big, redo, star_ctr, star_list, star_slot, star_bins, star_polys;
     size_t seg_nb, seg_bbase, seg_lo, seg_scale, seg_tbase, rt_base, totals;
     size_t bcount, bcur, bstart, blen, bu, bv, bi, kP, vP, cu, cv, ci, clen, ctmap, counters;
-    size_t zero_from, zero_to;   // bucket counters: cleared before each batch
+    size_t zero_from, zero_to;   // star bins and bucket counters: cleared before each batch
     size_t total;
     unsigned bcap, tcap, rtcap;
 };
 
 // big_pts: points of the sets that can exceed one block (more than kMidCap
 // points), big_sets: how many; they bound the buckets and chain tiles.
-static BLayout bt_layout(long long total, int k, long long big_pts, long long big_sets, long long tiles) {
+// slots: sets with a star slot (at least kBStarMinPts points).
+static BLayout bt_layout(long long total, int k, long long big_pts, long long big_sets, long long slots) {
     BLayout L;
     const long long cap = total + 16ll * k + 16;
     size_t o = 0;
@@ -827,14 +957,14 @@ static BLayout bt_layout(long long total, int k, long long big_pts, long long bi
     L.ctl = take(sizeof(Ctl) * (size_t)k);
     L.keys = take(sizeof(uint32_t) * (size_t)cap);
     L.vals = take(sizeof(uint64_t) * (size_t)cap);
-    L.tiles = take(sizeof(int) * ((size_t)k + 1));
-    L.tmap = take(sizeof(int) * ((size_t)tiles + 1));
     L.rtcap = (unsigned)((big_pts + 16 * big_sets) / kBLTile + big_sets + 1);
     L.rmap = take(sizeof(int) * (size_t)L.rtcap);
     L.big = take((size_t)k);
     L.redo = take((size_t)k);
     L.star_ctr = take(4 * 4);
     L.star_list = take(sizeof(int) * (size_t)k);
+    L.star_slot = take(sizeof(int) * (size_t)k);
+    L.star_polys = take(sizeof(StarPoly) * (size_t)slots);
     L.seg_nb = take(4 * nseg);
     L.seg_bbase = take(4 * (nseg + 1));
     L.seg_lo = take(4 * nseg);
@@ -842,10 +972,11 @@ static BLayout bt_layout(long long total, int k, long long big_pts, long long bi
     L.seg_tbase = take(4 * (nseg + 1));
     L.rt_base = take(4 * ((size_t)k + 1));
     L.totals = take(4 * 8);
-    // Cleared before every batch: bucket counters and the merge tree's
-    // arrival counters (the layout moves with the batch's sizes, so memory
-    // that held other data last time can land here).
+    // Cleared before every batch: the star bins, bucket counters and the
+    // merge tree's arrival counters (the layout moves with the batch's
+    // sizes, so memory that held other data last time can land here).
     L.zero_from = o;
+    L.star_bins = take(sizeof(unsigned long long) * kStarBins * (size_t)slots);
     L.bcount = take(4 * (size_t)L.bcap);
     L.bcur = take(4 * (size_t)L.bcap);
     L.counters = take(4 * (size_t)kMaxLevels * L.tcap);
@@ -867,9 +998,9 @@ static BLayout bt_layout(long long total, int k, long long big_pts, long long bi
 }
 
 static int bt_workspace(int dev, cudaStream_t s, long long total, int k, long long big_pts, long long big_sets,
-                        long long tiles, char** base, BLayout* L) {
+                        long long slots, char** base, BLayout* L) {
     std::lock_guard<std::mutex> lk(g_bmu);
-    *L = bt_layout(total, k, big_pts, big_sets, tiles);
+    *L = bt_layout(total, k, big_pts, big_sets, slots);
     BWork& w = g_bws[std::make_pair(dev, s)];
     if (w.bytes < L->total) {
         if (w.base) {
@@ -888,13 +1019,18 @@ static int bt_workspace(int dev, cudaStream_t s, long long total, int k, long lo
         w.bytes = want;
     }
     *base = w.base;
+    w.k = k;
+    w.ctl = L->ctl;
+    w.big = L->big;
+    w.redo = L->redo;
     return CH_OK;
 }
 
 int reserve_batched(int dev, cudaStream_t s, long long n, int k) {
     char* base = nullptr;
     BLayout L;
-    return bt_workspace(dev, s, n, std::max(k, 1), n, std::max(k, 1), n / kBTileMin + std::max(k, 1), &base, &L);
+    return bt_workspace(dev, s, n, std::max(k, 1), n, std::max(k, 1), std::min((long long)std::max(k, 1), n / kBStarMinPts),
+                        &base, &L);
 }
 
 void release_batched_stream(int dev, cudaStream_t s) {
@@ -936,7 +1072,8 @@ static void bt_occupancy(int* occ) {
     int a = 0, b = 0;
     cudaFuncSetAttribute(bt_extremes<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt_ext_smem(T, P));
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, bt_extremes<T, P>, T, bt_ext_smem(T, P));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, bt_filter<T, P>, T, 0);
+    cudaFuncSetAttribute(bt_filter<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt_ext_smem(T, P));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, bt_filter<T, P>, T, bt_ext_smem(T, P));
     occ[0] = std::max(1, a);
     occ[1] = std::max(1, b);
 }
@@ -960,7 +1097,8 @@ static int bt_configure(int dev, BtDevice* out) {
     d.name = prop.name;
     if (cudaFuncSetAttribute(bt_hull, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBHullSmem) != cudaSuccess)
         return CH_ECUDA;
-    if (cudaFuncSetAttribute(bt_star, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBStarSmem) != cudaSuccess)
+    if (cudaFuncSetAttribute(bt_star_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBStarSmem) !=
+        cudaSuccess)
         return CH_ECUDA;
     if (configure_batched_large() != cudaSuccess) return CH_ECUDA;
     bt_occupancy<128, 16>(d.occ[0]);
@@ -975,10 +1113,10 @@ static int bt_configure(int dev, BtDevice* out) {
     return CH_OK;
 }
 
-static void launch_bt_tiles(int shape, bool filter, const BArgs& a, int nt, int grid, cudaStream_t s) {
+static void launch_bt_tiles(int shape, bool filter, const BArgs& a, int grid, cudaStream_t s) {
 #define CH_BT_CASE(i, T, P)                                                   \
     case i:                                                                   \
-        if (filter) bt_filter<T, P><<<grid, T, 0, s>>>(a, nt);                \
+        if (filter) bt_filter<T, P><<<grid, T, bt_ext_smem(T, P), s>>>(a);    \
         else bt_extremes<T, P><<<grid, T, bt_ext_smem(T, P), s>>>(a);         \
         break;
     switch (shape) {
@@ -1091,48 +1229,48 @@ static void tune_save_locked() {
     rename(tmp.c_str(), path);
 }
 
-static long long count_tiles(const std::vector<int64_t>& off, int k, int tile) {
-    long long t = 0;
-    for (int i = 0; i < k; ++i) t += (off[i + 1] - off[i] + tile - 1) / tile;
-    return t;
-}
-
 // ---------------------------------------------------------------------------
 // The device work of one call.
 struct BtCall {
     BArgs a;
     BLArgs b;
-    int nt, shape, grid_e, grid_f, sms;
+    int shape, grid_e, grid_f, sms;
     char* base;
     BLayout L;
 };
 
-static void bt_enqueue_tiles(const BtCall& c, cudaStream_t s) {
+static int bt_enqueue_tiles(const BtCall& c, cudaStream_t s) {
     const BArgs& a = c.a;
     {
         ProfScope p("batched_prep", s);
-        bt_init<<<(a.k + 255) / 256, 256, 0, s>>>(a);
-        bt_scan<<<1, 1024, 0, s>>>(a.tile_base, a.tile_map, a.k);
+        if (cudaMemsetAsync(c.base + c.L.zero_from, 0, c.L.zero_to - c.L.zero_from, s) != cudaSuccess) return CH_ECUDA;
+        bt_init<<<(a.k + 7) / 8, 256, 0, s>>>(a);
+        bt_slots<<<1, 1024, 0, s>>>(a);
     }
     {
         ProfScope p("batched_extremes", s);
-        launch_bt_tiles(c.shape, false, a, c.nt, c.grid_e, s);
+        launch_bt_tiles(c.shape, false, a, c.grid_e, s);
     }
     { ProfScope p("batched_octagon", s); bt_octagon<<<a.k, kBOctThreads, 0, s>>>(a); }
     {
-        ProfScope p("batched_filter", s);
-        launch_bt_tiles(c.shape, true, a, c.nt, c.grid_f, s);
+        ProfScope p("batched_star", s);
+        bt_star_bin<<<c.sms * 8, kBStarBinThreads, 0, s>>>(a);
+        bt_star_build<<<c.sms, kBStarThreads, kBStarSmem, s>>>(a);
     }
+    {
+        ProfScope p("batched_filter", s);
+        launch_bt_tiles(c.shape, true, a, c.grid_f, s);
+    }
+    return CH_OK;
 }
 
 static int bt_enqueue(const BtCall& c, unsigned char* redo, cudaStream_t s) {
-    bt_enqueue_tiles(c, s);
+    const int st = bt_enqueue_tiles(c, s);
+    if (st != CH_OK) return st;
     { ProfScope p("batched_hull_small", s); bt_hull_small<<<c.a.k, kBSmallThreads, 0, s>>>(c.a); }
-    { ProfScope p("batched_star", s); bt_star<<<c.sms, kBStarThreads, kBStarSmem, s>>>(c.a); }
     { ProfScope p("batched_hull", s); bt_hull<<<c.a.k, kBHullThreads, kBHullSmem, s>>>(c.a); }
     // Sets with more records than one block holds: all together through the
     // bucketed path.
-    if (cudaMemsetAsync(c.base + c.L.zero_from, 0, c.L.zero_to - c.L.zero_from, s) != cudaSuccess) return CH_ECUDA;
     launch_batched_large(c.b, redo, c.sms, s);
     return cudaGetLastError() == cudaSuccess ? CH_OK : CH_ECUDA;
 }
@@ -1205,15 +1343,13 @@ static void drop_all_batched_graphs() {
     g_bgraphs.clear();
 }
 
-static void bt_set_shape(BtCall& c, const BtDevice& d, const std::vector<int64_t>& off, int shape) {
+static void bt_set_shape(BtCall& c, const BtDevice& d, int shape) {
     const BtShape& sh = kBtShapes[shape];
     c.shape = shape;
-    c.a.tile = sh.threads * sh.per;
-    c.nt = (int)count_tiles(off, c.a.k, c.a.tile);
     c.a.wtile = 32 * sh.per;
     c.a.nwt = (c.a.total - c.a.head) / c.a.wtile;
     c.grid_e = (int)std::max(1ll, std::min(c.a.nwt, (long long)d.sms * d.occ[shape][0]));
-    c.grid_f = std::max(1, std::min(c.nt, d.sms * d.occ[shape][1]));
+    c.grid_f = (int)std::max(1ll, std::min(c.a.nwt, (long long)d.sms * d.occ[shape][1]));
 }
 
 // Times every shape on this batch (tile kernels only, best of two runs).
@@ -1224,11 +1360,14 @@ static int bt_tune(BtCall& c, const BtDevice& d, const std::vector<int64_t>& off
     *best = 2;
     int st = CH_OK;
     for (int i = 0; i < kNumBtShapes && st == CH_OK; ++i) {
-        bt_set_shape(c, d, off, i);
+        bt_set_shape(c, d, i);
         double t_min = 1e30;
         for (int rep = 0; rep < 2; ++rep) {
             cudaEventRecord(e0, s);
-            bt_enqueue_tiles(c, s);
+            if (bt_enqueue_tiles(c, s) != CH_OK) {
+                st = CH_ECUDA;
+                break;
+            }
             cudaEventRecord(e1, s);
             float ms = 0.f;
             if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
@@ -1313,17 +1452,17 @@ int hull_batched_impl(const float* pts, const int64_t* offsets, int32_t k, int32
         if (cudaStreamSynchronize(s) != cudaSuccess) return CH_ECUDA;
     }
     if (off[0] != 0) return CH_EINVAL;
-    long long big_pts = 0, big_sets = 0;
+    long long big_pts = 0, big_sets = 0, slots = 0;
     for (int i = 0; i < k; ++i) {
         if (off[i + 1] < off[i] || off[i + 1] - off[i] > CH_MAX_POINTS) return CH_EINVAL;
         if (off[i + 1] - off[i] + 12 > kMidCap) {
             big_pts += off[i + 1] - off[i];
             ++big_sets;
         }
+        if (off[i + 1] - off[i] >= kBStarMinPts) ++slots;
     }
-    const long long max_tiles = count_tiles(off, k, kBTileMin);   // the most tiles of any shape
-    if (max_tiles > INT32_MAX) return CH_EINVAL;
     const int64_t total = off[k];
+    if (total / kBWarpTileMin + 2 > (int64_t)UINT32_MAX) return CH_EINVAL;   // 32-bit tile codes
     int st = check_points_args(pts, total);
     if (st != CH_OK) return st;
     if (total > 0 && !out_idx) return CH_EINVAL;
@@ -1332,7 +1471,7 @@ int hull_batched_impl(const float* pts, const int64_t* offsets, int32_t k, int32
     BtDevice d;
     if ((st = bt_configure(dev, &d)) != CH_OK) return st;
     BtCall c;
-    if ((st = bt_workspace(dev, s, total, k, big_pts, big_sets, max_tiles, &c.base, &c.L)) != CH_OK) return st;
+    if ((st = bt_workspace(dev, s, total, k, big_pts, big_sets, slots, &c.base, &c.L)) != CH_OK) return st;
     const BLayout& L = c.L;
     char* base = c.base;
     c.sms = d.sms;
@@ -1343,8 +1482,6 @@ int hull_batched_impl(const float* pts, const int64_t* offsets, int32_t k, int32
     a.ctl = (Ctl*)(base + L.ctl);
     a.keys = (uint32_t*)(base + L.keys);
     a.vals = (uint64_t*)(base + L.vals);
-    a.tile_base = (int*)(base + L.tiles);
-    a.tile_map = (int*)(base + L.tmap);
     a.out_idx = out_idx;
     a.out_n = out_n;
     a.big = (unsigned char*)(base + L.big);
@@ -1353,8 +1490,9 @@ int hull_batched_impl(const float* pts, const int64_t* offsets, int32_t k, int32
     a.head = (total > 0 && (reinterpret_cast<uintptr_t>(pts) & 15u) != 0u) ? 1 : 0;
     a.star_ctr = (unsigned*)(base + L.star_ctr);
     a.star_list = (int*)(base + L.star_list);
-    a.kP = (uint32_t*)(base + L.kP);
-    a.vP = (uint64_t*)(base + L.vP);
+    a.star_slot = (int*)(base + L.star_slot);
+    a.star_bins = (unsigned long long*)(base + L.star_bins);
+    a.star_polys = (StarPoly*)(base + L.star_polys);
     BLArgs& b = c.b;
     b.pts = pts;
     b.offsets = offsets;
@@ -1402,7 +1540,7 @@ int hull_batched_impl(const float* pts, const int64_t* offsets, int32_t k, int32
         else if (!allow_tune) shape = nearest_tuned_locked(d, total, k);
     }
     if (shape < 0 && (st = bt_tune(c, d, off, s, &shape)) != CH_OK) return st;
-    bt_set_shape(c, d, off, shape);
+    bt_set_shape(c, d, shape);
     if ((st = bt_launch_graph(c, redo, dev, s)) != CH_OK) return st;
     // Sets the bucketed path could not finish (a bucket chain too long): the
     // single-hull path, one by one, once their flags are on the host.
@@ -1418,6 +1556,38 @@ int hull_batched_impl(const float* pts, const int64_t* offsets, int32_t k, int32
 }  // namespace ch
 
 using namespace ch;
+
+extern "C" int ch_batched_counters(void* stream, int32_t k, int64_t* out) {
+    if (!out || k < 1) return CH_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CH_ECUDA;
+    char* base = nullptr;
+    size_t o_ctl = 0, o_big = 0, o_redo = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_bmu);
+        auto it = g_bws.find(std::make_pair(dev, s));
+        if (it == g_bws.end() || !it->second.base || it->second.k != k) return CH_EINVAL;
+        base = it->second.base;
+        o_ctl = it->second.ctl;
+        o_big = it->second.big;
+        o_redo = it->second.redo;
+    }
+    std::vector<Ctl> ctl((size_t)k);
+    std::vector<unsigned char> big((size_t)k), redo((size_t)k);
+    if (cudaMemcpyAsync(ctl.data(), base + o_ctl, sizeof(Ctl) * (size_t)k, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(big.data(), base + o_big, (size_t)k, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(redo.data(), base + o_redo, (size_t)k, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return CH_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return CH_ECUDA;
+    for (int i = 0; i < k; ++i) {
+        out[4 * (size_t)i] = (int64_t)ctl[i].count;
+        out[4 * (size_t)i + 1] = (int64_t)ctl[i].star_k;
+        out[4 * (size_t)i + 2] = (int64_t)ctl[i].status;
+        out[4 * (size_t)i + 3] = redo[i] ? 2 : big[i] ? 1 : 0;
+    }
+    return 4;
+}
 
 // Tile shape that ch_hull_batched uses for a batch of this size class on the
 // current device: from the environment, else the tuned choice (0 when the

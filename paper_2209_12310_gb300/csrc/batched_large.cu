@@ -66,15 +66,17 @@ __global__ void __launch_bounds__(1024) btl_prep(BLArgs a) {
         if (a.big[i]) {
             const Ctl* c = a.ctl + i;
             nb = bk_buckets_for(c->counts4[q]);
-            // Records that a star polygon left (bt_star) are mostly near the
-            // hull, a large share of them hull vertices when the set is
-            // small: at most kBkNearHull of them per bucket, or a quarter of
-            // that when at most 1 / 16 of the set's points are left.  With
-            // per / kBkAvg of the points left these buckets stay within the
-            // set's share of the workspace (n / kBkAvg + 4 kBkMinQ + 4).
+            // Records that a star polygon left are mostly near the hull, a
+            // large share of them hull vertices: 16 of them per bucket, or
+            // 32 or kBkNearHull (64) when the smaller size does not fit the
+            // set's share of the workspace (n / kBkAvg + 4 kBkMinQ + 4
+            // buckets): 16 fits with at most n / 16 records left, 32 with
+            // n / 8, 64 with n / 4.
             const long long ni = a.offsets[i + 1] - a.offsets[i];
-            if (c->star_k > 0 && 4ll * c->count <= ni) {
-                const unsigned per = 16ll * c->count <= ni ? kBkNearHull / 4 : kBkNearHull;
+            const long long m = c->count;
+            if (c->star_k > 0 && 4 * m <= ni) {
+                unsigned per = kBkNearHull / 4;
+                while (per < (unsigned)kBkNearHull && (long long)(kBkAvg / per) * m > ni) per *= 2;
                 const unsigned nh = (c->counts4[q] + per - 1) / per;
                 nb = nb > nh ? nb : nh;
             }

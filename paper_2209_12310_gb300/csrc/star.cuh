@@ -31,11 +31,16 @@ namespace ch {
 //   rin  per bin, an integer radius no larger than the distance from c to
 //        the line of any edge whose wedge meets the bin or its two
 //        neighbours on either side: a point of the bin closer to c than that
-//        is strictly inside (0 when no bound was found).
+//        is strictly inside (0 when no bound was found);
+//   rmin the smallest line radius of all edges: a point closer to c than
+//        that is strictly inside, whatever its bin (it lies in some wedge,
+//        on the inner side of that wedge's edge line).
 struct StarPoly {
     int2 v[kStarBins + 2];
     unsigned short tbl[kStarBins];
     unsigned rin[kStarBins];
+    unsigned rmin;
+    unsigned pad[3];
 };
 
 // Angular bin of an offset (dx, dy) from c: a pseudo-angle in [0, 4) that
@@ -284,12 +289,18 @@ __device__ int star_finish(const unsigned long long* bins, const float* __restri
     // smallest over the edges whose wedges can hold its points: from the last
     // vertex before bin b - 2 to the first vertex from bin b + 2 on
     unsigned* er = reinterpret_cast<unsigned*>(va);
+    if (t == 0) P.rmin = 0xFFFFFFFFu;
+    __syncthreads();
+    unsigned emin = 0xFFFFFFFFu;
     for (int e = t; e < K; e += T) {
         const int2 a = P.v[e], c2 = P.v[e + 1];
         const long long o = (long long)a.x * c2.y - (long long)a.y * c2.x;   // > 0 (checked above)
         const long long dx = (long long)c2.x - a.x, dy = (long long)c2.y - a.y;
         er[e] = star_line_radius(o, dx * dx + dy * dy);
+        emin = min(emin, er[e]);
     }
+    emin = __reduce_min_sync(0xFFFFFFFFu, emin);
+    if (lane == 0 && emin != 0xFFFFFFFFu) atomicMin(&P.rmin, emin);
     __syncthreads();
     CH_TL(ctl, 12, 1);
     for (int b = t; b < kStarBins; b += T) {
