@@ -80,8 +80,12 @@ struct BArgs {
     int* star_slot;           // k: the set's star slot, or -1
     unsigned long long* star_bins;   // kStarBins per slot (zeroed before every batch)
     StarPoly* star_polys;     // one per slot
-    unsigned* star_ctr;       // bt_star_build's work list: [0] dense sets listed, [1] taken
+    unsigned* star_ctr;       // work lists: [0] dense sets listed, [1] taken by bt_star_build;
+                              // [2] / [3] sets for bt_star_refine from the front / back, [4] taken
     int* star_list;           // k entries
+    int* refine_list;         // k entries
+    uint32_t* kP;             // the bucketed path's scatter buffer (set regions as keys / vals)
+    uint64_t* vP;
 };
 
 __device__ __forceinline__ long long region_base(const BArgs& a, int i) { return a.offsets[i] + 16ll * i; }
@@ -112,7 +116,7 @@ __global__ void __launch_bounds__(256) bt_init(BArgs a) {
         c->star_cy = 0;
         a.big[i] = 0;
     }
-    if (i == 0 && lane == 0) a.star_ctr[0] = a.star_ctr[1] = 0u;
+    if (i == 0 && lane < 5) a.star_ctr[lane] = 0u;
 }
 
 // Star slots (one block of 1024 threads): the sets of at least kBStarMinPts
@@ -447,75 +451,92 @@ struct BtWarpSmem {
     float qx[kBtQueue], qy[kBtQueue];   // points waiting for the exact tests
     unsigned qi[kBtQueue];
     unsigned char lanes[32];         // lanes whose tile the inner region did not settle
+    Ctl* c;                          // the warp's set: control block, record region,
+    long long rb;                    // star polygon and centre,
+    const StarPoly* P;
+    int cx, cy;
+    unsigned cnt;                    // records staged,
+    unsigned nq[4];                  // records per queue
 };
 
-// A warp's current set (warp-uniform registers).
+// A warp's current set: what the streaming loop reads stays in registers
+// (warp-uniform); what the exact path needs is in the warp's shared memory.
 struct BtWarpSet {
     int set = -1;
-    Ctl* c = nullptr;
-    long long base = 0, rb = 0;
+    long long base = 0;
     const StarPoly* P = nullptr;   // the set's star polygon, if any
     int cx = 0, cy = 0;
     unsigned rmin = 0u;            // its inscribed radius
     bool skip = true;              // empty or failed: nothing to classify
-    unsigned cnt = 0u;             // records staged
     unsigned qn = 0u;              // points queued
-    unsigned nq[4] = {0u, 0u, 0u, 0u};   // records per queue since the last flush
 };
 
-__device__ __forceinline__ void bt_flush_recs(BtWarpSmem& m, BtWarpSet& w, uint32_t* keys, uint64_t* vals) {
+__device__ __forceinline__ void bt_flush_recs(BtWarpSmem& m, uint32_t* keys, uint64_t* vals) {
     const int lane = threadIdx.x & 31;
-    if (w.cnt == 0u) return;
+    const unsigned cnt = m.cnt;
+    if (cnt == 0u) return;
     unsigned base = 0u;
-    if (lane == 0) base = atomicAdd(&w.c->count, w.cnt);
+    if (lane == 0) base = atomicAdd(&m.c->count, cnt);
     base = __shfl_sync(0xFFFFFFFFu, base, 0);
-    for (unsigned j = lane; j < w.cnt; j += 32) {
-        keys[w.rb + base + j] = m.key[j];
-        vals[w.rb + base + j] = m.val[j];
+    for (unsigned j = lane; j < cnt; j += 32) {
+        keys[m.rb + base + j] = m.key[j];
+        vals[m.rb + base + j] = m.val[j];
     }
     __syncwarp();
-    w.cnt = 0u;
+    if (lane == 0) m.cnt = 0u;
+    __syncwarp();
 }
 
-// Warp-collective: one point per lane of the warp's set (valid = false for
-// none), local index li; fast_done: its star radius test already failed.
-__device__ __forceinline__ void bt_filter_point(const BArgs& a, BtWarpSet& w, BtWarpSmem& m, bool valid,
-                                                bool fast_done, float x, float y, unsigned li) {
+// Warp-collective, out of line: one point per lane of the warp's set (valid
+// = false for none), local index li; fast_done: its star radius bound has
+// already failed.  The exact star test, the hull-rule classification, the
+// support-line reduction and the staging of the kept records.
+__device__ __noinline__ void bt_classify32(uint32_t* keys, uint64_t* vals, BtWarpSmem& m, bool valid,
+                                           bool fast_done, float x, float y, unsigned li) {
+    const int lane = threadIdx.x & 31;
     const Octagon& so = m.o;
+    const StarPoly* P = m.P;
     int r = -1, X = 0, Y = 0;
     if (valid) {
         X = __float2int_rn(x);
         Y = __float2int_rn(y);
         if (!in_inner(so, X, Y)) {
             bool drop = false;
-            if (w.P) {
-                const int px = X - w.cx, py = Y - w.cy, bn = star_bin(px, py);
-                drop = (!fast_done && star_inside_fast(px, py, bn, *w.P)) || star_inside_exact(px, py, bn, *w.P);
+            if (P) {
+                const int px = X - m.cx, py = Y - m.cy, bn = star_bin(px, py);
+                drop = (!fast_done && star_inside_fast(px, py, bn, *P)) || star_inside_exact(px, py, bn, *P);
             }
             if (!drop) r = classify_hull(x, y, so);
         }
     }
     bool keep = r >= 0;
     if (!__any_sync(0xFFFFFFFFu, keep)) return;
-    if (reduce_on_line(so, keep, X, Y, li, w.c)) keep = false;
+    if (reduce_on_line(so, keep, X, Y, li, m.c)) keep = false;
     const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
     if (!bal) return;
+    unsigned nq[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) w.nq[q] += (unsigned)__popc(__ballot_sync(0xFFFFFFFFu, keep && r == q));
-    if (w.cnt + (unsigned)__popc(bal) > (unsigned)kBtWarpRecs) bt_flush_recs(m, w, a.keys, a.vals);
+    for (int q = 0; q < 4; ++q) nq[q] = (unsigned)__popc(__ballot_sync(0xFFFFFFFFu, keep && r == q));
+    if (m.cnt + (unsigned)__popc(bal) > (unsigned)kBtWarpRecs) bt_flush_recs(m, keys, vals);
+    const unsigned cnt = m.cnt;
     if (keep) {
         uint32_t u, v;
         queue_frame(r, X, Y, u, v);
-        const unsigned pos = w.cnt + (unsigned)__popc(bal & lanemask_lt());
+        const unsigned pos = cnt + (unsigned)__popc(bal & lanemask_lt());
         m.key[pos] = make_key(r, u);
         m.val[pos] = make_val(v, li);
     }
-    w.cnt += (unsigned)__popc(bal);
+    __syncwarp();
+    if (lane == 0) {
+        m.cnt = cnt + (unsigned)__popc(bal);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) m.nq[q] += nq[q];
+    }
     __syncwarp();
 }
 
 // Warp-collective: queues the lanes' points with need = true; full rounds of
-// 32 go through bt_filter_point.
+// 32 go through bt_classify32.
 __device__ __forceinline__ void bt_queue_push(const BArgs& a, BtWarpSet& w, BtWarpSmem& m, bool need, float x, float y,
                                               unsigned li) {
     const int lane = threadIdx.x & 31;
@@ -534,7 +555,7 @@ __device__ __forceinline__ void bt_queue_push(const BArgs& a, BtWarpSet& w, BtWa
         const float qx = m.qx[w.qn + lane], qy = m.qy[w.qn + lane];
         const unsigned qi = m.qi[w.qn + lane];
         __syncwarp();
-        bt_filter_point(a, w, m, true, true, qx, qy, qi);
+        bt_classify32(a.keys, a.vals, m, true, true, qx, qy, qi);
     }
 }
 
@@ -548,15 +569,10 @@ __device__ __forceinline__ void bt_warp_done(const BArgs& a, BtWarpSmem& m, BtWa
         const unsigned qi = valid ? m.qi[lane] : 0u;
         __syncwarp();
         w.qn = 0u;
-        bt_filter_point(a, w, m, valid, true, qx, qy, qi);
+        bt_classify32(a.keys, a.vals, m, valid, true, qx, qy, qi);
     }
-    bt_flush_recs(m, w, a.keys, a.vals);
-    if (lane == 0)
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (w.nq[q]) atomicAdd(&w.c->counts4[q], w.nq[q]);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) w.nq[q] = 0u;
+    bt_flush_recs(m, a.keys, a.vals);
+    if (lane < 4 && m.nq[lane]) atomicAdd(&m.c->counts4[lane], m.nq[lane]);
     w.set = -1;
 }
 
@@ -564,18 +580,27 @@ __device__ __forceinline__ void bt_warp_done(const BArgs& a, BtWarpSmem& m, BtWa
 __device__ __forceinline__ void bt_warp_set(const BArgs& a, int q, BtWarpSet& w, BtWarpSmem& m) {
     const int lane = threadIdx.x & 31;
     bt_warp_done(a, m, w);
+    __syncwarp();
+    Ctl* c = a.ctl + q;
     w.set = q;
-    w.c = a.ctl + q;
     w.base = a.offsets[q];
-    w.rb = region_base(a, q);
-    w.skip = *(volatile int*)&w.c->done != 0;   // bt_octagon's verdict on empty and failed sets
+    w.skip = *(volatile int*)&c->done != 0;   // bt_octagon's verdict on empty and failed sets
     const int slot = a.star_slot[q];
-    w.P = (slot >= 0 && w.c->star_k > 0) ? a.star_polys + slot : nullptr;
+    w.P = (slot >= 0 && c->star_k > 0) ? a.star_polys + slot : nullptr;
     w.rmin = w.P ? w.P->rmin : 0u;
-    w.cx = w.c->star_cx;
-    w.cy = w.c->star_cy;
+    w.cx = c->star_cx;
+    w.cy = c->star_cy;
+    if (lane == 0) {
+        m.c = c;
+        m.rb = region_base(a, q);
+        m.P = w.P;
+        m.cx = w.cx;
+        m.cy = w.cy;
+        m.cnt = 0u;
+    }
+    if (lane < 4) m.nq[lane] = 0u;
     if (!w.skip) {
-        const int* src = reinterpret_cast<const int*>(&w.c->oct);
+        const int* src = reinterpret_cast<const int*>(&c->oct);
         int* dst = reinterpret_cast<int*>(&m.o);
         for (int j = lane; j < (int)(sizeof(Octagon) / 4); j += 32) dst[j] = src[j];
     }
@@ -598,7 +623,7 @@ __device__ void bt_filter_global(const BArgs& a, long long lo, long long hi, BtW
             const long long j = j0 + lane;
             const bool valid = j < e;
             const float2 p = valid ? reinterpret_cast<const float2*>(a.pts)[j] : make_float2(0.0f, 0.0f);
-            bt_filter_point(a, w, m, valid, false, p.x, p.y, (unsigned)(j - qb));
+            bt_classify32(a.keys, a.vals, m, valid, false, p.x, p.y, (unsigned)(j - qb));
         }
     }
 }
@@ -705,7 +730,7 @@ __global__ void __launch_bounds__(T) bt_filter(BArgs a) {
                     for (int j = 0; j < P; ++j) {
                         const long long i = p0 + 2 * ((j >> 1) * 32 + lane) + (j & 1);
                         const float2 p = cur2[2 * ((j >> 1) * 32 + lane) + (j & 1)];
-                        bt_filter_point(a, w, m, i >= qb && i < qe, false, p.x, p.y, (unsigned)(i - qb));
+                        bt_classify32(a.keys, a.vals, m, i >= qb && i < qe, false, p.x, p.y, (unsigned)(i - qb));
                     }
                 }
             }
@@ -815,6 +840,178 @@ __global__ void __launch_bounds__(kBStarThreads, 1) bt_star_build(BArgs a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Second star polygon of a set whose records one block still cannot hold
+// (bt_hull_small's list): its records are the points outside the first
+// polygon (or, for a sparse set, outside the octagon), so binning all of
+// them puts a rim point in nearly every bin.  One block per set, persistent
+// over the list (the sets with more than kBRefineHuge records first):
+//   1. bins of all the set's records in shared memory, around the centre of
+//      the octagon's box (each bin keeps its point farthest from it);
+//   2. the polygon (star_finish: vertices re-read from the input by index,
+//      checked exactly); without one the set is left as it is;
+//   3. the records whose point is not strictly inside it are copied to the
+//      set's region of the scatter buffer (free until the bucketed path),
+//      then back, and the per-queue counts are recounted.
+// Each warp streams a contiguous range of the records with the loads of its
+// next step in flight while it works on the current one.
+constexpr int kBRefineU = 8;                    // records per lane and step
+constexpr unsigned kBRefineHuge = 1u << 16;     // records of the sets taken first
+static_assert(sizeof(unsigned long long) * kStarBins <= (sizeof(int2) + sizeof(unsigned short)) * kStarBins,
+              "the bins fit in work area A");
+
+// One step of a warp: records [r, r + 32 kBRefineU) of a range ending at hi,
+// record r + 32 u + lane in slot u.
+__device__ __forceinline__ void bt_refine_load(const uint32_t* __restrict__ keys, const uint64_t* __restrict__ vals,
+                                               long long rb, unsigned r, unsigned hi, uint32_t (&kk)[kBRefineU],
+                                               uint64_t (&vv)[kBRefineU]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int u = 0; u < kBRefineU; ++u) {
+        const unsigned j = r + 32u * u + lane;
+        kk[u] = j < hi ? __ldcg(keys + rb + j) : 0u;
+        vv[u] = j < hi ? __ldcg(vals + rb + j) : 0ull;
+    }
+}
+
+__device__ __forceinline__ void bt_record_xy(uint32_t k, uint64_t v, int& X, int& Y) {
+    frame_to_xy((int)(k >> kKeyBits), (int)(k & kKeyMask), (int)(v >> 31), X, Y);
+}
+
+__global__ void __launch_bounds__(kBStarThreads, 1) bt_star_refine(BArgs a) {
+    extern __shared__ __align__(16) char dyn[];
+    StarPoly& P = *reinterpret_cast<StarPoly*>(dyn);
+    unsigned long long* bins = reinterpret_cast<unsigned long long*>(dyn + kBStarAOff);
+    int2* va = reinterpret_cast<int2*>(dyn + kBStarAOff);
+    unsigned short* ba = reinterpret_cast<unsigned short*>(dyn + kBStarAOff + sizeof(int2) * kStarBins);
+    constexpr int kWarps = kBStarThreads / 32;
+    constexpr unsigned kStep = 32u * kBRefineU;
+    __shared__ unsigned s_kept, s_q[4];
+    __shared__ int s_set, s_cx, s_cy;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned n_front = a.star_ctr[2], n_back = a.star_ctr[3];
+    for (;;) {
+        if (tid == 0) {
+            const unsigned g = atomicAdd(&a.star_ctr[4], 1u);
+            s_set = g < n_front ? a.refine_list[g]
+                                : (g - n_front < n_back ? a.refine_list[a.k - 1 - (int)(g - n_front)] : -1);
+        }
+        __syncthreads();
+        const int i = s_set;
+        if (i < 0) return;
+        Ctl* c = a.ctl + i;
+        const long long base = a.offsets[i], ni = a.offsets[i + 1] - base;
+        const long long rb = region_base(a, i);
+        const unsigned m = c->count;
+        if (tid == 0) {
+            s_cx = (c->oct.vx[W] + c->oct.vx[E]) / 2;
+            s_cy = (c->oct.vy[S] + c->oct.vy[N]) / 2;
+            s_kept = 0u;
+        }
+        if (tid < 4) s_q[tid] = 0u;
+        for (int b = tid; b < kStarBins; b += kBStarThreads) bins[b] = 0ull;
+        __syncthreads();
+        const int cx = s_cx, cy = s_cy;
+        const unsigned per = ((m + kWarps - 1) / kWarps + kStep - 1) / kStep * kStep;
+        const unsigned lo = min(m, warp * per), hi = min(m, lo + per);
+        {   // 1. bins
+            uint32_t kk[kBRefineU];
+            uint64_t vv[kBRefineU];
+            bt_refine_load(a.keys, a.vals, rb, lo, hi, kk, vv);
+            for (unsigned r = lo; r < hi; r += kStep) {
+                uint32_t nk[kBRefineU];
+                uint64_t nv[kBRefineU];
+                bt_refine_load(a.keys, a.vals, rb, r + kStep, hi, nk, nv);
+#pragma unroll
+                for (int u = 0; u < kBRefineU; ++u) {
+                    if (r + 32u * u + lane >= hi) continue;
+                    int X, Y;
+                    bt_record_xy(kk[u], vv[u], X, Y);
+                    const int dx = X - cx, dy = Y - cy;
+                    const unsigned long long d2 = (unsigned long long)((long long)dx * dx + (long long)dy * dy);
+                    const unsigned long long key = ((d2 >> 17) << 32) | (vv[u] & 0x7FFFFFFFull);
+                    const int b = star_bin(dx, dy);
+                    if (key > bins[b]) atomicMax(&bins[b], key);
+                }
+#pragma unroll
+                for (int u = 0; u < kBRefineU; ++u) {
+                    kk[u] = nk[u];
+                    vv[u] = nv[u];
+                }
+            }
+        }
+        __syncthreads();
+        // 2. the polygon
+        const int K = star_finish<kBStarThreads, true>(bins, a.pts + 2 * base, ni, cx, cy, va, ba, P, c);
+        if (K == 0) {
+            __syncthreads();
+            continue;
+        }
+        // 3. the records not strictly inside go to the scatter buffer, then back
+        unsigned t0 = 0u, t1 = 0u, t2 = 0u, t3 = 0u;   // kept per queue (lane counts)
+        {
+            uint32_t kk[kBRefineU];
+            uint64_t vv[kBRefineU];
+            bt_refine_load(a.keys, a.vals, rb, lo, hi, kk, vv);
+            for (unsigned r = lo; r < hi; r += kStep) {
+                uint32_t nk[kBRefineU];
+                uint64_t nv[kBRefineU];
+                bt_refine_load(a.keys, a.vals, rb, r + kStep, hi, nk, nv);
+#pragma unroll
+                for (int u = 0; u < kBRefineU; ++u) {
+                    bool keep = r + 32u * u + lane < hi;
+                    if (keep) {
+                        int X, Y;
+                        bt_record_xy(kk[u], vv[u], X, Y);
+                        keep = !star_inside(X - cx, Y - cy, P);
+                    }
+                    const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
+                    if (bal == 0u) continue;
+                    unsigned pos = 0u;
+                    if (lane == 0) pos = atomicAdd(&s_kept, (unsigned)__popc(bal));
+                    pos = __shfl_sync(0xFFFFFFFFu, pos, 0) + (unsigned)__popc(bal & lanemask_lt());
+                    if (keep) {
+                        a.kP[rb + pos] = kk[u];
+                        a.vP[rb + pos] = vv[u];
+                        const unsigned q = kk[u] >> kKeyBits;
+                        t0 += q == 0u;
+                        t1 += q == 1u;
+                        t2 += q == 2u;
+                        t3 += q == 3u;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kBRefineU; ++u) {
+                    kk[u] = nk[u];
+                    vv[u] = nv[u];
+                }
+            }
+        }
+        t0 = __reduce_add_sync(0xFFFFFFFFu, t0);
+        t1 = __reduce_add_sync(0xFFFFFFFFu, t1);
+        t2 = __reduce_add_sync(0xFFFFFFFFu, t2);
+        t3 = __reduce_add_sync(0xFFFFFFFFu, t3);
+        if (lane == 0) {
+            atomicAdd(&s_q[0], t0);
+            atomicAdd(&s_q[1], t1);
+            atomicAdd(&s_q[2], t2);
+            atomicAdd(&s_q[3], t3);
+        }
+        __syncthreads();
+        const unsigned kept = s_kept;
+        for (unsigned j = tid; j < kept; j += kBStarThreads) {
+            a.keys[rb + j] = __ldcg(a.kP + rb + j);
+            a.vals[rb + j] = __ldcg(a.vP + rb + j);
+        }
+        if (tid < 4) c->counts4[tid] = s_q[tid];
+        if (tid == 0) {
+            c->count = kept;
+            c->star_k = K;
+        }
+        __syncthreads();
+    }
+}
+
 // One block per set, in two kernels.  bt_hull_small (every set): the
 // support-line records, then the hull of a set of at most kBSmallRec records
 // in a small shared-memory footprint (several blocks per SM).  bt_hull (the
@@ -861,7 +1058,13 @@ __global__ void __launch_bounds__(kBSmallThreads) bt_hull_small(BArgs a) {
         a.vals[rb + s_lpos[tid]] = s_lval[tid];
         atomicAdd(&c->counts4[s_lkey[tid] >> kKeyBits], 1u);
     }
-    if (total > (unsigned)kBSmallRec) return;   // bt_hull's
+    if (total > (unsigned)kBSmallRec) {   // bt_hull's, after bt_star_refine's when one block cannot hold them
+        if (tid == 0 && total > (unsigned)kMidCap) {
+            if (total > kBRefineHuge) a.refine_list[atomicAdd(&a.star_ctr[2], 1u)] = i;
+            else a.refine_list[a.k - 1 - (int)atomicAdd(&a.star_ctr[3], 1u)] = i;
+        }
+        return;
+    }
     __syncthreads();   // also makes this block's line records visible to it
     for (unsigned j = tid; j < total; j += blockDim.x) {
         const uint32_t k = __ldcg(a.keys + rb + j);
@@ -882,6 +1085,7 @@ __global__ void __launch_bounds__(kBSmallThreads) bt_hull_small(BArgs a) {
 }
 
 constexpr size_t bt_cmax(size_t x, size_t y) { return x > y ? x : y; }
+constexpr int kBQhSkip = 2048;
 constexpr size_t kBHullSmem = bt_cmax(kMidSmemBytes, sizeof(QhSmem));
 
 __global__ void __launch_bounds__(kBHullThreads, 1) bt_hull(BArgs a) {
@@ -897,6 +1101,13 @@ __global__ void __launch_bounds__(kBHullThreads, 1) bt_hull(BArgs a) {
     const long long base = a.offsets[i], ni = a.offsets[i + 1] - base;
     if (total > (unsigned)kMidCap) {
         if (tid == 0) a.big[i] = 1;
+        return;
+    }
+    // Records that a star polygon left are near the hull: past kBQhSkip of
+    // them their chains would outgrow the quickhull rounds' vertex capacity
+    // (kQhCap), so the sort-based path takes them directly.
+    if (c->star_k > 0 && total > (unsigned)kBQhSkip) {
+        mid_hull(a.keys + rb, a.vals + rb, (int)total, a.pts + 2 * base, ni, c, a.out_idx + base, a.out_n + i, dyn);
         return;
     }
     QhSmem& q = *reinterpret_cast<QhSmem*>(dyn);
@@ -931,7 +1142,7 @@ static std::map<std::pair<int, cudaStream_t>, BWork> g_bws;
 static size_t bt_align(size_t x) { return (x + 255) / 256 * 256; }
 
 struct BLayout {
-    size_t ctl, keys, vals, rmap, big, redo, star_ctr, star_list, star_slot, star_bins, star_polys;
+    size_t ctl, keys, vals, rmap, big, redo, star_ctr, star_list, refine_list, star_slot, star_bins, star_polys;
     size_t seg_nb, seg_bbase, seg_lo, seg_scale, seg_tbase, rt_base, totals;
     size_t bcount, bcur, bstart, blen, bu, bv, bi, kP, vP, cu, cv, ci, clen, ctmap, counters;
     size_t zero_from, zero_to;   // star bins and bucket counters: cleared before each batch
@@ -961,7 +1172,8 @@ static BLayout bt_layout(long long total, int k, long long big_pts, long long bi
     L.rmap = take(sizeof(int) * (size_t)L.rtcap);
     L.big = take((size_t)k);
     L.redo = take((size_t)k);
-    L.star_ctr = take(4 * 4);
+    L.star_ctr = take(4 * 8);
+    L.refine_list = take(sizeof(int) * (size_t)k);
     L.star_list = take(sizeof(int) * (size_t)k);
     L.star_slot = take(sizeof(int) * (size_t)k);
     L.star_polys = take(sizeof(StarPoly) * (size_t)slots);
@@ -1098,7 +1310,9 @@ static int bt_configure(int dev, BtDevice* out) {
     if (cudaFuncSetAttribute(bt_hull, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBHullSmem) != cudaSuccess)
         return CH_ECUDA;
     if (cudaFuncSetAttribute(bt_star_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBStarSmem) !=
-        cudaSuccess)
+            cudaSuccess ||
+        cudaFuncSetAttribute(bt_star_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBStarSmem) !=
+            cudaSuccess)
         return CH_ECUDA;
     if (configure_batched_large() != cudaSuccess) return CH_ECUDA;
     bt_occupancy<128, 16>(d.occ[0]);
@@ -1268,6 +1482,7 @@ static int bt_enqueue(const BtCall& c, unsigned char* redo, cudaStream_t s) {
     const int st = bt_enqueue_tiles(c, s);
     if (st != CH_OK) return st;
     { ProfScope p("batched_hull_small", s); bt_hull_small<<<c.a.k, kBSmallThreads, 0, s>>>(c.a); }
+    { ProfScope p("batched_refine", s); bt_star_refine<<<c.sms, kBStarThreads, kBStarSmem, s>>>(c.a); }
     { ProfScope p("batched_hull", s); bt_hull<<<c.a.k, kBHullThreads, kBHullSmem, s>>>(c.a); }
     // Sets with more records than one block holds: all together through the
     // bucketed path.
@@ -1493,6 +1708,9 @@ int hull_batched_impl(const float* pts, const int64_t* offsets, int32_t k, int32
     a.star_slot = (int*)(base + L.star_slot);
     a.star_bins = (unsigned long long*)(base + L.star_bins);
     a.star_polys = (StarPoly*)(base + L.star_polys);
+    a.refine_list = (int*)(base + L.refine_list);
+    a.kP = (uint32_t*)(base + L.kP);
+    a.vP = (uint64_t*)(base + L.vP);
     BLArgs& b = c.b;
     b.pts = pts;
     b.offsets = offsets;
