@@ -81,9 +81,11 @@ struct BArgs {
     unsigned long long* star_bins;   // kStarBins per slot (zeroed before every batch)
     StarPoly* star_polys;     // one per slot
     unsigned* star_ctr;       // work lists: [0] dense sets listed, [1] taken by bt_star_build;
-                              // [2] / [3] sets for bt_star_refine from the front / back, [4] taken
+                              // [2] / [3] sets for bt_star_refine from the front / back, [4] taken;
+                              // [5] sets for bt_hull, [6] taken
     int* star_list;           // k entries
     int* refine_list;         // k entries
+    int* hull_list;           // k entries
     uint32_t* kP;             // the bucketed path's scatter buffer (set regions as keys / vals)
     uint64_t* vP;
 };
@@ -116,7 +118,7 @@ __global__ void __launch_bounds__(256) bt_init(BArgs a) {
         c->star_cy = 0;
         a.big[i] = 0;
     }
-    if (i == 0 && lane < 5) a.star_ctr[lane] = 0u;
+    if (i == 0 && lane < 8) a.star_ctr[lane] = 0u;
 }
 
 // Star slots (one block of 1024 threads): the sets of at least kBStarMinPts
@@ -1059,9 +1061,12 @@ __global__ void __launch_bounds__(kBSmallThreads) bt_hull_small(BArgs a) {
         atomicAdd(&c->counts4[s_lkey[tid] >> kKeyBits], 1u);
     }
     if (total > (unsigned)kBSmallRec) {   // bt_hull's, after bt_star_refine's when one block cannot hold them
-        if (tid == 0 && total > (unsigned)kMidCap) {
-            if (total > kBRefineHuge) a.refine_list[atomicAdd(&a.star_ctr[2], 1u)] = i;
-            else a.refine_list[a.k - 1 - (int)atomicAdd(&a.star_ctr[3], 1u)] = i;
+        if (tid == 0) {
+            a.hull_list[atomicAdd(&a.star_ctr[5], 1u)] = i;
+            if (total > (unsigned)kMidCap) {
+                if (total > kBRefineHuge) a.refine_list[atomicAdd(&a.star_ctr[2], 1u)] = i;
+                else a.refine_list[a.k - 1 - (int)atomicAdd(&a.star_ctr[3], 1u)] = i;
+            }
         }
         return;
     }
@@ -1088,43 +1093,53 @@ constexpr size_t bt_cmax(size_t x, size_t y) { return x > y ? x : y; }
 constexpr int kBQhSkip = 2048;
 constexpr size_t kBHullSmem = bt_cmax(kMidSmemBytes, sizeof(QhSmem));
 
+// Persistent over bt_hull_small's list of the sets with more records than
+// its small footprint holds (one block per set at a time).
 __global__ void __launch_bounds__(kBHullThreads, 1) bt_hull(BArgs a) {
     extern __shared__ __align__(16) char dyn[];
-    __shared__ int s_done, s_mv;
-    const int i = blockIdx.x, tid = threadIdx.x;
-    Ctl* c = a.ctl + i;
-    if (tid == 0) s_done = *(volatile int*)&c->done;
-    __syncthreads();
-    if (s_done) return;   // empty or failed, or done by bt_hull_small
-    const unsigned total = *(volatile unsigned*)&c->count;   // with the line records
-    const long long rb = region_base(a, i);
-    const long long base = a.offsets[i], ni = a.offsets[i + 1] - base;
-    if (total > (unsigned)kMidCap) {
-        if (tid == 0) a.big[i] = 1;
-        return;
-    }
-    // Records that a star polygon left are near the hull: past kBQhSkip of
-    // them their chains would outgrow the quickhull rounds' vertex capacity
-    // (kQhCap), so the sort-based path takes them directly.
-    if (c->star_k > 0 && total > (unsigned)kBQhSkip) {
-        mid_hull(a.keys + rb, a.vals + rb, (int)total, a.pts + 2 * base, ni, c, a.out_idx + base, a.out_n + i, dyn);
-        return;
-    }
-    QhSmem& q = *reinterpret_cast<QhSmem*>(dyn);
-    for (unsigned j = tid; j < total; j += blockDim.x) {
-        const uint32_t k = __ldcg(a.keys + rb + j);
-        const uint64_t w = __ldcg(a.vals + rb + j);
-        q.ru[j] = (int)(k & kKeyMask);
-        q.rv[j] = (int)(w >> 31);
-        q.ri[j] = (int)(w & 0x7FFFFFFFull);
-        q.rs[j] = (int)(k >> kKeyBits);
-    }
-    __syncthreads();
-    if (qh_chains(q, (int)total, &s_mv)) {
-        stitch_cycle(q.ru, q.rv, q.ri, s_mv, q.rs, c, ni, a.out_idx + base, a.out_n + i);
-    } else {
+    __shared__ int s_set, s_mv;
+    const int tid = threadIdx.x;
+    const unsigned listed = a.star_ctr[5];
+    for (;;) {
+        if (tid == 0) {
+            const unsigned g = atomicAdd(&a.star_ctr[6], 1u);
+            s_set = g < listed ? a.hull_list[g] : -1;
+        }
         __syncthreads();
-        mid_hull(a.keys + rb, a.vals + rb, (int)total, a.pts + 2 * base, ni, c, a.out_idx + base, a.out_n + i, dyn);
+        const int i = s_set;
+        if (i < 0) return;
+        Ctl* c = a.ctl + i;
+        const unsigned total = *(volatile unsigned*)&c->count;   // with the line records
+        const long long rb = region_base(a, i);
+        const long long base = a.offsets[i], ni = a.offsets[i + 1] - base;
+        // More than one block holds, or past kBQhSkip records that are near
+        // the hull (a star polygon left them, or more than a quarter of the
+        // points survived the octagon), whose chains would outgrow the
+        // quickhull rounds' vertex capacity (kQhCap): the bucketed path.
+        const bool dense = c->star_k > 0 || 4ll * total > ni;
+        if (*(volatile int*)&c->done || total > (unsigned)kMidCap || (dense && total > (unsigned)kBQhSkip)) {
+            if (tid == 0 && !*(volatile int*)&c->done) a.big[i] = 1;
+            __syncthreads();
+            continue;
+        }
+        QhSmem& q = *reinterpret_cast<QhSmem*>(dyn);
+        for (unsigned j = tid; j < total; j += blockDim.x) {
+            const uint32_t k = __ldcg(a.keys + rb + j);
+            const uint64_t w = __ldcg(a.vals + rb + j);
+            q.ru[j] = (int)(k & kKeyMask);
+            q.rv[j] = (int)(w >> 31);
+            q.ri[j] = (int)(w & 0x7FFFFFFFull);
+            q.rs[j] = (int)(k >> kKeyBits);
+        }
+        __syncthreads();
+        if (qh_chains(q, (int)total, &s_mv)) {
+            stitch_cycle(q.ru, q.rv, q.ri, s_mv, q.rs, c, ni, a.out_idx + base, a.out_n + i);
+        } else {
+            __syncthreads();
+            mid_hull(a.keys + rb, a.vals + rb, (int)total, a.pts + 2 * base, ni, c, a.out_idx + base, a.out_n + i,
+                     dyn);
+        }
+        __syncthreads();
     }
 }
 
@@ -1142,7 +1157,7 @@ static std::map<std::pair<int, cudaStream_t>, BWork> g_bws;
 static size_t bt_align(size_t x) { return (x + 255) / 256 * 256; }
 
 struct BLayout {
-    size_t ctl, keys, vals, rmap, big, redo, star_ctr, star_list, refine_list, star_slot, star_bins, star_polys;
+    size_t ctl, keys, vals, rmap, big, redo, star_ctr, star_list, refine_list, hull_list, star_slot, star_bins, star_polys;
     size_t seg_nb, seg_bbase, seg_lo, seg_scale, seg_tbase, rt_base, totals;
     size_t bcount, bcur, bstart, blen, bu, bv, bi, kP, vP, cu, cv, ci, clen, ctmap, counters;
     size_t zero_from, zero_to;   // star bins and bucket counters: cleared before each batch
@@ -1174,6 +1189,7 @@ static BLayout bt_layout(long long total, int k, long long big_pts, long long bi
     L.redo = take((size_t)k);
     L.star_ctr = take(4 * 8);
     L.refine_list = take(sizeof(int) * (size_t)k);
+    L.hull_list = take(sizeof(int) * (size_t)k);
     L.star_list = take(sizeof(int) * (size_t)k);
     L.star_slot = take(sizeof(int) * (size_t)k);
     L.star_polys = take(sizeof(StarPoly) * (size_t)slots);
@@ -1483,7 +1499,7 @@ static int bt_enqueue(const BtCall& c, unsigned char* redo, cudaStream_t s) {
     if (st != CH_OK) return st;
     { ProfScope p("batched_hull_small", s); bt_hull_small<<<c.a.k, kBSmallThreads, 0, s>>>(c.a); }
     { ProfScope p("batched_refine", s); bt_star_refine<<<c.sms, kBStarThreads, kBStarSmem, s>>>(c.a); }
-    { ProfScope p("batched_hull", s); bt_hull<<<c.a.k, kBHullThreads, kBHullSmem, s>>>(c.a); }
+    { ProfScope p("batched_hull", s); bt_hull<<<c.sms, kBHullThreads, kBHullSmem, s>>>(c.a); }
     // Sets with more records than one block holds: all together through the
     // bucketed path.
     launch_batched_large(c.b, redo, c.sms, s);
@@ -1709,6 +1725,7 @@ int hull_batched_impl(const float* pts, const int64_t* offsets, int32_t k, int32
     a.star_bins = (unsigned long long*)(base + L.star_bins);
     a.star_polys = (StarPoly*)(base + L.star_polys);
     a.refine_list = (int*)(base + L.refine_list);
+    a.hull_list = (int*)(base + L.hull_list);
     a.kP = (uint32_t*)(base + L.kP);
     a.vP = (uint64_t*)(base + L.vP);
     BLArgs& b = c.b;
