@@ -82,8 +82,9 @@ struct BArgs {
     StarPoly* star_polys;     // one per slot
     unsigned* star_ctr;       // work lists: [0] dense sets listed, [1] taken by bt_star_build;
                               // [2] / [3] sets for bt_star_refine from the front / back, [4] taken;
-                              // [5] sets for bt_hull, [6] taken
+                              // [5] sets for bt_hull, [6] taken; [7] bt_dense's units, [8] taken
     int* star_list;           // k entries
+    unsigned* unit_base;      // k entries: first bt_dense unit of each listed set
     int* refine_list;         // k entries
     int* hull_list;           // k entries
     uint32_t* kP;             // the bucketed path's scatter buffer (set regions as keys / vals)
@@ -118,7 +119,7 @@ __global__ void __launch_bounds__(256) bt_init(BArgs a) {
         c->star_cy = 0;
         a.big[i] = 0;
     }
-    if (i == 0 && lane < 8) a.star_ctr[lane] = 0u;
+    if (i == 0 && lane < 16) a.star_ctr[lane] = 0u;
 }
 
 // Star slots (one block of 1024 threads): the sets of at least kBStarMinPts
@@ -586,9 +587,11 @@ __device__ __forceinline__ void bt_warp_set(const BArgs& a, int q, BtWarpSet& w,
     Ctl* c = a.ctl + q;
     w.set = q;
     w.base = a.offsets[q];
-    w.skip = *(volatile int*)&c->done != 0;   // bt_octagon's verdict on empty and failed sets
     const int slot = a.star_slot[q];
-    w.P = (slot >= 0 && c->star_k > 0) ? a.star_polys + slot : nullptr;
+    // empty and failed sets (bt_octagon's verdict), and the sets with a star
+    // polygon, which bt_dense filters
+    w.skip = *(volatile int*)&c->done != 0 || (slot >= 0 && c->star_k > 0);
+    w.P = nullptr;
     w.rmin = w.P ? w.P->rmin : 0u;
     w.cx = c->star_cx;
     w.cy = c->star_cy;
@@ -839,6 +842,224 @@ __global__ void __launch_bounds__(kBStarThreads, 1) bt_star_build(BArgs a) {
         }
         if (tid == 0) c->star_k = K;
         __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The filter of the sets with a star polygon (bt_star_build's), which
+// bt_filter leaves to this kernel: the single hull's dense post pass per
+// set.  Work units are runs of up to kBDenseRun points of a set
+// (bt_dense_plan numbers them); a block takes units one at a time, copies the
+// set's polygon (all of it, 112 KB, mostly from L2) and octagon into shared
+// memory, and streams the run's points with the loads of its next step in
+// flight: a point closer to the centre than the polygon's inscribed radius,
+// or than its bin's radius bound, is strictly inside the polygon; the others
+// wait in a per-warp queue and go 32 at a time through the exact wedge test
+// and the hull-rule classification; kept points become records of their
+// queue, staged per warp and written to the set's region with one atomic per
+// batch.
+constexpr int kBDenseThreads = 512;
+constexpr int kBDenseRun = 1 << 18;    // points of a work unit
+constexpr int kBDenseU = 8;            // points per thread and step
+constexpr int kBDenseRecs = 256;       // records staged per warp
+constexpr int kBDenseQueue = 64;       // < 32 waiting + 32 added per step
+struct BtDenseWarp {
+    uint64_t val[kBDenseRecs];
+    uint32_t key[kBDenseRecs];
+    float qx[kBDenseQueue], qy[kBDenseQueue];
+    unsigned qi[kBDenseQueue];
+};
+constexpr size_t kBDenseWarpOff = (sizeof(StarPoly) + sizeof(Octagon) + 15) / 16 * 16;
+constexpr size_t kBDenseSmem = kBDenseWarpOff + (kBDenseThreads / 32) * sizeof(BtDenseWarp);
+
+// Work units of the sets with a polygon: unit_base[j] = first unit of listed
+// set j (one block of 1024 threads; star_ctr[7] = total units).
+__global__ void __launch_bounds__(1024) bt_dense_plan(BArgs a) {
+    __shared__ unsigned s_part[1024];
+    const int tid = threadIdx.x;
+    const int n = (int)a.star_ctr[0];
+    const int per = (n + 1023) / 1024;
+    const int lo = tid * per, hi = min(n, lo + per);
+    unsigned sum = 0u;
+    for (int j = lo; j < hi; ++j) {
+        const int i = a.star_list[j];
+        const long long ni = a.offsets[i + 1] - a.offsets[i];
+        sum += a.ctl[i].star_k > 0 ? (unsigned)((ni + kBDenseRun - 1) / kBDenseRun) : 0u;
+    }
+    s_part[tid] = sum;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const unsigned v = tid >= o ? s_part[tid - o] : 0u;
+        __syncthreads();
+        s_part[tid] += v;
+        __syncthreads();
+    }
+    unsigned run = s_part[tid] - sum;
+    for (int j = lo; j < hi; ++j) {
+        const int i = a.star_list[j];
+        const long long ni = a.offsets[i + 1] - a.offsets[i];
+        a.unit_base[j] = run;
+        run += a.ctl[i].star_k > 0 ? (unsigned)((ni + kBDenseRun - 1) / kBDenseRun) : 0u;
+    }
+    if (tid == 1023) a.star_ctr[7] = s_part[1023];
+}
+
+// Warp-collective: the exact tests of one queued point per lane (valid =
+// false for none) and the staging of the kept ones.
+__device__ __forceinline__ void bt_dense_exact(const BArgs& a, const StarPoly& P, const Octagon& so, Ctl* c,
+                                               long long rb, int cx, int cy, BtDenseWarp& wb, unsigned& cnt,
+                                               unsigned (&nq)[4], bool valid, float x, float y, unsigned li) {
+    const int lane = threadIdx.x & 31;
+    int r = -1, X = 0, Y = 0;
+    if (valid) {
+        X = __float2int_rn(x);
+        Y = __float2int_rn(y);
+        const int px = X - cx, py = Y - cy;
+        if (!star_inside_exact(px, py, star_bin(px, py), P)) r = classify_hull(x, y, so);
+    }
+    bool keep = r >= 0;
+    if (!__any_sync(0xFFFFFFFFu, keep)) return;
+    if (reduce_on_line(so, keep, X, Y, li, c)) keep = false;
+    const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
+    if (!bal) return;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) nq[q] += (unsigned)__popc(__ballot_sync(0xFFFFFFFFu, keep && r == q));
+    if (cnt + (unsigned)__popc(bal) > (unsigned)kBDenseRecs) {   // write the staged records out
+        unsigned base = 0u;
+        if (lane == 0) base = atomicAdd(&c->count, cnt);
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        for (unsigned j = lane; j < cnt; j += 32) {
+            a.keys[rb + base + j] = wb.key[j];
+            a.vals[rb + base + j] = wb.val[j];
+        }
+        __syncwarp();
+        cnt = 0u;
+    }
+    if (keep) {
+        uint32_t u, v;
+        queue_frame(r, X, Y, u, v);
+        const unsigned pos = cnt + (unsigned)__popc(bal & lanemask_lt());
+        wb.key[pos] = make_key(r, u);
+        wb.val[pos] = make_val(v, li);
+    }
+    cnt += (unsigned)__popc(bal);
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(kBDenseThreads, 1) bt_dense(BArgs a) {
+    extern __shared__ __align__(16) char dyn[];
+    StarPoly& P = *reinterpret_cast<StarPoly*>(dyn);
+    Octagon& so = *reinterpret_cast<Octagon*>(dyn + sizeof(StarPoly));
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    BtDenseWarp& wb = reinterpret_cast<BtDenseWarp*>(dyn + kBDenseWarpOff)[warp];
+    constexpr int kStep = kBDenseThreads * kBDenseU;
+    __shared__ int s_set, s_part;
+    const unsigned nunits = a.star_ctr[7];
+    const int listed = (int)a.star_ctr[0];
+    for (;;) {
+        if (tid == 0) {
+            const unsigned u = atomicAdd(&a.star_ctr[8], 1u);
+            int set = -1, part = 0;
+            if (u < nunits) {   // the last listed set whose first unit is at or before u
+                int l = 0, r = listed;
+                while (r - l > 1) {
+                    const int mid = (l + r) >> 1;
+                    if (a.unit_base[mid] <= u) l = mid;
+                    else r = mid;
+                }
+                set = a.star_list[l];
+                part = (int)(u - a.unit_base[l]);
+            }
+            s_set = set;
+            s_part = part;
+        }
+        __syncthreads();
+        const int i = s_set;
+        if (i < 0) return;
+        Ctl* c = a.ctl + i;
+        const long long base = a.offsets[i], ni = a.offsets[i + 1] - base;
+        const long long rb = region_base(a, i);
+        const long long lo = (long long)s_part * kBDenseRun, hi = min(ni, lo + kBDenseRun);
+        {   // the polygon and the octagon into shared memory
+            const int4* src = reinterpret_cast<const int4*>(a.star_polys + a.star_slot[i]);
+            int4* dst = reinterpret_cast<int4*>(&P);
+            for (int j = tid; j < (int)(sizeof(StarPoly) / 16); j += kBDenseThreads) dst[j] = __ldcg(src + j);
+            copy_octagon(&so, &c->oct);
+        }
+        __syncthreads();
+        const int cx = c->star_cx, cy = c->star_cy;
+        const long long r0 = P.rmin;
+        const float2* p2 = reinterpret_cast<const float2*>(a.pts) + base;
+        unsigned cnt = 0u, qn = 0u;
+        unsigned nq[4] = {0u, 0u, 0u, 0u};
+        float2 cur[kBDenseU];
+#pragma unroll
+        for (int u = 0; u < kBDenseU; ++u) {
+            const long long j = lo + u * kBDenseThreads + tid;
+            cur[u] = j < hi ? __ldcs(p2 + j) : make_float2(0.0f, 0.0f);
+        }
+        for (long long s0 = lo; s0 < hi; s0 += kStep) {
+            float2 nxt[kBDenseU];
+#pragma unroll
+            for (int u = 0; u < kBDenseU; ++u) {
+                const long long j = s0 + kStep + u * kBDenseThreads + tid;
+                nxt[u] = j < hi ? __ldcs(p2 + j) : make_float2(0.0f, 0.0f);
+            }
+#pragma unroll
+            for (int u = 0; u < kBDenseU; ++u) {
+                const long long j = s0 + u * kBDenseThreads + tid;
+                bool need = false;
+                if (j < hi) {
+                    const long long px = __float2int_rn(cur[u].x) - cx, py = __float2int_rn(cur[u].y) - cy;
+                    const long long d2 = px * px + py * py;
+                    if (d2 >= r0 * r0) {
+                        const long long rr = P.rin[star_bin((int)px, (int)py)];
+                        need = d2 >= rr * rr;
+                    }
+                }
+                const unsigned bal = __ballot_sync(0xFFFFFFFFu, need);
+                if (bal) {   // queued; full rounds of 32 go through the exact tests
+                    if (need) {
+                        const unsigned pos = qn + (unsigned)__popc(bal & lanemask_lt());
+                        wb.qx[pos] = cur[u].x;
+                        wb.qy[pos] = cur[u].y;
+                        wb.qi[pos] = (unsigned)j;
+                    }
+                    qn += (unsigned)__popc(bal);
+                    __syncwarp();
+                    if (qn >= 32u) {
+                        qn -= 32u;
+                        const float qx = wb.qx[qn + lane], qy = wb.qy[qn + lane];
+                        const unsigned qi = wb.qi[qn + lane];
+                        __syncwarp();
+                        bt_dense_exact(a, P, so, c, rb, cx, cy, wb, cnt, nq, true, qx, qy, qi);
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kBDenseU; ++u) cur[u] = nxt[u];
+        }
+        if (qn) {   // the queue's remainder
+            const bool valid = (unsigned)lane < qn;
+            const float qx = valid ? wb.qx[lane] : 0.0f, qy = valid ? wb.qy[lane] : 0.0f;
+            const unsigned qi = valid ? wb.qi[lane] : 0u;
+            __syncwarp();
+            bt_dense_exact(a, P, so, c, rb, cx, cy, wb, cnt, nq, valid, qx, qy, qi);
+        }
+        if (cnt) {
+            unsigned b0 = 0u;
+            if (lane == 0) b0 = atomicAdd(&c->count, cnt);
+            b0 = __shfl_sync(0xFFFFFFFFu, b0, 0);
+            for (unsigned j = lane; j < cnt; j += 32) {
+                a.keys[rb + b0 + j] = wb.key[j];
+                a.vals[rb + b0 + j] = wb.val[j];
+            }
+        }
+        if (lane == 0)
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (nq[q]) atomicAdd(&c->counts4[q], nq[q]);
+        __syncthreads();   // the polygon's shared memory is reloaded by the next unit
     }
 }
 
@@ -1157,7 +1378,7 @@ static std::map<std::pair<int, cudaStream_t>, BWork> g_bws;
 static size_t bt_align(size_t x) { return (x + 255) / 256 * 256; }
 
 struct BLayout {
-    size_t ctl, keys, vals, rmap, big, redo, star_ctr, star_list, refine_list, hull_list, star_slot, star_bins, star_polys;
+    size_t ctl, keys, vals, rmap, big, redo, star_ctr, star_list, refine_list, hull_list, unit_base, star_slot, star_bins, star_polys;
     size_t seg_nb, seg_bbase, seg_lo, seg_scale, seg_tbase, rt_base, totals;
     size_t bcount, bcur, bstart, blen, bu, bv, bi, kP, vP, cu, cv, ci, clen, ctmap, counters;
     size_t zero_from, zero_to;   // star bins and bucket counters: cleared before each batch
@@ -1187,7 +1408,8 @@ static BLayout bt_layout(long long total, int k, long long big_pts, long long bi
     L.rmap = take(sizeof(int) * (size_t)L.rtcap);
     L.big = take((size_t)k);
     L.redo = take((size_t)k);
-    L.star_ctr = take(4 * 8);
+    L.star_ctr = take(4 * 16);
+    L.unit_base = take(sizeof(unsigned) * (size_t)k);
     L.refine_list = take(sizeof(int) * (size_t)k);
     L.hull_list = take(sizeof(int) * (size_t)k);
     L.star_list = take(sizeof(int) * (size_t)k);
@@ -1328,7 +1550,8 @@ static int bt_configure(int dev, BtDevice* out) {
     if (cudaFuncSetAttribute(bt_star_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBStarSmem) !=
             cudaSuccess ||
         cudaFuncSetAttribute(bt_star_refine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBStarSmem) !=
-            cudaSuccess)
+            cudaSuccess ||
+        cudaFuncSetAttribute(bt_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBDenseSmem) != cudaSuccess)
         return CH_ECUDA;
     if (configure_batched_large() != cudaSuccess) return CH_ECUDA;
     bt_occupancy<128, 16>(d.occ[0]);
@@ -1486,6 +1709,11 @@ static int bt_enqueue_tiles(const BtCall& c, cudaStream_t s) {
         ProfScope p("batched_star", s);
         bt_star_bin<<<c.sms * 8, kBStarBinThreads, 0, s>>>(a);
         bt_star_build<<<c.sms, kBStarThreads, kBStarSmem, s>>>(a);
+    }
+    {
+        ProfScope p("batched_dense", s);
+        bt_dense_plan<<<1, 1024, 0, s>>>(a);
+        bt_dense<<<c.sms, kBDenseThreads, kBDenseSmem, s>>>(a);
     }
     {
         ProfScope p("batched_filter", s);
@@ -1726,6 +1954,7 @@ int hull_batched_impl(const float* pts, const int64_t* offsets, int32_t k, int32
     a.star_polys = (StarPoly*)(base + L.star_polys);
     a.refine_list = (int*)(base + L.refine_list);
     a.hull_list = (int*)(base + L.hull_list);
+    a.unit_base = (unsigned*)(base + L.unit_base);
     a.kP = (uint32_t*)(base + L.kP);
     a.vP = (uint64_t*)(base + L.vP);
     BLArgs& b = c.b;
