@@ -91,10 +91,13 @@ int ch_hull(const float* pts, int64_t n, int32_t* out_idx, int64_t* out_n, void*
  *   out_n    device int64[k]: hull sizes, or a negative ch_status per set.
  *   host_offsets  optional HOST copy of offsets (NULL allowed): lets the
  *            library size its launches without reading the device array.
- * Each result equals ch_hull on that set alone.
- * Tile shape of the per-point kernels (threads per block x points per thread
- * = points per tile): picked by an autotuner per (device name, SM count,
- * floor log2 of offsets[k], floor log2 of k).  The first call of such a size
+ * Each result equals ch_hull on that set alone.  The batch's points are
+ * streamed as one array (extremes, then filter); dense sets of at least 32768
+ * points are filtered by a star polygon of their own points (Table V's
+ * worst case); see ch_batched_counters.
+ * Shape of the streamed per-point kernels (threads per block x points per
+ * lane, a warp tile being 32 x points per lane): picked by an autotuner per
+ * (device name, SM count, floor log2 of offsets[k], floor log2 of k).  The first call of such a size
  * class times every compiled shape on that call's batch (the call blocks
  * meanwhile); the result is kept in memory and, when the environment variable
  * CH_TUNE_CACHE names a file, in that JSON file, read at the first lookup.
@@ -128,7 +131,7 @@ int ch_batched_counters(void* stream, int32_t k, int64_t* out);
 /*
  * ch_batched_config -- the tile shape ch_hull_batched uses on the current
  * device for a batch of total_points points in k >= 1 sets: *threads and
- * *per (points per thread) from CH_BLOCK / CH_PPT / CH_TILE, else from the
+ * *per (points per lane) from CH_BLOCK / CH_PPT / CH_TILE, else from the
  * autotuner's choice for that size class; both 0 when it has not been tuned
  * yet.  CH_EINVAL for bad arguments or an environment shape that is not one
  * of the compiled shapes (128x16, 256x8, 256x16, 256x32, 512x8, 512x16).

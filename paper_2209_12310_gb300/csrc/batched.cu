@@ -1,32 +1,39 @@
 // batched.cu -- k independent hulls packed back to back (ch_hull_batched).
 //
-// The sets are cut into tiles of at most `tile` points (a tile never spans
-// two sets; tile = threads x points per thread of the tile kernels, one of
-// the compiled shapes that the autotuner picks per device and batch size)
-// and every launch covers all sets at once:
-//   bt_init      per-set control blocks and tile counts;
-//   bt_scan      tile offsets (exclusive prefix over the sets, one block);
-//   bt_extremes  tiles: validation and the 8 extremes of each set as packed
-//                (key, lowest local index) maxima (Alg. 2, findExtremes);
-//   bt_octagon   one block per set: octagon, inner region, the chain end
-//                point records;
-//   bt_filter    tiles: the hull-rule classification of every point against
-//                its set's octagon, records compacted into the set's region
-//                (the loop of Alg. 1/2), support-line end points reduced;
+// The batch's points are one array; its 16-byte aligned body is cut into
+// warp tiles of 32 x P points whatever the sets (P points per lane and the
+// block size are one of the compiled shapes that the autotuner picks per
+// device and batch size), and every launch covers all sets at once:
+//   bt_init, bt_slots  control blocks; a star slot per set of at least
+//                kBStarMinPts points;
+//   bt_extremes  streamed warp tiles: validation and the 8 extremes of each
+//                set (Alg. 2, findExtremes) as packed (key, ~tile) maxima;
+//   bt_octagon   one block per set: the lowest index of each extreme (a
+//                rescan of its tile), octagon, inner region, chain end-point
+//                records; the density test that lists a set for a polygon;
+//   bt_star_bin, bt_star_build  the listed sets' angular bins and star
+//                polygons (star.cuh; points near a circle, Table V);
+//   bt_dense     the filter of the sets with a polygon: runs of their points
+//                against the polygon and the octagon, kept points as records;
+//   bt_filter    streamed warp tiles of the other sets: the hull-rule
+//                classification against the set's octagon, records compacted
+//                into the set's region (the loop of Alg. 1/2), support-line
+//                end points reduced;
 //   bt_hull_small  one block per set: the support-line records, then the
 //                hull of a set with few records in a small footprint;
-//   bt_star      sets with more records than one block holds: the star
-//                polygon of the set's records (star.cuh) drops the records
-//                strictly inside it (points near a circle, Table V);
-//   bt_hull      one block per set: the hull of its records (quickhull rounds
-//                and the stitch, as in the single hull's last block).
-// Sets whose records exceed what one block holds go through the bucketed
-// large-survivor path together (batched_large.cu); the rare set it cannot
-// finish (a bucket chain longer than kBkChain) is flagged and the host runs
-// the single-hull path on it.  Each result equals ch_hull on the set alone
-// (local indices).  The device work of one call is captured into a CUDA graph
-// on a private stream; the executable graph of a (device, stream) is updated
-// in place from call to call and launched on the caller's stream.
+//   bt_star_refine  sets with more records than one block holds: a second
+//                polygon from the set's records drops those strictly inside;
+//   bt_hull      persistent over the remaining sets: the hull of a set's
+//                records in one block (quickhull rounds and the stitch, as in
+//                the single hull's last block).
+// Sets whose records exceed what one block holds (or are many and near the
+// hull) go through the bucketed large-survivor path together
+// (batched_large.cu); the rare set it cannot finish (a bucket chain longer
+// than kBkChain) is flagged and the host runs the single-hull path on it.
+// Each result equals ch_hull on the set alone (local indices).  The device
+// work of one call is captured into a CUDA graph on a private stream; the
+// executable graph of a (device, stream) is updated in place from call to
+// call and launched on the caller's stream.
 #include "batched_large.h"
 #include "ch_internal.cuh"
 #include "extremes.cuh"
