@@ -869,7 +869,7 @@ constexpr int kBDenseThreads = 512;
 constexpr int kBDenseRun = 1 << 18;    // points of a work unit
 constexpr int kBDenseU = 8;            // points per thread and step
 constexpr int kBDenseRecs = 256;       // records staged per warp
-constexpr int kBDenseQueue = 64;       // < 32 waiting + 32 added per step
+constexpr int kBDenseQueue = 32 * kBDenseU + 32;   // < 32 waiting + a step's points
 struct BtDenseWarp {
     uint64_t val[kBDenseRecs];
     uint32_t key[kBDenseRecs];
@@ -878,6 +878,7 @@ struct BtDenseWarp {
 };
 constexpr size_t kBDenseWarpOff = (sizeof(StarPoly) + sizeof(Octagon) + 15) / 16 * 16;
 constexpr size_t kBDenseSmem = kBDenseWarpOff + (kBDenseThreads / 32) * sizeof(BtDenseWarp);
+static_assert(kBDenseSmem <= 227 * 1024, "one block's shared memory");
 
 // Work units of the sets with a polygon: unit_base[j] = first unit of listed
 // set j (one block of 1024 threads; star_ctr[7] = total units).
@@ -1025,23 +1026,21 @@ __global__ void __launch_bounds__(kBDenseThreads, 1) bt_dense(BArgs a) {
                     }
                 }
                 const unsigned bal = __ballot_sync(0xFFFFFFFFu, need);
-                if (bal) {   // queued; full rounds of 32 go through the exact tests
-                    if (need) {
-                        const unsigned pos = qn + (unsigned)__popc(bal & lanemask_lt());
-                        wb.qx[pos] = cur[u].x;
-                        wb.qy[pos] = cur[u].y;
-                        wb.qi[pos] = (unsigned)j;
-                    }
-                    qn += (unsigned)__popc(bal);
-                    __syncwarp();
-                    if (qn >= 32u) {
-                        qn -= 32u;
-                        const float qx = wb.qx[qn + lane], qy = wb.qy[qn + lane];
-                        const unsigned qi = wb.qi[qn + lane];
-                        __syncwarp();
-                        bt_dense_exact(a, P, so, c, rb, cx, cy, wb, cnt, nq, true, qx, qy, qi);
-                    }
+                if (need) {   // queued
+                    const unsigned pos = qn + (unsigned)__popc(bal & lanemask_lt());
+                    wb.qx[pos] = cur[u].x;
+                    wb.qy[pos] = cur[u].y;
+                    wb.qi[pos] = (unsigned)j;
                 }
+                qn += (unsigned)__popc(bal);
+            }
+            __syncwarp();
+            while (qn >= 32u) {   // full rounds of 32 through the exact tests
+                qn -= 32u;
+                const float qx = wb.qx[qn + lane], qy = wb.qy[qn + lane];
+                const unsigned qi = wb.qi[qn + lane];
+                __syncwarp();
+                bt_dense_exact(a, P, so, c, rb, cx, cy, wb, cnt, nq, true, qx, qy, qi);
             }
 #pragma unroll
             for (int u = 0; u < kBDenseU; ++u) cur[u] = nxt[u];
