@@ -395,12 +395,16 @@ def run_ours(args):
     step_roof = {"algorithmic_bytes": step_bytes, "achieved_gbs": step_bytes / (ms / args.steps / 1e3) / 1e9,
                  "frac_of_measured_hbm": step_bytes / (ms / args.steps / 1e3) / 1e9 / peak,
                  "note": "every kernel's algorithmic bytes over the whole step time"}
+    # The serving leg replays a 10 s stream in real time; it runs before the
+    # legs that leave large workspaces behind (the 1e8-point workloads, the
+    # 4096-set batch): measured after them, its p99 rose from about 10 ms to
+    # 35-410 ms (the cause is not the Python garbage collector).
+    serving = run_serving(ch, torch, args) if (args.serve_requests > 0 and world == 1) else None
     filters = run_filters(ch, torch, args, pts, n, sp, peak) if (args.filter_steps > 0 and world == 1) else None
     others = [w for w in args.workloads.split(",") if w and w != args.workload]
     workloads = run_workloads(ch, torch, args, others, sp, peak, peak_src, local) \
         if (others and world == 1) else None
     batched = run_batched(ch, torch, args, sp) if (args.batched_sets > 0 and world == 1) else None
-    serving = run_serving(ch, torch, args) if (args.serve_requests > 0 and world == 1) else None
 
     # End to end through the host-buffer entry point: pinned input, H2D, hull, D2H.
     import ctypes
@@ -751,7 +755,16 @@ def run_serving(ch, torch, args):
         return {"completed": stats["completed"], "wall_s": wall, "latency_ms_p50": stats["p50_ms"],
                 "latency_ms_p99": stats["p99_ms"], "points_per_s": pts_total / wall}
 
-    runs = [serve_once() for _ in range(max(1, args.serve_runs))]
+    # the arrival loop runs in Python: a garbage-collector pass in the middle
+    # of it would hold back the submissions behind it (a burst afterwards),
+    # so the collector is off while the streams are replayed
+    import gc
+    gc.collect()
+    gc.disable()
+    try:
+        runs = [serve_once() for _ in range(max(1, args.serve_runs))]
+    finally:
+        gc.enable()
 
     # the plain path, measured: one thread, one blocking ch_hull_host per
     # request in arrival order, each started no earlier than its arrival
