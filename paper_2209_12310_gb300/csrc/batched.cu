@@ -65,7 +65,7 @@ constexpr int kBOctThreads = 256;      // threads of bt_octagon: a warp per dire
 // kBStarParts evenly spread runs of the set (up to kBStarRun points each).
 constexpr long long kBStarMinPts = 32768;
 constexpr int kBStarParts = 16;
-constexpr int kBStarRun = 65536;
+constexpr int kBStarRun = 16384;
 constexpr int kBDenseSample = 2048;   // points of a set's density test
 static_assert(kBDenseSample <= kBStarMinPts, "the density sample is spread over the set");
 
