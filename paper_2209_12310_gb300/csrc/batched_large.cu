@@ -271,6 +271,7 @@ __global__ void __launch_bounds__(kChainThreads) btl_chain(BLArgs a) {
         if (tid == 0) s_old = (int)atomicAdd(&a.ctl[i].blocks_done[3], 1u);
         __syncthreads();
         if (s_old != 3) continue;
+        CH_MG_DECL
         __threadfence();
         if (tid == 0) s_fail = *(volatile int*)&a.ctl[i].bk_state == 2;
         __syncthreads();
@@ -309,6 +310,7 @@ __global__ void __launch_bounds__(kChainThreads) btl_chain(BLArgs a) {
                     [&](int p, long long& x, long long& y) { x = __ldcg(X + p); y = __ldcg(Y + p); }, ni,
                     a.ctl + i, a.out_idx + base, a.out_n + i);
         __syncthreads();
+        CH_MG(7);   // debug builds: the set's join and stitch
     }
 }
 
@@ -344,3 +346,15 @@ cudaError_t configure_batched_large() {
 }
 
 }  // namespace ch
+
+#ifdef CH_PHASEPROF
+// Debug builds: the merge tree's phase cycles of the batched path (this
+// translation unit's copy of the counters).
+extern "C" int ch_phase_read_batched_merge(unsigned long long* out16) {
+    return cudaMemcpyFromSymbol(out16, ch::g_mg_phase, sizeof(unsigned long long) * 16) == cudaSuccess ? 0 : -4;
+}
+extern "C" int ch_phase_reset_batched_merge(void) {
+    unsigned long long z[16] = {};
+    return cudaMemcpyToSymbol(ch::g_mg_phase, z, sizeof(z)) == cudaSuccess ? 0 : -4;
+}
+#endif

@@ -68,6 +68,51 @@ static __device__ void bridge_block(const ChainPtr& A, int la, const ChainPtr& B
     js = lo;
 }
 
+// Warp-cooperative bridge (all 32 lanes, the same arguments): each round
+// probes 32 evenly spread candidates of the monotone keep predicate, one per
+// lane, and narrows the range to the gap where it turns, so a bridge between
+// chains of a few hundred vertices takes two or three rounds of one
+// sequential inner search instead of a sequential outer one.
+template <bool kGlobal>
+static __device__ void bridge_warp(const ChainPtr& A, int la, const ChainPtr& B, int lb, int& is, int& js) {
+    const int lane = threadIdx.x & 31;
+    // A: largest k with keep_a(k); the predicate holds on [0, is]
+    int lo = 0, hi = la - 1;
+    while (lo < hi) {
+        const long long span = (long long)hi - lo;
+        const int k = lo + 1 + (int)(span * lane / 32);   // in (lo, hi], non-decreasing in lane
+        const unsigned ok = __ballot_sync(0xFFFFFFFFu, keep_a<kGlobal>(A, k, B, lb));
+        if (ok == 0u) {
+            hi = __shfl_sync(0xFFFFFFFFu, k, 0) - 1;
+        } else {
+            const int last = 31 - __clz((int)ok);             // the true probes are a prefix
+            const int klast = __shfl_sync(0xFFFFFFFFu, k, last);
+            const int knext = __shfl_sync(0xFFFFFFFFu, k, last < 31 ? last + 1 : 31);
+            lo = klast;
+            if (last < 31 && knext > klast) hi = knext - 1;
+        }
+    }
+    is = lo;
+    // B: smallest l with keep_b(l); the predicate holds on [js, lb - 1]
+    lo = 0;
+    hi = lb - 1;
+    while (lo < hi) {
+        const long long span = (long long)hi - lo;
+        const int l = lo + (int)(span * lane / 32);       // in [lo, hi), non-decreasing in lane
+        const unsigned ok = __ballot_sync(0xFFFFFFFFu, keep_b<kGlobal>(A, la, B, l, lb));
+        if (ok == 0u) {
+            lo = __shfl_sync(0xFFFFFFFFu, l, 31) + 1;
+        } else {
+            const int first = __ffs((int)ok) - 1;             // the true probes are a suffix
+            const int lfirst = __shfl_sync(0xFFFFFFFFu, l, first);
+            const int lprev = __shfl_sync(0xFFFFFFFFu, l, first > 0 ? first - 1 : 0);
+            hi = lfirst;
+            if (first > 0 && lprev < lfirst) lo = lprev + 1;
+        }
+    }
+    js = lo;
+}
+
 // Block-wide forward copy of n entries, dst <= src (possibly overlapping),
 // in chunks fully loaded before they are stored.
 static __device__ void copy_down(int* du, int* dv, int* di, const int* su, const int* sv, const int* si, int n) {
@@ -112,7 +157,35 @@ static __device__ bool tile_merge_climb(int* su, int* sv, int* si, int* s_len, i
         for (int l = 0; (1 << l) < nseg; ++l) {
             const int g = 1 << l;
             const int npairs = nseg >> (l + 1);
-            if (tid < nseg && (tid & (2 * g - 1)) == 0) {
+            if (npairs <= (int)(blockDim.x >> 5)) {
+                // few, longer pairs: one warp per pair
+                const int lane = tid & 31;
+                for (int p = tid >> 5; p < npairs; p += (int)(blockDim.x >> 5)) {
+                    const int a0 = p * 2 * g, b = a0 + g, la = s_len[a0], lb = s_len[b];
+                    int dst = a0 * seg, src = b * seg, cnt = 0, len = la;
+                    if (lb > 0) {
+                        if (la == 0) {
+                            cnt = lb;
+                            len = lb;
+                        } else {
+                            ChainPtr A{su + a0 * seg, sv + a0 * seg, si + a0 * seg};
+                            ChainPtr B{su + b * seg, sv + b * seg, si + b * seg};
+                            int is, js;
+                            bridge_warp<false>(A, la, B, lb, is, js);
+                            dst += is + 1;
+                            src += js;
+                            cnt = lb - js;
+                            len = is + 1 + cnt;
+                        }
+                    }
+                    if (lane == 0) {
+                        s_mv[p][0] = dst;
+                        s_mv[p][1] = src;
+                        s_mv[p][2] = cnt;
+                        s_len[a0] = len;
+                    }
+                }
+            } else if (tid < nseg && (tid & (2 * g - 1)) == 0) {
                 const int b = tid + g, la = s_len[tid], lb = s_len[b];
                 int dst = tid * seg, src = b * seg, cnt = 0, len = la;
                 if (lb > 0) {
