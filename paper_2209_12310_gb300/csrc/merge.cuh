@@ -157,7 +157,7 @@ static __device__ bool tile_merge_climb(int* su, int* sv, int* si, int* s_len, i
         for (int l = 0; (1 << l) < nseg; ++l) {
             const int g = 1 << l;
             const int npairs = nseg >> (l + 1);
-            if (npairs <= (int)(blockDim.x >> 5)) {
+            if (npairs <= 4 * (int)(blockDim.x >> 5)) {
                 // few, longer pairs: one warp per pair
                 const int lane = tid & 31;
                 for (int p = tid >> 5; p < npairs; p += (int)(blockDim.x >> 5)) {
