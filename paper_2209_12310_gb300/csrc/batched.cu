@@ -641,7 +641,7 @@ __device__ void bt_filter_global(const BArgs& a, long long lo, long long hi, BtW
 }
 
 template <int T, int P>
-__global__ void __launch_bounds__(T) bt_filter(BArgs a) {
+__global__ void __launch_bounds__(T, 1) bt_filter(BArgs a) {
     constexpr int kWarps = T / 32, kF4 = 16 * P;
     constexpr long long kPts = 32ll * P;
     extern __shared__ __align__(128) unsigned char dsm[];
