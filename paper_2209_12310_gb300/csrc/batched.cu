@@ -1262,7 +1262,17 @@ __global__ void __launch_bounds__(kBSmallThreads) bt_hull_small(BArgs a) {
     __shared__ Octagon s_o;
     const int i = blockIdx.x, tid = threadIdx.x;
     Ctl* c = a.ctl + i;
-    if (tid == 0) s_done = *(volatile int*)&c->done;
+    if (tid == 0) {
+        s_done = *(volatile int*)&c->done;
+        // a filter pass that gave up on a copy (CH_ETIMEOUT) left the set's
+        // records incomplete: report the status, compute nothing
+        const int st = read_status(c);
+        if (!s_done && st != CH_OK) {
+            a.out_n[i] = st;
+            c->done = 1;
+            s_done = 1;
+        }
+    }
     __syncthreads();
     if (s_done) return;
     copy_octagon(&s_o, &c->oct);
