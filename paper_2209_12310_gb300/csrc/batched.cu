@@ -439,19 +439,16 @@ __global__ void __launch_bounds__(kBOctThreads) bt_octagon(BArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// The filter of every set, streamed (the loop of Alg. 1/2): the warp tiles
-// and block chunks of bt_extremes.  A warp keeps the octagon of its current
-// set in shared memory; the set's star polygon, when bt_star_build made one,
-// stays in global memory, where the warps of a block (on the same set) share
-// it through L1.  Per point: the octagon's inner region drops it (a whole
-// lane's points at once when their key extremes lie in the region); the star
-// polygon's radius bound of the point's bin drops most points of a dense set
-// (the bounds of a lane's points are loaded together); the points it leaves
-// wait in a per-warp queue and go 32 at a time through the exact wedge test
-// and the hull-rule classification, and the kept ones become records of
-// their queue, staged per warp and written to the set's region with one
-// atomic per batch.  Survivors on a support line of the octagon reduce to
-// the lines' end points (reduce_on_line).
+// The filter of the sets without a star polygon, streamed (the loop of
+// Alg. 1/2): the warp tiles and block chunks of bt_extremes.  A warp keeps
+// the octagon of its current set in shared memory.  Per point: the octagon's
+// inner region drops it (a whole lane's points at once when their key
+// extremes lie in the region); the points it leaves wait in a per-warp queue
+// and go 32 at a time through the hull-rule classification, and the kept
+// ones become records of their queue, staged per warp and written to the
+// set's region with one atomic per batch.  Survivors on a support line of
+// the octagon reduce to the lines' end points (reduce_on_line).  The sets
+// with a star polygon are bt_dense's: their tiles are streamed and skipped.
 constexpr int kBtWarpRecs = 128;
 constexpr int kBtQueue = 64;   // < 32 waiting + 32 added per step
 struct BtWarpSmem {
@@ -462,22 +459,18 @@ struct BtWarpSmem {
     unsigned qi[kBtQueue];
     unsigned char lanes[32];         // lanes whose tile the inner region did not settle
     Ctl* c;                          // the warp's set: control block, record region,
-    long long rb;                    // star polygon and centre,
-    const StarPoly* P;
-    int cx, cy;
+    long long rb;
     unsigned cnt;                    // records staged,
     unsigned nq[4];                  // records per queue
 };
 
 // A warp's current set: what the streaming loop reads stays in registers
-// (warp-uniform); what the exact path needs is in the warp's shared memory.
+// (warp-uniform); what the classification needs is in the warp's shared
+// memory.
 struct BtWarpSet {
     int set = -1;
     long long base = 0;
-    const StarPoly* P = nullptr;   // the set's star polygon, if any
-    int cx = 0, cy = 0;
-    unsigned rmin = 0u;            // its inscribed radius
-    bool skip = true;              // empty or failed: nothing to classify
+    bool skip = true;              // empty, failed, or bt_dense's: nothing to classify
     unsigned qn = 0u;              // points queued
 };
 
@@ -498,26 +491,17 @@ __device__ __forceinline__ void bt_flush_recs(BtWarpSmem& m, uint32_t* keys, uin
 }
 
 // Warp-collective, out of line: one point per lane of the warp's set (valid
-// = false for none), local index li; fast_done: its star radius bound has
-// already failed.  The exact star test, the hull-rule classification, the
+// = false for none), local index li.  The hull-rule classification, the
 // support-line reduction and the staging of the kept records.
-__device__ __noinline__ void bt_classify32(uint32_t* keys, uint64_t* vals, BtWarpSmem& m, bool valid,
-                                           bool fast_done, float x, float y, unsigned li) {
+__device__ __noinline__ void bt_classify32(uint32_t* keys, uint64_t* vals, BtWarpSmem& m, bool valid, float x,
+                                           float y, unsigned li) {
     const int lane = threadIdx.x & 31;
     const Octagon& so = m.o;
-    const StarPoly* P = m.P;
     int r = -1, X = 0, Y = 0;
     if (valid) {
         X = __float2int_rn(x);
         Y = __float2int_rn(y);
-        if (!in_inner(so, X, Y)) {
-            bool drop = false;
-            if (P) {
-                const int px = X - m.cx, py = Y - m.cy, bn = star_bin(px, py);
-                drop = (!fast_done && star_inside_fast(px, py, bn, *P)) || star_inside_exact(px, py, bn, *P);
-            }
-            if (!drop) r = classify_hull(x, y, so);
-        }
+        r = classify_hull(x, y, so);
     }
     bool keep = r >= 0;
     if (!__any_sync(0xFFFFFFFFu, keep)) return;
@@ -565,7 +549,7 @@ __device__ __forceinline__ void bt_queue_push(const BArgs& a, BtWarpSet& w, BtWa
         const float qx = m.qx[w.qn + lane], qy = m.qy[w.qn + lane];
         const unsigned qi = m.qi[w.qn + lane];
         __syncwarp();
-        bt_classify32(a.keys, a.vals, m, true, true, qx, qy, qi);
+        bt_classify32(a.keys, a.vals, m, true, qx, qy, qi);
     }
 }
 
@@ -579,7 +563,7 @@ __device__ __forceinline__ void bt_warp_done(const BArgs& a, BtWarpSmem& m, BtWa
         const unsigned qi = valid ? m.qi[lane] : 0u;
         __syncwarp();
         w.qn = 0u;
-        bt_classify32(a.keys, a.vals, m, valid, true, qx, qy, qi);
+        bt_classify32(a.keys, a.vals, m, valid, qx, qy, qi);
     }
     bt_flush_recs(m, a.keys, a.vals);
     if (lane < 4 && m.nq[lane]) atomicAdd(&m.c->counts4[lane], m.nq[lane]);
@@ -598,16 +582,9 @@ __device__ __forceinline__ void bt_warp_set(const BArgs& a, int q, BtWarpSet& w,
     // empty and failed sets (bt_octagon's verdict), and the sets with a star
     // polygon, which bt_dense filters
     w.skip = *(volatile int*)&c->done != 0 || (slot >= 0 && c->star_k > 0);
-    w.P = nullptr;
-    w.rmin = w.P ? w.P->rmin : 0u;
-    w.cx = c->star_cx;
-    w.cy = c->star_cy;
     if (lane == 0) {
         m.c = c;
         m.rb = region_base(a, q);
-        m.P = w.P;
-        m.cx = w.cx;
-        m.cy = w.cy;
         m.cnt = 0u;
     }
     if (lane < 4) m.nq[lane] = 0u;
@@ -635,7 +612,7 @@ __device__ void bt_filter_global(const BArgs& a, long long lo, long long hi, BtW
             const long long j = j0 + lane;
             const bool valid = j < e;
             const float2 p = valid ? reinterpret_cast<const float2*>(a.pts)[j] : make_float2(0.0f, 0.0f);
-            bt_classify32(a.keys, a.vals, m, valid, false, p.x, p.y, (unsigned)(j - qb));
+            bt_classify32(a.keys, a.vals, m, valid, p.x, p.y, (unsigned)(j - qb));
         }
     }
 }
@@ -693,15 +670,13 @@ __global__ void __launch_bounds__(T, 1) bt_filter(BArgs a) {
                     // The points of the lanes whose tile failed are spread over
                     // the warp, 32 at a time (slot s: failing lane of rank
                     // s / P, its point s % P, in float4 (s % P) / 2, half s % 2).
-                    // A point needs the exact tests unless the inner region or,
-                    // with a star polygon, its inscribed radius or the bound of
-                    // the point's bin settles it.
+                    // A point outside the inner region waits for the
+                    // classification.
                     const unsigned fail = __ballot_sync(0xFFFFFFFFu, !inside);
                     if (fail) {
                         if (!inside) m.lanes[__popc(fail & lanemask_lt())] = (unsigned char)lane;
                         __syncwarp();
                         const unsigned slots = (unsigned)P * (unsigned)__popc(fail);
-                        const long long r0 = w.rmin;
 #pragma unroll 1
                         for (unsigned s0 = 0; s0 < slots; s0 += 32u) {
                             const unsigned sl = s0 + (unsigned)lane;
@@ -715,16 +690,7 @@ __global__ void __launch_bounds__(T, 1) bt_filter(BArgs a) {
                                 x = p.x;
                                 y = p.y;
                                 li = (unsigned)(p0 - w.base) + (unsigned)f2;
-                                const int X = __float2int_rn(x), Y = __float2int_rn(y);
-                                if (w.P) {   // the inscribed radius first: it settles most points of dense data
-                                    const long long px = X - w.cx, py = Y - w.cy, d2 = px * px + py * py;
-                                    if (d2 >= r0 * r0 && !in_inner(so, X, Y)) {
-                                        const long long r = __ldg(&w.P->rin[star_bin((int)px, (int)py)]);
-                                        need = d2 >= r * r;
-                                    }
-                                } else {
-                                    need = !in_inner(so, X, Y);
-                                }
+                                need = !in_inner(so, __float2int_rn(x), __float2int_rn(y));
                             }
                             bt_queue_push(a, w, m, need, x, y, li);
                         }
@@ -742,7 +708,7 @@ __global__ void __launch_bounds__(T, 1) bt_filter(BArgs a) {
                     for (int j = 0; j < P; ++j) {
                         const long long i = p0 + 2 * ((j >> 1) * 32 + lane) + (j & 1);
                         const float2 p = cur2[2 * ((j >> 1) * 32 + lane) + (j & 1)];
-                        bt_classify32(a.keys, a.vals, m, i >= qb && i < qe, false, p.x, p.y, (unsigned)(i - qb));
+                        bt_classify32(a.keys, a.vals, m, i >= qb && i < qe, p.x, p.y, (unsigned)(i - qb));
                     }
                 }
             }
