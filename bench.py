@@ -685,6 +685,25 @@ def run_batched(ch, torch, args, sp):
                       "device array of per-set flags)"}
 
 
+def batch_trace_summary(trace):
+    """Per-batch server trace (ch_server_trace) in a few numbers: p50 / p99 of
+    the batch size and of each phase, and the mean phases of the slowest 1 %
+    of the batches (by host time from formation to retirement)."""
+    if not trace:
+        return None
+    import numpy as np
+    t = np.array(trace, dtype=np.float64)
+    cols = {"requests": 1, "points": 2, "copy_in_ms": 3, "hull_ms": 4, "copy_out_ms": 5, "host_ms": 6}
+    out = {"batches": int(t.shape[0]), "sets_redone": int(t[:, 7].sum())}
+    for name, c in cols.items():
+        out[name + "_p50"] = float(np.percentile(t[:, c], 50))
+        out[name + "_p99"] = float(np.percentile(t[:, c], 99))
+    slow = t[t[:, 6] >= np.percentile(t[:, 6], 99)]
+    out["slowest_1pct_mean"] = {name: float(slow[:, c].mean()) for name, c in cols.items()}
+    out["slowest_1pct_mean"]["sets_redone"] = float(slow[:, 7].mean())
+    return out
+
+
 def run_serving(ch, torch, args):
     """Poisson request stream (20,000/s, sizes log-uniform [1e3, 1e7], 50% normal /
     40% uniform / 10% ring) replayed for its first R requests into the
@@ -750,10 +769,12 @@ def run_serving(ch, torch, args):
                 time.sleep(0.0002)
             wall = time.perf_counter() - t0
             stats = ch.ch_server_stats(srv)
+            trace = ch.ch_server_trace(srv)
         finally:
             ch.ch_server_destroy(srv)
         return {"completed": stats["completed"], "wall_s": wall, "latency_ms_p50": stats["p50_ms"],
-                "latency_ms_p99": stats["p99_ms"], "points_per_s": pts_total / wall}
+                "latency_ms_p99": stats["p99_ms"], "points_per_s": pts_total / wall,
+                "batches": batch_trace_summary(trace)}
 
     # the arrival loop runs in Python: a garbage-collector pass in the middle
     # of it would hold back the submissions behind it (a burst afterwards),

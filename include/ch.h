@@ -317,6 +317,17 @@ int ch_submit(void* srv, const float* pts_host, int64_t n, uint64_t* ticket);
 int ch_poll(void* srv, uint64_t ticket, int32_t* out_idx_host, int64_t cap, int64_t* out_n);
 int ch_server_stats(void* srv, double* p50_ms, double* p99_ms, double* points_per_s,
                     int64_t* completed);
+/*
+ * ch_server_trace -- the server's retired batches, in order, 8 values each:
+ * formation time (ms since the first submission), requests, points, time
+ * of the host-to-device copies, of the batched hull with its result counts
+ * back, of the index copies back (device time, CUDA events on the batch's
+ * stream, ms), host time from formation to retirement (ms), and the sets
+ * the batched kernels left to the single-hull path.  Writes up to cap
+ * batches to out (8 cap doubles; out may be NULL when cap == 0) and returns
+ * how many batches were traced (at most 2^20 are kept).
+ */
+int ch_server_trace(void* srv, double* out, int64_t cap);
 int ch_server_destroy(void* srv);
 
 #ifdef __cplusplus

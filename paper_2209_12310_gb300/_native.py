@@ -58,6 +58,7 @@ SIGNATURES = {
     "ch_poll": (_INT, [_P, ctypes.c_uint64, _P, _I64, ctypes.POINTER(_I64)]),
     "ch_server_stats": (_INT, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)]),
+    "ch_server_trace": (_INT, [_P, _P, _I64]),
     "ch_server_destroy": (_INT, [_P]),
 }
 
@@ -213,6 +214,16 @@ def ch_server_stats(srv):
                                   ctypes.byref(done)), "ch_server_stats")
     return {"p50_ms": p50.value, "p99_ms": p99.value, "points_per_s": pps.value,
             "completed": done.value}
+
+
+def ch_server_trace(srv):
+    """The server's retired batches: a list of 8-tuples (formation ms, requests,
+    points, copy-in ms, hull ms, index-copy ms, host ms, sets redone)."""
+    lib = load()
+    n = _check(lib.ch_server_trace(srv, None, 0), "ch_server_trace")
+    buf = (ctypes.c_double * (8 * max(n, 1)))()
+    n = min(n, _check(lib.ch_server_trace(srv, ctypes.addressof(buf), n), "ch_server_trace"))
+    return [tuple(buf[8 * i:8 * i + 8]) for i in range(n)]
 
 
 def ch_server_destroy(srv):

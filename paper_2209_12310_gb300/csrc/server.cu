@@ -96,6 +96,10 @@ struct Slot {
     int phase = 0;   // 1: waiting for counts, 2: waiting for indices
     cudaStream_t s = nullptr;
     cudaEvent_t ev = nullptr;
+    cudaEvent_t te[4] = {};        // timing: copies in start / end, hull and counts end, indices end
+    double t_form = 0;             // host time the batch was formed
+    int64_t batch_points = 0;
+    int redo_sets = 0;             // sets the batched kernels left to the single-hull path
     std::vector<Req*> reqs;
     std::vector<int64_t> off;       // host copy of the batch offsets
     int64_t* h_off = nullptr;       // pinned offsets (k + 1)
@@ -109,6 +113,8 @@ struct Slot {
 };
 
 constexpr size_t kMaxQueue = 1u << 17;
+constexpr int kBatchTrace = 8;
+constexpr size_t kMaxTrace = 1u << 20;   // batches traced at most
 constexpr int kMaxBatch = 4096;
 constexpr int kSlots = 3;
 
@@ -135,6 +141,7 @@ struct Server {
     std::atomic<bool> stop{false};
     std::thread engine;
     std::vector<double> lat_ms;
+    std::vector<double> trace;   // per batch: kBatchTrace values (ch_server_trace)
     int64_t served_points = 0, completed = 0;
     double t_first = 0, t_last = 0;
     int fatal = CH_OK;
@@ -171,6 +178,8 @@ bool Server::retire(Slot& sl) {
                 cudaMemsetAsync(d_n, 0xFF, 8 * k, sl.s);
             cudaMemcpyAsync(sl.h_n, d_n, 8 * k, cudaMemcpyDeviceToHost, sl.s);
             cudaEventRecord(sl.ev, sl.s);
+            sl.redo_sets = 0;
+            for (size_t i = 0; i < k; ++i) sl.redo_sets += sl.h_redo[i] != 0;
             return true;
         }
     }
@@ -193,6 +202,7 @@ bool Server::retire(Slot& sl) {
                 o += (size_t)h;
             }
         }
+        cudaEventRecord(sl.te[3], sl.s);
         cudaEventRecord(sl.ev, sl.s);
         sl.phase = 2;
         return true;
@@ -218,6 +228,16 @@ bool Server::retire(Slot& sl) {
         served_points += r->n;
         ++completed;
         t_last = t;
+    }
+    if (trace.size() < kMaxTrace * kBatchTrace) {
+        float h2d = 0.f, hull = 0.f, idx = 0.f;
+        if (cudaEventElapsedTime(&h2d, sl.te[0], sl.te[1]) != cudaSuccess) h2d = -1.f;
+        if (cudaEventElapsedTime(&hull, sl.te[1], sl.te[2]) != cudaSuccess) hull = -1.f;
+        if (cudaEventElapsedTime(&idx, sl.te[2], sl.te[3]) != cudaSuccess) idx = -1.f;
+        const double v[kBatchTrace] = {(sl.t_form - t_first) * 1e3, (double)k, (double)sl.batch_points,
+                                       (double)h2d, (double)hull, (double)idx, (t - sl.t_form) * 1e3,
+                                       (double)sl.redo_sets};
+        trace.insert(trace.end(), v, v + kBatchTrace);
     }
     arena.release(sl.arena_off, sl.arena_bytes);
     sl.reqs.clear();
@@ -278,16 +298,22 @@ bool Server::launch(Slot& sl) {
     int32_t* d_idx = (int32_t*)(base + align256(8 * (size_t)points));
     int64_t* d_off = (int64_t*)(base + align256(8 * (size_t)points) + align256(4 * (size_t)points));
     int64_t* d_n = (int64_t*)((char*)d_off + align256(8 * (k + 1)));
+    sl.t_form = now_s();
+    sl.batch_points = points;
+    sl.redo_sets = 0;
+    cudaEventRecord(sl.te[0], sl.s);
     for (size_t i = 0; i < k; ++i)
         cudaMemcpyAsync(d_pts + 2 * sl.off[i], batch[i]->host, 8 * (size_t)batch[i]->n, cudaMemcpyHostToDevice,
                         sl.s);
     cudaMemcpyAsync(d_off, sl.h_off, 8 * (k + 1), cudaMemcpyHostToDevice, sl.s);
+    cudaEventRecord(sl.te[1], sl.s);
     std::memset(sl.h_redo, 0, k);
     sl.redone = false;
     // no host synchronisation: the batch overlaps with the other slot's
     const int st = hull_batched_impl(d_pts, d_off, (int32_t)k, d_idx, d_n, sl.h_off, sl.s, false, sl.h_redo);
     if (st != CH_OK) cudaMemsetAsync(d_n, 0xFF, 8 * k, sl.s);   // -1 = CH_EINVAL per set
     cudaMemcpyAsync(sl.h_n, d_n, 8 * k, cudaMemcpyDeviceToHost, sl.s);
+    cudaEventRecord(sl.te[2], sl.s);
     cudaEventRecord(sl.ev, sl.s);
     sl.reqs = std::move(batch);
     sl.arena_off = off;
@@ -344,12 +370,16 @@ int ch_server_create(size_t budget_bytes, int device, void** srv) {
         if (cudaStreamCreateWithFlags(&S->slots[i].s, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&S->slots[i].ev, cudaEventDisableTiming) != cudaSuccess)
             st = CH_ECUDA;
+        for (int e = 0; st == CH_OK && e < 4; ++e)
+            if (cudaEventCreate(&S->slots[i].te[e]) != cudaSuccess) st = CH_ECUDA;
         else
             st = ch_reserve(S->max_points, kMaxBatch, S->slots[i].s);
     }
     if (st != CH_OK) {
         for (auto& sl : S->slots) {
             if (sl.ev) cudaEventDestroy(sl.ev);
+            for (cudaEvent_t e : sl.te)
+                if (e) cudaEventDestroy(e);
             if (sl.s) cudaStreamDestroy(sl.s);
         }
         if (S->arena_base) cudaFree(S->arena_base);
@@ -430,6 +460,16 @@ int ch_server_stats(void* srv, double* p50_ms, double* p99_ms, double* points_pe
     return CH_OK;
 }
 
+int ch_server_trace(void* srv, double* out, int64_t cap) {
+    Server* S = (Server*)srv;
+    if (!S || cap < 0 || (cap > 0 && !out)) return CH_EINVAL;
+    std::lock_guard<std::mutex> lk(S->mu);
+    const int64_t n = (int64_t)(S->trace.size() / kBatchTrace);
+    const int64_t m = std::min(n, cap);
+    if (m > 0) std::memcpy(out, S->trace.data(), sizeof(double) * kBatchTrace * (size_t)m);
+    return (int)std::min<int64_t>(n, INT32_MAX);
+}
+
 int ch_server_destroy(void* srv) {
     Server* S = (Server*)srv;
     if (!S) return CH_EINVAL;
@@ -442,6 +482,8 @@ int ch_server_destroy(void* srv) {
     for (auto& sl : S->slots) {
         if (sl.s) cudaStreamSynchronize(sl.s);
         if (sl.ev) cudaEventDestroy(sl.ev);
+        for (cudaEvent_t e : sl.te)
+            if (e) cudaEventDestroy(e);
         if (sl.h_off) cudaFreeHost(sl.h_off);
         if (sl.h_n) cudaFreeHost(sl.h_n);
         if (sl.h_redo) cudaFreeHost(sl.h_redo);

@@ -56,6 +56,12 @@ def test_server_mix_matches_oracle(lib):
         stats = lib.ch_server_stats(srv)
         assert stats["completed"] == len(reqs) + 1
         assert stats["p99_ms"] >= stats["p50_ms"] > 0
+        # the per-batch trace accounts for every request and point
+        trace = lib.ch_server_trace(srv)
+        assert sum(b[1] for b in trace) == len(reqs) + 1
+        assert sum(b[2] for b in trace) == sum(p.shape[0] for p in reqs) + p.shape[0]
+        for b in trace:
+            assert b[1] >= 1 and min(b[3], b[4], b[5]) >= 0.0 and b[6] > 0.0
     finally:
         lib.ch_server_destroy(srv)
 
