@@ -9,7 +9,7 @@ stream to them.  There is no CPU fallback.
 from __future__ import annotations
 
 from ._native import (CH_EBUSY, CH_ECUDA, CH_EINVAL, CH_ENOMEM, CH_ERANGE, CH_ETIMEOUT, CH_OK,  # noqa: F401
-                      CH_PENDING, CHError, LIB_PATH, ch_batched_config, ch_batched_counters, ch_filter, ch_filter16, ch_filter_manhattan, ch_hull,
+                      CH_MAX_POINTS, CH_PENDING, CHError, LIB_PATH, ch_batched_config, ch_batched_counters, ch_filter, ch_filter16, ch_filter_manhattan, ch_hull,
                       ch_hull_batched, ch_hull_counters, ch_hull_host,
                       ch_poll, ch_profile_enable, ch_profile_read, ch_profile_reset, ch_release,
                       ch_reserve, ch_server_create, ch_server_destroy, ch_server_stats, ch_server_trace, ch_strerror,

@@ -22,6 +22,7 @@ CH_ENOMEM = -3
 CH_ECUDA = -4
 CH_ETIMEOUT = -5
 CH_EBUSY = -6
+CH_MAX_POINTS = 0x7FFFFFF0   # largest point count of one hull (indices are int32)
 
 _lock = threading.Lock()
 _lib = None

@@ -65,6 +65,21 @@ def test_host_side_checks_without_gpu(native):
     assert ch.ch_strerror(ch.CH_ERANGE).startswith("coordinate")
 
 
+def test_point_count_limit_without_gpu(native):
+    """One point past CH_MAX_POINTS is refused by every entry point that
+    takes a point count, before any device work (the pointers are never
+    dereferenced)."""
+    import paper_2209_12310_gb300 as ch
+    text = open(HEADER).read()
+    assert int(re.search(r"#define CH_MAX_POINTS \(\(int64_t\)(0x[0-9A-Fa-f]+)\)", text).group(1), 16) == ch.CH_MAX_POINTS
+    over = ch.CH_MAX_POINTS + 1
+    assert native.ch_hull(8, over, 64, 64, None) == ch.CH_EINVAL
+    assert native.ch_hull_host(8, over, 64, 64, None) == ch.CH_EINVAL
+    assert native.ch_filter(8, over, 64, None, None, None) == ch.CH_EINVAL
+    assert native.ch_filter16(8, over, 64, None, None, None) == ch.CH_EINVAL
+    assert native.ch_filter_manhattan(8, over, 64, None, None, None) == ch.CH_EINVAL
+
+
 def test_workspace_size_is_linear(native):
     import paper_2209_12310_gb300 as ch
     a = ch.ch_workspace_bytes(1_000_000)

@@ -1,0 +1,117 @@
+"""The largest input one hull accepts: CH_MAX_POINTS = 2^31 - 16 points
+(17 GB of float32 pairs) through ch_hull, at an aligned and at an 8- but not
+16-byte aligned base address.
+
+It covers the streaming passes' point and tile numbering at the top of the
+int32 index range, the ragged tail after the last warp tile, and the lowest
+index rule (Alg. 1's output convention) for equal points that lie far apart.
+
+The expected hull is fixed by construction.  Every random point lies in a
+box strictly inside a planted polygon, so the hull of all the points is the
+hull of the planted points.  The oracle computes that hull from the planted
+points alone, kept in index order, so its lowest-index rule picks the same
+copy as it would among all the points."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+C = 1 << 23                # centre of the coordinate domain [0, 2^24)
+R_BOX = 1 << 22            # the random points: integers in [C - R_BOX, C + R_BOX)
+R_POLY = (1 << 23) - 1000  # circumradius of the planted polygon
+NEEDED_BYTES = 125 * 10**9  # points, output, the library's workspace and headroom
+
+
+def _polygon(k=12, phase=0.1):
+    a = phase + 2 * math.pi * np.arange(k) / k
+    return np.stack([np.rint(C + R_POLY * np.cos(a)), np.rint(C + R_POLY * np.sin(a))], 1).astype(np.int64)
+
+
+def _box_strictly_inside(poly):
+    lo, hi = C - R_BOX, C + R_BOX - 1
+    corners = [(lo, lo), (hi, lo), (hi, hi), (lo, hi)]
+    k = poly.shape[0]
+    for j in range(k):
+        ax, ay = poly[j]
+        bx, by = poly[(j + 1) % k]
+        for px, py in corners:
+            if (bx - ax) * (py - ay) - (by - ay) * (px - ax) <= 0:
+                return False
+    return True
+
+
+def _expected(planted, offset, n):
+    """The oracle's hull of the planted points that fall in the view
+    [offset, offset + n) of the buffer, as view indices."""
+    idx = np.array(sorted(i for i in planted if offset <= i < offset + n), dtype=np.int64)
+    pts = np.array([planted[i] for i in idx], dtype=np.float32)
+    return (idx[oracle.hull(pts)] - offset).astype(np.int64)
+
+
+def test_largest_single_hull(lib):
+    n = lib.CH_MAX_POINTS
+    lib.ch_release()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    free, _ = torch.cuda.mem_get_info()
+    if free < NEEDED_BYTES:
+        pytest.skip(f"needs {NEEDED_BYTES / 1e9:.0f} GB of free device memory, {free / 1e9:.0f} GB free")
+
+    poly = _polygon()
+    assert _box_strictly_inside(poly)
+    tiles = n // 512
+    tail = tiles * 512                     # first point of the ragged tail (aligned view)
+    # buffer positions of the planted vertices; the buffer holds n + 1 points,
+    # view A is [0, n) (aligned, no head point), view B is [1, n + 1) (one
+    # head point before the first 16-byte boundary)
+    where = {
+        0: [0, 1],                         # A: the first point; B: its first point too
+        1: [n - 1, n],                     # A: the last point; B: the last two
+        2: [511, 512],                     # both sides of a warp-tile boundary
+        3: [tail],                         # first point of A's tail
+        4: [1000, (1 << 31) - (1 << 20)],  # equal points 2^31 apart: the lower index wins
+        5: [tail - 1],                     # last point of A's last full tile
+        6: [1 << 30],
+        7: [(1 << 30) + 1, (1 << 30) + 7],
+    }
+    rng = np.random.default_rng(29)
+    used = {p for ps in where.values() for p in ps}
+    for v in range(8, poly.shape[0]):
+        p = int(rng.integers(2, n - 1))
+        while p in used:
+            p = int(rng.integers(2, n - 1))
+        where[v] = [p]
+        used.add(p)
+    planted = {p: (float(poly[v, 0]), float(poly[v, 1])) for v, ps in where.items() for p in ps}
+
+    buf = torch.empty((n + 1, 2), dtype=torch.float32, device="cuda")
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(2209)
+    buf.random_(C - R_BOX, C + R_BOX, generator=gen)
+    pos = torch.tensor(sorted(planted), dtype=torch.int64, device="cuda")
+    val = torch.tensor([planted[p] for p in sorted(planted)], dtype=torch.float32, device="cuda")
+    buf[pos] = val
+    out_idx = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+    out_n = torch.full((1,), -99, dtype=torch.int64, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    try:
+        for offset in (0, 1):
+            view = buf[offset:offset + n]
+            want = _expected(planted, offset, n)
+            for _ in range(2):   # the first call and a replay of its captured graph
+                out_n.fill_(-99)
+                lib.ch_hull(view.data_ptr(), n, out_idx.data_ptr(), out_n.data_ptr(), s)
+                h = int(out_n.item())
+                assert h == want.size, (offset, h, want.size)
+                np.testing.assert_array_equal(out_idx[:h].cpu().numpy().astype(np.int64), want)
+        assert want.size == poly.shape[0]
+    finally:
+        del buf, out_idx, out_n, pos, val
+        torch.cuda.synchronize()
+        lib.ch_release()
+        torch.cuda.empty_cache()
