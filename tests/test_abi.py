@@ -56,6 +56,7 @@ def test_host_side_checks_without_gpu(native):
     assert native.ch_filter16(None, 10, 64, None, None, None) == ch.CH_EINVAL     # null pts, n > 0
     assert native.ch_hull_batched(None, None, -1, None, None, None, None) == ch.CH_EINVAL
     assert native.ch_hull_batched(None, None, 0, None, None, None, None) == ch.CH_OK
+    assert native.ch_hull_batched(None, None, (1 << 20) + 1, None, None, None, None) == ch.CH_EINVAL  # k > 2^20
     assert native.ch_batched_counters(None, 4, None) == ch.CH_EINVAL                 # null out
     assert native.ch_batched_counters(None, 0, (ctypes.c_int64 * 4)()) == ch.CH_EINVAL  # k < 1
     assert native.ch_filter_manhattan(None, -5, None, None, None, None) == ch.CH_EINVAL

@@ -1,22 +1,24 @@
-"""The largest input one hull accepts: CH_MAX_POINTS = 2^31 - 16 points
-(17 GB of float32 pairs) through ch_hull, at an aligned and at an 8- but not
-16-byte aligned base address.
+"""The largest inputs: one hull of CH_MAX_POINTS = 2^31 - 16 points (17 GB of
+float32 pairs) through ch_hull, at an aligned and at an 8- but not 16-byte
+aligned base address; and a batch of the most sets ch_hull_batched takes
+(2^20), nearly all of them tiny.
 
 It covers the streaming passes' point and tile numbering at the top of the
 int32 index range, the ragged tail after the last warp tile, and the lowest
 index rule (Alg. 1's output convention) for equal points that lie far apart.
 
-The expected hull is fixed by construction.  Every random point lies in a
-box strictly inside a planted polygon, so the hull of all the points is the
-hull of the planted points.  The oracle computes that hull from the planted
-points alone, kept in index order, so its lowest-index rule picks the same
-copy as it would among all the points."""
+For the single hull the expected result is fixed by construction.  Every
+random point lies in a box strictly inside a planted polygon, so the hull of
+all the points is the hull of the planted points.  The oracle computes that
+hull from the planted points alone, kept in index order, so its lowest-index
+rule picks the same copy as it would among all the points."""
 import math
 
 import numpy as np
 import pytest
 
 import oracle
+from synth import workloads as W
 
 torch = pytest.importorskip("torch")
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
@@ -115,3 +117,50 @@ def test_largest_single_hull(lib):
         torch.cuda.synchronize()
         lib.ch_release()
         torch.cuda.empty_cache()
+
+
+def test_batched_largest_set_count(lib):
+    """2^20 sets: empty, one-point and tiny sets on a 4 x 4 grid (duplicates
+    and collinear runs everywhere, some at the top of the coordinate domain),
+    every 4096th set a few thousand points of the three workload kinds, and
+    rings of 40,000 points (star polygons) first, in the middle and last.
+    Every set's local index list equals the oracle's."""
+    k = 1 << 20
+    rng = np.random.default_rng(31)
+    sizes = rng.choice([0, 1, 2, 3, 4, 5, 8], size=k, p=[0.05, 0.15, 0.2, 0.2, 0.15, 0.15, 0.1])
+    sets = [None] * k
+    kinds = ("uniform", "normal", "ring")
+    for i in range(k):
+        if i in (0, k // 2, k - 1):
+            sets[i] = W.make("ring", 40_000, 100 + i % 7)
+        elif i % 4096 == 4095:
+            sets[i] = W.make(kinds[(i // 4096) % 3], 2000 + (i // 4096) * 16, i)
+        else:
+            g = rng.integers(0, 4, (int(sizes[i]), 2))
+            if i % 5 == 0:
+                g = (1 << 24) - 1 - g   # the top corner of the domain
+            sets[i] = g.astype(np.float32)
+    offsets = np.zeros(k + 1, np.int64)
+    offsets[1:] = np.cumsum([s.shape[0] for s in sets])
+    pts = np.ascontiguousarray(np.concatenate(sets))
+    d_pts = torch.from_numpy(pts).cuda()
+    d_off = torch.from_numpy(offsets).cuda()
+    out_idx = torch.full((int(offsets[-1]),), -7, dtype=torch.int32, device="cuda")
+    out_n = torch.full((k,), -99, dtype=torch.int64, device="cuda")
+    st = lib.load().ch_hull_batched(d_pts.data_ptr(), d_off.data_ptr(), k, out_idx.data_ptr(), out_n.data_ptr(),
+                                    offsets.ctypes.data, torch.cuda.current_stream().cuda_stream)
+    assert st == 0
+    ns = out_n.cpu().numpy()
+    idx = out_idx.cpu().numpy()
+    bad = []
+    for i in range(k):
+        want = oracle.hull(sets[i])
+        got = idx[offsets[i]:offsets[i] + max(int(ns[i]), 0)]
+        if ns[i] != want.size or not np.array_equal(got, want):
+            bad.append(i)
+            if len(bad) >= 5:
+                break
+    assert not bad, [(i, int(ns[i]), sets[i].shape[0]) for i in bad]
+    c = lib.ch_batched_counters(k, torch.cuda.current_stream().cuda_stream)
+    for i in (0, k // 2, k - 1):
+        assert c[i]["star_vertices"] > 0, (i, c[i])
