@@ -164,3 +164,85 @@ def test_batched_largest_set_count(lib):
     c = lib.ch_batched_counters(k, torch.cuda.current_stream().cuda_stream)
     for i in (0, k // 2, k - 1):
         assert c[i]["star_vertices"] > 0, (i, c[i])
+
+
+def test_batched_largest_total(lib):
+    """A batch of CH_MAX_POINTS points in all (the most one call takes),
+    starting 8 bytes past a 16-byte boundary: two sets of about 2^30 points
+    each (random points in a box strictly inside a planted 12-gon, copies of
+    the vertices at the set's first and last points and 2^29 apart) among
+    1002 tiny sets, the last of them in the batch's ragged tail.  Every set's
+    local index list equals the oracle's (for the two large sets, on their
+    planted points alone, as in the single-hull test)."""
+    n = lib.CH_MAX_POINTS
+    lib.ch_release()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    free, _ = torch.cuda.mem_get_info()
+    if free < NEEDED_BYTES:
+        pytest.skip(f"needs {NEEDED_BYTES / 1e9:.0f} GB of free device memory, {free / 1e9:.0f} GB free")
+    rng = np.random.default_rng(37)
+    tiny = [rng.integers(0, 6, (int(m), 2)).astype(np.float32) for m in rng.integers(0, 9, 1002)]
+    tiny[0] = np.array([[3, 3], [1, 2], [3, 3]], np.float32)
+    tiny[-1] = np.array([[7, 1], [2, 9]], np.float32)
+    n_tiny = sum(t.shape[0] for t in tiny)
+    n_a = (1 << 30) + 3
+    n_b = n - n_a - n_tiny
+    # set order: tiny[0], A, tiny[1..1000], B, tiny[1001]
+    sizes = [tiny[0].shape[0], n_a] + [t.shape[0] for t in tiny[1:-1]] + [n_b, tiny[-1].shape[0]]
+    k = len(sizes)
+    offsets = np.zeros(k + 1, np.int64)
+    offsets[1:] = np.cumsum(sizes)
+    assert offsets[-1] == n
+    ia, ib = 1, k - 2
+    poly = _polygon()
+    assert _box_strictly_inside(poly)
+    planted = {}
+    for set_i, extra in ((ia, 0), (ib, 5)):
+        m = sizes[set_i]
+        where = [[0, 1 << 29], [m - 1], [511 - extra], [m // 2, m // 2 + 1]]
+        used = {p for ps in where for p in ps}
+        while len(where) < poly.shape[0]:
+            p = int(rng.integers(2, m - 2))
+            if p not in used:
+                where.append([p])
+                used.add(p)
+        planted[set_i] = {p: (float(poly[v, 0]), float(poly[v, 1])) for v, ps in enumerate(where) for p in ps}
+
+    buf = torch.empty((n + 1, 2), dtype=torch.float32, device="cuda")
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(2210)
+    buf.random_(C - R_BOX, C + R_BOX, generator=gen)
+    view = buf[1:]   # 8 bytes past a 16-byte boundary: one head point
+    tiny_sets = [0] + list(range(2, k - 2)) + [k - 1]
+    for t, set_i in zip(tiny, tiny_sets):
+        if t.shape[0]:
+            view[int(offsets[set_i]):int(offsets[set_i + 1])] = torch.from_numpy(t).cuda()
+    for set_i, pl in planted.items():
+        pos = torch.tensor([int(offsets[set_i]) + p for p in sorted(pl)], dtype=torch.int64, device="cuda")
+        view[pos] = torch.tensor([pl[p] for p in sorted(pl)], dtype=torch.float32, device="cuda")
+    d_off = torch.from_numpy(offsets).cuda()
+    out_idx = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+    out_n = torch.full((k,), -99, dtype=torch.int64, device="cuda")
+    try:
+        st = lib.load().ch_hull_batched(view.data_ptr(), d_off.data_ptr(), k, out_idx.data_ptr(), out_n.data_ptr(),
+                                        offsets.ctypes.data, torch.cuda.current_stream().cuda_stream)
+        assert st == 0
+        ns = out_n.cpu().numpy()
+        for set_i in range(k):
+            if set_i in planted:
+                pl = planted[set_i]
+                idx = np.array(sorted(pl), dtype=np.int64)
+                want = idx[oracle.hull(np.array([pl[p] for p in idx], np.float32))]
+            else:
+                want = oracle.hull(tiny[tiny_sets.index(set_i)])
+            o = int(offsets[set_i])
+            assert ns[set_i] == want.size, (set_i, int(ns[set_i]), want.size)
+            got = out_idx[o:o + want.size].cpu().numpy().astype(np.int64)
+            np.testing.assert_array_equal(got, want, err_msg=str(set_i))
+        assert planted[ia] and ns[ia] == poly.shape[0] and ns[ib] == poly.shape[0]
+    finally:
+        del buf, view, d_off, out_idx, out_n
+        torch.cuda.synchronize()
+        lib.ch_release()
+        torch.cuda.empty_cache()
