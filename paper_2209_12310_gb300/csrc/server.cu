@@ -372,8 +372,7 @@ int ch_server_create(size_t budget_bytes, int device, void** srv) {
             st = CH_ECUDA;
         for (int e = 0; st == CH_OK && e < 4; ++e)
             if (cudaEventCreate(&S->slots[i].te[e]) != cudaSuccess) st = CH_ECUDA;
-        else
-            st = ch_reserve(S->max_points, kMaxBatch, S->slots[i].s);
+        if (st == CH_OK) st = ch_reserve(S->max_points, kMaxBatch, S->slots[i].s);
     }
     if (st != CH_OK) {
         for (auto& sl : S->slots) {
