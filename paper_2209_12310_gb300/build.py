@@ -65,9 +65,18 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             jobs.append([nvcc, *_flags(), *extra_flags, "-c", src, "-o", obj])
 
     def run(cmd):
+        # every output is written under a private name and renamed into
+        # place, so that processes building at the same time (one per rank)
+        # never see a partly written object or library
+        out = cmd[cmd.index("-o") + 1]
+        tmp = out + f".tmp{os.getpid()}"
+        cmd = cmd[:cmd.index("-o") + 1] + [tmp] + cmd[cmd.index("-o") + 2:]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
+            if os.path.exists(tmp):
+                os.remove(tmp)
             raise RuntimeError(f"nvcc failed: {' '.join(cmd)}\n{res.stdout}\n{res.stderr}")
+        os.replace(tmp, out)
         return res.stderr
 
     if jobs:
@@ -77,10 +86,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
                     print(log, file=sys.stderr)
     if force or jobs or _stale(LIB, objs):
         libdir = os.path.join(_cuda_home(), "lib64")
-        tmp = LIB + f".tmp{os.getpid()}"
-        run([nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
+        run([nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", LIB, *objs,
              "-Xlinker", f"-rpath,{libdir}"])
-        os.replace(tmp, LIB)
     return LIB
 
 
