@@ -294,9 +294,11 @@ def run_ours(args):
     import torch.distributed as dist
 
     rank, world, local = dist_env()
+    # the rank's device first: the process group's barriers and reductions
+    # then run on it rather than on device 0
+    torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
     from __graft_entry__ import build
     build()
     import paper_2209_12310_gb300 as ch
