@@ -146,3 +146,19 @@ def test_kernel_rooflines_pick_the_slowest_kernel_with_bytes():
     assert roof["achieved"] == pytest.approx(2e6 / 0.3e-3 / 1e9)
     assert per["main_filter"]["achieved_gbs"] == pytest.approx(8e6 / 0.1e-3 / 1e9)
     assert roof["traffic"] is None
+
+
+def test_batch_trace_summary():
+    """The server trace (8 values per batch, as ch_server_trace writes them)
+    reduced to percentiles and the slowest 1 % of the batches."""
+    assert bench.batch_trace_summary([]) is None
+    rows = []
+    for i in range(200):   # batch i: i % 10 + 1 requests, host time i ms, one set redone every 50
+        rows.append((float(i), float(i % 10 + 1), 1000.0 * (i + 1), 0.5, 0.25, 0.1, float(i), float(i % 50 == 0)))
+    s = bench.batch_trace_summary(rows)
+    assert s["batches"] == 200 and s["sets_redone"] == 4
+    assert s["copy_in_ms_p50"] == pytest.approx(0.5) and s["hull_ms_p99"] == pytest.approx(0.25)
+    assert s["host_ms_p50"] == pytest.approx(99.5) and s["requests_p99"] == pytest.approx(10.0)
+    # the slowest 1 %: host time at or above its 99th percentile (197.01 ms): batches 198 and 199
+    assert s["slowest_1pct_mean"]["host_ms"] == pytest.approx(198.5)
+    assert s["slowest_1pct_mean"]["points"] == pytest.approx(1000.0 * 199.5)
