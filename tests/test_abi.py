@@ -87,3 +87,28 @@ def test_workspace_size_is_linear(native):
     b = ch.ch_workspace_bytes(2_000_000)
     assert 20 * 1_000_000 < a < 80 * 1_000_000
     assert 1.8 < b / a < 2.2
+
+
+def test_no_fallback_without_the_library():
+    """Without libconvhull.so the binding raises instead of computing
+    anything, and the tensor helpers refuse host tensors (no CPU path)."""
+    import subprocess
+    import sys
+    code = (
+        "import paper_2209_12310_gb300 as ch, paper_2209_12310_gb300._native as n\n"
+        "n.LIB_PATH = '/nonexistent/libconvhull.so'\n"
+        "try:\n"
+        "    ch.load()\n"
+        "except RuntimeError as e:\n"
+        "    assert 'not built' in str(e)\n"
+        "else:\n"
+        "    raise SystemExit('loaded a library that does not exist')\n"
+        "import torch\n"
+        "try:\n"
+        "    ch.hull(torch.zeros((3, 2)))\n"
+        "except TypeError:\n"
+        "    print('refused')\n"
+    )
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=ROOT, timeout=120)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == "refused"
